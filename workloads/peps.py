@@ -1,0 +1,88 @@
+"""PEPS structure on a graph: which leg of which site tensor meets which.
+
+Structure only (no arithmetic).  Site tensors are created in site order with
+the arrows of every bond pointing from the later site to the earlier one and
+the +/- labels aligned with the arrows (Sec. IV.B): on bond (s, t) with
+s < t, site s holds the incoming ('-', dual 1) leg and site t the outgoing
+('+', dual 0) leg.  The physical leg is last and outgoing.
+"""
+from __future__ import annotations
+
+from .gen import random_blocks
+
+__all__ = ["peps_layout", "random_peps", "double_layer_tree", "site_sweep_tree"]
+
+
+def peps_layout(n, edges, D, phys=(2, 2)):
+    """Per-site leg lists and the ket-layer bonds.
+
+    ``D`` is a pair (d_even, d_odd) for every virtual bond (or a dict edge ->
+    pair).  Returns ``{"n", "legs": [[(d0, d1, dual), ...] per site],
+    "nbrs": [[neighbour per virtual leg] per site], "bonds": [(s, ks, t, kt)],
+    "edges"}``.
+    """
+    nbrs = [[] for _ in range(n)]
+    for a, b in edges:
+        nbrs[a].append(b)
+        nbrs[b].append(a)
+    for s in range(n):
+        nbrs[s].sort()
+    legs = []
+    for s in range(n):
+        ls = []
+        for t in nbrs[s]:
+            e = (min(s, t), max(s, t))
+            d = D[e] if isinstance(D, dict) else D
+            ls.append((int(d[0]), int(d[1]), 1 if s < t else 0))
+        ls.append((int(phys[0]), int(phys[1]), 0))
+        legs.append(ls)
+    bonds = []
+    for a, b in sorted(edges):
+        bonds.append((a, nbrs[a].index(b), b, nbrs[b].index(a)))
+    return {"n": n, "legs": legs, "nbrs": nbrs, "bonds": bonds, "edges": sorted(edges)}
+
+
+def random_peps(layout, seed, scale=1.0):
+    """Even-parity site tensors with i.i.d. N(0, scale^2) allowed entries, as
+    lists of (bits, block) per site."""
+    return [random_blocks(layout["legs"][s], 0, 7919 * seed + 31 * s + 5, scale) for s in range(layout["n"])]
+
+
+def double_layer_tree(n, site_tree, op_sites=()):
+    """SSA tree over a double-layer network with ids kets 0..n-1, bras n..2n-1
+    and (when ``op_sites`` is not empty) the operator at 2n.
+
+    First every site's ket and bra are merged (the operator is merged into the
+    ket of its first site before that site's bra); the merged site tensors then
+    follow ``site_tree``, an SSA tree over n site nodes.
+    """
+    pairs = []
+    nt = 2 * n + (1 if op_sites else 0)
+    nxt = nt
+    site_id = {}
+    for s in range(n):
+        k = s
+        if op_sites and s == op_sites[0]:
+            pairs.append((2 * n, k))
+            k = nxt
+            nxt += 1
+        pairs.append((k, n + s))
+        site_id[s] = nxt
+        nxt += 1
+    remap = dict(site_id)
+    for q, (a, b) in enumerate(site_tree):
+        pairs.append((remap[a], remap[b]))
+        remap[n + q] = nxt
+        nxt += 1
+    return pairs
+
+
+def site_sweep_tree(order):
+    """Site-level sequential tree: merge order[0], order[1], ... one by one."""
+    n = len(order)
+    pairs = []
+    cur = order[0]
+    for s, t in enumerate(order[1:]):
+        pairs.append((cur, t))
+        cur = n + s
+    return pairs
