@@ -1,0 +1,226 @@
+/*
+ * ftn.h -- C ABI of libftn, Z2-graded (fermionic) block-sparse tensor
+ * contraction on one NVIDIA GB300 (sm_103a).
+ *
+ * Method: Gao, Zhai, Gray, Peng, Park, Liu, Kjonstad, Chan, "Fermionic tensor
+ * network contraction for arbitrary geometries", arXiv:2410.02215.
+ *
+ * Conventions used by every entry point
+ * -------------------------------------
+ * Leg: sector dimensions (d_even, d_odd) and a dual flag.  dual = 1 marks an
+ *   incoming ('-') leg, dual = 0 an outgoing ('+') leg (Sec. II.A, symmetry
+ *   rule with H = 2).  A bond's arrow runs from its '+' leg to its '-' leg.
+ *   Dense index i of a leg has parity [i >= d_even] (even states first).
+ * Tensor: rank r <= FTN_MAX_RANK, total parity p in {0, 1} (Sec. II.B).
+ *   Its data is one contiguous device buffer of 2^(r-1) blocks (one block of
+ *   one element for r = 0 and p = 0; none for r = 0 and p = 1).  Block b has
+ *   the parity bitmask m (bit k = sector of leg k) with popcount(m) = p mod 2
+ *   and b = m >> 1; blocks are stored in increasing b, each block dense and
+ *   row-major in leg order (last leg fastest).  Zero-size blocks take no
+ *   space.  Element type is FP64 or FP32.
+ * Pairwise contraction op(X, Y) over leg pairs (ax[i], ay[i]): X's contracted
+ *   legs are moved to its end in the order ax, Y's to its front in mirror
+ *   order, each move a fermionic transposition with sign (-1)^{p_i p_j} per
+ *   swapped pair (Eqs. transposition, standardcontract); a pair whose X leg
+ *   is outgoing ('+') is contracted against its arrow and carries the bond
+ *   parity (-1)^p (locally ordered formalism, Eq. fermionictn2 and the text
+ *   after it).  Result legs: X's free legs in order, then Y's.  Contracted
+ *   legs must have equal (d_even, d_odd) and opposite duals.
+ * Streams: every call is asynchronous on the context's CUDA stream unless
+ *   stated otherwise.  Errors are returned as ftn_status; no exception
+ *   crosses the ABI; ftn_last_error() gives a message for the calling thread.
+ * Ownership: the caller owns the tensors it creates or wraps and releases
+ *   them with ftn_tensor_free.  Library-allocated buffers come from the
+ *   context's allocator callbacks (or cudaMallocAsync on the context stream
+ *   when none are given).
+ */
+#ifndef FTN_H
+#define FTN_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define FTN_MAX_RANK 16
+
+#if defined(__GNUC__)
+#define FTN_API __attribute__((visibility("default")))
+#else
+#define FTN_API
+#endif
+
+typedef struct ftn_ctx_s* ftn_ctx;
+typedef struct ftn_tensor_s* ftn_tensor;
+
+typedef enum {
+  FTN_OK = 0,
+  FTN_EINVAL = -1,       /* bad argument (null pointer, rank, axes, perm)      */
+  FTN_ESHAPE = -2,       /* contracted legs differ in (d_even, d_odd)           */
+  FTN_EPARITY = -3,      /* parity out of {0,1} or inconsistent                 */
+  FTN_EDUAL = -4,        /* contracted legs with equal duals                    */
+  FTN_ENOMEM = -5,       /* allocator returned NULL                             */
+  FTN_ECUDA = -6,        /* CUDA runtime error                                  */
+  FTN_ETIMEOUT = -7,     /* a device-side bounded wait gave up                  */
+  FTN_EUNSUPPORTED = -8  /* dtype/precision combination not provided           */
+} ftn_status;
+
+typedef enum { FTN_F64 = 0, FTN_F32 = 1 } ftn_dtype;
+
+/* Arithmetic of the sector GEMMs.  FTN_PREC_F64 needs FP64 tensors (DFMA).
+ * The others need FP32 tensors and run on the tcgen05 tensor cores with FP32
+ * accumulation: TF32 and BF16 round each operand once; TF32X3 and BF16X3
+ * split each operand x = hi + lo and sum hi*hi + hi*lo + lo*hi. */
+typedef enum {
+  FTN_PREC_F64 = 0,
+  FTN_PREC_TF32 = 1,
+  FTN_PREC_BF16 = 2,
+  FTN_PREC_TF32X3 = 3,
+  FTN_PREC_BF16X3 = 4
+} ftn_prec;
+
+typedef void* (*ftn_alloc_fn)(size_t bytes, void* user);
+typedef void (*ftn_free_fn)(void* ptr, void* user);
+
+/* ---- context ----------------------------------------------------------- */
+
+/* Create a context bound to the current CUDA device and to `cuda_stream`
+ * (a cudaStream_t, NULL = legacy default stream).  `alloc`/`free` (both or
+ * neither) supply device memory for library-owned buffers; `user` is passed
+ * back to them.  Returns FTN_ECUDA if no device is usable. */
+FTN_API ftn_status ftn_ctx_create(void* cuda_stream, ftn_alloc_fn alloc, ftn_free_fn free_fn, void* user,
+                          ftn_ctx* out);
+FTN_API ftn_status ftn_ctx_destroy(ftn_ctx ctx);
+/* Change the stream later calls are issued on. */
+FTN_API ftn_status ftn_ctx_set_stream(ftn_ctx ctx, void* cuda_stream);
+/* Synchronise the context stream and report a device-side error recorded
+ * since the last call (FTN_ETIMEOUT after a bounded wait gave up). */
+FTN_API ftn_status ftn_ctx_synchronize(ftn_ctx ctx);
+/* Number of kernels this context has launched so far. */
+FTN_API int64_t ftn_ctx_launch_count(ftn_ctx ctx);
+/* Message of the last failing call on this thread (never NULL). */
+FTN_API const char* ftn_last_error(void);
+
+/* ---- tensors (sector table + device buffer), Sec. II.A-II.B --------------- */
+
+/* Library-allocated tensor, contents undefined.  d_even/d_odd/dual have
+ * `rank` entries (ignored for rank 0); parity is 0 or 1. */
+FTN_API ftn_status ftn_tensor_create(ftn_ctx ctx, int rank, const int32_t* d_even, const int32_t* d_odd,
+                             const uint8_t* dual, int parity, ftn_dtype dtype, ftn_tensor* out);
+/* Same metadata over a caller-owned device buffer `dev_data` (borrowed: the
+ * caller keeps it alive and frees it; it must hold ftn_tensor_numel
+ * elements and be aligned to the element size). */
+FTN_API ftn_status ftn_tensor_wrap(ftn_ctx ctx, int rank, const int32_t* d_even, const int32_t* d_odd,
+                           const uint8_t* dual, int parity, ftn_dtype dtype, void* dev_data,
+                           ftn_tensor* out);
+FTN_API ftn_status ftn_tensor_free(ftn_tensor t);
+/* Metadata: any output pointer may be NULL; arrays need `rank` entries. */
+FTN_API ftn_status ftn_tensor_info(ftn_tensor t, int* rank, int32_t* d_even, int32_t* d_odd, uint8_t* dual,
+                           int* parity, ftn_dtype* dtype, int64_t* numel, void** dev_data);
+/* Element offsets and parity bitmasks of the 2^(rank-1) blocks in storage
+ * order (arrays sized by ftn_tensor_info's rank; *nblocks receives the count). */
+FTN_API ftn_status ftn_tensor_block_offsets(ftn_tensor t, int64_t* offsets, uint32_t* masks, int* nblocks);
+/* Copy numel elements between a host buffer (pinned or pageable) and the
+ * tensor, asynchronously on the context stream. */
+FTN_API ftn_status ftn_tensor_upload(ftn_ctx ctx, ftn_tensor t, const void* host);
+FTN_API ftn_status ftn_tensor_download(ftn_ctx ctx, ftn_tensor t, void* host);
+
+/* ---- sign-permute (Eq. transposition) ------------------------------------ */
+
+/* Fermionic transposition: out leg u = in leg perm[u]; every block is moved
+ * and multiplied by (-1)^{sum of p_a p_b over leg pairs whose order the
+ * permutation inverts}.  *out is created (same dtype) unless it is non-NULL
+ * on entry, in which case it must already have the permuted metadata. */
+FTN_API ftn_status ftn_tensor_transpose(ftn_ctx ctx, ftn_tensor t, const int* perm, ftn_tensor* out);
+/* Hermitian conjugate of one tensor (Sec. II.C): leg order reversed, duals
+ * flipped, no sign (real data). */
+FTN_API ftn_status ftn_tensor_dagger(ftn_ctx ctx, ftn_tensor t, ftn_tensor* out);
+
+/* ---- fermionic tensordot (Eqs. standardcontract, fermiswap, Sec. IV.A) --- */
+
+/* C = op(A, B) over n leg pairs (axes_a[i], axes_b[i]), with the bond parity
+ * (-1)^p applied additionally on every leg k of A with bit k of flip_a set
+ * and every leg k of B with bit k of flip_b set (the g tensors a global-order
+ * move accumulates, Sec. II.C).  If out_perm is not NULL the result is
+ * fermionically transposed to out leg u = result leg out_perm[u].  A and B
+ * must have the same dtype; prec selects the GEMM arithmetic.  *C is created
+ * unless non-NULL on entry (then it must match the result's metadata).
+ * n = 0 gives the outer product. */
+FTN_API ftn_status ftn_tensordot(ftn_ctx ctx, ftn_tensor A, ftn_tensor B, int n, const int* axes_a,
+                         const int* axes_b, uint64_t flip_a, uint64_t flip_b, const int* out_perm,
+                         ftn_prec prec, ftn_tensor* C);
+
+/* ---- bond compression (Sec. II.A symmetric QR/SVD, Sec. III) ------------- */
+
+typedef struct {
+  int kept[2];          /* new bond (d_even, d_odd)                           */
+  int rank[2];          /* numerical rank of each bond-parity sector          */
+  double discarded_sq;  /* sum of the squared discarded singular values       */
+  double total_sq;      /* sum of all squared singular values                 */
+  double s_max;         /* largest singular value                             */
+  double s_cut;         /* smallest kept singular value (0 if none kept)      */
+  double s_next;        /* largest discarded singular value (0 if none)       */
+} ftn_compress_info;
+
+/* Compress the bond formed by legs axes_x of *X paired with axes_y of *Y to at
+ * most chi states: per bond-parity sector the R factors of X = [free | bond]
+ * and of Y^T = [free | bond]^T, the core M = R_X R_Y^T, its SVD, the chi
+ * largest singular values pooled over both sectors (ties to the even sector,
+ * then the lower index), and the new pair X' = [free_X | new], Y' = [new |
+ * free_Y] with op(X', Y') the truncated op(X, Y) (the new leg is incoming on
+ * X' and outgoing on Y').  Singular values below 1e-14 * s_max are numerical
+ * zeros and never kept.  `arrows` = 0 contracts the bond without the arrow
+ * parity (plain ordered contraction F(XY) of the global formalism).  *X and
+ * *Y are replaced by new library-owned tensors and the old ones freed.  FP64
+ * arithmetic throughout.  Synchronises once (kept dimensions are data). */
+FTN_API ftn_status ftn_compress(ftn_ctx ctx, ftn_tensor* X, ftn_tensor* Y, int n, const int* axes_x,
+                        const int* axes_y, int chi, int arrows, ftn_compress_info* info);
+
+/* ---- contraction tree executor (Fig. 1, Secs. II.C-II.D, III) ------------ */
+
+typedef enum { FTN_POLICY_EXACT = 0, FTN_POLICY_EARLY = 1, FTN_POLICY_LATE = 2 } ftn_policy;
+
+typedef struct {
+  int n_tensors;
+  const ftn_tensor* tensors; /* borrowed, left untouched                       */
+  int n_bonds;
+  const int32_t* bonds;      /* 4 per bond: tensor1, leg1, tensor2, leg2        */
+  const int32_t* positions;  /* NULL: locally ordered; else global positions    */
+} ftn_network;
+
+typedef struct {
+  int n_steps;               /* n_tensors - 1                                  */
+  const int32_t* pairs;      /* 2 per step, SSA ids: inputs 0..n-1, step s -> n+s */
+  ftn_policy policy;
+  int chi;                   /* bond cap for EARLY/LATE                        */
+} ftn_tree;
+
+/* Contract a closed network along the tree.  Locally ordered when
+ * positions == NULL (bond parity when a bond is contracted against its
+ * arrow); globally ordered otherwise (the later tensor is moved past the
+ * tensors between, each shared bond passed carrying g and each odd tensor
+ * passed a phase, then plain F).  Late policy compresses, just before a
+ * step, every other bond of both operands whose dimension exceeds chi;
+ * early policy compresses the new tensor's bonds right after the step;
+ * neighbours in increasing id.  After every step the new tensor is divided
+ * by its largest |entry| and the natural log accumulated: value =
+ * (*mantissa) * exp(*log_scale).  Synchronises at the end. */
+FTN_API ftn_status ftn_contract(ftn_ctx ctx, const ftn_network* net, const ftn_tree* tree, ftn_prec prec,
+                        double* mantissa, double* log_scale);
+
+/* ---- Hubbard terms (Eq. fermi-hubbard-ham) -------------------------------- */
+
+/* Even operator tensors for <Psi| h_t |Psi> (physical leg (2,2): 0 = |0>,
+ * 1 = |up dn>, 2 = |up>, 3 = |dn>).  kind 0: hopping -t sum_s (c+_is c_js +
+ * h.c.) on a bond i < j, legs [i', j', j, i] with duals (0, 0, 1, 1); entries
+ * are matrix elements in the ordered creation-string basis with site i
+ * first.  kind 1: on-site U n_up n_dn, legs [i', i], duals (0, 1). */
+FTN_API ftn_status ftn_hubbard_term(ftn_ctx ctx, int kind, double t, double u, ftn_dtype dtype,
+                            ftn_tensor* out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FTN_H */

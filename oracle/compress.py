@@ -8,7 +8,7 @@ import numpy as np
 
 from .graded import GTensor, _check_pairs, flip_legs, index_parity, transpose
 
-__all__ = ["compress", "matricize_pair"]
+__all__ = ["compress", "matricize_pair", "transpose_sign_at", "contract_sampled"]
 
 
 def _multi_parity(legs):
@@ -122,3 +122,44 @@ def compress(x, y, ax, ay, chi, arrows=True):
         "gap": gap,
     }
     return GTensor(xnew.reshape(xs), xlegs, px), GTensor(ynew.reshape(ys), ylegs, py), info
+
+
+def transpose_sign_at(legs, perm, index):
+    """Sign of Eq. (transposition) for one dense index tuple ``index`` of the
+    *input* legs when permuted to out leg u = in leg perm[u]."""
+    par = [int(index[k] >= legs[k][0]) for k in range(len(legs))]
+    s = 0
+    r = len(perm)
+    for u in range(r):
+        for v in range(u + 1, r):
+            if perm[u] > perm[v]:
+                s ^= par[perm[u]] & par[perm[v]]
+    return -1.0 if s else 1.0
+
+
+def contract_sampled(x, y, ax, ay, out_perm, n_samples, seed, arrows=True):
+    """Selected entries of transpose(op(X, Y), out_perm), each computed as one
+    row of [free | bond] X times one column of [bond | free] Y (the
+    matricisation of Eq. standardcontract) times the transposition sign.
+
+    Returns (indices into the permuted result, values)."""
+    xm, ym, fx, fy, _, _, _ = matricize_pair(x, y, ax, ay, arrows=arrows)
+    legs = [x.legs[k] for k in fx] + [y.legs[k] for k in fy]
+    dims = [a + b for a, b, _ in legs]
+    nfx = len(fx)
+    r = len(legs)
+    perm = list(range(r)) if out_perm is None else [int(p) for p in out_perm]
+    g = np.random.Generator(np.random.PCG64(seed))
+    idx_out = []
+    vals = []
+    total_par = x.parity ^ y.parity
+    while len(vals) < n_samples:
+        idx = [int(g.integers(d)) for d in dims]
+        if sum(int(idx[k] >= legs[k][0]) for k in range(r)) % 2 != total_par:
+            continue  # structurally zero entry; sample allowed ones only
+        row = int(np.ravel_multi_index(idx[:nfx], dims[:nfx])) if nfx else 0
+        col = int(np.ravel_multi_index(idx[nfx:], dims[nfx:])) if r > nfx else 0
+        v = float(xm[row] @ ym[:, col]) * transpose_sign_at(legs, perm, idx)
+        idx_out.append(tuple(idx[p] for p in perm))
+        vals.append(v)
+    return idx_out, np.array(vals)

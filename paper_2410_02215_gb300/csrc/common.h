@@ -1,0 +1,173 @@
+// Internal declarations of libftn shared by the host runtime and the kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cstring>
+#include <map>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "../../include/ftn.h"
+
+namespace ftn {
+
+constexpr int MAXR = FTN_MAX_RANK;
+
+// Device-side error codes written into the context's error word.
+constexpr int DEV_ERR_TIMEOUT = 1;
+
+// ---- sign-permute job (one source block -> one destination layout) --------
+// The source block is dense row-major.  Legs are split in three groups:
+//   I: a suffix of the source legs (contiguous in the source, product PI),
+//   O: legs with the smallest destination strides not in I (product PO),
+//   B: the rest (product PB).
+// One CTA tile covers TI x TO elements of one batch index.
+constexpr int PERM_TI = 32;
+constexpr int PERM_TO = 32;
+
+struct PermJob {
+  int64_t src_off;   // elements from the source base
+  int64_t dst_off;   // elements from the destination base
+  int64_t tile_begin;
+  int64_t PB;
+  int32_t PI, PO;
+  int32_t tiles_i, tiles_o;
+  int32_t nI, nO, nB;
+  int32_t sign;      // +1 or -1
+  int32_t store_fast_i;  // destination contiguous along the I index
+  int32_t pad_;
+  int32_t dim[MAXR];     // I legs (source order), then O legs, then B legs
+  int64_t sstr[MAXR];    // source strides (unused for I legs)
+  int64_t dstr[MAXR];    // destination strides
+};
+
+// Output conversions of the sign-permute kernel.
+enum PermMode {
+  PERM_SAME = 0,      // same element type as the input
+  PERM_TF32 = 1,      // FP32 -> TF32-rounded FP32
+  PERM_TF32X2 = 2,    // FP32 -> TF32 hi + TF32 lo (two FP32 outputs)
+  PERM_BF16 = 3,      // FP32 -> BF16
+  PERM_BF16X2 = 4     // FP32 -> BF16 hi + BF16 lo
+};
+
+// ---- grouped sector GEMM problem: C[m, n] = sum_k A[m, k] B[n, k] ------------
+struct GemmProb {
+  int64_t tile_begin;
+  int64_t a_off;   // element offset of the first A row (FP64 path)
+  int64_t b_off;
+  int64_t c_off;   // element offset of the output block
+  int32_t M, N, K;
+  int32_t pi;      // fused-matrix pair (bond parity sector)
+  int32_t lda, ldb, ldc;
+  int32_t a_row0, b_row0;  // first row inside the fused pi-matrices (TMA)
+  int32_t tiles_m, tiles_n;
+  int32_t pad_;
+};
+
+}  // namespace ftn
+
+// ---- public opaque types -----------------------------------------------------
+struct ftn_ctx_s {
+  cudaStream_t stream = nullptr;
+  ftn_alloc_fn alloc = nullptr;
+  ftn_free_fn free_fn = nullptr;
+  void* user = nullptr;
+  int device = 0;
+  int num_sms = 0;
+  int* dev_err = nullptr;  // device error word (zeroed at creation)
+  int64_t launches = 0;
+  // grow-only workspace arena (reused by every call on this context)
+  void* ws = nullptr;
+  size_t ws_bytes = 0;
+};
+
+struct ftn_tensor_s {
+  ftn_ctx ctx = nullptr;
+  int rank = 0;
+  int32_t d0[FTN_MAX_RANK] = {};
+  int32_t d1[FTN_MAX_RANK] = {};
+  uint8_t dual[FTN_MAX_RANK] = {};
+  int parity = 0;
+  ftn_dtype dtype = FTN_F64;
+  int64_t numel = 0;
+  std::vector<int64_t> offsets;  // per block (index = mask >> 1)
+  void* data = nullptr;
+  bool owned = false;
+};
+
+namespace ftn {
+
+// error handling (thread-local message)
+ftn_status set_error(ftn_status st, const std::string& msg);
+ftn_status cuda_error(cudaError_t e, const char* where);
+#define FTN_CUDA(call)                                         \
+  do {                                                         \
+    cudaError_t _e = (call);                                   \
+    if (_e != cudaSuccess) return ::ftn::cuda_error(_e, #call); \
+  } while (0)
+#define FTN_TRY(call)                      \
+  do {                                     \
+    ftn_status _s = (call);                \
+    if (_s != FTN_OK) return _s;           \
+  } while (0)
+
+size_t dtype_size(ftn_dtype d);
+void* dev_alloc(ftn_ctx ctx, size_t bytes);
+void dev_free(ftn_ctx ctx, void* p);
+// Workspace of at least `bytes` (contents undefined), valid until the next
+// call that asks for workspace on the same context.
+void* workspace(ftn_ctx ctx, size_t bytes);
+
+inline int popc(uint32_t x) { return __builtin_popcount(x); }
+inline uint32_t block_mask(int rank, int parity, int64_t b) {
+  if (rank == 0) return 0;
+  uint32_t hi = (uint32_t)b << 1;
+  return hi | (uint32_t)((popc(hi) + parity) & 1);
+}
+inline int64_t nblocks(int rank, int parity) {
+  if (rank == 0) return parity == 0 ? 1 : 0;
+  return (int64_t)1 << (rank - 1);
+}
+inline int64_t leg_dim(const ftn_tensor_s* t, int k, uint32_t mask) {
+  return ((mask >> k) & 1) ? t->d1[k] : t->d0[k];
+}
+int64_t block_size(const ftn_tensor_s* t, uint32_t mask);
+
+// creates a library-owned tensor with the given metadata
+ftn_status make_tensor(ftn_ctx ctx, int rank, const int32_t* d0, const int32_t* d1, const uint8_t* dual,
+                       int parity, ftn_dtype dtype, ftn_tensor* out);
+bool same_meta(const ftn_tensor_s* a, int rank, const int32_t* d0, const int32_t* d1, const uint8_t* dual,
+               int parity, ftn_dtype dtype);
+
+// Permute-job builder: one source block (dims in source leg order, source
+// contiguous row-major) to a destination with per-leg strides.
+void add_perm_job(std::vector<PermJob>& jobs, int64_t& tiles, int rank, const int64_t* dims,
+                  const int64_t* dst_strides, int64_t src_off, int64_t dst_off, int sign);
+
+// kernel launchers (asynchronous on ctx->stream)
+ftn_status launch_permute(ftn_ctx ctx, const PermJob* d_jobs, int njobs, int64_t tiles, const void* src,
+                          void* dst0, void* dst1, ftn_dtype in_type, int mode);
+ftn_status launch_gemm_f64(ftn_ctx ctx, const GemmProb* d_probs, int nprobs, int64_t tiles, const double* a,
+                           const double* b, double* c);
+
+struct TcOperands {
+  // fused pi-matrices: rows x ldk elements, K-major; lo only for split modes
+  const void* a_hi[2];
+  const void* a_lo[2];
+  const void* b_hi[2];
+  const void* b_lo[2];
+  int64_t a_rows[2], b_rows[2];
+  int32_t kdim[2], ldk[2];
+};
+ftn_status launch_gemm_tc(ftn_ctx ctx, ftn_prec prec, const TcOperands& ops, const GemmProb* d_probs, int nprobs,
+                          int64_t tiles, int bn, float* c);
+int tc_pick_bn(int max_n, ftn_prec prec);
+int64_t tc_tiles_for(int M, int N, int bn);
+
+ftn_status upload_table(ftn_ctx ctx, const void* host, size_t bytes, void** dev);
+void clear_plan_caches(ftn_ctx ctx);
+
+}  // namespace ftn

@@ -1,0 +1,349 @@
+// Grouped sector GEMM on the tcgen05 tensor cores (sm_103a).
+//
+// One persistent launch covers every (row block, column block) problem of a
+// fermionic contraction: C_blk[m, n] = sum_k A_pi[row0 + m, k] B_pi[col0 + n, k]
+// where A_pi / B_pi are the fused sector matrices of bond parity pi (K-major,
+// produced by the sign-permute kernel).  Warp roles per CTA:
+//   warp 0    TMA producer: 128 x 32 (TF32) or 128 x 64 (BF16) A tiles and
+//             BN x same B tiles into a STAGES-deep shared-memory ring;
+//   warp 1    MMA issuer: tcgen05.mma (M = 128, N = BN) into one of two TMEM
+//             accumulators, tcgen05.commit releases ring slots;
+//   warps 2-5 epilogue: tcgen05.ld of the accumulator (one row per thread),
+//             FP32 stores into the output block.
+// Split modes (TF32X3 / BF16X3) load hi and lo planes and issue
+// hi*hi + hi*lo + lo*hi into the same accumulator.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include "common.h"
+#include "ptx.cuh"
+
+namespace ftn {
+
+constexpr int TC_BM = 128;
+constexpr int TC_THREADS = 192;
+
+struct TcParams {
+  CUtensorMap a_hi[2];
+  CUtensorMap b_hi[2];
+  CUtensorMap a_lo[2];
+  CUtensorMap b_lo[2];
+  const GemmProb* probs;
+  float* C;
+  int* err;
+  int64_t tiles;
+  int nprobs;
+};
+
+template <bool BF16, bool SPLIT, int BN>
+struct TcCfg {
+  static constexpr int A_BYTES = TC_BM * 128;
+  static constexpr int B_BYTES = BN * 128;
+  static constexpr int OPS = SPLIT ? 2 : 1;
+  static constexpr int STAGE_BYTES = (A_BYTES + B_BYTES) * OPS;
+  static constexpr int STAGES_RAW = (200 * 1024) / STAGE_BYTES;
+  static constexpr int STAGES = STAGES_RAW > 8 ? 8 : STAGES_RAW;
+  static constexpr int SMEM = STAGES * STAGE_BYTES + 1024 + 256;
+  static constexpr int TMEM_COLS = (2 * BN < 32) ? 32 : 2 * BN;
+  static constexpr int KB = BF16 ? 64 : 32;  // K elements per stage (128 B)
+  static constexpr uint32_t IDESC = idesc_f32acc(TC_BM, BN, BF16 ? 1u : 2u);
+  static_assert(STAGES >= 2, "shared memory ring too shallow");
+};
+
+__device__ __forceinline__ int tc_find_prob(const GemmProb* probs, int nprobs, int64_t t) {
+  int lo = 0, hi = nprobs - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (probs[mid].tile_begin <= t)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  return lo;
+}
+
+template <bool BF16, bool SPLIT, int BN>
+__global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_constant__ TcParams P) {
+  using Cfg = TcCfg<BF16, SPLIT, BN>;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + Cfg::STAGES * Cfg::STAGE_BYTES);
+  uint64_t* empty = full + Cfg::STAGES;
+  uint64_t* tfull = empty + Cfg::STAGES;
+  uint64_t* tempty = tfull + 2;
+  uint64_t* drain = tempty + 2;
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(drain + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < Cfg::STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int a = 0; a < 2; ++a) {
+      mbar_init(&tfull[a], 1);
+      mbar_init(&tempty[a], 4);
+    }
+    mbar_init(drain, 1);
+    fence_mbar_init();
+  }
+  if (warp == 1) {
+    tmem_alloc(tslot, Cfg::TMEM_COLS);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tslot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // ---------------- TMA producer ----------------
+      int stage = 0;
+      uint32_t phase = 0;
+      uint32_t issued = 0, lastpar = 0;
+      bool ok = true;
+      for (int64_t t = blockIdx.x; t < P.tiles && ok; t += gridDim.x) {
+        const GemmProb& p = P.probs[tc_find_prob(P.probs, P.nprobs, t)];
+        const int64_t local = t - p.tile_begin;
+        const int m0 = (int)(local / p.tiles_n) * TC_BM;
+        const int n0 = (int)(local % p.tiles_n) * BN;
+        const int nk = (p.K + Cfg::KB - 1) / Cfg::KB;
+        const int pi = p.pi;
+        for (int kb = 0; kb < nk; ++kb) {
+          if (!mbar_wait(&empty[stage], phase ^ 1, P.err)) {
+            ok = false;
+            break;
+          }
+          uint8_t* sa = smem + stage * Cfg::STAGE_BYTES;
+          mbar_expect_tx(&full[stage], Cfg::STAGE_BYTES);
+          tma_load_2d(sa, &P.a_hi[pi], kb * Cfg::KB, p.a_row0 + m0, &full[stage]);
+          tma_load_2d(sa + Cfg::A_BYTES, &P.b_hi[pi], kb * Cfg::KB, p.b_row0 + n0, &full[stage]);
+          if constexpr (SPLIT) {
+            tma_load_2d(sa + Cfg::A_BYTES + Cfg::B_BYTES, &P.a_lo[pi], kb * Cfg::KB, p.a_row0 + m0, &full[stage]);
+            tma_load_2d(sa + 2 * Cfg::A_BYTES + Cfg::B_BYTES, &P.b_lo[pi], kb * Cfg::KB, p.b_row0 + n0,
+                        &full[stage]);
+          }
+          issued |= 1u << stage;
+          lastpar = (lastpar & ~(1u << stage)) | (phase << stage);
+          if (++stage == Cfg::STAGES) {
+            stage = 0;
+            phase ^= 1;
+          }
+        }
+      }
+      // wait for this CTA's own copies still in flight
+      for (int s = 0; s < Cfg::STAGES; ++s)
+        if (issued & (1u << s)) mbar_wait(&full[s], (lastpar >> s) & 1, P.err, false);
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // ---------------- MMA issuer ----------------
+      int stage = 0;
+      uint32_t phase = 0;
+      int acc = 0;
+      uint32_t acc_phase = 0;
+      bool ok = true;
+      for (int64_t t = blockIdx.x; t < P.tiles && ok; t += gridDim.x) {
+        const GemmProb& p = P.probs[tc_find_prob(P.probs, P.nprobs, t)];
+        const int nk = (p.K + Cfg::KB - 1) / Cfg::KB;
+        if (nk == 0) continue;
+        if (!mbar_wait(&tempty[acc], acc_phase ^ 1, P.err)) break;
+        tc_fence_after();
+        const uint32_t d = tmem + (uint32_t)(acc * BN);
+        for (int kb = 0; kb < nk; ++kb) {
+          if (!mbar_wait(&full[stage], phase, P.err)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t sa = smem_u32(smem + stage * Cfg::STAGE_BYTES);
+          const uint32_t sb = sa + Cfg::A_BYTES;
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            const uint64_t ad = sdesc_sw128(sa + 32 * j);
+            const uint64_t bd = sdesc_sw128(sb + 32 * j);
+            const uint32_t accum = (kb | j) != 0;
+            if constexpr (BF16)
+              mma_f16(d, ad, bd, Cfg::IDESC, accum);
+            else
+              mma_tf32(d, ad, bd, Cfg::IDESC, accum);
+            if constexpr (SPLIT) {
+              const uint32_t sal = sa + Cfg::A_BYTES + Cfg::B_BYTES;
+              const uint32_t sbl = sal + Cfg::A_BYTES;
+              const uint64_t adl = sdesc_sw128(sal + 32 * j);
+              const uint64_t bdl = sdesc_sw128(sbl + 32 * j);
+              if constexpr (BF16) {
+                mma_f16(d, ad, bdl, Cfg::IDESC, 1);
+                mma_f16(d, adl, bd, Cfg::IDESC, 1);
+              } else {
+                mma_tf32(d, ad, bdl, Cfg::IDESC, 1);
+                mma_tf32(d, adl, bd, Cfg::IDESC, 1);
+              }
+            }
+          }
+          mma_commit(&empty[stage]);
+          if (++stage == Cfg::STAGES) {
+            stage = 0;
+            phase ^= 1;
+          }
+        }
+        if (!ok) break;
+        mma_commit(&tfull[acc]);
+        acc ^= 1;
+        if (acc == 0) acc_phase ^= 1;
+      }
+      // every issued MMA has completed before TMEM is released
+      mma_commit(drain);
+      mbar_wait(drain, 0, P.err, false);
+    }
+  } else {
+    // ---------------- epilogue (warps 2..5) ----------------
+    const int q = warp & 3;
+    int acc = 0;
+    uint32_t acc_phase = 0;
+    for (int64_t t = blockIdx.x; t < P.tiles; t += gridDim.x) {
+      const GemmProb& p = P.probs[tc_find_prob(P.probs, P.nprobs, t)];
+      const int64_t local = t - p.tile_begin;
+      const int m0 = (int)(local / p.tiles_n) * TC_BM;
+      const int n0 = (int)(local % p.tiles_n) * BN;
+      const int nk = (p.K + Cfg::KB - 1) / Cfg::KB;
+      const int row = m0 + 32 * q + lane;
+      float* crow = P.C + p.c_off + (int64_t)row * p.ldc + n0;
+      const int ncols = p.N - n0 < BN ? p.N - n0 : BN;
+      if (nk == 0) {
+        if (row < p.M)
+          for (int c = 0; c < ncols; ++c) crow[c] = 0.0f;
+        continue;
+      }
+      if (!mbar_wait(&tfull[acc], acc_phase, P.err)) break;
+      tc_fence_after();
+      const uint32_t taddr = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(acc * BN);
+#pragma unroll 1
+      for (int c = 0; c < BN; c += 16) {
+        uint32_t r[16];
+        tmem_ld16(taddr + (uint32_t)c, r);
+        tmem_wait_ld();
+        if (row < p.M) {
+#pragma unroll
+          for (int jj = 0; jj < 16; ++jj)
+            if (c + jj < ncols) crow[c + jj] = __uint_as_float(r[jj]);
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&tempty[acc]);
+      acc ^= 1;
+      if (acc == 0) acc_phase ^= 1;
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tmem, Cfg::TMEM_COLS);
+  }
+}
+
+// ---- host side -------------------------------------------------------------------
+static PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+
+static bool encode_2d(CUtensorMap* m, const void* base, bool bf16, int64_t rows, int32_t kdim, int32_t ldk,
+                      int box_k, int box_rows) {
+  auto enc = get_encode();
+  if (!enc) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)kdim, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)ldk * (bf16 ? 2 : 4)};
+  cuuint32_t box[2] = {(cuuint32_t)box_k, (cuuint32_t)box_rows};
+  cuuint32_t es[2] = {1, 1};
+  CUresult r = enc(m, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
+                   const_cast<void*>(base), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                   CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+template <bool BF16, bool SPLIT, int BN>
+static ftn_status run(ftn_ctx ctx, const TcOperands& ops, const GemmProb* d_probs, int nprobs, int64_t tiles,
+                      float* c) {
+  using Cfg = TcCfg<BF16, SPLIT, BN>;
+  TcParams P;
+  std::memset(&P, 0, sizeof(P));
+  for (int pi = 0; pi < 2; ++pi) {
+    if (ops.a_rows[pi] <= 0 || ops.b_rows[pi] <= 0 || ops.kdim[pi] <= 0) continue;
+    bool ok = encode_2d(&P.a_hi[pi], ops.a_hi[pi], BF16, ops.a_rows[pi], ops.kdim[pi], ops.ldk[pi], Cfg::KB, TC_BM) &&
+              encode_2d(&P.b_hi[pi], ops.b_hi[pi], BF16, ops.b_rows[pi], ops.kdim[pi], ops.ldk[pi], Cfg::KB, BN);
+    if (SPLIT)
+      ok = ok &&
+           encode_2d(&P.a_lo[pi], ops.a_lo[pi], BF16, ops.a_rows[pi], ops.kdim[pi], ops.ldk[pi], Cfg::KB, TC_BM) &&
+           encode_2d(&P.b_lo[pi], ops.b_lo[pi], BF16, ops.b_rows[pi], ops.kdim[pi], ops.ldk[pi], Cfg::KB, BN);
+    if (!ok) return set_error(FTN_ECUDA, "cuTensorMapEncodeTiled failed");
+  }
+  P.probs = d_probs;
+  P.C = c;
+  P.err = ctx->dev_err;
+  P.tiles = tiles;
+  P.nprobs = nprobs;
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel<BF16, SPLIT, BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         Cfg::SMEM);
+    if (e != cudaSuccess) return cuda_error(e, "cudaFuncSetAttribute(tc_gemm)");
+    attr_set = true;
+  }
+  int64_t grid = tiles < ctx->num_sms ? tiles : ctx->num_sms;
+  tc_gemm_kernel<BF16, SPLIT, BN><<<(unsigned)grid, TC_THREADS, Cfg::SMEM, ctx->stream>>>(P);
+  ctx->launches += 1;
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_error(e, "tc_gemm_kernel launch");
+  return FTN_OK;
+}
+
+int tc_pick_bn(int max_n, ftn_prec prec) {
+  const bool split = prec == FTN_PREC_TF32X3 || prec == FTN_PREC_BF16X3;
+  const int cap = split ? 128 : 256;
+  int bn = 16;
+  while (bn < max_n && bn < cap) bn *= 2;
+  return bn;
+}
+
+int64_t tc_tiles_for(int M, int N, int bn) {
+  return (int64_t)((M + TC_BM - 1) / TC_BM) * ((N + bn - 1) / bn);
+}
+
+template <bool BF16, bool SPLIT>
+static ftn_status by_bn(ftn_ctx ctx, int bn, const TcOperands& ops, const GemmProb* d, int np, int64_t tiles,
+                        float* c) {
+  switch (bn) {
+    case 16: return run<BF16, SPLIT, 16>(ctx, ops, d, np, tiles, c);
+    case 32: return run<BF16, SPLIT, 32>(ctx, ops, d, np, tiles, c);
+    case 64: return run<BF16, SPLIT, 64>(ctx, ops, d, np, tiles, c);
+    case 128: return run<BF16, SPLIT, 128>(ctx, ops, d, np, tiles, c);
+    default:
+      if constexpr (!SPLIT) return run<BF16, SPLIT, 256>(ctx, ops, d, np, tiles, c);
+      return set_error(FTN_EINVAL, "bad tile width");
+  }
+}
+
+ftn_status launch_gemm_tc(ftn_ctx ctx, ftn_prec prec, const TcOperands& ops, const GemmProb* d_probs, int nprobs,
+                          int64_t tiles, int bn, float* c) {
+  if (nprobs == 0 || tiles == 0) return FTN_OK;
+  switch (prec) {
+    case FTN_PREC_TF32: return by_bn<false, false>(ctx, bn, ops, d_probs, nprobs, tiles, c);
+    case FTN_PREC_TF32X3: return by_bn<false, true>(ctx, bn, ops, d_probs, nprobs, tiles, c);
+    case FTN_PREC_BF16: return by_bn<true, false>(ctx, bn, ops, d_probs, nprobs, tiles, c);
+    case FTN_PREC_BF16X3: return by_bn<true, true>(ctx, bn, ops, d_probs, nprobs, tiles, c);
+    default: return set_error(FTN_EUNSUPPORTED, "precision has no tensor-core path");
+  }
+}
+
+}  // namespace ftn

@@ -1,0 +1,359 @@
+// Context, tensor objects (packed sector table), allocation and error handling.
+#include <algorithm>
+#include <cstdio>
+#include <mutex>
+
+#include "common.h"
+
+namespace ftn {
+
+static thread_local std::string g_last_error = "no error";
+
+ftn_status set_error(ftn_status st, const std::string& msg) {
+  g_last_error = msg;
+  return st;
+}
+
+ftn_status cuda_error(cudaError_t e, const char* where) {
+  return set_error(FTN_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+size_t dtype_size(ftn_dtype d) { return d == FTN_F64 ? 8 : 4; }
+
+void* dev_alloc(ftn_ctx ctx, size_t bytes) {
+  if (bytes == 0) bytes = 256;
+  if (ctx->alloc) return ctx->alloc(bytes, ctx->user);
+  void* p = nullptr;
+  if (cudaMallocAsync(&p, bytes, ctx->stream) != cudaSuccess) return nullptr;
+  return p;
+}
+
+void dev_free(ftn_ctx ctx, void* p) {
+  if (!p) return;
+  if (ctx->free_fn)
+    ctx->free_fn(p, ctx->user);
+  else
+    cudaFreeAsync(p, ctx->stream);
+}
+
+void* workspace(ftn_ctx ctx, size_t bytes) {
+  bytes = (bytes + 255) & ~(size_t)255;
+  if (bytes <= ctx->ws_bytes) return ctx->ws;
+  dev_free(ctx, ctx->ws);
+  size_t want = std::max(bytes, ctx->ws_bytes + ctx->ws_bytes / 2);
+  ctx->ws = dev_alloc(ctx, want);
+  ctx->ws_bytes = ctx->ws ? want : 0;
+  return ctx->ws;
+}
+
+int64_t block_size(const ftn_tensor_s* t, uint32_t mask) {
+  int64_t s = 1;
+  for (int k = 0; k < t->rank; ++k) s *= leg_dim(t, k, mask);
+  return s;
+}
+
+static ftn_status fill_meta(ftn_tensor_s* t, int rank, const int32_t* d0, const int32_t* d1, const uint8_t* dual,
+                            int parity, ftn_dtype dtype) {
+  if (rank < 0 || rank > FTN_MAX_RANK) return set_error(FTN_EINVAL, "rank out of range");
+  if (parity != 0 && parity != 1) return set_error(FTN_EPARITY, "parity must be 0 or 1");
+  if (dtype != FTN_F64 && dtype != FTN_F32) return set_error(FTN_EINVAL, "bad dtype");
+  if (rank > 0 && (!d0 || !d1 || !dual)) return set_error(FTN_EINVAL, "null leg arrays");
+  t->rank = rank;
+  t->parity = parity;
+  t->dtype = dtype;
+  for (int k = 0; k < rank; ++k) {
+    if (d0[k] < 0 || d1[k] < 0) return set_error(FTN_EINVAL, "negative sector dimension");
+    if (dual[k] > 1) return set_error(FTN_EINVAL, "dual must be 0 or 1");
+    t->d0[k] = d0[k];
+    t->d1[k] = d1[k];
+    t->dual[k] = dual[k];
+  }
+  int64_t nb = nblocks(rank, parity);
+  t->offsets.resize(nb);
+  int64_t off = 0;
+  for (int64_t b = 0; b < nb; ++b) {
+    t->offsets[b] = off;
+    off += block_size(t, block_mask(rank, parity, b));
+  }
+  t->numel = off;
+  return FTN_OK;
+}
+
+bool same_meta(const ftn_tensor_s* a, int rank, const int32_t* d0, const int32_t* d1, const uint8_t* dual,
+               int parity, ftn_dtype dtype) {
+  if (a->rank != rank || a->parity != parity || a->dtype != dtype) return false;
+  for (int k = 0; k < rank; ++k)
+    if (a->d0[k] != d0[k] || a->d1[k] != d1[k] || a->dual[k] != dual[k]) return false;
+  return true;
+}
+
+ftn_status make_tensor(ftn_ctx ctx, int rank, const int32_t* d0, const int32_t* d1, const uint8_t* dual,
+                       int parity, ftn_dtype dtype, ftn_tensor* out) {
+  if (!ctx || !out) return set_error(FTN_EINVAL, "null argument");
+  auto* t = new ftn_tensor_s();
+  t->ctx = ctx;
+  ftn_status st = fill_meta(t, rank, d0, d1, dual, parity, dtype);
+  if (st != FTN_OK) {
+    delete t;
+    return st;
+  }
+  t->data = dev_alloc(ctx, (size_t)t->numel * dtype_size(dtype));
+  if (!t->data) {
+    delete t;
+    return set_error(FTN_ENOMEM, "device allocation failed");
+  }
+  t->owned = true;
+  *out = t;
+  return FTN_OK;
+}
+
+ftn_status upload_table(ftn_ctx ctx, const void* host, size_t bytes, void** dev) {
+  *dev = dev_alloc(ctx, bytes);
+  if (!*dev) return set_error(FTN_ENOMEM, "device allocation failed (table)");
+  if (bytes) FTN_CUDA(cudaMemcpyAsync(*dev, host, bytes, cudaMemcpyHostToDevice, ctx->stream));
+  return FTN_OK;
+}
+
+// ---- permute job builder ------------------------------------------------------
+void add_perm_job(std::vector<PermJob>& jobs, int64_t& tiles, int rank, const int64_t* dims_in,
+                  const int64_t* dstr_in, int64_t src_off, int64_t dst_off, int sign) {
+  // drop unit legs and merge neighbours contiguous in both layouts
+  int64_t dims[MAXR], dstr[MAXR];
+  int r = 0;
+  int64_t total = 1;
+  for (int k = 0; k < rank; ++k) {
+    total *= dims_in[k];
+    if (dims_in[k] == 1) continue;
+    if (r > 0 && dstr[r - 1] == dstr_in[k] * dims_in[k]) {
+      dims[r - 1] *= dims_in[k];
+      dstr[r - 1] = dstr_in[k];
+      continue;
+    }
+    dims[r] = dims_in[k];
+    dstr[r] = dstr_in[k];
+    ++r;
+  }
+  if (total == 0) return;
+  if (r == 0) {
+    dims[0] = 1;
+    dstr[0] = 1;
+    r = 1;
+  }
+  int64_t sstr[MAXR];
+  int64_t s = 1;
+  for (int k = r - 1; k >= 0; --k) {
+    sstr[k] = s;
+    s *= dims[k];
+  }
+  // I group: source suffix with product >= PERM_TI
+  int iI = r;
+  int64_t PI = 1;
+  while (iI > 0 && PI < PERM_TI) {
+    --iI;
+    PI *= dims[iI];
+  }
+  // O group: remaining legs by increasing destination stride
+  std::vector<int> rest;
+  for (int k = 0; k < iI; ++k) rest.push_back(k);
+  std::stable_sort(rest.begin(), rest.end(), [&](int a, int b) { return dstr[a] < dstr[b]; });
+  std::vector<int> O, B;
+  int64_t PO = 1;
+  for (int k : rest) {
+    if (PO < PERM_TO)
+      O.push_back(k), PO *= dims[k];
+    else
+      B.push_back(k);
+  }
+  // order O legs so that the last one is the fastest in the destination
+  std::sort(O.begin(), O.end(), [&](int a, int b) { return dstr[a] > dstr[b]; });
+  PermJob j;
+  std::memset(&j, 0, sizeof(j));
+  j.src_off = src_off;
+  j.dst_off = dst_off;
+  j.sign = sign;
+  int q = 0;
+  for (int k = iI; k < r; ++k, ++q) {
+    j.dim[q] = (int32_t)dims[k];
+    j.sstr[q] = sstr[k];
+    j.dstr[q] = dstr[k];
+  }
+  j.nI = r - iI;
+  for (int k : O) {
+    j.dim[q] = (int32_t)dims[k];
+    j.sstr[q] = sstr[k];
+    j.dstr[q] = dstr[k];
+    ++q;
+  }
+  j.nO = (int32_t)O.size();
+  int64_t PB = 1;
+  for (int k : B) {
+    j.dim[q] = (int32_t)dims[k];
+    j.sstr[q] = sstr[k];
+    j.dstr[q] = dstr[k];
+    PB *= dims[k];
+    ++q;
+  }
+  j.nB = (int32_t)B.size();
+  j.PI = (int32_t)PI;
+  j.PO = (int32_t)PO;
+  j.PB = PB;
+  j.tiles_i = (int32_t)((PI + PERM_TI - 1) / PERM_TI);
+  j.tiles_o = (int32_t)((PO + PERM_TO - 1) / PERM_TO);
+  // the destination is contiguous along I when I's fastest leg has stride 1
+  // and no O leg is faster
+  int64_t min_o = O.empty() ? INT64_MAX : dstr[O.back()];
+  j.store_fast_i = dstr[r - 1] <= min_o ? 1 : 0;
+  j.tile_begin = tiles;
+  tiles += (int64_t)j.tiles_i * j.tiles_o * PB;
+  jobs.push_back(j);
+}
+
+}  // namespace ftn
+
+using namespace ftn;
+
+extern "C" {
+
+const char* ftn_last_error(void) { return g_last_error.c_str(); }
+
+ftn_status ftn_ctx_create(void* cuda_stream, ftn_alloc_fn alloc, ftn_free_fn free_fn, void* user, ftn_ctx* out) {
+  if (!out) return set_error(FTN_EINVAL, "null out");
+  if ((alloc == nullptr) != (free_fn == nullptr)) return set_error(FTN_EINVAL, "give both alloc and free or neither");
+  int dev = 0;
+  FTN_CUDA(cudaGetDevice(&dev));
+  auto* c = new ftn_ctx_s();
+  c->stream = (cudaStream_t)cuda_stream;
+  c->alloc = alloc;
+  c->free_fn = free_fn;
+  c->user = user;
+  c->device = dev;
+  cudaError_t e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) {
+    delete c;
+    return cuda_error(e, "cudaDeviceGetAttribute");
+  }
+  c->dev_err = (int*)dev_alloc(c, 256);
+  if (!c->dev_err) {
+    delete c;
+    return set_error(FTN_ENOMEM, "device allocation failed (error word)");
+  }
+  e = cudaMemsetAsync(c->dev_err, 0, 256, c->stream);
+  if (e != cudaSuccess) {
+    delete c;
+    return cuda_error(e, "cudaMemsetAsync");
+  }
+  *out = c;
+  return FTN_OK;
+}
+
+ftn_status ftn_ctx_destroy(ftn_ctx ctx) {
+  if (!ctx) return FTN_OK;
+  cudaStreamSynchronize(ctx->stream);
+  clear_plan_caches(ctx);
+  dev_free(ctx, ctx->ws);
+  dev_free(ctx, ctx->dev_err);
+  cudaStreamSynchronize(ctx->stream);
+  delete ctx;
+  return FTN_OK;
+}
+
+ftn_status ftn_ctx_set_stream(ftn_ctx ctx, void* cuda_stream) {
+  if (!ctx) return set_error(FTN_EINVAL, "null ctx");
+  ctx->stream = (cudaStream_t)cuda_stream;
+  return FTN_OK;
+}
+
+ftn_status ftn_ctx_synchronize(ftn_ctx ctx) {
+  if (!ctx) return set_error(FTN_EINVAL, "null ctx");
+  FTN_CUDA(cudaStreamSynchronize(ctx->stream));
+  int err = 0;
+  FTN_CUDA(cudaMemcpy(&err, ctx->dev_err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (err) {
+    FTN_CUDA(cudaMemset(ctx->dev_err, 0, sizeof(int)));
+    return set_error(FTN_ETIMEOUT, "a device-side bounded wait timed out");
+  }
+  return FTN_OK;
+}
+
+int64_t ftn_ctx_launch_count(ftn_ctx ctx) { return ctx ? ctx->launches : 0; }
+
+ftn_status ftn_tensor_create(ftn_ctx ctx, int rank, const int32_t* d_even, const int32_t* d_odd, const uint8_t* dual,
+                             int parity, ftn_dtype dtype, ftn_tensor* out) {
+  return make_tensor(ctx, rank, d_even, d_odd, dual, parity, dtype, out);
+}
+
+ftn_status ftn_tensor_wrap(ftn_ctx ctx, int rank, const int32_t* d_even, const int32_t* d_odd, const uint8_t* dual,
+                           int parity, ftn_dtype dtype, void* dev_data, ftn_tensor* out) {
+  if (!ctx || !out) return set_error(FTN_EINVAL, "null argument");
+  auto* t = new ftn_tensor_s();
+  t->ctx = ctx;
+  ftn_status st = fill_meta(t, rank, d_even, d_odd, dual, parity, dtype);
+  if (st != FTN_OK) {
+    delete t;
+    return st;
+  }
+  if (!dev_data && t->numel > 0) {
+    delete t;
+    return set_error(FTN_EINVAL, "null device buffer");
+  }
+  if (((uintptr_t)dev_data) % dtype_size(dtype)) {
+    delete t;
+    return set_error(FTN_EINVAL, "device buffer not aligned to the element size");
+  }
+  t->data = dev_data;
+  t->owned = false;
+  *out = t;
+  return FTN_OK;
+}
+
+ftn_status ftn_tensor_free(ftn_tensor t) {
+  if (!t) return FTN_OK;
+  if (t->owned) dev_free(t->ctx, t->data);
+  delete t;
+  return FTN_OK;
+}
+
+ftn_status ftn_tensor_info(ftn_tensor t, int* rank, int32_t* d_even, int32_t* d_odd, uint8_t* dual, int* parity,
+                           ftn_dtype* dtype, int64_t* numel, void** dev_data) {
+  if (!t) return set_error(FTN_EINVAL, "null tensor");
+  if (rank) *rank = t->rank;
+  for (int k = 0; k < t->rank; ++k) {
+    if (d_even) d_even[k] = t->d0[k];
+    if (d_odd) d_odd[k] = t->d1[k];
+    if (dual) dual[k] = t->dual[k];
+  }
+  if (parity) *parity = t->parity;
+  if (dtype) *dtype = t->dtype;
+  if (numel) *numel = t->numel;
+  if (dev_data) *dev_data = t->data;
+  return FTN_OK;
+}
+
+ftn_status ftn_tensor_block_offsets(ftn_tensor t, int64_t* offsets, uint32_t* masks, int* nb) {
+  if (!t) return set_error(FTN_EINVAL, "null tensor");
+  int64_t n = nblocks(t->rank, t->parity);
+  for (int64_t b = 0; b < n; ++b) {
+    if (offsets) offsets[b] = t->offsets[b];
+    if (masks) masks[b] = block_mask(t->rank, t->parity, b);
+  }
+  if (nb) *nb = (int)n;
+  return FTN_OK;
+}
+
+ftn_status ftn_tensor_upload(ftn_ctx ctx, ftn_tensor t, const void* host) {
+  if (!ctx || !t || (!host && t->numel)) return set_error(FTN_EINVAL, "null argument");
+  if (t->numel)
+    FTN_CUDA(cudaMemcpyAsync(t->data, host, (size_t)t->numel * dtype_size(t->dtype), cudaMemcpyHostToDevice,
+                             ctx->stream));
+  return FTN_OK;
+}
+
+ftn_status ftn_tensor_download(ftn_ctx ctx, ftn_tensor t, void* host) {
+  if (!ctx || !t || (!host && t->numel)) return set_error(FTN_EINVAL, "null argument");
+  if (t->numel)
+    FTN_CUDA(cudaMemcpyAsync(host, t->data, (size_t)t->numel * dtype_size(t->dtype), cudaMemcpyDeviceToHost,
+                             ctx->stream));
+  return FTN_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,581 @@
+// Fermionic tensordot (Eq. standardcontract with the bond parity of the
+// locally ordered formalism, Eq. fermionictn2) and fermionic transposition
+// (Eq. transposition): block-pair planning, per-block signs and the fused
+// sector-matrix layout of Sec. IV.A, then sign-permute + grouped GEMM.
+#include <algorithm>
+#include <sstream>
+
+#include "common.h"
+
+namespace ftn {
+
+// parity (0/1) of the number of inverted pairs of set bits: out position u
+// holds source leg perm[u]; bits are indexed by source leg.
+static int inversion_parity(int r, const int* perm, uint32_t mask) {
+  int s = 0;
+  for (int u = 0; u < r; ++u) {
+    if (!((mask >> perm[u]) & 1)) continue;
+    for (int v = u + 1; v < r; ++v)
+      if (perm[u] > perm[v] && ((mask >> perm[v]) & 1)) s ^= 1;
+  }
+  return s;
+}
+
+static uint32_t gather_bits(uint32_t mask, const int* legs, int n) {
+  uint32_t m = 0;
+  for (int i = 0; i < n; ++i) m |= ((mask >> legs[i]) & 1u) << i;
+  return m;
+}
+
+// enumerate masks over `n` bits with a given parity, increasing order;
+// returns cumulative offsets indexed by mask (size 2^n) and the total.
+static int64_t sector_offsets(int n, const int64_t* d0, const int64_t* d1, int parity, std::vector<int64_t>& off,
+                              std::vector<int64_t>& size) {
+  off.assign((size_t)1 << n, -1);
+  size.assign((size_t)1 << n, 0);
+  int64_t tot = 0;
+  for (uint32_t m = 0; m < (1u << n); ++m) {
+    if ((popc(m) & 1) != parity) continue;
+    int64_t s = 1;
+    for (int i = 0; i < n; ++i) s *= ((m >> i) & 1) ? d1[i] : d0[i];
+    off[m] = tot;
+    size[m] = s;
+    tot += s;
+  }
+  return tot;
+}
+
+// Every index a permute job or a GEMM problem can touch must lie inside its
+// buffers; a plan that fails this is rejected before any launch.
+static bool jobs_in_bounds(const std::vector<PermJob>& jobs, int64_t src_n, int64_t dst_n) {
+  for (const PermJob& j : jobs) {
+    int64_t ms = j.src_off, md = j.dst_off;
+    const int nl = j.nI + j.nO + j.nB;
+    for (int q = 0; q < nl; ++q) {
+      if (j.dim[q] <= 0) return false;
+      ms += (int64_t)(j.dim[q] - 1) * j.sstr[q];
+      md += (int64_t)(j.dim[q] - 1) * j.dstr[q];
+    }
+    if (j.src_off < 0 || j.dst_off < 0 || ms >= src_n || md >= dst_n) return false;
+  }
+  return true;
+}
+
+static bool probs_in_bounds(const std::vector<GemmProb>& probs, int64_t a_n, int64_t b_n, int64_t c_n) {
+  for (const GemmProb& g : probs) {
+    if (g.M <= 0 || g.N <= 0 || g.K < 0) return false;
+    if (g.K > 0) {
+      if (g.a_off + (int64_t)(g.M - 1) * g.lda + g.K > a_n) return false;
+      if (g.b_off + (int64_t)(g.N - 1) * g.ldb + g.K > b_n) return false;
+    }
+    if (g.c_off + (int64_t)(g.M - 1) * g.ldc + g.N > c_n) return false;
+  }
+  return true;
+}
+
+struct DevTables {
+  ftn_ctx ctx;
+  void* p = nullptr;
+  ~DevTables() {
+    if (p) dev_free(ctx, p);
+  }
+};
+
+// ---------------------------------------------------------------------------------
+struct TdPlan {
+  int nfa = 0, nfb = 0, n = 0;
+  int fa[MAXR], fb[MAXR];
+  int64_t M[2] = {0, 0}, N[2] = {0, 0}, K[2] = {0, 0}, ldk[2] = {8, 8};
+  int64_t afoff[2] = {0, 0}, bfoff[2] = {0, 0};
+  int64_t af_elems = 0, bf_elems = 0;
+  std::vector<PermJob> ja, jb, jc;
+  int64_t ta = 0, tb = 0, tc = 0;
+  std::vector<GemmProb> probs;
+  int64_t gemm_tiles = 0;
+  int bn = 0;
+  bool out_perm = false;
+  int cr = 0;  // result rank
+  int32_t cd0[MAXR], cd1[MAXR];
+  uint8_t cdual[MAXR];
+  int cpar = 0;
+  int64_t tmp_numel = 0;  // result before out_perm
+  // device copies
+  std::shared_ptr<DevTables> dev;
+  PermJob* d_ja = nullptr;
+  PermJob* d_jb = nullptr;
+  PermJob* d_jc = nullptr;
+  GemmProb* d_probs = nullptr;
+};
+
+static std::string meta_key(const ftn_tensor_s* t) {
+  std::ostringstream o;
+  o << t->rank << ':' << t->parity << ':' << (int)t->dtype << ':';
+  for (int k = 0; k < t->rank; ++k) o << t->d0[k] << ',' << t->d1[k] << ',' << (int)t->dual[k] << ';';
+  return o.str();
+}
+
+static ftn_status upload_plan(ftn_ctx ctx, TdPlan& P) {
+  size_t sa = P.ja.size() * sizeof(PermJob), sb = P.jb.size() * sizeof(PermJob), sc = P.jc.size() * sizeof(PermJob),
+         sp = P.probs.size() * sizeof(GemmProb);
+  size_t tot = sa + sb + sc + sp;
+  std::vector<uint8_t> host(tot + 16);
+  std::memcpy(host.data(), P.ja.data(), sa);
+  std::memcpy(host.data() + sa, P.jb.data(), sb);
+  std::memcpy(host.data() + sa + sb, P.jc.data(), sc);
+  std::memcpy(host.data() + sa + sb + sc, P.probs.data(), sp);
+  P.dev = std::make_shared<DevTables>();
+  P.dev->ctx = ctx;
+  void* d = nullptr;
+  FTN_TRY(upload_table(ctx, host.data(), tot, &d));
+  // keep the pageable staging alive until the copy has been consumed
+  FTN_CUDA(cudaStreamSynchronize(ctx->stream));
+  P.dev->p = d;
+  uint8_t* b = (uint8_t*)d;
+  P.d_ja = (PermJob*)b;
+  P.d_jb = (PermJob*)(b + sa);
+  P.d_jc = (PermJob*)(b + sa + sb);
+  P.d_probs = (GemmProb*)(b + sa + sb + sc);
+  return FTN_OK;
+}
+
+static std::map<std::string, std::shared_ptr<TdPlan>>& plan_cache(ftn_ctx ctx) {
+  static std::map<ftn_ctx, std::map<std::string, std::shared_ptr<TdPlan>>> caches;
+  return caches[ctx];
+}
+
+static ftn_status build_plan(ftn_ctx ctx, const ftn_tensor_s* A, const ftn_tensor_s* B, int n, const int* ax,
+                             const int* ay, uint64_t flip_a, uint64_t flip_b, const int* out_perm, ftn_prec prec,
+                             std::shared_ptr<TdPlan>& out) {
+  auto P = std::make_shared<TdPlan>();
+  P->n = n;
+  bool in_a[MAXR] = {}, in_b[MAXR] = {};
+  for (int i = 0; i < n; ++i) {
+    in_a[ax[i]] = true;
+    in_b[ay[i]] = true;
+  }
+  for (int k = 0; k < A->rank; ++k)
+    if (!in_a[k]) P->fa[P->nfa++] = k;
+  for (int k = 0; k < B->rank; ++k)
+    if (!in_b[k]) P->fb[P->nfb++] = k;
+  const int pA = A->parity, pB = B->parity;
+  // sector offsets of free rows (A), free columns (B) and the fused bond (K)
+  int64_t fad0[MAXR], fad1[MAXR], fbd0[MAXR], fbd1[MAXR], kd0[MAXR], kd1[MAXR];
+  for (int j = 0; j < P->nfa; ++j) fad0[j] = A->d0[P->fa[j]], fad1[j] = A->d1[P->fa[j]];
+  for (int j = 0; j < P->nfb; ++j) fbd0[j] = B->d0[P->fb[j]], fbd1[j] = B->d1[P->fb[j]];
+  for (int i = 0; i < n; ++i) kd0[i] = A->d0[ax[i]], kd1[i] = A->d1[ax[i]];
+  std::vector<int64_t> rowoff[2], rowsz[2], coloff[2], colsz[2], koff[2], ksz[2];
+  for (int pi = 0; pi < 2; ++pi) {
+    P->M[pi] = sector_offsets(P->nfa, fad0, fad1, pA ^ pi, rowoff[pi], rowsz[pi]);
+    P->N[pi] = sector_offsets(P->nfb, fbd0, fbd1, pB ^ pi, coloff[pi], colsz[pi]);
+    P->K[pi] = sector_offsets(n, kd0, kd1, pi, koff[pi], ksz[pi]);
+    P->ldk[pi] = std::max<int64_t>(8, (P->K[pi] + 7) / 8 * 8);
+  }
+  P->afoff[0] = 0;
+  P->afoff[1] = (P->M[0] * P->ldk[0] + 63) / 64 * 64;
+  P->af_elems = P->afoff[1] + P->M[1] * P->ldk[1];
+  P->bfoff[0] = 0;
+  P->bfoff[1] = (P->N[0] * P->ldk[0] + 63) / 64 * 64;
+  P->bf_elems = P->bfoff[1] + P->N[1] * P->ldk[1];
+
+  // ---- A blocks -> fused A_pi rows ----
+  int permA[MAXR], permB[MAXR];
+  for (int j = 0; j < P->nfa; ++j) permA[j] = P->fa[j];
+  for (int i = 0; i < n; ++i) permA[P->nfa + i] = ax[i];
+  for (int i = 0; i < n; ++i) permB[i] = ay[n - 1 - i];
+  for (int j = 0; j < P->nfb; ++j) permB[n + j] = P->fb[j];
+  uint32_t arrow_a = 0;
+  for (int i = 0; i < n; ++i)
+    if (A->dual[ax[i]] == 0) arrow_a |= 1u << ax[i];
+  for (int64_t b = 0; b < nblocks(A->rank, pA); ++b) {
+    uint32_t m = block_mask(A->rank, pA, b);
+    uint32_t mA = gather_bits(m, P->fa, P->nfa), mK = gather_bits(m, ax, n);
+    int pi = popc(mK) & 1;
+    int64_t dims[MAXR], dstr[MAXR];
+    for (int k = 0; k < A->rank; ++k) dims[k] = leg_dim(A, k, m);
+    int64_t s = P->ldk[pi];
+    for (int j = P->nfa - 1; j >= 0; --j) {
+      dstr[P->fa[j]] = s;
+      s *= dims[P->fa[j]];
+    }
+    s = 1;
+    for (int i = n - 1; i >= 0; --i) {
+      dstr[ax[i]] = s;
+      s *= dims[ax[i]];
+    }
+    int sg = inversion_parity(A->rank, permA, m) ^ (popc(m & arrow_a) & 1) ^ (popc(m & (uint32_t)flip_a) & 1);
+    int64_t dst = P->afoff[pi] + rowoff[pi][mA] * P->ldk[pi] + koff[pi][mK];
+    add_perm_job(P->ja, P->ta, A->rank, dims, dstr, A->offsets[b], dst, sg ? -1 : 1);
+  }
+  // ---- B blocks -> fused B_pi^T rows (K-major) ----
+  for (int64_t b = 0; b < nblocks(B->rank, pB); ++b) {
+    uint32_t m = block_mask(B->rank, pB, b);
+    uint32_t mB = gather_bits(m, P->fb, P->nfb), mK = gather_bits(m, ay, n);
+    int pi = popc(mK) & 1;
+    int64_t dims[MAXR], dstr[MAXR];
+    for (int k = 0; k < B->rank; ++k) dims[k] = leg_dim(B, k, m);
+    int64_t s = P->ldk[pi];
+    for (int j = P->nfb - 1; j >= 0; --j) {
+      dstr[P->fb[j]] = s;
+      s *= dims[P->fb[j]];
+    }
+    s = 1;
+    for (int i = n - 1; i >= 0; --i) {
+      dstr[ay[i]] = s;
+      s *= dims[ay[i]];
+    }
+    int sg = inversion_parity(B->rank, permB, m) ^ (popc(m & (uint32_t)flip_b) & 1);
+    int64_t dst = P->bfoff[pi] + coloff[pi][mB] * P->ldk[pi] + koff[pi][mK];
+    add_perm_job(P->jb, P->tb, B->rank, dims, dstr, B->offsets[b], dst, sg ? -1 : 1);
+  }
+  // ---- result metadata (before out_perm) ----
+  const int cr = P->nfa + P->nfb;
+  ftn_tensor_s tmp;
+  tmp.rank = cr;
+  tmp.parity = pA ^ pB;
+  for (int j = 0; j < P->nfa; ++j) {
+    tmp.d0[j] = A->d0[P->fa[j]];
+    tmp.d1[j] = A->d1[P->fa[j]];
+    tmp.dual[j] = A->dual[P->fa[j]];
+  }
+  for (int j = 0; j < P->nfb; ++j) {
+    tmp.d0[P->nfa + j] = B->d0[P->fb[j]];
+    tmp.d1[P->nfa + j] = B->d1[P->fb[j]];
+    tmp.dual[P->nfa + j] = B->dual[P->fb[j]];
+  }
+  std::vector<int64_t> toff(nblocks(cr, tmp.parity));
+  int64_t tot = 0;
+  for (int64_t b = 0; b < (int64_t)toff.size(); ++b) {
+    toff[b] = tot;
+    tot += block_size(&tmp, block_mask(cr, tmp.parity, b));
+  }
+  P->tmp_numel = tot;
+  // ---- GEMM problems, one per result block ----
+  const bool tc = prec != FTN_PREC_F64;
+  int maxN = 1;
+  for (int64_t b = 0; b < (int64_t)toff.size(); ++b) {
+    uint32_t m = block_mask(cr, tmp.parity, b);
+    uint32_t mB = m >> P->nfa;
+    int pi = (popc(mB) & 1) ^ pB;
+    maxN = std::max<int64_t>(maxN, colsz[pi][mB]);
+  }
+  P->bn = tc ? tc_pick_bn(maxN, prec) : 64;
+  for (int64_t b = 0; b < (int64_t)toff.size(); ++b) {
+    uint32_t m = block_mask(cr, tmp.parity, b);
+    uint32_t mA = m & ((1u << P->nfa) - 1u), mB = m >> P->nfa;
+    int pi = (popc(mA) & 1) ^ pA;
+    GemmProb g;
+    std::memset(&g, 0, sizeof(g));
+    g.M = (int32_t)rowsz[pi][mA];
+    g.N = (int32_t)colsz[pi][mB];
+    g.K = (int32_t)P->K[pi];
+    if (g.M == 0 || g.N == 0) continue;
+    g.pi = pi;
+    g.lda = g.ldb = (int32_t)P->ldk[pi];
+    g.ldc = g.N;
+    g.a_row0 = (int32_t)rowoff[pi][mA];
+    g.b_row0 = (int32_t)coloff[pi][mB];
+    g.a_off = P->afoff[pi] + rowoff[pi][mA] * P->ldk[pi];
+    g.b_off = P->bfoff[pi] + coloff[pi][mB] * P->ldk[pi];
+    g.c_off = toff[b];
+    if (tc) {
+      g.tiles_m = (g.M + 127) / 128;
+      g.tiles_n = (g.N + P->bn - 1) / P->bn;
+    } else {
+      g.tiles_m = (g.M + 63) / 64;
+      g.tiles_n = (g.N + 63) / 64;
+    }
+    g.tile_begin = P->gemm_tiles;
+    P->gemm_tiles += (int64_t)g.tiles_m * g.tiles_n;
+    P->probs.push_back(g);
+  }
+  // ---- optional out_perm ----
+  P->cr = cr;
+  P->cpar = tmp.parity;
+  bool ident = true;
+  if (out_perm)
+    for (int u = 0; u < cr; ++u) ident = ident && out_perm[u] == u;
+  P->out_perm = !ident;
+  if (!P->out_perm) {
+    for (int k = 0; k < cr; ++k) P->cd0[k] = tmp.d0[k], P->cd1[k] = tmp.d1[k], P->cdual[k] = tmp.dual[k];
+  } else {
+    for (int u = 0; u < cr; ++u)
+      P->cd0[u] = tmp.d0[out_perm[u]], P->cd1[u] = tmp.d1[out_perm[u]], P->cdual[u] = tmp.dual[out_perm[u]];
+    ftn_tensor_s fin;
+    fin.rank = cr;
+    fin.parity = tmp.parity;
+    for (int u = 0; u < cr; ++u) fin.d0[u] = P->cd0[u], fin.d1[u] = P->cd1[u];
+    std::vector<int64_t> foff(nblocks(cr, fin.parity));
+    int64_t t2 = 0;
+    for (int64_t b = 0; b < (int64_t)foff.size(); ++b) {
+      foff[b] = t2;
+      t2 += block_size(&fin, block_mask(cr, fin.parity, b));
+    }
+    for (int64_t b = 0; b < (int64_t)toff.size(); ++b) {
+      uint32_t m = block_mask(cr, tmp.parity, b);
+      uint32_t mo = 0;
+      for (int u = 0; u < cr; ++u) mo |= ((m >> out_perm[u]) & 1u) << u;
+      int64_t dims[MAXR], dstr[MAXR], od[MAXR];
+      for (int k = 0; k < cr; ++k) dims[k] = leg_dim(&tmp, k, m);
+      for (int u = 0; u < cr; ++u) od[u] = dims[out_perm[u]];
+      int64_t s = 1;
+      for (int u = cr - 1; u >= 0; --u) {
+        dstr[out_perm[u]] = s;
+        s *= od[u];
+      }
+      int sg = inversion_parity(cr, out_perm, m);
+      add_perm_job(P->jc, P->tc, cr, dims, dstr, toff[b], foff[mo >> 1], sg ? -1 : 1);
+    }
+  }
+  if (!jobs_in_bounds(P->ja, A->numel, P->af_elems) || !jobs_in_bounds(P->jb, B->numel, P->bf_elems) ||
+      !probs_in_bounds(P->probs, P->af_elems, P->bf_elems, P->tmp_numel) ||
+      (P->out_perm && !jobs_in_bounds(P->jc, P->tmp_numel, P->tmp_numel)))
+    return set_error(FTN_EINVAL, "internal error: contraction plan out of bounds");
+  FTN_TRY(upload_plan(ctx, *P));
+  out = P;
+  return FTN_OK;
+}
+
+static ftn_status validate_pairs(const ftn_tensor_s* A, const ftn_tensor_s* B, int n, const int* ax, const int* ay) {
+  if (n < 0 || n > A->rank || n > B->rank) return set_error(FTN_EINVAL, "bad number of contracted legs");
+  if (n > 0 && (!ax || !ay)) return set_error(FTN_EINVAL, "null axes");
+  bool ua[MAXR] = {}, ub[MAXR] = {};
+  for (int i = 0; i < n; ++i) {
+    if (ax[i] < 0 || ax[i] >= A->rank || ay[i] < 0 || ay[i] >= B->rank)
+      return set_error(FTN_EINVAL, "axis out of range");
+    if (ua[ax[i]] || ub[ay[i]]) return set_error(FTN_EINVAL, "repeated axis");
+    ua[ax[i]] = ub[ay[i]] = true;
+    if (A->d0[ax[i]] != B->d0[ay[i]] || A->d1[ax[i]] != B->d1[ay[i]])
+      return set_error(FTN_ESHAPE, "contracted legs differ in sector dimensions");
+    if (A->dual[ax[i]] == B->dual[ay[i]]) return set_error(FTN_EDUAL, "contracted legs must have opposite duals");
+  }
+  if (A->rank + B->rank - 2 * n > FTN_MAX_RANK) return set_error(FTN_EINVAL, "result rank exceeds FTN_MAX_RANK");
+  return FTN_OK;
+}
+
+static ftn_status get_plan(ftn_ctx ctx, const ftn_tensor_s* A, const ftn_tensor_s* B, int n, const int* ax,
+                           const int* ay, uint64_t fa, uint64_t fb, const int* out_perm, ftn_prec prec,
+                           std::shared_ptr<TdPlan>& P) {
+  std::ostringstream key;
+  key << "td|" << meta_key(A) << '|' << meta_key(B) << '|' << n << ':';
+  for (int i = 0; i < n; ++i) key << ax[i] << ',' << ay[i] << ';';
+  key << '|' << fa << '|' << fb << '|' << (int)prec << '|';
+  if (out_perm)
+    for (int u = 0; u < A->rank + B->rank - 2 * n; ++u) key << out_perm[u] << ',';
+  auto& cache = plan_cache(ctx);
+  auto it = cache.find(key.str());
+  if (it != cache.end()) {
+    P = it->second;
+    return FTN_OK;
+  }
+  FTN_TRY(build_plan(ctx, A, B, n, ax, ay, fa, fb, out_perm, prec, P));
+  if (cache.size() > 4096) cache.clear();
+  cache[key.str()] = P;
+  return FTN_OK;
+}
+
+ftn_status tensordot_impl(ftn_ctx ctx, ftn_tensor A, ftn_tensor B, int n, const int* ax, const int* ay,
+                          uint64_t flip_a, uint64_t flip_b, const int* out_perm, ftn_prec prec, ftn_tensor* C) {
+  if (!ctx || !A || !B || !C) return set_error(FTN_EINVAL, "null argument");
+  if (A->dtype != B->dtype) return set_error(FTN_EINVAL, "A and B must have the same dtype");
+  if ((prec == FTN_PREC_F64) != (A->dtype == FTN_F64))
+    return set_error(FTN_EUNSUPPORTED, "FTN_PREC_F64 needs FP64 tensors; tensor-core precisions need FP32 tensors");
+  if (prec < FTN_PREC_F64 || prec > FTN_PREC_BF16X3) return set_error(FTN_EINVAL, "bad precision");
+  FTN_TRY(validate_pairs(A, B, n, ax, ay));
+  const int cr = A->rank + B->rank - 2 * n;
+  if (out_perm) {
+    bool seen[MAXR] = {};
+    for (int u = 0; u < cr; ++u) {
+      if (out_perm[u] < 0 || out_perm[u] >= cr || seen[out_perm[u]]) return set_error(FTN_EINVAL, "bad out_perm");
+      seen[out_perm[u]] = true;
+    }
+  }
+  std::shared_ptr<TdPlan> P;
+  FTN_TRY(get_plan(ctx, A, B, n, ax, ay, flip_a, flip_b, out_perm, prec, P));
+  ftn_tensor out = *C;
+  bool created = false;
+  if (out) {
+    if (!same_meta(out, cr, P->cd0, P->cd1, P->cdual, P->cpar, A->dtype))
+      return set_error(FTN_EINVAL, "preallocated output has the wrong metadata");
+  } else {
+    FTN_TRY(make_tensor(ctx, cr, P->cd0, P->cd1, P->cdual, P->cpar, A->dtype, &out));
+    created = true;
+  }
+  // workspace: A_f (hi, lo), B_f (hi, lo), pre-permutation result
+  const bool tc = prec != FTN_PREC_F64;
+  const bool split = prec == FTN_PREC_TF32X3 || prec == FTN_PREC_BF16X3;
+  const bool bf16 = prec == FTN_PREC_BF16 || prec == FTN_PREC_BF16X3;
+  const size_t es = tc ? (bf16 ? 2 : 4) : 8;
+  auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+  const size_t a_b = al((size_t)P->af_elems * es), b_b = al((size_t)P->bf_elems * es);
+  const size_t c_b = P->out_perm ? al((size_t)P->tmp_numel * dtype_size(A->dtype)) : 0;
+  const size_t need = a_b * (split ? 2 : 1) + b_b * (split ? 2 : 1) + c_b;
+  uint8_t* ws = (uint8_t*)workspace(ctx, need);
+  if (!ws) {
+    if (created) ftn_tensor_free(out);
+    return set_error(FTN_ENOMEM, "workspace allocation failed");
+  }
+  uint8_t* af_hi = ws;
+  uint8_t* af_lo = split ? af_hi + a_b : nullptr;
+  uint8_t* bf_hi = ws + a_b * (split ? 2 : 1);
+  uint8_t* bf_lo = split ? bf_hi + b_b : nullptr;
+  uint8_t* ctmp = P->out_perm ? bf_hi + b_b * (split ? 2 : 1) : (uint8_t*)out->data;
+  int mode = PERM_SAME;
+  if (prec == FTN_PREC_TF32) mode = PERM_TF32;
+  if (prec == FTN_PREC_TF32X3) mode = PERM_TF32X2;
+  if (prec == FTN_PREC_BF16) mode = PERM_BF16;
+  if (prec == FTN_PREC_BF16X3) mode = PERM_BF16X2;
+  ftn_status st = launch_permute(ctx, P->d_ja, (int)P->ja.size(), P->ta, A->data, af_hi, af_lo, A->dtype, mode);
+  if (st == FTN_OK)
+    st = launch_permute(ctx, P->d_jb, (int)P->jb.size(), P->tb, B->data, bf_hi, bf_lo, B->dtype, mode);
+  if (st == FTN_OK) {
+    if (!tc) {
+      st = launch_gemm_f64(ctx, P->d_probs, (int)P->probs.size(), P->gemm_tiles, (const double*)af_hi,
+                           (const double*)bf_hi, (double*)ctmp);
+    } else {
+      TcOperands ops;
+      for (int pi = 0; pi < 2; ++pi) {
+        ops.a_hi[pi] = af_hi + P->afoff[pi] * es;
+        ops.b_hi[pi] = bf_hi + P->bfoff[pi] * es;
+        ops.a_lo[pi] = split ? af_lo + P->afoff[pi] * es : nullptr;
+        ops.b_lo[pi] = split ? bf_lo + P->bfoff[pi] * es : nullptr;
+        ops.a_rows[pi] = P->M[pi];
+        ops.b_rows[pi] = P->N[pi];
+        ops.kdim[pi] = (int32_t)P->K[pi];
+        ops.ldk[pi] = (int32_t)P->ldk[pi];
+      }
+      st = launch_gemm_tc(ctx, prec, ops, P->d_probs, (int)P->probs.size(), P->gemm_tiles, P->bn, (float*)ctmp);
+    }
+  }
+  if (st == FTN_OK && P->out_perm)
+    st = launch_permute(ctx, P->d_jc, (int)P->jc.size(), P->tc, ctmp, out->data, nullptr, A->dtype, PERM_SAME);
+  if (st != FTN_OK) {
+    if (created) ftn_tensor_free(out);
+    return st;
+  }
+  *C = out;
+  return FTN_OK;
+}
+
+// ---- transposition / dagger -------------------------------------------------------
+struct TrPlan {
+  std::vector<PermJob> jobs;
+  int64_t tiles = 0;
+  std::shared_ptr<DevTables> dev;
+  PermJob* d_jobs = nullptr;
+};
+
+static std::map<std::string, std::shared_ptr<TrPlan>>& tr_cache(ftn_ctx ctx) {
+  static std::map<ftn_ctx, std::map<std::string, std::shared_ptr<TrPlan>>> caches;
+  return caches[ctx];
+}
+
+// out leg u = in leg perm[u]; `fermionic` selects the Eq. (transposition) sign
+ftn_status permute_impl(ftn_ctx ctx, ftn_tensor t, const int* perm, bool fermionic, bool flip_duals, ftn_tensor* out) {
+  if (!ctx || !t || !out || (t->rank > 0 && !perm)) return set_error(FTN_EINVAL, "null argument");
+  const int r = t->rank;
+  bool seen[MAXR] = {};
+  for (int u = 0; u < r; ++u) {
+    if (perm[u] < 0 || perm[u] >= r || seen[perm[u]]) return set_error(FTN_EINVAL, "bad permutation");
+    seen[perm[u]] = true;
+  }
+  int32_t d0[MAXR], d1[MAXR];
+  uint8_t du[MAXR];
+  for (int u = 0; u < r; ++u) {
+    d0[u] = t->d0[perm[u]];
+    d1[u] = t->d1[perm[u]];
+    du[u] = flip_duals ? (uint8_t)(1 - t->dual[perm[u]]) : t->dual[perm[u]];
+  }
+  ftn_tensor o = *out;
+  bool created = false;
+  if (o) {
+    if (!same_meta(o, r, d0, d1, du, t->parity, t->dtype))
+      return set_error(FTN_EINVAL, "preallocated output has the wrong metadata");
+  } else {
+    FTN_TRY(make_tensor(ctx, r, d0, d1, du, t->parity, t->dtype, &o));
+    created = true;
+  }
+  std::ostringstream key;
+  key << "tr|" << meta_key(t) << '|' << fermionic << '|';
+  for (int u = 0; u < r; ++u) key << perm[u] << ',';
+  auto& cache = tr_cache(ctx);
+  std::shared_ptr<TrPlan> P;
+  auto it = cache.find(key.str());
+  if (it != cache.end()) {
+    P = it->second;
+  } else {
+    P = std::make_shared<TrPlan>();
+    for (int64_t b = 0; b < nblocks(r, t->parity); ++b) {
+      uint32_t m = block_mask(r, t->parity, b);
+      uint32_t mo = 0;
+      for (int u = 0; u < r; ++u) mo |= ((m >> perm[u]) & 1u) << u;
+      int64_t dims[MAXR], dstr[MAXR];
+      for (int k = 0; k < r; ++k) dims[k] = leg_dim(t, k, m);
+      int64_t s = 1;
+      for (int u = r - 1; u >= 0; --u) {
+        dstr[perm[u]] = s;
+        s *= dims[perm[u]];
+      }
+      int sg = fermionic ? inversion_parity(r, perm, m) : 0;
+      int64_t dst = r == 0 ? 0 : o->offsets[mo >> 1];
+      if (r == 0) {
+        dims[0] = 1;
+        dstr[0] = 1;
+      }
+      add_perm_job(P->jobs, P->tiles, r == 0 ? 1 : r, dims, dstr, t->offsets[b], dst, sg ? -1 : 1);
+    }
+    if (!jobs_in_bounds(P->jobs, t->numel, o->numel)) {
+      if (created) ftn_tensor_free(o);
+      return set_error(FTN_EINVAL, "internal error: transposition plan out of bounds");
+    }
+    P->dev = std::make_shared<DevTables>();
+    P->dev->ctx = ctx;
+    void* d = nullptr;
+    ftn_status st = upload_table(ctx, P->jobs.data(), P->jobs.size() * sizeof(PermJob), &d);
+    if (st != FTN_OK) {
+      if (created) ftn_tensor_free(o);
+      return st;
+    }
+    cudaStreamSynchronize(ctx->stream);
+    P->dev->p = d;
+    P->d_jobs = (PermJob*)d;
+    if (cache.size() > 4096) cache.clear();
+    cache[key.str()] = P;
+  }
+  ftn_status st = launch_permute(ctx, P->d_jobs, (int)P->jobs.size(), P->tiles, t->data, o->data, nullptr, t->dtype,
+                                 PERM_SAME);
+  if (st != FTN_OK) {
+    if (created) ftn_tensor_free(o);
+    return st;
+  }
+  *out = o;
+  return FTN_OK;
+}
+
+void clear_plan_caches(ftn_ctx ctx) {
+  plan_cache(ctx).clear();
+  tr_cache(ctx).clear();
+}
+
+}  // namespace ftn
+
+using namespace ftn;
+
+extern "C" {
+
+ftn_status ftn_tensordot(ftn_ctx ctx, ftn_tensor A, ftn_tensor B, int n, const int* axes_a, const int* axes_b,
+                         uint64_t flip_a, uint64_t flip_b, const int* out_perm, ftn_prec prec, ftn_tensor* C) {
+  return tensordot_impl(ctx, A, B, n, axes_a, axes_b, flip_a, flip_b, out_perm, prec, C);
+}
+
+ftn_status ftn_tensor_transpose(ftn_ctx ctx, ftn_tensor t, const int* perm, ftn_tensor* out) {
+  return permute_impl(ctx, t, perm, true, false, out);
+}
+
+ftn_status ftn_tensor_dagger(ftn_ctx ctx, ftn_tensor t, ftn_tensor* out) {
+  if (!t) return set_error(FTN_EINVAL, "null tensor");
+  int perm[MAXR];
+  for (int u = 0; u < t->rank; ++u) perm[u] = t->rank - 1 - u;
+  return permute_impl(ctx, t, perm, false, true, out);
+}
+
+}  // extern "C"

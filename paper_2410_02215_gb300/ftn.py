@@ -1,0 +1,335 @@
+"""Thin ctypes binding of libftn (include/ftn.h).
+
+Argument marshalling only: every step of a contraction, transposition or
+compression runs in libftn's CUDA kernels.  PyTorch supplies device memory
+(through the context's allocator callbacks) and the CUDA stream.  Importing
+this module fails loudly when the compiled library is missing.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libftn.so")
+
+FTN_MAX_RANK = 16
+F64, F32 = 0, 1
+PREC_F64, PREC_TF32, PREC_BF16, PREC_TF32X3, PREC_BF16X3 = 0, 1, 2, 3, 4
+PREC_NAMES = {"f64": PREC_F64, "tf32": PREC_TF32, "bf16": PREC_BF16, "tf32x3": PREC_TF32X3, "bf16x3": PREC_BF16X3}
+POLICY_EXACT, POLICY_EARLY, POLICY_LATE = 0, 1, 2
+POLICY_NAMES = {"exact": POLICY_EXACT, "early": POLICY_EARLY, "late": POLICY_LATE}
+STATUS = {0: "FTN_OK", -1: "FTN_EINVAL", -2: "FTN_ESHAPE", -3: "FTN_EPARITY", -4: "FTN_EDUAL", -5: "FTN_ENOMEM",
+          -6: "FTN_ECUDA", -7: "FTN_ETIMEOUT", -8: "FTN_EUNSUPPORTED"}
+
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
+
+
+class FtnError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class CompressInfo(C.Structure):
+    _fields_ = [("kept", C.c_int * 2), ("rank", C.c_int * 2), ("discarded_sq", C.c_double),
+                ("total_sq", C.c_double), ("s_max", C.c_double), ("s_cut", C.c_double), ("s_next", C.c_double)]
+
+
+class Network(C.Structure):
+    _fields_ = [("n_tensors", C.c_int), ("tensors", C.POINTER(C.c_void_p)), ("n_bonds", C.c_int),
+                ("bonds", C.POINTER(C.c_int32)), ("positions", C.POINTER(C.c_int32))]
+
+
+class Tree(C.Structure):
+    _fields_ = [("n_steps", C.c_int), ("pairs", C.POINTER(C.c_int32)), ("policy", C.c_int), ("chi", C.c_int)]
+
+
+_lib = None
+
+
+def lib():
+    """The loaded libftn (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libftn is not built ({LIB_PATH} missing); run __graft_entry__.build()")
+    L = C.CDLL(LIB_PATH)
+    vp, i32p, u8p, i64p, u32p = C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_uint8), C.POINTER(C.c_int64), C.POINTER(C.c_uint32)
+    ip = C.POINTER(C.c_int)
+    sigs = {
+        "ftn_ctx_create": [vp, ALLOC_FN, FREE_FN, vp, C.POINTER(vp)],
+        "ftn_ctx_destroy": [vp],
+        "ftn_ctx_set_stream": [vp, vp],
+        "ftn_ctx_synchronize": [vp],
+        "ftn_tensor_create": [vp, C.c_int, i32p, i32p, u8p, C.c_int, C.c_int, C.POINTER(vp)],
+        "ftn_tensor_wrap": [vp, C.c_int, i32p, i32p, u8p, C.c_int, C.c_int, vp, C.POINTER(vp)],
+        "ftn_tensor_free": [vp],
+        "ftn_tensor_info": [vp, ip, i32p, i32p, u8p, ip, ip, i64p, C.POINTER(vp)],
+        "ftn_tensor_block_offsets": [vp, i64p, u32p, ip],
+        "ftn_tensor_upload": [vp, vp, vp],
+        "ftn_tensor_download": [vp, vp, vp],
+        "ftn_tensor_transpose": [vp, vp, ip, C.POINTER(vp)],
+        "ftn_tensor_dagger": [vp, vp, C.POINTER(vp)],
+        "ftn_tensordot": [vp, vp, vp, C.c_int, ip, ip, C.c_uint64, C.c_uint64, ip, C.c_int, C.POINTER(vp)],
+        "ftn_compress": [vp, C.POINTER(vp), C.POINTER(vp), C.c_int, ip, ip, C.c_int, C.c_int, C.POINTER(CompressInfo)],
+        "ftn_contract": [vp, C.POINTER(Network), C.POINTER(Tree), C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double)],
+        "ftn_hubbard_term": [vp, C.c_int, C.c_double, C.c_double, C.c_int, C.POINTER(vp)],
+    }
+    for name, args in sigs.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = C.c_int
+    L.ftn_last_error.argtypes = []
+    L.ftn_last_error.restype = C.c_char_p
+    L.ftn_ctx_launch_count.argtypes = [vp]
+    L.ftn_ctx_launch_count.restype = C.c_int64
+    _lib = L
+    return L
+
+
+def _check(st):
+    if st != 0:
+        raise FtnError(st, lib().ftn_last_error().decode())
+
+
+def _i32(seq):
+    seq = list(seq)
+    return (C.c_int32 * max(1, len(seq)))(*seq)
+
+
+def _int(seq):
+    seq = list(seq)
+    return (C.c_int * max(1, len(seq)))(*seq)
+
+
+class Context:
+    """ftn_ctx bound to a torch CUDA stream; device memory from torch's
+    caching allocator (via the context's allocator callbacks)."""
+
+    def __init__(self, stream=None, use_torch_allocator=True):
+        import torch
+
+        self._torch = torch
+        self.device = torch.cuda.current_device()
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self._keep = []
+        if use_torch_allocator:
+            dev, st = self.device, self.stream
+
+            def _alloc(nbytes, user):
+                try:
+                    return torch.cuda.caching_allocator_alloc(int(nbytes), dev, st)
+                except Exception:  # allocation failure becomes FTN_ENOMEM
+                    return None
+
+            def _free(ptr, user):
+                if ptr:
+                    torch.cuda.caching_allocator_delete(ptr)
+
+            a, f = ALLOC_FN(_alloc), FREE_FN(_free)
+            self._keep += [a, f]
+        else:
+            a, f = ALLOC_FN(0), FREE_FN(0)
+        h = C.c_void_p()
+        _check(lib().ftn_ctx_create(C.c_void_p(self.stream.cuda_stream), a, f, None, C.byref(h)))
+        self.handle = h
+
+    def synchronize(self):
+        _check(lib().ftn_ctx_synchronize(self.handle))
+
+    def launches(self):
+        return int(lib().ftn_ctx_launch_count(self.handle))
+
+    def close(self):
+        if self.handle:
+            lib().ftn_ctx_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class _CAI:
+    def __init__(self, ptr, n, typestr):
+        self.__cuda_array_interface__ = {"shape": (int(n),), "typestr": typestr, "data": (int(ptr), False),
+                                         "version": 3, "strides": None}
+
+
+class Tensor:
+    """A graded tensor in libftn's packed sector layout (ftn_tensor)."""
+
+    def __init__(self, ctx, handle, keep=None):
+        self.ctx = ctx
+        self.handle = handle
+        self._keep = keep  # borrowed storage kept alive for wrapped tensors
+        r = C.c_int()
+        d0 = (C.c_int32 * FTN_MAX_RANK)()
+        d1 = (C.c_int32 * FTN_MAX_RANK)()
+        du = (C.c_uint8 * FTN_MAX_RANK)()
+        par, dt, n, ptr = C.c_int(), C.c_int(), C.c_int64(), C.c_void_p()
+        _check(lib().ftn_tensor_info(handle, C.byref(r), d0, d1, du, C.byref(par), C.byref(dt), C.byref(n), C.byref(ptr)))
+        self.rank = r.value
+        self.legs = [(d0[k], d1[k], du[k]) for k in range(self.rank)]
+        self.parity = par.value
+        self.dtype = dt.value
+        self.numel = n.value
+        self.ptr = ptr.value or 0
+
+    # ---- construction ----
+    @staticmethod
+    def _meta(legs):
+        r = len(legs)
+        return r, _i32([l[0] for l in legs]), _i32([l[1] for l in legs]), (C.c_uint8 * max(1, r))(*[l[2] for l in legs])
+
+    @classmethod
+    def empty(cls, ctx, legs, parity, dtype=F64):
+        r, d0, d1, du = cls._meta(legs)
+        h = C.c_void_p()
+        _check(lib().ftn_tensor_create(ctx.handle, r, d0, d1, du, parity, dtype, C.byref(h)))
+        return cls(ctx, h)
+
+    @classmethod
+    def wrap(cls, ctx, legs, parity, storage, dtype=None):
+        """Borrow a contiguous torch CUDA tensor as the data buffer."""
+        torch = ctx._torch
+        if dtype is None:
+            dtype = F64 if storage.dtype == torch.float64 else F32
+        r, d0, d1, du = cls._meta(legs)
+        h = C.c_void_p()
+        _check(lib().ftn_tensor_wrap(ctx.handle, r, d0, d1, du, parity, dtype, C.c_void_p(storage.data_ptr()), C.byref(h)))
+        return cls(ctx, h, keep=storage)
+
+    def block_table(self):
+        nb = 1 << max(self.rank - 1, 0)
+        offs = (C.c_int64 * max(1, nb))()
+        masks = (C.c_uint32 * max(1, nb))()
+        cnt = C.c_int()
+        _check(lib().ftn_tensor_block_offsets(self.handle, offs, masks, C.byref(cnt)))
+        return [(int(masks[b]), int(offs[b])) for b in range(cnt.value)]
+
+    def bits_of(self, mask):
+        return tuple((mask >> k) & 1 for k in range(self.rank))
+
+    def block_shape(self, bits):
+        return tuple(l[1] if b else l[0] for l, b in zip(self.legs, bits))
+
+    def np_dtype(self):
+        return np.float64 if self.dtype == F64 else np.float32
+
+    def view(self):
+        """Zero-copy torch view of the packed buffer (valid while self lives)."""
+        torch = self.ctx._torch
+        typestr = "<f8" if self.dtype == F64 else "<f4"
+        if self.numel == 0:
+            return torch.empty(0, dtype=torch.float64 if self.dtype == F64 else torch.float32, device="cuda")
+        return torch.as_tensor(_CAI(self.ptr, self.numel, typestr), device="cuda")
+
+    def upload(self, flat):
+        flat = np.ascontiguousarray(flat, dtype=self.np_dtype())
+        assert flat.size == self.numel
+        _check(lib().ftn_tensor_upload(self.ctx.handle, self.handle, flat.ctypes.data_as(C.c_void_p)))
+        self.ctx.synchronize()
+
+    def download(self):
+        out = np.empty(self.numel, dtype=self.np_dtype())
+        _check(lib().ftn_tensor_download(self.ctx.handle, self.handle, out.ctypes.data_as(C.c_void_p)))
+        self.ctx.synchronize()
+        return out
+
+    @classmethod
+    def from_blocks(cls, ctx, legs, parity, blocks, dtype=F64):
+        """Pack ``[(bits, ndarray), ...]`` into a new library tensor."""
+        t = cls.empty(ctx, legs, parity, dtype)
+        flat = np.zeros(t.numel, dtype=t.np_dtype())
+        table = {t.bits_of(m): off for m, off in t.block_table()}
+        for bits, arr in blocks:
+            arr = np.asarray(arr)
+            off = table[tuple(int(b) for b in bits)]
+            flat[off:off + arr.size] = arr.reshape(-1)
+        t.upload(flat)
+        return t
+
+    def to_blocks(self):
+        flat = self.download()
+        out = []
+        for m, off in self.block_table():
+            bits = self.bits_of(m)
+            shp = self.block_shape(bits)
+            n = int(np.prod(shp)) if shp else 1
+            out.append((bits, flat[off:off + n].reshape(shp).astype(np.float64)))
+        return out
+
+    def free(self):
+        if self.handle:
+            lib().ftn_tensor_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+# ---- operations -------------------------------------------------------------------
+def _prec(p):
+    return PREC_NAMES[p] if isinstance(p, str) else int(p)
+
+
+def tensordot(ctx, a, b, axes_a, axes_b, flip_a=0, flip_b=0, out_perm=None, prec="f64", out=None):
+    h = C.c_void_p(out.handle.value if out is not None else None)
+    n = len(axes_a)
+    op = _int(out_perm) if out_perm is not None else None
+    _check(lib().ftn_tensordot(ctx.handle, a.handle, b.handle, n, _int(axes_a), _int(axes_b), int(flip_a), int(flip_b),
+                               op, _prec(prec), C.byref(h)))
+    return out if out is not None else Tensor(ctx, h)
+
+
+def transpose(ctx, t, perm, out=None):
+    h = C.c_void_p(out.handle.value if out is not None else None)
+    _check(lib().ftn_tensor_transpose(ctx.handle, t.handle, _int(perm), C.byref(h)))
+    return out if out is not None else Tensor(ctx, h)
+
+
+def dagger(ctx, t):
+    h = C.c_void_p()
+    _check(lib().ftn_tensor_dagger(ctx.handle, t.handle, C.byref(h)))
+    return Tensor(ctx, h)
+
+
+def compress(ctx, x, y, axes_x, axes_y, chi, arrows=True):
+    """Returns (X', Y', info); x and y are consumed (their handles released)."""
+    hx, hy = C.c_void_p(x.handle.value), C.c_void_p(y.handle.value)
+    info = CompressInfo()
+    _check(lib().ftn_compress(ctx.handle, C.byref(hx), C.byref(hy), len(axes_x), _int(axes_x), _int(axes_y), int(chi),
+                              1 if arrows else 0, C.byref(info)))
+    x.handle = None
+    y.handle = None
+    return Tensor(ctx, hx), Tensor(ctx, hy), info
+
+
+def contract(ctx, tensors, bonds, tree, positions=None, policy="exact", chi=0, prec="f64"):
+    """Contract a closed network; returns (mantissa, log_scale)."""
+    arr = (C.c_void_p * len(tensors))(*[t.handle.value for t in tensors])
+    flat_b = [int(v) for b in bonds for v in b]
+    flat_t = [int(v) for p in tree for v in p]
+    net = Network(len(tensors), C.cast(arr, C.POINTER(C.c_void_p)), len(bonds), _i32(flat_b),
+                  _i32(positions) if positions is not None else None)
+    tr = Tree(len(tree), _i32(flat_t), POLICY_NAMES[policy] if isinstance(policy, str) else int(policy), int(chi))
+    m, lg = C.c_double(), C.c_double()
+    _check(lib().ftn_contract(ctx.handle, C.byref(net), C.byref(tr), _prec(prec), C.byref(m), C.byref(lg)))
+    return m.value, lg.value
+
+
+def hubbard_term(ctx, kind, t=1.0, u=0.0, dtype=F64):
+    h = C.c_void_p()
+    _check(lib().ftn_hubbard_term(ctx.handle, int(kind), float(t), float(u), int(dtype), C.byref(h)))
+    return Tensor(ctx, h)

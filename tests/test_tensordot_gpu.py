@@ -1,0 +1,189 @@
+"""Parity of the CUDA sign-permute and tensordot path (through the C ABI)
+with the CPU oracle.
+
+Tolerances (normwise: max |got - ref| / max |ref| over the compared entries):
+FP64 1e-10; TF32x3 1e-5; BF16x3 5e-5; TF32 5e-3; BF16 5e-2 (the operand
+rounding of each format times a sqrt(K)-grown accumulation).
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"f64": 1e-10, "tf32x3": 1e-5, "bf16x3": 5e-5, "tf32": 5e-3, "bf16": 5e-2}
+
+
+@pytest.fixture(scope="module")
+def F():
+    import torch
+
+    from paper_2410_02215_gb300 import ftn
+
+    assert torch.cuda.is_available()
+    ftn.lib()
+    return ftn
+
+
+@pytest.fixture(scope="module")
+def ctx(F):
+    c = F.Context()
+    yield c
+    c.synchronize()
+    c.close()
+
+
+def dense(t_blocks, legs, parity):
+    return O.embed_blocks(legs, parity, t_blocks)
+
+
+def relerr(got, ref):
+    den = np.max(np.abs(ref)) if ref.size else 1.0
+    return float(np.max(np.abs(got - ref), initial=0.0) / max(den, 1e-300))
+
+
+def upload(F, ctx, legs, parity, blocks, prec):
+    return F.Tensor.from_blocks(ctx, legs, parity, blocks, F.F64 if prec == "f64" else F.F32)
+
+
+LEGSETS = [
+    [(2, 1, 0), (1, 2, 1), (2, 2, 0), (1, 1, 1)],
+    [(1, 1, 1), (3, 1, 0), (2, 3, 1), (1, 2, 0), (2, 1, 1)],
+    [(3, 0, 1), (2, 2, 0), (0, 2, 1), (1, 3, 0)],
+    [(5, 3, 0), (4, 7, 1), (2, 1, 0), (33, 31, 1), (1, 1, 0), (2, 2, 1)],
+]
+
+
+@pytest.mark.parametrize("li", range(len(LEGSETS)))
+@pytest.mark.parametrize("parity", [0, 1])
+@pytest.mark.parametrize("dt", ["f64", "f32"])
+def test_transpose_parity(F, ctx, li, parity, dt):
+    legs = LEGSETS[li]
+    blocks = W.random_blocks(legs, parity, 100 + li)
+    t = F.Tensor.from_blocks(ctx, legs, parity, blocks, F.F64 if dt == "f64" else F.F32)
+    ref_in = dense(blocks, legs, parity)
+    if dt == "f32":
+        ref_in = O.GTensor(ref_in.data.astype(np.float32).astype(np.float64), ref_in.legs, parity)
+    for s in range(4):
+        perm = W.random_perm(len(legs), 7 * s + li)
+        out = F.transpose(ctx, t, perm)
+        got = dense(out.to_blocks(), out.legs, out.parity)
+        ref = O.transpose(ref_in, perm)
+        assert out.legs == ref.legs
+        assert np.array_equal(got.data, ref.data)  # sign flips and moves only: exact
+
+
+def test_dagger_parity(F, ctx):
+    legs = LEGSETS[1]
+    blocks = W.random_blocks(legs, 1, 5)
+    t = F.Tensor.from_blocks(ctx, legs, 1, blocks)
+    d = F.dagger(ctx, t)
+    ref = O.dagger(dense(blocks, legs, 1))
+    assert d.legs == ref.legs
+    assert np.array_equal(dense(d.to_blocks(), d.legs, d.parity).data, ref.data)
+
+
+def random_pair_case(seed):
+    g = W.rng(seed)
+    n = int(g.integers(0, 4))
+    ra, rb = n + int(g.integers(0, 4)), n + int(g.integers(0, 4))
+    ra, rb = max(ra, 1), max(rb, 1)
+    n = min(n, ra, rb)
+
+    def leg():
+        return (int(g.integers(0, 5)), int(g.integers(0, 5)), int(g.integers(0, 2)))
+
+    la = [leg() for _ in range(ra)]
+    lb = [leg() for _ in range(rb)]
+    ax = [int(v) for v in g.permutation(ra)[:n]]
+    ay = [int(v) for v in g.permutation(rb)[:n]]
+    for a, b in zip(ax, ay):
+        lb[b] = (la[a][0], la[a][1], 1 - la[a][2])
+    pa, pb = int(g.integers(0, 2)), int(g.integers(0, 2))
+    rc = ra + rb - 2 * n
+    perm = [int(v) for v in g.permutation(rc)] if g.integers(0, 2) else None
+    flip_a = int(g.integers(0, 1 << ra))
+    flip_b = int(g.integers(0, 1 << rb))
+    return la, lb, ax, ay, pa, pb, perm, flip_a, flip_b
+
+
+@pytest.mark.parametrize("prec", ["f64", "tf32x3", "bf16x3", "tf32", "bf16"])
+def test_tensordot_random_small(F, ctx, prec):
+    """Random ranks, sector sizes (incl. empty sectors), parities, arrows,
+    extra bond parities and output permutations."""
+    for seed in range(40):
+        la, lb, ax, ay, pa, pb, perm, fa, fb = random_pair_case(seed)
+        ba, bb = W.random_blocks(la, pa, 2 * seed), W.random_blocks(lb, pb, 2 * seed + 1)
+        A, B = dense(ba, la, pa), dense(bb, lb, pb)
+        ref = O.contract(A, B, ax, ay, flip_x=[k for k in range(len(la)) if fa >> k & 1],
+                         flip_y=[k for k in range(len(lb)) if fb >> k & 1])
+        if perm is not None:
+            ref = O.transpose(ref, perm)
+        a, b = upload(F, ctx, la, pa, ba, prec), upload(F, ctx, lb, pb, bb, prec)
+        c = F.tensordot(ctx, a, b, ax, ay, flip_a=fa, flip_b=fb, out_perm=perm, prec=prec)
+        got = dense(c.to_blocks(), c.legs, c.parity)
+        assert c.legs == ref.legs and c.parity == ref.parity
+        assert relerr(got.data, ref.data) <= TOL[prec], (seed, relerr(got.data, ref.data))
+    ctx.synchronize()
+
+
+@pytest.mark.parametrize("name", ["T1", "T2", "T3", "T4"])
+@pytest.mark.parametrize("prec", ["f64", "tf32x3", "bf16x3", "tf32"])
+def test_tensordot_cases_reduced(F, ctx, name, prec):
+    """The four microbenchmark contractions with every sector dimension halved:
+    full element-wise comparison (several tiles and ragged tails)."""
+    case = W.tensordot_case(name, seed=1, shrink=2 if name != "T4" else 4)
+    ba = W.random_blocks(case["legs_a"], 0, case["seed_a"])
+    bb = W.random_blocks(case["legs_b"], 0, case["seed_b"])
+    ref = O.transpose(O.contract(dense(ba, case["legs_a"], 0), dense(bb, case["legs_b"], 0), case["axes_a"],
+                                 case["axes_b"]), case["out_perm"])
+    a, b = upload(F, ctx, case["legs_a"], 0, ba, prec), upload(F, ctx, case["legs_b"], 0, bb, prec)
+    c = F.tensordot(ctx, a, b, case["axes_a"], case["axes_b"], out_perm=case["out_perm"], prec=prec)
+    got = dense(c.to_blocks(), c.legs, c.parity)
+    assert relerr(got.data, ref.data) <= TOL[prec]
+    ctx.synchronize()
+
+
+def read_entries(t, flat, indices):
+    table = {t.bits_of(m): off for m, off in t.block_table()}
+    out = []
+    for idx in indices:
+        bits = tuple(int(i >= l[0]) for i, l in zip(idx, t.legs))
+        loc = [i - l[0] if b else i for i, l, b in zip(idx, t.legs, bits)]
+        shp = t.block_shape(bits)
+        out.append(flat[table[bits] + int(np.ravel_multi_index(loc, shp))])
+    return np.array(out, dtype=np.float64)
+
+
+@pytest.mark.parametrize("name", ["T1", "T2", "T3", "T4"])
+@pytest.mark.parametrize("prec", ["f64", "tf32x3"])
+def test_tensordot_cases_full_size_sampled(F, ctx, name, prec):
+    """Full-size microbenchmark shapes, in the launch configuration the
+    benchmark times (same permutations), on 400 sampled output entries."""
+    case = W.tensordot_case(name, seed=0)
+    ba = W.random_blocks(case["legs_a"], 0, case["seed_a"])
+    bb = W.random_blocks(case["legs_b"], 0, case["seed_b"])
+    A, B = dense(ba, case["legs_a"], 0), dense(bb, case["legs_b"], 0)
+    idx, ref = O.contract_sampled(A, B, case["axes_a"], case["axes_b"], case["out_perm"], 400, 9)
+    a, b = upload(F, ctx, case["legs_a"], 0, ba, prec), upload(F, ctx, case["legs_b"], 0, bb, prec)
+    c = F.tensordot(ctx, a, b, case["axes_a"], case["axes_b"], out_perm=case["out_perm"], prec=prec)
+    got = read_entries(c, c.download(), idx)
+    assert relerr(got, ref) <= TOL[prec]
+    ctx.synchronize()
+
+
+def test_errors_are_reported(F, ctx):
+    la = [(2, 1, 0), (1, 2, 1)]
+    a = F.Tensor.from_blocks(ctx, la, 0, W.random_blocks(la, 0, 1))
+    b = F.Tensor.from_blocks(ctx, la, 0, W.random_blocks(la, 0, 2))
+    with pytest.raises(F.FtnError) as e:
+        F.tensordot(ctx, a, b, [0], [0])  # same duals
+    assert e.value.status == -4
+    with pytest.raises(F.FtnError) as e:
+        F.tensordot(ctx, a, b, [0], [1])  # sector dims differ
+    assert e.value.status == -2
+    with pytest.raises(F.FtnError) as e:
+        F.tensordot(ctx, a, b, [0], [1], prec="tf32")  # FP64 data on a TF32 path
+    assert e.value.status == -8
