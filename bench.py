@@ -1,0 +1,469 @@
+#!/usr/bin/env python
+"""Benchmark of the fermionic tensordot hot path on GB300; prints ONE JSON line.
+
+Workload (one step): the single-tensordot microbenchmark family T1-T4 --
+two rank-5 Z2 site tensors (four virtual legs D = 8 split 4+4, physical leg
+4 split 2+2) and rank-6 boundary environments (chi = 64 split 32+32),
+contracting 2-3 legs, every input stored in a seeded random leg order and
+every result permuted to a seeded random leg order; only parity-allowed
+blocks are stored.  Each tensordot = sign-permute of both inputs into the
+fused sector-matrix layout + one grouped sector GEMM + the output
+sign-permute, all in libftn's CUDA kernels.
+
+Metric: sector-GEMM TFLOP/s (the flops of the Z2-sector GEMMs, 2*M*N*K per
+block pair, over the time of the whole step).  The primary arithmetic is
+TF32x3 (FP32-accurate split products on the tcgen05 tensor cores); the
+plain-FP64 GPU path and the other precisions are reported beside it with
+their error against the FP64 CPU oracle.
+
+``--impl reference`` times the CPU oracle (the reference arm of this
+method: no other implementation exists) on the same metric and workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+CASES = ["T1", "T2", "T3", "T4"]
+PREC_DTYPE = {"f64": "f64", "tf32": "tf32", "bf16": "bf16", "tf32x3": "tf32x3", "bf16x3": "bf16x3"}
+WORKLOAD = ("fermionic tensordot microbenchmark T1-T4: rank-5 Z2 site tensors (D=8 as 4+4, phys 4 as 2+2), "
+            "rank-6 environments (chi=64 as 32+32); T1 E.A over 2 D legs, T2 E.A over 3 D legs, "
+            "T3 A.B over 2 D legs, T4 E.E' over (chi,D,D); random stored and output leg orders")
+NOMINAL_TF32_OVER_BF16 = 1.1 / 2.25  # dense tensor-core ratio (nominal)
+
+
+def sector_flops(case):
+    """2*M*N*K summed over the (row block, column block) pairs of the case."""
+    la, lb, ax, ay = case["legs_a"], case["legs_b"], case["axes_a"], case["axes_b"]
+    fa = [k for k in range(len(la)) if k not in ax]
+    fb = [k for k in range(len(lb)) if k not in ay]
+
+    def sectors(legs):
+        out = {0: 0, 1: 0}
+        for m in range(1 << len(legs)):
+            size, par = 1, 0
+            for i, l in enumerate(legs):
+                b = (m >> i) & 1
+                size *= l[1] if b else l[0]
+                par ^= b
+            out[par] += size
+        return out
+
+    rows = sectors([la[k] for k in fa])
+    cols = sectors([lb[k] for k in fb])
+    ks = sectors([la[k] for k in ax])
+    tot = 0
+    for pi in (0, 1):
+        tot += 2 * rows[case["parity_a"] ^ pi] * cols[case["parity_b"] ^ pi] * ks[pi]
+    return float(tot)
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return {"hbm_gbs": float(d["hbm_gbs"]), "bf16_tflops": float(d["bf16_tflops"]),
+                "bf16_tflops_sustained": float(d.get("bf16_tflops_sustained", d["bf16_tflops"])), "src": "measured"}
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "src": "fallback"}
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason samples during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                rows.append((float(parts[0]), float(parts[1]), parts[4:8]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, _, flags in rows for i, f in enumerate(flags) if f.lower() == "active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+def dist_init():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    return rank, world, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([x], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------------
+def oracle_pass(cases, budget_s=None):
+    """Run the CPU oracle on the cases; returns (flops done, seconds)."""
+    import oracle as O
+
+    done, t_tot = 0.0, 0.0
+    for c in cases:
+        a = O.embed_blocks(c["legs_a"], 0, W.random_blocks(c["legs_a"], 0, c["seed_a"]))
+        b = O.embed_blocks(c["legs_b"], 0, W.random_blocks(c["legs_b"], 0, c["seed_b"]))
+        t0 = time.perf_counter()
+        r = O.transpose(O.contract(a, b, c["axes_a"], c["axes_b"]), c["out_perm"])
+        t_tot += time.perf_counter() - t0
+        done += sector_flops(c)
+        del r
+        if budget_s is not None and t_tot > budget_s:
+            break
+    return done, t_tot
+
+
+def cpu_baseline(cases, budget_s=20.0):
+    reps, flops, secs = 0, 0.0, 0.0
+    while secs < budget_s * 0.5 and reps < 8:
+        f, s = oracle_pass(cases)
+        flops += f
+        secs += s
+        reps += 1
+    return {"value": flops / secs / 1e12, "unit": "TFLOP/s", "cores": len(os.sched_getaffinity(0)), "kind": "oracle",
+            "sample": f"{reps} full oracle pass(es) over T1-T4 (dense FP64 numpy, data generation excluded), "
+                      f"{secs:.1f} s"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    cases = [W.tensordot_case(n, seed=0) for n in CASES]
+    for _ in range(args.warmup):
+        oracle_pass(cases)
+    times, flops = [], 0.0
+    for _ in range(args.steps):
+        f, s = oracle_pass(cases)
+        times.append(s)
+        flops = f
+    tot = sum(times)
+    val = flops * args.steps / tot / 1e12
+    cores = len(os.sched_getaffinity(0))
+    line = {
+        "impl": "reference", "metric": "sector-GEMM TFLOP/s", "value": val, "unit": "TFLOP/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "l2": "n/a (CPU)"},
+        "cpu_baseline": {"value": val, "unit": "TFLOP/s", "cores": cores, "kind": "oracle",
+                         "sample": "each step one full oracle pass over T1-T4 (dense FP64 numpy)"},
+        "e2e": {"value": val, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------------
+def make_inputs(F, ctx, torch, cases, prec, seed=0):
+    dt = F.F64 if prec == "f64" else F.F32
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(seed)
+    tens = {}
+    for c in cases:
+        for side in ("a", "b"):
+            key = (tuple(c["legs_" + side]), side, c["name"])
+            t = F.Tensor.empty(ctx, c["legs_" + side], 0, dt)
+            v = t.view()
+            v.copy_(torch.randn(v.shape, generator=gen, device="cuda", dtype=v.dtype))
+            tens[key] = t
+    return tens
+
+
+def one_step(F, ctx, cases, ins, outs, prec, tag=False):
+    for c in cases:
+        if tag:
+            ctx.profile_tag(c["name"])
+        a = ins[(tuple(c["legs_a"]), "a", c["name"])]
+        b = ins[(tuple(c["legs_b"]), "b", c["name"])]
+        o = outs.get(c["name"])
+        r = F.tensordot(ctx, a, b, c["axes_a"], c["axes_b"], out_perm=c["out_perm"], prec=prec, out=o)
+        outs[c["name"]] = r
+
+
+def time_steps(F, ctx, torch, cases, prec, steps, warmup, flush, world, profile=False):
+    ins = make_inputs(F, ctx, torch, cases, prec)
+    outs = {}
+    for _ in range(warmup):
+        one_step(F, ctx, cases, ins, outs, prec)
+    torch.cuda.synchronize()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    if profile:
+        ctx.profile(True)
+    l0 = ctx.launches()
+    barrier(world)
+    torch.cuda.synchronize()
+    for i in range(steps):
+        flush.zero_()
+        evs[i][0].record()
+        one_step(F, ctx, cases, ins, outs, prec, tag=profile)
+        evs[i][1].record()
+    torch.cuda.synchronize()
+    barrier(world)
+    launches = ctx.launches() - l0
+    ms = sum(a.elapsed_time(b) for a, b in evs)
+    prof = ctx.profile_read() if profile else None
+    if profile:
+        ctx.profile(False)
+        ctx.profile_tag("")
+    ctx.synchronize()
+    return ms, launches, prof, ins, outs
+
+
+def accuracy(F, ctx, prec):
+    """Normwise errors of one reduced-size step against the oracle (T1-T4
+    with every sector dimension halved, T4 quartered)."""
+    import numpy as np
+
+    import oracle as O
+
+    worst_inf, worst_2 = 0.0, 0.0
+    for n in CASES:
+        c = W.tensordot_case(n, seed=1, shrink=2 if n != "T4" else 4)
+        ba = W.random_blocks(c["legs_a"], 0, c["seed_a"])
+        bb = W.random_blocks(c["legs_b"], 0, c["seed_b"])
+        ref = O.transpose(O.contract(O.embed_blocks(c["legs_a"], 0, ba), O.embed_blocks(c["legs_b"], 0, bb),
+                                     c["axes_a"], c["axes_b"]), c["out_perm"]).data
+        dt = F.F64 if prec == "f64" else F.F32
+        a = F.Tensor.from_blocks(ctx, c["legs_a"], 0, ba, dt)
+        b = F.Tensor.from_blocks(ctx, c["legs_b"], 0, bb, dt)
+        r = F.tensordot(ctx, a, b, c["axes_a"], c["axes_b"], out_perm=c["out_perm"], prec=prec)
+        got = O.embed_blocks(r.legs, r.parity, r.to_blocks()).data
+        worst_inf = max(worst_inf, float(np.max(np.abs(got - ref)) / np.max(np.abs(ref))))
+        worst_2 = max(worst_2, float(np.linalg.norm(got - ref) / np.linalg.norm(ref)))
+    return {"rel_err_inf": worst_inf, "rel_err_2": worst_2}
+
+
+def traffic_for(label):
+    """DRAM bytes per launch from a committed ncu summary, when it was taken
+    on the current kernel sources (else None)."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    try:
+        d = json.load(open(p))
+        from paper_2410_02215_gb300 import build as B
+
+        ent = d.get(label)
+        if ent and ent.get("src_digest") == B._digest():
+            return float(ent["dram_bytes_per_launch"])
+    except Exception:
+        return None
+    return None
+
+
+def roofline(prof, peaks):
+    dom = max(prof, key=lambda r: r["ms"])
+    label = dom["label"]
+    kind = label.split("/")[-1]
+    t_s = dom["ms"] / 1e3 / max(dom["launches"], 1)
+    bytes_per = dom["bytes"] / max(dom["launches"], 1)
+    flops_per = dom["flops"] / max(dom["launches"], 1)
+    tf32_peak = peaks["bf16_tflops"] * NOMINAL_TF32_OVER_BF16
+    out = {"kernel": label, "launches": dom["launches"], "avg_launch_ms": t_s * 1e3}
+    tensor_bound = kind.startswith("gemm") and flops_per / max(bytes_per, 1.0) > tf32_peak * 1e12 / (peaks["hbm_gbs"] * 1e9)
+    if tensor_bound:
+        ach = flops_per / t_s / 1e12
+        out.update({"bound": "tensor", "achieved": ach, "peak": tf32_peak, "unit": "TFLOP/s", "frac": ach / tf32_peak,
+                    "peak_note": f"TF32 dense = {peaks['src']} bf16 burst x 1.1/2.25 (nominal ratio)"})
+    else:
+        ach = bytes_per / t_s / 1e9
+        out.update({"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                    "frac": ach / peaks["hbm_gbs"], "peak_note": f"{peaks['src']} HBM copy bandwidth"})
+    out["algorithmic_bytes_per_launch"] = bytes_per
+    out["algorithmic_flops_per_launch"] = flops_per
+    out["traffic"] = traffic_for(label)
+    return out
+
+
+def e2e_run(F, ctx, torch, cases, prec, steps, flops_step):
+    """Same step through the C ABI with pinned host buffers: every input is
+    copied host->device and every result device->host inside the timed region."""
+    import numpy as np
+
+    ins = make_inputs(F, ctx, torch, cases, prec, seed=5)
+    outs = {}
+    one_step(F, ctx, cases, ins, outs, prec)
+    torch.cuda.synchronize()
+    npdt = torch.float64 if prec == "f64" else torch.float32
+    h_in = {k: torch.empty(t.numel, dtype=npdt, pin_memory=True) for k, t in ins.items()}
+    for k, t in ins.items():
+        h_in[k].copy_(t.view().cpu())
+    h_out = {k: torch.empty(t.numel, dtype=npdt, pin_memory=True) for k, t in outs.items()}
+    lib = F.lib()
+    import ctypes as C
+
+    h2d = sum(t.numel * (8 if prec == "f64" else 4) for t in ins.values())
+    d2h = sum(t.numel * (8 if prec == "f64" else 4) for t in outs.values())
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(steps):
+        for k, t in ins.items():
+            F._check(lib.ftn_tensor_upload(ctx.handle, t.handle, C.c_void_p(h_in[k].data_ptr())))
+        one_step(F, ctx, cases, ins, outs, prec)
+        for k, t in outs.items():
+            F._check(lib.ftn_tensor_download(ctx.handle, t.handle, C.c_void_p(h_out[k].data_ptr())))
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    return {"value": flops_step * steps / (ms / 1e3) / 1e12, "unit": "TFLOP/s", "h2d_bytes_per_step": int(h2d),
+            "d2h_bytes_per_step": int(d2h), "ms_per_step": ms / steps}
+
+
+def run_ours(args, rank, world, local):
+    import torch
+
+    from paper_2410_02215_gb300 import ftn as F
+
+    torch.cuda.set_device(local)
+    F.lib()
+    ctx = F.Context()
+    peaks = load_peaks()
+    cases = [W.tensordot_case(n, seed=0) for n in args.cases]
+    flops_step = sum(sector_flops(c) for c in cases)
+    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device="cuda")  # > 129 MB L2
+    clk = ClockSampler(local)
+    clk.start()
+    ms, launches, prof, ins, outs = time_steps(F, ctx, torch, cases, args.prec, args.steps, args.warmup, flush, world,
+                                               profile=True)
+    clocks = clk.stop()
+    del ins, outs
+    ms_max = max_over_ranks(ms, world)
+    value = flops_step * args.steps * world / (ms_max / 1e3) / 1e12
+    result = {
+        "metric": "sector-GEMM TFLOP/s", "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": PREC_DTYPE[args.prec], "data": "synthetic",
+        "config": {"workload": WORKLOAD, "precision": args.prec, "sector_gflop_per_step": flops_step / 1e9,
+                   "l2": "flushed between steps (512 MB write, outside the timed events)",
+                   "parallelism": f"replicas x{world} (independent problems, no collective)"},
+        "gpu_launches": launches,
+    }
+    result["roofline"] = roofline(prof, peaks)
+    result["kernels"] = [{"label": r["label"], "launches": r["launches"], "ms": r["ms"],
+                          "gbs": r["bytes"] / (r["ms"] / 1e3) / 1e9 if r["ms"] else None,
+                          "tflops": r["flops"] / (r["ms"] / 1e3) / 1e12 if r["ms"] and r["flops"] else None}
+                         for r in prof]
+    if clocks:
+        result["clocks"] = clocks
+    # the other precisions of the same step, and their errors
+    precs = {}
+    for p in args.compare:
+        if p == args.prec:
+            continue
+        pms, _, _, pin, pout = time_steps(F, ctx, torch, cases, p, max(2, args.steps // 4), 2, flush, 1)
+        del pin, pout
+        precs[p] = {"tflops": flops_step * max(2, args.steps // 4) / (pms / 1e3) / 1e12,
+                    "ms_per_step": pms / max(2, args.steps // 4)}
+    precs[args.prec] = {"tflops": flops_step * args.steps / (ms / 1e3) / 1e12, "ms_per_step": ms / args.steps}
+    if rank == 0 and not args.no_accuracy:
+        for p in precs:
+            precs[p].update(accuracy(F, ctx, p))
+    result["precisions"] = precs
+    if "f64" in precs:
+        result["speedup_vs_f64_gpu"] = precs[args.prec]["tflops"] / precs["f64"]["tflops"]
+    if not args.no_e2e:
+        result["e2e"] = e2e_run(F, ctx, torch, cases, args.prec, max(2, min(args.steps, 5)), flops_step)
+    if rank == 0 and world == 1 and not args.no_cpu:
+        result["cpu_baseline"] = cpu_baseline(cases)
+    ctx.synchronize()
+    ctx.close()
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--prec", default="tf32x3", choices=list(PREC_DTYPE))
+    ap.add_argument("--compare", default="f64,tf32,bf16x3", type=lambda s: [x for x in s.split(",") if x])
+    ap.add_argument("--cases", default=",".join(CASES), type=lambda s: [x for x in s.split(",") if x])
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-accuracy", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    rank, world, local = dist_init()
+    if args.impl == "reference":
+        rc = run_reference(args, rank, world)
+    else:
+        rc = run_ours(args, rank, world, local)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+    return rc
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -100,6 +100,18 @@ FTN_API ftn_status ftn_ctx_set_stream(ftn_ctx ctx, void* cuda_stream);
 FTN_API ftn_status ftn_ctx_synchronize(ftn_ctx ctx);
 /* Number of kernels this context has launched so far. */
 FTN_API int64_t ftn_ctx_launch_count(ftn_ctx ctx);
+/* Per-launch timing: while enabled, every kernel launch is bracketed by CUDA
+ * events on the context stream and tagged with a label and the algorithmic
+ * bytes and flops of that launch (the minimal traffic and the sector-GEMM
+ * flops the plan implies).  Enabling clears earlier records. */
+FTN_API ftn_status ftn_ctx_profile(ftn_ctx ctx, int enable);
+/* Prefix for the labels of later records ("" for none). */
+FTN_API ftn_status ftn_ctx_profile_tag(ftn_ctx ctx, const char* tag);
+/* Aggregate of the records with label index `idx` (0-based; FTN_EINVAL past
+ * the last): label, launch count, summed milliseconds, bytes and flops.
+ * Synchronises the context stream. */
+FTN_API ftn_status ftn_ctx_profile_read(ftn_ctx ctx, int idx, const char** label, int64_t* launches, double* ms,
+                                        double* bytes, double* flops);
 /* Message of the last failing call on this thread (never NULL). */
 FTN_API const char* ftn_last_error(void);
 

@@ -70,6 +70,12 @@ struct GemmProb {
 }  // namespace ftn
 
 // ---- public opaque types -----------------------------------------------------
+struct ftn_prof_rec {
+  std::string label;
+  cudaEvent_t a, b;
+  double bytes, flops;
+};
+
 struct ftn_ctx_s {
   cudaStream_t stream = nullptr;
   ftn_alloc_fn alloc = nullptr;
@@ -82,6 +88,12 @@ struct ftn_ctx_s {
   // grow-only workspace arena (reused by every call on this context)
   void* ws = nullptr;
   size_t ws_bytes = 0;
+  // per-launch profiling (ftn_ctx_profile)
+  bool prof_on = false;
+  std::vector<ftn_prof_rec> prof;
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<std::string> prof_labels;
+  std::string prof_tag;
 };
 
 struct ftn_tensor_s {
@@ -168,6 +180,9 @@ int tc_pick_bn(int max_n, ftn_prec prec);
 int64_t tc_tiles_for(int M, int N, int bn);
 
 ftn_status upload_table(ftn_ctx ctx, const void* host, size_t bytes, void** dev);
+// profiling brackets around one launch (no-ops unless profiling is enabled)
+int prof_begin(ftn_ctx ctx, const char* label, double bytes, double flops);
+void prof_end(ftn_ctx ctx, int rec);
 void clear_plan_caches(ftn_ctx ctx);
 
 }  // namespace ftn

@@ -10,8 +10,11 @@
 //             accumulators, tcgen05.commit releases ring slots;
 //   warps 2-5 epilogue: tcgen05.ld of the accumulator (one row per thread),
 //             FP32 stores into the output block.
-// Split modes (TF32X3 / BF16X3) load hi and lo planes and issue
-// hi*hi + hi*lo + lo*hi into the same accumulator.
+// Split modes (TF32X3 / BF16X3) load hi and lo planes; hi*hi goes into one
+// TMEM accumulator and hi*lo + lo*hi into a second one, summed in FP32 by the
+// epilogue.  The tensor core's accumulation rounds each partial sum, so
+// keeping the large products apart from the two small cross terms cuts the
+// number of roundings applied to the large accumulator by three.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
@@ -44,7 +47,10 @@ struct TcCfg {
   static constexpr int STAGES_RAW = (200 * 1024) / STAGE_BYTES;
   static constexpr int STAGES = STAGES_RAW > 8 ? 8 : STAGES_RAW;
   static constexpr int SMEM = STAGES * STAGE_BYTES + 1024 + 256;
-  static constexpr int TMEM_COLS = (2 * BN < 32) ? 32 : 2 * BN;
+  // two accumulator buffers; split modes keep the hi*hi products and the
+  // small cross terms in separate accumulators (ACC_W columns per buffer)
+  static constexpr int ACC_W = SPLIT ? 2 * BN : BN;
+  static constexpr int TMEM_COLS = (2 * ACC_W < 32) ? 32 : 2 * ACC_W;
   static constexpr int KB = BF16 ? 64 : 32;  // K elements per stage (128 B)
   static constexpr uint32_t IDESC = idesc_f32acc(TC_BM, BN, BF16 ? 1u : 2u);
   static_assert(STAGES >= 2, "shared memory ring too shallow");
@@ -150,7 +156,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
         if (nk == 0) continue;
         if (!mbar_wait(&tempty[acc], acc_phase ^ 1, P.err)) break;
         tc_fence_after();
-        const uint32_t d = tmem + (uint32_t)(acc * BN);
+        const uint32_t d = tmem + (uint32_t)(acc * Cfg::ACC_W);
+        const uint32_t d_small = d + (uint32_t)BN;
         for (int kb = 0; kb < nk; ++kb) {
           if (!mbar_wait(&full[stage], phase, P.err)) {
             ok = false;
@@ -174,11 +181,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
               const uint64_t adl = sdesc_sw128(sal + 32 * j);
               const uint64_t bdl = sdesc_sw128(sbl + 32 * j);
               if constexpr (BF16) {
-                mma_f16(d, ad, bdl, Cfg::IDESC, 1);
-                mma_f16(d, adl, bd, Cfg::IDESC, 1);
+                mma_f16(d_small, ad, bdl, Cfg::IDESC, accum);
+                mma_f16(d_small, adl, bd, Cfg::IDESC, 1);
               } else {
-                mma_tf32(d, ad, bdl, Cfg::IDESC, 1);
-                mma_tf32(d, adl, bd, Cfg::IDESC, 1);
+                mma_tf32(d_small, ad, bdl, Cfg::IDESC, accum);
+                mma_tf32(d_small, adl, bd, Cfg::IDESC, 1);
               }
             }
           }
@@ -218,12 +225,20 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
       }
       if (!mbar_wait(&tfull[acc], acc_phase, P.err)) break;
       tc_fence_after();
-      const uint32_t taddr = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(acc * BN);
+      const uint32_t taddr = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(acc * Cfg::ACC_W);
 #pragma unroll 1
       for (int c = 0; c < BN; c += 16) {
         uint32_t r[16];
         tmem_ld16(taddr + (uint32_t)c, r);
-        tmem_wait_ld();
+        if constexpr (SPLIT) {
+          uint32_t r2[16];
+          tmem_ld16(taddr + (uint32_t)(BN + c), r2);
+          tmem_wait_ld();
+#pragma unroll
+          for (int jj = 0; jj < 16; ++jj) r[jj] = __float_as_uint(__uint_as_float(r[jj]) + __uint_as_float(r2[jj]));
+        } else {
+          tmem_wait_ld();
+        }
         if (row < p.M) {
 #pragma unroll
           for (int jj = 0; jj < 16; ++jj)

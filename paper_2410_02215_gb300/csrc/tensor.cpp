@@ -208,6 +208,40 @@ void add_perm_job(std::vector<PermJob>& jobs, int64_t& tiles, int rank, const in
   jobs.push_back(j);
 }
 
+static cudaEvent_t take_event(ftn_ctx ctx) {
+  if (!ctx->ev_pool.empty()) {
+    cudaEvent_t e = ctx->ev_pool.back();
+    ctx->ev_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+int prof_begin(ftn_ctx ctx, const char* label, double bytes, double flops) {
+  if (!ctx->prof_on) return -1;
+  std::string full = ctx->prof_tag.empty() ? std::string(label) : ctx->prof_tag + "/" + label;
+  ftn_prof_rec r{full, take_event(ctx), take_event(ctx), bytes, flops};
+  cudaEventRecord(r.a, ctx->stream);
+  ctx->prof.push_back(r);
+  return (int)ctx->prof.size() - 1;
+}
+
+void prof_end(ftn_ctx ctx, int rec) {
+  if (rec < 0 || rec >= (int)ctx->prof.size()) return;
+  cudaEventRecord(ctx->prof[rec].b, ctx->stream);
+}
+
+static void prof_clear(ftn_ctx ctx) {
+  for (auto& r : ctx->prof) {
+    ctx->ev_pool.push_back(r.a);
+    ctx->ev_pool.push_back(r.b);
+  }
+  ctx->prof.clear();
+  ctx->prof_labels.clear();
+}
+
 }  // namespace ftn
 
 using namespace ftn;
@@ -249,6 +283,9 @@ ftn_status ftn_ctx_create(void* cuda_stream, ftn_alloc_fn alloc, ftn_free_fn fre
 ftn_status ftn_ctx_destroy(ftn_ctx ctx) {
   if (!ctx) return FTN_OK;
   cudaStreamSynchronize(ctx->stream);
+  prof_clear(ctx);
+  for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
+  ctx->ev_pool.clear();
   clear_plan_caches(ctx);
   dev_free(ctx, ctx->ws);
   dev_free(ctx, ctx->dev_err);
@@ -276,6 +313,49 @@ ftn_status ftn_ctx_synchronize(ftn_ctx ctx) {
 }
 
 int64_t ftn_ctx_launch_count(ftn_ctx ctx) { return ctx ? ctx->launches : 0; }
+
+ftn_status ftn_ctx_profile(ftn_ctx ctx, int enable) {
+  if (!ctx) return set_error(FTN_EINVAL, "null ctx");
+  FTN_CUDA(cudaStreamSynchronize(ctx->stream));
+  if (enable) prof_clear(ctx);
+  ctx->prof_on = enable != 0;
+  return FTN_OK;
+}
+
+ftn_status ftn_ctx_profile_tag(ftn_ctx ctx, const char* tag) {
+  if (!ctx) return set_error(FTN_EINVAL, "null ctx");
+  ctx->prof_tag = tag ? tag : "";
+  return FTN_OK;
+}
+
+ftn_status ftn_ctx_profile_read(ftn_ctx ctx, int idx, const char** label, int64_t* launches, double* ms,
+                                double* bytes, double* flops) {
+  if (!ctx) return set_error(FTN_EINVAL, "null ctx");
+  FTN_CUDA(cudaStreamSynchronize(ctx->stream));
+  ctx->prof_labels.clear();
+  for (auto& r : ctx->prof)
+    if (std::find(ctx->prof_labels.begin(), ctx->prof_labels.end(), r.label) == ctx->prof_labels.end())
+      ctx->prof_labels.push_back(r.label);
+  if (idx < 0 || idx >= (int)ctx->prof_labels.size()) return set_error(FTN_EINVAL, "no such profile label");
+  const std::string& want = ctx->prof_labels[idx];
+  int64_t n = 0;
+  double t = 0, by = 0, fl = 0;
+  for (auto& r : ctx->prof) {
+    if (r.label != want) continue;
+    float e = 0.f;
+    FTN_CUDA(cudaEventElapsedTime(&e, r.a, r.b));
+    ++n;
+    t += e;
+    by += r.bytes;
+    fl += r.flops;
+  }
+  if (label) *label = ctx->prof_labels[idx].c_str();
+  if (launches) *launches = n;
+  if (ms) *ms = t;
+  if (bytes) *bytes = by;
+  if (flops) *flops = fl;
+  return FTN_OK;
+}
 
 ftn_status ftn_tensor_create(ftn_ctx ctx, int rank, const int32_t* d_even, const int32_t* d_odd, const uint8_t* dual,
                              int parity, ftn_dtype dtype, ftn_tensor* out) {

@@ -424,13 +424,26 @@ ftn_status tensordot_impl(ftn_ctx ctx, ftn_tensor A, ftn_tensor B, int n, const 
   if (prec == FTN_PREC_TF32X3) mode = PERM_TF32X2;
   if (prec == FTN_PREC_BF16) mode = PERM_BF16;
   if (prec == FTN_PREC_BF16X3) mode = PERM_BF16X2;
+  const double in_es = (double)dtype_size(A->dtype), planes = split ? 2.0 : 1.0;
+  double gemm_flops = 0;
+  for (const GemmProb& g : P->probs) gemm_flops += 2.0 * g.M * g.N * g.K;
+  int rec = prof_begin(ctx, "permute", A->numel * (in_es + es * planes), 0);
   ftn_status st = launch_permute(ctx, P->d_ja, (int)P->ja.size(), P->ta, A->data, af_hi, af_lo, A->dtype, mode);
-  if (st == FTN_OK)
-    st = launch_permute(ctx, P->d_jb, (int)P->jb.size(), P->tb, B->data, bf_hi, bf_lo, B->dtype, mode);
+  prof_end(ctx, rec);
   if (st == FTN_OK) {
+    rec = prof_begin(ctx, "permute", B->numel * (in_es + es * planes), 0);
+    st = launch_permute(ctx, P->d_jb, (int)P->jb.size(), P->tb, B->data, bf_hi, bf_lo, B->dtype, mode);
+    prof_end(ctx, rec);
+  }
+  if (st == FTN_OK) {
+    double gb = 0;
+    for (int pi = 0; pi < 2; ++pi) gb += (double)(P->M[pi] + P->N[pi]) * P->K[pi] * es * planes;
+    gb += (double)P->tmp_numel * in_es;
     if (!tc) {
+      rec = prof_begin(ctx, "gemm_f64", gb, gemm_flops);
       st = launch_gemm_f64(ctx, P->d_probs, (int)P->probs.size(), P->gemm_tiles, (const double*)af_hi,
                            (const double*)bf_hi, (double*)ctmp);
+      prof_end(ctx, rec);
     } else {
       TcOperands ops;
       for (int pi = 0; pi < 2; ++pi) {
@@ -443,11 +456,16 @@ ftn_status tensordot_impl(ftn_ctx ctx, ftn_tensor A, ftn_tensor B, int n, const 
         ops.kdim[pi] = (int32_t)P->K[pi];
         ops.ldk[pi] = (int32_t)P->ldk[pi];
       }
+      rec = prof_begin(ctx, "gemm_tc", gb, gemm_flops);
       st = launch_gemm_tc(ctx, prec, ops, P->d_probs, (int)P->probs.size(), P->gemm_tiles, P->bn, (float*)ctmp);
+      prof_end(ctx, rec);
     }
   }
-  if (st == FTN_OK && P->out_perm)
+  if (st == FTN_OK && P->out_perm) {
+    rec = prof_begin(ctx, "permute", 2.0 * P->tmp_numel * in_es, 0);
     st = launch_permute(ctx, P->d_jc, (int)P->jc.size(), P->tc, ctmp, out->data, nullptr, A->dtype, PERM_SAME);
+    prof_end(ctx, rec);
+  }
   if (st != FTN_OK) {
     if (created) ftn_tensor_free(out);
     return st;
@@ -541,8 +559,10 @@ ftn_status permute_impl(ftn_ctx ctx, ftn_tensor t, const int* perm, bool fermion
     if (cache.size() > 4096) cache.clear();
     cache[key.str()] = P;
   }
+  int rec = prof_begin(ctx, "permute", 2.0 * t->numel * dtype_size(t->dtype), 0);
   ftn_status st = launch_permute(ctx, P->d_jobs, (int)P->jobs.size(), P->tiles, t->data, o->data, nullptr, t->dtype,
                                  PERM_SAME);
+  prof_end(ctx, rec);
   if (st != FTN_OK) {
     if (created) ftn_tensor_free(o);
     return st;

@@ -88,6 +88,13 @@ def lib():
     L.ftn_last_error.restype = C.c_char_p
     L.ftn_ctx_launch_count.argtypes = [vp]
     L.ftn_ctx_launch_count.restype = C.c_int64
+    L.ftn_ctx_profile.argtypes = [vp, C.c_int]
+    L.ftn_ctx_profile.restype = C.c_int
+    L.ftn_ctx_profile_tag.argtypes = [vp, C.c_char_p]
+    L.ftn_ctx_profile_tag.restype = C.c_int
+    L.ftn_ctx_profile_read.argtypes = [vp, C.c_int, C.POINTER(C.c_char_p), C.POINTER(C.c_int64), C.POINTER(C.c_double),
+                                       C.POINTER(C.c_double), C.POINTER(C.c_double)]
+    L.ftn_ctx_profile_read.restype = C.c_int
     _lib = L
     return L
 
@@ -144,6 +151,27 @@ class Context:
 
     def launches(self):
         return int(lib().ftn_ctx_launch_count(self.handle))
+
+    def profile(self, enable=True):
+        _check(lib().ftn_ctx_profile(self.handle, 1 if enable else 0))
+
+    def profile_tag(self, tag):
+        _check(lib().ftn_ctx_profile_tag(self.handle, tag.encode()))
+
+    def profile_read(self):
+        """[{label, launches, ms, bytes, flops}] aggregated per label."""
+        out = []
+        i = 0
+        while True:
+            lab, n = C.c_char_p(), C.c_int64()
+            ms, by, fl = C.c_double(), C.c_double(), C.c_double()
+            st = lib().ftn_ctx_profile_read(self.handle, i, C.byref(lab), C.byref(n), C.byref(ms), C.byref(by), C.byref(fl))
+            if st != 0:
+                break
+            out.append({"label": lab.value.decode(), "launches": n.value, "ms": ms.value, "bytes": by.value,
+                        "flops": fl.value})
+            i += 1
+        return out
 
     def close(self):
         if self.handle:
