@@ -26,7 +26,7 @@ constexpr int DEV_ERR_TIMEOUT = 1;
 //   B: the rest (product PB).
 // One CTA tile covers TI x TO elements of one batch index.
 constexpr int PERM_TI = 32;
-constexpr int PERM_TO = 32;
+constexpr int PERM_TO = 64;
 
 struct PermJob {
   int64_t src_off;   // elements from the source base
@@ -54,6 +54,11 @@ enum PermMode {
 };
 
 // ---- grouped sector GEMM problem: C[m, n] = sum_k A[m, k] B[n, k] ------------
+// The result element (m, n) is stored at c_off + rowpart(m) + colpart(n)
+// multiplied by c_sign, where rowpart/colpart expand m and n row-major over
+// the row legs (rdim, rstr) and the column legs (cdim, cstr).  This places
+// the result directly in a permuted output layout (the fermionic sign of the
+// permutation is one sign per block).
 struct GemmProb {
   int64_t tile_begin;
   int64_t a_off;   // element offset of the first A row (FP64 path)
@@ -61,11 +66,27 @@ struct GemmProb {
   int64_t c_off;   // element offset of the output block
   int32_t M, N, K;
   int32_t pi;      // fused-matrix pair (bond parity sector)
-  int32_t lda, ldb, ldc;
+  int32_t lda, ldb;
   int32_t a_row0, b_row0;  // first row inside the fused pi-matrices (TMA)
   int32_t tiles_m, tiles_n;
+  int32_t c_sign;
+  int32_t nrl, ncl;
   int32_t pad_;
+  int32_t rdim[MAXR], cdim[MAXR];
+  int64_t rstr[MAXR], cstr[MAXR];
 };
+
+// Offset of the row-major multi-index of x over n legs (last leg fastest).
+__host__ __device__ inline int64_t expand_index(int64_t x, int n, const int32_t* dim, const int64_t* str) {
+  int64_t off = 0;
+  for (int l = n - 1; l >= 0; --l) {
+    const int64_t d = dim[l];
+    const int64_t idx = x % d;
+    x /= d;
+    off += idx * str[l];
+  }
+  return off;
+}
 
 }  // namespace ftn
 

@@ -32,7 +32,7 @@ __global__ void __launch_bounds__(256) gemm_f64_kernel(const GemmProb* __restric
   for (int64_t t = blockIdx.x; t < tiles; t += gridDim.x) {
     if (tid == 0) s_p = find_prob(probs, nprobs, t);
     __syncthreads();
-    const GemmProb p = probs[s_p];
+    const GemmProb& p = probs[s_p];
     const int64_t local = t - p.tile_begin;
     const int m0 = (int)(local / p.tiles_n) * F64_BM;
     const int n0 = (int)(local % p.tiles_n) * F64_BN;
@@ -68,14 +68,22 @@ __global__ void __launch_bounds__(256) gemm_f64_kernel(const GemmProb* __restric
       }
       __syncthreads();
     }
+    int64_t cpart[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      int gn = n0 + tx + 16 * c;
+      cpart[c] = gn < p.N ? expand_index(gn, p.ncl, p.cdim, p.cstr) : 0;
+    }
+    const double sg = (double)p.c_sign;
 #pragma unroll
     for (int a = 0; a < 4; ++a) {
       int gm = m0 + ty + 16 * a;
       if (gm >= p.M) continue;
+      const int64_t rpart = p.c_off + expand_index(gm, p.nrl, p.rdim, p.rstr);
 #pragma unroll
       for (int c = 0; c < 4; ++c) {
         int gn = n0 + tx + 16 * c;
-        if (gn < p.N) C[p.c_off + (int64_t)gm * p.ldc + gn] = acc[a][c];
+        if (gn < p.N) C[rpart + cpart[c]] = sg * acc[a][c];
       }
     }
     __syncthreads();

@@ -44,9 +44,13 @@ struct TcCfg {
   static constexpr int B_BYTES = BN * 128;
   static constexpr int OPS = SPLIT ? 2 : 1;
   static constexpr int STAGE_BYTES = (A_BYTES + B_BYTES) * OPS;
-  static constexpr int STAGES_RAW = (200 * 1024) / STAGE_BYTES;
+  // epilogue staging: per epilogue warp a 32 x (CW + 1) FP32 tile
+  static constexpr int CW = BN < 32 ? BN : 32;
+  static constexpr int EPI_BYTES = 4 * 32 * (CW + 1) * 4;
+  static constexpr int BUDGET = 227 * 1024 - 1024 - 256 - EPI_BYTES;
+  static constexpr int STAGES_RAW = BUDGET / STAGE_BYTES;
   static constexpr int STAGES = STAGES_RAW > 8 ? 8 : STAGES_RAW;
-  static constexpr int SMEM = STAGES * STAGE_BYTES + 1024 + 256;
+  static constexpr int SMEM = STAGES * STAGE_BYTES + 1024 + 256 + EPI_BYTES;
   // two accumulator buffers; split modes keep the hi*hi products and the
   // small cross terms in separate accumulators (ACC_W columns per buffer)
   static constexpr int ACC_W = SPLIT ? 2 * BN : BN;
@@ -79,6 +83,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
   uint64_t* tempty = tfull + 2;
   uint64_t* drain = tempty + 2;
   uint32_t* tslot = reinterpret_cast<uint32_t*>(drain + 1);
+  float* epi = reinterpret_cast<float*>(smem + Cfg::STAGES * Cfg::STAGE_BYTES + 256);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
@@ -206,7 +211,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
     }
   } else {
     // ---------------- epilogue (warps 2..5) ----------------
+    // TMEM -> registers (one row per lane) -> shared memory -> global, one
+    // 32-column chunk at a time, so that every warp store writes consecutive
+    // columns of one row.  Output addresses follow the problem's row/column
+    // leg tables (a permuted output layout costs nothing extra here).
     const int q = warp & 3;
+    float* stg = epi + (warp - 2) * 32 * (Cfg::CW + 1);
     int acc = 0;
     uint32_t acc_phase = 0;
     for (int64_t t = blockIdx.x; t < P.tiles; t += gridDim.x) {
@@ -216,40 +226,59 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
       const int n0 = (int)(local % p.tiles_n) * BN;
       const int nk = (p.K + Cfg::KB - 1) / Cfg::KB;
       const int row = m0 + 32 * q + lane;
-      float* crow = P.C + p.c_off + (int64_t)row * p.ldc + n0;
+      const int64_t rpart = row < p.M ? p.c_off + expand_index(row, p.nrl, p.rdim, p.rstr) : 0;
       const int ncols = p.N - n0 < BN ? p.N - n0 : BN;
-      if (nk == 0) {
-        if (row < p.M)
-          for (int c = 0; c < ncols; ++c) crow[c] = 0.0f;
-        continue;
+      const int nrows = p.M - (m0 + 32 * q) < 32 ? p.M - (m0 + 32 * q) : 32;
+      const float sg = (float)p.c_sign;
+      if (nk > 0) {
+        if (!mbar_wait(&tfull[acc], acc_phase, P.err)) break;
+        tc_fence_after();
       }
-      if (!mbar_wait(&tfull[acc], acc_phase, P.err)) break;
-      tc_fence_after();
       const uint32_t taddr = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(acc * Cfg::ACC_W);
 #pragma unroll 1
-      for (int c = 0; c < BN; c += 16) {
-        uint32_t r[16];
-        tmem_ld16(taddr + (uint32_t)c, r);
-        if constexpr (SPLIT) {
-          uint32_t r2[16];
-          tmem_ld16(taddr + (uint32_t)(BN + c), r2);
-          tmem_wait_ld();
+      for (int c = 0; c < BN; c += Cfg::CW) {
+        float v[Cfg::CW];
+        if (nk > 0) {
 #pragma unroll
-          for (int jj = 0; jj < 16; ++jj) r[jj] = __float_as_uint(__uint_as_float(r[jj]) + __uint_as_float(r2[jj]));
+          for (int h = 0; h < Cfg::CW; h += 16) {
+            uint32_t r[16];
+            tmem_ld16(taddr + (uint32_t)(c + h), r);
+            if constexpr (SPLIT) {
+              uint32_t r2[16];
+              tmem_ld16(taddr + (uint32_t)(BN + c + h), r2);
+              tmem_wait_ld();
+#pragma unroll
+              for (int jj = 0; jj < 16; ++jj) v[h + jj] = __uint_as_float(r[jj]) + __uint_as_float(r2[jj]);
+            } else {
+              tmem_wait_ld();
+#pragma unroll
+              for (int jj = 0; jj < 16; ++jj) v[h + jj] = __uint_as_float(r[jj]);
+            }
+          }
         } else {
-          tmem_wait_ld();
-        }
-        if (row < p.M) {
 #pragma unroll
-          for (int jj = 0; jj < 16; ++jj)
-            if (c + jj < ncols) crow[c + jj] = __uint_as_float(r[jj]);
+          for (int jj = 0; jj < Cfg::CW; ++jj) v[jj] = 0.0f;
         }
+#pragma unroll
+        for (int jj = 0; jj < Cfg::CW; ++jj) stg[lane * (Cfg::CW + 1) + jj] = v[jj];
+        __syncwarp();
+        const int col = c + lane;
+        const bool okc = lane < Cfg::CW && col < ncols;
+        const int64_t cpart = okc ? expand_index(n0 + col, p.ncl, p.cdim, p.cstr) : 0;
+#pragma unroll 4
+        for (int rr = 0; rr < 32; ++rr) {
+          const int64_t rp = __shfl_sync(0xffffffffu, rpart, rr);
+          if (rr < nrows && okc) P.C[rp + cpart] = sg * stg[rr * (Cfg::CW + 1) + lane];
+        }
+        __syncwarp();
       }
-      tc_fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&tempty[acc]);
-      acc ^= 1;
-      if (acc == 0) acc_phase ^= 1;
+      if (nk > 0) {
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&tempty[acc]);
+        acc ^= 1;
+        if (acc == 0) acc_phase ^= 1;
+      }
     }
   }
   tc_fence_before();

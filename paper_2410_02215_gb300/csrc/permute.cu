@@ -2,9 +2,14 @@
 // order or into the fused sector-matrix layout of a contraction, multiplying
 // it by its fermionic sign (one sign per block: every factor of Eq.
 // (transposition), of the bond parity g and of the fusion order depends only
-// on the block's parity bits).  Tiled through shared memory so that both the
-// reads (along the source's contiguous suffix I) and the writes (along the
-// destination's fastest legs) are coalesced.
+// on the block's parity bits).
+//
+// Each CTA tile covers PERM_TO rows of the O group (destination-fast legs)
+// times PERM_TI elements of the I group (the source's contiguous suffix) for
+// one batch index.  Loads run along I (coalesced in the source); stores run
+// along O through a shared-memory transpose, or directly along I when the
+// destination is also contiguous there.  Every thread keeps PERM_TO / 8 loads
+// in flight so that enough bytes are outstanding per SM to cover HBM latency.
 #include <cuda_bf16.h>
 
 #include "common.h"
@@ -36,14 +41,17 @@ __device__ __forceinline__ void put(void* dst0, void* dst1, int64_t idx, Tin v) 
   }
 }
 
+constexpr int PT = 256;              // threads per CTA
+constexpr int PR = PERM_TO / (PT / 32);  // rows per thread in a phase
+
 template <typename Tin, int MODE>
-__global__ void __launch_bounds__(256) perm_kernel(const PermJob* __restrict__ jobs, int njobs, int64_t tiles,
-                                                   const Tin* __restrict__ src, void* __restrict__ dst0,
-                                                   void* __restrict__ dst1) {
+__global__ void __launch_bounds__(PT) perm_kernel(const PermJob* __restrict__ jobs, int njobs, int64_t tiles,
+                                                  const Tin* __restrict__ src, void* __restrict__ dst0,
+                                                  void* __restrict__ dst1) {
   __shared__ Tin tile[PERM_TO][PERM_TI + 1];
-  __shared__ int64_t rowS[PERM_TO];
-  __shared__ int64_t rowD[PERM_TO];
-  __shared__ int64_t colD[PERM_TI];
+  __shared__ int32_t rowS[PERM_TO];
+  __shared__ int32_t rowD[PERM_TO];
+  __shared__ int32_t colD[PERM_TI];
   __shared__ int64_t baseS, baseD;
   __shared__ int s_job;
   const int tid = threadIdx.x;
@@ -62,16 +70,16 @@ __global__ void __launch_bounds__(256) perm_kernel(const PermJob* __restrict__ j
     }
     __syncthreads();
     const PermJob* j = jobs + s_job;
-    const int nI = j->nI, nO = j->nO, nB = j->nB;
+    const int nI = j->nI, nO = j->nO;
     const int PI = j->PI, PO = j->PO;
     const int64_t local = t - j->tile_begin;
     const int64_t per_b = (int64_t)j->tiles_i * j->tiles_o;
     const int64_t b = local / per_b;
     const int rem = (int)(local - b * per_b);
     const int ti = rem % j->tiles_i, to = rem / j->tiles_i;
-    if (tid == 0) {
+    if (tid == PT - 1) {
       int64_t s = j->src_off, d = j->dst_off, x = b;
-      for (int q = nI + nO + nB - 1; q >= nI + nO; --q) {
+      for (int q = nI + nO + j->nB - 1; q >= nI + nO; --q) {
         int64_t idx = x % j->dim[q];
         x /= j->dim[q];
         s += idx * j->sstr[q];
@@ -82,14 +90,14 @@ __global__ void __launch_bounds__(256) perm_kernel(const PermJob* __restrict__ j
     }
     if (tid < PERM_TO) {
       int o = to * PERM_TO + tid;
-      int64_t s = 0, d = 0;
+      int32_t s = 0, d = 0;
       if (o < PO) {
         int x = o;
         for (int q = nI + nO - 1; q >= nI; --q) {
           int idx = x % j->dim[q];
           x /= j->dim[q];
-          s += idx * j->sstr[q];
-          d += idx * j->dstr[q];
+          s += idx * (int32_t)j->sstr[q];
+          d += idx * (int32_t)j->dstr[q];
         }
       }
       rowS[tid] = s;
@@ -97,13 +105,13 @@ __global__ void __launch_bounds__(256) perm_kernel(const PermJob* __restrict__ j
     } else if (tid < PERM_TO + PERM_TI) {
       int c = tid - PERM_TO;
       int i = ti * PERM_TI + c;
-      int64_t d = 0;
+      int32_t d = 0;
       if (i < PI) {
         int x = i;
         for (int q = nI - 1; q >= 0; --q) {
           int idx = x % j->dim[q];
           x /= j->dim[q];
-          d += idx * j->dstr[q];
+          d += idx * (int32_t)j->dstr[q];
         }
       }
       colD[c] = d;
@@ -111,24 +119,40 @@ __global__ void __launch_bounds__(256) perm_kernel(const PermJob* __restrict__ j
     __syncthreads();
     const int i = ti * PERM_TI + tx;
     const Tin sgn = (Tin)j->sign;
-#pragma unroll
-    for (int r = ty; r < PERM_TO; r += 8) {
-      int o = to * PERM_TO + r;
-      if (o < PO && i < PI) tile[r][tx] = src[baseS + rowS[r] + i];
-    }
-    __syncthreads();
+    const int64_t bS = baseS, bD = baseD;
+    const int o0 = to * PERM_TO;
     if (j->store_fast_i) {
+      // destination contiguous along I: copy straight through registers
+      Tin v[PR];
 #pragma unroll
-      for (int r = ty; r < PERM_TO; r += 8) {
-        int o = to * PERM_TO + r;
-        if (o < PO && i < PI) put<Tin, MODE>(dst0, dst1, baseD + rowD[r] + colD[tx], sgn * tile[r][tx]);
+      for (int r = 0; r < PR; ++r) {
+        int row = ty + r * (PT / 32);
+        v[r] = (o0 + row < PO && i < PI) ? src[bS + rowS[row] + i] : Tin(0);
+      }
+      const int32_t cd = colD[tx];
+#pragma unroll
+      for (int r = 0; r < PR; ++r) {
+        int row = ty + r * (PT / 32);
+        if (o0 + row < PO && i < PI) put<Tin, MODE>(dst0, dst1, bD + rowD[row] + cd, sgn * v[r]);
       }
     } else {
-      const int o = to * PERM_TO + tx;
 #pragma unroll
-      for (int c = ty; c < PERM_TI; c += 8) {
-        int i2 = ti * PERM_TI + c;
-        if (o < PO && i2 < PI) put<Tin, MODE>(dst0, dst1, baseD + rowD[tx] + colD[c], sgn * tile[tx][c]);
+      for (int r = 0; r < PR; ++r) {
+        int row = ty + r * (PT / 32);
+        if (o0 + row < PO && i < PI) tile[row][tx] = src[bS + rowS[row] + i];
+      }
+      __syncthreads();
+      // stores along O: lane -> row, warps -> columns of I
+#pragma unroll
+      for (int half = 0; half < PERM_TO / 32; ++half) {
+        const int row = half * 32 + tx;
+        const bool okr = o0 + row < PO;
+        const int32_t rd = rowD[row];
+#pragma unroll
+        for (int c = ty; c < PERM_TI; c += PT / 32) {
+          const int i2 = ti * PERM_TI + c;
+          if (okr && i2 < PI) put<Tin, MODE>(dst0, dst1, bD + rd + colD[c], sgn * tile[row][c]);
+        }
       }
     }
     __syncthreads();
@@ -139,9 +163,9 @@ template <typename Tin, int MODE>
 static cudaError_t go(ftn_ctx ctx, const PermJob* d_jobs, int njobs, int64_t tiles, const void* src, void* dst0,
                       void* dst1) {
   int64_t grid = tiles;
-  int64_t cap = (int64_t)ctx->num_sms * 8;
+  int64_t cap = (int64_t)ctx->num_sms * 16;
   if (grid > cap) grid = cap;
-  perm_kernel<Tin, MODE><<<(unsigned)grid, 256, 0, ctx->stream>>>(d_jobs, njobs, tiles, (const Tin*)src, dst0, dst1);
+  perm_kernel<Tin, MODE><<<(unsigned)grid, PT, 0, ctx->stream>>>(d_jobs, njobs, tiles, (const Tin*)src, dst0, dst1);
   return cudaGetLastError();
 }
 

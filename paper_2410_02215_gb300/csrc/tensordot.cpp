@@ -57,6 +57,8 @@ static bool jobs_in_bounds(const std::vector<PermJob>& jobs, int64_t src_n, int6
       md += (int64_t)(j.dim[q] - 1) * j.dstr[q];
     }
     if (j.src_off < 0 || j.dst_off < 0 || ms >= src_n || md >= dst_n) return false;
+    // the kernel keeps offsets relative to a block in 32-bit integers
+    if (ms - j.src_off >= ((int64_t)1 << 31) || md - j.dst_off >= ((int64_t)1 << 31)) return false;
   }
   return true;
 }
@@ -68,7 +70,10 @@ static bool probs_in_bounds(const std::vector<GemmProb>& probs, int64_t a_n, int
       if (g.a_off + (int64_t)(g.M - 1) * g.lda + g.K > a_n) return false;
       if (g.b_off + (int64_t)(g.N - 1) * g.ldb + g.K > b_n) return false;
     }
-    if (g.c_off + (int64_t)(g.M - 1) * g.ldc + g.N > c_n) return false;
+    int64_t mr = 1, mc = 1, top = g.c_off;
+    for (int l = 0; l < g.nrl; ++l) mr *= g.rdim[l], top += (int64_t)(g.rdim[l] - 1) * g.rstr[l];
+    for (int l = 0; l < g.ncl; ++l) mc *= g.cdim[l], top += (int64_t)(g.cdim[l] - 1) * g.cstr[l];
+    if (mr != g.M || mc != g.N || g.c_off < 0 || top >= c_n) return false;
   }
   return true;
 }
@@ -98,7 +103,7 @@ struct TdPlan {
   int32_t cd0[MAXR], cd1[MAXR];
   uint8_t cdual[MAXR];
   int cpar = 0;
-  int64_t tmp_numel = 0;  // result before out_perm
+  int64_t tmp_numel = 0;  // elements of the result
   // device copies
   std::shared_ptr<DevTables> dev;
   PermJob* d_ja = nullptr;
@@ -249,6 +254,28 @@ static ftn_status build_plan(ftn_ctx ctx, const ftn_tensor_s* A, const ftn_tenso
     tot += block_size(&tmp, block_mask(cr, tmp.parity, b));
   }
   P->tmp_numel = tot;
+  // ---- final result layout (out_perm applied in the GEMM epilogue) ----
+  P->cr = cr;
+  P->cpar = tmp.parity;
+  bool ident = true;
+  if (out_perm)
+    for (int u = 0; u < cr; ++u) ident = ident && out_perm[u] == u;
+  P->out_perm = !ident;
+  int perm[MAXR];
+  for (int u = 0; u < cr; ++u) perm[u] = P->out_perm ? out_perm[u] : u;
+  for (int u = 0; u < cr; ++u)
+    P->cd0[u] = tmp.d0[perm[u]], P->cd1[u] = tmp.d1[perm[u]], P->cdual[u] = tmp.dual[perm[u]];
+  ftn_tensor_s fin;
+  fin.rank = cr;
+  fin.parity = tmp.parity;
+  for (int u = 0; u < cr; ++u) fin.d0[u] = P->cd0[u], fin.d1[u] = P->cd1[u];
+  std::vector<int64_t> foff(nblocks(cr, fin.parity));
+  int64_t fin_numel = 0;
+  for (int64_t b = 0; b < (int64_t)foff.size(); ++b) {
+    foff[b] = fin_numel;
+    fin_numel += block_size(&fin, block_mask(cr, fin.parity, b));
+  }
+  P->tmp_numel = fin_numel;
   // ---- GEMM problems, one per result block ----
   const bool tc = prec != FTN_PREC_F64;
   int maxN = 1;
@@ -271,12 +298,26 @@ static ftn_status build_plan(ftn_ctx ctx, const ftn_tensor_s* A, const ftn_tenso
     if (g.M == 0 || g.N == 0) continue;
     g.pi = pi;
     g.lda = g.ldb = (int32_t)P->ldk[pi];
-    g.ldc = g.N;
     g.a_row0 = (int32_t)rowoff[pi][mA];
     g.b_row0 = (int32_t)coloff[pi][mB];
     g.a_off = P->afoff[pi] + rowoff[pi][mA] * P->ldk[pi];
     g.b_off = P->bfoff[pi] + coloff[pi][mB] * P->ldk[pi];
-    g.c_off = toff[b];
+    // destination block in the (permuted) result and the stride of each leg
+    uint32_t mo = 0;
+    for (int u = 0; u < cr; ++u) mo |= ((m >> perm[u]) & 1u) << u;
+    int64_t dims[MAXR], str[MAXR];
+    for (int k = 0; k < cr; ++k) dims[k] = leg_dim(&tmp, k, m);
+    int64_t st = 1;
+    for (int u = cr - 1; u >= 0; --u) {
+      str[perm[u]] = st;
+      st *= dims[perm[u]];
+    }
+    g.c_off = cr == 0 ? 0 : foff[mo >> 1];
+    g.c_sign = inversion_parity(cr, perm, m) ? -1 : 1;
+    g.nrl = P->nfa;
+    g.ncl = P->nfb;
+    for (int k = 0; k < P->nfa; ++k) g.rdim[k] = (int32_t)dims[k], g.rstr[k] = str[k];
+    for (int k = 0; k < P->nfb; ++k) g.cdim[k] = (int32_t)dims[P->nfa + k], g.cstr[k] = str[P->nfa + k];
     if (tc) {
       g.tiles_m = (g.M + 127) / 128;
       g.tiles_n = (g.N + P->bn - 1) / P->bn;
@@ -288,47 +329,8 @@ static ftn_status build_plan(ftn_ctx ctx, const ftn_tensor_s* A, const ftn_tenso
     P->gemm_tiles += (int64_t)g.tiles_m * g.tiles_n;
     P->probs.push_back(g);
   }
-  // ---- optional out_perm ----
-  P->cr = cr;
-  P->cpar = tmp.parity;
-  bool ident = true;
-  if (out_perm)
-    for (int u = 0; u < cr; ++u) ident = ident && out_perm[u] == u;
-  P->out_perm = !ident;
-  if (!P->out_perm) {
-    for (int k = 0; k < cr; ++k) P->cd0[k] = tmp.d0[k], P->cd1[k] = tmp.d1[k], P->cdual[k] = tmp.dual[k];
-  } else {
-    for (int u = 0; u < cr; ++u)
-      P->cd0[u] = tmp.d0[out_perm[u]], P->cd1[u] = tmp.d1[out_perm[u]], P->cdual[u] = tmp.dual[out_perm[u]];
-    ftn_tensor_s fin;
-    fin.rank = cr;
-    fin.parity = tmp.parity;
-    for (int u = 0; u < cr; ++u) fin.d0[u] = P->cd0[u], fin.d1[u] = P->cd1[u];
-    std::vector<int64_t> foff(nblocks(cr, fin.parity));
-    int64_t t2 = 0;
-    for (int64_t b = 0; b < (int64_t)foff.size(); ++b) {
-      foff[b] = t2;
-      t2 += block_size(&fin, block_mask(cr, fin.parity, b));
-    }
-    for (int64_t b = 0; b < (int64_t)toff.size(); ++b) {
-      uint32_t m = block_mask(cr, tmp.parity, b);
-      uint32_t mo = 0;
-      for (int u = 0; u < cr; ++u) mo |= ((m >> out_perm[u]) & 1u) << u;
-      int64_t dims[MAXR], dstr[MAXR], od[MAXR];
-      for (int k = 0; k < cr; ++k) dims[k] = leg_dim(&tmp, k, m);
-      for (int u = 0; u < cr; ++u) od[u] = dims[out_perm[u]];
-      int64_t s = 1;
-      for (int u = cr - 1; u >= 0; --u) {
-        dstr[out_perm[u]] = s;
-        s *= od[u];
-      }
-      int sg = inversion_parity(cr, out_perm, m);
-      add_perm_job(P->jc, P->tc, cr, dims, dstr, toff[b], foff[mo >> 1], sg ? -1 : 1);
-    }
-  }
   if (!jobs_in_bounds(P->ja, A->numel, P->af_elems) || !jobs_in_bounds(P->jb, B->numel, P->bf_elems) ||
-      !probs_in_bounds(P->probs, P->af_elems, P->bf_elems, P->tmp_numel) ||
-      (P->out_perm && !jobs_in_bounds(P->jc, P->tmp_numel, P->tmp_numel)))
+      !probs_in_bounds(P->probs, P->af_elems, P->bf_elems, P->tmp_numel))
     return set_error(FTN_EINVAL, "internal error: contraction plan out of bounds");
   FTN_TRY(upload_plan(ctx, *P));
   out = P;
@@ -407,7 +409,7 @@ ftn_status tensordot_impl(ftn_ctx ctx, ftn_tensor A, ftn_tensor B, int n, const 
   const size_t es = tc ? (bf16 ? 2 : 4) : 8;
   auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
   const size_t a_b = al((size_t)P->af_elems * es), b_b = al((size_t)P->bf_elems * es);
-  const size_t c_b = P->out_perm ? al((size_t)P->tmp_numel * dtype_size(A->dtype)) : 0;
+  const size_t c_b = 0;
   const size_t need = a_b * (split ? 2 : 1) + b_b * (split ? 2 : 1) + c_b;
   uint8_t* ws = (uint8_t*)workspace(ctx, need);
   if (!ws) {
@@ -418,7 +420,7 @@ ftn_status tensordot_impl(ftn_ctx ctx, ftn_tensor A, ftn_tensor B, int n, const 
   uint8_t* af_lo = split ? af_hi + a_b : nullptr;
   uint8_t* bf_hi = ws + a_b * (split ? 2 : 1);
   uint8_t* bf_lo = split ? bf_hi + b_b : nullptr;
-  uint8_t* ctmp = P->out_perm ? bf_hi + b_b * (split ? 2 : 1) : (uint8_t*)out->data;
+  uint8_t* ctmp = (uint8_t*)out->data;  // the GEMM epilogue writes the final (permuted) layout
   int mode = PERM_SAME;
   if (prec == FTN_PREC_TF32) mode = PERM_TF32;
   if (prec == FTN_PREC_TF32X3) mode = PERM_TF32X2;
@@ -460,11 +462,6 @@ ftn_status tensordot_impl(ftn_ctx ctx, ftn_tensor A, ftn_tensor B, int n, const 
       st = launch_gemm_tc(ctx, prec, ops, P->d_probs, (int)P->probs.size(), P->gemm_tiles, P->bn, (float*)ctmp);
       prof_end(ctx, rec);
     }
-  }
-  if (st == FTN_OK && P->out_perm) {
-    rec = prof_begin(ctx, "permute", 2.0 * P->tmp_numel * in_es, 0);
-    st = launch_permute(ctx, P->d_jc, (int)P->jc.size(), P->tc, ctmp, out->data, nullptr, A->dtype, PERM_SAME);
-    prof_end(ctx, rec);
   }
   if (st != FTN_OK) {
     if (created) ftn_tensor_free(out);
