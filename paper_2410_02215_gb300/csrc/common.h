@@ -24,9 +24,16 @@ constexpr int DEV_ERR_TIMEOUT = 1;
 //   I: a suffix of the source legs (contiguous in the source, product PI),
 //   O: legs with the smallest destination strides not in I (product PO),
 //   B: the rest (product PB).
-// One CTA tile covers TI x TO elements of one batch index.
-constexpr int PERM_TI = 32;
-constexpr int PERM_TO = 64;
+// A tile covers tr values of the O index times ti values of the I index for
+// one batch index.  Two kernels share the job format: a TMA-staged one
+// (bulk copies of contiguous source rows into a shared-memory ring; needs
+// 16-byte aligned rows) and a register-staged fallback with fixed 32 x 64
+// tiles.  finalize_perm_jobs() picks the kernel and the tiling.
+constexpr int PERM_TI = 32;   // fallback tile: I extent
+constexpr int PERM_TO = 64;   // fallback tile: O extent
+constexpr int PERM_TILE_BYTES = 16384;  // staged tile payload
+constexpr int PERM_MAX_ROWS = 128;
+constexpr int PERM_STAGES = 3;
 
 struct PermJob {
   int64_t src_off;   // elements from the source base
@@ -38,9 +45,11 @@ struct PermJob {
   int32_t nI, nO, nB;
   int32_t sign;      // +1 or -1
   int32_t store_fast_i;  // destination contiguous along the I index
+  int32_t ti, tr;        // tile extents (I, O)
+  int32_t bulk_ok;       // rows are 16-byte aligned with 16-byte multiple sizes
   int32_t pad_;
   int32_t dim[MAXR];     // I legs (source order), then O legs, then B legs
-  int64_t sstr[MAXR];    // source strides (unused for I legs)
+  int64_t sstr[MAXR];    // source strides
   int64_t dstr[MAXR];    // destination strides
 };
 
@@ -71,7 +80,7 @@ struct GemmProb {
   int32_t tiles_m, tiles_n;
   int32_t c_sign;
   int32_t nrl, ncl;
-  int32_t pad_;
+  int32_t epi_rows;  // epilogue writes lane -> row (the destination is contiguous along rows)
   int32_t rdim[MAXR], cdim[MAXR];
   int64_t rstr[MAXR], cstr[MAXR];
 };
@@ -181,7 +190,10 @@ void add_perm_job(std::vector<PermJob>& jobs, int64_t& tiles, int rank, const in
                   const int64_t* dst_strides, int64_t src_off, int64_t dst_off, int sign);
 
 // kernel launchers (asynchronous on ctx->stream)
-ftn_status launch_permute(ftn_ctx ctx, const PermJob* d_jobs, int njobs, int64_t tiles, const void* src,
+// Chooses the kernel (returns 1 for the TMA-staged one) and fills the tiling
+// and tile prefix sums of every job; *tiles receives the total.
+int finalize_perm_jobs(std::vector<PermJob>& jobs, size_t elem_size, int64_t* tiles, bool allow_staged);
+ftn_status launch_permute(ftn_ctx ctx, const PermJob* d_jobs, int njobs, int64_t tiles, int staged, const void* src,
                           void* dst0, void* dst1, ftn_dtype in_type, int mode);
 ftn_status launch_gemm_f64(ftn_ctx ctx, const GemmProb* d_probs, int nprobs, int64_t tiles, const double* a,
                            const double* b, double* c);

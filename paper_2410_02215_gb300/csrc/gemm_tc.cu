@@ -265,10 +265,19 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
         const int col = c + lane;
         const bool okc = lane < Cfg::CW && col < ncols;
         const int64_t cpart = okc ? expand_index(n0 + col, p.ncl, p.cdim, p.cstr) : 0;
+        if (p.epi_rows) {
+          // destination contiguous along rows: lane -> row, loop over columns
 #pragma unroll 4
-        for (int rr = 0; rr < 32; ++rr) {
-          const int64_t rp = __shfl_sync(0xffffffffu, rpart, rr);
-          if (rr < nrows && okc) P.C[rp + cpart] = sg * stg[rr * (Cfg::CW + 1) + lane];
+          for (int cc = 0; cc < Cfg::CW; ++cc) {
+            const int64_t cp = __shfl_sync(0xffffffffu, cpart, cc);
+            if (lane < nrows && c + cc < ncols) P.C[rpart + cp] = sg * stg[lane * (Cfg::CW + 1) + cc];
+          }
+        } else {
+#pragma unroll 4
+          for (int rr = 0; rr < 32; ++rr) {
+            const int64_t rp = __shfl_sync(0xffffffffu, rpart, rr);
+            if (rr < nrows && okc) P.C[rp + cpart] = sg * stg[rr * (Cfg::CW + 1) + lane];
+          }
         }
         __syncwarp();
       }

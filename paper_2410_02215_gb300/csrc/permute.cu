@@ -4,6 +4,13 @@
 // (transposition), of the bond parity g and of the fusion order depends only
 // on the block's parity bits).
 //
+// Two kernels share the job format.  The staged kernel (used when every
+// source row of a job starts 16-byte aligned): warp 0 of each persistent CTA
+// issues cp.async.bulk copies of the contiguous source rows of upcoming tiles
+// into a PERM_STAGES-deep shared-memory ring (completion on an mbarrier), and
+// all eight warps write the current tile out along the destination's
+// contiguous direction; the TMA engine keeps the HBM reads in flight without
+// holding registers.  The fallback kernel stages through registers:
 // Each CTA tile covers PERM_TO rows of the O group (destination-fast legs)
 // times PERM_TI elements of the I group (the source's contiguous suffix) for
 // one batch index.  Loads run along I (coalesced in the source); stores run
@@ -13,6 +20,7 @@
 #include <cuda_bf16.h>
 
 #include "common.h"
+#include "ptx.cuh"
 
 namespace ftn {
 
@@ -159,6 +167,213 @@ __global__ void __launch_bounds__(PT) perm_kernel(const PermJob* __restrict__ jo
   }
 }
 
+
+// ---------------------------------------------------------------------------------
+// TMA-staged sign-permute
+struct StageMeta {
+  int64_t baseD;
+  int32_t nrows, ncols;
+  int32_t ti, fast_i;
+  int32_t sign, failed;
+};
+
+template <typename Tin>
+struct StagedCfg {
+  static constexpr int V = 16 / (int)sizeof(Tin);
+  static constexpr int TE = PERM_TILE_BYTES / (int)sizeof(Tin);
+  static constexpr int MAXTI = TE / 8;
+  static constexpr int STAGE_ELEMS = TE + PERM_MAX_ROWS * V;
+  static constexpr int BYTES = PERM_STAGES * STAGE_ELEMS * (int)sizeof(Tin) + PERM_STAGES * PERM_MAX_ROWS * 4 +
+                               PERM_STAGES * MAXTI * 4 + PERM_STAGES * (int)sizeof(StageMeta) + PERM_STAGES * 8 + 128;
+};
+
+template <typename Tin>
+__device__ __forceinline__ void staged_issue(const PermJob* __restrict__ jobs, int njobs, int64_t t,
+                                             const Tin* __restrict__ src, Tin* buf, int32_t* rowD, int32_t* colD,
+                                             StageMeta* meta, uint64_t* bar, int lane) {
+  using Cfg = StagedCfg<Tin>;
+  int jb = 0;
+  if (lane == 0) {
+    int lo = 0, hi = njobs - 1;
+    while (lo < hi) {
+      int mid = (lo + hi + 1) >> 1;
+      if (jobs[mid].tile_begin <= t)
+        lo = mid;
+      else
+        hi = mid - 1;
+    }
+    jb = lo;
+  }
+  jb = __shfl_sync(0xffffffffu, jb, 0);
+  const PermJob* j = jobs + jb;
+  const int nI = j->nI, nO = j->nO;
+  const int64_t local = t - j->tile_begin;
+  const int64_t per_b = (int64_t)j->tiles_i * j->tiles_o;
+  const int64_t b = local / per_b;
+  const int rem = (int)(local - b * per_b);
+  const int i0 = (rem % j->tiles_i) * j->ti, o0 = (rem / j->tiles_i) * j->tr;
+  const int ncols = min(j->ti, j->PI - i0), nrows = min(j->tr, j->PO - o0);
+  int64_t bS = j->src_off, bD = j->dst_off;
+  {
+    int64_t x = b;
+    for (int q = nI + nO + j->nB - 1; q >= nI + nO; --q) {
+      const int64_t idx = x % j->dim[q];
+      x /= j->dim[q];
+      bS += idx * j->sstr[q];
+      bD += idx * j->dstr[q];
+    }
+  }
+  const int stride = j->ti + Cfg::V;
+  uint32_t mine = 0;
+  for (int r = lane; r < nrows; r += 32) {
+    int x = o0 + r;
+    int64_t rs = 0;
+    int32_t rd = 0;
+    for (int q = nI + nO - 1; q >= nI; --q) {
+      const int idx = x % j->dim[q];
+      x /= j->dim[q];
+      rs += (int64_t)idx * j->sstr[q];
+      rd += idx * (int32_t)j->dstr[q];
+    }
+    rowD[r] = rd;
+    mine += (uint32_t)(ncols * sizeof(Tin));
+  }
+  for (int c = lane; c < ncols; c += 32) {
+    int x = i0 + c;
+    int32_t dd = 0;
+    for (int q = nI - 1; q >= 0; --q) {
+      const int idx = x % j->dim[q];
+      x /= j->dim[q];
+      dd += idx * (int32_t)j->dstr[q];
+    }
+    colD[c] = dd;
+  }
+  if (lane == 0) {
+    meta->baseD = bD;
+    meta->nrows = nrows;
+    meta->ncols = ncols;
+    meta->ti = j->ti;
+    meta->fast_i = j->store_fast_i;
+    meta->sign = j->sign;
+  }
+  // order this warp's earlier generic reads of the stage before the async writes
+  fence_proxy_async_smem();
+  mbar_expect_tx(bar, mine);
+  for (int r = lane; r < nrows; r += 32) {
+    int x = o0 + r;
+    int64_t rs = 0;
+    for (int q = nI + nO - 1; q >= nI; --q) {
+      const int idx = x % j->dim[q];
+      x /= j->dim[q];
+      rs += (int64_t)idx * j->sstr[q];
+    }
+    bulk_g2s(buf + r * stride, src + bS + rs + i0, (uint32_t)(ncols * sizeof(Tin)), bar);
+  }
+}
+
+template <typename Tin, int MODE>
+__global__ void __launch_bounds__(PT) perm_staged_kernel(const PermJob* __restrict__ jobs, int njobs, int64_t tiles,
+                                                         const Tin* __restrict__ src, void* __restrict__ dst0,
+                                                         void* __restrict__ dst1, int* err) {
+  using Cfg = StagedCfg<Tin>;
+  extern __shared__ uint8_t sm_raw[];
+  uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(sm_raw) + 127) & ~uintptr_t(127));
+  Tin* buf = reinterpret_cast<Tin*>(sm);
+  int32_t* rowD = reinterpret_cast<int32_t*>(buf + PERM_STAGES * Cfg::STAGE_ELEMS);
+  int32_t* colD = rowD + PERM_STAGES * PERM_MAX_ROWS;
+  StageMeta* meta = reinterpret_cast<StageMeta*>(colD + PERM_STAGES * Cfg::MAXTI);
+  uint64_t* full = reinterpret_cast<uint64_t*>(meta + PERM_STAGES);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (tid == 0) {
+    for (int s = 0; s < PERM_STAGES; ++s) mbar_init(&full[s], 32);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  const int64_t stride_t = gridDim.x;
+  int64_t issued = 0;
+  if (warp == 0) {
+    for (int s = 0; s < PERM_STAGES; ++s) {
+      const int64_t t = blockIdx.x + s * stride_t;
+      if (t >= tiles) break;
+      staged_issue<Tin>(jobs, njobs, t, src, buf + s * Cfg::STAGE_ELEMS, rowD + s * PERM_MAX_ROWS,
+                        colD + s * Cfg::MAXTI, meta + s, &full[s], lane);
+      ++issued;
+    }
+  }
+  int64_t k = 0;
+  for (;; ++k) {
+    const int64_t t = blockIdx.x + k * stride_t;
+    if (t >= tiles) break;
+    const int s = (int)(k % PERM_STAGES);
+    const uint32_t par = (uint32_t)((k / PERM_STAGES) & 1);
+    const bool ok = mbar_wait(&full[s], par, err);
+    if (__syncthreads_or(!ok)) break;
+    const StageMeta m = meta[s];
+    const Tin* tb = buf + s * Cfg::STAGE_ELEMS;
+    const int32_t* rd = rowD + s * PERM_MAX_ROWS;
+    const int32_t* cd = colD + s * Cfg::MAXTI;
+    const int stride = m.ti + Cfg::V;
+    const Tin sgn = (Tin)m.sign;
+    if (m.fast_i) {
+      for (int r = warp; r < m.nrows; r += PT / 32) {
+        const int64_t base = m.baseD + rd[r];
+        for (int c = lane; c < m.ncols; c += 32) put<Tin, MODE>(dst0, dst1, base + cd[c], sgn * tb[r * stride + c]);
+      }
+    } else {
+      for (int c0 = warp * Cfg::V; c0 < m.ncols; c0 += (PT / 32) * Cfg::V) {
+        for (int r = lane; r < m.nrows; r += 32) {
+          Tin v[Cfg::V];
+          if constexpr (sizeof(Tin) == 4) {
+            const float4 w = *reinterpret_cast<const float4*>(tb + r * stride + c0);
+            v[0] = w.x, v[1] = w.y, v[2] = w.z, v[3] = w.w;
+          } else {
+            const double2 w = *reinterpret_cast<const double2*>(tb + r * stride + c0);
+            v[0] = w.x, v[1] = w.y;
+          }
+          const int64_t base = m.baseD + rd[r];
+#pragma unroll
+          for (int q = 0; q < Cfg::V; ++q)
+            if (c0 + q < m.ncols) put<Tin, MODE>(dst0, dst1, base + cd[c0 + q], sgn * v[q]);
+        }
+      }
+    }
+    __syncthreads();
+    if (warp == 0) {
+      const int64_t tn = blockIdx.x + (k + PERM_STAGES) * stride_t;
+      if (tn < tiles) {
+        staged_issue<Tin>(jobs, njobs, tn, src, buf + s * Cfg::STAGE_ELEMS, rowD + s * PERM_MAX_ROWS,
+                          colD + s * Cfg::MAXTI, meta + s, &full[s], lane);
+        ++issued;
+      }
+    }
+  }
+  // after an early exit, wait for this CTA's copies still in flight
+  if (warp == 0 && lane == 0) {
+    for (int64_t q = k; q < issued; ++q)
+      mbar_wait(&full[q % PERM_STAGES], (uint32_t)((q / PERM_STAGES) & 1), err, false);
+  }
+}
+
+template <typename Tin, int MODE>
+static cudaError_t go_staged(ftn_ctx ctx, const PermJob* d_jobs, int njobs, int64_t tiles, const void* src,
+                             void* dst0, void* dst1) {
+  using Cfg = StagedCfg<Tin>;
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(perm_staged_kernel<Tin, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         Cfg::BYTES);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  int64_t grid = tiles;
+  int64_t cap = (int64_t)ctx->num_sms * 3;
+  if (grid > cap) grid = cap;
+  perm_staged_kernel<Tin, MODE><<<(unsigned)grid, PT, Cfg::BYTES, ctx->stream>>>(d_jobs, njobs, tiles,
+                                                                                 (const Tin*)src, dst0, dst1,
+                                                                                 ctx->dev_err);
+  return cudaGetLastError();
+}
+
 template <typename Tin, int MODE>
 static cudaError_t go(ftn_ctx ctx, const PermJob* d_jobs, int njobs, int64_t tiles, const void* src, void* dst0,
                       void* dst1) {
@@ -169,20 +384,27 @@ static cudaError_t go(ftn_ctx ctx, const PermJob* d_jobs, int njobs, int64_t til
   return cudaGetLastError();
 }
 
-ftn_status launch_permute(ftn_ctx ctx, const PermJob* d_jobs, int njobs, int64_t tiles, const void* src, void* dst0,
-                          void* dst1, ftn_dtype in_type, int mode) {
+template <typename Tin, int MODE>
+static cudaError_t pick(ftn_ctx ctx, int staged, const PermJob* d_jobs, int njobs, int64_t tiles, const void* src,
+                        void* dst0, void* dst1) {
+  return staged ? go_staged<Tin, MODE>(ctx, d_jobs, njobs, tiles, src, dst0, dst1)
+                : go<Tin, MODE>(ctx, d_jobs, njobs, tiles, src, dst0, dst1);
+}
+
+ftn_status launch_permute(ftn_ctx ctx, const PermJob* d_jobs, int njobs, int64_t tiles, int staged, const void* src,
+                          void* dst0, void* dst1, ftn_dtype in_type, int mode) {
   if (njobs == 0 || tiles == 0) return FTN_OK;
   cudaError_t e;
   if (in_type == FTN_F64) {
     if (mode != PERM_SAME) return set_error(FTN_EUNSUPPORTED, "FP64 permute supports only the same-type output");
-    e = go<double, PERM_SAME>(ctx, d_jobs, njobs, tiles, src, dst0, dst1);
+    e = pick<double, PERM_SAME>(ctx, staged, d_jobs, njobs, tiles, src, dst0, dst1);
   } else {
     switch (mode) {
-      case PERM_SAME: e = go<float, PERM_SAME>(ctx, d_jobs, njobs, tiles, src, dst0, dst1); break;
-      case PERM_TF32: e = go<float, PERM_TF32>(ctx, d_jobs, njobs, tiles, src, dst0, dst1); break;
-      case PERM_TF32X2: e = go<float, PERM_TF32X2>(ctx, d_jobs, njobs, tiles, src, dst0, dst1); break;
-      case PERM_BF16: e = go<float, PERM_BF16>(ctx, d_jobs, njobs, tiles, src, dst0, dst1); break;
-      case PERM_BF16X2: e = go<float, PERM_BF16X2>(ctx, d_jobs, njobs, tiles, src, dst0, dst1); break;
+      case PERM_SAME: e = pick<float, PERM_SAME>(ctx, staged, d_jobs, njobs, tiles, src, dst0, dst1); break;
+      case PERM_TF32: e = pick<float, PERM_TF32>(ctx, staged, d_jobs, njobs, tiles, src, dst0, dst1); break;
+      case PERM_TF32X2: e = pick<float, PERM_TF32X2>(ctx, staged, d_jobs, njobs, tiles, src, dst0, dst1); break;
+      case PERM_BF16: e = pick<float, PERM_BF16>(ctx, staged, d_jobs, njobs, tiles, src, dst0, dst1); break;
+      case PERM_BF16X2: e = pick<float, PERM_BF16X2>(ctx, staged, d_jobs, njobs, tiles, src, dst0, dst1); break;
       default: return set_error(FTN_EINVAL, "bad permute mode");
     }
   }

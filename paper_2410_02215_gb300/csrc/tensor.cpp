@@ -159,7 +159,7 @@ void add_perm_job(std::vector<PermJob>& jobs, int64_t& tiles, int rank, const in
   std::vector<int> O, B;
   int64_t PO = 1;
   for (int k : rest) {
-    if (PO < PERM_TO)
+    if (PO < PERM_MAX_ROWS)
       O.push_back(k), PO *= dims[k];
     else
       B.push_back(k);
@@ -197,15 +197,45 @@ void add_perm_job(std::vector<PermJob>& jobs, int64_t& tiles, int rank, const in
   j.PI = (int32_t)PI;
   j.PO = (int32_t)PO;
   j.PB = PB;
-  j.tiles_i = (int32_t)((PI + PERM_TI - 1) / PERM_TI);
-  j.tiles_o = (int32_t)((PO + PERM_TO - 1) / PERM_TO);
+
   // the destination is contiguous along I when I's fastest leg has stride 1
   // and no O leg is faster
   int64_t min_o = O.empty() ? INT64_MAX : dstr[O.back()];
   j.store_fast_i = dstr[r - 1] <= min_o ? 1 : 0;
-  j.tile_begin = tiles;
-  tiles += (int64_t)j.tiles_i * j.tiles_o * PB;
   jobs.push_back(j);
+  (void)tiles;
+}
+
+int finalize_perm_jobs(std::vector<PermJob>& jobs, size_t es, int64_t* tiles, bool allow_staged) {
+  const int64_t V = 16 / (int64_t)es;  // elements per 16 bytes
+  bool staged = allow_staged && !jobs.empty();
+  for (PermJob& j : jobs) {
+    bool ok = (j.PI % V == 0) && (j.src_off % V == 0);
+    for (int q = j.nI; q < j.nI + j.nO + j.nB; ++q) ok = ok && (j.sstr[q] % V == 0);
+    j.bulk_ok = ok ? 1 : 0;
+    staged = staged && ok;
+  }
+  const int64_t te = PERM_TILE_BYTES / (int64_t)es;
+  int64_t t = 0;
+  for (PermJob& j : jobs) {
+    if (staged) {
+      int64_t ti = std::min<int64_t>(j.PI, te / 8);
+      ti = (ti + V - 1) / V * V;
+      int64_t tr = std::min<int64_t>(std::max<int64_t>(te / ti, 1), PERM_MAX_ROWS);
+      tr = std::min<int64_t>(tr, j.PO);
+      j.ti = (int32_t)ti;
+      j.tr = (int32_t)tr;
+    } else {
+      j.ti = PERM_TI;
+      j.tr = PERM_TO;
+    }
+    j.tiles_i = (int32_t)((j.PI + j.ti - 1) / j.ti);
+    j.tiles_o = (int32_t)((j.PO + j.tr - 1) / j.tr);
+    j.tile_begin = t;
+    t += (int64_t)j.tiles_i * j.tiles_o * j.PB;
+  }
+  *tiles = t;
+  return staged ? 1 : 0;
 }
 
 static cudaEvent_t take_event(ftn_ctx ctx) {

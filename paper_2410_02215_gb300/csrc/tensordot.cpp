@@ -95,6 +95,8 @@ struct TdPlan {
   int64_t af_elems = 0, bf_elems = 0;
   std::vector<PermJob> ja, jb, jc;
   int64_t ta = 0, tb = 0, tc = 0;
+  int sa = 0, sb = 0, sc = 0;  // staged (TMA) permute kernel usable
+  bool fused = true;           // the GEMM epilogue writes the final layout
   std::vector<GemmProb> probs;
   int64_t gemm_tiles = 0;
   int bn = 0;
@@ -232,6 +234,9 @@ static ftn_status build_plan(ftn_ctx ctx, const ftn_tensor_s* A, const ftn_tenso
     int64_t dst = P->bfoff[pi] + coloff[pi][mB] * P->ldk[pi] + koff[pi][mK];
     add_perm_job(P->jb, P->tb, B->rank, dims, dstr, B->offsets[b], dst, sg ? -1 : 1);
   }
+  // the staged permute needs 16-byte aligned source rows (buffer base included)
+  P->sa = finalize_perm_jobs(P->ja, dtype_size(A->dtype), &P->ta, ((uintptr_t)A->data & 15) == 0);
+  P->sb = finalize_perm_jobs(P->jb, dtype_size(B->dtype), &P->tb, ((uintptr_t)B->data & 15) == 0);
   // ---- result metadata (before out_perm) ----
   const int cr = P->nfa + P->nfb;
   ftn_tensor_s tmp;
@@ -276,6 +281,29 @@ static ftn_status build_plan(ftn_ctx ctx, const ftn_tensor_s* A, const ftn_tenso
     fin_numel += block_size(&fin, block_mask(cr, fin.parity, b));
   }
   P->tmp_numel = fin_numel;
+  // ---- how the result reaches its final layout ----
+  // The epilogue writes 32 consecutive columns (or rows) per warp store; it
+  // applies the permutation itself when the destination's fastest legs form
+  // a long enough run along one of those directions, otherwise the GEMM
+  // writes the plain block layout and a sign-permute pass follows.
+  bool fuse = true;
+  int epi_rows = 0;
+  if (P->out_perm) {
+    int64_t run_c = 1, run_r = 1;
+    for (int u = cr - 1, k = cr - 1; u >= 0 && k >= P->nfa && perm[u] == k; --u, --k)
+      run_c *= std::max(1, std::min(tmp.d0[k] ? tmp.d0[k] : tmp.d1[k], tmp.d1[k] ? tmp.d1[k] : tmp.d0[k]));
+    for (int u = cr - 1, k = P->nfa - 1; u >= 0 && k >= 0 && perm[u] == k; --u, --k)
+      run_r *= std::max(1, std::min(tmp.d0[k] ? tmp.d0[k] : tmp.d1[k], tmp.d1[k] ? tmp.d1[k] : tmp.d0[k]));
+    if (run_c >= 16 && run_c >= run_r) {
+      epi_rows = 0;
+    } else if (run_r >= 16) {
+      epi_rows = 1;
+    } else {
+      fuse = false;
+    }
+  }
+  P->fused = fuse;
+  if (!fuse) P->tmp_numel = tot;
   // ---- GEMM problems, one per result block ----
   const bool tc = prec != FTN_PREC_F64;
   int maxN = 1;
@@ -302,22 +330,34 @@ static ftn_status build_plan(ftn_ctx ctx, const ftn_tensor_s* A, const ftn_tenso
     g.b_row0 = (int32_t)coloff[pi][mB];
     g.a_off = P->afoff[pi] + rowoff[pi][mA] * P->ldk[pi];
     g.b_off = P->bfoff[pi] + coloff[pi][mB] * P->ldk[pi];
-    // destination block in the (permuted) result and the stride of each leg
-    uint32_t mo = 0;
-    for (int u = 0; u < cr; ++u) mo |= ((m >> perm[u]) & 1u) << u;
-    int64_t dims[MAXR], str[MAXR];
-    for (int k = 0; k < cr; ++k) dims[k] = leg_dim(&tmp, k, m);
-    int64_t st = 1;
-    for (int u = cr - 1; u >= 0; --u) {
-      str[perm[u]] = st;
-      st *= dims[perm[u]];
+    if (fuse) {
+      // destination block in the (permuted) result and the stride of each leg
+      uint32_t mo = 0;
+      for (int u = 0; u < cr; ++u) mo |= ((m >> perm[u]) & 1u) << u;
+      int64_t dims[MAXR], str[MAXR];
+      for (int k = 0; k < cr; ++k) dims[k] = leg_dim(&tmp, k, m);
+      int64_t st = 1;
+      for (int u = cr - 1; u >= 0; --u) {
+        str[perm[u]] = st;
+        st *= dims[perm[u]];
+      }
+      g.c_off = cr == 0 ? 0 : foff[mo >> 1];
+      g.c_sign = inversion_parity(cr, perm, m) ? -1 : 1;
+      g.nrl = P->nfa;
+      g.ncl = P->nfb;
+      for (int k = 0; k < P->nfa; ++k) g.rdim[k] = (int32_t)dims[k], g.rstr[k] = str[k];
+      for (int k = 0; k < P->nfb; ++k) g.cdim[k] = (int32_t)dims[P->nfa + k], g.cstr[k] = str[P->nfa + k];
+      g.epi_rows = epi_rows;
+    } else {
+      // plain row-major block of the unpermuted result
+      g.c_off = toff[b];
+      g.c_sign = 1;
+      g.nrl = g.ncl = 1;
+      g.rdim[0] = g.M;
+      g.rstr[0] = g.N;
+      g.cdim[0] = g.N;
+      g.cstr[0] = 1;
     }
-    g.c_off = cr == 0 ? 0 : foff[mo >> 1];
-    g.c_sign = inversion_parity(cr, perm, m) ? -1 : 1;
-    g.nrl = P->nfa;
-    g.ncl = P->nfb;
-    for (int k = 0; k < P->nfa; ++k) g.rdim[k] = (int32_t)dims[k], g.rstr[k] = str[k];
-    for (int k = 0; k < P->nfb; ++k) g.cdim[k] = (int32_t)dims[P->nfa + k], g.cstr[k] = str[P->nfa + k];
     if (tc) {
       g.tiles_m = (g.M + 127) / 128;
       g.tiles_n = (g.N + P->bn - 1) / P->bn;
@@ -329,8 +369,27 @@ static ftn_status build_plan(ftn_ctx ctx, const ftn_tensor_s* A, const ftn_tenso
     P->gemm_tiles += (int64_t)g.tiles_m * g.tiles_n;
     P->probs.push_back(g);
   }
+  // ---- the separate sign-permute of the result, when not fused ----
+  if (!fuse) {
+    for (int64_t b = 0; b < (int64_t)toff.size(); ++b) {
+      uint32_t m = block_mask(cr, tmp.parity, b);
+      uint32_t mo = 0;
+      for (int u = 0; u < cr; ++u) mo |= ((m >> perm[u]) & 1u) << u;
+      int64_t dims[MAXR], dstr[MAXR];
+      for (int k = 0; k < cr; ++k) dims[k] = leg_dim(&tmp, k, m);
+      int64_t st = 1;
+      for (int u = cr - 1; u >= 0; --u) {
+        dstr[perm[u]] = st;
+        st *= dims[perm[u]];
+      }
+      int sg = inversion_parity(cr, perm, m);
+      add_perm_job(P->jc, P->tc, cr, dims, dstr, toff[b], foff[mo >> 1], sg ? -1 : 1);
+    }
+    P->sc = finalize_perm_jobs(P->jc, dtype_size(A->dtype), &P->tc, true);
+  }
   if (!jobs_in_bounds(P->ja, A->numel, P->af_elems) || !jobs_in_bounds(P->jb, B->numel, P->bf_elems) ||
-      !probs_in_bounds(P->probs, P->af_elems, P->bf_elems, P->tmp_numel))
+      !probs_in_bounds(P->probs, P->af_elems, P->bf_elems, P->tmp_numel) ||
+      (!P->fused && !jobs_in_bounds(P->jc, P->tmp_numel, P->tmp_numel)))
     return set_error(FTN_EINVAL, "internal error: contraction plan out of bounds");
   FTN_TRY(upload_plan(ctx, *P));
   out = P;
@@ -360,7 +419,8 @@ static ftn_status get_plan(ftn_ctx ctx, const ftn_tensor_s* A, const ftn_tensor_
   std::ostringstream key;
   key << "td|" << meta_key(A) << '|' << meta_key(B) << '|' << n << ':';
   for (int i = 0; i < n; ++i) key << ax[i] << ',' << ay[i] << ';';
-  key << '|' << fa << '|' << fb << '|' << (int)prec << '|';
+  key << '|' << fa << '|' << fb << '|' << (int)prec << '|' << (((uintptr_t)A->data & 15) == 0)
+      << (((uintptr_t)B->data & 15) == 0) << '|';
   if (out_perm)
     for (int u = 0; u < A->rank + B->rank - 2 * n; ++u) key << out_perm[u] << ',';
   auto& cache = plan_cache(ctx);
@@ -409,7 +469,7 @@ ftn_status tensordot_impl(ftn_ctx ctx, ftn_tensor A, ftn_tensor B, int n, const 
   const size_t es = tc ? (bf16 ? 2 : 4) : 8;
   auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
   const size_t a_b = al((size_t)P->af_elems * es), b_b = al((size_t)P->bf_elems * es);
-  const size_t c_b = 0;
+  const size_t c_b = P->fused ? 0 : al((size_t)P->tmp_numel * dtype_size(A->dtype));
   const size_t need = a_b * (split ? 2 : 1) + b_b * (split ? 2 : 1) + c_b;
   uint8_t* ws = (uint8_t*)workspace(ctx, need);
   if (!ws) {
@@ -420,7 +480,8 @@ ftn_status tensordot_impl(ftn_ctx ctx, ftn_tensor A, ftn_tensor B, int n, const 
   uint8_t* af_lo = split ? af_hi + a_b : nullptr;
   uint8_t* bf_hi = ws + a_b * (split ? 2 : 1);
   uint8_t* bf_lo = split ? bf_hi + b_b : nullptr;
-  uint8_t* ctmp = (uint8_t*)out->data;  // the GEMM epilogue writes the final (permuted) layout
+  // the GEMM epilogue writes the final layout, or the plain one into workspace
+  uint8_t* ctmp = P->fused ? (uint8_t*)out->data : bf_hi + b_b * (split ? 2 : 1);
   int mode = PERM_SAME;
   if (prec == FTN_PREC_TF32) mode = PERM_TF32;
   if (prec == FTN_PREC_TF32X3) mode = PERM_TF32X2;
@@ -430,11 +491,12 @@ ftn_status tensordot_impl(ftn_ctx ctx, ftn_tensor A, ftn_tensor B, int n, const 
   double gemm_flops = 0;
   for (const GemmProb& g : P->probs) gemm_flops += 2.0 * g.M * g.N * g.K;
   int rec = prof_begin(ctx, "permute", A->numel * (in_es + es * planes), 0);
-  ftn_status st = launch_permute(ctx, P->d_ja, (int)P->ja.size(), P->ta, A->data, af_hi, af_lo, A->dtype, mode);
+  ftn_status st =
+      launch_permute(ctx, P->d_ja, (int)P->ja.size(), P->ta, P->sa, A->data, af_hi, af_lo, A->dtype, mode);
   prof_end(ctx, rec);
   if (st == FTN_OK) {
     rec = prof_begin(ctx, "permute", B->numel * (in_es + es * planes), 0);
-    st = launch_permute(ctx, P->d_jb, (int)P->jb.size(), P->tb, B->data, bf_hi, bf_lo, B->dtype, mode);
+    st = launch_permute(ctx, P->d_jb, (int)P->jb.size(), P->tb, P->sb, B->data, bf_hi, bf_lo, B->dtype, mode);
     prof_end(ctx, rec);
   }
   if (st == FTN_OK) {
@@ -463,6 +525,11 @@ ftn_status tensordot_impl(ftn_ctx ctx, ftn_tensor A, ftn_tensor B, int n, const 
       prof_end(ctx, rec);
     }
   }
+  if (st == FTN_OK && !P->fused) {
+    rec = prof_begin(ctx, "permute", 2.0 * P->tmp_numel * in_es, 0);
+    st = launch_permute(ctx, P->d_jc, (int)P->jc.size(), P->tc, P->sc, ctmp, out->data, nullptr, A->dtype, PERM_SAME);
+    prof_end(ctx, rec);
+  }
   if (st != FTN_OK) {
     if (created) ftn_tensor_free(out);
     return st;
@@ -475,6 +542,7 @@ ftn_status tensordot_impl(ftn_ctx ctx, ftn_tensor A, ftn_tensor B, int n, const 
 struct TrPlan {
   std::vector<PermJob> jobs;
   int64_t tiles = 0;
+  int staged = 0;
   std::shared_ptr<DevTables> dev;
   PermJob* d_jobs = nullptr;
 };
@@ -510,7 +578,7 @@ ftn_status permute_impl(ftn_ctx ctx, ftn_tensor t, const int* perm, bool fermion
     created = true;
   }
   std::ostringstream key;
-  key << "tr|" << meta_key(t) << '|' << fermionic << '|';
+  key << "tr|" << meta_key(t) << '|' << fermionic << '|' << (((uintptr_t)t->data & 15) == 0) << '|';
   for (int u = 0; u < r; ++u) key << perm[u] << ',';
   auto& cache = tr_cache(ctx);
   std::shared_ptr<TrPlan> P;
@@ -538,6 +606,7 @@ ftn_status permute_impl(ftn_ctx ctx, ftn_tensor t, const int* perm, bool fermion
       }
       add_perm_job(P->jobs, P->tiles, r == 0 ? 1 : r, dims, dstr, t->offsets[b], dst, sg ? -1 : 1);
     }
+    P->staged = finalize_perm_jobs(P->jobs, dtype_size(t->dtype), &P->tiles, ((uintptr_t)t->data & 15) == 0);
     if (!jobs_in_bounds(P->jobs, t->numel, o->numel)) {
       if (created) ftn_tensor_free(o);
       return set_error(FTN_EINVAL, "internal error: transposition plan out of bounds");
@@ -557,8 +626,8 @@ ftn_status permute_impl(ftn_ctx ctx, ftn_tensor t, const int* perm, bool fermion
     cache[key.str()] = P;
   }
   int rec = prof_begin(ctx, "permute", 2.0 * t->numel * dtype_size(t->dtype), 0);
-  ftn_status st = launch_permute(ctx, P->d_jobs, (int)P->jobs.size(), P->tiles, t->data, o->data, nullptr, t->dtype,
-                                 PERM_SAME);
+  ftn_status st = launch_permute(ctx, P->d_jobs, (int)P->jobs.size(), P->tiles, P->staged, t->data, o->data,
+                                 nullptr, t->dtype, PERM_SAME);
   prof_end(ctx, rec);
   if (st != FTN_OK) {
     if (created) ftn_tensor_free(o);

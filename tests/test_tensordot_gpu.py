@@ -187,3 +187,29 @@ def test_errors_are_reported(F, ctx):
     with pytest.raises(F.FtnError) as e:
         F.tensordot(ctx, a, b, [0], [1], prec="tf32")  # FP64 data on a TF32 path
     assert e.value.status == -8
+
+
+def test_misaligned_wrapped_input_uses_fallback_permute(F, ctx):
+    """A borrowed buffer that is not 16-byte aligned cannot feed the TMA-staged
+    permute; the register-staged kernel must take over with the same result."""
+    import torch
+
+    case = W.tensordot_case("T2", seed=2, shrink=2)
+    for prec, tdt in (("f64", torch.float64), ("tf32x3", torch.float32)):
+        ba = W.random_blocks(case["legs_a"], 0, case["seed_a"])
+        bb = W.random_blocks(case["legs_b"], 0, case["seed_b"])
+        ref = O.transpose(O.contract(dense(ba, case["legs_a"], 0), dense(bb, case["legs_b"], 0), case["axes_a"],
+                                     case["axes_b"]), case["out_perm"])
+        a0 = upload(F, ctx, case["legs_a"], 0, ba, prec)
+        store = torch.empty(a0.numel + 1, dtype=tdt, device="cuda")
+        store[1:].copy_(a0.view())
+        a = F.Tensor.wrap(ctx, case["legs_a"], 0, store[1:])
+        assert a.ptr % 16 != 0
+        b = upload(F, ctx, case["legs_b"], 0, bb, prec)
+        c = F.tensordot(ctx, a, b, case["axes_a"], case["axes_b"], out_perm=case["out_perm"], prec=prec)
+        got = dense(c.to_blocks(), c.legs, c.parity)
+        assert relerr(got.data, ref.data) <= TOL[prec]
+        t = F.transpose(ctx, a, list(reversed(range(len(case["legs_a"])))))
+        want = O.transpose(dense(a0.to_blocks(), a0.legs, 0), list(reversed(range(len(case["legs_a"])))))
+        assert np.array_equal(dense(t.to_blocks(), t.legs, t.parity).data, want.data)
+    ctx.synchronize()
