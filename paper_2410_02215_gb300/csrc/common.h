@@ -83,6 +83,11 @@ struct GemmProb {
   int32_t epi_rows;  // epilogue writes lane -> row (the destination is contiguous along rows)
   int32_t rdim[MAXR], cdim[MAXR];
   int64_t rstr[MAXR], cstr[MAXR];
+  // FP64 path: element strides of the operands (A[m, k] = A[a_off + m*a_sm + k*a_sk])
+  int64_t a_sm, a_sk, b_sn, b_sk;
+  // FP64 path split-K: nsplit slices of kchunk, slice s written at c_off + s*c_slab
+  int32_t nsplit, kchunk;
+  int64_t c_slab;
 };
 
 // Offset of the row-major multi-index of x over n legs (last leg fastest).
@@ -197,6 +202,10 @@ ftn_status launch_permute(ftn_ctx ctx, const PermJob* d_jobs, int njobs, int64_t
                           void* dst0, void* dst1, ftn_dtype in_type, int mode);
 ftn_status launch_gemm_f64(ftn_ctx ctx, const GemmProb* d_probs, int nprobs, int64_t tiles, const double* a,
                            const double* b, double* c);
+// plain row-major output block (rows x cols, row stride ld) at c_off
+void gemm_plain_output(GemmProb& g, int64_t c_off, int64_t ld);
+// dst[e] = sum_s src[s * slab + e] for e < count (split-K reduction)
+ftn_status launch_sum_slabs(ftn_ctx ctx, double* dst, const double* src, int64_t count, int nsplit, int64_t slab);
 
 struct TcOperands {
   // fused pi-matrices: rows x ldk elements, K-major; lo only for split modes
@@ -217,5 +226,6 @@ ftn_status upload_table(ftn_ctx ctx, const void* host, size_t bytes, void** dev)
 int prof_begin(ftn_ctx ctx, const char* label, double bytes, double flops);
 void prof_end(ftn_ctx ctx, int rec);
 void clear_plan_caches(ftn_ctx ctx);
+bool probs_in_bounds(const std::vector<GemmProb>& probs, int64_t a_n, int64_t b_n, int64_t c_n);
 
 }  // namespace ftn

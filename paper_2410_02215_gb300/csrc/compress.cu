@@ -1,0 +1,565 @@
+// Bond compression ftn_compress (Sec. II.A: symmetric QR/SVD with the chi
+// largest singular values pooled over all symmetry blocks; Sec. II.B: the
+// decomposition runs after transposing into row | column order).
+//
+// GPU pipeline, FP64 throughout, per bond-parity sector pi:
+//   1. sign-permute X -> X_pi = [free_X | bond] and Y -> Y_pi^T = [free_Y | bond]
+//      (the fused layouts of the tensordot, bond parity of the arrow folded in);
+//   2. R factors with R^T R = X_pi^T X_pi (resp. Y_pi Y_pi^T): Gram matrix by the
+//      FP64 GEMM and a semi-definite Cholesky; a side with fewer rows than bond
+//      states uses the matrix itself (X_pi = I * X_pi);
+//   3. core M_pi = R_X R_Y^T and its SVD by one-sided (Hestenes) Jacobi;
+//   4. one host synchronisation: the singular values of both sectors are
+//      pooled and the chi largest kept;
+//   5. X' = X_pi (R_Y^T V_k S_k^{-1/2}) and Y'^T = Y_pi^T (R_X^T U_k S_k^{-1/2}),
+//      written straight into the block layouts of the new tensors.
+// Step 5 is the projector form of X' = Q_X U sqrt(S), Y' = sqrt(S) V^T Q_Y^T:
+// Q_X U_k S_k = X R_Y^T V_k, so no orthogonal factor is ever formed.  With
+// chi at or above the rank, op(X', Y') = op(X, Y) exactly for any invertible
+// R factors.
+#include <algorithm>
+#include <cmath>
+
+#include "ptx.cuh"
+#include "tdplan.h"
+
+namespace ftn {
+
+constexpr int LA_THREADS = 512;
+constexpr int LA_MAX_DIM = 1024;  // largest bond sector handled by the Jacobi SVD
+
+struct CholJob {
+  double* G;  // n x n row-major, symmetric; replaced by R (upper, R^T R = G)
+  int n;
+};
+
+struct SvdJob {
+  double* At;  // n x m row-major; rows are orthogonalised in place
+  double* Vt;  // n x n row-major; accumulated rotations (starts as identity)
+  double* s;   // n singular values (row norms at convergence)
+  int n, m;
+};
+
+struct GatherJob {
+  const double* left;   // source row (length nl)
+  const double* right;  // source row (length nr)
+  double* dl;
+  double* dr;
+  double sl, sr;  // scale factors
+  int nl, nr;
+};
+
+__device__ __forceinline__ double block_max(double v, double* red) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int o = 16; o; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  if (warp == 0) {
+    v = lane < (int)(blockDim.x >> 5) ? red[lane] : 0.0;
+    for (int o = 16; o; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if (lane == 0) red[32] = v;
+  }
+  __syncthreads();
+  return red[32];
+}
+
+// Semi-definite Cholesky G = L L^T (right-looking); a pivot at or below
+// 1e-12 * max(diag G) marks a numerically dependent direction (a singular
+// value of the underlying matrix below 1e-6 of its largest, where a Gram
+// matrix carries only rounding noise) whose row of R is set to zero.
+// Writes R = L^T (upper triangle, zeros below).
+__global__ void __launch_bounds__(LA_THREADS) chol_kernel(const CholJob* jobs) {
+  __shared__ double red[33];
+  __shared__ double piv;
+  const CholJob jb = jobs[blockIdx.x];
+  double* G = jb.G;
+  const int n = jb.n;
+  double dmax = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) dmax = fmax(dmax, G[(int64_t)i * n + i]);
+  dmax = block_max(dmax, red);
+  const double tol = 1e-12 * dmax;
+  for (int j = 0; j < n; ++j) {
+    if (threadIdx.x == 0) {
+      const double d = G[(int64_t)j * n + j];
+      piv = d > tol ? sqrt(d) : 0.0;
+      G[(int64_t)j * n + j] = piv;
+    }
+    __syncthreads();
+    const double p = piv;
+    for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x)
+      G[(int64_t)i * n + j] = p > 0.0 ? G[(int64_t)i * n + j] / p : 0.0;
+    __syncthreads();
+    const int rest = n - j - 1;
+    const int64_t cnt = (int64_t)rest * rest;
+    for (int64_t e = threadIdx.x; e < cnt; e += blockDim.x) {
+      const int i = j + 1 + (int)(e / rest), k = j + 1 + (int)(e % rest);
+      if (k <= i) G[(int64_t)i * n + k] -= G[(int64_t)i * n + j] * G[(int64_t)k * n + j];
+    }
+    __syncthreads();
+  }
+  // R = L^T in place
+  const int64_t tot = (int64_t)n * n;
+  for (int64_t e = threadIdx.x; e < tot; e += blockDim.x) {
+    const int i = (int)(e / n), k = (int)(e % n);
+    if (i < k) {
+      G[(int64_t)i * n + k] = G[(int64_t)k * n + i];
+      G[(int64_t)k * n + i] = 0.0;
+    }
+  }
+}
+
+// One-sided Jacobi: orthogonalise the n rows of At (length m) by plane
+// rotations in round-robin order (n/2 disjoint pairs per round, one warp per
+// pair), accumulating the rotations in Vt.  Converged when a sweep applies no
+// rotation, i.e. every pair satisfies |a_p . a_q| <= 1e-15 |a_p| |a_q|.
+__global__ void __launch_bounds__(LA_THREADS) svd_jacobi_kernel(const SvdJob* jobs) {
+  __shared__ int rotated;
+  const SvdJob jb = jobs[blockIdx.x];
+  const int n = jb.n, m = jb.m;
+  double* At = jb.At;
+  double* Vt = jb.Vt;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int64_t e = threadIdx.x; e < (int64_t)n * n; e += blockDim.x) Vt[e] = (e / n == e % n) ? 1.0 : 0.0;
+  __syncthreads();
+  const int np = n + (n & 1);
+  for (int sweep = 0; sweep < 40 && np > 1; ++sweep) {
+    if (threadIdx.x == 0) rotated = 0;
+    __syncthreads();
+    for (int r = 0; r < np - 1; ++r) {
+      for (int k = warp; k < np / 2; k += nw) {
+        const int a = k, b = np - 1 - k;
+        const int p = a == 0 ? 0 : 1 + (a - 1 + r) % (np - 1);
+        const int q = b == 0 ? 0 : 1 + (b - 1 + r) % (np - 1);
+        if (p >= n || q >= n) continue;
+        double* ap = At + (int64_t)p * m;
+        double* aq = At + (int64_t)q * m;
+        double al = 0.0, be = 0.0, ga = 0.0;
+        for (int i = lane; i < m; i += 32) {
+          const double x = ap[i], y = aq[i];
+          al = fma(x, x, al);
+          be = fma(y, y, be);
+          ga = fma(x, y, ga);
+        }
+        for (int o = 16; o; o >>= 1) {
+          al += __shfl_xor_sync(0xffffffffu, al, o);
+          be += __shfl_xor_sync(0xffffffffu, be, o);
+          ga += __shfl_xor_sync(0xffffffffu, ga, o);
+        }
+        if (fabs(ga) <= 1e-15 * sqrt(al * be) || ga == 0.0) continue;
+        const double zeta = (be - al) / (2.0 * ga);
+        const double t = copysign(1.0, zeta) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+        const double c = 1.0 / sqrt(1.0 + t * t), sn = c * t;
+        for (int i = lane; i < m; i += 32) {
+          const double x = ap[i], y = aq[i];
+          ap[i] = c * x - sn * y;
+          aq[i] = sn * x + c * y;
+        }
+        double* vp = Vt + (int64_t)p * n;
+        double* vq = Vt + (int64_t)q * n;
+        for (int i = lane; i < n; i += 32) {
+          const double x = vp[i], y = vq[i];
+          vp[i] = c * x - sn * y;
+          vq[i] = sn * x + c * y;
+        }
+        if (lane == 0) rotated = 1;
+      }
+      __syncthreads();
+    }
+    if (!rotated) break;
+    __syncthreads();
+  }
+  for (int j = warp; j < n; j += nw) {
+    double ss = 0.0;
+    for (int i = lane; i < m; i += 32) ss = fma(At[(int64_t)j * m + i], At[(int64_t)j * m + i], ss);
+    for (int o = 16; o; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+    if (lane == 0) jb.s[j] = sqrt(ss);
+  }
+}
+
+__global__ void gather_kernel(const GatherJob* jobs) {
+  const GatherJob g = jobs[blockIdx.x];
+  for (int i = threadIdx.x; i < g.nl; i += blockDim.x) g.dl[i] = g.left[i] * g.sl;
+  for (int i = threadIdx.x; i < g.nr; i += blockDim.x) g.dr[i] = g.right[i] * g.sr;
+}
+
+// ---------------------------------------------------------------------------------
+namespace {
+
+template <typename T>
+ftn_status put_table(ftn_ctx ctx, const std::vector<T>& v, void** d) {
+  return upload_table(ctx, v.data(), v.size() * sizeof(T), d);
+}
+
+struct DevBuf {
+  ftn_ctx ctx;
+  void* p = nullptr;
+  explicit DevBuf(ftn_ctx c) : ctx(c) {}
+  ~DevBuf() {
+    if (p) dev_free(ctx, p);
+  }
+};
+
+GemmProb make_prob(int M, int N, int K, int64_t a_off, int64_t a_sm, int64_t a_sk, int64_t b_off, int64_t b_sn,
+                   int64_t b_sk) {
+  GemmProb g;
+  std::memset(&g, 0, sizeof(g));
+  g.M = M;
+  g.N = N;
+  g.K = K;
+  g.a_off = a_off;
+  g.a_sm = a_sm;
+  g.a_sk = a_sk;
+  g.b_off = b_off;
+  g.b_sn = b_sn;
+  g.b_sk = b_sk;
+  g.tiles_m = (M + 63) / 64;
+  g.tiles_n = (N + 63) / 64;
+  return g;
+}
+
+ftn_status run_gemms(ftn_ctx ctx, std::vector<GemmProb>& probs, const double* A, const double* B, double* C,
+                     int64_t a_n, int64_t b_n, int64_t c_n, DevBuf& keep) {
+  if (probs.empty()) return FTN_OK;
+  int64_t tiles = 0;
+  for (auto& g : probs) {
+    g.tile_begin = tiles;
+    tiles += (int64_t)g.tiles_m * g.tiles_n * (g.nsplit > 1 ? g.nsplit : 1);
+  }
+  if (!probs_in_bounds(probs, a_n, b_n, c_n)) return set_error(FTN_EINVAL, "internal error: compression GEMM out of bounds");
+  FTN_TRY(put_table(ctx, probs, &keep.p));
+  return launch_gemm_f64(ctx, (const GemmProb*)keep.p, (int)probs.size(), tiles, A, B, C);
+}
+
+}  // namespace
+
+ftn_status compress_impl(ftn_ctx ctx, ftn_tensor* pX, ftn_tensor* pY, int n, const int* ax, const int* ay, int chi,
+                         int arrows, ftn_compress_info* info) {
+  if (!ctx || !pX || !pY || !*pX || !*pY) return set_error(FTN_EINVAL, "null argument");
+  ftn_tensor X = *pX, Y = *pY;
+  if (X->dtype != FTN_F64 || Y->dtype != FTN_F64)
+    return set_error(FTN_EUNSUPPORTED, "ftn_compress works on FP64 tensors");
+  if (chi < 0) return set_error(FTN_EINVAL, "chi must be >= 0");
+  if (n < 1) return set_error(FTN_EINVAL, "a bond needs at least one leg pair");
+  FTN_TRY(validate_pairs(X, Y, n, ax, ay));
+  uint64_t flip = 0;
+  if (!arrows)  // cancel the arrow parity: plain ordered contraction F(XY)
+    for (int i = 0; i < n; ++i)
+      if (X->dual[ax[i]] == 0) flip |= 1ull << ax[i];
+  std::shared_ptr<TdPlan> P;
+  FTN_TRY(get_plan(ctx, X, Y, n, ax, ay, flip, 0, nullptr, FTN_PREC_F64, P));
+  for (int pi = 0; pi < 2; ++pi)
+    if (P->K[pi] > LA_MAX_DIM) return set_error(FTN_EUNSUPPORTED, "bond sector larger than the batched Jacobi SVD handles");
+
+  // ---- workspace layout (doubles) ----
+  auto al = [](int64_t x) { return (x + 31) / 32 * 32; };
+  int64_t off = 0;
+  const int64_t o_xf = off;
+  off += al(P->af_elems);
+  const int64_t o_yf = off;
+  off += al(P->bf_elems);
+  int64_t o_px_part[2], o_py_part[2];
+  int sp_x[2], sp_y[2];
+  int64_t o_gx[2], o_gy[2], o_m[2], o_vt[2], o_s[2], o_wk[2], o_zk[2], o_px[2], o_qy[2];
+  int rx[2], ry[2], ldx[2], ldy[2], nrot[2], mlen[2];
+  int64_t rx_off[2], ry_off[2];
+  bool tall_x[2], tall_y[2], trans[2];
+  for (int pi = 0; pi < 2; ++pi) {
+    const int64_t K = P->K[pi], R = P->M[pi], Cc = P->N[pi];
+    tall_x[pi] = R > K;
+    tall_y[pi] = Cc > K;
+    rx[pi] = (int)std::min(R, K);
+    ry[pi] = (int)std::min(Cc, K);
+    o_gx[pi] = off;
+    off += tall_x[pi] ? al(K * K) : 0;
+    o_gy[pi] = off;
+    off += tall_y[pi] ? al(K * K) : 0;
+    // split-K over the long (row) dimension of the Gram products
+    auto split_for = [&](int64_t rows) {
+      const int64_t tiles = ((K + 63) / 64) * ((K + 63) / 64);
+      int64_t s = std::max<int64_t>(1, (2 * (int64_t)ctx->num_sms + tiles - 1) / tiles);
+      s = std::min<int64_t>(s, std::max<int64_t>(1, rows / 512));
+      return (int)std::min<int64_t>(s, 64);
+    };
+    sp_x[pi] = tall_x[pi] ? split_for(R) : 1;
+    sp_y[pi] = tall_y[pi] ? split_for(Cc) : 1;
+    o_px_part[pi] = off;
+    off += sp_x[pi] > 1 ? al((int64_t)sp_x[pi] * K * K) : 0;
+    o_py_part[pi] = off;
+    off += sp_y[pi] > 1 ? al((int64_t)sp_y[pi] * K * K) : 0;
+    rx_off[pi] = tall_x[pi] ? o_gx[pi] : o_xf + P->afoff[pi];
+    ldx[pi] = tall_x[pi] ? (int)K : (int)P->ldk[pi];
+    ry_off[pi] = tall_y[pi] ? o_gy[pi] : o_yf + P->bfoff[pi];
+    ldy[pi] = tall_y[pi] ? (int)K : (int)P->ldk[pi];
+    trans[pi] = rx[pi] > ry[pi];  // rotate the shorter side
+    nrot[pi] = trans[pi] ? ry[pi] : rx[pi];
+    mlen[pi] = trans[pi] ? rx[pi] : ry[pi];
+    o_m[pi] = off;
+    off += al((int64_t)nrot[pi] * mlen[pi]);
+    o_vt[pi] = off;
+    off += al((int64_t)nrot[pi] * nrot[pi]);
+    o_s[pi] = off;
+    off += al(nrot[pi]);
+    // kept vectors and projectors (at most nrot of them)
+    o_wk[pi] = off;
+    off += al((int64_t)nrot[pi] * rx[pi]);
+    o_zk[pi] = off;
+    off += al((int64_t)nrot[pi] * ry[pi]);
+    o_px[pi] = off;
+    off += al((int64_t)nrot[pi] * K);
+    o_qy[pi] = off;
+    off += al((int64_t)nrot[pi] * K);
+  }
+  const int64_t ws_n = off;
+  double* ws = (double*)workspace(ctx, (size_t)ws_n * 8);
+  if (!ws) return set_error(FTN_ENOMEM, "workspace allocation failed");
+
+  // ---- 1. fused matrices ----
+  int rec = prof_begin(ctx, "permute", (X->numel + Y->numel) * 16.0, 0);
+  FTN_TRY(launch_permute(ctx, P->d_ja, (int)P->ja.size(), P->ta, P->sa, X->data, ws + o_xf, nullptr, FTN_F64,
+                         PERM_SAME));
+  FTN_TRY(launch_permute(ctx, P->d_jb, (int)P->jb.size(), P->tb, P->sb, Y->data, ws + o_yf, nullptr, FTN_F64,
+                         PERM_SAME));
+  prof_end(ctx, rec);
+
+  DevBuf t_gram(ctx), t_chol(ctx), t_m(ctx), t_svd(ctx), t_gat(ctx), t_proj(ctx), t_fx(ctx), t_fy(ctx);
+  // ---- 2. Gram matrices and R factors ----
+  std::vector<GemmProb> gram;
+  std::vector<CholJob> chol;
+  struct Red {
+    int64_t dst, src;
+    int64_t count;
+    int nsplit;
+  };
+  std::vector<Red> reds;
+  auto add_gram = [&](int K, int rows, int64_t src, int64_t ld, int64_t dst, int64_t part, int nsplit) {
+    GemmProb g = make_prob(K, K, rows, src, 1, ld, src, 1, ld);
+    if (nsplit > 1) {
+      g.nsplit = nsplit;
+      g.kchunk = (rows + nsplit - 1) / nsplit;
+      g.kchunk = (g.kchunk + 15) / 16 * 16;
+      g.nsplit = (rows + g.kchunk - 1) / g.kchunk;
+      gemm_plain_output(g, part, K);
+      g.c_slab = (int64_t)K * K;
+      reds.push_back({dst, part, (int64_t)K * K, g.nsplit});
+    } else {
+      gemm_plain_output(g, dst, K);
+    }
+    gram.push_back(g);
+    chol.push_back({ws + dst, K});
+  };
+  for (int pi = 0; pi < 2; ++pi) {
+    const int K = (int)P->K[pi];
+    if (K == 0) continue;
+    if (tall_x[pi] && P->M[pi] > 0)
+      add_gram(K, (int)P->M[pi], o_xf + P->afoff[pi], P->ldk[pi], o_gx[pi], o_px_part[pi], sp_x[pi]);
+    if (tall_y[pi] && P->N[pi] > 0)
+      add_gram(K, (int)P->N[pi], o_yf + P->bfoff[pi], P->ldk[pi], o_gy[pi], o_py_part[pi], sp_y[pi]);
+  }
+  double gram_fl = 0;
+  for (auto& g : gram) gram_fl += 2.0 * g.M * g.N * g.K;
+  rec = prof_begin(ctx, "gemm_f64", 0, gram_fl);
+  FTN_TRY(run_gemms(ctx, gram, ws, ws, ws, ws_n, ws_n, ws_n, t_gram));
+  for (auto& r : reds) FTN_TRY(launch_sum_slabs(ctx, ws + r.dst, ws + r.src, r.count, r.nsplit, r.count));
+  prof_end(ctx, rec);
+  if (!chol.empty()) {
+    FTN_TRY(put_table(ctx, chol, &t_chol.p));
+    rec = prof_begin(ctx, "cholesky", 0, 0);
+    chol_kernel<<<(unsigned)chol.size(), LA_THREADS, 0, ctx->stream>>>((const CholJob*)t_chol.p);
+    ctx->launches += 1;
+    FTN_CUDA(cudaGetLastError());
+    prof_end(ctx, rec);
+  }
+  // ---- 3. core M = R_X R_Y^T (stored with the rotated side as rows) and SVD ----
+  std::vector<GemmProb> mg;
+  std::vector<SvdJob> svd;
+  for (int pi = 0; pi < 2; ++pi) {
+    const int K = (int)P->K[pi];
+    if (K == 0 || rx[pi] == 0 || ry[pi] == 0) {
+      nrot[pi] = 0;
+      continue;
+    }
+    GemmProb g = make_prob(rx[pi], ry[pi], K, rx_off[pi], ldx[pi], 1, ry_off[pi], ldy[pi], 1);
+    if (!trans[pi])
+      gemm_plain_output(g, o_m[pi], ry[pi]);  // M: rx x ry
+    else {
+      gemm_plain_output(g, o_m[pi], 0);  // M^T: ry x rx  (element (i, j) at j * rx + i)
+      g.rstr[0] = 1;
+      g.cstr[0] = rx[pi];
+    }
+    mg.push_back(g);
+    svd.push_back({ws + o_m[pi], ws + o_vt[pi], ws + o_s[pi], nrot[pi], mlen[pi]});
+  }
+  rec = prof_begin(ctx, "gemm_f64", 0, 0);
+  FTN_TRY(run_gemms(ctx, mg, ws, ws, ws, ws_n, ws_n, ws_n, t_m));
+  prof_end(ctx, rec);
+  if (!svd.empty()) {
+    FTN_TRY(put_table(ctx, svd, &t_svd.p));
+    rec = prof_begin(ctx, "svd_jacobi", 0, 0);
+    svd_jacobi_kernel<<<(unsigned)svd.size(), LA_THREADS, 0, ctx->stream>>>((const SvdJob*)t_svd.p);
+    ctx->launches += 1;
+    FTN_CUDA(cudaGetLastError());
+    prof_end(ctx, rec);
+  }
+  // ---- 4. pooled truncation (one synchronisation) ----
+  std::vector<double> sv[2];
+  for (int pi = 0; pi < 2; ++pi) {
+    sv[pi].resize(nrot[pi]);
+    if (nrot[pi])
+      FTN_CUDA(cudaMemcpyAsync(sv[pi].data(), ws + o_s[pi], nrot[pi] * 8, cudaMemcpyDeviceToHost, ctx->stream));
+  }
+  FTN_CUDA(cudaStreamSynchronize(ctx->stream));
+  struct Cand {
+    double s;
+    int pi, idx;
+  };
+  std::vector<Cand> cand;
+  double smax = 0, total = 0;
+  for (int pi = 0; pi < 2; ++pi)
+    for (int i = 0; i < nrot[pi]; ++i) {
+      cand.push_back({sv[pi][i], pi, i});
+      smax = std::max(smax, sv[pi][i]);
+      total += sv[pi][i] * sv[pi][i];
+    }
+  std::stable_sort(cand.begin(), cand.end(), [](const Cand& a, const Cand& b) {
+    if (a.s != b.s) return a.s > b.s;
+    if (a.pi != b.pi) return a.pi < b.pi;
+    return a.idx < b.idx;
+  });
+  const double zero_tol = 1e-14 * smax;
+  int rank_s[2] = {0, 0};
+  for (auto& c : cand)
+    if (c.s > zero_tol) rank_s[c.pi]++;
+  std::vector<Cand> kept;
+  double disc = 0;
+  for (size_t i = 0; i < cand.size(); ++i) {
+    if ((int)kept.size() < chi && cand[i].s > zero_tol)
+      kept.push_back(cand[i]);
+    else
+      disc += cand[i].s * cand[i].s;
+  }
+  int k[2] = {0, 0};
+  for (auto& c : kept) k[c.pi]++;
+  // ---- 5. projectors and the new tensors ----
+  std::vector<GatherJob> gat;
+  int pos[2] = {0, 0};
+  for (auto& c : kept) {
+    const int pi = c.pi, j = pos[pi]++;
+    const double* rot = ws + o_vt[pi] + (int64_t)c.idx * nrot[pi];  // rotation row (length nrot)
+    const double* vec = ws + o_m[pi] + (int64_t)c.idx * mlen[pi];   // orthogonalised row (length mlen)
+    const double is = 1.0 / sqrt(c.s);
+    GatherJob g;
+    // left singular vectors of M live in the rx-long rows, right ones in the ry-long rows
+    if (!trans[pi]) {
+      g.left = rot, g.nl = rx[pi], g.sl = is;
+      g.right = vec, g.nr = ry[pi], g.sr = is / c.s;
+    } else {
+      g.left = vec, g.nl = rx[pi], g.sl = is / c.s;
+      g.right = rot, g.nr = ry[pi], g.sr = is;
+    }
+    g.dl = ws + o_wk[pi] + (int64_t)j * rx[pi];
+    g.dr = ws + o_zk[pi] + (int64_t)j * ry[pi];
+    gat.push_back(g);
+  }
+  if (!gat.empty()) {
+    FTN_TRY(put_table(ctx, gat, &t_gat.p));
+    gather_kernel<<<(unsigned)gat.size(), 128, 0, ctx->stream>>>((const GatherJob*)t_gat.p);
+    ctx->launches += 1;
+    FTN_CUDA(cudaGetLastError());
+  }
+  // P_X^T = Z_k R_Y (k x K) and Q_Y^T = W_k R_X (k x K)
+  std::vector<GemmProb> proj;
+  for (int pi = 0; pi < 2; ++pi) {
+    const int K = (int)P->K[pi];
+    if (k[pi] == 0) continue;
+    GemmProb a = make_prob(k[pi], K, ry[pi], o_zk[pi], ry[pi], 1, ry_off[pi], 1, ldy[pi]);
+    gemm_plain_output(a, o_px[pi], K);
+    proj.push_back(a);
+    GemmProb b = make_prob(k[pi], K, rx[pi], o_wk[pi], rx[pi], 1, rx_off[pi], 1, ldx[pi]);
+    gemm_plain_output(b, o_qy[pi], K);
+    proj.push_back(b);
+  }
+  rec = prof_begin(ctx, "gemm_f64", 0, 0);
+  FTN_TRY(run_gemms(ctx, proj, ws, ws, ws, ws_n, ws_n, ws_n, t_proj));
+  prof_end(ctx, rec);
+  // new tensors: X' = [free_X | new(-)], Y' = [new(+) | free_Y]
+  int32_t xd0[MAXR], xd1[MAXR], yd0[MAXR], yd1[MAXR];
+  uint8_t xdu[MAXR], ydu[MAXR];
+  for (int j = 0; j < P->nfa; ++j)
+    xd0[j] = X->d0[P->fa[j]], xd1[j] = X->d1[P->fa[j]], xdu[j] = X->dual[P->fa[j]];
+  xd0[P->nfa] = k[0], xd1[P->nfa] = k[1], xdu[P->nfa] = 1;
+  yd0[0] = k[0], yd1[0] = k[1], ydu[0] = 0;
+  for (int j = 0; j < P->nfb; ++j)
+    yd0[j + 1] = Y->d0[P->fb[j]], yd1[j + 1] = Y->d1[P->fb[j]], ydu[j + 1] = Y->dual[P->fb[j]];
+  ftn_tensor Xn = nullptr, Yn = nullptr;
+  FTN_TRY(make_tensor(ctx, P->nfa + 1, xd0, xd1, xdu, X->parity, FTN_F64, &Xn));
+  ftn_status st = make_tensor(ctx, P->nfb + 1, yd0, yd1, ydu, Y->parity, FTN_F64, &Yn);
+  if (st != FTN_OK) {
+    ftn_tensor_free(Xn);
+    return st;
+  }
+  std::vector<GemmProb> fx, fy;
+  for (int pi = 0; pi < 2; ++pi) {
+    if (k[pi] == 0) continue;
+    const int K = (int)P->K[pi];
+    const int rho = X->parity ^ pi, sig = Y->parity ^ pi;
+    for (uint32_t mA = 0; mA < (1u << P->nfa); ++mA) {
+      if ((popc(mA) & 1) != rho || P->rowsz[pi][mA] == 0) continue;
+      const uint32_t mask = mA | ((uint32_t)pi << P->nfa);
+      GemmProb g = make_prob((int)P->rowsz[pi][mA], k[pi], K, o_xf + P->afoff[pi] + P->rowoff[pi][mA] * P->ldk[pi],
+                             P->ldk[pi], 1, o_px[pi], K, 1);
+      gemm_plain_output(g, Xn->offsets[mask >> 1], k[pi]);
+      fx.push_back(g);
+    }
+    for (uint32_t mB = 0; mB < (1u << P->nfb); ++mB) {
+      if ((popc(mB) & 1) != sig || P->colsz[pi][mB] == 0) continue;
+      const uint32_t mask = (uint32_t)pi | (mB << 1);
+      const int Cm = (int)P->colsz[pi][mB];
+      GemmProb g = make_prob(Cm, k[pi], K, o_yf + P->bfoff[pi] + P->coloff[pi][mB] * P->ldk[pi], P->ldk[pi], 1,
+                             o_qy[pi], K, 1);
+      gemm_plain_output(g, Yn->offsets[mask >> 1], 0);  // written transposed: (new, free)
+      g.rstr[0] = 1;
+      g.cstr[0] = Cm;
+      fy.push_back(g);
+    }
+  }
+  // blocks of the new tensors that no GEMM writes (empty kept sector) are zero
+  if (Xn->numel) FTN_CUDA(cudaMemsetAsync(Xn->data, 0, Xn->numel * 8, ctx->stream));
+  if (Yn->numel) FTN_CUDA(cudaMemsetAsync(Yn->data, 0, Yn->numel * 8, ctx->stream));
+  double fl = 0;
+  for (auto& g : fx) fl += 2.0 * g.M * g.N * g.K;
+  for (auto& g : fy) fl += 2.0 * g.M * g.N * g.K;
+  rec = prof_begin(ctx, "gemm_f64", 0, fl);
+  st = run_gemms(ctx, fx, ws, ws, (double*)Xn->data, ws_n, ws_n, Xn->numel, t_fx);
+  if (st == FTN_OK) st = run_gemms(ctx, fy, ws, ws, (double*)Yn->data, ws_n, ws_n, Yn->numel, t_fy);
+  prof_end(ctx, rec);
+  if (st != FTN_OK) {
+    ftn_tensor_free(Xn);
+    ftn_tensor_free(Yn);
+    return st;
+  }
+  if (info) {
+    info->kept[0] = k[0];
+    info->kept[1] = k[1];
+    info->rank[0] = rank_s[0];
+    info->rank[1] = rank_s[1];
+    info->discarded_sq = disc;
+    info->total_sq = total;
+    info->s_max = smax;
+    info->s_cut = kept.empty() ? 0.0 : kept.back().s;
+    info->s_next = kept.size() < cand.size() ? cand[kept.size()].s : 0.0;
+  }
+  ftn_tensor_free(X);
+  ftn_tensor_free(Y);
+  *pX = Xn;
+  *pY = Yn;
+  return FTN_OK;
+}
+
+}  // namespace ftn
+
+using namespace ftn;
+
+extern "C" ftn_status ftn_compress(ftn_ctx ctx, ftn_tensor* X, ftn_tensor* Y, int n, const int* axes_x,
+                                   const int* axes_y, int chi, int arrows, ftn_compress_info* info) {
+  return compress_impl(ctx, X, Y, n, axes_x, axes_y, chi, arrows, info);
+}

@@ -33,9 +33,14 @@ __global__ void __launch_bounds__(256) gemm_f64_kernel(const GemmProb* __restric
     if (tid == 0) s_p = find_prob(probs, nprobs, t);
     __syncthreads();
     const GemmProb& p = probs[s_p];
-    const int64_t local = t - p.tile_begin;
+    int64_t local = t - p.tile_begin;
+    const int nsp = p.nsplit > 1 ? p.nsplit : 1;
+    const int ks = (int)(local % nsp);
+    local /= nsp;
     const int m0 = (int)(local / p.tiles_n) * F64_BM;
     const int n0 = (int)(local % p.tiles_n) * F64_BN;
+    const int kbeg = nsp > 1 ? ks * p.kchunk : 0;
+    const int kend = nsp > 1 ? min(p.K, kbeg + p.kchunk) : p.K;
     double acc[4][4];
 #pragma unroll
     for (int a = 0; a < 4; ++a)
@@ -43,15 +48,20 @@ __global__ void __launch_bounds__(256) gemm_f64_kernel(const GemmProb* __restric
       for (int c = 0; c < 4; ++c) acc[a][c] = 0.0;
     const double* Ap = A + p.a_off;
     const double* Bp = B + p.b_off;
-    for (int k0 = 0; k0 < p.K; k0 += F64_BK) {
+    const bool a_kfast = p.a_sk == 1, b_kfast = p.b_sk == 1;
+    for (int k0 = kbeg; k0 < kend; k0 += F64_BK) {
+      // threads run along whichever operand index has unit stride
 #pragma unroll
       for (int e = 0; e < 4; ++e) {
         int idx = tid + 256 * e;
-        int row = idx >> 4, kk = idx & 15;
+        int row = a_kfast ? idx >> 4 : idx & 63, kk = a_kfast ? idx & 15 : idx >> 6;
         int gm = m0 + row, gk = k0 + kk;
-        As[kk][row] = (gm < p.M && gk < p.K) ? Ap[(int64_t)gm * p.lda + gk] : 0.0;
+        As[kk][row] = (gm < p.M && gk < kend) ? Ap[(int64_t)gm * p.a_sm + (int64_t)gk * p.a_sk] : 0.0;
+        row = b_kfast ? idx >> 4 : idx & 63;
+        kk = b_kfast ? idx & 15 : idx >> 6;
+        gk = k0 + kk;
         int gn = n0 + row;
-        Bs[kk][row] = (gn < p.N && gk < p.K) ? Bp[(int64_t)gn * p.ldb + gk] : 0.0;
+        Bs[kk][row] = (gn < p.N && gk < kend) ? Bp[(int64_t)gn * p.b_sn + (int64_t)gk * p.b_sk] : 0.0;
       }
       __syncthreads();
 #pragma unroll
@@ -79,7 +89,7 @@ __global__ void __launch_bounds__(256) gemm_f64_kernel(const GemmProb* __restric
     for (int a = 0; a < 4; ++a) {
       int gm = m0 + ty + 16 * a;
       if (gm >= p.M) continue;
-      const int64_t rpart = p.c_off + expand_index(gm, p.nrl, p.rdim, p.rstr);
+      const int64_t rpart = p.c_off + (int64_t)ks * p.c_slab + expand_index(gm, p.nrl, p.rdim, p.rstr);
 #pragma unroll
       for (int c = 0; c < 4; ++c) {
         int gn = n0 + tx + 16 * c;
@@ -88,6 +98,36 @@ __global__ void __launch_bounds__(256) gemm_f64_kernel(const GemmProb* __restric
     }
     __syncthreads();
   }
+}
+
+__global__ void sum_slabs_kernel(double* __restrict__ dst, const double* __restrict__ src, int64_t count, int nsplit,
+                                 int64_t slab) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < count; e += (int64_t)gridDim.x * blockDim.x) {
+    double acc = 0.0;
+    for (int s = 0; s < nsplit; ++s) acc += src[s * slab + e];
+    dst[e] = acc;
+  }
+}
+
+ftn_status launch_sum_slabs(ftn_ctx ctx, double* dst, const double* src, int64_t count, int nsplit, int64_t slab) {
+  if (count <= 0) return FTN_OK;
+  int64_t grid = (count + 255) / 256;
+  if (grid > (int64_t)ctx->num_sms * 8) grid = (int64_t)ctx->num_sms * 8;
+  sum_slabs_kernel<<<(unsigned)grid, 256, 0, ctx->stream>>>(dst, src, count, nsplit, slab);
+  ctx->launches += 1;
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_error(e, "sum_slabs_kernel launch");
+  return FTN_OK;
+}
+
+void gemm_plain_output(GemmProb& g, int64_t c_off, int64_t ld) {
+  g.c_off = c_off;
+  g.c_sign = 1;
+  g.nrl = g.ncl = 1;
+  g.rdim[0] = g.M;
+  g.rstr[0] = ld;
+  g.cdim[0] = g.N;
+  g.cstr[0] = 1;
 }
 
 ftn_status launch_gemm_f64(ftn_ctx ctx, const GemmProb* d_probs, int nprobs, int64_t tiles, const double* a,

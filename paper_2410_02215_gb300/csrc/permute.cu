@@ -5,12 +5,13 @@
 // on the block's parity bits).
 //
 // Two kernels share the job format.  The staged kernel (used when every
-// source row of a job starts 16-byte aligned): warp 0 of each persistent CTA
-// issues cp.async.bulk copies of the contiguous source rows of upcoming tiles
-// into a PERM_STAGES-deep shared-memory ring (completion on an mbarrier), and
-// all eight warps write the current tile out along the destination's
-// contiguous direction; the TMA engine keeps the HBM reads in flight without
-// holding registers.  The fallback kernel stages through registers:
+// source row of a job starts 16-byte aligned): each persistent CTA
+// copies the contiguous source rows of upcoming tiles with cp.async.bulk
+// into a PERM_STAGES-deep shared-memory ring (completion on an mbarrier); a
+// dedicated producer warp runs ahead and eight consumer warps write tiles out
+// along the destination's contiguous direction, releasing ring slots through
+// a second set of mbarriers (no block-wide synchronisation in the loop).  The
+// TMA engine keeps the HBM reads in flight without holding registers.  The fallback kernel stages through registers:
 // Each CTA tile covers PERM_TO rows of the O group (destination-fast legs)
 // times PERM_TI elements of the I group (the source's contiguous suffix) for
 // one batch index.  Loads run along I (coalesced in the source); stores run
@@ -184,7 +185,8 @@ struct StagedCfg {
   static constexpr int MAXTI = TE / 8;
   static constexpr int STAGE_ELEMS = TE + PERM_MAX_ROWS * V;
   static constexpr int BYTES = PERM_STAGES * STAGE_ELEMS * (int)sizeof(Tin) + PERM_STAGES * PERM_MAX_ROWS * 4 +
-                               PERM_STAGES * MAXTI * 4 + PERM_STAGES * (int)sizeof(StageMeta) + PERM_STAGES * 8 + 128;
+                               PERM_STAGES * MAXTI * 4 + PERM_STAGES * (int)sizeof(StageMeta) + 2 * PERM_STAGES * 8 +
+                               128;
 };
 
 template <typename Tin>
@@ -271,10 +273,12 @@ __device__ __forceinline__ void staged_issue(const PermJob* __restrict__ jobs, i
   }
 }
 
+constexpr int SPT = PT + 32;  // eight consumer warps + one producer warp
+
 template <typename Tin, int MODE>
-__global__ void __launch_bounds__(PT) perm_staged_kernel(const PermJob* __restrict__ jobs, int njobs, int64_t tiles,
-                                                         const Tin* __restrict__ src, void* __restrict__ dst0,
-                                                         void* __restrict__ dst1, int* err) {
+__global__ void __launch_bounds__(SPT) perm_staged_kernel(const PermJob* __restrict__ jobs, int njobs, int64_t tiles,
+                                                          const Tin* __restrict__ src, void* __restrict__ dst0,
+                                                          void* __restrict__ dst1, int* err) {
   using Cfg = StagedCfg<Tin>;
   extern __shared__ uint8_t sm_raw[];
   uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(sm_raw) + 127) & ~uintptr_t(127));
@@ -283,31 +287,46 @@ __global__ void __launch_bounds__(PT) perm_staged_kernel(const PermJob* __restri
   int32_t* colD = rowD + PERM_STAGES * PERM_MAX_ROWS;
   StageMeta* meta = reinterpret_cast<StageMeta*>(colD + PERM_STAGES * Cfg::MAXTI);
   uint64_t* full = reinterpret_cast<uint64_t*>(meta + PERM_STAGES);
+  uint64_t* empty = full + PERM_STAGES;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  constexpr int NCW = PT / 32;  // consumer warps
   if (tid == 0) {
-    for (int s = 0; s < PERM_STAGES; ++s) mbar_init(&full[s], 32);
+    for (int s = 0; s < PERM_STAGES; ++s) {
+      mbar_init(&full[s], 32);
+      mbar_init(&empty[s], NCW);
+    }
     fence_mbar_init();
   }
   __syncthreads();
   const int64_t stride_t = gridDim.x;
-  int64_t issued = 0;
-  if (warp == 0) {
-    for (int s = 0; s < PERM_STAGES; ++s) {
-      const int64_t t = blockIdx.x + s * stride_t;
+  if (warp == NCW) {
+    // ---------------- producer warp ----------------
+    int64_t k = 0;
+    for (;; ++k) {
+      const int64_t t = blockIdx.x + k * stride_t;
       if (t >= tiles) break;
+      const int s = (int)(k % PERM_STAGES);
+      const uint32_t par = (uint32_t)((k / PERM_STAGES) & 1);
+      bool ok = true;
+      if (lane == 0) ok = mbar_wait(&empty[s], par ^ 1, err);
+      if (!__shfl_sync(0xffffffffu, ok ? 1 : 0, 0)) break;
       staged_issue<Tin>(jobs, njobs, t, src, buf + s * Cfg::STAGE_ELEMS, rowD + s * PERM_MAX_ROWS,
                         colD + s * Cfg::MAXTI, meta + s, &full[s], lane);
-      ++issued;
     }
+    // wait for this CTA's copies still in flight (all consumed on a normal exit)
+    if (lane == 0) {
+      for (int64_t q = (k >= PERM_STAGES ? k - PERM_STAGES : 0); q < k; ++q)
+        mbar_wait(&full[q % PERM_STAGES], (uint32_t)((q / PERM_STAGES) & 1), err, false);
+    }
+    return;
   }
-  int64_t k = 0;
-  for (;; ++k) {
+  // ---------------- consumer warps ----------------
+  for (int64_t k = 0;; ++k) {
     const int64_t t = blockIdx.x + k * stride_t;
     if (t >= tiles) break;
     const int s = (int)(k % PERM_STAGES);
     const uint32_t par = (uint32_t)((k / PERM_STAGES) & 1);
-    const bool ok = mbar_wait(&full[s], par, err);
-    if (__syncthreads_or(!ok)) break;
+    if (!mbar_wait(&full[s], par, err)) break;
     const StageMeta m = meta[s];
     const Tin* tb = buf + s * Cfg::STAGE_ELEMS;
     const int32_t* rd = rowD + s * PERM_MAX_ROWS;
@@ -315,12 +334,12 @@ __global__ void __launch_bounds__(PT) perm_staged_kernel(const PermJob* __restri
     const int stride = m.ti + Cfg::V;
     const Tin sgn = (Tin)m.sign;
     if (m.fast_i) {
-      for (int r = warp; r < m.nrows; r += PT / 32) {
+      for (int r = warp; r < m.nrows; r += NCW) {
         const int64_t base = m.baseD + rd[r];
         for (int c = lane; c < m.ncols; c += 32) put<Tin, MODE>(dst0, dst1, base + cd[c], sgn * tb[r * stride + c]);
       }
     } else {
-      for (int c0 = warp * Cfg::V; c0 < m.ncols; c0 += (PT / 32) * Cfg::V) {
+      for (int c0 = warp * Cfg::V; c0 < m.ncols; c0 += NCW * Cfg::V) {
         for (int r = lane; r < m.nrows; r += 32) {
           Tin v[Cfg::V];
           if constexpr (sizeof(Tin) == 4) {
@@ -337,20 +356,8 @@ __global__ void __launch_bounds__(PT) perm_staged_kernel(const PermJob* __restri
         }
       }
     }
-    __syncthreads();
-    if (warp == 0) {
-      const int64_t tn = blockIdx.x + (k + PERM_STAGES) * stride_t;
-      if (tn < tiles) {
-        staged_issue<Tin>(jobs, njobs, tn, src, buf + s * Cfg::STAGE_ELEMS, rowD + s * PERM_MAX_ROWS,
-                          colD + s * Cfg::MAXTI, meta + s, &full[s], lane);
-        ++issued;
-      }
-    }
-  }
-  // after an early exit, wait for this CTA's copies still in flight
-  if (warp == 0 && lane == 0) {
-    for (int64_t q = k; q < issued; ++q)
-      mbar_wait(&full[q % PERM_STAGES], (uint32_t)((q / PERM_STAGES) & 1), err, false);
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&empty[s]);
   }
 }
 
@@ -368,7 +375,7 @@ static cudaError_t go_staged(ftn_ctx ctx, const PermJob* d_jobs, int njobs, int6
   int64_t grid = tiles;
   int64_t cap = (int64_t)ctx->num_sms * 3;
   if (grid > cap) grid = cap;
-  perm_staged_kernel<Tin, MODE><<<(unsigned)grid, PT, Cfg::BYTES, ctx->stream>>>(d_jobs, njobs, tiles,
+  perm_staged_kernel<Tin, MODE><<<(unsigned)grid, SPT, Cfg::BYTES, ctx->stream>>>(d_jobs, njobs, tiles,
                                                                                  (const Tin*)src, dst0, dst1,
                                                                                  ctx->dev_err);
   return cudaGetLastError();

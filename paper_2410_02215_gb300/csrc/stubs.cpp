@@ -5,10 +5,6 @@ using namespace ftn;
 
 extern "C" {
 
-ftn_status ftn_compress(ftn_ctx, ftn_tensor*, ftn_tensor*, int, const int*, const int*, int, int, ftn_compress_info*) {
-  return set_error(FTN_EUNSUPPORTED, "ftn_compress is not built yet");
-}
-
 ftn_status ftn_contract(ftn_ctx, const ftn_network*, const ftn_tree*, ftn_prec, double*, double*) {
   return set_error(FTN_EUNSUPPORTED, "ftn_contract is not built yet");
 }

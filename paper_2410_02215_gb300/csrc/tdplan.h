@@ -1,0 +1,50 @@
+// Contraction plan shared by the tensordot and the compression code.
+#pragma once
+#include "common.h"
+
+namespace ftn {
+
+struct DevTables {
+  ftn_ctx ctx;
+  void* p = nullptr;
+  ~DevTables() {
+    if (p) dev_free(ctx, p);
+  }
+};
+
+// ---------------------------------------------------------------------------------
+struct TdPlan {
+  int nfa = 0, nfb = 0, n = 0;
+  int fa[MAXR], fb[MAXR];
+  int64_t M[2] = {0, 0}, N[2] = {0, 0}, K[2] = {0, 0}, ldk[2] = {8, 8};
+  int64_t afoff[2] = {0, 0}, bfoff[2] = {0, 0};
+  int64_t af_elems = 0, bf_elems = 0;
+  std::vector<PermJob> ja, jb, jc;
+  int64_t ta = 0, tb = 0, tc = 0;
+  int sa = 0, sb = 0, sc = 0;  // staged (TMA) permute kernel usable
+  bool fused = true;           // the GEMM epilogue writes the final layout
+  std::vector<GemmProb> probs;
+  int64_t gemm_tiles = 0;
+  int bn = 0;
+  bool out_perm = false;
+  int cr = 0;  // result rank
+  int32_t cd0[MAXR], cd1[MAXR];
+  uint8_t cdual[MAXR];
+  int cpar = 0;
+  int64_t tmp_numel = 0;  // elements of the result
+  // fused-matrix row/column offsets and sizes per pi, indexed by free-leg mask
+  std::vector<int64_t> rowoff[2], rowsz[2], coloff[2], colsz[2];
+  // device copies
+  std::shared_ptr<DevTables> dev;
+  PermJob* d_ja = nullptr;
+  PermJob* d_jb = nullptr;
+  PermJob* d_jc = nullptr;
+  GemmProb* d_probs = nullptr;
+};
+
+ftn_status get_plan(ftn_ctx ctx, const ftn_tensor_s* A, const ftn_tensor_s* B, int n, const int* ax, const int* ay,
+                    uint64_t fa, uint64_t fb, const int* out_perm, ftn_prec prec, std::shared_ptr<TdPlan>& P);
+ftn_status validate_pairs(const ftn_tensor_s* A, const ftn_tensor_s* B, int n, const int* ax, const int* ay);
+int inversion_parity(int r, const int* perm, uint32_t mask);
+
+}  // namespace ftn

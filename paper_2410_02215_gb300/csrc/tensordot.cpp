@@ -5,13 +5,13 @@
 #include <algorithm>
 #include <sstream>
 
-#include "common.h"
+#include "tdplan.h"
 
 namespace ftn {
 
 // parity (0/1) of the number of inverted pairs of set bits: out position u
 // holds source leg perm[u]; bits are indexed by source leg.
-static int inversion_parity(int r, const int* perm, uint32_t mask) {
+int inversion_parity(int r, const int* perm, uint32_t mask) {
   int s = 0;
   for (int u = 0; u < r; ++u) {
     if (!((mask >> perm[u]) & 1)) continue;
@@ -63,56 +63,21 @@ static bool jobs_in_bounds(const std::vector<PermJob>& jobs, int64_t src_n, int6
   return true;
 }
 
-static bool probs_in_bounds(const std::vector<GemmProb>& probs, int64_t a_n, int64_t b_n, int64_t c_n) {
+bool probs_in_bounds(const std::vector<GemmProb>& probs, int64_t a_n, int64_t b_n, int64_t c_n) {
   for (const GemmProb& g : probs) {
     if (g.M <= 0 || g.N <= 0 || g.K < 0) return false;
     if (g.K > 0) {
-      if (g.a_off + (int64_t)(g.M - 1) * g.lda + g.K > a_n) return false;
-      if (g.b_off + (int64_t)(g.N - 1) * g.ldb + g.K > b_n) return false;
+      if (g.a_off + (int64_t)(g.M - 1) * g.a_sm + (int64_t)(g.K - 1) * g.a_sk >= a_n) return false;
+      if (g.b_off + (int64_t)(g.N - 1) * g.b_sn + (int64_t)(g.K - 1) * g.b_sk >= b_n) return false;
     }
-    int64_t mr = 1, mc = 1, top = g.c_off;
+    int64_t mr = 1, mc = 1, top = g.c_off + (g.nsplit > 1 ? (int64_t)(g.nsplit - 1) * g.c_slab : 0);
+    if (g.nsplit > 1 && ((int64_t)g.nsplit * g.kchunk < g.K || g.kchunk <= 0)) return false;
     for (int l = 0; l < g.nrl; ++l) mr *= g.rdim[l], top += (int64_t)(g.rdim[l] - 1) * g.rstr[l];
     for (int l = 0; l < g.ncl; ++l) mc *= g.cdim[l], top += (int64_t)(g.cdim[l] - 1) * g.cstr[l];
     if (mr != g.M || mc != g.N || g.c_off < 0 || top >= c_n) return false;
   }
   return true;
 }
-
-struct DevTables {
-  ftn_ctx ctx;
-  void* p = nullptr;
-  ~DevTables() {
-    if (p) dev_free(ctx, p);
-  }
-};
-
-// ---------------------------------------------------------------------------------
-struct TdPlan {
-  int nfa = 0, nfb = 0, n = 0;
-  int fa[MAXR], fb[MAXR];
-  int64_t M[2] = {0, 0}, N[2] = {0, 0}, K[2] = {0, 0}, ldk[2] = {8, 8};
-  int64_t afoff[2] = {0, 0}, bfoff[2] = {0, 0};
-  int64_t af_elems = 0, bf_elems = 0;
-  std::vector<PermJob> ja, jb, jc;
-  int64_t ta = 0, tb = 0, tc = 0;
-  int sa = 0, sb = 0, sc = 0;  // staged (TMA) permute kernel usable
-  bool fused = true;           // the GEMM epilogue writes the final layout
-  std::vector<GemmProb> probs;
-  int64_t gemm_tiles = 0;
-  int bn = 0;
-  bool out_perm = false;
-  int cr = 0;  // result rank
-  int32_t cd0[MAXR], cd1[MAXR];
-  uint8_t cdual[MAXR];
-  int cpar = 0;
-  int64_t tmp_numel = 0;  // elements of the result
-  // device copies
-  std::shared_ptr<DevTables> dev;
-  PermJob* d_ja = nullptr;
-  PermJob* d_jb = nullptr;
-  PermJob* d_jc = nullptr;
-  GemmProb* d_probs = nullptr;
-};
 
 static std::string meta_key(const ftn_tensor_s* t) {
   std::ostringstream o;
@@ -170,7 +135,8 @@ static ftn_status build_plan(ftn_ctx ctx, const ftn_tensor_s* A, const ftn_tenso
   for (int j = 0; j < P->nfa; ++j) fad0[j] = A->d0[P->fa[j]], fad1[j] = A->d1[P->fa[j]];
   for (int j = 0; j < P->nfb; ++j) fbd0[j] = B->d0[P->fb[j]], fbd1[j] = B->d1[P->fb[j]];
   for (int i = 0; i < n; ++i) kd0[i] = A->d0[ax[i]], kd1[i] = A->d1[ax[i]];
-  std::vector<int64_t> rowoff[2], rowsz[2], coloff[2], colsz[2], koff[2], ksz[2];
+  std::vector<int64_t>*rowoff = P->rowoff, *rowsz = P->rowsz, *coloff = P->coloff, *colsz = P->colsz;
+  std::vector<int64_t> koff[2], ksz[2];
   for (int pi = 0; pi < 2; ++pi) {
     P->M[pi] = sector_offsets(P->nfa, fad0, fad1, pA ^ pi, rowoff[pi], rowsz[pi]);
     P->N[pi] = sector_offsets(P->nfb, fbd0, fbd1, pB ^ pi, coloff[pi], colsz[pi]);
@@ -330,6 +296,8 @@ static ftn_status build_plan(ftn_ctx ctx, const ftn_tensor_s* A, const ftn_tenso
     g.b_row0 = (int32_t)coloff[pi][mB];
     g.a_off = P->afoff[pi] + rowoff[pi][mA] * P->ldk[pi];
     g.b_off = P->bfoff[pi] + coloff[pi][mB] * P->ldk[pi];
+    g.a_sm = g.b_sn = P->ldk[pi];
+    g.a_sk = g.b_sk = 1;
     if (fuse) {
       // destination block in the (permuted) result and the stride of each leg
       uint32_t mo = 0;
@@ -396,7 +364,7 @@ static ftn_status build_plan(ftn_ctx ctx, const ftn_tensor_s* A, const ftn_tenso
   return FTN_OK;
 }
 
-static ftn_status validate_pairs(const ftn_tensor_s* A, const ftn_tensor_s* B, int n, const int* ax, const int* ay) {
+ftn_status validate_pairs(const ftn_tensor_s* A, const ftn_tensor_s* B, int n, const int* ax, const int* ay) {
   if (n < 0 || n > A->rank || n > B->rank) return set_error(FTN_EINVAL, "bad number of contracted legs");
   if (n > 0 && (!ax || !ay)) return set_error(FTN_EINVAL, "null axes");
   bool ua[MAXR] = {}, ub[MAXR] = {};
@@ -413,7 +381,7 @@ static ftn_status validate_pairs(const ftn_tensor_s* A, const ftn_tensor_s* B, i
   return FTN_OK;
 }
 
-static ftn_status get_plan(ftn_ctx ctx, const ftn_tensor_s* A, const ftn_tensor_s* B, int n, const int* ax,
+ftn_status get_plan(ftn_ctx ctx, const ftn_tensor_s* A, const ftn_tensor_s* B, int n, const int* ax,
                            const int* ay, uint64_t fa, uint64_t fb, const int* out_perm, ftn_prec prec,
                            std::shared_ptr<TdPlan>& P) {
   std::ostringstream key;
