@@ -39,7 +39,7 @@ CASES = [
     ([(3, 2, 1), (2, 2, 0), (2, 1, 1)], [(1, 2, 0), (2, 2, 1), (2, 1, 0)], [1], [1], 1, 0),
     ([(2, 2, 1), (3, 3, 0), (2, 1, 1), (1, 1, 0)], [(3, 3, 1), (1, 1, 1), (2, 2, 0)], [1, 3], [0, 1], 1, 1),
     # tall on both sides, bond of 2 legs (16 + 16 states)
-    ([(8, 8, 0), (4, 4, 1), (4, 4, 0), (6, 5, 1)], [(4, 4, 1), (8, 8, 0), (6, 5, 0), (3, 3, 1)], [1, 3], [0, 2], 0, 0),
+    ([(8, 8, 0), (4, 4, 1), (4, 4, 0), (6, 5, 1)], [(4, 4, 0), (8, 8, 0), (6, 5, 0), (3, 3, 1)], [1, 3], [0, 2], 0, 0),
     # bond wider than one side
     ([(1, 1, 0), (8, 8, 1)], [(8, 8, 0), (5, 7, 1), (4, 4, 0)], [1], [0], 0, 1),
 ]
