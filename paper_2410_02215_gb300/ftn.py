@@ -9,6 +9,7 @@ from __future__ import annotations
 
 import ctypes as C
 import os
+import weakref
 
 import numpy as np
 
@@ -136,7 +137,10 @@ class Context:
 
             def _free(ptr, user):
                 if ptr:
-                    torch.cuda.caching_allocator_delete(ptr)
+                    try:
+                        torch.cuda.caching_allocator_delete(ptr)
+                    except Exception:  # interpreter shutdown: torch already finalised
+                        pass
 
             a, f = ALLOC_FN(_alloc), FREE_FN(_free)
             self._keep += [a, f]
@@ -145,6 +149,7 @@ class Context:
         h = C.c_void_p()
         _check(lib().ftn_ctx_create(C.c_void_p(self.stream.cuda_stream), a, f, None, C.byref(h)))
         self.handle = h
+        self._tensors = weakref.WeakSet()  # tensors to release before the context goes
 
     def synchronize(self):
         _check(lib().ftn_ctx_synchronize(self.handle))
@@ -175,6 +180,8 @@ class Context:
 
     def close(self):
         if self.handle:
+            for t in list(self._tensors):
+                t.free()
             lib().ftn_ctx_destroy(self.handle)
             self.handle = None
 
@@ -198,6 +205,7 @@ class Tensor:
         self.ctx = ctx
         self.handle = handle
         self._keep = keep  # borrowed storage kept alive for wrapped tensors
+        ctx._tensors.add(self)
         r = C.c_int()
         d0 = (C.c_int32 * FTN_MAX_RANK)()
         d1 = (C.c_int32 * FTN_MAX_RANK)()
@@ -297,7 +305,8 @@ class Tensor:
 
     def free(self):
         if self.handle:
-            lib().ftn_tensor_free(self.handle)
+            if self.ctx.handle:  # a closed context has already released its tensors
+                lib().ftn_tensor_free(self.handle)
             self.handle = None
 
     def __del__(self):
