@@ -164,6 +164,40 @@ FTN_API ftn_status ftn_tensordot(ftn_ctx ctx, ftn_tensor A, ftn_tensor B, int n,
                          const int* axes_b, uint64_t flip_a, uint64_t flip_b, const int* out_perm,
                          ftn_prec prec, ftn_tensor* C);
 
+/* ---- tensordot without device allocation ---------------------------------- */
+
+/* The paper has no counterpart of this entry point; it exists for callers
+ * that cannot allocate device memory, directly or through the library --
+ * code running inside a stream capture that forbids allocation, plug-in
+ * hosts that hand over only pre-reserved buffers, latency-critical loops
+ * that cannot afford an allocator round trip.
+ *
+ * Same operation as ftn_tensordot (without the extra bond-parity masks) on
+ * raw device buffers: A and B are described by their legs and parity and
+ * hold their blocks in the layout above (element type `dtype`); the result
+ * (legs: free legs of A then of B, permuted by out_perm when not NULL) is
+ * written to the caller-owned device buffer `c` of at least c_capacity
+ * elements.  Every temporary (fused sector matrices, plan tables, error
+ * word) lives in one file-scope static device array of
+ * FTN_NOALLOC_SCRATCH_BYTES that every GPU loading the library keeps until
+ * the process exits; the call never calls cudaMalloc, cudaFree or any other
+ * device-allocating routine (host bookkeeping uses the C++ heap).  A
+ * contraction that needs more scratch than the array holds, or a result
+ * larger than c_capacity, is rejected with FTN_EINVAL and a message.  The
+ * first call on each device (that device current) looks up the array's
+ * device address once; make it before any stream capture.  All calls share
+ * the array and it keeps the last call's contents: calls whose work overlaps
+ * on the GPU race on it (host threads are serialised, GPU streams are not).
+ * The call synchronises `cuda_stream` once while it uploads its plan. */
+#define FTN_NOALLOC_SCRATCH_BYTES ((size_t)64 << 20)
+FTN_API ftn_status ftn_tensordot_noalloc(void* cuda_stream, int rank_a, const int32_t* d_even_a,
+                                         const int32_t* d_odd_a, const uint8_t* dual_a, int parity_a,
+                                         const void* a, int rank_b, const int32_t* d_even_b,
+                                         const int32_t* d_odd_b, const uint8_t* dual_b, int parity_b,
+                                         const void* b, ftn_dtype dtype, int n, const int* axes_a,
+                                         const int* axes_b, const int* out_perm, ftn_prec prec, void* c,
+                                         int64_t c_capacity);
+
 /* ---- bond compression (Sec. II.A symmetric QR/SVD, Sec. III) ------------- */
 
 typedef struct {
