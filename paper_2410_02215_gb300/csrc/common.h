@@ -88,9 +88,29 @@ struct GemmProb {
   // FP64 path split-K: nsplit slices of kchunk, slice s written at c_off + s*c_slab
   int32_t nsplit, kchunk;
   int64_t c_slab;
+  // tensor-core path tile order: problems sharing the same A rows (same pi
+  // and row block) form a group whose tiles run m-tile by m-tile across all
+  // its problems, so that concurrent CTAs reuse the A tile from L2.
+  // tile_begin is the group's first tile for every member.
+  int32_t grp_first, grp_count;
+  int32_t row_tiles, tn_off;
 };
 
-// Offset of the row-major multi-index of x over n legs (last leg fastest).
+// Offset of the row-major multi-index of x over n legs (last leg fastest),
+// 32-bit index arithmetic (every leg dimension and every row or column
+// index fits in 31 bits).
+__host__ __device__ inline int64_t expand_index32(int x, int n, const int32_t* dim, const int64_t* str) {
+  int64_t off = 0;
+  for (int l = n - 1; l >= 0; --l) {
+    const int d = dim[l];
+    const int q = x / d;
+    off += (int64_t)(x - q * d) * str[l];
+    x = q;
+  }
+  return off;
+}
+
+// Same with 64-bit indices.
 __host__ __device__ inline int64_t expand_index(int64_t x, int n, const int32_t* dim, const int64_t* str) {
   int64_t off = 0;
   for (int l = n - 1; l >= 0; --l) {

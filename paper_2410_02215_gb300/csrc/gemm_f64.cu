@@ -82,14 +82,14 @@ __global__ void __launch_bounds__(256) gemm_f64_kernel(const GemmProb* __restric
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
       int gn = n0 + tx + 16 * c;
-      cpart[c] = gn < p.N ? expand_index(gn, p.ncl, p.cdim, p.cstr) : 0;
+      cpart[c] = gn < p.N ? expand_index32(gn, p.ncl, p.cdim, p.cstr) : 0;
     }
     const double sg = (double)p.c_sign;
 #pragma unroll
     for (int a = 0; a < 4; ++a) {
       int gm = m0 + ty + 16 * a;
       if (gm >= p.M) continue;
-      const int64_t rpart = p.c_off + (int64_t)ks * p.c_slab + expand_index(gm, p.nrl, p.rdim, p.rstr);
+      const int64_t rpart = p.c_off + (int64_t)ks * p.c_slab + expand_index32(gm, p.nrl, p.rdim, p.rstr);
 #pragma unroll
       for (int c = 0; c < 4; ++c) {
         int gn = n0 + tx + 16 * c;

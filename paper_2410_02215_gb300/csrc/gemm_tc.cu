@@ -8,8 +8,9 @@
 //             BN x same B tiles into a STAGES-deep shared-memory ring;
 //   warp 1    MMA issuer: tcgen05.mma (M = 128, N = BN) into one of two TMEM
 //             accumulators, tcgen05.commit releases ring slots;
-//   warps 2-5 epilogue: tcgen05.ld of the accumulator (one row per thread),
-//             FP32 stores into the output block.
+//   warps 2-9 epilogue, two sets of four (one per TMEM accumulator buffer):
+//             tcgen05.ld of the accumulator (one row per thread), FP32
+//             stores into the output block.
 // Split modes (TF32X3 / BF16X3) load hi and lo planes; hi*hi goes into one
 // TMEM accumulator and hi*lo + lo*hi into a second one, summed in FP32 by the
 // epilogue.  The tensor core's accumulation rounds each partial sum, so
@@ -24,7 +25,8 @@
 namespace ftn {
 
 constexpr int TC_BM = 128;
-constexpr int TC_THREADS = 192;
+constexpr int TC_EPI_WARPS = 8;  // two sets of four, one per TMEM accumulator buffer
+constexpr int TC_THREADS = 64 + 32 * TC_EPI_WARPS;
 
 struct TcParams {
   CUtensorMap a_hi[2];
@@ -46,7 +48,7 @@ struct TcCfg {
   static constexpr int STAGE_BYTES = (A_BYTES + B_BYTES) * OPS;
   // epilogue staging: per epilogue warp a 32 x (CW + 1) FP32 tile
   static constexpr int CW = BN < 32 ? BN : 32;
-  static constexpr int EPI_BYTES = 4 * 32 * (CW + 1) * 4;
+  static constexpr int EPI_BYTES = TC_EPI_WARPS * 32 * (CW + 1) * 4;
   static constexpr int BUDGET = 227 * 1024 - 1024 - 256 - EPI_BYTES;
   static constexpr int STAGES_RAW = BUDGET / STAGE_BYTES;
   static constexpr int STAGES = STAGES_RAW > 8 ? 8 : STAGES_RAW;
@@ -70,6 +72,21 @@ __device__ __forceinline__ int tc_find_prob(const GemmProb* probs, int nprobs, i
       hi = mid - 1;
   }
   return lo;
+}
+
+// Tile t -> (problem, m0, n0) under the grouped order (see GemmProb).
+template <int BN>
+__device__ __forceinline__ const GemmProb* tc_decode(const TcParams& P, int64_t t, int& m0, int& n0) {
+  const GemmProb* g = P.probs + tc_find_prob(P.probs, P.nprobs, t);
+  const int64_t local = t - g->tile_begin;
+  const int tm = (int)(local / g->row_tiles);
+  int rem = (int)(local - (int64_t)tm * g->row_tiles);
+  const GemmProb* p = P.probs + g->grp_first;
+  for (int q = 0; q < g->grp_count; ++q, ++p)
+    if (rem < p->tn_off + p->tiles_n) break;
+  m0 = tm * TC_BM;
+  n0 = (rem - p->tn_off) * BN;
+  return p;
 }
 
 template <bool BF16, bool SPLIT, int BN>
@@ -115,10 +132,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
       uint32_t issued = 0, lastpar = 0;
       bool ok = true;
       for (int64_t t = blockIdx.x; t < P.tiles && ok; t += gridDim.x) {
-        const GemmProb& p = P.probs[tc_find_prob(P.probs, P.nprobs, t)];
-        const int64_t local = t - p.tile_begin;
-        const int m0 = (int)(local / p.tiles_n) * TC_BM;
-        const int n0 = (int)(local % p.tiles_n) * BN;
+        int m0, n0;
+        const GemmProb& p = *tc_decode<BN>(P, t, m0, n0);
         const int nk = (p.K + Cfg::KB - 1) / Cfg::KB;
         const int pi = p.pi;
         for (int kb = 0; kb < nk; ++kb) {
@@ -156,7 +171,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
       uint32_t acc_phase = 0;
       bool ok = true;
       for (int64_t t = blockIdx.x; t < P.tiles && ok; t += gridDim.x) {
-        const GemmProb& p = P.probs[tc_find_prob(P.probs, P.nprobs, t)];
+        int m0, n0;
+        const GemmProb& p = *tc_decode<BN>(P, t, m0, n0);
         const int nk = (p.K + Cfg::KB - 1) / Cfg::KB;
         if (nk == 0) continue;
         if (!mbar_wait(&tempty[acc], acc_phase ^ 1, P.err)) break;
@@ -210,28 +226,32 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
       mbar_wait(drain, 0, P.err, false);
     }
   } else {
-    // ---------------- epilogue (warps 2..5) ----------------
-    // TMEM -> registers (one row per lane) -> shared memory -> global, one
-    // 32-column chunk at a time, so that every warp store writes consecutive
-    // columns of one row.  Output addresses follow the problem's row/column
-    // leg tables (a permuted output layout costs nothing extra here).
+    // ---------------- epilogue (warps 2..9) ----------------
+    // Two sets of four warps; set s drains the tiles that used TMEM buffer s,
+    // so two tiles are written out concurrently.  Within a set, warp w reads
+    // TMEM lanes 32*(w%4)..+31 (one output row per lane).  TMEM -> registers
+    // -> shared memory -> global, one 32-column chunk at a time, so that every
+    // warp store writes 32 consecutive destination elements.  Output
+    // addresses follow the problem's row/column leg tables (a permuted output
+    // layout costs nothing extra here).
     const int q = warp & 3;
+    const int set = (warp - 2) >> 2;
     float* stg = epi + (warp - 2) * 32 * (Cfg::CW + 1);
-    int acc = 0;
-    uint32_t acc_phase = 0;
+    uint32_t j = 0;  // tiles with K > 0 seen so far (all sets count them)
     for (int64_t t = blockIdx.x; t < P.tiles; t += gridDim.x) {
-      const GemmProb& p = P.probs[tc_find_prob(P.probs, P.nprobs, t)];
-      const int64_t local = t - p.tile_begin;
-      const int m0 = (int)(local / p.tiles_n) * TC_BM;
-      const int n0 = (int)(local % p.tiles_n) * BN;
+      int m0, n0;
+      const GemmProb& p = *tc_decode<BN>(P, t, m0, n0);
       const int nk = (p.K + Cfg::KB - 1) / Cfg::KB;
+      const int acc = (int)(j & 1);
+      if (nk > 0) ++j;
+      if (nk > 0 ? acc != set : set != 0) continue;
       const int row = m0 + 32 * q + lane;
-      const int64_t rpart = row < p.M ? p.c_off + expand_index(row, p.nrl, p.rdim, p.rstr) : 0;
+      const int64_t rpart = row < p.M ? p.c_off + expand_index32(row, p.nrl, p.rdim, p.rstr) : 0;
       const int ncols = p.N - n0 < BN ? p.N - n0 : BN;
       const int nrows = p.M - (m0 + 32 * q) < 32 ? p.M - (m0 + 32 * q) : 32;
       const float sg = (float)p.c_sign;
       if (nk > 0) {
-        if (!mbar_wait(&tfull[acc], acc_phase, P.err)) break;
+        if (!mbar_wait(&tfull[acc], ((j - 1) >> 1) & 1, P.err)) break;
         tc_fence_after();
       }
       const uint32_t taddr = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(acc * Cfg::ACC_W);
@@ -264,7 +284,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
         __syncwarp();
         const int col = c + lane;
         const bool okc = lane < Cfg::CW && col < ncols;
-        const int64_t cpart = okc ? expand_index(n0 + col, p.ncl, p.cdim, p.cstr) : 0;
+        const int64_t cpart = okc ? expand_index32(n0 + col, p.ncl, p.cdim, p.cstr) : 0;
         if (p.epi_rows) {
           // destination contiguous along rows: lane -> row, loop over columns
 #pragma unroll 4
@@ -285,8 +305,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
         tc_fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive(&tempty[acc]);
-        acc ^= 1;
-        if (acc == 0) acc_phase ^= 1;
       }
     }
   }

@@ -333,9 +333,37 @@ static ftn_status build_plan(ftn_ctx ctx, const ftn_tensor_s* A, const ftn_tenso
       g.tiles_m = (g.M + 63) / 64;
       g.tiles_n = (g.N + 63) / 64;
     }
-    g.tile_begin = P->gemm_tiles;
-    P->gemm_tiles += (int64_t)g.tiles_m * g.tiles_n;
     P->probs.push_back(g);
+  }
+  if (tc) {
+    // group problems by (pi, row block); inside a group the tiles run
+    // m-tile by m-tile across all member problems (A tile reuse in L2)
+    std::stable_sort(P->probs.begin(), P->probs.end(), [](const GemmProb& x, const GemmProb& y) {
+      if (x.pi != y.pi) return x.pi < y.pi;
+      return x.a_row0 < y.a_row0;
+    });
+    for (size_t i = 0; i < P->probs.size();) {
+      size_t j = i;
+      int32_t row_tiles = 0;
+      while (j < P->probs.size() && P->probs[j].pi == P->probs[i].pi && P->probs[j].a_row0 == P->probs[i].a_row0) {
+        P->probs[j].tn_off = row_tiles;
+        row_tiles += P->probs[j].tiles_n;
+        ++j;
+      }
+      for (size_t q = i; q < j; ++q) {
+        P->probs[q].grp_first = (int32_t)i;
+        P->probs[q].grp_count = (int32_t)(j - i);
+        P->probs[q].row_tiles = row_tiles;
+        P->probs[q].tile_begin = P->gemm_tiles;
+      }
+      P->gemm_tiles += (int64_t)P->probs[i].tiles_m * row_tiles;
+      i = j;
+    }
+  } else {
+    for (GemmProb& g : P->probs) {
+      g.tile_begin = P->gemm_tiles;
+      P->gemm_tiles += (int64_t)g.tiles_m * g.tiles_n;
+    }
   }
   // ---- the separate sign-permute of the result, when not fused ----
   if (!fuse) {
