@@ -94,6 +94,10 @@ struct GemmProb {
   // tile_begin is the group's first tile for every member.
   int32_t grp_first, grp_count;
   int32_t row_tiles, tn_off;
+  // 1: groups of 4 consecutive elements along the epilogue's write direction
+  // are contiguous and 16-byte aligned in the destination (vector stores)
+  int32_t vec4;
+  int32_t pad2_;
 };
 
 // Offset of the row-major multi-index of x over n legs (last leg fastest),

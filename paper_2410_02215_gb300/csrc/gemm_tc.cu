@@ -285,7 +285,43 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
         const int col = c + lane;
         const bool okc = lane < Cfg::CW && col < ncols;
         const int64_t cpart = okc ? expand_index32(n0 + col, p.ncl, p.cdim, p.cstr) : 0;
-        if (p.epi_rows) {
+        if (p.vec4) {
+          // 16-byte stores: quads of consecutive elements along the contiguous direction
+          const int sub = lane & 7, grp = lane >> 3;
+          if (p.epi_rows) {
+            // lane -> rows 4*sub..+3 of column cc = 4*it + grp
+            const int64_t rq = __shfl_sync(0xffffffffu, rpart, 4 * sub);
+#pragma unroll
+            for (int it = 0; it < Cfg::CW / 4; ++it) {
+              const int cc = 4 * it + grp;
+              const int64_t cp = __shfl_sync(0xffffffffu, cpart, cc);
+              if (4 * sub < nrows && c + cc < ncols) {
+                float4 w;
+                w.x = sg * stg[(4 * sub + 0) * (Cfg::CW + 1) + cc];
+                w.y = sg * stg[(4 * sub + 1) * (Cfg::CW + 1) + cc];
+                w.z = sg * stg[(4 * sub + 2) * (Cfg::CW + 1) + cc];
+                w.w = sg * stg[(4 * sub + 3) * (Cfg::CW + 1) + cc];
+                *reinterpret_cast<float4*>(P.C + rq + cp) = w;
+              }
+            }
+          } else {
+            // lane -> columns 4*sub..+3 (sub < CW/4) of row rr = 4*it + grp
+            const int64_t cq = __shfl_sync(0xffffffffu, cpart, (4 * sub) & 31);
+#pragma unroll
+            for (int it = 0; it < 8; ++it) {
+              const int rr = 4 * it + grp;
+              const int64_t rp = __shfl_sync(0xffffffffu, rpart, rr);
+              if (4 * sub < Cfg::CW && rr < nrows && c + 4 * sub < ncols) {
+                float4 w;
+                w.x = sg * stg[rr * (Cfg::CW + 1) + 4 * sub + 0];
+                w.y = sg * stg[rr * (Cfg::CW + 1) + 4 * sub + 1];
+                w.z = sg * stg[rr * (Cfg::CW + 1) + 4 * sub + 2];
+                w.w = sg * stg[rr * (Cfg::CW + 1) + 4 * sub + 3];
+                *reinterpret_cast<float4*>(P.C + rp + cq) = w;
+              }
+            }
+          }
+        } else if (p.epi_rows) {
           // destination contiguous along rows: lane -> row, loop over columns
 #pragma unroll 4
           for (int cc = 0; cc < Cfg::CW; ++cc) {

@@ -186,28 +186,16 @@ struct StagedCfg {
   static constexpr int STAGE_ELEMS = TE + PERM_MAX_ROWS * V;
   static constexpr int BYTES = PERM_STAGES * STAGE_ELEMS * (int)sizeof(Tin) + PERM_STAGES * PERM_MAX_ROWS * 4 +
                                PERM_STAGES * MAXTI * 4 + PERM_STAGES * (int)sizeof(StageMeta) + 2 * PERM_STAGES * 8 +
-                               128;
+                               (int)sizeof(PermJob) + 128;
 };
 
+// Issue the bulk copies of tile t (producer warp; `j` is the tile's job,
+// cached in shared memory by the caller).
 template <typename Tin>
-__device__ __forceinline__ void staged_issue(const PermJob* __restrict__ jobs, int njobs, int64_t t,
-                                             const Tin* __restrict__ src, Tin* buf, int32_t* rowD, int32_t* colD,
-                                             StageMeta* meta, uint64_t* bar, int lane) {
+__device__ __forceinline__ void staged_issue(const PermJob* j, int64_t t, const Tin* __restrict__ src, Tin* buf,
+                                             int32_t* rowD, int32_t* colD, StageMeta* meta, uint64_t* bar,
+                                             int lane) {
   using Cfg = StagedCfg<Tin>;
-  int jb = 0;
-  if (lane == 0) {
-    int lo = 0, hi = njobs - 1;
-    while (lo < hi) {
-      int mid = (lo + hi + 1) >> 1;
-      if (jobs[mid].tile_begin <= t)
-        lo = mid;
-      else
-        hi = mid - 1;
-    }
-    jb = lo;
-  }
-  jb = __shfl_sync(0xffffffffu, jb, 0);
-  const PermJob* j = jobs + jb;
   const int nI = j->nI, nO = j->nO;
   const int64_t local = t - j->tile_begin;
   const int64_t per_b = (int64_t)j->tiles_i * j->tiles_o;
@@ -226,26 +214,34 @@ __device__ __forceinline__ void staged_issue(const PermJob* __restrict__ jobs, i
     }
   }
   const int stride = j->ti + Cfg::V;
+  int64_t rsrc[PERM_MAX_ROWS / 32];
   uint32_t mine = 0;
-  for (int r = lane; r < nrows; r += 32) {
+#pragma unroll
+  for (int u = 0; u < PERM_MAX_ROWS / 32; ++u) {
+    const int r = lane + 32 * u;
+    rsrc[u] = 0;
+    if (r >= nrows) continue;
     int x = o0 + r;
     int64_t rs = 0;
     int32_t rd = 0;
     for (int q = nI + nO - 1; q >= nI; --q) {
-      const int idx = x % j->dim[q];
-      x /= j->dim[q];
+      const int d = j->dim[q];
+      const int qq = x / d, idx = x - qq * d;
+      x = qq;
       rs += (int64_t)idx * j->sstr[q];
       rd += idx * (int32_t)j->dstr[q];
     }
     rowD[r] = rd;
+    rsrc[u] = rs;
     mine += (uint32_t)(ncols * sizeof(Tin));
   }
   for (int c = lane; c < ncols; c += 32) {
     int x = i0 + c;
     int32_t dd = 0;
     for (int q = nI - 1; q >= 0; --q) {
-      const int idx = x % j->dim[q];
-      x /= j->dim[q];
+      const int d = j->dim[q];
+      const int qq = x / d, idx = x - qq * d;
+      x = qq;
       dd += idx * (int32_t)j->dstr[q];
     }
     colD[c] = dd;
@@ -261,15 +257,10 @@ __device__ __forceinline__ void staged_issue(const PermJob* __restrict__ jobs, i
   // order this warp's earlier generic reads of the stage before the async writes
   fence_proxy_async_smem();
   mbar_expect_tx(bar, mine);
-  for (int r = lane; r < nrows; r += 32) {
-    int x = o0 + r;
-    int64_t rs = 0;
-    for (int q = nI + nO - 1; q >= nI; --q) {
-      const int idx = x % j->dim[q];
-      x /= j->dim[q];
-      rs += (int64_t)idx * j->sstr[q];
-    }
-    bulk_g2s(buf + r * stride, src + bS + rs + i0, (uint32_t)(ncols * sizeof(Tin)), bar);
+#pragma unroll
+  for (int u = 0; u < PERM_MAX_ROWS / 32; ++u) {
+    const int r = lane + 32 * u;
+    if (r < nrows) bulk_g2s(buf + r * stride, src + bS + rsrc[u] + i0, (uint32_t)(ncols * sizeof(Tin)), bar);
   }
 }
 
@@ -288,6 +279,7 @@ __global__ void __launch_bounds__(SPT) perm_staged_kernel(const PermJob* __restr
   StageMeta* meta = reinterpret_cast<StageMeta*>(colD + PERM_STAGES * Cfg::MAXTI);
   uint64_t* full = reinterpret_cast<uint64_t*>(meta + PERM_STAGES);
   uint64_t* empty = full + PERM_STAGES;
+  PermJob* sjob = reinterpret_cast<PermJob*>(empty + PERM_STAGES);  // producer's copy of the current job
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   constexpr int NCW = PT / 32;  // consumer warps
   if (tid == 0) {
@@ -301,17 +293,43 @@ __global__ void __launch_bounds__(SPT) perm_staged_kernel(const PermJob* __restr
   const int64_t stride_t = gridDim.x;
   if (warp == NCW) {
     // ---------------- producer warp ----------------
+    // this CTA's tiles increase, so the job index only moves forward
+    int cur = -1;
     int64_t k = 0;
     for (;; ++k) {
       const int64_t t = blockIdx.x + k * stride_t;
       if (t >= tiles) break;
+      int nj = cur < 0 ? 0 : cur;
+      if (lane == 0) {
+        if (cur < 0) {
+          int lo = 0, hi = njobs - 1;
+          while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (jobs[mid].tile_begin <= t)
+              lo = mid;
+            else
+              hi = mid - 1;
+          }
+          nj = lo;
+        } else {
+          while (nj + 1 < njobs && jobs[nj + 1].tile_begin <= t) ++nj;
+        }
+      }
+      nj = __shfl_sync(0xffffffffu, nj, 0);
+      if (nj != cur) {
+        const uint64_t* from = reinterpret_cast<const uint64_t*>(jobs + nj);
+        uint64_t* to = reinterpret_cast<uint64_t*>(sjob);
+        for (int w = lane; w < (int)(sizeof(PermJob) / 8); w += 32) to[w] = from[w];
+        __syncwarp();
+        cur = nj;
+      }
       const int s = (int)(k % PERM_STAGES);
       const uint32_t par = (uint32_t)((k / PERM_STAGES) & 1);
       bool ok = true;
       if (lane == 0) ok = mbar_wait(&empty[s], par ^ 1, err);
       if (!__shfl_sync(0xffffffffu, ok ? 1 : 0, 0)) break;
-      staged_issue<Tin>(jobs, njobs, t, src, buf + s * Cfg::STAGE_ELEMS, rowD + s * PERM_MAX_ROWS,
-                        colD + s * Cfg::MAXTI, meta + s, &full[s], lane);
+      staged_issue<Tin>(sjob, t, src, buf + s * Cfg::STAGE_ELEMS, rowD + s * PERM_MAX_ROWS, colD + s * Cfg::MAXTI,
+                        meta + s, &full[s], lane);
     }
     // wait for this CTA's copies still in flight (all consumed on a normal exit)
     if (lane == 0) {

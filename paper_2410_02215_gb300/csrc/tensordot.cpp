@@ -335,6 +335,21 @@ static ftn_status build_plan(ftn_ctx ctx, const ftn_tensor_s* A, const ftn_tenso
     }
     P->probs.push_back(g);
   }
+  // vector stores in the epilogue: the fastest leg along the write direction
+  // has stride 1 and a dimension divisible by 4; every other stride and the
+  // block offset are multiples of 4 elements
+  for (GemmProb& g : P->probs) {
+    bool ok = g.c_off % 4 == 0;
+    const int nf = g.epi_rows ? g.nrl : g.ncl;
+    const int32_t* fd = g.epi_rows ? g.rdim : g.cdim;
+    const int64_t* fs = g.epi_rows ? g.rstr : g.cstr;
+    ok = ok && nf > 0 && fs[nf - 1] == 1 && fd[nf - 1] % 4 == 0;
+    for (int l = 0; l < g.nrl; ++l)
+      if (!(g.epi_rows && l == nf - 1)) ok = ok && g.rstr[l] % 4 == 0;
+    for (int l = 0; l < g.ncl; ++l)
+      if (!(!g.epi_rows && l == nf - 1)) ok = ok && g.cstr[l] % 4 == 0;
+    g.vec4 = ok ? 1 : 0;
+  }
   if (tc) {
     // group problems by (pi, row block); inside a group the tiles run
     // m-tile by m-tile across all member problems (A tile reuse in L2)
