@@ -47,7 +47,7 @@ struct PermJob {
   int32_t store_fast_i;  // destination contiguous along the I index
   int32_t ti, tr;        // tile extents (I, O)
   int32_t bulk_ok;       // rows are 16-byte aligned with 16-byte multiple sizes
-  int32_t pad_;
+  int32_t vec4;          // quads along the store direction are contiguous and 4-element aligned
   int32_t dim[MAXR];     // I legs (source order), then O legs, then B legs
   int64_t sstr[MAXR];    // source strides
   int64_t dstr[MAXR];    // destination strides

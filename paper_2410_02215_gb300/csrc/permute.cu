@@ -50,7 +50,42 @@ __device__ __forceinline__ void put(void* dst0, void* dst1, int64_t idx, Tin v) 
   }
 }
 
-constexpr int PT = 256;              // threads per CTA
+constexpr int PT = 256;              // threads per CTA (register-staged kernel)
+
+// Four consecutive outputs at a 4-element aligned index (vector stores).
+template <typename Tin, int MODE>
+__device__ __forceinline__ void put4(void* dst0, void* dst1, int64_t idx, Tin a, Tin b, Tin c, Tin d) {
+  if constexpr (MODE == PERM_SAME && sizeof(Tin) == 8) {
+    double2* p = reinterpret_cast<double2*>(reinterpret_cast<double*>(dst0) + idx);
+    p[0] = make_double2((double)a, (double)b);
+    p[1] = make_double2((double)c, (double)d);
+  } else if constexpr (MODE == PERM_SAME) {
+    *reinterpret_cast<float4*>(reinterpret_cast<float*>(dst0) + idx) = make_float4(a, b, c, d);
+  } else if constexpr (MODE == PERM_TF32) {
+    *reinterpret_cast<float4*>(reinterpret_cast<float*>(dst0) + idx) =
+        make_float4(tf32_rna(a), tf32_rna(b), tf32_rna(c), tf32_rna(d));
+  } else if constexpr (MODE == PERM_TF32X2) {
+    const float ha = tf32_rna(a), hb = tf32_rna(b), hc = tf32_rna(c), hd = tf32_rna(d);
+    *reinterpret_cast<float4*>(reinterpret_cast<float*>(dst0) + idx) = make_float4(ha, hb, hc, hd);
+    *reinterpret_cast<float4*>(reinterpret_cast<float*>(dst1) + idx) =
+        make_float4(tf32_rna(a - ha), tf32_rna(b - hb), tf32_rna(c - hc), tf32_rna(d - hd));
+  } else {
+    const __nv_bfloat162 h01 = __floats2bfloat162_rn(a, b), h23 = __floats2bfloat162_rn(c, d);
+    uint2 hv;
+    hv.x = *reinterpret_cast<const uint32_t*>(&h01);
+    hv.y = *reinterpret_cast<const uint32_t*>(&h23);
+    *reinterpret_cast<uint2*>(reinterpret_cast<__nv_bfloat16*>(dst0) + idx) = hv;
+    if constexpr (MODE == PERM_BF16X2) {
+      const float2 f01 = __bfloat1622float2(h01), f23 = __bfloat1622float2(h23);
+      const __nv_bfloat162 l01 = __floats2bfloat162_rn(a - f01.x, b - f01.y);
+      const __nv_bfloat162 l23 = __floats2bfloat162_rn(c - f23.x, d - f23.y);
+      uint2 lv;
+      lv.x = *reinterpret_cast<const uint32_t*>(&l01);
+      lv.y = *reinterpret_cast<const uint32_t*>(&l23);
+      *reinterpret_cast<uint2*>(reinterpret_cast<__nv_bfloat16*>(dst1) + idx) = lv;
+    }
+  }
+}
 constexpr int PR = PERM_TO / (PT / 32);  // rows per thread in a phase
 
 template <typename Tin, int MODE>
@@ -175,7 +210,7 @@ struct StageMeta {
   int64_t baseD;
   int32_t nrows, ncols;
   int32_t ti, fast_i;
-  int32_t sign, failed;
+  int32_t sign, vec4;
 };
 
 template <typename Tin>
@@ -253,6 +288,7 @@ __device__ __forceinline__ void staged_issue(const PermJob* j, int64_t t, const 
     meta->ti = j->ti;
     meta->fast_i = j->store_fast_i;
     meta->sign = j->sign;
+    meta->vec4 = j->vec4;
   }
   // order this warp's earlier generic reads of the stage before the async writes
   fence_proxy_async_smem();
@@ -264,7 +300,8 @@ __device__ __forceinline__ void staged_issue(const PermJob* j, int64_t t, const 
   }
 }
 
-constexpr int SPT = PT + 32;  // eight consumer warps + one producer warp
+constexpr int SPW = 16;             // consumer warps of the staged kernel
+constexpr int SPT = 32 * SPW + 32;  // consumer warps + one producer warp
 
 template <typename Tin, int MODE>
 __global__ void __launch_bounds__(SPT) perm_staged_kernel(const PermJob* __restrict__ jobs, int njobs, int64_t tiles,
@@ -281,7 +318,7 @@ __global__ void __launch_bounds__(SPT) perm_staged_kernel(const PermJob* __restr
   uint64_t* empty = full + PERM_STAGES;
   PermJob* sjob = reinterpret_cast<PermJob*>(empty + PERM_STAGES);  // producer's copy of the current job
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  constexpr int NCW = PT / 32;  // consumer warps
+  constexpr int NCW = SPW;  // consumer warps
   if (tid == 0) {
     for (int s = 0; s < PERM_STAGES; ++s) {
       mbar_init(&full[s], 32);
@@ -351,7 +388,26 @@ __global__ void __launch_bounds__(SPT) perm_staged_kernel(const PermJob* __restr
     const int32_t* cd = colD + s * Cfg::MAXTI;
     const int stride = m.ti + Cfg::V;
     const Tin sgn = (Tin)m.sign;
-    if (m.fast_i) {
+    if (m.vec4 && m.fast_i) {
+      // quads of consecutive I elements, contiguous in the destination
+      for (int r = warp; r < m.nrows; r += NCW) {
+        const int64_t base = m.baseD + rd[r];
+        for (int c4 = 4 * lane; c4 < m.ncols; c4 += 128) {
+          const Tin* x = tb + r * stride + c4;
+          put4<Tin, MODE>(dst0, dst1, base + cd[c4], sgn * x[0], sgn * x[1], sgn * x[2], sgn * x[3]);
+        }
+      }
+    } else if (m.vec4) {
+      // quads of consecutive O rows, contiguous in the destination
+      for (int c = warp; c < m.ncols; c += NCW) {
+        const int32_t cc = cd[c];
+        for (int r4 = 4 * lane; r4 < m.nrows; r4 += 128) {
+          const Tin* x = tb + r4 * stride + c;
+          put4<Tin, MODE>(dst0, dst1, m.baseD + rd[r4] + cc, sgn * x[0], sgn * x[stride], sgn * x[2 * stride],
+                          sgn * x[3 * stride]);
+        }
+      }
+    } else if (m.fast_i) {
       for (int r = warp; r < m.nrows; r += NCW) {
         const int64_t base = m.baseD + rd[r];
         for (int c = lane; c < m.ncols; c += 32) put<Tin, MODE>(dst0, dst1, base + cd[c], sgn * tb[r * stride + c]);
@@ -391,7 +447,7 @@ static cudaError_t go_staged(ftn_ctx ctx, const PermJob* d_jobs, int njobs, int6
     attr = true;
   }
   int64_t grid = tiles;
-  int64_t cap = (int64_t)ctx->num_sms * 3;
+  int64_t cap = (int64_t)ctx->num_sms * 2;
   if (grid > cap) grid = cap;
   perm_staged_kernel<Tin, MODE><<<(unsigned)grid, SPT, Cfg::BYTES, ctx->stream>>>(d_jobs, njobs, tiles,
                                                                                  (const Tin*)src, dst0, dst1,

@@ -209,6 +209,9 @@ void add_perm_job(std::vector<PermJob>& jobs, int64_t& tiles, int rank, const in
 int finalize_perm_jobs(std::vector<PermJob>& jobs, size_t es, int64_t* tiles, bool allow_staged) {
   const int64_t V = 16 / (int64_t)es;  // elements per 16 bytes
   bool staged = allow_staged && !jobs.empty();
+  int64_t total = 0;
+  for (const PermJob& j : jobs) total += (int64_t)j.PI * j.PO * j.PB;
+  if (total < 65536) staged = false;  // tiny tensors: launch latency dominates, skip the TMA round trip
   for (PermJob& j : jobs) {
     bool ok = (j.PI % V == 0) && (j.src_off % V == 0);
     for (int q = j.nI; q < j.nI + j.nO + j.nB; ++q) ok = ok && (j.sstr[q] % V == 0);
@@ -218,11 +221,24 @@ int finalize_perm_jobs(std::vector<PermJob>& jobs, size_t es, int64_t* tiles, bo
   const int64_t te = PERM_TILE_BYTES / (int64_t)es;
   int64_t t = 0;
   for (PermJob& j : jobs) {
+    j.vec4 = 0;
+    if (staged) {
+      // vector stores: the fastest destination leg along the store direction
+      // has stride 1 and a dimension divisible by 4, every other destination
+      // stride and the offset are multiples of 4 elements
+      const int nl = j.nI + j.nO + j.nB;
+      const int fast = j.store_fast_i ? j.nI - 1 : j.nI + j.nO - 1;
+      bool v = fast >= (j.store_fast_i ? 0 : j.nI) && j.dst_off % 4 == 0 && j.dstr[fast] == 1 && j.dim[fast] % 4 == 0;
+      for (int q = 0; q < nl; ++q)
+        if (q != fast) v = v && j.dstr[q] % 4 == 0;
+      j.vec4 = v ? 1 : 0;
+    }
     if (staged) {
       int64_t ti = std::min<int64_t>(j.PI, te / 8);
       ti = (ti + V - 1) / V * V;
       int64_t tr = std::min<int64_t>(std::max<int64_t>(te / ti, 1), PERM_MAX_ROWS);
       tr = std::min<int64_t>(tr, j.PO);
+      if (j.vec4 && !j.store_fast_i) tr = tr / 4 * 4;  // whole quads of rows (PO is a multiple of 4)
       j.ti = (int32_t)ti;
       j.tr = (int32_t)tr;
     } else {
