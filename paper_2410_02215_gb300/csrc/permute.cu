@@ -221,7 +221,7 @@ struct StagedCfg {
   static constexpr int STAGE_ELEMS = TE + PERM_MAX_ROWS * V;
   static constexpr int BYTES = PERM_STAGES * STAGE_ELEMS * (int)sizeof(Tin) + PERM_STAGES * PERM_MAX_ROWS * 4 +
                                PERM_STAGES * MAXTI * 4 + PERM_STAGES * (int)sizeof(StageMeta) + 2 * PERM_STAGES * 8 +
-                               (int)sizeof(PermJob) + 128;
+                               2 * (int)sizeof(PermJob) + 128;
 };
 
 // Issue the bulk copies of tile t (producer warp; `j` is the tile's job,
@@ -300,8 +300,9 @@ __device__ __forceinline__ void staged_issue(const PermJob* j, int64_t t, const 
   }
 }
 
-constexpr int SPW = 16;             // consumer warps of the staged kernel
-constexpr int SPT = 32 * SPW + 32;  // consumer warps + one producer warp
+constexpr int SPW = 8;                    // consumer warps of the staged kernel
+constexpr int SPP = 2;                    // producer warps (alternate tiles)
+constexpr int SPT = 32 * (SPW + SPP);
 
 template <typename Tin, int MODE>
 __global__ void __launch_bounds__(SPT) perm_staged_kernel(const PermJob* __restrict__ jobs, int njobs, int64_t tiles,
@@ -316,7 +317,7 @@ __global__ void __launch_bounds__(SPT) perm_staged_kernel(const PermJob* __restr
   StageMeta* meta = reinterpret_cast<StageMeta*>(colD + PERM_STAGES * Cfg::MAXTI);
   uint64_t* full = reinterpret_cast<uint64_t*>(meta + PERM_STAGES);
   uint64_t* empty = full + PERM_STAGES;
-  PermJob* sjob = reinterpret_cast<PermJob*>(empty + PERM_STAGES);  // producer's copy of the current job
+  PermJob* sjob_all = reinterpret_cast<PermJob*>(empty + PERM_STAGES);  // each producer's copy of its job
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   constexpr int NCW = SPW;  // consumer warps
   if (tid == 0) {
@@ -328,12 +329,15 @@ __global__ void __launch_bounds__(SPT) perm_staged_kernel(const PermJob* __restr
   }
   __syncthreads();
   const int64_t stride_t = gridDim.x;
-  if (warp == NCW) {
-    // ---------------- producer warp ----------------
+  if (warp >= NCW) {
+    // ---------------- producer warps (tiles k = p, p + SPP, ...) ----------------
     // this CTA's tiles increase, so the job index only moves forward
+    const int pw = warp - NCW;
+    PermJob* sjob = sjob_all + pw;
     int cur = -1;
-    int64_t k = 0;
-    for (;; ++k) {
+    bool failed = false;
+    int64_t k = pw;
+    for (;; k += SPP) {
       const int64_t t = blockIdx.x + k * stride_t;
       if (t >= tiles) break;
       int nj = cur < 0 ? 0 : cur;
@@ -364,13 +368,17 @@ __global__ void __launch_bounds__(SPT) perm_staged_kernel(const PermJob* __restr
       const uint32_t par = (uint32_t)((k / PERM_STAGES) & 1);
       bool ok = true;
       if (lane == 0) ok = mbar_wait(&empty[s], par ^ 1, err);
-      if (!__shfl_sync(0xffffffffu, ok ? 1 : 0, 0)) break;
+      if (!__shfl_sync(0xffffffffu, ok ? 1 : 0, 0)) {
+        failed = true;
+        break;
+      }
       staged_issue<Tin>(sjob, t, src, buf + s * Cfg::STAGE_ELEMS, rowD + s * PERM_MAX_ROWS, colD + s * Cfg::MAXTI,
                         meta + s, &full[s], lane);
     }
-    // wait for this CTA's copies still in flight (all consumed on a normal exit)
-    if (lane == 0) {
-      for (int64_t q = (k >= PERM_STAGES ? k - PERM_STAGES : 0); q < k; ++q)
+    // after an early exit, wait for this producer's copies still in flight (on
+    // a normal exit the consumers wait for every issued tile themselves)
+    if (failed && lane == 0) {
+      for (int64_t q = k - SPP; q >= 0 && q >= k - PERM_STAGES - SPP; q -= SPP)
         mbar_wait(&full[q % PERM_STAGES], (uint32_t)((q / PERM_STAGES) & 1), err, false);
     }
     return;
@@ -395,16 +403,6 @@ __global__ void __launch_bounds__(SPT) perm_staged_kernel(const PermJob* __restr
         for (int c4 = 4 * lane; c4 < m.ncols; c4 += 128) {
           const Tin* x = tb + r * stride + c4;
           put4<Tin, MODE>(dst0, dst1, base + cd[c4], sgn * x[0], sgn * x[1], sgn * x[2], sgn * x[3]);
-        }
-      }
-    } else if (m.vec4) {
-      // quads of consecutive O rows, contiguous in the destination
-      for (int c = warp; c < m.ncols; c += NCW) {
-        const int32_t cc = cd[c];
-        for (int r4 = 4 * lane; r4 < m.nrows; r4 += 128) {
-          const Tin* x = tb + r4 * stride + c;
-          put4<Tin, MODE>(dst0, dst1, m.baseD + rd[r4] + cc, sgn * x[0], sgn * x[stride], sgn * x[2 * stride],
-                          sgn * x[3 * stride]);
         }
       }
     } else if (m.fast_i) {
@@ -447,7 +445,7 @@ static cudaError_t go_staged(ftn_ctx ctx, const PermJob* d_jobs, int njobs, int6
     attr = true;
   }
   int64_t grid = tiles;
-  int64_t cap = (int64_t)ctx->num_sms * 2;
+  int64_t cap = (int64_t)ctx->num_sms * 3;
   if (grid > cap) grid = cap;
   perm_staged_kernel<Tin, MODE><<<(unsigned)grid, SPT, Cfg::BYTES, ctx->stream>>>(d_jobs, njobs, tiles,
                                                                                  (const Tin*)src, dst0, dst1,

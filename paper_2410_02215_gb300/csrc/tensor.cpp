@@ -227,8 +227,9 @@ int finalize_perm_jobs(std::vector<PermJob>& jobs, size_t es, int64_t* tiles, bo
       // has stride 1 and a dimension divisible by 4, every other destination
       // stride and the offset are multiples of 4 elements
       const int nl = j.nI + j.nO + j.nB;
-      const int fast = j.store_fast_i ? j.nI - 1 : j.nI + j.nO - 1;
-      bool v = fast >= (j.store_fast_i ? 0 : j.nI) && j.dst_off % 4 == 0 && j.dstr[fast] == 1 && j.dim[fast] % 4 == 0;
+      // (only along I: quads of O rows would read shared memory down a column)
+      const int fast = j.nI - 1;
+      bool v = j.store_fast_i && fast >= 0 && j.dst_off % 4 == 0 && j.dstr[fast] == 1 && j.dim[fast] % 4 == 0;
       for (int q = 0; q < nl; ++q)
         if (q != fast) v = v && j.dstr[q] % 4 == 0;
       j.vec4 = v ? 1 : 0;
@@ -238,7 +239,6 @@ int finalize_perm_jobs(std::vector<PermJob>& jobs, size_t es, int64_t* tiles, bo
       ti = (ti + V - 1) / V * V;
       int64_t tr = std::min<int64_t>(std::max<int64_t>(te / ti, 1), PERM_MAX_ROWS);
       tr = std::min<int64_t>(tr, j.PO);
-      if (j.vec4 && !j.store_fast_i) tr = tr / 4 * 4;  // whole quads of rows (PO is a multiple of 4)
       j.ti = (int32_t)ti;
       j.tr = (int32_t)tr;
     } else {
