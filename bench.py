@@ -299,18 +299,19 @@ def accuracy(F, ctx, prec):
 
 
 def traffic_for(label):
-    """DRAM bytes per launch from a committed ncu summary, when it was taken
-    on the current kernel sources (else None)."""
-    p = os.path.join(ROOT, "profiles", "traffic.json")
+    """DRAM bytes per launch from a committed ncu summary (profiles/traffic.txt),
+    when it was taken on the current kernel sources (else None)."""
+    p = os.path.join(ROOT, "profiles", "traffic.txt")
     if not os.path.exists(p):
         return None
     try:
-        d = json.load(open(p))
         from paper_2410_02215_gb300 import build as B
 
-        ent = d.get(label)
-        if ent and ent.get("src_digest") == B._digest():
-            return float(ent["dram_bytes_per_launch"])
+        dig = B.kernel_digest()
+        for line in open(p):
+            parts = line.split()
+            if len(parts) >= 3 and not line.startswith("#") and parts[0] == label and parts[1] == dig:
+                return float(parts[2])
     except Exception:
         return None
     return None

@@ -49,6 +49,21 @@ def _digest(extra=()):
     return h.hexdigest()
 
 
+def kernel_digest() -> str:
+    """Digest of the kernel and runtime sources alone (independent of the
+    machine), used to tell whether a stored profile still describes them."""
+    h = hashlib.sha256()
+    for f in sorted(os.listdir(CSRC)):
+        p = os.path.join(CSRC, f)
+        if os.path.isfile(p):
+            h.update(f.encode())
+            with open(p, "rb") as fh:
+                h.update(fh.read())
+    with open(os.path.join(INCLUDE, "ftn.h"), "rb") as fh:
+        h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
 def build(force: bool = False, verbose: bool = False, extra=()) -> str:
     os.makedirs(OUT, exist_ok=True)
     stamp = os.path.join(OUT, "stamp")
