@@ -11,7 +11,10 @@ fused sector-matrix layout + one grouped sector GEMM + the output
 sign-permute, all in libftn's CUDA kernels.
 
 Metric: sector-GEMM TFLOP/s (the flops of the Z2-sector GEMMs, 2*M*N*K per
-block pair, over the time of the whole step).  The primary arithmetic is
+block pair, over the time of the whole step).  The second half of the metric,
+fPEPS energy evaluations per second, is reported under "energy" (FP64 and
+mixed precision, with their errors against the oracle) on a compressed
+square-lattice Hubbard fPEPS (see ENERGY_WORKLOAD).  The primary arithmetic is
 TF32x3 (FP32-accurate split products on the tcgen05 tensor cores); the
 plain-FP64 GPU path and the other precisions are reported beside it with
 their error against the FP64 CPU oracle.
@@ -376,6 +379,48 @@ def e2e_run(F, ctx, torch, cases, prec, steps, flops_step):
             "d2h_bytes_per_step": int(d2h), "ms_per_step": ms / steps}
 
 
+ENERGY_WORKLOAD = ("Hubbard fPEPS energy <H>/<Psi|Psi> on a 4x4 open square lattice, D=4 (2+2), phys 4 (2+2), "
+                   "t=1, U=8, N(0,1) site tensors (seed 1), row-sweep double-layer tree, late compression chi=32: "
+                   "24 hopping + 16 on-site terms + the norm = 41 contractions per evaluation")
+
+
+def energy_bench(F, ctx, evals, with_oracle):
+    """fPEPS energy evaluations per second, FP64 and mixed (TF32x3 GEMMs with
+    FP64 compression), and their errors."""
+    from paper_2410_02215_gb300 import peps
+
+    n, edges = W.square_lattice(4, 4)
+    lay = W.peps_layout(n, edges, (2, 2), (2, 2))
+    blocks = W.random_peps(lay, 1)
+    st = W.site_sweep_tree(list(range(n)))
+    tf = lambda ops: W.double_layer_tree(n, st, ops)  # noqa: E731
+    out = {"workload": ENERGY_WORKLOAD}
+    res = {}
+    for prec, dt in (("f64", F.F64), ("tf32x3", F.F32)):
+        kets = [F.Tensor.from_blocks(ctx, lay["legs"][s_], 0, blocks[s_], dt) for s_ in range(n)]
+        e, _, _ = peps.energy(ctx, lay, kets, 1.0, 8.0, tf, policy="late", chi=32, prec=prec)  # warm-up (plans)
+        l0 = ctx.launches()
+        t0 = time.perf_counter()
+        for _ in range(evals):
+            e, _, _ = peps.energy(ctx, lay, kets, 1.0, 8.0, tf, policy="late", chi=32, prec=prec)
+        dt_s = time.perf_counter() - t0
+        res[prec] = e
+        out[prec] = {"evals_per_s": evals / dt_s, "s_per_eval": dt_s / evals, "energy": e,
+                     "gpu_launches_per_eval": (ctx.launches() - l0) / evals}
+    out["mixed_vs_f64_rel_err"] = abs(res["tf32x3"] - res["f64"]) / abs(res["f64"])
+    out["speedup_mixed_vs_f64"] = out["tf32x3"]["evals_per_s"] / out["f64"]["evals_per_s"]
+    if with_oracle:
+        import oracle as O
+
+        t0 = time.perf_counter()
+        e_ref, *_ = O.energy_terms(lay, O.ket_tensors(lay, blocks), 1.0, 8.0, tf, policy="late", chi=32)
+        out["oracle_energy"] = e_ref
+        out["oracle_s_per_eval"] = time.perf_counter() - t0
+        out["f64_rel_err_vs_oracle"] = abs(res["f64"] - e_ref) / abs(e_ref)
+        out["tf32x3_rel_err_vs_oracle"] = abs(res["tf32x3"] - e_ref) / abs(e_ref)
+    return out
+
+
 def run_ours(args, rank, world, local):
     import torch
 
@@ -430,6 +475,8 @@ def run_ours(args, rank, world, local):
         result["speedup_vs_f64_gpu"] = precs[args.prec]["tflops"] / precs["f64"]["tflops"]
     if not args.no_e2e:
         result["e2e"] = e2e_run(F, ctx, torch, cases, args.prec, max(2, min(args.steps, 5)), flops_step)
+    if not args.no_energy:
+        result["energy"] = energy_bench(F, ctx, args.energy_evals, rank == 0 and world == 1 and not args.no_cpu)
     if rank == 0 and world == 1 and not args.no_cpu:
         result["cpu_baseline"] = cpu_baseline(cases)
     ctx.synchronize()
@@ -450,6 +497,8 @@ def main():
     ap.add_argument("--cases", default=",".join(CASES), type=lambda s: [x for x in s.split(",") if x])
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-energy", action="store_true")
+    ap.add_argument("--energy-evals", type=int, default=3)
     ap.add_argument("--no-accuracy", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:

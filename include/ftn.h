@@ -208,6 +208,7 @@ typedef struct {
   double s_max;         /* largest singular value                             */
   double s_cut;         /* smallest kept singular value (0 if none kept)      */
   double s_next;        /* largest discarded singular value (0 if none)       */
+  int jacobi_sweeps;    /* sweeps the one-sided Jacobi SVD needed (diagnostic) */
 } ftn_compress_info;
 
 /* Compress the bond formed by legs axes_x of *X paired with axes_y of *Y to at

@@ -34,11 +34,19 @@ struct CholJob {
 };
 
 struct SvdJob {
-  double* At;  // n x m row-major; rows are orthogonalised in place
-  double* Vt;  // n x n row-major; accumulated rotations (starts as identity)
-  double* s;   // n singular values (row norms at convergence)
+  const double* T;  // n x m row-major input, left untouched
+  double* Tf;       // n x m output: the rows orthogonalised (row j = s_j u_j^T)
+  double* s;        // n singular values (row norms at convergence)
+  int* sweeps;      // sweeps used (diagnostic)
   int n, m;
 };
+
+// Cluster Jacobi: SVDC_WARPS warps per CTA (one per SM sub-partition), rows
+// of up to 32 * SVDC_MAX_E elements held in registers while a pair is
+// rotated, and at most SVDC_SMEM_BYTES of rows per CTA.
+constexpr int SVDC_WARPS = 4;
+constexpr int SVDC_MAX_E = 16;
+constexpr int SVDC_SMEM_BYTES = 192 * 1024;
 
 struct GatherJob {
   const double* left;   // source row (length nl)
@@ -108,31 +116,86 @@ __global__ void __launch_bounds__(LA_THREADS) chol_kernel(const CholJob* jobs) {
   }
 }
 
-// One-sided Jacobi: orthogonalise the n rows of At (length m) by plane
-// rotations in round-robin order (n/2 disjoint pairs per round, one warp per
-// pair), accumulating the rotations in Vt.  Converged when a sweep applies no
-// rotation, i.e. every pair satisfies |a_p . a_q| <= 1e-15 |a_p| |a_q|.
-__global__ void __launch_bounds__(LA_THREADS) svd_jacobi_kernel(const SvdJob* jobs) {
-  __shared__ int rotated;
-  const SvdJob jb = jobs[blockIdx.x];
-  const int n = jb.n, m = jb.m;
-  double* At = jb.At;
-  double* Vt = jb.Vt;
+// Sum of three per-lane values over the warp with 6 additions instead of 15:
+// the first two levels split the lanes between the values.  Every lane gets
+// the three totals.
+__device__ __forceinline__ void warp_sum3(double& a, double& b, double& c) {
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const bool h16 = lane & 16, h8 = lane & 8;
+  double k = h16 ? b : a;
+  k += __shfl_xor_sync(full, h16 ? a : b, 16);
+  c += __shfl_xor_sync(full, c, 16);
+  double k2 = h8 ? c : k;
+  k2 += __shfl_xor_sync(full, h8 ? k : c, 8);
+  k2 += __shfl_xor_sync(full, k2, 4);
+  k2 += __shfl_xor_sync(full, k2, 2);
+  k2 += __shfl_xor_sync(full, k2, 1);
+  a = __shfl_sync(full, k2, 0);
+  b = __shfl_sync(full, k2, 16);
+  c = __shfl_sync(full, k2, 8);
+}
+
+// Jacobi rotation for the pair (t_p, t_q) with al = |t_p|^2, be = |t_q|^2,
+// ga = t_p . t_q: returns false when the pair is orthogonal to the
+// tolerance (|ga| <= tol |t_p| |t_q|).  The tangent of the rotation angle,
+// t = 2 ga sgn(d) / (|d| + sqrt(d^2 + 4 ga^2)) with d = be - al, is formed in
+// FP32 from the pair scaled by a power of two; c = (1 + t^2)^{-1/2} and
+// s = c t are then formed in FP64 from that t, so the rotation is orthogonal
+// to FP64 rounding whatever the accuracy of the angle (an angle off by a
+// relative 1e-7 leaves 1e-7 of ga, removed in the next sweep).
+__device__ __forceinline__ bool jacobi_rotation(double al, double be, double ga, double tol2, double& c,
+                                                double& s) {
+  if (!(ga * ga > tol2 * (al * be))) return false;
+  const double d = be - al, g2 = 2.0 * ga;
+  const double h = fmax(fabs(d), fabs(g2));
+  const int e = (__double2hiint(h) >> 20) & 0x7ff;
+  if (e == 0 || e >= 2046) return false;  // subnormal or non-finite pair: leave it
+  const double sc = __hiloint2double((2046 - e) << 20, 0);  // 2^(1023 - e): h * sc in [1, 2)
+  const float df = (float)(d * sc), gf = (float)(g2 * sc);
+  const float tf = copysignf(1.0f, df) * gf / (fabsf(df) + sqrtf(df * df + gf * gf));
+  const double t = (double)tf;
+  c = rsqrt(fma(t, t, 1.0));
+  s = c * t;
+  return true;
+}
+
+// One-sided (Hestenes) Jacobi: orthogonalise the n rows of an n x m matrix
+// T by plane rotations in round-robin order (n/2 disjoint pairs per round).
+// Converged when a sweep applies no rotation, i.e. every pair satisfies
+// |t_p . t_q| <= m eps |t_p| |t_q| (a computed dot product of length m
+// carries rounding of about m eps relative to |t_p| |t_q|, so a tighter test
+// would never be met).  Then T_f = Q^T T has rows s_j u_j^T (u_j the right
+// singular vectors of T) and the left ones follow as q_j = T u_j / s_j, so the
+// rotations themselves are never accumulated.
+__device__ __forceinline__ double jacobi_tol2(int m) {
+  const double tol = (double)(m > 8 ? m : 8) * 2.220446049250313e-16;
+  return tol * tol;
+}
+
+__device__ __forceinline__ void round_robin_pair(int k, int r, int np, int& p, int& q) {
+  const int a = k, b = np - 1 - k;
+  p = a == 0 ? 0 : 1 + (a - 1 + r) % (np - 1);
+  q = b == 0 ? 0 : 1 + (b - 1 + r) % (np - 1);
+}
+
+// Single-CTA version over a matrix in global memory (rows longer than the
+// cluster kernel holds in registers).
+__device__ __forceinline__ void jacobi_rows(double* A, int n, int m, int* rotated, double* s_out, int* sweeps_out) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int64_t e = threadIdx.x; e < (int64_t)n * n; e += blockDim.x) Vt[e] = (e / n == e % n) ? 1.0 : 0.0;
-  __syncthreads();
   const int np = n + (n & 1);
-  for (int sweep = 0; sweep < 40 && np > 1; ++sweep) {
-    if (threadIdx.x == 0) rotated = 0;
+  const double tol2 = jacobi_tol2(m);
+  int sweep = 0;
+  for (; sweep < 40 && np > 1; ++sweep) {
+    if (threadIdx.x == 0) *rotated = 0;
     __syncthreads();
     for (int r = 0; r < np - 1; ++r) {
       for (int k = warp; k < np / 2; k += nw) {
-        const int a = k, b = np - 1 - k;
-        const int p = a == 0 ? 0 : 1 + (a - 1 + r) % (np - 1);
-        const int q = b == 0 ? 0 : 1 + (b - 1 + r) % (np - 1);
+        int p, q;
+        round_robin_pair(k, r, np, p, q);
         if (p >= n || q >= n) continue;
-        double* ap = At + (int64_t)p * m;
-        double* aq = At + (int64_t)q * m;
+        double* ap = A + (int64_t)p * m;
+        double* aq = A + (int64_t)q * m;
         double al = 0.0, be = 0.0, ga = 0.0;
         for (int i = lane; i < m; i += 32) {
           const double x = ap[i], y = aq[i];
@@ -140,40 +203,149 @@ __global__ void __launch_bounds__(LA_THREADS) svd_jacobi_kernel(const SvdJob* jo
           be = fma(y, y, be);
           ga = fma(x, y, ga);
         }
-        for (int o = 16; o; o >>= 1) {
-          al += __shfl_xor_sync(0xffffffffu, al, o);
-          be += __shfl_xor_sync(0xffffffffu, be, o);
-          ga += __shfl_xor_sync(0xffffffffu, ga, o);
-        }
-        if (fabs(ga) <= 1e-15 * sqrt(al * be) || ga == 0.0) continue;
-        const double zeta = (be - al) / (2.0 * ga);
-        const double t = copysign(1.0, zeta) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-        const double c = 1.0 / sqrt(1.0 + t * t), sn = c * t;
+        warp_sum3(al, be, ga);
+        double c, sn;
+        if (!jacobi_rotation(al, be, ga, tol2, c, sn)) continue;
         for (int i = lane; i < m; i += 32) {
           const double x = ap[i], y = aq[i];
-          ap[i] = c * x - sn * y;
-          aq[i] = sn * x + c * y;
+          ap[i] = fma(c, x, -sn * y);
+          aq[i] = fma(sn, x, c * y);
         }
-        double* vp = Vt + (int64_t)p * n;
-        double* vq = Vt + (int64_t)q * n;
-        for (int i = lane; i < n; i += 32) {
-          const double x = vp[i], y = vq[i];
-          vp[i] = c * x - sn * y;
-          vq[i] = sn * x + c * y;
-        }
-        if (lane == 0) rotated = 1;
+        if (lane == 0) *rotated = 1;
       }
       __syncthreads();
     }
-    if (!rotated) break;
+    if (!*rotated) break;
     __syncthreads();
   }
+  if (threadIdx.x == 0) *sweeps_out = sweep;
   for (int j = warp; j < n; j += nw) {
     double ss = 0.0;
-    for (int i = lane; i < m; i += 32) ss = fma(At[(int64_t)j * m + i], At[(int64_t)j * m + i], ss);
+    for (int i = lane; i < m; i += 32) ss = fma(A[(int64_t)j * m + i], A[(int64_t)j * m + i], ss);
     for (int o = 16; o; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
-    if (lane == 0) jb.s[j] = sqrt(ss);
+    if (lane == 0) s_out[j] = sqrt(ss);
   }
+}
+
+__global__ void __launch_bounds__(LA_THREADS) svd_rows_global_kernel(const SvdJob* jobs) {
+  __shared__ int rotated;
+  const SvdJob jb = jobs[blockIdx.x];
+  const int64_t nm = (int64_t)jb.n * jb.m;
+  for (int64_t e = threadIdx.x; e < nm; e += blockDim.x) jb.Tf[e] = jb.T[e];
+  __syncthreads();
+  jacobi_rows(jb.Tf, jb.n, jb.m, &rotated, jb.s, jb.sweeps);
+}
+
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ uint32_t map_rank(uint32_t saddr, uint32_t rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(saddr), "r"(rank));
+  return r;
+}
+__device__ __forceinline__ double ld_cluster(uint32_t a) {
+  double v;
+  asm volatile("ld.shared::cluster.f64 %0, [%1];" : "=d"(v) : "r"(a) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_cluster(uint32_t a, double v) {
+  asm volatile("st.shared::cluster.f64 [%0], %1;" ::"r"(a), "d"(v) : "memory");
+}
+__device__ __forceinline__ int ld_cluster_s32(uint32_t a) {
+  int v;
+  asm volatile("ld.shared::cluster.s32 %0, [%1];" : "=r"(v) : "r"(a) : "memory");
+  return v;
+}
+// Hardware barrier over all threads of the cluster; release/acquire makes the
+// shared-memory writes of every CTA visible to all of them.
+__device__ __forceinline__ void cluster_sync_all() {
+  asm volatile("barrier.cluster.arrive.release;\n\tbarrier.cluster.wait.acquire;" ::: "memory");
+}
+
+// Cluster Jacobi: one cluster of C CTAs per matrix.  Row i lives in the
+// shared memory of CTA i mod C (slot i / C); each round the C * SVDC_WARPS
+// warps take the round's pairs, read both rows through distributed shared
+// memory into registers, and write the rotated rows back in place; a
+// cluster barrier separates the rounds.  Spreading a matrix over C SMs
+// multiplies the FP64 rate the rotations get by C.
+template <int E>
+__global__ void __launch_bounds__(SVDC_WARPS * 32) svd_rows_cluster_kernel(const SvdJob* jobs, int C) {
+  extern __shared__ __align__(16) double rows[];
+  __shared__ int flag[2];
+  const uint32_t rank = cluster_rank();
+  const SvdJob jb = jobs[blockIdx.x / C];
+  const int n = jb.n, m = jb.m;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nloc = ((int)(n - rank) + C - 1) / C;  // rows rank, rank + C, ...
+  for (int l = 0; l < nloc; ++l)
+    for (int i = threadIdx.x; i < m; i += blockDim.x) rows[(int64_t)l * m + i] = jb.T[(int64_t)(l * C + rank) * m + i];
+  if (threadIdx.x == 0) flag[0] = flag[1] = 0;
+  const uint32_t base = smem_u32(rows);
+  cluster_sync_all();
+  const int np = n + (n & 1);
+  const double tol2 = jacobi_tol2(m);
+  const int gw = (int)rank * SVDC_WARPS + warp, nwarps = C * SVDC_WARPS;
+  int sweep = 0;
+  for (; sweep < 40 && np > 1; ++sweep) {
+    for (int r = 0; r < np - 1; ++r) {
+      for (int k = gw; k < np / 2; k += nwarps) {
+        int p, q;
+        round_robin_pair(k, r, np, p, q);
+        if (p >= n || q >= n) continue;
+        const uint32_t ap = map_rank(base + (uint32_t)((p / C) * m) * 8u, (uint32_t)(p % C));
+        const uint32_t aq = map_rank(base + (uint32_t)((q / C) * m) * 8u, (uint32_t)(q % C));
+        double x[E], y[E];
+        double al = 0.0, be = 0.0, ga = 0.0;
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+          const int i = lane + 32 * e;
+          x[e] = i < m ? ld_cluster(ap + 8u * i) : 0.0;
+          y[e] = i < m ? ld_cluster(aq + 8u * i) : 0.0;
+        }
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+          al = fma(x[e], x[e], al);
+          be = fma(y[e], y[e], be);
+          ga = fma(x[e], y[e], ga);
+        }
+        warp_sum3(al, be, ga);
+        double c, sn;
+        if (!jacobi_rotation(al, be, ga, tol2, c, sn)) continue;
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+          const int i = lane + 32 * e;
+          if (i < m) {
+            st_cluster(ap + 8u * i, fma(c, x[e], -sn * y[e]));
+            st_cluster(aq + 8u * i, fma(sn, x[e], c * y[e]));
+          }
+        }
+        if (lane == 0) flag[sweep & 1] = 1;
+      }
+      cluster_sync_all();
+      // every CTA read the other flag at the end of the previous sweep,
+      // before this barrier: clear it for the next sweep
+      if (r == 0 && threadIdx.x == 0) flag[(sweep + 1) & 1] = 0;
+    }
+    int any = lane < C ? ld_cluster_s32(map_rank(smem_u32(&flag[sweep & 1]), (uint32_t)lane)) : 0;
+    if (!__any_sync(0xffffffffu, any != 0)) break;
+  }
+  if (rank == 0 && threadIdx.x == 0) *jb.sweeps = sweep;
+  for (int l = warp; l < nloc; l += SVDC_WARPS) {
+    const double* src = rows + (int64_t)l * m;
+    double* dst = jb.Tf + (int64_t)(l * C + rank) * m;
+    double ss = 0.0;
+    for (int i = lane; i < m; i += 32) {
+      const double v = src[i];
+      ss = fma(v, v, ss);
+      dst[i] = v;
+    }
+    for (int o = 16; o; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+    if (lane == 0) jb.s[l * C + rank] = sqrt(ss);
+  }
+  cluster_sync_all();  // no CTA leaves while a peer may still read its flags
 }
 
 __global__ void gather_kernel(const GatherJob* jobs) {
@@ -230,6 +402,79 @@ ftn_status run_gemms(ftn_ctx ctx, std::vector<GemmProb>& probs, const double* A,
   return launch_gemm_f64(ctx, (const GemmProb*)keep.p, (int)probs.size(), tiles, A, B, C);
 }
 
+template <int E>
+ftn_status setup_svd_cluster(int* cmax) {
+  auto k = svd_rows_cluster_kernel<E>;
+  FTN_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, SVDC_SMEM_BYTES));
+  FTN_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+  if (E == 1) {  // probe once whether 16-CTA clusters with full shared memory can be resident
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(16);
+    cfg.blockDim = dim3(SVDC_WARPS * 32);
+    cfg.dynamicSmemBytes = SVDC_SMEM_BYTES;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = 16;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    int num = 0;
+    if (cudaOccupancyMaxActiveClusters(&num, k, &cfg) != cudaSuccess) {
+      (void)cudaGetLastError();
+      num = 0;
+    }
+    *cmax = num >= 1 ? 16 : 8;
+  }
+  return FTN_OK;
+}
+
+// Largest cluster size the Jacobi kernel uses on this device (16 where
+// non-portable clusters of that size fit, else the portable 8).
+int svd_cluster_max(ftn_ctx ctx) {
+  static int cmax[64] = {0};
+  const int dev = ctx->device < 64 ? ctx->device : 0;
+  if (!cmax[dev]) {
+    int c = 8;
+    if (setup_svd_cluster<1>(&c) != FTN_OK || setup_svd_cluster<2>(&c) != FTN_OK ||
+        setup_svd_cluster<4>(&c) != FTN_OK || setup_svd_cluster<8>(&c) != FTN_OK ||
+        setup_svd_cluster<16>(&c) != FTN_OK)
+      c = 8;
+    cmax[dev] = c;
+  }
+  return cmax[dev];
+}
+
+template <int E>
+ftn_status launch_svd_cluster_e(ftn_ctx ctx, const SvdJob* jobs, int njobs, int C, size_t smem) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(C * njobs));
+  cfg.blockDim = dim3(SVDC_WARPS * 32);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = ctx->stream;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = (unsigned)C;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  FTN_CUDA(cudaLaunchKernelEx(&cfg, svd_rows_cluster_kernel<E>, jobs, C));
+  ctx->launches += 1;
+  return FTN_OK;
+}
+
+ftn_status launch_svd_cluster(ftn_ctx ctx, const SvdJob* jobs, int njobs, int C, int E, size_t smem) {
+  switch (E) {
+    case 1: return launch_svd_cluster_e<1>(ctx, jobs, njobs, C, smem);
+    case 2: return launch_svd_cluster_e<2>(ctx, jobs, njobs, C, smem);
+    case 4: return launch_svd_cluster_e<4>(ctx, jobs, njobs, C, smem);
+    case 8: return launch_svd_cluster_e<8>(ctx, jobs, njobs, C, smem);
+    case 16: return launch_svd_cluster_e<16>(ctx, jobs, njobs, C, smem);
+    default: return set_error(FTN_EINVAL, "internal error: Jacobi row length");
+  }
+}
+
 }  // namespace
 
 ftn_status compress_impl(ftn_ctx ctx, ftn_tensor* pX, ftn_tensor* pY, int n, const int* ax, const int* ay, int chi,
@@ -259,7 +504,7 @@ ftn_status compress_impl(ftn_ctx ctx, ftn_tensor* pX, ftn_tensor* pY, int n, con
   off += al(P->bf_elems);
   int64_t o_px_part[2], o_py_part[2];
   int sp_x[2], sp_y[2];
-  int64_t o_gx[2], o_gy[2], o_m[2], o_vt[2], o_s[2], o_wk[2], o_zk[2], o_px[2], o_qy[2];
+  int64_t o_gx[2], o_gy[2], o_m[2], o_tf[2], o_s[2], o_wk[2], o_zk[2], o_px[2], o_qy[2], o_ms3[2];
   int rx[2], ry[2], ldx[2], ldy[2], nrot[2], mlen[2];
   int64_t rx_off[2], ry_off[2];
   bool tall_x[2], tall_y[2], trans[2];
@@ -295,10 +540,12 @@ ftn_status compress_impl(ftn_ctx ctx, ftn_tensor* pX, ftn_tensor* pY, int n, con
     mlen[pi] = trans[pi] ? rx[pi] : ry[pi];
     o_m[pi] = off;
     off += al((int64_t)nrot[pi] * mlen[pi]);
-    o_vt[pi] = off;
-    off += al((int64_t)nrot[pi] * nrot[pi]);
+    o_tf[pi] = off;
+    off += al((int64_t)nrot[pi] * mlen[pi]);
+    o_ms3[pi] = off;
+    off += al((int64_t)nrot[pi] * mlen[pi]);
     o_s[pi] = off;
-    off += al(nrot[pi]);
+    off += al(nrot[pi] + 1);  // singular values, then the sweep count
     // kept vectors and projectors (at most nrot of them)
     o_wk[pi] = off;
     off += al((int64_t)nrot[pi] * rx[pi]);
@@ -387,27 +634,66 @@ ftn_status compress_impl(ftn_ctx ctx, ftn_tensor* pX, ftn_tensor* pY, int n, con
       g.cstr[0] = rx[pi];
     }
     mg.push_back(g);
-    svd.push_back({ws + o_m[pi], ws + o_vt[pi], ws + o_s[pi], nrot[pi], mlen[pi]});
+    svd.push_back({ws + o_m[pi], ws + o_tf[pi], ws + o_s[pi], (int*)(ws + o_s[pi] + nrot[pi]), nrot[pi], mlen[pi]});
   }
   rec = prof_begin(ctx, "gemm_f64", 0, 0);
   FTN_TRY(run_gemms(ctx, mg, ws, ws, ws, ws_n, ws_n, ws_n, t_m));
   prof_end(ctx, rec);
   if (!svd.empty()) {
-    FTN_TRY(put_table(ctx, svd, &t_svd.p));
+    // rows up to 32 * SVDC_MAX_E long whose cluster share fits in shared
+    // memory go to the cluster kernel, the others to the single-CTA one
+    const int cmax = svd_cluster_max(ctx);
+    std::vector<SvdJob> small, big;
+    int e_max = 1, c_use = 1;
+    for (const SvdJob& j : svd) {
+      const int np = j.n + (j.n & 1);
+      int c = 1;
+      while (c < cmax && c * SVDC_WARPS < np / 2) c *= 2;
+      while (c < cmax && (int64_t)((j.n + c - 1) / c) * j.m * 8 > SVDC_SMEM_BYTES) c *= 2;
+      if (j.m > 32 * SVDC_MAX_E || (int64_t)((j.n + c - 1) / c) * j.m * 8 > SVDC_SMEM_BYTES) {
+        big.push_back(j);
+        continue;
+      }
+      small.push_back(j);
+      c_use = std::max(c_use, c);
+      int e = 1;
+      while (32 * e < j.m) e *= 2;
+      e_max = std::max(e_max, e);
+    }
+    std::vector<SvdJob> all(small);
+    all.insert(all.end(), big.begin(), big.end());
+    FTN_TRY(put_table(ctx, all, &t_svd.p));
     rec = prof_begin(ctx, "svd_jacobi", 0, 0);
-    svd_jacobi_kernel<<<(unsigned)svd.size(), LA_THREADS, 0, ctx->stream>>>((const SvdJob*)t_svd.p);
-    ctx->launches += 1;
-    FTN_CUDA(cudaGetLastError());
+    if (!small.empty()) {
+      size_t smem = 0;
+      for (const SvdJob& j : small) smem = std::max(smem, (size_t)((j.n + c_use - 1) / c_use) * j.m * 8);
+      FTN_TRY(launch_svd_cluster(ctx, (const SvdJob*)t_svd.p, (int)small.size(), c_use, e_max, smem));
+    }
+    if (!big.empty()) {
+      svd_rows_global_kernel<<<(unsigned)big.size(), LA_THREADS, 0, ctx->stream>>>((const SvdJob*)t_svd.p +
+                                                                                   small.size());
+      ctx->launches += 1;
+      FTN_CUDA(cudaGetLastError());
+    }
     prof_end(ctx, rec);
   }
   // ---- 4. pooled truncation (one synchronisation) ----
   std::vector<double> sv[2];
   for (int pi = 0; pi < 2; ++pi) {
-    sv[pi].resize(nrot[pi]);
+    sv[pi].resize(nrot[pi] + 1);
     if (nrot[pi])
-      FTN_CUDA(cudaMemcpyAsync(sv[pi].data(), ws + o_s[pi], nrot[pi] * 8, cudaMemcpyDeviceToHost, ctx->stream));
+      FTN_CUDA(cudaMemcpyAsync(sv[pi].data(), ws + o_s[pi], (nrot[pi] + 1) * 8, cudaMemcpyDeviceToHost,
+                               ctx->stream));
   }
   FTN_CUDA(cudaStreamSynchronize(ctx->stream));
+  int sweeps_used = 0;
+  for (int pi = 0; pi < 2; ++pi) {
+    if (!nrot[pi]) continue;
+    int sw = 0;
+    std::memcpy(&sw, &sv[pi][nrot[pi]], sizeof(int));
+    sweeps_used = std::max(sweeps_used, sw);
+    sv[pi].resize(nrot[pi]);
+  }
   struct Cand {
     double s;
     int pi, idx;
@@ -440,24 +726,26 @@ ftn_status compress_impl(ftn_ctx ctx, ftn_tensor* pX, ftn_tensor* pY, int n, con
   int k[2] = {0, 0};
   for (auto& c : kept) k[c.pi]++;
   // ---- 5. projectors and the new tensors ----
+  // m-side vectors (the orthogonalised rows' direction) come from T_f rows;
+  // n-side vectors as T u_j / s_j by one GEMM with the untouched T.  Both are
+  // wanted scaled by s^{-1/2}: MS = T_f row * s^{-3/2}, MS3 = T_f row * s^{-5/2}
+  // and NS = MS3 T^T.  Without transposition the m side is the right (ry)
+  // side of M, with it the left (rx) side.
   std::vector<GatherJob> gat;
   int pos[2] = {0, 0};
   for (auto& c : kept) {
     const int pi = c.pi, j = pos[pi]++;
-    const double* rot = ws + o_vt[pi] + (int64_t)c.idx * nrot[pi];  // rotation row (length nrot)
-    const double* vec = ws + o_m[pi] + (int64_t)c.idx * mlen[pi];   // orthogonalised row (length mlen)
+    const double* row = ws + o_tf[pi] + (int64_t)c.idx * mlen[pi];
     const double is = 1.0 / sqrt(c.s);
     GatherJob g;
-    // left singular vectors of M live in the rx-long rows, right ones in the ry-long rows
-    if (!trans[pi]) {
-      g.left = rot, g.nl = rx[pi], g.sl = is;
-      g.right = vec, g.nr = ry[pi], g.sr = is / c.s;
-    } else {
-      g.left = vec, g.nl = rx[pi], g.sl = is / c.s;
-      g.right = rot, g.nr = ry[pi], g.sr = is;
-    }
-    g.dl = ws + o_wk[pi] + (int64_t)j * rx[pi];
-    g.dr = ws + o_zk[pi] + (int64_t)j * ry[pi];
+    g.left = row;
+    g.nl = mlen[pi];
+    g.sl = is / c.s;
+    g.right = row;
+    g.nr = mlen[pi];
+    g.sr = is / (c.s * c.s);
+    g.dl = ws + (trans[pi] ? o_wk[pi] : o_zk[pi]) + (int64_t)j * mlen[pi];
+    g.dr = ws + o_ms3[pi] + (int64_t)j * mlen[pi];
     gat.push_back(g);
   }
   if (!gat.empty()) {
@@ -466,6 +754,18 @@ ftn_status compress_impl(ftn_ctx ctx, ftn_tensor* pX, ftn_tensor* pY, int n, con
     ctx->launches += 1;
     FTN_CUDA(cudaGetLastError());
   }
+  std::vector<GemmProb> nside;
+  for (int pi = 0; pi < 2; ++pi) {
+    if (k[pi] == 0) continue;
+    // NS[j, r] = sum_c MS3[j, c] T[r, c]   (k x nrot)
+    GemmProb g = make_prob(k[pi], nrot[pi], mlen[pi], o_ms3[pi], mlen[pi], 1, o_m[pi], mlen[pi], 1);
+    gemm_plain_output(g, trans[pi] ? o_zk[pi] : o_wk[pi], nrot[pi]);
+    nside.push_back(g);
+  }
+  DevBuf t_ns(ctx);
+  rec = prof_begin(ctx, "gemm_f64", 0, 0);
+  FTN_TRY(run_gemms(ctx, nside, ws, ws, ws, ws_n, ws_n, ws_n, t_ns));
+  prof_end(ctx, rec);
   // P_X^T = Z_k R_Y (k x K) and Q_Y^T = W_k R_X (k x K)
   std::vector<GemmProb> proj;
   for (int pi = 0; pi < 2; ++pi) {
@@ -547,6 +847,7 @@ ftn_status compress_impl(ftn_ctx ctx, ftn_tensor* pX, ftn_tensor* pY, int n, con
     info->s_max = smax;
     info->s_cut = kept.empty() ? 0.0 : kept.back().s;
     info->s_next = kept.size() < cand.size() ? cand[kept.size()].s : 0.0;
+    info->jacobi_sweeps = sweeps_used;
   }
   ftn_tensor_free(X);
   ftn_tensor_free(Y);

@@ -21,7 +21,7 @@
 
 namespace ftn {
 
-ftn_status normalize_tensor(ftn_ctx ctx, ftn_tensor t, void* d_state);
+ftn_status normalize_tensor(ftn_ctx ctx, ftn_tensor t, void* d_state, int step);
 ftn_status cast_tensor(ftn_ctx ctx, ftn_tensor t, ftn_dtype to, ftn_tensor* out);
 ftn_status compress_impl(ftn_ctx ctx, ftn_tensor* pX, ftn_tensor* pY, int n, const int* ax, const int* ay, int chi,
                          int arrows, ftn_compress_info* info);
@@ -177,7 +177,7 @@ ftn_status contract_impl(ftn_ctx ctx, const ftn_network* net, const ftn_tree* tr
     E.partner[u] = v;
     E.partner[v] = u;
   }
-  // device scratch: [max |x| bits, log-scale accumulator]
+  // device scratch: [log-scale accumulator, two max |x| words]
   void* d_state = dev_alloc(ctx, 256);
   if (!d_state) return set_error(FTN_ENOMEM, "device allocation failed");
   struct Guard {
@@ -185,7 +185,7 @@ ftn_status contract_impl(ftn_ctx ctx, const ftn_network* net, const ftn_tree* tr
     void* p;
     ~Guard() { dev_free(c, p); }
   } guard{ctx, d_state};
-  FTN_CUDA(cudaMemsetAsync(d_state, 0, 16, ctx->stream));
+  FTN_CUDA(cudaMemsetAsync(d_state, 0, 24, ctx->stream));
   const int chi = tree->chi;
   for (int s = 0; s < n - 1; ++s) {
     const int64_t a = tree->pairs[2 * s], b = tree->pairs[2 * s + 1];
@@ -243,7 +243,7 @@ ftn_status contract_impl(ftn_ctx ctx, const ftn_network* net, const ftn_tree* tr
     if (tree->policy == FTN_POLICY_EARLY)
       for (int64_t nb : E.neighbours(id))
         if (E.bond_dim(id, nb) > chi) FTN_TRY(E.compress_pair(id, nb, chi));
-    FTN_TRY(normalize_tensor(ctx, E.live[id].t, d_state));
+    FTN_TRY(normalize_tensor(ctx, E.live[id].t, d_state, s));
   }
   if (E.live.size() != 1) return set_error(FTN_EINVAL, "tree does not reduce the network to one tensor");
   ftn_tensor last = E.live.begin()->second.t;
@@ -265,7 +265,7 @@ ftn_status contract_impl(ftn_ctx ctx, const ftn_network* net, const ftn_tree* tr
     FTN_CUDA(cudaStreamSynchronize(ctx->stream));
   }
   *mantissa = val * E.sign;
-  *log_scale = host_state[1];
+  *log_scale = host_state[0];
   return FTN_OK;
 }
 

@@ -5,8 +5,7 @@
 
 namespace ftn {
 
-// d_state[0]: running max |x| of the current tensor (as ordered bits of a
-// non-negative double); d_state[1]: log-scale accumulator (double).
+// max |x| as the ordered bits of a non-negative double (atomicMax).
 template <typename T>
 __global__ void maxabs_kernel(const T* __restrict__ x, int64_t n, unsigned long long* __restrict__ mx) {
   double m = 0.0;
@@ -16,21 +15,50 @@ __global__ void maxabs_kernel(const T* __restrict__ x, int64_t n, unsigned long 
   if ((threadIdx.x & 31) == 0 && m > 0.0) atomicMax(mx, (unsigned long long)__double_as_longlong(m));
 }
 
+template <typename Ti, typename To>
+__global__ void cast_kernel(const Ti* __restrict__ x, To* __restrict__ y, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = (To)x[i];
+}
+
+// Small tensors: one CTA finds max |x|, scales and accumulates the log; it
+// also clears both max words of the large-tensor path.
 template <typename T>
-__global__ void scale_kernel(T* __restrict__ x, int64_t n, const unsigned long long* __restrict__ mx,
-                             double* __restrict__ logacc) {
-  const double m = __longlong_as_double((long long)*mx);
+__global__ void __launch_bounds__(1024) normalize_small_kernel(T* __restrict__ x, int64_t n,
+                                                                double* __restrict__ logacc,
+                                                                unsigned long long* __restrict__ words) {
+  if (threadIdx.x == 0) words[0] = words[1] = 0ull;
+  __shared__ double red[32];
+  double m = 0.0;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) m = fmax(m, fabs((double)x[i]));
+  for (int o = 16; o; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    m = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+    for (int o = 16; o; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (threadIdx.x == 0) red[0] = m;
+  }
+  __syncthreads();
+  m = red[0];
+  if (!(m > 0.0)) return;
+  const T inv = (T)(1.0 / m);
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) x[i] *= inv;
+  if (threadIdx.x == 0) *logacc += log(m);
+}
+
+// Large tensors: max |x| into word `cur` (atomicMax), then scale; the scale
+// kernel clears the other word for the next step, so no separate memset.
+template <typename T>
+__global__ void scale2_kernel(T* __restrict__ x, int64_t n, unsigned long long* __restrict__ words, int cur,
+                              double* __restrict__ logacc) {
+  const double m = __longlong_as_double((long long)words[cur]);
+  if (blockIdx.x == 0 && threadIdx.x == 0) words[cur ^ 1] = 0ull;
   if (!(m > 0.0)) return;
   const T inv = (T)(1.0 / m);
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     x[i] *= inv;
   if (blockIdx.x == 0 && threadIdx.x == 0) *logacc += log(m);
-}
-
-template <typename Ti, typename To>
-__global__ void cast_kernel(const Ti* __restrict__ x, To* __restrict__ y, int64_t n) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    y[i] = (To)x[i];
 }
 
 static unsigned grid_for(ftn_ctx ctx, int64_t n) {
@@ -39,18 +67,29 @@ static unsigned grid_for(ftn_ctx ctx, int64_t n) {
   return (unsigned)(g < 1 ? 1 : g);
 }
 
-ftn_status normalize_tensor(ftn_ctx ctx, ftn_tensor t, void* d_state) {
-  unsigned long long* mx = (unsigned long long*)d_state;
-  double* logacc = (double*)((char*)d_state + 8);
-  FTN_CUDA(cudaMemsetAsync(mx, 0, 8, ctx->stream));
+// d_state layout: [0] log-scale accumulator (double), [1], [2] max words.
+// `step` alternates the max word; both start zeroed.
+ftn_status normalize_tensor(ftn_ctx ctx, ftn_tensor t, void* d_state, int step) {
+  double* logacc = (double*)d_state;
+  unsigned long long* words = (unsigned long long*)((char*)d_state + 8);
   if (t->numel == 0) return FTN_OK;
+  const int cur = step & 1;
+  if (t->numel <= 65536) {
+    if (t->dtype == FTN_F64)
+      normalize_small_kernel<double><<<1, 1024, 0, ctx->stream>>>((double*)t->data, t->numel, logacc, words);
+    else
+      normalize_small_kernel<float><<<1, 1024, 0, ctx->stream>>>((float*)t->data, t->numel, logacc, words);
+    ctx->launches += 1;
+    FTN_CUDA(cudaGetLastError());
+    return FTN_OK;
+  }
   const unsigned g = grid_for(ctx, t->numel);
   if (t->dtype == FTN_F64) {
-    maxabs_kernel<double><<<g, 256, 0, ctx->stream>>>((const double*)t->data, t->numel, mx);
-    scale_kernel<double><<<g, 256, 0, ctx->stream>>>((double*)t->data, t->numel, mx, logacc);
+    maxabs_kernel<double><<<g, 256, 0, ctx->stream>>>((const double*)t->data, t->numel, words + cur);
+    scale2_kernel<double><<<g, 256, 0, ctx->stream>>>((double*)t->data, t->numel, words, cur, logacc);
   } else {
-    maxabs_kernel<float><<<g, 256, 0, ctx->stream>>>((const float*)t->data, t->numel, mx);
-    scale_kernel<float><<<g, 256, 0, ctx->stream>>>((float*)t->data, t->numel, mx, logacc);
+    maxabs_kernel<float><<<g, 256, 0, ctx->stream>>>((const float*)t->data, t->numel, words + cur);
+    scale2_kernel<float><<<g, 256, 0, ctx->stream>>>((float*)t->data, t->numel, words, cur, logacc);
   }
   ctx->launches += 2;
   FTN_CUDA(cudaGetLastError());

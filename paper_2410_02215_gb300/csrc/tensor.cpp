@@ -312,6 +312,15 @@ ftn_status ftn_ctx_create(void* cuda_stream, ftn_alloc_fn alloc, ftn_free_fn fre
     delete c;
     return cuda_error(e, "cudaDeviceGetAttribute");
   }
+  if (!alloc) {
+    // library-owned buffers come from the device's stream-ordered pool; keep
+    // freed memory pooled instead of returning it to the driver at every sync
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+      uint64_t keep = UINT64_MAX;
+      cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    }
+  }
   c->dev_err = (int*)dev_alloc(c, 256);
   if (!c->dev_err) {
     delete c;

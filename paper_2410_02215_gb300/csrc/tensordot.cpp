@@ -98,9 +98,8 @@ static ftn_status upload_plan(ftn_ctx ctx, TdPlan& P) {
   P.dev = std::make_shared<DevTables>();
   P.dev->ctx = ctx;
   void* d = nullptr;
+  // (a pageable host-to-device copy has staged its source when the call returns)
   FTN_TRY(upload_table(ctx, host.data(), tot, &d));
-  // keep the pageable staging alive until the copy has been consumed
-  FTN_CUDA(cudaStreamSynchronize(ctx->stream));
   P.dev->p = d;
   uint8_t* b = (uint8_t*)d;
   P.d_ja = (PermJob*)b;
@@ -441,7 +440,7 @@ ftn_status get_plan(ftn_ctx ctx, const ftn_tensor_s* A, const ftn_tensor_s* B, i
     return FTN_OK;
   }
   FTN_TRY(build_plan(ctx, A, B, n, ax, ay, fa, fb, out_perm, prec, P));
-  if (cache.size() > 4096) cache.clear();
+  if (cache.size() > 65536) cache.clear();
   cache[key.str()] = P;
   return FTN_OK;
 }
@@ -630,10 +629,9 @@ ftn_status permute_impl(ftn_ctx ctx, ftn_tensor t, const int* perm, bool fermion
       if (created) ftn_tensor_free(o);
       return st;
     }
-    cudaStreamSynchronize(ctx->stream);
     P->dev->p = d;
     P->d_jobs = (PermJob*)d;
-    if (cache.size() > 4096) cache.clear();
+    if (cache.size() > 65536) cache.clear();
     cache[key.str()] = P;
   }
   int rec = prof_begin(ctx, "permute", 2.0 * t->numel * dtype_size(t->dtype), 0);

@@ -37,7 +37,8 @@ class FtnError(RuntimeError):
 
 class CompressInfo(C.Structure):
     _fields_ = [("kept", C.c_int * 2), ("rank", C.c_int * 2), ("discarded_sq", C.c_double),
-                ("total_sq", C.c_double), ("s_max", C.c_double), ("s_cut", C.c_double), ("s_next", C.c_double)]
+                ("total_sq", C.c_double), ("s_max", C.c_double), ("s_cut", C.c_double), ("s_next", C.c_double),
+                ("jacobi_sweeps", C.c_int)]
 
 
 class Network(C.Structure):
@@ -116,10 +117,12 @@ def _int(seq):
 
 
 class Context:
-    """ftn_ctx bound to a torch CUDA stream; device memory from torch's
-    caching allocator (via the context's allocator callbacks)."""
+    """ftn_ctx bound to a torch CUDA stream.  Library-owned device memory comes
+    from the device's stream-ordered pool (cudaMallocAsync, native, no Python
+    on the allocation path) or, with use_torch_allocator=True, from torch's
+    caching allocator through the context's allocator callbacks."""
 
-    def __init__(self, stream=None, use_torch_allocator=True):
+    def __init__(self, stream=None, use_torch_allocator=False):
         import torch
 
         self._torch = torch

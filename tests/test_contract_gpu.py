@@ -122,3 +122,22 @@ def test_approximate_energy_3x3_matches_oracle(F, ctx):
     kets = gpu_kets(F, ctx, lay, blocks, F.F64)
     e, _, _ = peps.energy(ctx, lay, kets, 1.0, 8.0, tf, policy="late", chi=8)
     assert abs(e - e_ref) <= 1e-9 * max(1.0, abs(e_ref))
+
+
+def test_energy_4x4_compressed_fp64_and_mixed(F, ctx):
+    """The energy workload of the benchmark (4x4 square lattice, D = 4 as 2+2,
+    chi = 32, late compression): FP64 GPU vs the oracle (1e-9), and the
+    mixed path (FP32 tensors, TF32x3 sector GEMMs, FP64 compression) vs the
+    FP64 GPU path (1e-6)."""
+    from paper_2410_02215_gb300 import peps
+
+    n, edges, lay, blocks = setup(4, 4, (2, 2), 1)
+    st = W.site_sweep_tree(list(range(n)))
+    tf = lambda ops: W.double_layer_tree(n, st, ops)  # noqa: E731
+    e_ref, *_ = O.energy_terms(lay, O.ket_tensors(lay, blocks), 1.0, 8.0, tf, policy="late", chi=32)
+    k64 = gpu_kets(F, ctx, lay, blocks, F.F64)
+    e64, _, _ = peps.energy(ctx, lay, k64, 1.0, 8.0, tf, policy="late", chi=32)
+    assert abs(e64 - e_ref) <= 1e-9 * abs(e_ref)
+    k32 = gpu_kets(F, ctx, lay, blocks, F.F32)
+    e32, _, _ = peps.energy(ctx, lay, k32, 1.0, 8.0, tf, policy="late", chi=32, prec="tf32x3")
+    assert abs(e32 - e64) <= 1e-6 * abs(e64)
