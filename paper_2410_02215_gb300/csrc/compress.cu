@@ -173,6 +173,17 @@ __device__ __forceinline__ double jacobi_tol2(int m) {
   return tol * tol;
 }
 
+// Rows whose squared norm is at or below tau2 = (m eps |T|_F)^2 are
+// numerically zero: rounding in a rotation with a row of norm |T| moves them
+// by about their own size, so they are never rotated, they leave the
+// round-robin at the next sweep boundary, and their singular value is
+// reported as exactly 0.  (A rank-deficient core would otherwise keep its
+// rounding-level rows rotating until the sweep limit.)
+__device__ __forceinline__ double jacobi_tau2(int m, double fro2) {
+  const double f = (double)(m > 8 ? m : 8) * 2.220446049250313e-16;
+  return f * f * fro2;
+}
+
 __device__ __forceinline__ void round_robin_pair(int k, int r, int np, int& p, int& q) {
   const int a = k, b = np - 1 - k;
   p = a == 0 ? 0 : 1 + (a - 1 + r) % (np - 1);
@@ -181,7 +192,8 @@ __device__ __forceinline__ void round_robin_pair(int k, int r, int np, int& p, i
 
 // Single-CTA version over a matrix in global memory (rows longer than the
 // cluster kernel holds in registers).
-__device__ __forceinline__ void jacobi_rows(double* A, int n, int m, int* rotated, double* s_out, int* sweeps_out) {
+__device__ __forceinline__ void jacobi_rows(double* A, int n, int m, int* rotated, double* s_out, int* sweeps_out,
+                                            double tau2) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int np = n + (n & 1);
   const double tol2 = jacobi_tol2(m);
@@ -204,6 +216,7 @@ __device__ __forceinline__ void jacobi_rows(double* A, int n, int m, int* rotate
           ga = fma(x, y, ga);
         }
         warp_sum3(al, be, ga);
+        if (al <= tau2 || be <= tau2) continue;
         double c, sn;
         if (!jacobi_rotation(al, be, ga, tol2, c, sn)) continue;
         for (int i = lane; i < m; i += 32) {
@@ -223,17 +236,32 @@ __device__ __forceinline__ void jacobi_rows(double* A, int n, int m, int* rotate
     double ss = 0.0;
     for (int i = lane; i < m; i += 32) ss = fma(A[(int64_t)j * m + i], A[(int64_t)j * m + i], ss);
     for (int o = 16; o; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
-    if (lane == 0) s_out[j] = sqrt(ss);
+    if (lane == 0) s_out[j] = ss > tau2 ? sqrt(ss) : 0.0;
   }
 }
 
 __global__ void __launch_bounds__(LA_THREADS) svd_rows_global_kernel(const SvdJob* jobs) {
   __shared__ int rotated;
+  __shared__ double red[33];
   const SvdJob jb = jobs[blockIdx.x];
   const int64_t nm = (int64_t)jb.n * jb.m;
-  for (int64_t e = threadIdx.x; e < nm; e += blockDim.x) jb.Tf[e] = jb.T[e];
+  double ss = 0.0;
+  for (int64_t e = threadIdx.x; e < nm; e += blockDim.x) {
+    const double v = jb.T[e];
+    jb.Tf[e] = v;
+    ss = fma(v, v, ss);
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int o = 16; o; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+  if (lane == 0) red[warp] = ss;
   __syncthreads();
-  jacobi_rows(jb.Tf, jb.n, jb.m, &rotated, jb.s, jb.sweeps);
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    red[32] = t;
+  }
+  __syncthreads();
+  jacobi_rows(jb.Tf, jb.n, jb.m, &rotated, jb.s, jb.sweeps, jacobi_tau2(jb.m, red[32]));
 }
 
 __device__ __forceinline__ uint32_t cluster_rank() {
@@ -265,36 +293,104 @@ __device__ __forceinline__ void cluster_sync_all() {
   asm volatile("barrier.cluster.arrive.release;\n\tbarrier.cluster.wait.acquire;" ::: "memory");
 }
 
+__device__ __forceinline__ unsigned ld_cluster_u8(uint32_t a) {
+  unsigned short v;
+  asm volatile("ld.shared::cluster.u8 %0, [%1];" : "=h"(v) : "r"(a) : "memory");
+  return v;
+}
+
 // Cluster Jacobi: one cluster of C CTAs per matrix.  Row i lives in the
 // shared memory of CTA i mod C (slot i / C); each round the C * SVDC_WARPS
-// warps take the round's pairs, read both rows through distributed shared
-// memory into registers, and write the rotated rows back in place; a
-// cluster barrier separates the rounds.  Spreading a matrix over C SMs
-// multiplies the FP64 rate the rotations get by C.
+// warps take the round's pairs of live rows, read both rows through
+// distributed shared memory into registers, and write the rotated rows back
+// in place; a cluster barrier separates the rounds.  Spreading a matrix over
+// C SMs multiplies the FP64 rate the rotations get by C.  The list of live
+// rows is rebuilt identically in every CTA at each sweep boundary.
 template <int E>
 __global__ void __launch_bounds__(SVDC_WARPS * 32) svd_rows_cluster_kernel(const SvdJob* jobs, int C) {
   extern __shared__ __align__(16) double rows[];
   __shared__ int flag[2];
+  __shared__ double part;
+  __shared__ int act[LA_MAX_DIM];
+  __shared__ unsigned char live[LA_MAX_DIM];  // this CTA's slots
+  __shared__ unsigned char all_live[LA_MAX_DIM];
+  __shared__ int n_act;
+  __shared__ double red[SVDC_WARPS];
   const uint32_t rank = cluster_rank();
   const SvdJob jb = jobs[blockIdx.x / C];
   const int n = jb.n, m = jb.m;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int nloc = ((int)(n - rank) + C - 1) / C;  // rows rank, rank + C, ...
+  double ss = 0.0;
   for (int l = 0; l < nloc; ++l)
-    for (int i = threadIdx.x; i < m; i += blockDim.x) rows[(int64_t)l * m + i] = jb.T[(int64_t)(l * C + rank) * m + i];
+    for (int i = threadIdx.x; i < m; i += blockDim.x) {
+      const double v = jb.T[(int64_t)(l * C + rank) * m + i];
+      rows[(int64_t)l * m + i] = v;
+      ss = fma(v, v, ss);
+    }
+  for (int o = 16; o; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+  if (lane == 0) red[warp] = ss;
   if (threadIdx.x == 0) flag[0] = flag[1] = 0;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < SVDC_WARPS; ++w) t += red[w];
+    part = t;
+  }
   const uint32_t base = smem_u32(rows);
   cluster_sync_all();
-  const int np = n + (n & 1);
-  const double tol2 = jacobi_tol2(m);
+  // |T|_F^2 from the C partial sums, added in the same order in every CTA
+  double fro2 = 0.0;
+  for (int c = 0; c < C; ++c) {
+    double v;
+    asm volatile("ld.shared::cluster.f64 %0, [%1];" : "=d"(v) : "r"(map_rank(smem_u32(&part), (uint32_t)c)) : "memory");
+    fro2 += v;
+  }
+  const double tol2 = jacobi_tol2(m), tau2 = jacobi_tau2(m, fro2);
+
+  // marks this CTA's live rows, then (after a cluster barrier) rebuilds the
+  // ordered list of live rows from all CTAs' marks
+  auto mark_live = [&]() {
+    for (int l = warp; l < nloc; l += SVDC_WARPS) {
+      const double* r = rows + (int64_t)l * m;
+      double q = 0.0;
+      for (int i = lane; i < m; i += 32) q = fma(r[i], r[i], q);
+      for (int o = 16; o; o >>= 1) q += __shfl_xor_sync(0xffffffffu, q, o);
+      if (lane == 0) live[l] = q > tau2 ? 1 : 0;
+    }
+  };
+  auto build_list = [&]() {
+    for (int i = threadIdx.x; i < n; i += blockDim.x)
+      all_live[i] = (unsigned char)ld_cluster_u8(map_rank(smem_u32(&live[i / C]), (uint32_t)(i % C)));
+    __syncthreads();
+    if (warp == 0) {
+      int run = 0;
+      for (int b0 = 0; b0 < n; b0 += 32) {
+        const int i = b0 + lane;
+        const bool on = i < n && all_live[i];
+        const unsigned bal = __ballot_sync(0xffffffffu, on);
+        if (on) act[run + __popc(bal & ((1u << lane) - 1u))] = i;
+        run += __popc(bal);
+      }
+      if (lane == 0) n_act = run;
+    }
+    __syncthreads();
+  };
+  mark_live();
+  cluster_sync_all();
+  build_list();
+
   const int gw = (int)rank * SVDC_WARPS + warp, nwarps = C * SVDC_WARPS;
   int sweep = 0;
-  for (; sweep < 40 && np > 1; ++sweep) {
-    for (int r = 0; r < np - 1; ++r) {
+  for (; sweep < 40; ++sweep) {
+    const int na = n_act;
+    const int np = na + (na & 1);
+    for (int r = 0; r + 1 < np; ++r) {
       for (int k = gw; k < np / 2; k += nwarps) {
-        int p, q;
-        round_robin_pair(k, r, np, p, q);
-        if (p >= n || q >= n) continue;
+        int pa, qa;
+        round_robin_pair(k, r, np, pa, qa);
+        if (pa >= na || qa >= na) continue;
+        const int p = act[pa], q = act[qa];
         const uint32_t ap = map_rank(base + (uint32_t)((p / C) * m) * 8u, (uint32_t)(p % C));
         const uint32_t aq = map_rank(base + (uint32_t)((q / C) * m) * 8u, (uint32_t)(q % C));
         double x[E], y[E];
@@ -312,6 +408,7 @@ __global__ void __launch_bounds__(SVDC_WARPS * 32) svd_rows_cluster_kernel(const
           ga = fma(x[e], y[e], ga);
         }
         warp_sum3(al, be, ga);
+        if (al <= tau2 || be <= tau2) continue;
         double c, sn;
         if (!jacobi_rotation(al, be, ga, tol2, c, sn)) continue;
 #pragma unroll
@@ -329,23 +426,74 @@ __global__ void __launch_bounds__(SVDC_WARPS * 32) svd_rows_cluster_kernel(const
       // before this barrier: clear it for the next sweep
       if (r == 0 && threadIdx.x == 0) flag[(sweep + 1) & 1] = 0;
     }
-    int any = lane < C ? ld_cluster_s32(map_rank(smem_u32(&flag[sweep & 1]), (uint32_t)lane)) : 0;
+    const int any = lane < C ? ld_cluster_s32(map_rank(smem_u32(&flag[sweep & 1]), (uint32_t)lane)) : 0;
     if (!__any_sync(0xffffffffu, any != 0)) break;
+    // peers finished reading the marks before the first barrier of this sweep
+    mark_live();
+    cluster_sync_all();
+    build_list();
   }
   if (rank == 0 && threadIdx.x == 0) *jb.sweeps = sweep;
   for (int l = warp; l < nloc; l += SVDC_WARPS) {
     const double* src = rows + (int64_t)l * m;
     double* dst = jb.Tf + (int64_t)(l * C + rank) * m;
-    double ss = 0.0;
+    double q = 0.0;
     for (int i = lane; i < m; i += 32) {
       const double v = src[i];
-      ss = fma(v, v, ss);
+      q = fma(v, v, q);
       dst[i] = v;
     }
-    for (int o = 16; o; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
-    if (lane == 0) jb.s[l * C + rank] = sqrt(ss);
+    for (int o = 16; o; o >>= 1) q += __shfl_xor_sync(0xffffffffu, q, o);
+    if (lane == 0) jb.s[l * C + rank] = q > tau2 ? sqrt(q) : 0.0;
   }
   cluster_sync_all();  // no CTA leaves while a peer may still read its flags
+}
+
+struct CompactJob {
+  const double* src;  // rows x cols, leading dimension ld
+  double* dst;        // the nonzero rows, packed (leading dimension cols)
+  int* count;         // number of nonzero rows
+  int rows, cols, ld;
+};
+
+// Packs the rows of an R factor that are not identically zero (rows of
+// dropped Cholesky pivots, or zero rows of a short matrix used as its own
+// factor).  They add nothing to M = R_X R_Y^T, so leaving them out gives the
+// same nonzero singular triplets from a smaller core.  rows <= LA_MAX_DIM.
+__global__ void __launch_bounds__(256) compact_rows_kernel(const CompactJob* jobs) {
+  __shared__ unsigned char nz[LA_MAX_DIM];
+  __shared__ int chunk_off[LA_MAX_DIM / 32 + 1];
+  const CompactJob jb = jobs[blockIdx.x];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int r = warp; r < jb.rows; r += nw) {
+    bool any = false;
+    for (int c = lane; c < jb.cols; c += 32) any |= jb.src[(int64_t)r * jb.ld + c] != 0.0;
+    any = __any_sync(0xffffffffu, any);
+    if (lane == 0) nz[r] = any ? 1 : 0;
+  }
+  __syncthreads();
+  const int nchunk = (jb.rows + 31) / 32;
+  if (warp == 0) {
+    int run = 0;
+    for (int ch = 0; ch < nchunk; ++ch) {
+      const int r = ch * 32 + lane;
+      const unsigned b = __ballot_sync(0xffffffffu, r < jb.rows && nz[r]);
+      if (lane == 0) chunk_off[ch] = run;
+      run += __popc(b);
+    }
+    if (lane == 0) {
+      chunk_off[nchunk] = run;
+      *jb.count = run;
+    }
+  }
+  __syncthreads();
+  for (int r = warp; r < jb.rows; r += nw) {
+    if (!nz[r]) continue;
+    const int ch = r / 32;
+    int pos = chunk_off[ch];
+    for (int q = ch * 32; q < r; ++q) pos += nz[q];
+    for (int c = lane; c < jb.cols; c += 32) jb.dst[(int64_t)pos * jb.cols + c] = jb.src[(int64_t)r * jb.ld + c];
+  }
 }
 
 __global__ void gather_kernel(const GatherJob* jobs) {
@@ -505,6 +653,7 @@ ftn_status compress_impl(ftn_ctx ctx, ftn_tensor* pX, ftn_tensor* pY, int n, con
   int64_t o_px_part[2], o_py_part[2];
   int sp_x[2], sp_y[2];
   int64_t o_gx[2], o_gy[2], o_m[2], o_tf[2], o_s[2], o_wk[2], o_zk[2], o_px[2], o_qy[2], o_ms3[2];
+  int64_t o_rxc[2], o_ryc[2];
   int rx[2], ry[2], ldx[2], ldy[2], nrot[2], mlen[2];
   int64_t rx_off[2], ry_off[2];
   bool tall_x[2], tall_y[2], trans[2];
@@ -531,6 +680,10 @@ ftn_status compress_impl(ftn_ctx ctx, ftn_tensor* pX, ftn_tensor* pY, int n, con
     off += sp_x[pi] > 1 ? al((int64_t)sp_x[pi] * K * K) : 0;
     o_py_part[pi] = off;
     off += sp_y[pi] > 1 ? al((int64_t)sp_y[pi] * K * K) : 0;
+    o_rxc[pi] = off;
+    off += al((int64_t)rx[pi] * K);
+    o_ryc[pi] = off;
+    off += al((int64_t)ry[pi] * K);
     rx_off[pi] = tall_x[pi] ? o_gx[pi] : o_xf + P->afoff[pi];
     ldx[pi] = tall_x[pi] ? (int)K : (int)P->ldk[pi];
     ry_off[pi] = tall_y[pi] ? o_gy[pi] : o_yf + P->bfoff[pi];
@@ -556,6 +709,8 @@ ftn_status compress_impl(ftn_ctx ctx, ftn_tensor* pX, ftn_tensor* pY, int n, con
     o_qy[pi] = off;
     off += al((int64_t)nrot[pi] * K);
   }
+  const int64_t o_cnt = off;  // four int row counts
+  off += 32;
   const int64_t ws_n = off;
   double* ws = (double*)workspace(ctx, (size_t)ws_n * 8);
   if (!ws) return set_error(FTN_ENOMEM, "workspace allocation failed");
@@ -615,6 +770,46 @@ ftn_status compress_impl(ftn_ctx ctx, ftn_tensor* pX, ftn_tensor* pY, int n, con
     ctx->launches += 1;
     FTN_CUDA(cudaGetLastError());
     prof_end(ctx, rec);
+  }
+  // ---- 2b. nonzero rows of the R factors (one synchronisation for the counts) ----
+  {
+    std::vector<CompactJob> cj;
+    int* cnt = (int*)(ws + o_cnt);
+    for (int pi = 0; pi < 2; ++pi) {
+      const int K = (int)P->K[pi];
+      if (K == 0 || rx[pi] == 0 || ry[pi] == 0) continue;
+      cj.push_back({ws + rx_off[pi], ws + o_rxc[pi], cnt + 2 * pi, rx[pi], K, ldx[pi]});
+      cj.push_back({ws + ry_off[pi], ws + o_ryc[pi], cnt + 2 * pi + 1, ry[pi], K, ldy[pi]});
+    }
+    int hc[4] = {0, 0, 0, 0};
+    if (!cj.empty()) {
+      DevBuf t_cj(ctx);
+      FTN_TRY(put_table(ctx, cj, &t_cj.p));
+      FTN_CUDA(cudaMemsetAsync(cnt, 0, 4 * sizeof(int), ctx->stream));
+      compact_rows_kernel<<<(unsigned)cj.size(), 256, 0, ctx->stream>>>((const CompactJob*)t_cj.p);
+      ctx->launches += 1;
+      FTN_CUDA(cudaGetLastError());
+      FTN_CUDA(cudaMemcpyAsync(hc, cnt, sizeof(hc), cudaMemcpyDeviceToHost, ctx->stream));
+      FTN_CUDA(cudaStreamSynchronize(ctx->stream));
+    }
+    for (int pi = 0; pi < 2; ++pi) {
+      const int K = (int)P->K[pi];
+      if (K == 0 || rx[pi] == 0 || ry[pi] == 0) {
+        rx[pi] = ry[pi] = 0;
+        continue;
+      }
+      if (hc[2 * pi] < 0 || hc[2 * pi] > rx[pi] || hc[2 * pi + 1] < 0 || hc[2 * pi + 1] > ry[pi])
+        return set_error(FTN_EINVAL, "internal error: R factor row count");
+      rx[pi] = hc[2 * pi];
+      ry[pi] = hc[2 * pi + 1];
+      rx_off[pi] = o_rxc[pi];
+      ldx[pi] = K;
+      ry_off[pi] = o_ryc[pi];
+      ldy[pi] = K;
+      trans[pi] = rx[pi] > ry[pi];  // rotate the shorter side
+      nrot[pi] = trans[pi] ? ry[pi] : rx[pi];
+      mlen[pi] = trans[pi] ? rx[pi] : ry[pi];
+    }
   }
   // ---- 3. core M = R_X R_Y^T (stored with the rotated side as rows) and SVD ----
   std::vector<GemmProb> mg;
