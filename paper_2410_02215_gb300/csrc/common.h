@@ -224,12 +224,25 @@ void add_perm_job(std::vector<PermJob>& jobs, int64_t& tiles, int rank, const in
 int finalize_perm_jobs(std::vector<PermJob>& jobs, size_t elem_size, int64_t* tiles, bool allow_staged);
 ftn_status launch_permute(ftn_ctx ctx, const PermJob* d_jobs, int njobs, int64_t tiles, int staged, const void* src,
                           void* dst0, void* dst1, ftn_dtype in_type, int mode);
+// FP64 tiles are 64 x bn, bn in {16, 32, 64} (f64_pick_bn of the widest
+// problem); the problems' tiles_n must be counted with the same bn.
 ftn_status launch_gemm_f64(ftn_ctx ctx, const GemmProb* d_probs, int nprobs, int64_t tiles, const double* a,
-                           const double* b, double* c);
+                           const double* b, double* c, int bn);
+int f64_pick_bn(int max_n);
 // plain row-major output block (rows x cols, row stride ld) at c_off
 void gemm_plain_output(GemmProb& g, int64_t c_off, int64_t ld);
 // dst[e] = sum_s src[s * slab + e] for e < count (split-K reduction)
 ftn_status launch_sum_slabs(ftn_ctx ctx, double* dst, const double* src, int64_t count, int nsplit, int64_t slab);
+// FP64 split-K for launches with fewer than two tiles per SM: rewrites probs
+// to write partial slabs (offsets into a separate buffer) and fills red with
+// the reduction jobs carrying the original epilogues.  Returns the partial
+// buffer's element count (0: no split, probs untouched); updates the tile
+// count and sets red_total to the number of output elements.
+int64_t plan_splitk_f64(std::vector<GemmProb>& probs, int num_sms, std::vector<GemmProb>& red, int64_t& tiles,
+                        int64_t& red_total);
+bool red_in_bounds(const std::vector<GemmProb>& red, int64_t part_n, int64_t c_n);
+ftn_status launch_splitk_reduce(ftn_ctx ctx, const GemmProb* d_red, int nred, int64_t total, const double* part,
+                                double* c);
 
 struct TcOperands {
   // fused pi-matrices: rows x ldk elements, K-major; lo only for split modes

@@ -537,17 +537,41 @@ GemmProb make_prob(int M, int N, int K, int64_t a_off, int64_t a_sm, int64_t a_s
   return g;
 }
 
+// One FP64 GEMM launch over `probs`; a launch with few output tiles that
+// is not split already gets the split-K treatment (partial slabs after the
+// tables in the same device allocation, then the ordered reduction).
 ftn_status run_gemms(ftn_ctx ctx, std::vector<GemmProb>& probs, const double* A, const double* B, double* C,
                      int64_t a_n, int64_t b_n, int64_t c_n, DevBuf& keep) {
   if (probs.empty()) return FTN_OK;
+  int max_n = 1;
+  for (auto& g : probs) max_n = std::max(max_n, g.N);
+  const int bn = f64_pick_bn(max_n);
+  for (auto& g : probs) g.tiles_n = (g.N + bn - 1) / bn;
   int64_t tiles = 0;
+  bool presplit = false;
   for (auto& g : probs) {
     g.tile_begin = tiles;
     tiles += (int64_t)g.tiles_m * g.tiles_n * (g.nsplit > 1 ? g.nsplit : 1);
+    presplit = presplit || g.nsplit > 1;
   }
-  if (!probs_in_bounds(probs, a_n, b_n, c_n)) return set_error(FTN_EINVAL, "internal error: compression GEMM out of bounds");
-  FTN_TRY(put_table(ctx, probs, &keep.p));
-  return launch_gemm_f64(ctx, (const GemmProb*)keep.p, (int)probs.size(), tiles, A, B, C);
+  std::vector<GemmProb> red;
+  int64_t red_total = 0, part_n = 0;
+  if (!presplit) part_n = plan_splitk_f64(probs, ctx->num_sms, red, tiles, red_total);
+  if (!probs_in_bounds(probs, a_n, b_n, part_n ? part_n : c_n) || (part_n && !red_in_bounds(red, part_n, c_n)))
+    return set_error(FTN_EINVAL, "internal error: compression GEMM out of bounds");
+  const size_t tp = probs.size() * sizeof(GemmProb), tr = red.size() * sizeof(GemmProb);
+  const size_t tab = (tp + tr + 255) & ~(size_t)255;
+  std::vector<uint8_t> host(tp + tr);
+  std::memcpy(host.data(), probs.data(), tp);
+  if (tr) std::memcpy(host.data() + tp, red.data(), tr);
+  keep.p = dev_alloc(ctx, tab + (size_t)part_n * 8);
+  if (!keep.p) return set_error(FTN_ENOMEM, "device allocation failed (GEMM tables)");
+  FTN_CUDA(cudaMemcpyAsync(keep.p, host.data(), tp + tr, cudaMemcpyHostToDevice, ctx->stream));
+  const GemmProb* d_probs = (const GemmProb*)keep.p;
+  if (!part_n) return launch_gemm_f64(ctx, d_probs, (int)probs.size(), tiles, A, B, C, bn);
+  double* part = (double*)((uint8_t*)keep.p + tab);
+  FTN_TRY(launch_gemm_f64(ctx, d_probs, (int)probs.size(), tiles, A, B, part, bn));
+  return launch_splitk_reduce(ctx, d_probs + probs.size(), (int)red.size(), red_total, part, C);
 }
 
 template <int E>

@@ -3,11 +3,13 @@
 // operands K-major in the fused sector-matrix layout.  tcgen05 has no FP64
 // kind, so this is a DFMA kernel: 64x64 tiles, 4x4 outputs per thread,
 // persistent grid over the flattened tile list of all problems.
+#include <algorithm>
+
 #include "common.h"
 
 namespace ftn {
 
-constexpr int F64_BM = 64, F64_BN = 64, F64_BK = 16;
+constexpr int F64_BM = 64, F64_BK = 16;
 
 __device__ __forceinline__ int find_prob(const GemmProb* probs, int nprobs, int64_t t) {
   int lo = 0, hi = nprobs - 1;
@@ -21,11 +23,17 @@ __device__ __forceinline__ int find_prob(const GemmProb* probs, int nprobs, int6
   return lo;
 }
 
+// 64 x BN tiles (BN = 16, 32 or 64, chosen per launch from the widest
+// problem): 256 threads, 4 x (BN / 16) outputs each.  FP64 is the bound, so
+// the tile width follows the problems' column counts instead of wasting
+// DFMAs on padding columns.
+template <int BN>
 __global__ void __launch_bounds__(256) gemm_f64_kernel(const GemmProb* __restrict__ probs, int nprobs, int64_t tiles,
                                                        const double* __restrict__ A, const double* __restrict__ B,
                                                        double* __restrict__ C) {
+  constexpr int TN = BN / 16;
   __shared__ double As[F64_BK][F64_BM + 1];
-  __shared__ double Bs[F64_BK][F64_BN + 1];
+  __shared__ double Bs[F64_BK][BN + 1];
   __shared__ int s_p;
   const int tid = threadIdx.x;
   const int tx = tid & 15, ty = tid >> 4;
@@ -38,14 +46,14 @@ __global__ void __launch_bounds__(256) gemm_f64_kernel(const GemmProb* __restric
     const int ks = (int)(local % nsp);
     local /= nsp;
     const int m0 = (int)(local / p.tiles_n) * F64_BM;
-    const int n0 = (int)(local % p.tiles_n) * F64_BN;
+    const int n0 = (int)(local % p.tiles_n) * BN;
     const int kbeg = nsp > 1 ? ks * p.kchunk : 0;
     const int kend = nsp > 1 ? min(p.K, kbeg + p.kchunk) : p.K;
-    double acc[4][4];
+    double acc[4][TN];
 #pragma unroll
     for (int a = 0; a < 4; ++a)
 #pragma unroll
-      for (int c = 0; c < 4; ++c) acc[a][c] = 0.0;
+      for (int c = 0; c < TN; ++c) acc[a][c] = 0.0;
     const double* Ap = A + p.a_off;
     const double* Bp = B + p.b_off;
     const bool a_kfast = p.a_sk == 1, b_kfast = p.b_sk == 1;
@@ -53,34 +61,36 @@ __global__ void __launch_bounds__(256) gemm_f64_kernel(const GemmProb* __restric
       // threads run along whichever operand index has unit stride
 #pragma unroll
       for (int e = 0; e < 4; ++e) {
-        int idx = tid + 256 * e;
-        int row = a_kfast ? idx >> 4 : idx & 63, kk = a_kfast ? idx & 15 : idx >> 6;
-        int gm = m0 + row, gk = k0 + kk;
+        const int idx = tid + 256 * e;
+        const int row = a_kfast ? idx >> 4 : idx & 63, kk = a_kfast ? idx & 15 : idx >> 6;
+        const int gm = m0 + row, gk = k0 + kk;
         As[kk][row] = (gm < p.M && gk < kend) ? Ap[(int64_t)gm * p.a_sm + (int64_t)gk * p.a_sk] : 0.0;
-        row = b_kfast ? idx >> 4 : idx & 63;
-        kk = b_kfast ? idx & 15 : idx >> 6;
-        gk = k0 + kk;
-        int gn = n0 + row;
+      }
+#pragma unroll
+      for (int e = 0; e < TN; ++e) {
+        const int idx = tid + 256 * e;
+        const int row = b_kfast ? idx >> 4 : idx % BN, kk = b_kfast ? idx & 15 : idx / BN;
+        const int gn = n0 + row, gk = k0 + kk;
         Bs[kk][row] = (gn < p.N && gk < kend) ? Bp[(int64_t)gn * p.b_sn + (int64_t)gk * p.b_sk] : 0.0;
       }
       __syncthreads();
 #pragma unroll
       for (int kk = 0; kk < F64_BK; ++kk) {
-        double av[4], bv[4];
+        double av[4], bv[TN];
 #pragma unroll
         for (int a = 0; a < 4; ++a) av[a] = As[kk][ty + 16 * a];
 #pragma unroll
-        for (int c = 0; c < 4; ++c) bv[c] = Bs[kk][tx + 16 * c];
+        for (int c = 0; c < TN; ++c) bv[c] = Bs[kk][tx + 16 * c];
 #pragma unroll
         for (int a = 0; a < 4; ++a)
 #pragma unroll
-          for (int c = 0; c < 4; ++c) acc[a][c] = fma(av[a], bv[c], acc[a][c]);
+          for (int c = 0; c < TN; ++c) acc[a][c] = fma(av[a], bv[c], acc[a][c]);
       }
       __syncthreads();
     }
-    int64_t cpart[4];
+    int64_t cpart[TN];
 #pragma unroll
-    for (int c = 0; c < 4; ++c) {
+    for (int c = 0; c < TN; ++c) {
       int gn = n0 + tx + 16 * c;
       cpart[c] = gn < p.N ? expand_index32(gn, p.ncl, p.cdim, p.cstr) : 0;
     }
@@ -91,7 +101,7 @@ __global__ void __launch_bounds__(256) gemm_f64_kernel(const GemmProb* __restric
       if (gm >= p.M) continue;
       const int64_t rpart = p.c_off + (int64_t)ks * p.c_slab + expand_index32(gm, p.nrl, p.rdim, p.rstr);
 #pragma unroll
-      for (int c = 0; c < 4; ++c) {
+      for (int c = 0; c < TN; ++c) {
         int gn = n0 + tx + 16 * c;
         if (gn < p.N) C[rpart + cpart[c]] = sg * acc[a][c];
       }
@@ -99,6 +109,8 @@ __global__ void __launch_bounds__(256) gemm_f64_kernel(const GemmProb* __restric
     __syncthreads();
   }
 }
+
+int f64_pick_bn(int max_n) { return max_n <= 16 ? 16 : max_n <= 32 ? 32 : 64; }
 
 __global__ void sum_slabs_kernel(double* __restrict__ dst, const double* __restrict__ src, int64_t count, int nsplit,
                                  int64_t slab) {
@@ -120,6 +132,88 @@ ftn_status launch_sum_slabs(ftn_ctx ctx, double* dst, const double* src, int64_t
   return FTN_OK;
 }
 
+// Split-K reduction with the problems' own epilogues: red[i] carries the
+// epilogue mapping of problem i (c_off, row/column leg dims and strides,
+// sign), a_off = its partial slabs' offset in `part`, nsplit slabs of
+// c_slab = M * N elements, and tile_begin = its first element in the
+// flattened element list.  Slabs are added in split order, so the result
+// does not depend on the launch.
+__global__ void splitk_reduce_kernel(const GemmProb* __restrict__ red, int nred, int64_t total,
+                                     const double* __restrict__ part, double* __restrict__ C) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const GemmProb& g = red[find_prob(red, nred, e)];
+    const int64_t local = e - g.tile_begin;
+    const int m = (int)(local / g.N), n = (int)(local - (int64_t)m * g.N);
+    const double* src = part + g.a_off + local;
+    double acc = 0.0;
+    for (int s = 0; s < g.nsplit; ++s) acc += src[(int64_t)s * g.c_slab];
+    C[g.c_off + expand_index32(m, g.nrl, g.rdim, g.rstr) + expand_index32(n, g.ncl, g.cdim, g.cstr)] =
+        (double)g.c_sign * acc;
+  }
+}
+
+int64_t plan_splitk_f64(std::vector<GemmProb>& probs, int num_sms, std::vector<GemmProb>& red, int64_t& tiles,
+                        int64_t& red_total) {
+  red.clear();
+  red_total = 0;
+  int64_t t0 = 0;
+  int kmax = 0;
+  for (const GemmProb& g : probs) {
+    t0 += (int64_t)g.tiles_m * g.tiles_n;
+    kmax = std::max(kmax, g.K);
+  }
+  if (probs.empty() || t0 >= 2 * (int64_t)num_sms || kmax < 64) return 0;
+  const int64_t want = (2 * (int64_t)num_sms + t0 - 1) / t0;
+  int64_t part = 0, elems = 0, tb = 0;
+  for (GemmProb& g : probs) {
+    GemmProb r = g;  // keeps the epilogue
+    int s = (int)std::min<int64_t>(std::min<int64_t>(want, 64), std::max(1, (g.K + 15) / 16));
+    int kchunk = std::max(16, ((g.K + s - 1) / s + 15) / 16 * 16);
+    s = std::max(1, (g.K + kchunk - 1) / kchunk);
+    const int64_t mn = (int64_t)g.M * g.N;
+    r.a_off = part;
+    r.nsplit = s;
+    r.c_slab = mn;
+    r.tile_begin = elems;
+    red.push_back(r);
+    g.nsplit = s;
+    g.kchunk = kchunk;
+    gemm_plain_output(g, part, g.N);
+    g.c_slab = mn;
+    g.tile_begin = tb;
+    tb += (int64_t)g.tiles_m * g.tiles_n * s;
+    part += mn * s;
+    elems += mn;
+  }
+  tiles = tb;
+  red_total = elems;
+  return part;
+}
+
+bool red_in_bounds(const std::vector<GemmProb>& red, int64_t part_n, int64_t c_n) {
+  for (const GemmProb& g : red) {
+    if (g.M <= 0 || g.N <= 0 || g.nsplit < 1 || g.c_slab != (int64_t)g.M * g.N) return false;
+    if (g.a_off < 0 || g.a_off + (int64_t)g.nsplit * g.c_slab > part_n) return false;
+    int64_t mr = 1, mc = 1, top = g.c_off;
+    for (int l = 0; l < g.nrl; ++l) mr *= g.rdim[l], top += (int64_t)(g.rdim[l] - 1) * g.rstr[l];
+    for (int l = 0; l < g.ncl; ++l) mc *= g.cdim[l], top += (int64_t)(g.cdim[l] - 1) * g.cstr[l];
+    if (mr != g.M || mc != g.N || g.c_off < 0 || top >= c_n) return false;
+  }
+  return true;
+}
+
+ftn_status launch_splitk_reduce(ftn_ctx ctx, const GemmProb* d_red, int nred, int64_t total, const double* part,
+                                double* c) {
+  if (nred == 0 || total == 0) return FTN_OK;
+  int64_t grid = (total + 255) / 256;
+  if (grid > (int64_t)ctx->num_sms * 8) grid = (int64_t)ctx->num_sms * 8;
+  splitk_reduce_kernel<<<(unsigned)grid, 256, 0, ctx->stream>>>(d_red, nred, total, part, c);
+  ctx->launches += 1;
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_error(e, "splitk_reduce_kernel launch");
+  return FTN_OK;
+}
+
 void gemm_plain_output(GemmProb& g, int64_t c_off, int64_t ld) {
   g.c_off = c_off;
   g.c_sign = 1;
@@ -131,12 +225,19 @@ void gemm_plain_output(GemmProb& g, int64_t c_off, int64_t ld) {
 }
 
 ftn_status launch_gemm_f64(ftn_ctx ctx, const GemmProb* d_probs, int nprobs, int64_t tiles, const double* a,
-                           const double* b, double* c) {
+                           const double* b, double* c, int bn) {
   if (nprobs == 0 || tiles == 0) return FTN_OK;
   int64_t grid = tiles;
   int64_t cap = (int64_t)ctx->num_sms * 4;
   if (grid > cap) grid = cap;
-  gemm_f64_kernel<<<(unsigned)grid, 256, 0, ctx->stream>>>(d_probs, nprobs, tiles, a, b, c);
+  if (bn == 16)
+    gemm_f64_kernel<16><<<(unsigned)grid, 256, 0, ctx->stream>>>(d_probs, nprobs, tiles, a, b, c);
+  else if (bn == 32)
+    gemm_f64_kernel<32><<<(unsigned)grid, 256, 0, ctx->stream>>>(d_probs, nprobs, tiles, a, b, c);
+  else if (bn == 64)
+    gemm_f64_kernel<64><<<(unsigned)grid, 256, 0, ctx->stream>>>(d_probs, nprobs, tiles, a, b, c);
+  else
+    return set_error(FTN_EINVAL, "internal error: FP64 GEMM tile width");
   ctx->launches += 1;
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_error(e, "gemm_f64_kernel launch");

@@ -25,6 +25,9 @@ struct TdPlan {
   bool fused = true;           // the GEMM epilogue writes the final layout
   std::vector<GemmProb> probs;
   int64_t gemm_tiles = 0;
+  // FP64 split-K (few output tiles): partial slabs and their reduction
+  std::vector<GemmProb> red;
+  int64_t part_elems = 0, red_total = 0;
   int bn = 0;
   bool out_perm = false;
   int cr = 0;  // result rank
@@ -40,6 +43,7 @@ struct TdPlan {
   PermJob* d_jb = nullptr;
   PermJob* d_jc = nullptr;
   GemmProb* d_probs = nullptr;
+  GemmProb* d_red = nullptr;
 };
 
 ftn_status get_plan(ftn_ctx ctx, const ftn_tensor_s* A, const ftn_tensor_s* B, int n, const int* ax, const int* ay,

@@ -88,13 +88,14 @@ static std::string meta_key(const ftn_tensor_s* t) {
 
 static ftn_status upload_plan(ftn_ctx ctx, TdPlan& P) {
   size_t sa = P.ja.size() * sizeof(PermJob), sb = P.jb.size() * sizeof(PermJob), sc = P.jc.size() * sizeof(PermJob),
-         sp = P.probs.size() * sizeof(GemmProb);
-  size_t tot = sa + sb + sc + sp;
+         sp = P.probs.size() * sizeof(GemmProb), sr = P.red.size() * sizeof(GemmProb);
+  size_t tot = sa + sb + sc + sp + sr;
   std::vector<uint8_t> host(tot + 16);
   std::memcpy(host.data(), P.ja.data(), sa);
   std::memcpy(host.data() + sa, P.jb.data(), sb);
   std::memcpy(host.data() + sa + sb, P.jc.data(), sc);
   std::memcpy(host.data() + sa + sb + sc, P.probs.data(), sp);
+  if (sr) std::memcpy(host.data() + sa + sb + sc + sp, P.red.data(), sr);
   P.dev = std::make_shared<DevTables>();
   P.dev->ctx = ctx;
   void* d = nullptr;
@@ -106,6 +107,7 @@ static ftn_status upload_plan(ftn_ctx ctx, TdPlan& P) {
   P.d_jb = (PermJob*)(b + sa);
   P.d_jc = (PermJob*)(b + sa + sb);
   P.d_probs = (GemmProb*)(b + sa + sb + sc);
+  P.d_red = sr ? (GemmProb*)(b + sa + sb + sc + sp) : nullptr;
   return FTN_OK;
 }
 
@@ -278,7 +280,7 @@ static ftn_status build_plan(ftn_ctx ctx, const ftn_tensor_s* A, const ftn_tenso
     int pi = (popc(mB) & 1) ^ pB;
     maxN = std::max<int64_t>(maxN, colsz[pi][mB]);
   }
-  P->bn = tc ? tc_pick_bn(maxN, prec) : 64;
+  P->bn = tc ? tc_pick_bn(maxN, prec) : f64_pick_bn(maxN);
   for (int64_t b = 0; b < (int64_t)toff.size(); ++b) {
     uint32_t m = block_mask(cr, tmp.parity, b);
     uint32_t mA = m & ((1u << P->nfa) - 1u), mB = m >> P->nfa;
@@ -330,7 +332,7 @@ static ftn_status build_plan(ftn_ctx ctx, const ftn_tensor_s* A, const ftn_tenso
       g.tiles_n = (g.N + P->bn - 1) / P->bn;
     } else {
       g.tiles_m = (g.M + 63) / 64;
-      g.tiles_n = (g.N + 63) / 64;
+      g.tiles_n = (g.N + P->bn - 1) / P->bn;
     }
     P->probs.push_back(g);
   }
@@ -378,6 +380,7 @@ static ftn_status build_plan(ftn_ctx ctx, const ftn_tensor_s* A, const ftn_tenso
       g.tile_begin = P->gemm_tiles;
       P->gemm_tiles += (int64_t)g.tiles_m * g.tiles_n;
     }
+    P->part_elems = plan_splitk_f64(P->probs, ctx->num_sms, P->red, P->gemm_tiles, P->red_total);
   }
   // ---- the separate sign-permute of the result, when not fused ----
   if (!fuse) {
@@ -398,7 +401,8 @@ static ftn_status build_plan(ftn_ctx ctx, const ftn_tensor_s* A, const ftn_tenso
     P->sc = finalize_perm_jobs(P->jc, dtype_size(A->dtype), &P->tc, true);
   }
   if (!jobs_in_bounds(P->ja, A->numel, P->af_elems) || !jobs_in_bounds(P->jb, B->numel, P->bf_elems) ||
-      !probs_in_bounds(P->probs, P->af_elems, P->bf_elems, P->tmp_numel) ||
+      !probs_in_bounds(P->probs, P->af_elems, P->bf_elems, P->part_elems ? P->part_elems : P->tmp_numel) ||
+      (P->part_elems && !red_in_bounds(P->red, P->part_elems, P->tmp_numel)) ||
       (!P->fused && !jobs_in_bounds(P->jc, P->tmp_numel, P->tmp_numel)))
     return set_error(FTN_EINVAL, "internal error: contraction plan out of bounds");
   FTN_TRY(upload_plan(ctx, *P));
@@ -480,7 +484,8 @@ ftn_status tensordot_impl(ftn_ctx ctx, ftn_tensor A, ftn_tensor B, int n, const 
   auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
   const size_t a_b = al((size_t)P->af_elems * es), b_b = al((size_t)P->bf_elems * es);
   const size_t c_b = P->fused ? 0 : al((size_t)P->tmp_numel * dtype_size(A->dtype));
-  const size_t need = a_b * (split ? 2 : 1) + b_b * (split ? 2 : 1) + c_b;
+  const size_t p_b = al((size_t)P->part_elems * 8);
+  const size_t need = a_b * (split ? 2 : 1) + b_b * (split ? 2 : 1) + c_b + p_b;
   uint8_t* ws = (uint8_t*)workspace(ctx, need);
   if (!ws) {
     if (created) ftn_tensor_free(out);
@@ -515,8 +520,16 @@ ftn_status tensordot_impl(ftn_ctx ctx, ftn_tensor A, ftn_tensor B, int n, const 
     gb += (double)P->tmp_numel * in_es;
     if (!tc) {
       rec = prof_begin(ctx, "gemm_f64", gb, gemm_flops);
-      st = launch_gemm_f64(ctx, P->d_probs, (int)P->probs.size(), P->gemm_tiles, (const double*)af_hi,
-                           (const double*)bf_hi, (double*)ctmp);
+      if (P->part_elems) {
+        double* part = (double*)(ws + need - p_b);
+        st = launch_gemm_f64(ctx, P->d_probs, (int)P->probs.size(), P->gemm_tiles, (const double*)af_hi,
+                             (const double*)bf_hi, part, P->bn);
+        if (st == FTN_OK)
+          st = launch_splitk_reduce(ctx, P->d_red, (int)P->red.size(), P->red_total, part, (double*)ctmp);
+      } else {
+        st = launch_gemm_f64(ctx, P->d_probs, (int)P->probs.size(), P->gemm_tiles, (const double*)af_hi,
+                             (const double*)bf_hi, (double*)ctmp, P->bn);
+      }
       prof_end(ctx, rec);
     } else {
       TcOperands ops;
