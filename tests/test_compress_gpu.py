@@ -112,3 +112,86 @@ def test_compress_rank_deficient(F, ctx):
     assert sum(info.kept) <= 4
     got = O.contract(dense(xg), dense(yg), [xg.rank - 1], [0])
     assert np.max(np.abs(got.data - exact.data)) <= 1e-10 * np.max(np.abs(exact.data))
+
+
+def _low_rank_blocks(g, legs, parity, inner, noise=0.0):
+    out = []
+    for bits in W.block_bits(legs, parity):
+        shp = W.block_shape(legs, bits)
+        blk = g.standard_normal((shp[0], inner)) @ g.standard_normal((inner, shp[1]))
+        if noise:
+            blk = blk + noise * g.standard_normal(shp)
+        out.append((bits, blk))
+    return out
+
+
+def test_compress_zero_bond_columns(F, ctx):
+    """Bond states that X never reaches: the Gram matrix has zero rows and
+    columns, the R factor exact zero rows; the core is formed from the
+    nonzero rows only and the result matches the oracle."""
+    g = W.rng(21)
+    lx = [(40, 36, 0), (24, 20, 1)]
+    bx = []
+    for bits in W.block_bits(lx, 0):
+        blk = g.standard_normal(W.block_shape(lx, bits))
+        blk[:, ::3] = 0.0  # every third bond state unused
+        bx.append((bits, blk))
+    ly = [(24, 20, 0), (30, 31, 1)]
+    by = W.random_blocks(ly, 0, 22)
+    X, Y = O.embed_blocks(lx, 0, bx), O.embed_blocks(ly, 0, by)
+    for chi in (5, 10**6):
+        xr, yr, info_r = O.compress(X, Y, [1], [0], chi)
+        ref = O.contract(xr, yr, [1], [0])
+        xg, yg, info = F.compress(ctx, F.Tensor.from_blocks(ctx, lx, 0, bx), F.Tensor.from_blocks(ctx, ly, 0, by),
+                                  [1], [0], chi)
+        got = O.contract(dense(xg), dense(yg), [1], [0])
+        assert np.max(np.abs(got.data - ref.data)) <= 1e-10 * np.max(np.abs(ref.data))
+        if chi == 5:
+            assert tuple(info.kept) == tuple(info_r["kept"])
+        else:
+            assert sum(info.kept) == 16 + 13  # the numerical rank: nonzero bond states per sector
+
+
+@pytest.mark.parametrize("noise", [0.0, 1e-15])
+def test_compress_rounding_level_rank_deficiency(F, ctx, noise):
+    """A bond of 64 + 64 states carried by rank-6 sectors (plus optional
+    rounding-level noise): rows of the core at the rounding level are
+    numerically zero for the Jacobi; the kept part and the product match."""
+    g = W.rng(31)
+    lx = [(150, 140, 0), (64, 64, 1)]
+    ly = [(64, 64, 0), (70, 90, 1)]
+    bx = _low_rank_blocks(g, lx, 0, 6, noise)
+    by = W.random_blocks(ly, 0, 32)
+    X, Y = O.embed_blocks(lx, 0, bx), O.embed_blocks(ly, 0, by)
+    exact = O.contract(X, Y, [1], [0])
+    for chi in (8, 10**6):
+        xr, yr, info_r = O.compress(X, Y, [1], [0], chi)
+        ref = O.contract(xr, yr, [1], [0])
+        xg, yg, info = F.compress(ctx, F.Tensor.from_blocks(ctx, lx, 0, bx), F.Tensor.from_blocks(ctx, ly, 0, by),
+                                  [1], [0], chi)
+        got = O.contract(dense(xg), dense(yg), [1], [0])
+        assert np.max(np.abs(got.data - ref.data)) <= 1e-10 * np.max(np.abs(ref.data))
+        assert info.jacobi_sweeps < 40
+        if chi == 8:
+            assert tuple(info.kept) == tuple(info_r["kept"])
+        else:
+            assert sum(info.kept) == 12
+            assert np.max(np.abs(got.data - exact.data)) <= 1e-10 * np.max(np.abs(exact.data))
+
+
+@pytest.mark.parametrize("chi", [40, 10**6])
+def test_compress_wide_bond_cluster_jacobi(F, ctx, chi):
+    """A 128 + 128 bond between two tall full-rank sides: 128 x 128 cores,
+    rotated by a 16-CTA cluster."""
+    lx = [(300, 260, 0), (128, 128, 1)]
+    ly = [(128, 128, 0), (280, 270, 1)]
+    bx, by = W.random_blocks(lx, 0, 41), W.random_blocks(ly, 0, 42)
+    X, Y = O.embed_blocks(lx, 0, bx), O.embed_blocks(ly, 0, by)
+    xr, yr, info_r = O.compress(X, Y, [1], [0], chi)
+    ref = O.contract(xr, yr, [1], [0])
+    xg, yg, info = F.compress(ctx, F.Tensor.from_blocks(ctx, lx, 0, bx), F.Tensor.from_blocks(ctx, ly, 0, by), [1],
+                              [0], chi)
+    got = O.contract(dense(xg), dense(yg), [1], [0])
+    assert np.max(np.abs(got.data - ref.data)) <= 1e-10 * np.max(np.abs(ref.data))
+    assert tuple(info.kept) == tuple(info_r["kept"])
+    assert abs(info.discarded_sq - info_r["discarded_sq"]) <= 1e-10 * info.total_sq

@@ -213,3 +213,32 @@ def test_misaligned_wrapped_input_uses_fallback_permute(F, ctx):
         want = O.transpose(dense(a0.to_blocks(), a0.legs, 0), list(reversed(range(len(case["legs_a"])))))
         assert np.array_equal(dense(t.to_blocks(), t.legs, t.parity).data, want.data)
     ctx.synchronize()
+
+
+NARROW = [
+    # (A legs, B legs, axes A, axes B, out_perm): long contracted legs, few
+    # output tiles (split-K with the ordered slab reduction) and narrow
+    # column blocks (16- and 32-wide FP64 tiles); ragged sizes throughout
+    ([(9, 7, 0), (64, 50, 1), (3, 2, 0)], [(64, 50, 0), (5, 6, 1)], [1], [0], None),
+    ([(9, 7, 0), (64, 50, 1), (3, 2, 0)], [(64, 50, 0), (5, 6, 1)], [1], [0], [2, 0, 1]),
+    ([(17, 15, 1), (40, 33, 0), (2, 3, 1)], [(2, 3, 0), (40, 33, 1), (20, 12, 0)], [1, 2], [1, 0], [1, 0]),
+    ([(130, 70, 0), (8, 9, 1), (4, 4, 0)], [(8, 9, 0), (4, 4, 1), (30, 29, 1)], [1, 2], [0, 1], None),
+    ([(3, 1, 0), (2, 2, 1), (96, 64, 0)], [(96, 64, 1), (2, 2, 0), (45, 50, 1)], [2, 1], [0, 1], [1, 0]),
+]
+
+
+@pytest.mark.parametrize("ci", range(len(NARROW)))
+@pytest.mark.parametrize("parity", [(0, 0), (1, 0), (1, 1)])
+def test_tensordot_f64_splitk_and_narrow_tiles(F, ctx, ci, parity):
+    la, lb, ax, ay, perm = NARROW[ci]
+    pa, pb = parity
+    ba, bb = W.random_blocks(la, pa, 300 + ci), W.random_blocks(lb, pb, 400 + ci)
+    ref = O.contract(dense(ba, la, pa), dense(bb, lb, pb), ax, ay)
+    if perm is not None:
+        ref = O.transpose(ref, perm)
+    a, b = upload(F, ctx, la, pa, ba, "f64"), upload(F, ctx, lb, pb, bb, "f64")
+    for _ in range(2):  # the second call runs from the cached plan
+        c = F.tensordot(ctx, a, b, ax, ay, out_perm=perm, prec="f64")
+        got = dense(c.to_blocks(), c.legs, c.parity)
+        assert c.legs == ref.legs and c.parity == ref.parity
+        assert relerr(got.data, ref.data) <= TOL["f64"]
