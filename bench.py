@@ -384,29 +384,42 @@ ENERGY_WORKLOAD = ("Hubbard fPEPS energy <H>/<Psi|Psi> on a 4x4 open square latt
                    "24 hopping + 16 on-site terms + the norm = 41 contractions per evaluation")
 
 
-def energy_bench(F, ctx, evals, with_oracle):
+def energy_bench(F, ctx, evals, with_oracle, workers=8):
     """fPEPS energy evaluations per second, FP64 and mixed (TF32x3 GEMMs with
-    FP64 compression), and their errors."""
+    FP64 compression), and their errors.  The 41 contractions of an
+    evaluation are independent: `workers` contexts on their own streams run
+    them concurrently (the value is the same as a sequential run)."""
+    import torch
+
     from paper_2410_02215_gb300 import peps
+
+    ctxs = [ctx] + [F.Context(stream=torch.cuda.Stream()) for _ in range(max(workers, 1) - 1)]
 
     n, edges = W.square_lattice(4, 4)
     lay = W.peps_layout(n, edges, (2, 2), (2, 2))
     blocks = W.random_peps(lay, 1)
     st = W.site_sweep_tree(list(range(n)))
     tf = lambda ops: W.double_layer_tree(n, st, ops)  # noqa: E731
-    out = {"workload": ENERGY_WORKLOAD}
+    out = {"workload": ENERGY_WORKLOAD, "streams": len(ctxs)}
     res = {}
     for prec, dt in (("f64", F.F64), ("tf32x3", F.F32)):
         kets = [F.Tensor.from_blocks(ctx, lay["legs"][s_], 0, blocks[s_], dt) for s_ in range(n)]
-        e, _, _ = peps.energy(ctx, lay, kets, 1.0, 8.0, tf, policy="late", chi=32, prec=prec)  # warm-up (plans)
-        l0 = ctx.launches()
+        ctx.synchronize()
+        for c in ctxs:  # warm-up: every context builds its plans
+            e, _, _ = peps.energy(c, lay, kets, 1.0, 8.0, tf, policy="late", chi=32, prec=prec)
+        e1, _, _ = peps.energy(ctx, lay, kets, 1.0, 8.0, tf, policy="late", chi=32, prec=prec)
+        t0 = time.perf_counter()
+        e1, _, _ = peps.energy(ctx, lay, kets, 1.0, 8.0, tf, policy="late", chi=32, prec=prec)
+        one_s = time.perf_counter() - t0
+        l0 = sum(c.launches() for c in ctxs)
         t0 = time.perf_counter()
         for _ in range(evals):
-            e, _, _ = peps.energy(ctx, lay, kets, 1.0, 8.0, tf, policy="late", chi=32, prec=prec)
+            e, _, _ = peps.energy(ctxs, lay, kets, 1.0, 8.0, tf, policy="late", chi=32, prec=prec)
         dt_s = time.perf_counter() - t0
         res[prec] = e
         out[prec] = {"evals_per_s": evals / dt_s, "s_per_eval": dt_s / evals, "energy": e,
-                     "gpu_launches_per_eval": (ctx.launches() - l0) / evals}
+                     "gpu_launches_per_eval": (sum(c.launches() for c in ctxs) - l0) / evals,
+                     "one_stream_s_per_eval": one_s, "same_as_one_stream": e == e1}
     out["mixed_vs_f64_rel_err"] = abs(res["tf32x3"] - res["f64"]) / abs(res["f64"])
     out["speedup_mixed_vs_f64"] = out["tf32x3"]["evals_per_s"] / out["f64"]["evals_per_s"]
     if with_oracle:
@@ -418,6 +431,9 @@ def energy_bench(F, ctx, evals, with_oracle):
         out["oracle_s_per_eval"] = time.perf_counter() - t0
         out["f64_rel_err_vs_oracle"] = abs(res["f64"] - e_ref) / abs(e_ref)
         out["tf32x3_rel_err_vs_oracle"] = abs(res["tf32x3"] - e_ref) / abs(e_ref)
+    for c in ctxs[1:]:
+        c.synchronize()
+        c.close()
     return out
 
 
@@ -476,7 +492,8 @@ def run_ours(args, rank, world, local):
     if not args.no_e2e:
         result["e2e"] = e2e_run(F, ctx, torch, cases, args.prec, max(2, min(args.steps, 5)), flops_step)
     if not args.no_energy:
-        result["energy"] = energy_bench(F, ctx, args.energy_evals, rank == 0 and world == 1 and not args.no_cpu)
+        result["energy"] = energy_bench(F, ctx, args.energy_evals, rank == 0 and world == 1 and not args.no_cpu,
+                                        args.energy_streams)
     if rank == 0 and world == 1 and not args.no_cpu:
         result["cpu_baseline"] = cpu_baseline(cases)
     ctx.synchronize()
@@ -499,6 +516,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-energy", action="store_true")
     ap.add_argument("--energy-evals", type=int, default=3)
+    ap.add_argument("--energy-streams", type=int, default=8,
+                    help="contexts (CUDA streams) that run an evaluation's contractions concurrently")
     ap.add_argument("--no-accuracy", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:

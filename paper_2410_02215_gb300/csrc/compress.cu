@@ -19,6 +19,7 @@
 // R factors.
 #include <algorithm>
 #include <cmath>
+#include <mutex>
 
 #include "ptx.cuh"
 #include "tdplan.h"
@@ -604,8 +605,10 @@ ftn_status setup_svd_cluster(int* cmax) {
 // Largest cluster size the Jacobi kernel uses on this device (16 where
 // non-portable clusters of that size fit, else the portable 8).
 int svd_cluster_max(ftn_ctx ctx) {
+  static std::mutex mu;
   static int cmax[64] = {0};
-  const int dev = ctx->device < 64 ? ctx->device : 0;
+  const int dev = ctx->device >= 0 && ctx->device < 64 ? ctx->device : 0;
+  std::lock_guard<std::mutex> lock(mu);
   if (!cmax[dev]) {
     int c = 8;
     if (setup_svd_cluster<1>(&c) != FTN_OK || setup_svd_cluster<2>(&c) != FTN_OK ||

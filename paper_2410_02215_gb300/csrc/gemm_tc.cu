@@ -354,14 +354,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
 
 // ---- host side -------------------------------------------------------------------
 static PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
-  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-  if (!fn) {
+  // resolved once; static initialisation is thread-safe
+  static const PFN_cuTensorMapEncodeTiled_v12000 fn = []() -> PFN_cuTensorMapEncodeTiled_v12000 {
     void* p = nullptr;
     cudaDriverEntryPointQueryResult q;
     if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
         q == cudaDriverEntryPointSuccess)
-      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
-  }
+      return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    return nullptr;
+  }();
   return fn;
 }
 
@@ -400,13 +401,9 @@ static ftn_status run(ftn_ctx ctx, const TcOperands& ops, const GemmProb* d_prob
   P.err = ctx->dev_err;
   P.tiles = tiles;
   P.nprobs = nprobs;
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel<BF16, SPLIT, BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         Cfg::SMEM);
-    if (e != cudaSuccess) return cuda_error(e, "cudaFuncSetAttribute(tc_gemm)");
-    attr_set = true;
-  }
+  static const cudaError_t attr = cudaFuncSetAttribute(tc_gemm_kernel<BF16, SPLIT, BN>,
+                                                       cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM);
+  if (attr != cudaSuccess) return cuda_error(attr, "cudaFuncSetAttribute(tc_gemm)");
   int64_t grid = tiles < ctx->num_sms ? tiles : ctx->num_sms;
   tc_gemm_kernel<BF16, SPLIT, BN><<<(unsigned)grid, TC_THREADS, Cfg::SMEM, ctx->stream>>>(P);
   ctx->launches += 1;

@@ -437,13 +437,9 @@ template <typename Tin, int MODE>
 static cudaError_t go_staged(ftn_ctx ctx, const PermJob* d_jobs, int njobs, int64_t tiles, const void* src,
                              void* dst0, void* dst1) {
   using Cfg = StagedCfg<Tin>;
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(perm_staged_kernel<Tin, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         Cfg::BYTES);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
+  static const cudaError_t attr =
+      cudaFuncSetAttribute(perm_staged_kernel<Tin, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::BYTES);
+  if (attr != cudaSuccess) return attr;
   int64_t grid = tiles;
   int64_t cap = (int64_t)ctx->num_sms * 3;
   if (grid > cap) grid = cap;

@@ -3,6 +3,7 @@
 // (Eq. transposition): block-pair planning, per-block signs and the fused
 // sector-matrix layout of Sec. IV.A, then sign-permute + grouped GEMM.
 #include <algorithm>
+#include <mutex>
 #include <sstream>
 
 #include "tdplan.h"
@@ -111,8 +112,15 @@ static ftn_status upload_plan(ftn_ctx ctx, TdPlan& P) {
   return FTN_OK;
 }
 
+// Plan caches are per context.  The maps from context to cache are shared
+// by all host threads, so lookups and erasures take a lock; a cache itself
+// is used only by the thread that drives its context (one host thread per
+// context at a time), and std::map nodes do not move on insertion.
+static std::mutex g_cache_mu;
+
 static std::map<std::string, std::shared_ptr<TdPlan>>& plan_cache(ftn_ctx ctx) {
   static std::map<ftn_ctx, std::map<std::string, std::shared_ptr<TdPlan>>> caches;
+  std::lock_guard<std::mutex> lock(g_cache_mu);
   return caches[ctx];
 }
 
@@ -572,6 +580,7 @@ struct TrPlan {
 
 static std::map<std::string, std::shared_ptr<TrPlan>>& tr_cache(ftn_ctx ctx) {
   static std::map<ftn_ctx, std::map<std::string, std::shared_ptr<TrPlan>>> caches;
+  std::lock_guard<std::mutex> lock(g_cache_mu);
   return caches[ctx];
 }
 

@@ -71,25 +71,68 @@ def term_network(layout, kets, bras, op, sites):
 def energy(ctx, layout, kets, t, u, tree_fn, mode="local", policy="exact", chi=0, prec="f64"):
     """sum_t <h_t>/<Psi|Psi> over all nearest-neighbour hopping and on-site
     terms; each term and the norm are contracted with tree_fn(op_sites).
-    Returns (energy, norm mantissa, norm log-scale)."""
+    Returns (energy, norm mantissa, norm log-scale).
+
+    ``ctx`` may be a list of contexts (each on its own stream): the norm and
+    the terms are independent contractions, so host threads, one per
+    context, take them from a shared counter and run them concurrently on
+    the GPU.  The kets, bras and operator tensors belong to the first
+    context and are only read by the others.  The sum runs in term order,
+    so the result does not depend on the schedule."""
+    ctxs = list(ctx) if isinstance(ctx, (list, tuple)) else [ctx]
+    c0 = ctxs[0]
     dt = ftn.F64 if prec == "f64" else ftn.F32
     n = layout["n"]
-    bras = [ftn.dagger(ctx, k) for k in kets]
-    tens, bonds, pos = norm_network(ctx, layout, kets, bras)
+    bras = [ftn.dagger(c0, k) for k in kets]
     glob = mode == "global"
-    nm, nl = ftn.contract(ctx, tens, bonds, tree_fn(()), positions=pos if glob else None, policy=policy, chi=chi,
-                          prec=prec)
-    hop = ftn.hubbard_term(ctx, 0, t, 0.0, dt)
-    onsite = ftn.hubbard_term(ctx, 1, 0.0, u, dt)
-    total = 0.0
+    hop = ftn.hubbard_term(c0, 0, t, 0.0, dt)
+    onsite = ftn.hubbard_term(c0, 1, 0.0, u, dt)
+    jobs = []
+    tens, bonds, pos = norm_network(c0, layout, kets, bras)
+    jobs.append((tens, bonds, pos, tree_fn(())))
     for a, b in layout["edges"]:
         tens, bonds, pos = term_network(layout, kets, bras, hop, (a, b))
-        m, lg = ftn.contract(ctx, tens, bonds, tree_fn((a, b)), positions=pos if glob else None, policy=policy,
-                             chi=chi, prec=prec)
-        total += m / nm * math.exp(lg - nl)
+        jobs.append((tens, bonds, pos, tree_fn((a, b))))
     for s in range(n):
         tens, bonds, pos = term_network(layout, kets, bras, onsite, (s,))
-        m, lg = ftn.contract(ctx, tens, bonds, tree_fn((s,)), positions=pos if glob else None, policy=policy, chi=chi,
-                             prec=prec)
+        jobs.append((tens, bonds, pos, tree_fn((s,))))
+
+    def run(c, job):
+        tens, bonds, pos, tree = job
+        return ftn.contract(c, tens, bonds, tree, positions=pos if glob else None, policy=policy, chi=chi, prec=prec)
+
+    if len(ctxs) == 1:
+        results = [run(c0, job) for job in jobs]
+    else:
+        import threading
+
+        c0.synchronize()  # inputs ready before other streams read them
+        results = [None] * len(jobs)
+        errors = []
+        lock = threading.Lock()
+        nxt = [0]
+
+        def worker(c):
+            try:
+                while True:
+                    with lock:
+                        i = nxt[0]
+                        nxt[0] += 1
+                    if i >= len(jobs) or errors:
+                        return
+                    results[i] = run(c, jobs[i])
+            except BaseException as e:  # re-raised on the calling thread
+                errors.append(e)
+
+        threads = [threading.Thread(target=worker, args=(c,)) for c in ctxs]
+        for th in threads:
+            th.start()
+        for th in threads:
+            th.join()
+        if errors:
+            raise errors[0]
+    nm, nl = results[0]
+    total = 0.0
+    for m, lg in results[1:]:
         total += m / nm * math.exp(lg - nl)
     return total, nm, nl

@@ -141,3 +141,26 @@ def test_energy_4x4_compressed_fp64_and_mixed(F, ctx):
     k32 = gpu_kets(F, ctx, lay, blocks, F.F32)
     e32, _, _ = peps.energy(ctx, lay, k32, 1.0, 8.0, tf, policy="late", chi=32, prec="tf32x3")
     assert abs(e32 - e64) <= 1e-6 * abs(e64)
+
+
+def test_energy_concurrent_streams_match_sequential(F, ctx):
+    """The norm and the terms run concurrently on three contexts with their
+    own streams: the same value, bit for bit, as one context."""
+    import torch
+
+    from paper_2410_02215_gb300 import peps
+
+    n, edges, lay, blocks = setup(3, 3, (1, 1), 2)
+    st = W.site_sweep_tree(list(range(n)))
+    tf = lambda ops: W.double_layer_tree(n, st, ops)  # noqa: E731
+    kets = gpu_kets(F, ctx, lay, blocks, F.F64)
+    e1, nm1, nl1 = peps.energy(ctx, lay, kets, 1.0, 8.0, tf, policy="late", chi=8)
+    extra = [F.Context(stream=torch.cuda.Stream()) for _ in range(2)]
+    try:
+        for _ in range(2):
+            e3, nm3, nl3 = peps.energy([ctx] + extra, lay, kets, 1.0, 8.0, tf, policy="late", chi=8)
+            assert (e3, nm3, nl3) == (e1, nm1, nl1)
+    finally:
+        for c in extra:
+            c.synchronize()
+            c.close()
