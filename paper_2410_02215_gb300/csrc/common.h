@@ -30,6 +30,10 @@ constexpr int DEV_ERR_TIMEOUT = 1;
 // 16-byte aligned rows) and a register-staged fallback with fixed 32 x 64
 // tiles.  finalize_perm_jobs() picks the kernel and the tiling.
 constexpr int PERM_TI = 32;   // fallback tile: I extent
+constexpr int PERM_GROUP_MIN = 32;   // I group (source-contiguous suffix): at least this many elements,
+constexpr int PERM_GROUP_I = 128;    // grown further towards this many (never past PERM_GROUP_IMAX)
+constexpr int PERM_GROUP_IMAX = 256;  // largest I grown beyond the minimum (whole in a tile for FP64 too)
+constexpr int PERM_GROUP_O = 32;     // contiguous destination elements kept for the rows of a tile
 constexpr int PERM_TO = 64;   // fallback tile: O extent
 constexpr int PERM_TILE_BYTES = 16384;  // staged tile payload
 constexpr int PERM_MAX_ROWS = 128;
@@ -48,6 +52,10 @@ struct PermJob {
   int32_t ti, tr;        // tile extents (I, O)
   int32_t bulk_ok;       // rows are 16-byte aligned with 16-byte multiple sizes
   int32_t vec4;          // quads along the store direction are contiguous and 4-element aligned
+  int32_t iwrite;        // staged kernel: stores run along I in destination order (I whole in a tile)
+  int32_t wmask;         // I legs (bit l = l-th I leg) forming the destination's contiguous run
+  int32_t qw;            // elements of that run (product of the wmask legs)
+  int32_t wsuf;          // the run is the innermost I legs in the same order: source columns run with it
   int32_t dim[MAXR];     // I legs (source order), then O legs, then B legs
   int64_t sstr[MAXR];    // source strides
   int64_t dstr[MAXR];    // destination strides

@@ -211,6 +211,7 @@ struct StageMeta {
   int32_t nrows, ncols;
   int32_t ti, fast_i;
   int32_t sign, vec4;
+  int32_t iwrite, qw, qp, wsuf;
 };
 
 template <typename Tin>
@@ -220,16 +221,17 @@ struct StagedCfg {
   static constexpr int MAXTI = TE / 8;
   static constexpr int STAGE_ELEMS = TE + PERM_MAX_ROWS * V;
   static constexpr int BYTES = PERM_STAGES * STAGE_ELEMS * (int)sizeof(Tin) + PERM_STAGES * PERM_MAX_ROWS * 4 +
-                               PERM_STAGES * MAXTI * 4 + PERM_STAGES * (int)sizeof(StageMeta) + 2 * PERM_STAGES * 8 +
-                               2 * (int)sizeof(PermJob) + 128;
+                               PERM_STAGES * MAXTI * 4 + PERM_STAGES * MAXTI * 2 * 2 +
+                               PERM_STAGES * (int)sizeof(StageMeta) + 2 * PERM_STAGES * 8 + 2 * (int)sizeof(PermJob) +
+                               128;
 };
 
 // Issue the bulk copies of tile t (producer warp; `j` is the tile's job,
 // cached in shared memory by the caller).
 template <typename Tin>
 __device__ __forceinline__ void staged_issue(const PermJob* j, int64_t t, const Tin* __restrict__ src, Tin* buf,
-                                             int32_t* rowD, int32_t* colD, StageMeta* meta, uint64_t* bar,
-                                             int lane) {
+                                             int32_t* rowD, int32_t* colD, int16_t* colS, int16_t* colP,
+                                             StageMeta* meta, uint64_t* bar, int lane) {
   using Cfg = StagedCfg<Tin>;
   const int nI = j->nI, nO = j->nO;
   const int64_t local = t - j->tile_begin;
@@ -270,16 +272,46 @@ __device__ __forceinline__ void staged_issue(const PermJob* j, int64_t t, const 
     rsrc[u] = rs;
     mine += (uint32_t)(ncols * sizeof(Tin));
   }
-  for (int c = lane; c < ncols; c += 32) {
-    int x = i0 + c;
-    int32_t dd = 0;
-    for (int q = nI - 1; q >= 0; --q) {
-      const int d = j->dim[q];
-      const int qq = x / d, idx = x - qq * d;
-      x = qq;
-      dd += idx * (int32_t)j->dstr[q];
+  int32_t qp = 1;
+  if (j->iwrite) {
+    // the whole I group is in the tile (i0 = 0).  W (the destination run):
+    // colS[q] = source column of the q-th element of the run (its legs'
+    // destination strides are the run's own mixed radix).  P (the other I
+    // legs, last fastest): colP[p] = source column, colD[p] = destination
+    // offset of the p-th combination.
+    for (int q = lane; q < j->qw; q += 32) {
+      int32_t cs = 0;
+      for (int l = 0; l < nI; ++l)
+        if (j->wmask >> l & 1) cs += ((q / (int32_t)j->dstr[l]) % j->dim[l]) * (int32_t)j->sstr[l];
+      colS[q] = (int16_t)cs;
     }
-    colD[c] = dd;
+    qp = ncols / j->qw;
+    for (int p = lane; p < qp; p += 32) {
+      int x = p;
+      int32_t cs = 0, dd = 0;
+      for (int l = nI - 1; l >= 0; --l) {
+        if (j->wmask >> l & 1) continue;
+        const int d = j->dim[l];
+        const int qq = x / d, idx = x - qq * d;
+        x = qq;
+        cs += idx * (int32_t)j->sstr[l];
+        dd += idx * (int32_t)j->dstr[l];
+      }
+      colP[p] = (int16_t)cs;
+      colD[p] = dd;
+    }
+  } else {
+    for (int c = lane; c < ncols; c += 32) {
+      int x = i0 + c;
+      int32_t dd = 0;
+      for (int q = nI - 1; q >= 0; --q) {
+        const int d = j->dim[q];
+        const int qq = x / d, idx = x - qq * d;
+        x = qq;
+        dd += idx * (int32_t)j->dstr[q];
+      }
+      colD[c] = dd;
+    }
   }
   if (lane == 0) {
     meta->baseD = bD;
@@ -289,6 +321,10 @@ __device__ __forceinline__ void staged_issue(const PermJob* j, int64_t t, const 
     meta->fast_i = j->store_fast_i;
     meta->sign = j->sign;
     meta->vec4 = j->vec4;
+    meta->iwrite = j->iwrite;
+    meta->qw = j->qw;
+    meta->qp = qp;
+    meta->wsuf = j->wsuf;
   }
   // order this warp's earlier generic reads of the stage before the async writes
   fence_proxy_async_smem();
@@ -314,7 +350,9 @@ __global__ void __launch_bounds__(SPT) perm_staged_kernel(const PermJob* __restr
   Tin* buf = reinterpret_cast<Tin*>(sm);
   int32_t* rowD = reinterpret_cast<int32_t*>(buf + PERM_STAGES * Cfg::STAGE_ELEMS);
   int32_t* colD = rowD + PERM_STAGES * PERM_MAX_ROWS;
-  StageMeta* meta = reinterpret_cast<StageMeta*>(colD + PERM_STAGES * Cfg::MAXTI);
+  int16_t* colS = reinterpret_cast<int16_t*>(colD + PERM_STAGES * Cfg::MAXTI);
+  int16_t* colP = colS + PERM_STAGES * Cfg::MAXTI;
+  StageMeta* meta = reinterpret_cast<StageMeta*>(colP + PERM_STAGES * Cfg::MAXTI);
   uint64_t* full = reinterpret_cast<uint64_t*>(meta + PERM_STAGES);
   uint64_t* empty = full + PERM_STAGES;
   PermJob* sjob_all = reinterpret_cast<PermJob*>(empty + PERM_STAGES);  // each producer's copy of its job
@@ -373,7 +411,7 @@ __global__ void __launch_bounds__(SPT) perm_staged_kernel(const PermJob* __restr
         break;
       }
       staged_issue<Tin>(sjob, t, src, buf + s * Cfg::STAGE_ELEMS, rowD + s * PERM_MAX_ROWS, colD + s * Cfg::MAXTI,
-                        meta + s, &full[s], lane);
+                        colS + s * Cfg::MAXTI, colP + s * Cfg::MAXTI, meta + s, &full[s], lane);
     }
     // after an early exit, wait for this producer's copies still in flight (on
     // a normal exit the consumers wait for every issued tile themselves)
@@ -396,7 +434,48 @@ __global__ void __launch_bounds__(SPT) perm_staged_kernel(const PermJob* __restr
     const int32_t* cd = colD + s * Cfg::MAXTI;
     const int stride = m.ti + Cfg::V;
     const Tin sgn = (Tin)m.sign;
-    if (m.vec4 && m.fast_i) {
+    if (m.iwrite) {
+      // destination order along I: every (row, P) pair owns a contiguous run
+      // of qw destination elements, gathered from the stage by colS (or read
+      // straight when the run is the innermost I legs in order)
+      const int16_t* csw = colS + s * Cfg::MAXTI;
+      const int16_t* csp = colP + s * Cfg::MAXTI;
+      const int npairs = m.nrows * m.qp;
+      const int qps = (m.qp & (m.qp - 1)) == 0 ? __ffs(m.qp) - 1 : -1;
+      const int vq = m.vec4 ? 4 : 1, units = m.qw / vq;
+      const bool grouped = units < 32 && (units & (units - 1)) == 0;
+      const int lg = grouped ? __ffs(units) - 1 : 5, per = grouped ? 32 >> lg : 1;
+      const int sub = grouped ? lane >> lg : 0;
+      const int q0 = grouped ? (lane & (units - 1)) * vq : lane * vq;
+      const int qstep = grouped ? m.qw : 32 * vq;
+      for (int rp0 = warp * per; rp0 < npairs; rp0 += NCW * per) {
+        const int rp = rp0 + sub;
+        if (rp >= npairs) continue;
+        int r, p;
+        if (qps >= 0) {
+          r = rp >> qps;
+          p = rp & (m.qp - 1);
+        } else {
+          r = rp / m.qp;
+          p = rp - r * m.qp;
+        }
+        const Tin* x = tb + r * stride + csp[p];
+        const int64_t base = m.baseD + rd[r] + cd[p];
+        for (int q = q0; q < m.qw; q += qstep) {
+          if (vq == 4) {
+            Tin a, b, c, d;
+            if (m.wsuf) {
+              a = x[q], b = x[q + 1], c = x[q + 2], d = x[q + 3];
+            } else {
+              a = x[csw[q]], b = x[csw[q + 1]], c = x[csw[q + 2]], d = x[csw[q + 3]];
+            }
+            put4<Tin, MODE>(dst0, dst1, base + q, sgn * a, sgn * b, sgn * c, sgn * d);
+          } else {
+            put<Tin, MODE>(dst0, dst1, base + q, sgn * x[m.wsuf ? q : csw[q]]);
+          }
+        }
+      }
+    } else if (m.vec4 && m.fast_i) {
       // quads of consecutive I elements, contiguous in the destination
       for (int r = warp; r < m.nrows; r += NCW) {
         const int64_t base = m.baseD + rd[r];

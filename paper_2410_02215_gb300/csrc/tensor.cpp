@@ -145,17 +145,89 @@ void add_perm_job(std::vector<PermJob>& jobs, int64_t& tiles, int rank, const in
     sstr[k] = s;
     s *= dims[k];
   }
-  // I group: source suffix with product >= PERM_TI
+  // Tile groups.  I: a suffix of the source, read as contiguous rows (the
+  // tile's columns); O: legs by increasing destination stride (the tile's
+  // rows); B: the rest (batch).  I takes at least PERM_GROUP_MIN elements.
+  // The destination's contiguous run (its unit-stride leg, then the legs
+  // continuing it) is written either along I, in destination order, as far
+  // as it lies inside I (I grown to take the unit-stride leg), or along O,
+  // as far as it lies outside I (the run's legs kept out of I); the plan
+  // with the longer run wins.  I grows further towards PERM_GROUP_I (at
+  // most PERM_GROUP_IMAX) without breaking the chosen run.
+  std::vector<int> by_d(r);
+  for (int k = 0; k < r; ++k) by_d[k] = k;
+  std::stable_sort(by_d.begin(), by_d.end(), [&](int a, int b) { return dstr[a] < dstr[b]; });
+  const int fleg = by_d[0];
+  std::vector<int> chain;  // the destination's contiguous run, fastest first
+  if (dstr[fleg] == 1) {
+    int64_t run = 1;
+    for (;;) {
+      int nxt = -1;
+      for (int k = 0; k < r; ++k)
+        if (dstr[k] == run && std::find(chain.begin(), chain.end(), k) == chain.end()) nxt = k;
+      if (nxt < 0) break;
+      chain.push_back(nxt);
+      run *= dims[nxt];
+    }
+  }
+  auto prod = [&](int from) {
+    int64_t p = 1;
+    for (int k = from; k < r; ++k) p *= dims[k];
+    return p;
+  };
+  auto run_in = [&](int from) {  // run length along I = [from, r)
+    int64_t p = 1;
+    for (int k : chain) {
+      if (k < from) break;
+      p *= dims[k];
+    }
+    return p;
+  };
+  auto run_out = [&](int from) {  // run length along O (legs below from)
+    int64_t p = 1;
+    for (int k : chain) {
+      if (k >= from) break;
+      p *= dims[k];
+    }
+    return p;
+  };
   int iI = r;
-  int64_t PI = 1;
-  while (iI > 0 && PI < PERM_TI) {
-    --iI;
-    PI *= dims[iI];
+  while (iI > 0 && prod(iI) < PERM_GROUP_MIN) --iI;
+  // plan along I: I reaches down to the unit-stride leg
+  int iB = std::min(iI, fleg);
+  const bool b_ok = prod(iB) <= PERM_GROUP_IMAX || iB == iI;
+  if (b_ok)
+    while (iB > 0 && prod(iB) < PERM_GROUP_I && prod(iB - 1) <= PERM_GROUP_IMAX) --iB;
+  // plan along O: the run's legs stay out of I
+  int iA = iI;
+  if (fleg < iI) {
+    std::vector<char> keep(r, 0);
+    int64_t po = 1;
+    for (int k : by_d) {
+      if (po >= PERM_GROUP_O) break;
+      if (k >= iA) continue;
+      keep[k] = 1;
+      po *= dims[k];
+    }
+    while (iA > 0 && prod(iA) < PERM_GROUP_I && prod(iA - 1) <= PERM_GROUP_IMAX && !keep[iA - 1]) --iA;
+  }
+  if (fleg >= iI || (b_ok && run_in(iB) > run_out(iA)))
+    iI = iB;
+  else
+    iI = iA;
+  const int64_t PI = prod(iI);
+  // W: the part of the run inside I (the I legs are job legs 0..nI-1 in source order)
+  int32_t wmask = 0;
+  int64_t qw = 1;
+  for (int k : chain) {
+    if (k < iI) break;
+    wmask |= 1 << (k - iI);
+    qw *= dims[k];
   }
   // O group: remaining legs by increasing destination stride
   std::vector<int> rest;
-  for (int k = 0; k < iI; ++k) rest.push_back(k);
-  std::stable_sort(rest.begin(), rest.end(), [&](int a, int b) { return dstr[a] < dstr[b]; });
+  for (int k : by_d)
+    if (k < iI) rest.push_back(k);
   std::vector<int> O, B;
   int64_t PO = 1;
   for (int k : rest) {
@@ -198,10 +270,19 @@ void add_perm_job(std::vector<PermJob>& jobs, int64_t& tiles, int rank, const in
   j.PO = (int32_t)PO;
   j.PB = PB;
 
-  // the destination is contiguous along I when I's fastest leg has stride 1
-  // and no O leg is faster
-  int64_t min_o = O.empty() ? INT64_MAX : dstr[O.back()];
-  j.store_fast_i = dstr[r - 1] <= min_o ? 1 : 0;
+  // stores run along I when I holds the destination's unit-stride leg
+  j.store_fast_i = fleg >= iI ? 1 : 0;
+  j.wmask = wmask;
+  j.qw = (int32_t)qw;
+  j.iwrite = 0;
+  {
+    // the run's source strides equal its destination strides: q-th run
+    // element = q-th source column of the run
+    bool suf = wmask != 0;
+    for (int q = 0; q < j.nI; ++q)
+      if (wmask >> q & 1) suf = suf && j.sstr[q] == j.dstr[q];
+    j.wsuf = suf ? 1 : 0;
+  }
   jobs.push_back(j);
   (void)tiles;
 }
@@ -222,6 +303,8 @@ int finalize_perm_jobs(std::vector<PermJob>& jobs, size_t es, int64_t* tiles, bo
   int64_t t = 0;
   for (PermJob& j : jobs) {
     j.vec4 = 0;
+    // destination-order stores along I need the whole I group in one tile
+    j.iwrite = staged && j.store_fast_i && j.wmask && j.PI <= te / 8 ? 1 : 0;
     if (staged) {
       // vector stores: the fastest destination leg along the store direction
       // has stride 1 and a dimension divisible by 4, every other destination
@@ -234,8 +317,17 @@ int finalize_perm_jobs(std::vector<PermJob>& jobs, size_t es, int64_t* tiles, bo
         if (q != fast) v = v && j.dstr[q] % 4 == 0;
       j.vec4 = v ? 1 : 0;
     }
+    if (j.iwrite) {
+      // quads of the destination run: the run length and every other
+      // destination stride are multiples of 4 elements
+      const int nl = j.nI + j.nO + j.nB;
+      bool v = j.dst_off % 4 == 0 && j.qw % 4 == 0;
+      for (int q = 0; q < nl; ++q)
+        if (!(q < j.nI && (j.wmask >> q & 1))) v = v && j.dstr[q] % 4 == 0;
+      j.vec4 = v ? 1 : 0;
+    }
     if (staged) {
-      int64_t ti = std::min<int64_t>(j.PI, te / 8);
+      int64_t ti = j.iwrite ? j.PI : std::min<int64_t>(j.PI, te / 8);
       ti = (ti + V - 1) / V * V;
       int64_t tr = std::min<int64_t>(std::max<int64_t>(te / ti, 1), PERM_MAX_ROWS);
       tr = std::min<int64_t>(tr, j.PO);
