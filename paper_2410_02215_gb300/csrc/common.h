@@ -105,7 +105,11 @@ struct GemmProb {
   // 1: groups of 4 consecutive elements along the epilogue's write direction
   // are contiguous and 16-byte aligned in the destination (vector stores)
   int32_t vec4;
-  int32_t pad2_;
+  // 1: the group's tiles run over its members' concatenated columns (their
+  // column blocks are adjacent rows of B_pi and multiples of 32 wide); gcol
+  // is this member's first column within the group
+  int32_t gmerge;
+  int32_t gcol, pad3_;
 };
 
 // Offset of the row-major multi-index of x over n legs (last leg fastest),

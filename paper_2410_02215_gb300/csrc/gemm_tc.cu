@@ -74,14 +74,32 @@ __device__ __forceinline__ int tc_find_prob(const GemmProb* probs, int nprobs, i
   return lo;
 }
 
-// Tile t -> (problem, m0, n0) under the grouped order (see GemmProb).
+// Tile t -> (problem, m0, n0) under the grouped order (see GemmProb).  A
+// CTA's tiles increase, so `cur` (the group found for the previous tile, -1
+// at the start) only moves forward: one look at the next group's first
+// tile instead of a binary search of the table per tile.
 template <int BN>
-__device__ __forceinline__ const GemmProb* tc_decode(const TcParams& P, int64_t t, int& m0, int& n0) {
-  const GemmProb* g = P.probs + tc_find_prob(P.probs, P.nprobs, t);
+__device__ __forceinline__ const GemmProb* tc_decode(const TcParams& P, int64_t t, int& m0, int& n0, int& cur) {
+  if (cur < 0) {
+    cur = tc_find_prob(P.probs, P.nprobs, t);
+    cur = P.probs[cur].grp_first;
+  } else {
+    for (;;) {
+      const int nxt = P.probs[cur].grp_first + P.probs[cur].grp_count;
+      if (nxt >= P.nprobs || P.probs[nxt].tile_begin > t) break;
+      cur = nxt;
+    }
+  }
+  const GemmProb* g = P.probs + cur;
   const int64_t local = t - g->tile_begin;
   const int tm = (int)(local / g->row_tiles);
   int rem = (int)(local - (int64_t)tm * g->row_tiles);
   const GemmProb* p = P.probs + g->grp_first;
+  if (g->gmerge) {  // column n0 counts across the group's members
+    m0 = tm * TC_BM;
+    n0 = rem * BN;
+    return p;
+  }
   for (int q = 0; q < g->grp_count; ++q, ++p)
     if (rem < p->tn_off + p->tiles_n) break;
   m0 = tm * TC_BM;
@@ -131,9 +149,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
       uint32_t phase = 0;
       uint32_t issued = 0, lastpar = 0;
       bool ok = true;
+      int cur = -1;
       for (int64_t t = blockIdx.x; t < P.tiles && ok; t += gridDim.x) {
         int m0, n0;
-        const GemmProb& p = *tc_decode<BN>(P, t, m0, n0);
+        const GemmProb& p = *tc_decode<BN>(P, t, m0, n0, cur);
         const int nk = (p.K + Cfg::KB - 1) / Cfg::KB;
         const int pi = p.pi;
         for (int kb = 0; kb < nk; ++kb) {
@@ -170,9 +189,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
       int acc = 0;
       uint32_t acc_phase = 0;
       bool ok = true;
+      int cur = -1;
       for (int64_t t = blockIdx.x; t < P.tiles && ok; t += gridDim.x) {
         int m0, n0;
-        const GemmProb& p = *tc_decode<BN>(P, t, m0, n0);
+        const GemmProb& p = *tc_decode<BN>(P, t, m0, n0, cur);
         const int nk = (p.K + Cfg::KB - 1) / Cfg::KB;
         if (nk == 0) continue;
         if (!mbar_wait(&tempty[acc], acc_phase ^ 1, P.err)) break;
@@ -238,25 +258,64 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
     const int set = (warp - 2) >> 2;
     float* stg = epi + (warp - 2) * 32 * (Cfg::CW + 1);
     uint32_t j = 0;  // tiles with K > 0 seen so far (all sets count them)
+    int cur = -1;
     for (int64_t t = blockIdx.x; t < P.tiles; t += gridDim.x) {
       int m0, n0;
-      const GemmProb& p = *tc_decode<BN>(P, t, m0, n0);
+      const GemmProb& p = *tc_decode<BN>(P, t, m0, n0, cur);
       const int nk = (p.K + Cfg::KB - 1) / Cfg::KB;
       const int acc = (int)(j & 1);
       if (nk > 0) ++j;
       if (nk > 0 ? acc != set : set != 0) continue;
       const int row = m0 + 32 * q + lane;
-      const int64_t rpart = row < p.M ? p.c_off + expand_index32(row, p.nrl, p.rdim, p.rstr) : 0;
-      const int ncols = p.N - n0 < BN ? p.N - n0 : BN;
       const int nrows = p.M - (m0 + 32 * q) < 32 ? p.M - (m0 + 32 * q) : 32;
-      const float sg = (float)p.c_sign;
+      // Per chunk of CW columns: its problem (a member of a merged group),
+      // valid columns, this lane's row and column offsets, sign and store
+      // mode -- read from the problem table before waiting for the
+      // accumulator, so the table's latency overlaps the MMAs.
+      constexpr int NCH = BN / Cfg::CW;
+      int64_t rp_c[NCH], cp_c[NCH];
+      int cn_c[NCH], fl_c[NCH];
+      float sg_c[NCH];
+      {
+        const GemmProb* last = nullptr;
+        int64_t rpl = 0;
+#pragma unroll
+        for (int ch = 0; ch < NCH; ++ch) {
+          const GemmProb* mp = &p;
+          int lcol = n0 + ch * Cfg::CW;
+          if (p.gmerge) {
+            for (int qq = 1; qq < p.grp_count && lcol >= mp->gcol + mp->N; ++qq) ++mp;
+            lcol -= mp->gcol;
+          }
+          const int cn = mp->N - lcol < Cfg::CW ? mp->N - lcol : Cfg::CW;
+          cn_c[ch] = cn;
+          rp_c[ch] = cp_c[ch] = 0;
+          sg_c[ch] = 1.0f;
+          fl_c[ch] = 0;
+          if (cn > 0) {
+            if (mp != last) {
+              last = mp;
+              rpl = row < mp->M ? mp->c_off + expand_index32(row, mp->nrl, mp->rdim, mp->rstr) : 0;
+            }
+            rp_c[ch] = rpl;
+            cp_c[ch] = lane < Cfg::CW && lane < cn ? expand_index32(lcol + lane, mp->ncl, mp->cdim, mp->cstr) : 0;
+            sg_c[ch] = (float)mp->c_sign;
+            fl_c[ch] = (mp->vec4 ? 1 : 0) | (mp->epi_rows ? 2 : 0);
+          }
+        }
+      }
       if (nk > 0) {
         if (!mbar_wait(&tfull[acc], ((j - 1) >> 1) & 1, P.err)) break;
         tc_fence_after();
       }
       const uint32_t taddr = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(acc * Cfg::ACC_W);
-#pragma unroll 1
-      for (int c = 0; c < BN; c += Cfg::CW) {
+#pragma unroll
+      for (int ch = 0; ch < NCH; ++ch) {
+        const int c = ch * Cfg::CW;
+        const int cn = cn_c[ch];
+        if (cn <= 0) break;
+        const int64_t rpart = rp_c[ch];
+        const float sg = sg_c[ch];
         float v[Cfg::CW];
         if (nk > 0) {
 #pragma unroll
@@ -282,20 +341,19 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
 #pragma unroll
         for (int jj = 0; jj < Cfg::CW; ++jj) stg[lane * (Cfg::CW + 1) + jj] = v[jj];
         __syncwarp();
-        const int col = c + lane;
-        const bool okc = lane < Cfg::CW && col < ncols;
-        const int64_t cpart = okc ? expand_index32(n0 + col, p.ncl, p.cdim, p.cstr) : 0;
-        if (p.vec4) {
+        const bool okc = lane < Cfg::CW && lane < cn;
+        const int64_t cpart = cp_c[ch];
+        if (fl_c[ch] & 1) {
           // 16-byte stores: quads of consecutive elements along the contiguous direction
           const int sub = lane & 7, grp = lane >> 3;
-          if (p.epi_rows) {
+          if (fl_c[ch] & 2) {
             // lane -> rows 4*sub..+3 of column cc = 4*it + grp
             const int64_t rq = __shfl_sync(0xffffffffu, rpart, 4 * sub);
 #pragma unroll
             for (int it = 0; it < Cfg::CW / 4; ++it) {
               const int cc = 4 * it + grp;
               const int64_t cp = __shfl_sync(0xffffffffu, cpart, cc);
-              if (4 * sub < nrows && c + cc < ncols) {
+              if (4 * sub < nrows && cc < cn) {
                 float4 w;
                 w.x = sg * stg[(4 * sub + 0) * (Cfg::CW + 1) + cc];
                 w.y = sg * stg[(4 * sub + 1) * (Cfg::CW + 1) + cc];
@@ -311,7 +369,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
             for (int it = 0; it < 8; ++it) {
               const int rr = 4 * it + grp;
               const int64_t rp = __shfl_sync(0xffffffffu, rpart, rr);
-              if (4 * sub < Cfg::CW && rr < nrows && c + 4 * sub < ncols) {
+              if (4 * sub < Cfg::CW && rr < nrows && 4 * sub < cn) {
                 float4 w;
                 w.x = sg * stg[rr * (Cfg::CW + 1) + 4 * sub + 0];
                 w.y = sg * stg[rr * (Cfg::CW + 1) + 4 * sub + 1];
@@ -321,12 +379,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
               }
             }
           }
-        } else if (p.epi_rows) {
+        } else if (fl_c[ch] & 2) {
           // destination contiguous along rows: lane -> row, loop over columns
 #pragma unroll 4
           for (int cc = 0; cc < Cfg::CW; ++cc) {
             const int64_t cp = __shfl_sync(0xffffffffu, cpart, cc);
-            if (lane < nrows && c + cc < ncols) P.C[rpart + cp] = sg * stg[lane * (Cfg::CW + 1) + cc];
+            if (lane < nrows && cc < cn) P.C[rpart + cp] = sg * stg[lane * (Cfg::CW + 1) + cc];
           }
         } else {
 #pragma unroll 4

@@ -364,24 +364,64 @@ static ftn_status build_plan(ftn_ctx ctx, const ftn_tensor_s* A, const ftn_tenso
     // m-tile by m-tile across all member problems (A tile reuse in L2)
     std::stable_sort(P->probs.begin(), P->probs.end(), [](const GemmProb& x, const GemmProb& y) {
       if (x.pi != y.pi) return x.pi < y.pi;
-      return x.a_row0 < y.a_row0;
+      if (x.a_row0 != y.a_row0) return x.a_row0 < y.a_row0;
+      return x.b_row0 < y.b_row0;
     });
+    std::vector<std::pair<size_t, size_t>> groups;
     for (size_t i = 0; i < P->probs.size();) {
       size_t j = i;
-      int32_t row_tiles = 0;
-      while (j < P->probs.size() && P->probs[j].pi == P->probs[i].pi && P->probs[j].a_row0 == P->probs[i].a_row0) {
-        P->probs[j].tn_off = row_tiles;
-        row_tiles += P->probs[j].tiles_n;
-        ++j;
-      }
-      for (size_t q = i; q < j; ++q) {
-        P->probs[q].grp_first = (int32_t)i;
-        P->probs[q].grp_count = (int32_t)(j - i);
-        P->probs[q].row_tiles = row_tiles;
-        P->probs[q].tile_begin = P->gemm_tiles;
-      }
-      P->gemm_tiles += (int64_t)P->probs[i].tiles_m * row_tiles;
+      while (j < P->probs.size() && P->probs[j].pi == P->probs[i].pi && P->probs[j].a_row0 == P->probs[i].a_row0) ++j;
+      groups.push_back({i, j});
       i = j;
+    }
+    // Merged groups: when every group's column blocks are adjacent rows of
+    // B_pi and each a multiple of 32 wide, a tile may cross problems (its
+    // epilogue picks the member per 32-column chunk), so the tile width
+    // follows the group's total width: fewer, wider tiles and one read of
+    // each A tile.
+    bool merge = !groups.empty();
+    int max_group_n = 1;
+    for (auto& gr : groups) {
+      int tot = 0;
+      for (size_t q = gr.first; q < gr.second; ++q) {
+        const GemmProb& g = P->probs[q];
+        merge = merge && g.N % 32 == 0 && (q == gr.first || g.b_row0 == P->probs[q - 1].b_row0 + P->probs[q - 1].N);
+        tot += g.N;
+      }
+      max_group_n = std::max(max_group_n, tot);
+    }
+    const int bn_merged = tc_pick_bn(max_group_n, prec);
+    merge = merge && bn_merged > P->bn && bn_merged >= 32;
+    if (merge) {  // only while the wider tiles still fill the GPU twice over
+      int64_t mt = 0;
+      for (auto& gr : groups) {
+        int tot = 0;
+        for (size_t q = gr.first; q < gr.second; ++q) tot += P->probs[q].N;
+        mt += (int64_t)P->probs[gr.first].tiles_m * ((tot + bn_merged - 1) / bn_merged);
+      }
+      merge = mt >= 2 * (int64_t)ctx->num_sms;
+    }
+    if (merge) P->bn = bn_merged;
+    for (auto& gr : groups) {
+      int32_t row_tiles = 0, gcol = 0;
+      for (size_t q = gr.first; q < gr.second; ++q) {
+        GemmProb& g = P->probs[q];
+        g.tiles_n = (g.N + P->bn - 1) / P->bn;
+        g.tn_off = row_tiles;
+        g.gmerge = merge ? 1 : 0;
+        g.gcol = gcol;
+        gcol += g.N;
+        row_tiles += g.tiles_n;
+      }
+      if (merge) row_tiles = (gcol + P->bn - 1) / P->bn;
+      for (size_t q = gr.first; q < gr.second; ++q) {
+        GemmProb& g = P->probs[q];
+        g.grp_first = (int32_t)gr.first;
+        g.grp_count = (int32_t)(gr.second - gr.first);
+        g.row_tiles = row_tiles;
+        g.tile_begin = P->gemm_tiles;
+      }
+      P->gemm_tiles += (int64_t)P->probs[gr.first].tiles_m * row_tiles;
     }
   } else {
     for (GemmProb& g : P->probs) {
