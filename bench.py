@@ -320,20 +320,31 @@ def traffic_for(label):
     return None
 
 
-def roofline(prof, peaks):
+def roofline(prof, peaks, prec="tf32x3"):
+    """Roofline of the dominant kernel.  A tensor-core contraction takes the
+    dense peak of its operand type (TF32: the measured bf16 burst x 1.1/2.25,
+    the nominal ratio; BF16: the measured bf16 burst).  The split modes run
+    3 tensor-core products per algorithmic product, so beside `frac` the
+    fraction of the peak / 3 is reported as `frac_of_split_peak`."""
     dom = max(prof, key=lambda r: r["ms"])
     label = dom["label"]
     kind = label.split("/")[-1]
     t_s = dom["ms"] / 1e3 / max(dom["launches"], 1)
     bytes_per = dom["bytes"] / max(dom["launches"], 1)
     flops_per = dom["flops"] / max(dom["launches"], 1)
-    tf32_peak = peaks["bf16_tflops"] * NOMINAL_TF32_OVER_BF16
+    bf16 = prec.startswith("bf16")
+    tc_peak = peaks["bf16_tflops"] * (1.0 if bf16 else NOMINAL_TF32_OVER_BF16)
+    passes = 3 if prec.endswith("x3") else 1
     out = {"kernel": label, "launches": dom["launches"], "avg_launch_ms": t_s * 1e3}
-    tensor_bound = kind.startswith("gemm") and flops_per / max(bytes_per, 1.0) > tf32_peak * 1e12 / (peaks["hbm_gbs"] * 1e9)
+    tensor_bound = kind == "gemm_tc" and flops_per / max(bytes_per, 1.0) > tc_peak * 1e12 / (peaks["hbm_gbs"] * 1e9)
     if tensor_bound:
         ach = flops_per / t_s / 1e12
-        out.update({"bound": "tensor", "achieved": ach, "peak": tf32_peak, "unit": "TFLOP/s", "frac": ach / tf32_peak,
-                    "peak_note": f"TF32 dense = {peaks['src']} bf16 burst x 1.1/2.25 (nominal ratio)"})
+        note = (f"BF16 dense = {peaks['src']} bf16 burst" if bf16 else
+                f"TF32 dense = {peaks['src']} bf16 burst x 1.1/2.25 (nominal ratio)")
+        out.update({"bound": "tensor", "achieved": ach, "peak": tc_peak, "unit": "TFLOP/s", "frac": ach / tc_peak,
+                    "peak_note": note})
+        if passes > 1:
+            out.update({"tensor_passes_per_product": passes, "frac_of_split_peak": ach * passes / tc_peak})
     else:
         ach = bytes_per / t_s / 1e9
         out.update({"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
@@ -466,7 +477,7 @@ def run_ours(args, rank, world, local):
                    "parallelism": f"replicas x{world} (independent problems, no collective)"},
         "gpu_launches": launches,
     }
-    result["roofline"] = roofline(prof, peaks)
+    result["roofline"] = roofline(prof, peaks, args.prec)
     result["kernels"] = [{"label": r["label"], "launches": r["launches"], "ms": r["ms"],
                           "gbs": r["bytes"] / (r["ms"] / 1e3) / 1e9 if r["ms"] else None,
                           "tflops": r["flops"] / (r["ms"] / 1e3) / 1e12 if r["ms"] and r["flops"] else None}
