@@ -17,7 +17,9 @@ explicitly to the dense arrays, following the paper (arXiv:2410.02215):
 * globally ordered formalism, Eq. (fermionictn), Sec. II.C;
 * locally ordered formalism, Eq. (fermionictn2), Sec. II.D;
 * index fusion, Sec. IV.A; symmetric QR/SVD truncation, Sec. II.A;
-* Fermi-Hubbard Hamiltonian, Eq. (fermi-hubbard-ham), Sec. V.
+* Fermi-Hubbard Hamiltonian, Eq. (fermi-hubbard-ham), Sec. V;
+* the gradient of a contraction with respect to either operand, by its
+  definition (one contraction per parity-allowed entry).
 
 Parity pins: every function is checked by ``tests/test_oracle_*.py`` against
 closed forms printed in the paper, textbook reductions (bosonic legs ->
@@ -28,3 +30,4 @@ from .graded import *  # noqa: F401,F403
 from .network import *  # noqa: F401,F403
 from .compress import *  # noqa: F401,F403
 from .hubbard import *  # noqa: F401,F403
+from .adjoint import *  # noqa: F401,F403
