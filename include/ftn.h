@@ -164,6 +164,25 @@ FTN_API ftn_status ftn_tensordot(ftn_ctx ctx, ftn_tensor A, ftn_tensor B, int n,
                          const int* axes_b, uint64_t flip_a, uint64_t flip_b, const int* out_perm,
                          ftn_prec prec, ftn_tensor* C);
 
+/* ---- adjoint of the tensordot (the contraction is linear in each operand) - */
+
+/* Gradients of L = sum(G * C) with C = ftn_tensordot(A, B, n, axes_a, axes_b,
+ * flip_a, flip_b, out_perm): G holds dL/dC and must have exactly C's metadata
+ * (legs after out_perm, parity p_A + p_B) and A's dtype.  dA (if dA is not
+ * NULL) gets A's metadata and dL/dA, dB (if not NULL) B's and dL/dB; each is
+ * created unless non-NULL on entry (then its metadata must match).  Every
+ * block pair of the forward product carries one sign (transposition of the
+ * operands into the contraction order with the arrow and extra bond
+ * parities, and of the result into out_perm); the adjoint applies the same
+ * signs, so <dA, A> = <G, C> = <dB, B>.  prec: as for ftn_tensordot.
+ * Gradients of contractions serve the variational optimisation of fermionic
+ * PEPS that the paper refers to (Sec. II.D); the paper prints no adjoint, and
+ * this is a hand-written one.  Errors: as ftn_tensordot, and FTN_ESHAPE when
+ * G's legs or parity differ from C's. */
+FTN_API ftn_status ftn_tensordot_grad(ftn_ctx ctx, ftn_tensor A, ftn_tensor B, ftn_tensor G, int n,
+                                      const int* axes_a, const int* axes_b, uint64_t flip_a, uint64_t flip_b,
+                                      const int* out_perm, ftn_prec prec, ftn_tensor* dA, ftn_tensor* dB);
+
 /* ---- tensordot without device allocation ---------------------------------- */
 
 /* The paper has no counterpart of this entry point; it exists for callers

@@ -50,5 +50,16 @@ ftn_status get_plan(ftn_ctx ctx, const ftn_tensor_s* A, const ftn_tensor_s* B, i
                     uint64_t fa, uint64_t fb, const int* out_perm, ftn_prec prec, std::shared_ptr<TdPlan>& P);
 ftn_status validate_pairs(const ftn_tensor_s* A, const ftn_tensor_s* B, int n, const int* ax, const int* ay);
 int inversion_parity(int r, const int* perm, uint32_t mask);
+// bits legs[0..n) of mask, packed (bit i = bit legs[i])
+uint32_t gather_bits(uint32_t mask, const int* legs, int n);
+// masks over n legs with the given parity, in increasing order: offset and
+// size of each (indexed by mask, -1 / 0 for the other parity) and the total
+int64_t sector_offsets(int n, const int64_t* d0, const int64_t* d1, int parity, std::vector<int64_t>& off,
+                       std::vector<int64_t>& size);
+bool jobs_in_bounds(const std::vector<PermJob>& jobs, int64_t src_n, int64_t dst_n);
+void clear_grad_caches(ftn_ctx ctx);
+ftn_status tensordot_grad_impl(ftn_ctx ctx, ftn_tensor A, ftn_tensor B, ftn_tensor G, int n, const int* ax,
+                               const int* ay, uint64_t flip_a, uint64_t flip_b, const int* out_perm, ftn_prec prec,
+                               ftn_tensor* dA, ftn_tensor* dB);
 
 }  // namespace ftn

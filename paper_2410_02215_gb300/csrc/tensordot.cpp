@@ -22,7 +22,7 @@ int inversion_parity(int r, const int* perm, uint32_t mask) {
   return s;
 }
 
-static uint32_t gather_bits(uint32_t mask, const int* legs, int n) {
+uint32_t gather_bits(uint32_t mask, const int* legs, int n) {
   uint32_t m = 0;
   for (int i = 0; i < n; ++i) m |= ((mask >> legs[i]) & 1u) << i;
   return m;
@@ -30,8 +30,8 @@ static uint32_t gather_bits(uint32_t mask, const int* legs, int n) {
 
 // enumerate masks over `n` bits with a given parity, increasing order;
 // returns cumulative offsets indexed by mask (size 2^n) and the total.
-static int64_t sector_offsets(int n, const int64_t* d0, const int64_t* d1, int parity, std::vector<int64_t>& off,
-                              std::vector<int64_t>& size) {
+int64_t sector_offsets(int n, const int64_t* d0, const int64_t* d1, int parity, std::vector<int64_t>& off,
+                       std::vector<int64_t>& size) {
   off.assign((size_t)1 << n, -1);
   size.assign((size_t)1 << n, 0);
   int64_t tot = 0;
@@ -48,7 +48,7 @@ static int64_t sector_offsets(int n, const int64_t* d0, const int64_t* d1, int p
 
 // Every index a permute job or a GEMM problem can touch must lie inside its
 // buffers; a plan that fails this is rejected before any launch.
-static bool jobs_in_bounds(const std::vector<PermJob>& jobs, int64_t src_n, int64_t dst_n) {
+bool jobs_in_bounds(const std::vector<PermJob>& jobs, int64_t src_n, int64_t dst_n) {
   for (const PermJob& j : jobs) {
     int64_t ms = j.src_off, md = j.dst_off;
     const int nl = j.nI + j.nO + j.nB;
@@ -711,6 +711,7 @@ ftn_status permute_impl(ftn_ctx ctx, ftn_tensor t, const int* perm, bool fermion
 void clear_plan_caches(ftn_ctx ctx) {
   plan_cache(ctx).clear();
   tr_cache(ctx).clear();
+  clear_grad_caches(ctx);
 }
 
 }  // namespace ftn

@@ -8,6 +8,7 @@ this module fails loudly when the compiled library is missing.
 from __future__ import annotations
 
 import ctypes as C
+import itertools
 import os
 import weakref
 
@@ -78,6 +79,8 @@ def lib():
         "ftn_tensor_transpose": [vp, vp, ip, C.POINTER(vp)],
         "ftn_tensor_dagger": [vp, vp, C.POINTER(vp)],
         "ftn_tensordot": [vp, vp, vp, C.c_int, ip, ip, C.c_uint64, C.c_uint64, ip, C.c_int, C.POINTER(vp)],
+        "ftn_tensordot_grad": [vp, vp, vp, vp, C.c_int, ip, ip, C.c_uint64, C.c_uint64, ip, C.c_int, C.POINTER(vp),
+                               C.POINTER(vp)],
         "ftn_compress": [vp, C.POINTER(vp), C.POINTER(vp), C.c_int, ip, ip, C.c_int, C.c_int, C.POINTER(CompressInfo)],
         "ftn_contract": [vp, C.POINTER(Network), C.POINTER(Tree), C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double)],
         "ftn_hubbard_term": [vp, C.c_int, C.c_double, C.c_double, C.c_int, C.POINTER(vp)],
@@ -331,6 +334,100 @@ def tensordot(ctx, a, b, axes_a, axes_b, flip_a=0, flip_b=0, out_perm=None, prec
     _check(lib().ftn_tensordot(ctx.handle, a.handle, b.handle, n, _int(axes_a), _int(axes_b), int(flip_a), int(flip_b),
                                op, _prec(prec), C.byref(h)))
     return out if out is not None else Tensor(ctx, h)
+
+
+def tensordot_grad(ctx, a, b, g, axes_a, axes_b, flip_a=0, flip_b=0, out_perm=None, prec="f64", wrt=("a", "b"),
+                   out_a=None, out_b=None):
+    """Gradients (dA, dB) of sum(G * C) for C = tensordot(a, b, ...) with the
+    same arguments; g has C's metadata.  Entries of `wrt` not requested come
+    back as None; out_a / out_b may be preallocated tensors."""
+    n = len(axes_a)
+    op = _int(out_perm) if out_perm is not None else None
+    ha = C.c_void_p(out_a.handle.value if out_a is not None else None)
+    hb = C.c_void_p(out_b.handle.value if out_b is not None else None)
+    _check(lib().ftn_tensordot_grad(ctx.handle, a.handle, b.handle, g.handle, n, _int(axes_a), _int(axes_b),
+                                    int(flip_a), int(flip_b), op, _prec(prec),
+                                    C.byref(ha) if "a" in wrt else None, C.byref(hb) if "b" in wrt else None))
+    da = (out_a if out_a is not None else Tensor(ctx, ha)) if "a" in wrt else None
+    db = (out_b if out_b is not None else Tensor(ctx, hb)) if "b" in wrt else None
+    return da, db
+
+
+def _numel(legs, parity):
+    """Stored elements of a graded tensor: sum over parity-allowed blocks."""
+    tot = 0
+    for bits in itertools.product((0, 1), repeat=len(legs)):
+        if sum(bits) % 2 == parity:
+            n = 1
+            for (d0, d1, _), bt in zip(legs, bits):
+                n *= d1 if bt else d0
+            tot += n
+    return tot
+
+
+def _result_legs(legs_a, legs_b, axes_a, axes_b, out_perm):
+    free = [l for k, l in enumerate(legs_a) if k not in axes_a] + [l for k, l in enumerate(legs_b) if k not in axes_b]
+    return [free[p] for p in out_perm] if out_perm is not None else free
+
+
+class _TensordotFn:
+    """torch.autograd.Function over flat block-data tensors (built lazily so
+    that importing this module does not need torch)."""
+
+    _cls = None
+
+    @classmethod
+    def get(cls):
+        if cls._cls is None:
+            import torch
+
+            class Fn(torch.autograd.Function):
+                @staticmethod
+                def forward(fctx, a_data, b_data, spec):
+                    ctx, la, pa, lb, pb, axa, axb, fa, fb, perm, prec = spec
+                    dt = F64 if a_data.dtype == torch.float64 else F32
+                    a = Tensor.wrap(ctx, la, pa, a_data, dt)
+                    b = Tensor.wrap(ctx, lb, pb, b_data, dt)
+                    lc = _result_legs(la, lb, axa, axb, perm)
+                    c_data = torch.empty(_numel(lc, pa ^ pb), dtype=a_data.dtype, device=a_data.device)
+                    c = Tensor.wrap(ctx, lc, pa ^ pb, c_data, dt)
+                    tensordot(ctx, a, b, axa, axb, fa, fb, perm, prec, out=c)
+                    fctx.save_for_backward(a_data, b_data)
+                    fctx.spec = spec
+                    return c_data
+
+                @staticmethod
+                def backward(fctx, g_data):
+                    a_data, b_data = fctx.saved_tensors
+                    ctx, la, pa, lb, pb, axa, axb, fa, fb, perm, prec = fctx.spec
+                    dt = F64 if a_data.dtype == torch.float64 else F32
+                    g_data = g_data.contiguous()
+                    a = Tensor.wrap(ctx, la, pa, a_data, dt)
+                    b = Tensor.wrap(ctx, lb, pb, b_data, dt)
+                    g = Tensor.wrap(ctx, _result_legs(la, lb, axa, axb, perm), pa ^ pb, g_data, dt)
+                    wa, wb = fctx.needs_input_grad[0], fctx.needs_input_grad[1]
+                    da_data = torch.empty_like(a_data) if wa else None
+                    db_data = torch.empty_like(b_data) if wb else None
+                    wrt = ("a",) * bool(wa) + ("b",) * bool(wb)
+                    if wrt:
+                        tensordot_grad(ctx, a, b, g, axa, axb, fa, fb, perm, prec, wrt,
+                                       Tensor.wrap(ctx, la, pa, da_data, dt) if wa else None,
+                                       Tensor.wrap(ctx, lb, pb, db_data, dt) if wb else None)
+                    return da_data, db_data, None
+
+            cls._cls = Fn
+        return cls._cls
+
+
+def tensordot_autograd(ctx, a_data, legs_a, parity_a, b_data, legs_b, parity_b, axes_a, axes_b, flip_a=0, flip_b=0,
+                       out_perm=None, prec="f64"):
+    """Differentiable tensordot on flat torch CUDA tensors holding the blocks
+    of A and B (block layout of the library).  Returns (C's block data, C's
+    legs, C's parity); backward runs ftn_tensordot_grad."""
+    spec = (ctx, [tuple(l) for l in legs_a], int(parity_a), [tuple(l) for l in legs_b], int(parity_b),
+            list(axes_a), list(axes_b), int(flip_a), int(flip_b), None if out_perm is None else list(out_perm), prec)
+    c = _TensordotFn.get().apply(a_data, b_data, spec)
+    return c, _result_legs(spec[1], spec[3], spec[5], spec[6], spec[9]), spec[2] ^ spec[4]
 
 
 def transpose(ctx, t, perm, out=None):
