@@ -277,6 +277,61 @@ def time_steps(F, ctx, torch, cases, prec, steps, warmup, flush, world, profile=
     return ms, launches, prof, ins, outs
 
 
+def backward_bench(F, ctx, torch, cases, prec, steps, warmup, flush, ins, outs, flops_step):
+    """The adjoint of the step: dA and dB of every T1-T4 contraction from a
+    resident G (C's metadata), timed like the forward step.  Each gradient
+    costs the forward's sector flops, so a backward step is 2x the forward's.
+    Accuracy: normwise against the FP64 gradients of the same inputs (the
+    FP64 adjoint is checked against the oracle's gradient by definition in
+    the tests)."""
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(11)
+    gs, da, db = {}, {}, {}
+    for c in cases:
+        r = outs[c["name"]]
+        g = F.Tensor.empty(ctx, r.legs, r.parity, F.F64 if prec == "f64" else F.F32)
+        v = g.view()
+        v.copy_(torch.randn(v.shape, generator=gen, device="cuda", dtype=v.dtype))
+        gs[c["name"]] = g
+
+    def step():
+        for c in cases:
+            a = ins[(tuple(c["legs_a"]), "a", c["name"])]
+            b = ins[(tuple(c["legs_b"]), "b", c["name"])]
+            x, y = F.tensordot_grad(ctx, a, b, gs[c["name"]], c["axes_a"], c["axes_b"], out_perm=c["out_perm"],
+                                    prec=prec, out_a=da.get(c["name"]), out_b=db.get(c["name"]))
+            da[c["name"]], db[c["name"]] = x, y
+
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for i in range(steps):
+        flush.zero_()
+        evs[i][0].record()
+        step()
+        evs[i][1].record()
+    torch.cuda.synchronize()
+    ms = sum(a.elapsed_time(b) for a, b in evs) / steps
+    worst = 0.0
+    if prec != "f64":
+        for c in cases:
+            up = lambda t: F.Tensor.wrap(ctx, t.legs, t.parity, t.view().double().contiguous(), F.F64)  # noqa: E731
+            a64 = up(ins[(tuple(c["legs_a"]), "a", c["name"])])
+            b64 = up(ins[(tuple(c["legs_b"]), "b", c["name"])])
+            g64 = up(gs[c["name"]])
+            ra, rb = F.tensordot_grad(ctx, a64, b64, g64, c["axes_a"], c["axes_b"], out_perm=c["out_perm"],
+                                      prec="f64")
+            for got, ref in ((da[c["name"]], ra), (db[c["name"]], rb)):
+                x, y = got.view().double(), ref.view()
+                worst = max(worst, float((x - y).abs().max() / y.abs().max()))
+            for t in (ra, rb, a64, b64, g64):
+                t.free()
+    return {"metric": "sector-GEMM TFLOP/s of the adjoint step (dA and dB of T1-T4)", "precision": prec,
+            "ms_per_step": ms, "tflops": 2.0 * flops_step / (ms * 1e-3) / 1e12,
+            "rel_err_inf_vs_f64_gpu": worst}
+
+
 def accuracy(F, ctx, prec):
     """Normwise errors of one reduced-size step against the oracle (T1-T4
     with every sector dimension halved, T4 quartered)."""
@@ -465,6 +520,10 @@ def run_ours(args, rank, world, local):
     ms, launches, prof, ins, outs = time_steps(F, ctx, torch, cases, args.prec, args.steps, args.warmup, flush, world,
                                                profile=True)
     clocks = clk.stop()
+    back = None
+    if not args.no_backward:
+        back = backward_bench(F, ctx, torch, cases, args.prec, max(2, args.steps // 2), args.warmup, flush, ins, outs,
+                              flops_step)
     del ins, outs
     ms_max = max_over_ranks(ms, world)
     value = flops_step * args.steps * world / (ms_max / 1e3) / 1e12
@@ -478,6 +537,8 @@ def run_ours(args, rank, world, local):
         "gpu_launches": launches,
     }
     result["roofline"] = roofline(prof, peaks, args.prec)
+    if back is not None:
+        result["backward"] = back
     result["kernels"] = [{"label": r["label"], "launches": r["launches"], "ms": r["ms"],
                           "gbs": r["bytes"] / (r["ms"] / 1e3) / 1e9 if r["ms"] else None,
                           "tflops": r["flops"] / (r["ms"] / 1e3) / 1e12 if r["ms"] and r["flops"] else None}
@@ -526,6 +587,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-energy", action="store_true")
+    ap.add_argument("--no-backward", action="store_true")
     ap.add_argument("--energy-evals", type=int, default=3)
     ap.add_argument("--energy-streams", type=int, default=8,
                     help="contexts (CUDA streams) that run an evaluation's contractions concurrently")

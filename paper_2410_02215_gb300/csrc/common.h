@@ -109,7 +109,8 @@ struct GemmProb {
   // column blocks are adjacent rows of B_pi and multiples of 32 wide); gcol
   // is this member's first column within the group
   int32_t gmerge;
-  int32_t gcol, pad3_;
+  int32_t gcol;
+  int32_t k0;  // tensor-core path: first K element of this problem (K-split parts)
 };
 
 // Offset of the row-major multi-index of x over n legs (last leg fastest),
@@ -255,6 +256,9 @@ int64_t plan_splitk_f64(std::vector<GemmProb>& probs, int num_sms, std::vector<G
 bool red_in_bounds(const std::vector<GemmProb>& red, int64_t part_n, int64_t c_n);
 ftn_status launch_splitk_reduce(ftn_ctx ctx, const GemmProb* d_red, int nred, int64_t total, const double* part,
                                 double* c);
+// The same for FP32 partial slabs and output, added in FP64.
+ftn_status launch_splitk_reduce_f32(ftn_ctx ctx, const GemmProb* d_red, int nred, int64_t total, const float* part,
+                                    float* c);
 
 struct TcOperands {
   // fused pi-matrices: rows x ldk elements, K-major; lo only for split modes

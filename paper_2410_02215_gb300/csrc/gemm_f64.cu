@@ -152,6 +152,33 @@ __global__ void splitk_reduce_kernel(const GemmProb* __restrict__ red, int nred,
   }
 }
 
+// FP32 partial slabs (tensor-core K-split parts), added in FP64.
+__global__ void splitk_reduce_f32_kernel(const GemmProb* __restrict__ red, int nred, int64_t total,
+                                         const float* __restrict__ part, float* __restrict__ C) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const GemmProb& g = red[find_prob(red, nred, e)];
+    const int64_t local = e - g.tile_begin;
+    const int m = (int)(local / g.N), n = (int)(local - (int64_t)m * g.N);
+    const float* src = part + g.a_off + local;
+    double acc = 0.0;
+    for (int s = 0; s < g.nsplit; ++s) acc += (double)src[(int64_t)s * g.c_slab];
+    C[g.c_off + expand_index32(m, g.nrl, g.rdim, g.rstr) + expand_index32(n, g.ncl, g.cdim, g.cstr)] =
+        (float)((double)g.c_sign * acc);
+  }
+}
+
+ftn_status launch_splitk_reduce_f32(ftn_ctx ctx, const GemmProb* d_red, int nred, int64_t total, const float* part,
+                                    float* c) {
+  if (nred == 0 || total == 0) return FTN_OK;
+  int64_t grid = (total + 255) / 256;
+  if (grid > (int64_t)ctx->num_sms * 8) grid = (int64_t)ctx->num_sms * 8;
+  splitk_reduce_f32_kernel<<<(unsigned)grid, 256, 0, ctx->stream>>>(d_red, nred, total, part, c);
+  ctx->launches += 1;
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_error(e, "splitk_reduce_f32_kernel launch");
+  return FTN_OK;
+}
+
 int64_t plan_splitk_f64(std::vector<GemmProb>& probs, int num_sms, std::vector<GemmProb>& red, int64_t& tiles,
                         int64_t& red_total) {
   red.clear();

@@ -162,12 +162,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
           }
           uint8_t* sa = smem + stage * Cfg::STAGE_BYTES;
           mbar_expect_tx(&full[stage], Cfg::STAGE_BYTES);
-          tma_load_2d(sa, &P.a_hi[pi], kb * Cfg::KB, p.a_row0 + m0, &full[stage]);
-          tma_load_2d(sa + Cfg::A_BYTES, &P.b_hi[pi], kb * Cfg::KB, p.b_row0 + n0, &full[stage]);
+          const int kx = p.k0 + kb * Cfg::KB;  // K element; k0 is a multiple of KB
+          tma_load_2d(sa, &P.a_hi[pi], kx, p.a_row0 + m0, &full[stage]);
+          tma_load_2d(sa + Cfg::A_BYTES, &P.b_hi[pi], kx, p.b_row0 + n0, &full[stage]);
           if constexpr (SPLIT) {
-            tma_load_2d(sa + Cfg::A_BYTES + Cfg::B_BYTES, &P.a_lo[pi], kb * Cfg::KB, p.a_row0 + m0, &full[stage]);
-            tma_load_2d(sa + 2 * Cfg::A_BYTES + Cfg::B_BYTES, &P.b_lo[pi], kb * Cfg::KB, p.b_row0 + n0,
-                        &full[stage]);
+            tma_load_2d(sa + Cfg::A_BYTES + Cfg::B_BYTES, &P.a_lo[pi], kx, p.a_row0 + m0, &full[stage]);
+            tma_load_2d(sa + 2 * Cfg::A_BYTES + Cfg::B_BYTES, &P.b_lo[pi], kx, p.b_row0 + n0, &full[stage]);
           }
           issued |= 1u << stage;
           lastpar = (lastpar & ~(1u << stage)) | (phase << stage);

@@ -36,6 +36,7 @@ struct GradPlan {
   int sg = 0, sy = 0;
   std::vector<GemmProb> probs, red;
   int64_t tiles = 0, part_elems = 0, red_total = 0;
+  bool tc_parts = false;  // tensor-core path: every problem writes FP32 partial slabs, reduced in FP64
   int bn = 0;
   int32_t xd0[MAXR], xd1[MAXR];
   uint8_t xdu[MAXR];
@@ -256,6 +257,51 @@ ftn_status build(ftn_ctx ctx, const ftn_tensor_s* A, const ftn_tensor_s* B, cons
     g.tiles_n = (g.N + P->bn - 1) / P->bn;
   }
   if (tc) {
+    // Long contractions (the gradient of a small operand contracts over all
+    // free states of the large one): K parts of at most TC_KPART elements,
+    // and enough parts to give two tiles per SM.  The tensor core
+    // accumulates each part in FP32; the parts are added in FP64.  If any
+    // problem is split, every problem writes partial slabs (the kernel has
+    // one output base) and one reduction writes the gradient.
+    constexpr int TC_KPART = 2048, KALIGN = 64;  // a multiple of both TMA K boxes (32 TF32, 64 BF16)
+    int64_t tiles0 = 0;
+    for (const GemmProb& g : P->probs) tiles0 += (int64_t)g.tiles_m * g.tiles_n;
+    const int64_t want = tiles0 > 0 ? (2 * (int64_t)ctx->num_sms + tiles0 - 1) / tiles0 : 1;
+    bool need = false;
+    for (const GemmProb& g : P->probs) need = need || g.K > TC_KPART || (want > 1 && g.K >= 8 * KALIGN);
+    if (need) {
+      std::vector<GemmProb> parts;
+      int64_t part = 0, elems = 0;
+      for (const GemmProb& g : P->probs) {
+        int s = (int)std::max<int64_t>((g.K + TC_KPART - 1) / TC_KPART, std::min<int64_t>(want, g.K / (4 * KALIGN)));
+        s = std::max(1, std::min(s, 256));
+        int kchunk = (g.K + s - 1) / s;
+        kchunk = std::max(KALIGN, (kchunk + KALIGN - 1) / KALIGN * KALIGN);
+        s = std::max(1, (g.K + kchunk - 1) / kchunk);
+        const int64_t mn = (int64_t)g.M * g.N;
+        GemmProb r = g;  // reduction job: the original epilogue
+        r.a_off = part;
+        r.nsplit = s;
+        r.c_slab = mn;
+        r.tile_begin = elems;
+        P->red.push_back(r);
+        for (int q = 0; q < s; ++q) {
+          GemmProb h = g;
+          h.k0 = q * kchunk;
+          h.K = std::min(kchunk, g.K - h.k0);
+          gemm_plain_output(h, part + (int64_t)q * mn, g.N);
+          h.epi_rows = 0;
+          h.vec4 = (g.N % 4 == 0 && (part + (int64_t)q * mn) % 4 == 0) ? 1 : 0;
+          parts.push_back(h);
+        }
+        part += mn * s;
+        elems += mn;
+      }
+      P->probs.swap(parts);
+      P->part_elems = part;
+      P->red_total = elems;
+      P->tc_parts = true;
+    }
     std::stable_sort(P->probs.begin(), P->probs.end(), [](const GemmProb& x, const GemmProb& y) {
       if (x.pi != y.pi) return x.pi < y.pi;
       if (x.a_row0 != y.a_row0) return x.a_row0 < y.a_row0;
@@ -286,7 +332,9 @@ ftn_status build(ftn_ctx ctx, const ftn_tensor_s* A, const ftn_tensor_s* B, cons
     P->part_elems = plan_splitk_f64(P->probs, ctx->num_sms, P->red, P->tiles, P->red_total);
   }
   const int64_t x_numel = X->numel;
-  if (!jobs_in_bounds(P->jg, G->numel, P->g_elems) || !jobs_in_bounds(P->jy, Y->numel, P->y_elems) ||
+  bool k_ok = true;  // K parts stay inside the contraction and start on a TMA box boundary
+  for (const GemmProb& g : P->probs) k_ok = k_ok && g.k0 >= 0 && g.k0 % 64 == 0 && g.k0 + g.K <= P->L[g.pi];
+  if (!k_ok || !jobs_in_bounds(P->jg, G->numel, P->g_elems) || !jobs_in_bounds(P->jy, Y->numel, P->y_elems) ||
       !probs_in_bounds(P->probs, P->g_elems, P->y_elems, P->part_elems ? P->part_elems : x_numel) ||
       (P->part_elems && !red_in_bounds(P->red, P->part_elems, x_numel)))
     return set_error(FTN_EINVAL, "internal error: gradient plan out of bounds");
@@ -326,7 +374,7 @@ ftn_status run_grad(ftn_ctx ctx, const GradPlan& P, const ftn_tensor_s* G, const
   const size_t es = tc ? (bf16 ? 2 : 4) : 8;
   auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
   const size_t g_b = al((size_t)P.g_elems * es), y_b = al((size_t)P.y_elems * es);
-  const size_t p_b = al((size_t)P.part_elems * 8);
+  const size_t p_b = al((size_t)P.part_elems * (tc ? 4 : 8));
   const int planes = split ? 2 : 1;
   const size_t need = (g_b + y_b) * planes + p_b;
   uint8_t* ws = (uint8_t*)workspace(ctx, need);
@@ -373,7 +421,13 @@ ftn_status run_grad(ftn_ctx ctx, const GradPlan& P, const ftn_tensor_s* G, const
     ops.ldk[pi] = (int32_t)P.ld[pi];
   }
   rec = prof_begin(ctx, "gemm_tc", 0, fl);
-  FTN_TRY(launch_gemm_tc(ctx, prec, ops, P.d_probs, (int)P.probs.size(), P.tiles, P.bn, (float*)dX->data));
+  if (P.tc_parts) {
+    float* part = (float*)(ws + need - p_b);
+    FTN_TRY(launch_gemm_tc(ctx, prec, ops, P.d_probs, (int)P.probs.size(), P.tiles, P.bn, part));
+    FTN_TRY(launch_splitk_reduce_f32(ctx, P.d_red, (int)P.red.size(), P.red_total, part, (float*)dX->data));
+  } else {
+    FTN_TRY(launch_gemm_tc(ctx, prec, ops, P.d_probs, (int)P.probs.size(), P.tiles, P.bn, (float*)dX->data));
+  }
   prof_end(ctx, rec);
   return FTN_OK;
 }

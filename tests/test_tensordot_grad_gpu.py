@@ -135,3 +135,27 @@ def test_grad_rejects_wrong_result_legs(F, ctx):
     g = F.Tensor.from_blocks(ctx, bad, 0, W.random_blocks(bad, 0, 3))
     with pytest.raises(F.FtnError):
         F.tensordot_grad(ctx, a, b, g, [1], [0])
+
+
+@pytest.mark.parametrize("name", ["T1", "T2"])
+def test_long_contraction_gradient_full_size(F, ctx, name):
+    """dB of T1 / T2 contracts over every free state of the environment
+    (131072 / 16384 per sector): the tensor-core gradient runs it as K parts
+    accumulated in FP32 and added in FP64.  TF32x3 vs FP64 gradients of the
+    same FP32-rounded inputs, normwise 1e-5."""
+    c = W.tensordot_case(name, seed=0)
+    rnd = lambda legs, par, seed: [(k, v.astype(np.float32).astype(np.float64))  # noqa: E731
+                                   for k, v in W.random_blocks(legs, par, seed)]
+    ba, bb = rnd(c["legs_a"], 0, 1), rnd(c["legs_b"], 0, 2)
+    a64 = F.Tensor.from_blocks(ctx, c["legs_a"], 0, ba)
+    b64 = F.Tensor.from_blocks(ctx, c["legs_b"], 0, bb)
+    r = F.tensordot(ctx, a64, b64, c["axes_a"], c["axes_b"], out_perm=c["out_perm"], prec="f64")
+    bg = rnd(r.legs, r.parity, 3)
+    g64 = F.Tensor.from_blocks(ctx, r.legs, r.parity, bg)
+    ref = F.tensordot_grad(ctx, a64, b64, g64, c["axes_a"], c["axes_b"], out_perm=c["out_perm"], prec="f64")
+    a32 = F.Tensor.from_blocks(ctx, c["legs_a"], 0, ba, F.F32)
+    b32 = F.Tensor.from_blocks(ctx, c["legs_b"], 0, bb, F.F32)
+    g32 = F.Tensor.from_blocks(ctx, r.legs, r.parity, bg, F.F32)
+    got = F.tensordot_grad(ctx, a32, b32, g32, c["axes_a"], c["axes_b"], out_perm=c["out_perm"], prec="tf32x3")
+    for x, y in zip(got, ref):
+        assert relerr(x.download().astype(np.float64), y.download()) <= TOL["tf32x3"]
