@@ -19,7 +19,9 @@ explicitly to the dense arrays, following the paper (arXiv:2410.02215):
 * index fusion, Sec. IV.A; symmetric QR/SVD truncation, Sec. II.A;
 * Fermi-Hubbard Hamiltonian, Eq. (fermi-hubbard-ham), Sec. V;
 * the gradient of a contraction with respect to either operand, by its
-  definition (one contraction per parity-allowed entry).
+  definition (one contraction per parity-allowed entry);
+* the cluster approximation of local energy terms, Sec. V (cluster networks
+  in the globally ordered formalism, Fig. 4b).
 
 Parity pins: every function is checked by ``tests/test_oracle_*.py`` against
 closed forms printed in the paper, textbook reductions (bosonic legs ->
@@ -31,3 +33,4 @@ from .network import *  # noqa: F401,F403
 from .compress import *  # noqa: F401,F403
 from .hubbard import *  # noqa: F401,F403
 from .adjoint import *  # noqa: F401,F403
+from .cluster import *  # noqa: F401,F403

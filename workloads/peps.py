@@ -10,7 +10,8 @@ from __future__ import annotations
 
 from .gen import random_blocks
 
-__all__ = ["peps_layout", "random_peps", "double_layer_tree", "site_sweep_tree"]
+__all__ = ["peps_layout", "random_peps", "double_layer_tree", "site_sweep_tree", "cluster_sites", "dangling_bonds",
+           "bond_gauges", "cluster_ids", "cluster_tree"]
 
 
 def peps_layout(n, edges, D, phys=(2, 2)):
@@ -85,4 +86,98 @@ def site_sweep_tree(order):
     for s, t in enumerate(order[1:]):
         pairs.append((cur, t))
         cur = n + s
+    return pairs
+
+
+# ---- cluster approximation (structure and stand-in gauges) -------------------
+
+def cluster_sites(layout, targets, r):
+    """Sites within graph distance r of any target site, sorted."""
+    dist = {t: 0 for t in targets}
+    frontier = list(targets)
+    for d in range(1, r + 1):
+        nxt = []
+        for s in frontier:
+            for t in layout["nbrs"][s]:
+                if t not in dist:
+                    dist[t] = d
+                    nxt.append(t)
+        frontier = nxt
+    return sorted(dist)
+
+
+def dangling_bonds(layout, sites):
+    """Bonds leaving the cluster: (s, leg of s, t) with s inside, t outside, in
+    increasing (s, t)."""
+    inside = set(sites)
+    out = []
+    for s in sites:
+        for k, t in enumerate(layout["nbrs"][s]):
+            if t not in inside:
+                out.append((s, k, t))
+    return out
+
+
+def bond_gauges(layout, decay=0.5):
+    """Stand-in for simple-update bond gauges: on every bond the diagonal
+    weights decay**k for the k-th state of each sector.  Returns
+    {edge (s, t), s < t: (even weights, odd weights)}."""
+    out = {}
+    for s, ks, t, kt in layout["bonds"]:
+        d0, d1, _ = layout["legs"][s][ks]
+        out[(s, t)] = ([decay**k for k in range(d0)], [decay**k for k in range(d1)])
+    return out
+
+
+def cluster_ids(layout, sites, with_op):
+    """Tensor ids of a cluster network: kets 0..m-1 (cluster order), bras
+    m..2m-1, the operator 2m (if any), then one gauge tensor per dangling bond
+    in :func:`dangling_bonds` order.  Returns (local index of each cluster site,
+    operator id or None, first gauge id)."""
+    m = len(sites)
+    loc = {s: i for i, s in enumerate(sites)}
+    op = 2 * m if with_op else None
+    return loc, op, 2 * m + (1 if with_op else 0)
+
+
+def cluster_tree(layout, sites, targets, with_op):
+    """SSA contraction tree of a cluster network (ids of :func:`cluster_ids`):
+    every gauge tensor is merged into its site's ket, the operator into the
+    ket of its first site, each ket into its bra, and the merged sites in
+    breadth-first order from the targets."""
+    m = len(sites)
+    loc, op, g0 = cluster_ids(layout, sites, with_op)
+    dang = dangling_bonds(layout, sites)
+    nt = g0 + len(dang)
+    nxt = nt
+    cur = {i: i for i in range(m)}  # current node of each site's ket
+    pairs = []
+    for g, (s, _, _) in enumerate(dang):
+        pairs.append((g0 + g, cur[loc[s]]))
+        cur[loc[s]] = nxt
+        nxt += 1
+    site_node = {}
+    for i in range(m):
+        k = cur[i]
+        if with_op and sites[i] == targets[0]:
+            pairs.append((op, k))
+            k = nxt
+            nxt += 1
+        pairs.append((k, m + i))
+        site_node[i] = nxt
+        nxt += 1
+    order = []
+    seen = set()
+    frontier = list(targets)
+    while frontier:
+        for s in frontier:
+            if s not in seen:
+                seen.add(s)
+                order.append(s)
+        frontier = sorted({t for s in frontier for t in layout["nbrs"][s] if t in loc and t not in seen})
+    acc = site_node[loc[order[0]]]
+    for s in order[1:]:
+        pairs.append((acc, site_node[loc[s]]))
+        acc = nxt
+        nxt += 1
     return pairs
