@@ -101,38 +101,148 @@ def energy(ctx, layout, kets, t, u, tree_fn, mode="local", policy="exact", chi=0
         tens, bonds, pos, tree = job
         return ftn.contract(c, tens, bonds, tree, positions=pos if glob else None, policy=policy, chi=chi, prec=prec)
 
-    if len(ctxs) == 1:
-        results = [run(c0, job) for job in jobs]
-    else:
-        import threading
-
-        c0.synchronize()  # inputs ready before other streams read them
-        results = [None] * len(jobs)
-        errors = []
-        lock = threading.Lock()
-        nxt = [0]
-
-        def worker(c):
-            try:
-                while True:
-                    with lock:
-                        i = nxt[0]
-                        nxt[0] += 1
-                    if i >= len(jobs) or errors:
-                        return
-                    results[i] = run(c, jobs[i])
-            except BaseException as e:  # re-raised on the calling thread
-                errors.append(e)
-
-        threads = [threading.Thread(target=worker, args=(c,)) for c in ctxs]
-        for th in threads:
-            th.start()
-        for th in threads:
-            th.join()
-        if errors:
-            raise errors[0]
+    results = _run_jobs(ctxs, jobs, run)
     nm, nl = results[0]
     total = 0.0
     for m, lg in results[1:]:
         total += m / nm * math.exp(lg - nl)
     return total, nm, nl
+
+
+def _run_jobs(ctxs, jobs, run):
+    """run(ctx, job) for every job; with several contexts, host threads (one
+    per context) take jobs from a shared counter.  Results in job order."""
+    c0 = ctxs[0]
+    if len(ctxs) == 1:
+        return [run(c0, job) for job in jobs]
+    import threading
+
+    c0.synchronize()  # inputs ready before other streams read them
+    results = [None] * len(jobs)
+    errors = []
+    lock = threading.Lock()
+    nxt = [0]
+
+    def worker(c):
+        try:
+            while True:
+                with lock:
+                    i = nxt[0]
+                    nxt[0] += 1
+                if i >= len(jobs) or errors:
+                    return
+                results[i] = run(c, jobs[i])
+        except BaseException as e:  # re-raised on the calling thread
+            errors.append(e)
+
+    threads = [threading.Thread(target=worker, args=(c,)) for c in ctxs]
+    for th in threads:
+        th.start()
+    for th in threads:
+        th.join()
+    if errors:
+        raise errors[0]
+    return results
+
+
+# ---- cluster approximation (Sec. V) -------------------------------------------
+
+def gauge_tensor(ctx, lam_even, lam_odd, dual_to_bra, dtype=ftn.F64):
+    """Even rank-2 tensor diag(lambda^2) closing a dangling bond: leg 0 meets
+    the bra's leg, leg 1 the ket's (``dual_to_bra`` = the ket leg's dual)."""
+    import numpy as np
+
+    d0, d1 = len(lam_even), len(lam_odd)
+    legs = [(d0, d1, dual_to_bra), (d0, d1, 1 - dual_to_bra)]
+    blocks = []
+    if d0:
+        blocks.append(((0, 0), np.diag(np.asarray(lam_even, float) ** 2)))
+    if d1:
+        blocks.append(((1, 1), np.diag(np.asarray(lam_odd, float) ** 2)))
+    return ftn.Tensor.from_blocks(ctx, legs, 0, blocks, dtype)
+
+
+def cluster_network(layout, kets, bras, sites, dangling, gauge_of, op=None, targets=()):
+    """Globally ordered network of one cluster (Fig. 4b): bra cluster in
+    reversed order, then the operator (if any) and one gauge tensor per
+    dangling bond, then the ket cluster.  Ids: kets 0..m-1 (order of
+    ``sites``), bras m..2m-1, operator 2m, then the gauges in ``dangling``
+    order; ``gauge_of(s, leg)`` gives the library gauge tensor of a dangling
+    ket leg.  Returns (tensors, bonds, positions)."""
+    m = len(sites)
+    loc = {s: i for i, s in enumerate(sites)}
+    tensors = [kets[s] for s in sites] + [bras[s] for s in sites]
+    rank = [kets[s].rank for s in sites]
+    bonds = []
+    for s, a, t, b in layout["bonds"]:
+        if s in loc and t in loc:
+            i, j = loc[s], loc[t]
+            bonds.append((i, a, j, b))
+            bonds.append((m + i, rank[i] - 1 - a, m + j, rank[j] - 1 - b))
+    targets = list(targets)
+    for s in sites:
+        if op is None or s not in targets:
+            i = loc[s]
+            bonds.append((m + i, 0, i, rank[i] - 1))
+    nmid = 0
+    if op is not None:
+        tensors.append(op)
+        nmid = 1
+        k = len(targets)
+        for q, s in enumerate(targets):
+            i = loc[s]
+            bonds.append((m + i, 0, 2 * m, q))
+            bonds.append((2 * m, 2 * k - 1 - q, i, rank[i] - 1))
+    for s, a, _t in dangling:
+        i = loc[s]
+        gid = len(tensors)
+        tensors.append(gauge_of(s, a))
+        nmid += 1
+        bonds.append((m + i, rank[i] - 1 - a, gid, 0))
+        bonds.append((gid, 1, i, a))
+    pos = [m + nmid + i for i in range(m)] + [m - 1 - i for i in range(m)] + [m + q for q in range(nmid)]
+    return tensors, bonds, pos
+
+
+def cluster_energy(ctx, layout, kets, t, u, cluster_fn, gauges, policy="exact", chi=0, prec="f64"):
+    """Cluster approximation of sum_t <h_t>: every hopping and on-site term
+    is the ratio of its cluster network with the operator to the same network
+    without it, both contracted in the globally ordered formalism.
+    ``cluster_fn(targets)`` gives (sites, dangling bonds, tree with the
+    operator, tree without it); ``gauges[(s, t)]`` = (even, odd) weights of
+    the bond's stand-in gauge.  ``ctx`` may be a list of contexts (the
+    contractions then run concurrently, as in :func:`energy`).  Returns
+    (energy, per-term ratios)."""
+    ctxs = list(ctx) if isinstance(ctx, (list, tuple)) else [ctx]
+    c0 = ctxs[0]
+    dt = ftn.F64 if prec == "f64" else ftn.F32
+    bras = [ftn.dagger(c0, k) for k in kets]
+    cache = {}
+
+    def gauge_of(s, a):
+        key = (s, a)
+        if key not in cache:
+            nb = layout["nbrs"][s][a]
+            lam = gauges[(min(s, nb), max(s, nb))]
+            cache[key] = gauge_tensor(c0, lam[0], lam[1], kets[s].legs[a][2], dt)
+        return cache[key]
+
+    hop = ftn.hubbard_term(c0, 0, t, 0.0, dt)
+    onsite = ftn.hubbard_term(c0, 1, 0.0, u, dt)
+    terms = [((a, b), hop) for a, b in layout["edges"]] + [((s,), onsite) for s in range(layout["n"])]
+    jobs = []
+    for targets, op in terms:
+        sites, dang, tree_op, tree_norm = cluster_fn(list(targets))
+        jobs.append(cluster_network(layout, kets, bras, sites, dang, gauge_of, op, targets) + (tree_op,))
+        jobs.append(cluster_network(layout, kets, bras, sites, dang, gauge_of) + (tree_norm,))
+
+    def run(c, job):
+        tens, bonds, pos, tree = job
+        return ftn.contract(c, tens, bonds, tree, positions=pos, policy=policy, chi=chi, prec=prec)
+
+    res = _run_jobs(ctxs, jobs, run)
+    ratios = []
+    for q in range(len(terms)):
+        (mn, ln), (md, ld) = res[2 * q], res[2 * q + 1]
+        ratios.append(mn / md * math.exp(ln - ld))
+    return float(sum(ratios)), ratios
