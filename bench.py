@@ -277,6 +277,74 @@ def time_steps(F, ctx, torch, cases, prec, steps, warmup, flush, world, profile=
     return ms, launches, prof, ins, outs
 
 
+CLUSTER_WORKLOAD = ("Hubbard fPEPS energy terms by the cluster approximation (radius 1, Sec. V) on 64 random "
+                    "3-regular graphs (pairing model, seeds 0..63), N uniform over even integers in [16, 48], D cycling "
+                    "through 3 (2+1), 4 (3+1), 6 (4+2), phys 4 (2+2), t=1, U=8, N(0,1) site tensors, stand-in gauges "
+                    "0.5^k per sector on dangling bonds, late compression chi=32; one term = the cluster network with "
+                    "and without the operator")
+
+
+def cluster_bench(F, ctx, torch, n_graphs, streams, with_oracle):
+    """Energy terms per second of the cluster approximation over a set of
+    random regular graphs (FP64 and mixed), and the oracle's rate on the
+    smallest graph of the set."""
+    import numpy as np
+
+    from paper_2410_02215_gb300 import peps
+
+    rg = np.random.default_rng(12345)
+    Ds = [(2, 1), (3, 1), (4, 2)]
+    graphs = []
+    for g in range(n_graphs):
+        n = int(rg.integers(8, 25)) * 2
+        nn, e = W.random_regular_graph(n, 3, g)
+        lay = W.peps_layout(nn, e, Ds[g % 3], (2, 2))
+        graphs.append((lay, W.random_peps(lay, g), W.bond_gauges(lay)))
+
+    def cfn(lay):
+        def f(targets):
+            sites = W.cluster_sites(lay, targets, 1)
+            return (sites, W.dangling_bonds(lay, sites), W.cluster_tree(lay, sites, targets, True),
+                    W.cluster_tree(lay, sites, targets, False))
+        return f
+
+    ctxs = [ctx] + [F.Context(stream=torch.cuda.Stream()) for _ in range(max(streams, 1) - 1)]
+    out = {"workload": CLUSTER_WORKLOAD, "graphs": n_graphs, "streams": len(ctxs)}
+    res = {}
+    for prec, dt in (("f64", F.F64), ("tf32x3", F.F32)):
+        kets = [[F.Tensor.from_blocks(ctx, lay["legs"][s], 0, bl[s], dt) for s in range(lay["n"])]
+                for lay, bl, _ in graphs]
+        ctx.synchronize()
+        for c in ctxs:  # warm-up: every context builds its plans
+            for (lay, _, gs), k in zip(graphs[:3], kets[:3]):
+                peps.cluster_energy(c, lay, k, 1.0, 8.0, cfn(lay), gs, policy="late", chi=32, prec=prec)
+        nterms, energies = 0, []
+        t0 = time.perf_counter()
+        for (lay, _, gs), k in zip(graphs, kets):
+            en, rat = peps.cluster_energy(ctxs, lay, k, 1.0, 8.0, cfn(lay), gs, policy="late", chi=32, prec=prec)
+            nterms += len(rat)
+            energies.append(en)
+        dt_s = time.perf_counter() - t0
+        res[prec] = energies
+        out[prec] = {"terms_per_s": nterms / dt_s, "terms": nterms, "s": dt_s}
+    e64, e32 = np.array(res["f64"]), np.array(res["tf32x3"])
+    out["mixed_vs_f64_max_rel_err"] = float(np.max(np.abs(e32 - e64) / np.abs(e64)))
+    if with_oracle:
+        import oracle as O
+
+        small = min(range(n_graphs), key=lambda g: graphs[g][0]["n"] * (1 + g % 3))
+        lay, bl, gs = graphs[small]
+        t0 = time.perf_counter()
+        e_ref, rref = O.cluster_energy(lay, O.ket_tensors(lay, bl), 1.0, 8.0, cfn(lay), gs, policy="late", chi=32)
+        dt_s = time.perf_counter() - t0
+        out["oracle"] = {"terms_per_s": len(rref) / dt_s, "graph_sites": lay["n"], "D": list(lay["legs"][0][0][:2]),
+                         "energy_rel_err_f64_gpu": abs(res["f64"][small] - e_ref) / abs(e_ref)}
+    for c in ctxs[1:]:
+        c.synchronize()
+        c.close()
+    return out
+
+
 def backward_bench(F, ctx, torch, cases, prec, steps, warmup, flush, ins, outs, flops_step):
     """The adjoint of the step: dA and dB of every T1-T4 contraction from a
     resident G (C's metadata), timed like the forward step.  Each gradient
@@ -563,6 +631,9 @@ def run_ours(args, rank, world, local):
         result["speedup_vs_f64_gpu"] = precs[args.prec]["tflops"] / precs["f64"]["tflops"]
     if not args.no_e2e:
         result["e2e"] = e2e_run(F, ctx, torch, cases, args.prec, max(2, min(args.steps, 5)), flops_step)
+    if not args.no_cluster:
+        result["cluster"] = cluster_bench(F, ctx, torch, args.cluster_graphs, args.energy_streams,
+                                          rank == 0 and world == 1 and not args.no_cpu)
     if not args.no_energy:
         result["energy"] = energy_bench(F, ctx, args.energy_evals, rank == 0 and world == 1 and not args.no_cpu,
                                         args.energy_streams)
@@ -588,6 +659,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-energy", action="store_true")
     ap.add_argument("--no-backward", action="store_true")
+    ap.add_argument("--no-cluster", action="store_true")
+    ap.add_argument("--cluster-graphs", type=int, default=64)
     ap.add_argument("--energy-evals", type=int, default=3)
     ap.add_argument("--energy-streams", type=int, default=8,
                     help="contexts (CUDA streams) that run an evaluation's contractions concurrently")
