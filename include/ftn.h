@@ -240,7 +240,8 @@ typedef struct {
  * zeros and never kept.  `arrows` = 0 contracts the bond without the arrow
  * parity (plain ordered contraction F(XY) of the global formalism).  *X and
  * *Y are replaced by new library-owned tensors and the old ones freed.  FP64
- * arithmetic throughout.  Synchronises once (kept dimensions are data). */
+ * arithmetic throughout.  Synchronises twice (the nonzero rows of the R
+ * factors and the kept dimensions are data). */
 FTN_API ftn_status ftn_compress(ftn_ctx ctx, ftn_tensor* X, ftn_tensor* Y, int n, const int* axes_x,
                         const int* axes_y, int chi, int arrows, ftn_compress_info* info);
 
@@ -275,6 +276,25 @@ typedef struct {
  * (*mantissa) * exp(*log_scale).  Synchronises at the end. */
 FTN_API ftn_status ftn_contract(ftn_ctx ctx, const ftn_network* net, const ftn_tree* tree, ftn_prec prec,
                         double* mantissa, double* log_scale);
+
+/* Contract `count` independent closed networks (for instance the cluster
+ * networks of all energy terms of many states, Sec. V): nets[i] along
+ * trees[i], each exactly as ftn_contract would, with results
+ * mantissa[i] * exp(log_scale[i]) (host arrays of count doubles).  The
+ * networks advance in lock step -- round s runs step s of every network that
+ * has one -- and every stage of a round (sign-permutes, grouped sector GEMMs,
+ * the compressions before or after the step, normalisation) is one launch per
+ * kernel over all networks, so the launch count grows with the number of
+ * steps, not with the number of networks.  Each network keeps the arithmetic
+ * it has alone (plans, tiles, reduction orders): results are bit-identical
+ * to count separate ftn_contract calls.  All networks share `prec`; trees may
+ * differ in policy and chi.  Memory: the live tensors of all networks are
+ * held at once.  Errors: as ftn_contract, for the first network that fails
+ * validation (nothing is launched then); FTN_EINVAL when count < 0 or an
+ * array is NULL with count > 0.  Synchronises at the end and, with
+ * compression, twice per sub-round of compressions. */
+FTN_API ftn_status ftn_contract_batch(ftn_ctx ctx, int count, const ftn_network* nets, const ftn_tree* trees,
+                              ftn_prec prec, double* mantissa, double* log_scale);
 
 /* ---- Hubbard terms (Eq. fermi-hubbard-ham) -------------------------------- */
 

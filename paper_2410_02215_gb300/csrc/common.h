@@ -271,6 +271,15 @@ struct TcOperands {
 };
 ftn_status launch_gemm_tc(ftn_ctx ctx, ftn_prec prec, const TcOperands& ops, const GemmProb* d_probs, int nprobs,
                           int64_t tiles, int bn, float* c);
+// Four TMA tensor maps (A hi, B hi, A lo, B lo) of one fused-matrix pair,
+// encoded for tile width bn, as stored in a device table for batched launches.
+struct alignas(64) TcMapSet {
+  uint8_t bytes[4][128];
+};
+ftn_status tc_encode_set(ftn_prec prec, int bn, const TcOperands& ops, int pi, TcMapSet* out);
+// Problem p reads its operands through d_maps[p.pi] (a device table, 64-byte aligned).
+ftn_status launch_gemm_tc_maps(ftn_ctx ctx, ftn_prec prec, const TcMapSet* d_maps, const GemmProb* d_probs,
+                               int nprobs, int64_t tiles, int bn, float* c);
 int tc_pick_bn(int max_n, ftn_prec prec);
 int64_t tc_tiles_for(int M, int N, int bn);
 

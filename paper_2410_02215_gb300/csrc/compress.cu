@@ -19,10 +19,11 @@
 // R factors.
 #include <algorithm>
 #include <cmath>
+#include <map>
 #include <mutex>
 
+#include "batch.h"
 #include "ptx.cuh"
-#include "tdplan.h"
 
 namespace ftn {
 
@@ -538,43 +539,6 @@ GemmProb make_prob(int M, int N, int K, int64_t a_off, int64_t a_sm, int64_t a_s
   return g;
 }
 
-// One FP64 GEMM launch over `probs`; a launch with few output tiles that
-// is not split already gets the split-K treatment (partial slabs after the
-// tables in the same device allocation, then the ordered reduction).
-ftn_status run_gemms(ftn_ctx ctx, std::vector<GemmProb>& probs, const double* A, const double* B, double* C,
-                     int64_t a_n, int64_t b_n, int64_t c_n, DevBuf& keep) {
-  if (probs.empty()) return FTN_OK;
-  int max_n = 1;
-  for (auto& g : probs) max_n = std::max(max_n, g.N);
-  const int bn = f64_pick_bn(max_n);
-  for (auto& g : probs) g.tiles_n = (g.N + bn - 1) / bn;
-  int64_t tiles = 0;
-  bool presplit = false;
-  for (auto& g : probs) {
-    g.tile_begin = tiles;
-    tiles += (int64_t)g.tiles_m * g.tiles_n * (g.nsplit > 1 ? g.nsplit : 1);
-    presplit = presplit || g.nsplit > 1;
-  }
-  std::vector<GemmProb> red;
-  int64_t red_total = 0, part_n = 0;
-  if (!presplit) part_n = plan_splitk_f64(probs, ctx->num_sms, red, tiles, red_total);
-  if (!probs_in_bounds(probs, a_n, b_n, part_n ? part_n : c_n) || (part_n && !red_in_bounds(red, part_n, c_n)))
-    return set_error(FTN_EINVAL, "internal error: compression GEMM out of bounds");
-  const size_t tp = probs.size() * sizeof(GemmProb), tr = red.size() * sizeof(GemmProb);
-  const size_t tab = (tp + tr + 255) & ~(size_t)255;
-  std::vector<uint8_t> host(tp + tr);
-  std::memcpy(host.data(), probs.data(), tp);
-  if (tr) std::memcpy(host.data() + tp, red.data(), tr);
-  keep.p = dev_alloc(ctx, tab + (size_t)part_n * 8);
-  if (!keep.p) return set_error(FTN_ENOMEM, "device allocation failed (GEMM tables)");
-  FTN_CUDA(cudaMemcpyAsync(keep.p, host.data(), tp + tr, cudaMemcpyHostToDevice, ctx->stream));
-  const GemmProb* d_probs = (const GemmProb*)keep.p;
-  if (!part_n) return launch_gemm_f64(ctx, d_probs, (int)probs.size(), tiles, A, B, C, bn);
-  double* part = (double*)((uint8_t*)keep.p + tab);
-  FTN_TRY(launch_gemm_f64(ctx, d_probs, (int)probs.size(), tiles, A, B, part, bn));
-  return launch_splitk_reduce(ctx, d_probs + probs.size(), (int)red.size(), red_total, part, C);
-}
-
 template <int E>
 ftn_status setup_svd_cluster(int* cmax) {
   auto k = svd_rows_cluster_kernel<E>;
@@ -652,48 +616,65 @@ ftn_status launch_svd_cluster(ftn_ctx ctx, const SvdJob* jobs, int njobs, int C,
 
 }  // namespace
 
-ftn_status compress_impl(ftn_ctx ctx, ftn_tensor* pX, ftn_tensor* pY, int n, const int* ax, const int* ay, int chi,
-                         int arrows, ftn_compress_info* info) {
-  if (!ctx || !pX || !pY || !*pX || !*pY) return set_error(FTN_EINVAL, "null argument");
-  ftn_tensor X = *pX, Y = *pY;
+namespace {
+
+// Per-job state of a batched compression (one bond of one pair of tensors).
+// Offsets are in doubles from the job's own workspace.
+struct CJob {
+  CompressItem* it = nullptr;
+  std::shared_ptr<TdPlan> P;
+  int64_t ws_n = 0, ws_off = 0;
+  double* ws = nullptr;
+  int64_t o_xf = 0, o_yf = 0;
+  int64_t o_px_part[2], o_py_part[2], o_gx[2], o_gy[2], o_m[2], o_tf[2], o_wk[2], o_zk[2], o_px[2], o_qy[2],
+      o_ms3[2], o_rxc[2], o_ryc[2];
+  int64_t s_off[2];  // singular values + sweep count in the batch's shared buffer
+  int sp_x[2], sp_y[2], rx[2], ry[2], ldx[2], ldy[2], nrot[2], mlen[2];
+  int64_t rx_off[2], ry_off[2];
+  bool tall_x[2], tall_y[2], trans[2];
+  struct Cand {
+    double s;
+    int pi, idx;
+  };
+  std::vector<Cand> kept;  // kept singular values, largest first
+  int k[2] = {0, 0};
+  ftn_tensor Xn = nullptr, Yn = nullptr;
+};
+
+ftn_status cj_prepare(ftn_ctx ctx, CJob& J) {
+  CompressItem& it = *J.it;
+  ftn_tensor X = it.X, Y = it.Y;
+  if (!X || !Y) return set_error(FTN_EINVAL, "null argument");
   if (X->dtype != FTN_F64 || Y->dtype != FTN_F64)
     return set_error(FTN_EUNSUPPORTED, "ftn_compress works on FP64 tensors");
-  if (chi < 0) return set_error(FTN_EINVAL, "chi must be >= 0");
-  if (n < 1) return set_error(FTN_EINVAL, "a bond needs at least one leg pair");
-  FTN_TRY(validate_pairs(X, Y, n, ax, ay));
+  if (it.chi < 0) return set_error(FTN_EINVAL, "chi must be >= 0");
+  if (it.n < 1) return set_error(FTN_EINVAL, "a bond needs at least one leg pair");
+  FTN_TRY(validate_pairs(X, Y, it.n, it.ax, it.ay));
   uint64_t flip = 0;
-  if (!arrows)  // cancel the arrow parity: plain ordered contraction F(XY)
-    for (int i = 0; i < n; ++i)
-      if (X->dual[ax[i]] == 0) flip |= 1ull << ax[i];
-  std::shared_ptr<TdPlan> P;
-  FTN_TRY(get_plan(ctx, X, Y, n, ax, ay, flip, 0, nullptr, FTN_PREC_F64, P));
+  if (!it.arrows)  // cancel the arrow parity: plain ordered contraction F(XY)
+    for (int i = 0; i < it.n; ++i)
+      if (X->dual[it.ax[i]] == 0) flip |= 1ull << it.ax[i];
+  FTN_TRY(get_plan(ctx, X, Y, it.n, it.ax, it.ay, flip, 0, nullptr, FTN_PREC_F64, J.P));
+  const TdPlan* P = J.P.get();
   for (int pi = 0; pi < 2; ++pi)
     if (P->K[pi] > LA_MAX_DIM) return set_error(FTN_EUNSUPPORTED, "bond sector larger than the batched Jacobi SVD handles");
-
   // ---- workspace layout (doubles) ----
   auto al = [](int64_t x) { return (x + 31) / 32 * 32; };
   int64_t off = 0;
-  const int64_t o_xf = off;
+  J.o_xf = off;
   off += al(P->af_elems);
-  const int64_t o_yf = off;
+  J.o_yf = off;
   off += al(P->bf_elems);
-  int64_t o_px_part[2], o_py_part[2];
-  int sp_x[2], sp_y[2];
-  int64_t o_gx[2], o_gy[2], o_m[2], o_tf[2], o_s[2], o_wk[2], o_zk[2], o_px[2], o_qy[2], o_ms3[2];
-  int64_t o_rxc[2], o_ryc[2];
-  int rx[2], ry[2], ldx[2], ldy[2], nrot[2], mlen[2];
-  int64_t rx_off[2], ry_off[2];
-  bool tall_x[2], tall_y[2], trans[2];
   for (int pi = 0; pi < 2; ++pi) {
     const int64_t K = P->K[pi], R = P->M[pi], Cc = P->N[pi];
-    tall_x[pi] = R > K;
-    tall_y[pi] = Cc > K;
-    rx[pi] = (int)std::min(R, K);
-    ry[pi] = (int)std::min(Cc, K);
-    o_gx[pi] = off;
-    off += tall_x[pi] ? al(K * K) : 0;
-    o_gy[pi] = off;
-    off += tall_y[pi] ? al(K * K) : 0;
+    J.tall_x[pi] = R > K;
+    J.tall_y[pi] = Cc > K;
+    J.rx[pi] = (int)std::min(R, K);
+    J.ry[pi] = (int)std::min(Cc, K);
+    J.o_gx[pi] = off;
+    off += J.tall_x[pi] ? al(K * K) : 0;
+    J.o_gy[pi] = off;
+    off += J.tall_y[pi] ? al(K * K) : 0;
     // split-K over the long (row) dimension of the Gram products
     auto split_for = [&](int64_t rows) {
       const int64_t tiles = ((K + 63) / 64) * ((K + 63) / 64);
@@ -701,65 +682,49 @@ ftn_status compress_impl(ftn_ctx ctx, ftn_tensor* pX, ftn_tensor* pY, int n, con
       s = std::min<int64_t>(s, std::max<int64_t>(1, rows / 512));
       return (int)std::min<int64_t>(s, 64);
     };
-    sp_x[pi] = tall_x[pi] ? split_for(R) : 1;
-    sp_y[pi] = tall_y[pi] ? split_for(Cc) : 1;
-    o_px_part[pi] = off;
-    off += sp_x[pi] > 1 ? al((int64_t)sp_x[pi] * K * K) : 0;
-    o_py_part[pi] = off;
-    off += sp_y[pi] > 1 ? al((int64_t)sp_y[pi] * K * K) : 0;
-    o_rxc[pi] = off;
-    off += al((int64_t)rx[pi] * K);
-    o_ryc[pi] = off;
-    off += al((int64_t)ry[pi] * K);
-    rx_off[pi] = tall_x[pi] ? o_gx[pi] : o_xf + P->afoff[pi];
-    ldx[pi] = tall_x[pi] ? (int)K : (int)P->ldk[pi];
-    ry_off[pi] = tall_y[pi] ? o_gy[pi] : o_yf + P->bfoff[pi];
-    ldy[pi] = tall_y[pi] ? (int)K : (int)P->ldk[pi];
-    trans[pi] = rx[pi] > ry[pi];  // rotate the shorter side
-    nrot[pi] = trans[pi] ? ry[pi] : rx[pi];
-    mlen[pi] = trans[pi] ? rx[pi] : ry[pi];
-    o_m[pi] = off;
-    off += al((int64_t)nrot[pi] * mlen[pi]);
-    o_tf[pi] = off;
-    off += al((int64_t)nrot[pi] * mlen[pi]);
-    o_ms3[pi] = off;
-    off += al((int64_t)nrot[pi] * mlen[pi]);
-    o_s[pi] = off;
-    off += al(nrot[pi] + 1);  // singular values, then the sweep count
+    J.sp_x[pi] = J.tall_x[pi] ? split_for(R) : 1;
+    J.sp_y[pi] = J.tall_y[pi] ? split_for(Cc) : 1;
+    J.o_px_part[pi] = off;
+    off += J.sp_x[pi] > 1 ? al((int64_t)J.sp_x[pi] * K * K) : 0;
+    J.o_py_part[pi] = off;
+    off += J.sp_y[pi] > 1 ? al((int64_t)J.sp_y[pi] * K * K) : 0;
+    J.o_rxc[pi] = off;
+    off += al((int64_t)J.rx[pi] * K);
+    J.o_ryc[pi] = off;
+    off += al((int64_t)J.ry[pi] * K);
+    J.rx_off[pi] = J.tall_x[pi] ? J.o_gx[pi] : J.o_xf + P->afoff[pi];
+    J.ldx[pi] = J.tall_x[pi] ? (int)K : (int)P->ldk[pi];
+    J.ry_off[pi] = J.tall_y[pi] ? J.o_gy[pi] : J.o_yf + P->bfoff[pi];
+    J.ldy[pi] = J.tall_y[pi] ? (int)K : (int)P->ldk[pi];
+    J.trans[pi] = J.rx[pi] > J.ry[pi];  // rotate the shorter side
+    J.nrot[pi] = J.trans[pi] ? J.ry[pi] : J.rx[pi];
+    J.mlen[pi] = J.trans[pi] ? J.rx[pi] : J.ry[pi];
+    J.o_m[pi] = off;
+    off += al((int64_t)J.nrot[pi] * J.mlen[pi]);
+    J.o_tf[pi] = off;
+    off += al((int64_t)J.nrot[pi] * J.mlen[pi]);
+    J.o_ms3[pi] = off;
+    off += al((int64_t)J.nrot[pi] * J.mlen[pi]);
     // kept vectors and projectors (at most nrot of them)
-    o_wk[pi] = off;
-    off += al((int64_t)nrot[pi] * rx[pi]);
-    o_zk[pi] = off;
-    off += al((int64_t)nrot[pi] * ry[pi]);
-    o_px[pi] = off;
-    off += al((int64_t)nrot[pi] * K);
-    o_qy[pi] = off;
-    off += al((int64_t)nrot[pi] * K);
+    J.o_wk[pi] = off;
+    off += al((int64_t)J.nrot[pi] * J.rx[pi]);
+    J.o_zk[pi] = off;
+    off += al((int64_t)J.nrot[pi] * J.ry[pi]);
+    J.o_px[pi] = off;
+    off += al((int64_t)J.nrot[pi] * K);
+    J.o_qy[pi] = off;
+    off += al((int64_t)J.nrot[pi] * K);
   }
-  const int64_t o_cnt = off;  // four int row counts
-  off += 32;
-  const int64_t ws_n = off;
-  double* ws = (double*)workspace(ctx, (size_t)ws_n * 8);
-  if (!ws) return set_error(FTN_ENOMEM, "workspace allocation failed");
+  J.ws_n = off;
+  return FTN_OK;
+}
 
-  // ---- 1. fused matrices ----
-  int rec = prof_begin(ctx, "permute", (X->numel + Y->numel) * 16.0, 0);
-  FTN_TRY(launch_permute(ctx, P->d_ja, (int)P->ja.size(), P->ta, P->sa, X->data, ws + o_xf, nullptr, FTN_F64,
-                         PERM_SAME));
-  FTN_TRY(launch_permute(ctx, P->d_jb, (int)P->jb.size(), P->tb, P->sb, Y->data, ws + o_yf, nullptr, FTN_F64,
-                         PERM_SAME));
-  prof_end(ctx, rec);
-
-  DevBuf t_gram(ctx), t_chol(ctx), t_m(ctx), t_svd(ctx), t_gat(ctx), t_proj(ctx), t_fx(ctx), t_fy(ctx);
-  // ---- 2. Gram matrices and R factors ----
-  std::vector<GemmProb> gram;
-  std::vector<CholJob> chol;
-  struct Red {
-    int64_t dst, src;
-    int64_t count;
-    int nsplit;
-  };
-  std::vector<Red> reds;
+// Gram products of the tall sides (split over rows where that gives more
+// tiles; the slabs are added by the ordered reduction) and their Cholesky jobs.
+ftn_status cj_gram(CJob& J, GemmF64Batch& gb, std::vector<CholJob>& chol) {
+  const TdPlan* P = J.P.get();
+  double* ws = J.ws;
+  std::vector<GemmProb> gram, reds;
   auto add_gram = [&](int K, int rows, int64_t src, int64_t ld, int64_t dst, int64_t part, int nsplit) {
     GemmProb g = make_prob(K, K, rows, src, 1, ld, src, 1, ld);
     if (nsplit > 1) {
@@ -769,7 +734,12 @@ ftn_status compress_impl(ftn_ctx ctx, ftn_tensor* pX, ftn_tensor* pY, int n, con
       g.nsplit = (rows + g.kchunk - 1) / g.kchunk;
       gemm_plain_output(g, part, K);
       g.c_slab = (int64_t)K * K;
-      reds.push_back({dst, part, (int64_t)K * K, g.nsplit});
+      // the slabs at `part`, added in split order into the plain K x K result at dst
+      GemmProb r = make_prob(K, K, 0, part, 0, 0, 0, 0, 0);
+      gemm_plain_output(r, dst, K);
+      r.nsplit = g.nsplit;
+      r.c_slab = (int64_t)K * K;
+      reds.push_back(r);
     } else {
       gemm_plain_output(g, dst, K);
     }
@@ -779,156 +749,60 @@ ftn_status compress_impl(ftn_ctx ctx, ftn_tensor* pX, ftn_tensor* pY, int n, con
   for (int pi = 0; pi < 2; ++pi) {
     const int K = (int)P->K[pi];
     if (K == 0) continue;
-    if (tall_x[pi] && P->M[pi] > 0)
-      add_gram(K, (int)P->M[pi], o_xf + P->afoff[pi], P->ldk[pi], o_gx[pi], o_px_part[pi], sp_x[pi]);
-    if (tall_y[pi] && P->N[pi] > 0)
-      add_gram(K, (int)P->N[pi], o_yf + P->bfoff[pi], P->ldk[pi], o_gy[pi], o_py_part[pi], sp_y[pi]);
+    if (J.tall_x[pi] && P->M[pi] > 0)
+      add_gram(K, (int)P->M[pi], J.o_xf + P->afoff[pi], P->ldk[pi], J.o_gx[pi], J.o_px_part[pi], J.sp_x[pi]);
+    if (J.tall_y[pi] && P->N[pi] > 0)
+      add_gram(K, (int)P->N[pi], J.o_yf + P->bfoff[pi], P->ldk[pi], J.o_gy[pi], J.o_py_part[pi], J.sp_y[pi]);
   }
-  double gram_fl = 0;
-  for (auto& g : gram) gram_fl += 2.0 * g.M * g.N * g.K;
-  rec = prof_begin(ctx, "gemm_f64", 0, gram_fl);
-  FTN_TRY(run_gemms(ctx, gram, ws, ws, ws, ws_n, ws_n, ws_n, t_gram));
-  for (auto& r : reds) FTN_TRY(launch_sum_slabs(ctx, ws + r.dst, ws + r.src, r.count, r.nsplit, r.count));
-  prof_end(ctx, rec);
-  if (!chol.empty()) {
-    FTN_TRY(put_table(ctx, chol, &t_chol.p));
-    rec = prof_begin(ctx, "cholesky", 0, 0);
-    chol_kernel<<<(unsigned)chol.size(), LA_THREADS, 0, ctx->stream>>>((const CholJob*)t_chol.p);
-    ctx->launches += 1;
-    FTN_CUDA(cudaGetLastError());
-    prof_end(ctx, rec);
-  }
-  // ---- 2b. nonzero rows of the R factors (one synchronisation for the counts) ----
-  {
-    std::vector<CompactJob> cj;
-    int* cnt = (int*)(ws + o_cnt);
-    for (int pi = 0; pi < 2; ++pi) {
-      const int K = (int)P->K[pi];
-      if (K == 0 || rx[pi] == 0 || ry[pi] == 0) continue;
-      cj.push_back({ws + rx_off[pi], ws + o_rxc[pi], cnt + 2 * pi, rx[pi], K, ldx[pi]});
-      cj.push_back({ws + ry_off[pi], ws + o_ryc[pi], cnt + 2 * pi + 1, ry[pi], K, ldy[pi]});
-    }
-    int hc[4] = {0, 0, 0, 0};
-    if (!cj.empty()) {
-      DevBuf t_cj(ctx);
-      FTN_TRY(put_table(ctx, cj, &t_cj.p));
-      FTN_CUDA(cudaMemsetAsync(cnt, 0, 4 * sizeof(int), ctx->stream));
-      compact_rows_kernel<<<(unsigned)cj.size(), 256, 0, ctx->stream>>>((const CompactJob*)t_cj.p);
-      ctx->launches += 1;
-      FTN_CUDA(cudaGetLastError());
-      FTN_CUDA(cudaMemcpyAsync(hc, cnt, sizeof(hc), cudaMemcpyDeviceToHost, ctx->stream));
-      FTN_CUDA(cudaStreamSynchronize(ctx->stream));
-    }
-    for (int pi = 0; pi < 2; ++pi) {
-      const int K = (int)P->K[pi];
-      if (K == 0 || rx[pi] == 0 || ry[pi] == 0) {
-        rx[pi] = ry[pi] = 0;
-        continue;
-      }
-      if (hc[2 * pi] < 0 || hc[2 * pi] > rx[pi] || hc[2 * pi + 1] < 0 || hc[2 * pi + 1] > ry[pi])
-        return set_error(FTN_EINVAL, "internal error: R factor row count");
-      rx[pi] = hc[2 * pi];
-      ry[pi] = hc[2 * pi + 1];
-      rx_off[pi] = o_rxc[pi];
-      ldx[pi] = K;
-      ry_off[pi] = o_ryc[pi];
-      ldy[pi] = K;
-      trans[pi] = rx[pi] > ry[pi];  // rotate the shorter side
-      nrot[pi] = trans[pi] ? ry[pi] : rx[pi];
-      mlen[pi] = trans[pi] ? rx[pi] : ry[pi];
-    }
-  }
-  // ---- 3. core M = R_X R_Y^T (stored with the rotated side as rows) and SVD ----
-  std::vector<GemmProb> mg;
-  std::vector<SvdJob> svd;
+  FTN_TRY(add_gemm_set(gb, gram, ws, ws, ws, J.ws_n, J.ws_n, J.ws_n));
+  if (!red_in_bounds(reds, J.ws_n, J.ws_n)) return set_error(FTN_EINVAL, "internal error: Gram reduction out of bounds");
+  add_reductions(gb, reds, ws, ws);
+  return FTN_OK;
+}
+
+// After the row counts: the compacted R factors and the core's shape.
+ftn_status cj_counts(CJob& J, const int* hc) {
+  const TdPlan* P = J.P.get();
   for (int pi = 0; pi < 2; ++pi) {
     const int K = (int)P->K[pi];
-    if (K == 0 || rx[pi] == 0 || ry[pi] == 0) {
-      nrot[pi] = 0;
+    if (K == 0 || J.rx[pi] == 0 || J.ry[pi] == 0) {
+      J.rx[pi] = J.ry[pi] = 0;
       continue;
     }
-    GemmProb g = make_prob(rx[pi], ry[pi], K, rx_off[pi], ldx[pi], 1, ry_off[pi], ldy[pi], 1);
-    if (!trans[pi])
-      gemm_plain_output(g, o_m[pi], ry[pi]);  // M: rx x ry
-    else {
-      gemm_plain_output(g, o_m[pi], 0);  // M^T: ry x rx  (element (i, j) at j * rx + i)
-      g.rstr[0] = 1;
-      g.cstr[0] = rx[pi];
-    }
-    mg.push_back(g);
-    svd.push_back({ws + o_m[pi], ws + o_tf[pi], ws + o_s[pi], (int*)(ws + o_s[pi] + nrot[pi]), nrot[pi], mlen[pi]});
+    if (hc[2 * pi] < 0 || hc[2 * pi] > J.rx[pi] || hc[2 * pi + 1] < 0 || hc[2 * pi + 1] > J.ry[pi])
+      return set_error(FTN_EINVAL, "internal error: R factor row count");
+    J.rx[pi] = hc[2 * pi];
+    J.ry[pi] = hc[2 * pi + 1];
+    J.rx_off[pi] = J.o_rxc[pi];
+    J.ldx[pi] = K;
+    J.ry_off[pi] = J.o_ryc[pi];
+    J.ldy[pi] = K;
+    J.trans[pi] = J.rx[pi] > J.ry[pi];  // rotate the shorter side
+    J.nrot[pi] = J.trans[pi] ? J.ry[pi] : J.rx[pi];
+    J.mlen[pi] = J.trans[pi] ? J.rx[pi] : J.ry[pi];
   }
-  rec = prof_begin(ctx, "gemm_f64", 0, 0);
-  FTN_TRY(run_gemms(ctx, mg, ws, ws, ws, ws_n, ws_n, ws_n, t_m));
-  prof_end(ctx, rec);
-  if (!svd.empty()) {
-    // rows up to 32 * SVDC_MAX_E long whose cluster share fits in shared
-    // memory go to the cluster kernel, the others to the single-CTA one
-    const int cmax = svd_cluster_max(ctx);
-    std::vector<SvdJob> small, big;
-    int e_max = 1, c_use = 1;
-    for (const SvdJob& j : svd) {
-      const int np = j.n + (j.n & 1);
-      int c = 1;
-      while (c < cmax && c * SVDC_WARPS < np / 2) c *= 2;
-      while (c < cmax && (int64_t)((j.n + c - 1) / c) * j.m * 8 > SVDC_SMEM_BYTES) c *= 2;
-      if (j.m > 32 * SVDC_MAX_E || (int64_t)((j.n + c - 1) / c) * j.m * 8 > SVDC_SMEM_BYTES) {
-        big.push_back(j);
-        continue;
-      }
-      small.push_back(j);
-      c_use = std::max(c_use, c);
-      int e = 1;
-      while (32 * e < j.m) e *= 2;
-      e_max = std::max(e_max, e);
-    }
-    std::vector<SvdJob> all(small);
-    all.insert(all.end(), big.begin(), big.end());
-    FTN_TRY(put_table(ctx, all, &t_svd.p));
-    rec = prof_begin(ctx, "svd_jacobi", 0, 0);
-    if (!small.empty()) {
-      size_t smem = 0;
-      for (const SvdJob& j : small) smem = std::max(smem, (size_t)((j.n + c_use - 1) / c_use) * j.m * 8);
-      FTN_TRY(launch_svd_cluster(ctx, (const SvdJob*)t_svd.p, (int)small.size(), c_use, e_max, smem));
-    }
-    if (!big.empty()) {
-      svd_rows_global_kernel<<<(unsigned)big.size(), LA_THREADS, 0, ctx->stream>>>((const SvdJob*)t_svd.p +
-                                                                                   small.size());
-      ctx->launches += 1;
-      FTN_CUDA(cudaGetLastError());
-    }
-    prof_end(ctx, rec);
-  }
-  // ---- 4. pooled truncation (one synchronisation) ----
-  std::vector<double> sv[2];
-  for (int pi = 0; pi < 2; ++pi) {
-    sv[pi].resize(nrot[pi] + 1);
-    if (nrot[pi])
-      FTN_CUDA(cudaMemcpyAsync(sv[pi].data(), ws + o_s[pi], (nrot[pi] + 1) * 8, cudaMemcpyDeviceToHost,
-                               ctx->stream));
-  }
-  FTN_CUDA(cudaStreamSynchronize(ctx->stream));
+  return FTN_OK;
+}
+
+// Pooled truncation from the singular values of both sectors (values, then
+// the sweep count, per sector at sv + s_off).
+void cj_truncate(CJob& J, const double* sv) {
+  std::vector<CJob::Cand> cand;
+  double smax = 0, total = 0;
   int sweeps_used = 0;
   for (int pi = 0; pi < 2; ++pi) {
-    if (!nrot[pi]) continue;
+    if (!J.nrot[pi]) continue;
+    const double* s = sv + J.s_off[pi];
     int sw = 0;
-    std::memcpy(&sw, &sv[pi][nrot[pi]], sizeof(int));
+    std::memcpy(&sw, s + J.nrot[pi], sizeof(int));
     sweeps_used = std::max(sweeps_used, sw);
-    sv[pi].resize(nrot[pi]);
-  }
-  struct Cand {
-    double s;
-    int pi, idx;
-  };
-  std::vector<Cand> cand;
-  double smax = 0, total = 0;
-  for (int pi = 0; pi < 2; ++pi)
-    for (int i = 0; i < nrot[pi]; ++i) {
-      cand.push_back({sv[pi][i], pi, i});
-      smax = std::max(smax, sv[pi][i]);
-      total += sv[pi][i] * sv[pi][i];
+    for (int i = 0; i < J.nrot[pi]; ++i) {
+      cand.push_back({s[i], pi, i});
+      smax = std::max(smax, s[i]);
+      total += s[i] * s[i];
     }
-  std::stable_sort(cand.begin(), cand.end(), [](const Cand& a, const Cand& b) {
+  }
+  std::stable_sort(cand.begin(), cand.end(), [](const CJob::Cand& a, const CJob::Cand& b) {
     if (a.s != b.s) return a.s > b.s;
     if (a.pi != b.pi) return a.pi < b.pi;
     return a.idx < b.idx;
@@ -937,144 +811,350 @@ ftn_status compress_impl(ftn_ctx ctx, ftn_tensor* pX, ftn_tensor* pY, int n, con
   int rank_s[2] = {0, 0};
   for (auto& c : cand)
     if (c.s > zero_tol) rank_s[c.pi]++;
-  std::vector<Cand> kept;
   double disc = 0;
+  J.kept.clear();
   for (size_t i = 0; i < cand.size(); ++i) {
-    if ((int)kept.size() < chi && cand[i].s > zero_tol)
-      kept.push_back(cand[i]);
+    if ((int)J.kept.size() < J.it->chi && cand[i].s > zero_tol)
+      J.kept.push_back(cand[i]);
     else
       disc += cand[i].s * cand[i].s;
   }
-  int k[2] = {0, 0};
-  for (auto& c : kept) k[c.pi]++;
+  J.k[0] = J.k[1] = 0;
+  for (auto& c : J.kept) J.k[c.pi]++;
+  if (ftn_compress_info* info = J.it->info) {
+    info->kept[0] = J.k[0];
+    info->kept[1] = J.k[1];
+    info->rank[0] = rank_s[0];
+    info->rank[1] = rank_s[1];
+    info->discarded_sq = disc;
+    info->total_sq = total;
+    info->s_max = smax;
+    info->s_cut = J.kept.empty() ? 0.0 : J.kept.back().s;
+    info->s_next = J.kept.size() < cand.size() ? cand[J.kept.size()].s : 0.0;
+    info->jacobi_sweeps = sweeps_used;
+  }
+}
+
+}  // namespace
+
+// Batched compression: every stage of every job contributes to one launch
+// per kernel; two host synchronisations per batch (the R-factor row counts
+// and the singular values).
+ftn_status compress_batch(ftn_ctx ctx, std::vector<CompressItem>& items) {
+  if (!ctx) return set_error(FTN_EINVAL, "null argument");
+  if (items.empty()) return FTN_OK;
+  std::vector<CJob> jobs(items.size());
+  int64_t total = 0;
+  for (size_t i = 0; i < items.size(); ++i) {
+    jobs[i].it = &items[i];
+    FTN_TRY(cj_prepare(ctx, jobs[i]));
+    jobs[i].ws_off = total;
+    total += jobs[i].ws_n;
+  }
+  // shared small buffers after the jobs' workspaces: [row counts: 4 ints per job | singular values]
+  int64_t s_total = 0;
+  for (CJob& J : jobs)
+    for (int pi = 0; pi < 2; ++pi) {
+      J.s_off[pi] = s_total;
+      s_total += J.nrot[pi] + 1;  // values, then the sweep count
+    }
+  const int64_t cnt_words = ((int64_t)jobs.size() * 4 * (int64_t)sizeof(int) + 7) / 8;
+  double* ws = (double*)workspace(ctx, (size_t)(total + cnt_words + s_total + 32) * 8);
+  if (!ws) return set_error(FTN_ENOMEM, "workspace allocation failed");
+  for (CJob& J : jobs) J.ws = ws + J.ws_off;
+  int* cnt = (int*)(ws + total);
+  double* sbuf = ws + total + cnt_words;
+
+  // ---- 1. fused matrices ----
+  {
+    PermBatch pb;
+    for (CJob& J : jobs) {
+      const TdPlan* P = J.P.get();
+      pb.add(P->ja, P->ta, P->sa, J.it->X->data, J.ws + J.o_xf);
+      pb.add(P->jb, P->tb, P->sb, J.it->Y->data, J.ws + J.o_yf);
+    }
+    FTN_TRY(flush_perm(ctx, pb, FTN_F64, PERM_SAME, 0));
+  }
+  // ---- 2. Gram matrices and R factors ----
+  {
+    GemmF64Batch gb(ctx);
+    std::vector<CholJob> chol;
+    for (CJob& J : jobs) FTN_TRY(cj_gram(J, gb, chol));
+    FTN_TRY(flush_gemm_f64(gb));
+    if (!chol.empty()) {
+      DevBuf t_chol(ctx);
+      FTN_TRY(put_table(ctx, chol, &t_chol.p));
+      const int rec = prof_begin(ctx, "cholesky", 0, 0);
+      chol_kernel<<<(unsigned)chol.size(), LA_THREADS, 0, ctx->stream>>>((const CholJob*)t_chol.p);
+      ctx->launches += 1;
+      FTN_CUDA(cudaGetLastError());
+      prof_end(ctx, rec);
+    }
+  }
+  // ---- 2b. nonzero rows of the R factors (one synchronisation for the counts) ----
+  {
+    std::vector<CompactJob> cj;
+    for (size_t q = 0; q < jobs.size(); ++q) {
+      CJob& J = jobs[q];
+      for (int pi = 0; pi < 2; ++pi) {
+        const int K = (int)J.P->K[pi];
+        if (K == 0 || J.rx[pi] == 0 || J.ry[pi] == 0) continue;
+        cj.push_back({J.ws + J.rx_off[pi], J.ws + J.o_rxc[pi], cnt + 4 * q + 2 * pi, J.rx[pi], K, J.ldx[pi]});
+        cj.push_back({J.ws + J.ry_off[pi], J.ws + J.o_ryc[pi], cnt + 4 * q + 2 * pi + 1, J.ry[pi], K, J.ldy[pi]});
+      }
+    }
+    std::vector<int> hc(4 * jobs.size(), 0);
+    if (!cj.empty()) {
+      DevBuf t_cj(ctx);
+      FTN_TRY(put_table(ctx, cj, &t_cj.p));
+      FTN_CUDA(cudaMemsetAsync(cnt, 0, hc.size() * sizeof(int), ctx->stream));
+      compact_rows_kernel<<<(unsigned)cj.size(), 256, 0, ctx->stream>>>((const CompactJob*)t_cj.p);
+      ctx->launches += 1;
+      FTN_CUDA(cudaGetLastError());
+      FTN_CUDA(cudaMemcpyAsync(hc.data(), cnt, hc.size() * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+      FTN_CUDA(cudaStreamSynchronize(ctx->stream));
+    }
+    for (size_t q = 0; q < jobs.size(); ++q) FTN_TRY(cj_counts(jobs[q], hc.data() + 4 * q));
+  }
+  // ---- 3. core M = R_X R_Y^T (stored with the rotated side as rows) and SVD ----
+  {
+    GemmF64Batch gb(ctx);
+    std::vector<SvdJob> svd;
+    for (CJob& J : jobs) {
+      std::vector<GemmProb> mg;
+      for (int pi = 0; pi < 2; ++pi) {
+        const int K = (int)J.P->K[pi];
+        if (K == 0 || J.rx[pi] == 0 || J.ry[pi] == 0) {
+          J.nrot[pi] = 0;
+          continue;
+        }
+        GemmProb g = make_prob(J.rx[pi], J.ry[pi], K, J.rx_off[pi], J.ldx[pi], 1, J.ry_off[pi], J.ldy[pi], 1);
+        if (!J.trans[pi])
+          gemm_plain_output(g, J.o_m[pi], J.ry[pi]);  // M: rx x ry
+        else {
+          gemm_plain_output(g, J.o_m[pi], 0);  // M^T: ry x rx  (element (i, j) at j * rx + i)
+          g.rstr[0] = 1;
+          g.cstr[0] = J.rx[pi];
+        }
+        mg.push_back(g);
+        double* s = sbuf + J.s_off[pi];
+        svd.push_back({J.ws + J.o_m[pi], J.ws + J.o_tf[pi], s, (int*)(s + J.nrot[pi]), J.nrot[pi], J.mlen[pi]});
+      }
+      FTN_TRY(add_gemm_set(gb, mg, J.ws, J.ws, J.ws, J.ws_n, J.ws_n, J.ws_n));
+    }
+    FTN_TRY(flush_gemm_f64(gb));
+    if (!svd.empty()) {
+      // rows up to 32 * SVDC_MAX_E long whose cluster share fits in shared
+      // memory go to the cluster kernel -- one launch per cluster size and
+      // row length, so that a decomposition does not depend on the others
+      // in the batch -- the others to the single-CTA one
+      const int cmax = svd_cluster_max(ctx);
+      std::map<std::pair<int, int>, std::vector<SvdJob>> small;
+      std::vector<SvdJob> big;
+      for (const SvdJob& j : svd) {
+        const int np = j.n + (j.n & 1);
+        int c = 1;
+        while (c < cmax && c * SVDC_WARPS < np / 2) c *= 2;
+        while (c < cmax && (int64_t)((j.n + c - 1) / c) * j.m * 8 > SVDC_SMEM_BYTES) c *= 2;
+        if (j.m > 32 * SVDC_MAX_E || (int64_t)((j.n + c - 1) / c) * j.m * 8 > SVDC_SMEM_BYTES) {
+          big.push_back(j);
+          continue;
+        }
+        int e = 1;
+        while (32 * e < j.m) e *= 2;
+        small[{c, e}].push_back(j);
+      }
+      std::vector<SvdJob> all;
+      std::vector<size_t> first;
+      for (auto& kv : small) {
+        first.push_back(all.size());
+        all.insert(all.end(), kv.second.begin(), kv.second.end());
+      }
+      const size_t big0 = all.size();
+      all.insert(all.end(), big.begin(), big.end());
+      DevBuf t_svd(ctx);
+      FTN_TRY(put_table(ctx, all, &t_svd.p));
+      const int rec = prof_begin(ctx, "svd_jacobi", 0, 0);
+      size_t g = 0;
+      for (auto& kv : small) {
+        size_t smem = 0;
+        const int c = kv.first.first;
+        for (const SvdJob& j : kv.second) smem = std::max(smem, (size_t)((j.n + c - 1) / c) * j.m * 8);
+        FTN_TRY(launch_svd_cluster(ctx, (const SvdJob*)t_svd.p + first[g++], (int)kv.second.size(), c,
+                                   kv.first.second, smem));
+      }
+      if (!big.empty()) {
+        svd_rows_global_kernel<<<(unsigned)big.size(), LA_THREADS, 0, ctx->stream>>>((const SvdJob*)t_svd.p + big0);
+        ctx->launches += 1;
+        FTN_CUDA(cudaGetLastError());
+      }
+      prof_end(ctx, rec);
+    }
+  }
+  // ---- 4. pooled truncation (one synchronisation) ----
+  {
+    std::vector<double> sv(s_total + 1);
+    if (s_total) FTN_CUDA(cudaMemcpyAsync(sv.data(), sbuf, s_total * 8, cudaMemcpyDeviceToHost, ctx->stream));
+    FTN_CUDA(cudaStreamSynchronize(ctx->stream));
+    for (CJob& J : jobs) cj_truncate(J, sv.data());
+  }
   // ---- 5. projectors and the new tensors ----
   // m-side vectors (the orthogonalised rows' direction) come from T_f rows;
   // n-side vectors as T u_j / s_j by one GEMM with the untouched T.  Both are
   // wanted scaled by s^{-1/2}: MS = T_f row * s^{-3/2}, MS3 = T_f row * s^{-5/2}
   // and NS = MS3 T^T.  Without transposition the m side is the right (ry)
   // side of M, with it the left (rx) side.
-  std::vector<GatherJob> gat;
-  int pos[2] = {0, 0};
-  for (auto& c : kept) {
-    const int pi = c.pi, j = pos[pi]++;
-    const double* row = ws + o_tf[pi] + (int64_t)c.idx * mlen[pi];
-    const double is = 1.0 / sqrt(c.s);
-    GatherJob g;
-    g.left = row;
-    g.nl = mlen[pi];
-    g.sl = is / c.s;
-    g.right = row;
-    g.nr = mlen[pi];
-    g.sr = is / (c.s * c.s);
-    g.dl = ws + (trans[pi] ? o_wk[pi] : o_zk[pi]) + (int64_t)j * mlen[pi];
-    g.dr = ws + o_ms3[pi] + (int64_t)j * mlen[pi];
-    gat.push_back(g);
+  {
+    std::vector<GatherJob> gat;
+    for (CJob& J : jobs) {
+      int pos[2] = {0, 0};
+      for (auto& c : J.kept) {
+        const int pi = c.pi, j = pos[pi]++;
+        const double* row = J.ws + J.o_tf[pi] + (int64_t)c.idx * J.mlen[pi];
+        const double is = 1.0 / sqrt(c.s);
+        GatherJob g;
+        g.left = row;
+        g.nl = J.mlen[pi];
+        g.sl = is / c.s;
+        g.right = row;
+        g.nr = J.mlen[pi];
+        g.sr = is / (c.s * c.s);
+        g.dl = J.ws + (J.trans[pi] ? J.o_wk[pi] : J.o_zk[pi]) + (int64_t)j * J.mlen[pi];
+        g.dr = J.ws + J.o_ms3[pi] + (int64_t)j * J.mlen[pi];
+        gat.push_back(g);
+      }
+    }
+    if (!gat.empty()) {
+      DevBuf t_gat(ctx);
+      FTN_TRY(put_table(ctx, gat, &t_gat.p));
+      gather_kernel<<<(unsigned)gat.size(), 128, 0, ctx->stream>>>((const GatherJob*)t_gat.p);
+      ctx->launches += 1;
+      FTN_CUDA(cudaGetLastError());
+    }
   }
-  if (!gat.empty()) {
-    FTN_TRY(put_table(ctx, gat, &t_gat.p));
-    gather_kernel<<<(unsigned)gat.size(), 128, 0, ctx->stream>>>((const GatherJob*)t_gat.p);
-    ctx->launches += 1;
-    FTN_CUDA(cudaGetLastError());
-  }
-  std::vector<GemmProb> nside;
-  for (int pi = 0; pi < 2; ++pi) {
-    if (k[pi] == 0) continue;
+  {
     // NS[j, r] = sum_c MS3[j, c] T[r, c]   (k x nrot)
-    GemmProb g = make_prob(k[pi], nrot[pi], mlen[pi], o_ms3[pi], mlen[pi], 1, o_m[pi], mlen[pi], 1);
-    gemm_plain_output(g, trans[pi] ? o_zk[pi] : o_wk[pi], nrot[pi]);
-    nside.push_back(g);
-  }
-  DevBuf t_ns(ctx);
-  rec = prof_begin(ctx, "gemm_f64", 0, 0);
-  FTN_TRY(run_gemms(ctx, nside, ws, ws, ws, ws_n, ws_n, ws_n, t_ns));
-  prof_end(ctx, rec);
-  // P_X^T = Z_k R_Y (k x K) and Q_Y^T = W_k R_X (k x K)
-  std::vector<GemmProb> proj;
-  for (int pi = 0; pi < 2; ++pi) {
-    const int K = (int)P->K[pi];
-    if (k[pi] == 0) continue;
-    GemmProb a = make_prob(k[pi], K, ry[pi], o_zk[pi], ry[pi], 1, ry_off[pi], 1, ldy[pi]);
-    gemm_plain_output(a, o_px[pi], K);
-    proj.push_back(a);
-    GemmProb b = make_prob(k[pi], K, rx[pi], o_wk[pi], rx[pi], 1, rx_off[pi], 1, ldx[pi]);
-    gemm_plain_output(b, o_qy[pi], K);
-    proj.push_back(b);
-  }
-  rec = prof_begin(ctx, "gemm_f64", 0, 0);
-  FTN_TRY(run_gemms(ctx, proj, ws, ws, ws, ws_n, ws_n, ws_n, t_proj));
-  prof_end(ctx, rec);
-  // new tensors: X' = [free_X | new(-)], Y' = [new(+) | free_Y]
-  int32_t xd0[MAXR], xd1[MAXR], yd0[MAXR], yd1[MAXR];
-  uint8_t xdu[MAXR], ydu[MAXR];
-  for (int j = 0; j < P->nfa; ++j)
-    xd0[j] = X->d0[P->fa[j]], xd1[j] = X->d1[P->fa[j]], xdu[j] = X->dual[P->fa[j]];
-  xd0[P->nfa] = k[0], xd1[P->nfa] = k[1], xdu[P->nfa] = 1;
-  yd0[0] = k[0], yd1[0] = k[1], ydu[0] = 0;
-  for (int j = 0; j < P->nfb; ++j)
-    yd0[j + 1] = Y->d0[P->fb[j]], yd1[j + 1] = Y->d1[P->fb[j]], ydu[j + 1] = Y->dual[P->fb[j]];
-  ftn_tensor Xn = nullptr, Yn = nullptr;
-  FTN_TRY(make_tensor(ctx, P->nfa + 1, xd0, xd1, xdu, X->parity, FTN_F64, &Xn));
-  ftn_status st = make_tensor(ctx, P->nfb + 1, yd0, yd1, ydu, Y->parity, FTN_F64, &Yn);
-  if (st != FTN_OK) {
-    ftn_tensor_free(Xn);
-    return st;
-  }
-  std::vector<GemmProb> fx, fy;
-  for (int pi = 0; pi < 2; ++pi) {
-    if (k[pi] == 0) continue;
-    const int K = (int)P->K[pi];
-    const int rho = X->parity ^ pi, sig = Y->parity ^ pi;
-    for (uint32_t mA = 0; mA < (1u << P->nfa); ++mA) {
-      if ((popc(mA) & 1) != rho || P->rowsz[pi][mA] == 0) continue;
-      const uint32_t mask = mA | ((uint32_t)pi << P->nfa);
-      GemmProb g = make_prob((int)P->rowsz[pi][mA], k[pi], K, o_xf + P->afoff[pi] + P->rowoff[pi][mA] * P->ldk[pi],
-                             P->ldk[pi], 1, o_px[pi], K, 1);
-      gemm_plain_output(g, Xn->offsets[mask >> 1], k[pi]);
-      fx.push_back(g);
+    GemmF64Batch gb(ctx);
+    for (CJob& J : jobs) {
+      std::vector<GemmProb> nside;
+      for (int pi = 0; pi < 2; ++pi) {
+        if (J.k[pi] == 0) continue;
+        GemmProb g = make_prob(J.k[pi], J.nrot[pi], J.mlen[pi], J.o_ms3[pi], J.mlen[pi], 1, J.o_m[pi], J.mlen[pi], 1);
+        gemm_plain_output(g, J.trans[pi] ? J.o_zk[pi] : J.o_wk[pi], J.nrot[pi]);
+        nside.push_back(g);
+      }
+      FTN_TRY(add_gemm_set(gb, nside, J.ws, J.ws, J.ws, J.ws_n, J.ws_n, J.ws_n));
     }
-    for (uint32_t mB = 0; mB < (1u << P->nfb); ++mB) {
-      if ((popc(mB) & 1) != sig || P->colsz[pi][mB] == 0) continue;
-      const uint32_t mask = (uint32_t)pi | (mB << 1);
-      const int Cm = (int)P->colsz[pi][mB];
-      GemmProb g = make_prob(Cm, k[pi], K, o_yf + P->bfoff[pi] + P->coloff[pi][mB] * P->ldk[pi], P->ldk[pi], 1,
-                             o_qy[pi], K, 1);
-      gemm_plain_output(g, Yn->offsets[mask >> 1], 0);  // written transposed: (new, free)
-      g.rstr[0] = 1;
-      g.cstr[0] = Cm;
-      fy.push_back(g);
+    FTN_TRY(flush_gemm_f64(gb));
+  }
+  {
+    // P_X^T = Z_k R_Y (k x K) and Q_Y^T = W_k R_X (k x K)
+    GemmF64Batch gb(ctx);
+    for (CJob& J : jobs) {
+      std::vector<GemmProb> proj;
+      for (int pi = 0; pi < 2; ++pi) {
+        const int K = (int)J.P->K[pi];
+        if (J.k[pi] == 0) continue;
+        GemmProb a = make_prob(J.k[pi], K, J.ry[pi], J.o_zk[pi], J.ry[pi], 1, J.ry_off[pi], 1, J.ldy[pi]);
+        gemm_plain_output(a, J.o_px[pi], K);
+        proj.push_back(a);
+        GemmProb b = make_prob(J.k[pi], K, J.rx[pi], J.o_wk[pi], J.rx[pi], 1, J.rx_off[pi], 1, J.ldx[pi]);
+        gemm_plain_output(b, J.o_qy[pi], K);
+        proj.push_back(b);
+      }
+      FTN_TRY(add_gemm_set(gb, proj, J.ws, J.ws, J.ws, J.ws_n, J.ws_n, J.ws_n));
     }
+    FTN_TRY(flush_gemm_f64(gb));
   }
-  // blocks of the new tensors that no GEMM writes (empty kept sector) are zero
-  if (Xn->numel) FTN_CUDA(cudaMemsetAsync(Xn->data, 0, Xn->numel * 8, ctx->stream));
-  if (Yn->numel) FTN_CUDA(cudaMemsetAsync(Yn->data, 0, Yn->numel * 8, ctx->stream));
-  double fl = 0;
-  for (auto& g : fx) fl += 2.0 * g.M * g.N * g.K;
-  for (auto& g : fy) fl += 2.0 * g.M * g.N * g.K;
-  rec = prof_begin(ctx, "gemm_f64", 0, fl);
-  st = run_gemms(ctx, fx, ws, ws, (double*)Xn->data, ws_n, ws_n, Xn->numel, t_fx);
-  if (st == FTN_OK) st = run_gemms(ctx, fy, ws, ws, (double*)Yn->data, ws_n, ws_n, Yn->numel, t_fy);
-  prof_end(ctx, rec);
-  if (st != FTN_OK) {
-    ftn_tensor_free(Xn);
-    ftn_tensor_free(Yn);
-    return st;
+  // new tensors: X' = [free_X | new(-)], Y' = [new(+) | free_Y].  Every
+  // element of every block is written by one GEMM below: a block has nonzero
+  // size only if its sector of the new leg kept states (k > 0), and then its
+  // free-row (free-column) sector is one problem of the set.
+  struct Outs {
+    std::vector<CJob>& v;
+    bool ok = false;
+    ~Outs() {
+      if (ok) return;
+      for (CJob& J : v) {
+        ftn_tensor_free(J.Xn);
+        ftn_tensor_free(J.Yn);
+        J.Xn = J.Yn = nullptr;
+      }
+    }
+  } outs{jobs};
+  {
+    GemmF64Batch gb(ctx);
+    for (CJob& J : jobs) {
+      const TdPlan* P = J.P.get();
+      ftn_tensor X = J.it->X, Y = J.it->Y;
+      int32_t xd0[MAXR], xd1[MAXR], yd0[MAXR], yd1[MAXR];
+      uint8_t xdu[MAXR], ydu[MAXR];
+      for (int j = 0; j < P->nfa; ++j)
+        xd0[j] = X->d0[P->fa[j]], xd1[j] = X->d1[P->fa[j]], xdu[j] = X->dual[P->fa[j]];
+      xd0[P->nfa] = J.k[0], xd1[P->nfa] = J.k[1], xdu[P->nfa] = 1;
+      yd0[0] = J.k[0], yd1[0] = J.k[1], ydu[0] = 0;
+      for (int j = 0; j < P->nfb; ++j)
+        yd0[j + 1] = Y->d0[P->fb[j]], yd1[j + 1] = Y->d1[P->fb[j]], ydu[j + 1] = Y->dual[P->fb[j]];
+      FTN_TRY(make_tensor(ctx, P->nfa + 1, xd0, xd1, xdu, X->parity, FTN_F64, &J.Xn));
+      FTN_TRY(make_tensor(ctx, P->nfb + 1, yd0, yd1, ydu, Y->parity, FTN_F64, &J.Yn));
+      std::vector<GemmProb> fx, fy;
+      for (int pi = 0; pi < 2; ++pi) {
+        if (J.k[pi] == 0) continue;
+        const int K = (int)P->K[pi];
+        const int rho = X->parity ^ pi, sig = Y->parity ^ pi;
+        for (uint32_t mA = 0; mA < (1u << P->nfa); ++mA) {
+          if ((popc(mA) & 1) != rho || P->rowsz[pi][mA] == 0) continue;
+          const uint32_t mask = mA | ((uint32_t)pi << P->nfa);
+          GemmProb g = make_prob((int)P->rowsz[pi][mA], J.k[pi], K,
+                                 J.o_xf + P->afoff[pi] + P->rowoff[pi][mA] * P->ldk[pi], P->ldk[pi], 1, J.o_px[pi], K,
+                                 1);
+          gemm_plain_output(g, J.Xn->offsets[mask >> 1], J.k[pi]);
+          fx.push_back(g);
+        }
+        for (uint32_t mB = 0; mB < (1u << P->nfb); ++mB) {
+          if ((popc(mB) & 1) != sig || P->colsz[pi][mB] == 0) continue;
+          const uint32_t mask = (uint32_t)pi | (mB << 1);
+          const int Cm = (int)P->colsz[pi][mB];
+          GemmProb g = make_prob(Cm, J.k[pi], K, J.o_yf + P->bfoff[pi] + P->coloff[pi][mB] * P->ldk[pi], P->ldk[pi],
+                                 1, J.o_qy[pi], K, 1);
+          gemm_plain_output(g, J.Yn->offsets[mask >> 1], 0);  // written transposed: (new, free)
+          g.rstr[0] = 1;
+          g.cstr[0] = Cm;
+          fy.push_back(g);
+        }
+      }
+      FTN_TRY(add_gemm_set(gb, fx, J.ws, J.ws, (double*)J.Xn->data, J.ws_n, J.ws_n, J.Xn->numel));
+      FTN_TRY(add_gemm_set(gb, fy, J.ws, J.ws, (double*)J.Yn->data, J.ws_n, J.ws_n, J.Yn->numel));
+    }
+    FTN_TRY(flush_gemm_f64(gb));
   }
-  if (info) {
-    info->kept[0] = k[0];
-    info->kept[1] = k[1];
-    info->rank[0] = rank_s[0];
-    info->rank[1] = rank_s[1];
-    info->discarded_sq = disc;
-    info->total_sq = total;
-    info->s_max = smax;
-    info->s_cut = kept.empty() ? 0.0 : kept.back().s;
-    info->s_next = kept.size() < cand.size() ? cand[kept.size()].s : 0.0;
-    info->jacobi_sweeps = sweeps_used;
+  outs.ok = true;
+  for (CJob& J : jobs) {
+    ftn_tensor_free(J.it->X);
+    ftn_tensor_free(J.it->Y);
+    J.it->X = J.Xn;
+    J.it->Y = J.Yn;
   }
-  ftn_tensor_free(X);
-  ftn_tensor_free(Y);
-  *pX = Xn;
-  *pY = Yn;
+  return FTN_OK;
+}
+
+ftn_status compress_impl(ftn_ctx ctx, ftn_tensor* pX, ftn_tensor* pY, int n, const int* ax, const int* ay, int chi,
+                         int arrows, ftn_compress_info* info) {
+  if (!ctx || !pX || !pY || !*pX || !*pY || (n > 0 && (!ax || !ay))) return set_error(FTN_EINVAL, "null argument");
+  if (n < 1) return set_error(FTN_EINVAL, "a bond needs at least one leg pair");
+  if (n > MAXR) return set_error(FTN_EINVAL, "too many bond legs");
+  std::vector<CompressItem> items(1);
+  CompressItem& it = items[0];
+  it.X = *pX;
+  it.Y = *pY;
+  it.n = n;
+  for (int i = 0; i < n; ++i) it.ax[i] = ax[i], it.ay[i] = ay[i];
+  it.chi = chi;
+  it.arrows = arrows;
+  it.info = info;
+  FTN_TRY(compress_batch(ctx, items));
+  *pX = it.X;
+  *pY = it.Y;
   return FTN_OK;
 }
 

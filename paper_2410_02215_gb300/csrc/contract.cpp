@@ -1,5 +1,6 @@
-// Contraction-tree executor ftn_contract (Fig. 1; Secs. II.C-II.D; Sec. III)
-// and the Hubbard operator tensors ftn_hubbard_term (Eq. fermi-hubbard-ham).
+// Contraction-tree executor ftn_contract / ftn_contract_batch (Fig. 1;
+// Secs. II.C-II.D; Sec. III) and the Hubbard operator tensors
+// ftn_hubbard_term (Eq. fermi-hubbard-ham).
 //
 // The executor walks an SSA tree of pairwise contractions.  Locally ordered
 // formalism (no positions): every step is op(a, b) with the bond parity of
@@ -12,21 +13,25 @@
 // late, bonds above chi, neighbours in increasing id) uses ftn_compress; each
 // new tensor is divided by its largest |entry| on the device with the natural
 // log accumulated in FP64.
+//
+// Many networks run in lock step: round s performs step s of every network
+// that has one -- the compressions before it (one sub-round per position in
+// each network's own list, so a network's compressions keep their order),
+// the pairwise contraction, the compressions after it and the normalisation
+// -- each stage as one batched launch per kernel over all networks.  One
+// network is the batch of one.
 #include <algorithm>
 #include <cmath>
 #include <map>
+#include <memory>
 #include <set>
 
-#include "tdplan.h"
+#include "batch.h"
 
 namespace ftn {
 
 ftn_status normalize_tensor(ftn_ctx ctx, ftn_tensor t, void* d_state, int step);
 ftn_status cast_tensor(ftn_ctx ctx, ftn_tensor t, ftn_dtype to, ftn_tensor* out);
-ftn_status compress_impl(ftn_ctx ctx, ftn_tensor* pX, ftn_tensor* pY, int n, const int* ax, const int* ay, int chi,
-                         int arrows, ftn_compress_info* info);
-ftn_status tensordot_impl(ftn_ctx ctx, ftn_tensor A, ftn_tensor B, int n, const int* ax, const int* ay,
-                          uint64_t flip_a, uint64_t flip_b, const int* out_perm, ftn_prec prec, ftn_tensor* C);
 
 namespace {
 
@@ -37,14 +42,18 @@ struct Live {
 };
 
 struct Exec {
-  ftn_ctx ctx;
-  ftn_prec prec;
+  ftn_prec prec = FTN_PREC_F64;
   bool global = false;
+  const ftn_tree* tree = nullptr;
+  int n = 0;
   std::map<int64_t, Live> live;
   std::map<int64_t, int64_t> partner;  // leg id -> leg id
   std::map<int64_t, int64_t> owner;    // leg id -> tensor id
   int64_t next_leg = 1ll << 40;
   int sign = 1;
+  Exec() = default;
+  Exec(const Exec&) = delete;
+  Exec& operator=(const Exec&) = delete;
   ~Exec() {
     for (auto& kv : live) ftn_tensor_free(kv.second.t);
   }
@@ -85,48 +94,99 @@ struct Exec {
     live[i].ids = std::move(ids);
   }
 
-  ftn_status compress_pair(int64_t x, int64_t y, int chi) {
+  ftn_status init(ftn_ctx ctx, const ftn_network* net, const ftn_tree* tr, ftn_prec pr) {
+    if (!net || !tr) return set_error(FTN_EINVAL, "null argument");
+    n = net->n_tensors;
+    if (n < 1 || !net->tensors) return set_error(FTN_EINVAL, "empty network");
+    if (tr->n_steps != n - 1 || (n > 1 && !tr->pairs)) return set_error(FTN_EINVAL, "tree needs n_tensors - 1 steps");
+    if (tr->policy != FTN_POLICY_EXACT && tr->chi < 1) return set_error(FTN_EINVAL, "chi must be >= 1");
+    if (net->n_bonds > 0 && !net->bonds) return set_error(FTN_EINVAL, "null bond table");
+    tree = tr;
+    prec = pr;
+    global = net->positions != nullptr;
+    const ftn_dtype want = prec == FTN_PREC_F64 ? FTN_F64 : FTN_F32;
+    for (int i = 0; i < n; ++i) {
+      ftn_tensor t = net->tensors[i];
+      if (!t) return set_error(FTN_EINVAL, "null tensor in network");
+      if (t->dtype != want) return set_error(FTN_EUNSUPPORTED, "tensor dtype does not match the precision");
+      ftn_tensor view = nullptr;  // borrowed view: the executor never frees caller buffers
+      FTN_TRY(ftn_tensor_wrap(ctx, t->rank, t->d0, t->d1, t->dual, t->parity, t->dtype, t->data, &view));
+      Live L;
+      L.t = view;
+      L.pos = global ? net->positions[i] : 0;
+      for (int k = 0; k < t->rank; ++k) L.ids.push_back((int64_t)i * 64 + k);
+      live[i] = L;
+      for (int k = 0; k < t->rank; ++k) owner[(int64_t)i * 64 + k] = i;
+    }
+    for (int b = 0; b < net->n_bonds; ++b) {
+      const int32_t* q = net->bonds + 4 * b;
+      if (q[0] < 0 || q[0] >= n || q[2] < 0 || q[2] >= n || q[1] < 0 || q[3] < 0 ||
+          q[1] >= net->tensors[q[0]]->rank || q[3] >= net->tensors[q[2]]->rank)
+        return set_error(FTN_EINVAL, "bond out of range");
+      const int64_t u = (int64_t)q[0] * 64 + q[1], v = (int64_t)q[2] * 64 + q[3];
+      if (u == v || partner.count(u) || partner.count(v)) return set_error(FTN_EINVAL, "leg bonded twice");
+      partner[u] = v;
+      partner[v] = u;
+    }
+    return FTN_OK;
+  }
+
+  // the operands of step s, checked
+  ftn_status step_pair(int s, int64_t& a, int64_t& b) {
+    a = tree->pairs[2 * s];
+    b = tree->pairs[2 * s + 1];
+    if (!live.count(a) || !live.count(b) || a == b) return set_error(FTN_EINVAL, "tree refers to a dead tensor");
+    return FTN_OK;
+  }
+
+  // Compressions before a step (late policy): every other bond of both
+  // operands above chi, operand a first, neighbours in increasing id.  A
+  // compression changes only the bond it compresses, so the whole list can
+  // be taken before the first of them runs.
+  std::vector<std::pair<int64_t, int64_t>> late_pairs(int64_t a, int64_t b) {
+    std::vector<std::pair<int64_t, int64_t>> out;
+    for (int64_t op : {a, b}) {
+      const int64_t other = op == a ? b : a;
+      for (int64_t nb : neighbours(op))
+        if (nb != other && bond_dim(op, nb) > tree->chi) out.push_back({op, nb});
+    }
+    return out;
+  }
+
+  // Compressions after a step (early policy): every bond of the new tensor above chi.
+  std::vector<std::pair<int64_t, int64_t>> early_pairs(int64_t id) {
+    std::vector<std::pair<int64_t, int64_t>> out;
+    for (int64_t nb : neighbours(id))
+      if (bond_dim(id, nb) > tree->chi) out.push_back({id, nb});
+    return out;
+  }
+
+  // The compression of the bond between x and y as a batch item (x becomes
+  // the earlier tensor in the global order).
+  void compress_item(int64_t& x, int64_t& y, CompressItem& it) {
     if (global && live[x].pos > live[y].pos) std::swap(x, y);
     std::vector<int> ax, ay;
     shared(x, y, ax, ay);
+    it.X = live[x].t;
+    it.Y = live[y].t;
+    it.n = (int)ax.size();
+    for (int i = 0; i < it.n; ++i) it.ax[i] = ax[i], it.ay[i] = ay[i];
+    it.chi = tree->chi;
+    it.arrows = global ? 0 : 1;
+  }
+
+  // After the compression: the shared legs of x and y are one new bond (last
+  // leg of x, first leg of y).
+  void compress_done(int64_t x, int64_t y, const CompressItem& it) {
     Live& X = live[x];
     Live& Y = live[y];
-    ftn_tensor tx = X.t, ty = Y.t;
-    const bool f32 = tx->dtype == FTN_F32;
-    if (f32) {  // the decomposition runs in FP64
-      ftn_tensor wx = nullptr, wy = nullptr;
-      FTN_TRY(cast_tensor(ctx, tx, FTN_F64, &wx));
-      ftn_status st = cast_tensor(ctx, ty, FTN_F64, &wy);
-      if (st != FTN_OK) {
-        ftn_tensor_free(wx);
-        return st;
-      }
-      ftn_tensor_free(tx);
-      ftn_tensor_free(ty);
-      tx = wx;
-      ty = wy;
-      X.t = tx;
-      Y.t = ty;
-    }
-    FTN_TRY(compress_impl(ctx, &tx, &ty, (int)ax.size(), ax.data(), ay.data(), chi, global ? 0 : 1, nullptr));
-    X.t = tx;
-    Y.t = ty;
-    if (f32) {
-      ftn_tensor nx = nullptr, ny = nullptr;
-      FTN_TRY(cast_tensor(ctx, tx, FTN_F32, &nx));
-      FTN_TRY(cast_tensor(ctx, ty, FTN_F32, &ny));
-      ftn_tensor_free(tx);
-      ftn_tensor_free(ty);
-      X.t = nx;
-      Y.t = ny;
-    }
     std::vector<int64_t> fx, fy;
     for (int k = 0; k < (int)X.ids.size(); ++k)
-      if (std::find(ax.begin(), ax.end(), k) == ax.end()) fx.push_back(X.ids[k]);
+      if (std::find(it.ax, it.ax + it.n, k) == it.ax + it.n) fx.push_back(X.ids[k]);
       else
         partner.erase(X.ids[k]);
     for (int k = 0; k < (int)Y.ids.size(); ++k)
-      if (std::find(ay.begin(), ay.end(), k) == ay.end()) fy.push_back(Y.ids[k]);
+      if (std::find(it.ay, it.ay + it.n, k) == it.ay + it.n) fy.push_back(Y.ids[k]);
       else
         partner.erase(Y.ids[k]);
     const int64_t lx = next_leg++, ly = next_leg++;
@@ -136,137 +196,226 @@ struct Exec {
     fy.insert(fy.begin(), ly);
     set_ids(x, fx);
     set_ids(y, fy);
-    return FTN_OK;
+  }
+
+  // The pairwise contraction of a step as a batch item: e is the earlier
+  // operand, l the later (moved past the tensors between them).
+  void step_item(int64_t a, int64_t b, int64_t& e, int64_t& l, TdItem& it) {
+    std::vector<int> ax, ay;
+    e = a;
+    l = b;
+    uint64_t flip_e = 0, flip_l = 0;
+    if (global) {
+      if (live[a].pos > live[b].pos) std::swap(e, l);
+      std::vector<int> cx, cl;
+      for (auto& kv : live) {
+        const int64_t c = kv.first;
+        if (c == e || c == l || !(live[e].pos < kv.second.pos && kv.second.pos < live[l].pos)) continue;
+        shared(c, l, cx, cl);
+        for (int k : cl) flip_l |= 1ull << k;
+        if (kv.second.t->parity & live[l].t->parity) sign = -sign;
+      }
+      shared(e, l, ax, ay);
+      for (int k : ax)  // plain ordered contraction: cancel the arrow parity
+        if (live[e].t->dual[k] == 0) flip_e |= 1ull << k;
+    } else {
+      shared(e, l, ax, ay);
+    }
+    it.A = live[e].t;
+    it.B = live[l].t;
+    it.n = (int)ax.size();
+    for (int i = 0; i < it.n; ++i) it.ax[i] = ax[i], it.ay[i] = ay[i];
+    it.fa = flip_e;
+    it.fb = flip_l;
+    it.C = nullptr;
+  }
+
+  // The result of step s replaces its operands (id n + s at e's position).
+  int64_t step_done(int s, int64_t e, int64_t l, const TdItem& it) {
+    std::vector<int64_t> ids;
+    for (int k = 0; k < (int)live[e].ids.size(); ++k)
+      if (std::find(it.ax, it.ax + it.n, k) == it.ax + it.n) ids.push_back(live[e].ids[k]);
+      else
+        partner.erase(live[e].ids[k]);
+    for (int k = 0; k < (int)live[l].ids.size(); ++k)
+      if (std::find(it.ay, it.ay + it.n, k) == it.ay + it.n) ids.push_back(live[l].ids[k]);
+      else
+        partner.erase(live[l].ids[k]);
+    const int64_t pos = live[e].pos;
+    ftn_tensor_free(live[e].t);
+    ftn_tensor_free(live[l].t);
+    live.erase(e);
+    live.erase(l);
+    const int64_t id = n + s;
+    Live L;
+    L.t = it.C;
+    L.pos = pos;
+    live[id] = L;
+    set_ids(id, ids);
+    return id;
   }
 };
 
+// Replaces the two tensors of every pair by their cast to `to` (batched).
+ftn_status cast_pairs(ftn_ctx ctx, std::vector<Exec*>& nets, std::vector<std::pair<int64_t, int64_t>>& pairs,
+                      std::vector<CompressItem>& items, ftn_dtype to) {
+  std::vector<ftn_tensor> in, out;
+  for (auto& it : items) {
+    in.push_back(it.X);
+    in.push_back(it.Y);
+  }
+  FTN_TRY(cast_batch(ctx, in, to, out));
+  for (size_t q = 0; q < items.size(); ++q) {
+    Live& X = nets[q]->live[pairs[q].first];
+    Live& Y = nets[q]->live[pairs[q].second];
+    ftn_tensor_free(X.t);
+    ftn_tensor_free(Y.t);
+    X.t = items[q].X = out[2 * q];
+    Y.t = items[q].Y = out[2 * q + 1];
+  }
+  return FTN_OK;
+}
+
+// One sub-round of compressions: pairs[q] of network nets[q].  FP32
+// networks compress in FP64 (cast there and back, batched as well).
+ftn_status run_compressions(ftn_ctx ctx, std::vector<Exec*>& nets, std::vector<std::pair<int64_t, int64_t>>& pairs) {
+  if (nets.empty()) return FTN_OK;
+  std::vector<CompressItem> items(nets.size());
+  for (size_t q = 0; q < nets.size(); ++q) nets[q]->compress_item(pairs[q].first, pairs[q].second, items[q]);
+  const bool f32 = items[0].X->dtype == FTN_F32;
+  if (f32) FTN_TRY(cast_pairs(ctx, nets, pairs, items, FTN_F64));  // the decomposition runs in FP64
+  // on failure the inputs are untouched and still owned by their networks
+  FTN_TRY(compress_batch(ctx, items));
+  for (size_t q = 0; q < items.size(); ++q) {
+    nets[q]->live[pairs[q].first].t = items[q].X;
+    nets[q]->live[pairs[q].second].t = items[q].Y;
+  }
+  if (f32) FTN_TRY(cast_pairs(ctx, nets, pairs, items, FTN_F32));
+  for (size_t q = 0; q < items.size(); ++q) nets[q]->compress_done(pairs[q].first, pairs[q].second, items[q]);
+  return FTN_OK;
+}
+
+// The compressions of one round in sub-rounds: position j of every network's list.
+ftn_status compress_lists(ftn_ctx ctx, std::vector<Exec*>& nets,
+                          std::vector<std::vector<std::pair<int64_t, int64_t>>>& lists) {
+  size_t depth = 0;
+  for (auto& l : lists) depth = std::max(depth, l.size());
+  for (size_t j = 0; j < depth; ++j) {
+    std::vector<Exec*> sub;
+    std::vector<std::pair<int64_t, int64_t>> pairs;
+    for (size_t q = 0; q < nets.size(); ++q)
+      if (j < lists[q].size()) {
+        sub.push_back(nets[q]);
+        pairs.push_back(lists[q][j]);
+      }
+    FTN_TRY(run_compressions(ctx, sub, pairs));
+  }
+  return FTN_OK;
+}
+
 }  // namespace
 
-ftn_status contract_impl(ftn_ctx ctx, const ftn_network* net, const ftn_tree* tree, ftn_prec prec, double* mantissa,
-                         double* log_scale) {
-  if (!ctx || !net || !tree || !mantissa || !log_scale) return set_error(FTN_EINVAL, "null argument");
-  const int n = net->n_tensors;
-  if (n < 1 || !net->tensors) return set_error(FTN_EINVAL, "empty network");
-  if (tree->n_steps != n - 1 || (n > 1 && !tree->pairs)) return set_error(FTN_EINVAL, "tree needs n_tensors - 1 steps");
-  if (tree->policy != FTN_POLICY_EXACT && tree->chi < 1) return set_error(FTN_EINVAL, "chi must be >= 1");
-  const ftn_dtype want = prec == FTN_PREC_F64 ? FTN_F64 : FTN_F32;
-  Exec E;
-  E.ctx = ctx;
-  E.prec = prec;
-  E.global = net->positions != nullptr;
-  for (int i = 0; i < n; ++i) {
-    ftn_tensor t = net->tensors[i];
-    if (!t) return set_error(FTN_EINVAL, "null tensor in network");
-    if (t->dtype != want) return set_error(FTN_EUNSUPPORTED, "tensor dtype does not match the precision");
-    ftn_tensor view = nullptr;  // borrowed view: the executor never frees caller buffers
-    FTN_TRY(ftn_tensor_wrap(ctx, t->rank, t->d0, t->d1, t->dual, t->parity, t->dtype, t->data, &view));
-    Live L;
-    L.t = view;
-    L.pos = E.global ? net->positions[i] : 0;
-    for (int k = 0; k < t->rank; ++k) L.ids.push_back((int64_t)i * 64 + k);
-    E.live[i] = L;
-    for (int k = 0; k < t->rank; ++k) E.owner[(int64_t)i * 64 + k] = i;
+ftn_status contract_batch_impl(ftn_ctx ctx, int count, const ftn_network* nets, const ftn_tree* trees, ftn_prec prec,
+                               double* mantissa, double* log_scale) {
+  if (!ctx || count < 0 || (count > 0 && (!nets || !trees || !mantissa || !log_scale)))
+    return set_error(FTN_EINVAL, "null argument");
+  if (count == 0) return FTN_OK;
+  if (prec < FTN_PREC_F64 || prec > FTN_PREC_BF16X3) return set_error(FTN_EINVAL, "bad precision");
+  std::vector<std::unique_ptr<Exec>> ex(count);
+  int max_steps = 0;
+  for (int i = 0; i < count; ++i) {
+    ex[i].reset(new Exec());
+    FTN_TRY(ex[i]->init(ctx, &nets[i], &trees[i], prec));
+    max_steps = std::max(max_steps, ex[i]->n - 1);
   }
-  for (int b = 0; b < net->n_bonds; ++b) {
-    const int32_t* q = net->bonds + 4 * b;
-    if (q[0] < 0 || q[0] >= n || q[2] < 0 || q[2] >= n || q[1] < 0 || q[3] < 0 ||
-        q[1] >= net->tensors[q[0]]->rank || q[3] >= net->tensors[q[2]]->rank)
-      return set_error(FTN_EINVAL, "bond out of range");
-    const int64_t u = (int64_t)q[0] * 64 + q[1], v = (int64_t)q[2] * 64 + q[3];
-    if (E.partner.count(u) || E.partner.count(v)) return set_error(FTN_EINVAL, "leg bonded twice");
-    E.partner[u] = v;
-    E.partner[v] = u;
-  }
-  // device scratch: [log-scale accumulator, two max |x| words]
-  void* d_state = dev_alloc(ctx, 256);
+  // device scratch per network: [log-scale accumulator, two max |x| words]
+  constexpr int STATE = 32;
+  void* d_state = dev_alloc(ctx, (size_t)count * STATE + 256);
   if (!d_state) return set_error(FTN_ENOMEM, "device allocation failed");
   struct Guard {
     ftn_ctx c;
     void* p;
     ~Guard() { dev_free(c, p); }
   } guard{ctx, d_state};
-  FTN_CUDA(cudaMemsetAsync(d_state, 0, 24, ctx->stream));
-  const int chi = tree->chi;
-  for (int s = 0; s < n - 1; ++s) {
-    const int64_t a = tree->pairs[2 * s], b = tree->pairs[2 * s + 1];
-    if (!E.live.count(a) || !E.live.count(b) || a == b) return set_error(FTN_EINVAL, "tree refers to a dead tensor");
-    if (tree->policy == FTN_POLICY_LATE) {
-      for (int64_t op : {a, b}) {
-        const int64_t other = op == a ? b : a;
-        for (int64_t nb : E.neighbours(op))
-          if (nb != other && E.bond_dim(op, nb) > chi) FTN_TRY(E.compress_pair(op, nb, chi));
-      }
+  FTN_CUDA(cudaMemsetAsync(d_state, 0, (size_t)count * STATE, ctx->stream));
+  auto state = [&](int i) { return (void*)((char*)d_state + (size_t)i * STATE); };
+  for (int s = 0; s < max_steps; ++s) {
+    std::vector<int> act;
+    for (int i = 0; i < count; ++i)
+      if (s < ex[i]->n - 1) act.push_back(i);
+    std::vector<Exec*> an;
+    std::vector<int64_t> a(act.size()), b(act.size());
+    for (size_t q = 0; q < act.size(); ++q) {
+      an.push_back(ex[act[q]].get());
+      FTN_TRY(an[q]->step_pair(s, a[q], b[q]));
     }
-    std::vector<int> ax, ay;
-    int64_t e = a, l = b;
-    uint64_t flip_e = 0, flip_l = 0;
-    if (E.global) {
-      if (E.live[a].pos > E.live[b].pos) std::swap(e, l);
-      // move l leftwards past every tensor between the two positions
-      std::vector<int> cx, cl;
-      for (auto& kv : E.live) {
-        const int64_t c = kv.first;
-        if (c == e || c == l || !(E.live[e].pos < kv.second.pos && kv.second.pos < E.live[l].pos)) continue;
-        E.shared(c, l, cx, cl);
-        for (int k : cl) flip_l |= 1ull << k;
-        if (kv.second.t->parity & E.live[l].t->parity) E.sign = -E.sign;
-      }
-      E.shared(e, l, ax, ay);
-      for (int k : ax)  // plain ordered contraction: cancel the arrow parity
-        if (E.live[e].t->dual[k] == 0) flip_e |= 1ull << k;
-    } else {
-      E.shared(e, l, ax, ay);
+    {  // compressions before the step
+      std::vector<Exec*> who;
+      std::vector<std::vector<std::pair<int64_t, int64_t>>> lists;
+      for (size_t q = 0; q < act.size(); ++q)
+        if (an[q]->tree->policy == FTN_POLICY_LATE) {
+          who.push_back(an[q]);
+          lists.push_back(an[q]->late_pairs(a[q], b[q]));
+        }
+      FTN_TRY(compress_lists(ctx, who, lists));
     }
-    ftn_tensor C = nullptr;
-    FTN_TRY(tensordot_impl(ctx, E.live[e].t, E.live[l].t, (int)ax.size(), ax.data(), ay.data(), flip_e, flip_l,
-                           nullptr, prec, &C));
-    std::vector<int64_t> ids;
-    for (int k = 0; k < (int)E.live[e].ids.size(); ++k)
-      if (std::find(ax.begin(), ax.end(), k) == ax.end()) ids.push_back(E.live[e].ids[k]);
-      else
-        E.partner.erase(E.live[e].ids[k]);
-    for (int k = 0; k < (int)E.live[l].ids.size(); ++k)
-      if (std::find(ay.begin(), ay.end(), k) == ay.end()) ids.push_back(E.live[l].ids[k]);
-      else
-        E.partner.erase(E.live[l].ids[k]);
-    const int64_t pos = E.live[e].pos;
-    ftn_tensor_free(E.live[e].t);
-    ftn_tensor_free(E.live[l].t);
-    E.live.erase(e);
-    E.live.erase(l);
-    const int64_t id = n + s;
-    Live L;
-    L.t = C;
-    L.pos = pos;
-    E.live[id] = L;
-    E.set_ids(id, ids);
-    if (tree->policy == FTN_POLICY_EARLY)
-      for (int64_t nb : E.neighbours(id))
-        if (E.bond_dim(id, nb) > chi) FTN_TRY(E.compress_pair(id, nb, chi));
-    FTN_TRY(normalize_tensor(ctx, E.live[id].t, d_state, s));
+    // the pairwise contractions
+    std::vector<TdItem> items(act.size());
+    std::vector<int64_t> e(act.size()), l(act.size()), id(act.size());
+    for (size_t q = 0; q < act.size(); ++q) an[q]->step_item(a[q], b[q], e[q], l[q], items[q]);
+    FTN_TRY(tensordot_batch(ctx, items, prec));
+    for (size_t q = 0; q < act.size(); ++q) id[q] = an[q]->step_done(s, e[q], l[q], items[q]);
+    {  // compressions after the step
+      std::vector<Exec*> who;
+      std::vector<std::vector<std::pair<int64_t, int64_t>>> lists;
+      for (size_t q = 0; q < act.size(); ++q)
+        if (an[q]->tree->policy == FTN_POLICY_EARLY) {
+          who.push_back(an[q]);
+          lists.push_back(an[q]->early_pairs(id[q]));
+        }
+      FTN_TRY(compress_lists(ctx, who, lists));
+    }
+    std::vector<NormItem> norm;
+    for (size_t q = 0; q < act.size(); ++q) norm.push_back({an[q]->live[id[q]].t, state(act[q]), s});
+    FTN_TRY(normalize_batch(ctx, norm));
   }
-  if (E.live.size() != 1) return set_error(FTN_EINVAL, "tree does not reduce the network to one tensor");
-  ftn_tensor last = E.live.begin()->second.t;
-  if (last->rank != 0) return set_error(FTN_EINVAL, "network is not closed (open legs remain)");
-  double host_state[2] = {0, 0};
-  double val = 0.0;
-  FTN_CUDA(cudaMemcpyAsync(host_state, d_state, 16, cudaMemcpyDeviceToHost, ctx->stream));
-  if (last->numel) {
-    if (last->dtype == FTN_F64) {
-      FTN_CUDA(cudaMemcpyAsync(&val, last->data, 8, cudaMemcpyDeviceToHost, ctx->stream));
-      FTN_CUDA(cudaStreamSynchronize(ctx->stream));
-    } else {
-      float v32 = 0.f;
-      FTN_CUDA(cudaMemcpyAsync(&v32, last->data, 4, cudaMemcpyDeviceToHost, ctx->stream));
-      FTN_CUDA(cudaStreamSynchronize(ctx->stream));
-      val = v32;
-    }
-  } else {
-    FTN_CUDA(cudaStreamSynchronize(ctx->stream));
+  std::vector<ResultJob> res(count);
+  for (int i = 0; i < count; ++i) {
+    Exec& E = *ex[i];
+    if (E.live.size() != 1) return set_error(FTN_EINVAL, "tree does not reduce the network to one tensor");
+    ftn_tensor last = E.live.begin()->second.t;
+    if (last->rank != 0) return set_error(FTN_EINVAL, "network is not closed (open legs remain)");
+    res[i].value = last->numel ? last->data : nullptr;
+    res[i].logacc = (const double*)state(i);
+    res[i].f64 = last->dtype == FTN_F64 ? 1 : 0;
+    res[i].pad_ = 0;
   }
-  *mantissa = val * E.sign;
-  *log_scale = host_state[0];
+  // [result jobs | two doubles per network] in one device buffer, one copy back
+  const size_t jb = ((size_t)count * sizeof(ResultJob) + 255) & ~(size_t)255;
+  void* d_res = dev_alloc(ctx, jb + (size_t)count * 16);
+  if (!d_res) return set_error(FTN_ENOMEM, "device allocation failed");
+  struct Guard2 {
+    ftn_ctx c;
+    void* p;
+    ~Guard2() { dev_free(c, p); }
+  } guard2{ctx, d_res};
+  FTN_CUDA(cudaMemcpyAsync(d_res, res.data(), (size_t)count * sizeof(ResultJob), cudaMemcpyHostToDevice, ctx->stream));
+  double* d_out = (double*)((char*)d_res + jb);
+  FTN_TRY(launch_gather_results(ctx, (const ResultJob*)d_res, count, d_out));
+  std::vector<double> host(2 * (size_t)count);
+  FTN_CUDA(cudaMemcpyAsync(host.data(), d_out, host.size() * 8, cudaMemcpyDeviceToHost, ctx->stream));
+  FTN_CUDA(cudaStreamSynchronize(ctx->stream));
+  for (int i = 0; i < count; ++i) {
+    mantissa[i] = host[2 * i] * ex[i]->sign;
+    log_scale[i] = host[2 * i + 1];
+  }
   return FTN_OK;
+}
+
+ftn_status contract_impl(ftn_ctx ctx, const ftn_network* net, const ftn_tree* tree, ftn_prec prec, double* mantissa,
+                         double* log_scale) {
+  if (!ctx || !net || !tree || !mantissa || !log_scale) return set_error(FTN_EINVAL, "null argument");
+  return contract_batch_impl(ctx, 1, net, tree, prec, mantissa, log_scale);
 }
 
 // ---- Hubbard operator tensors ---------------------------------------------------
@@ -364,6 +513,11 @@ extern "C" {
 ftn_status ftn_contract(ftn_ctx ctx, const ftn_network* net, const ftn_tree* tree, ftn_prec prec, double* mantissa,
                         double* log_scale) {
   return contract_impl(ctx, net, tree, prec, mantissa, log_scale);
+}
+
+ftn_status ftn_contract_batch(ftn_ctx ctx, int count, const ftn_network* nets, const ftn_tree* trees, ftn_prec prec,
+                              double* mantissa, double* log_scale) {
+  return contract_batch_impl(ctx, count, nets, trees, prec, mantissa, log_scale);
 }
 
 ftn_status ftn_hubbard_term(ftn_ctx ctx, int kind, double t, double u, ftn_dtype dtype, ftn_tensor* out) {

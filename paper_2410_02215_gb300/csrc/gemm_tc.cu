@@ -33,6 +33,10 @@ struct TcParams {
   CUtensorMap b_hi[2];
   CUtensorMap a_lo[2];
   CUtensorMap b_lo[2];
+  // Batched launches (problems of many contractions): when set, problem p
+  // reads its operands through gmaps[4 * p.pi + {0: A hi, 1: B hi, 2: A lo,
+  // 3: B lo}] (global memory, 64-byte aligned) instead of the maps above.
+  const CUtensorMap* gmaps;
   const GemmProb* probs;
   float* C;
   int* err;
@@ -149,12 +153,29 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
       uint32_t phase = 0;
       uint32_t issued = 0, lastpar = 0;
       bool ok = true;
-      int cur = -1;
+      int cur = -1, fenced = -1;
       for (int64_t t = blockIdx.x; t < P.tiles && ok; t += gridDim.x) {
         int m0, n0;
         const GemmProb& p = *tc_decode<BN>(P, t, m0, n0, cur);
         const int nk = (p.K + Cfg::KB - 1) / Cfg::KB;
         const int pi = p.pi;
+        const CUtensorMap *ma = &P.a_hi[pi & 1], *mb = &P.b_hi[pi & 1], *mal = &P.a_lo[pi & 1],
+                          *mbl = &P.b_lo[pi & 1];
+        if (P.gmaps) {
+          ma = P.gmaps + 4 * pi;
+          mb = ma + 1;
+          mal = ma + 2;
+          mbl = ma + 3;
+          if (nk > 0 && fenced != pi) {
+            tensormap_acquire(ma);
+            tensormap_acquire(mb);
+            if constexpr (SPLIT) {
+              tensormap_acquire(mal);
+              tensormap_acquire(mbl);
+            }
+            fenced = pi;
+          }
+        }
         for (int kb = 0; kb < nk; ++kb) {
           if (!mbar_wait(&empty[stage], phase ^ 1, P.err)) {
             ok = false;
@@ -163,11 +184,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
           uint8_t* sa = smem + stage * Cfg::STAGE_BYTES;
           mbar_expect_tx(&full[stage], Cfg::STAGE_BYTES);
           const int kx = p.k0 + kb * Cfg::KB;  // K element; k0 is a multiple of KB
-          tma_load_2d(sa, &P.a_hi[pi], kx, p.a_row0 + m0, &full[stage]);
-          tma_load_2d(sa + Cfg::A_BYTES, &P.b_hi[pi], kx, p.b_row0 + n0, &full[stage]);
+          tma_load_2d(sa, ma, kx, p.a_row0 + m0, &full[stage]);
+          tma_load_2d(sa + Cfg::A_BYTES, mb, kx, p.b_row0 + n0, &full[stage]);
           if constexpr (SPLIT) {
-            tma_load_2d(sa + Cfg::A_BYTES + Cfg::B_BYTES, &P.a_lo[pi], kx, p.a_row0 + m0, &full[stage]);
-            tma_load_2d(sa + 2 * Cfg::A_BYTES + Cfg::B_BYTES, &P.b_lo[pi], kx, p.b_row0 + n0, &full[stage]);
+            tma_load_2d(sa + Cfg::A_BYTES + Cfg::B_BYTES, mal, kx, p.a_row0 + m0, &full[stage]);
+            tma_load_2d(sa + 2 * Cfg::A_BYTES + Cfg::B_BYTES, mbl, kx, p.b_row0 + n0, &full[stage]);
           }
           issued |= 1u << stage;
           lastpar = (lastpar & ~(1u << stage)) | (phase << stage);
@@ -438,22 +459,31 @@ static bool encode_2d(CUtensorMap* m, const void* base, bool bf16, int64_t rows,
   return r == CUDA_SUCCESS;
 }
 
+// The four maps (A hi, B hi, A lo, B lo) of fused-matrix pair pi.
 template <bool BF16, bool SPLIT, int BN>
-static ftn_status run(ftn_ctx ctx, const TcOperands& ops, const GemmProb* d_probs, int nprobs, int64_t tiles,
-                      float* c) {
+static bool encode_set(const TcOperands& ops, int pi, CUtensorMap* a_hi, CUtensorMap* b_hi, CUtensorMap* a_lo,
+                       CUtensorMap* b_lo) {
+  using Cfg = TcCfg<BF16, SPLIT, BN>;
+  bool ok = encode_2d(a_hi, ops.a_hi[pi], BF16, ops.a_rows[pi], ops.kdim[pi], ops.ldk[pi], Cfg::KB, TC_BM) &&
+            encode_2d(b_hi, ops.b_hi[pi], BF16, ops.b_rows[pi], ops.kdim[pi], ops.ldk[pi], Cfg::KB, BN);
+  if (SPLIT)
+    ok = ok && encode_2d(a_lo, ops.a_lo[pi], BF16, ops.a_rows[pi], ops.kdim[pi], ops.ldk[pi], Cfg::KB, TC_BM) &&
+         encode_2d(b_lo, ops.b_lo[pi], BF16, ops.b_rows[pi], ops.kdim[pi], ops.ldk[pi], Cfg::KB, BN);
+  return ok;
+}
+
+template <bool BF16, bool SPLIT, int BN>
+static ftn_status run(ftn_ctx ctx, const TcOperands* ops, const void* gmaps, const GemmProb* d_probs, int nprobs,
+                      int64_t tiles, float* c) {
   using Cfg = TcCfg<BF16, SPLIT, BN>;
   TcParams P;
   std::memset(&P, 0, sizeof(P));
-  for (int pi = 0; pi < 2; ++pi) {
-    if (ops.a_rows[pi] <= 0 || ops.b_rows[pi] <= 0 || ops.kdim[pi] <= 0) continue;
-    bool ok = encode_2d(&P.a_hi[pi], ops.a_hi[pi], BF16, ops.a_rows[pi], ops.kdim[pi], ops.ldk[pi], Cfg::KB, TC_BM) &&
-              encode_2d(&P.b_hi[pi], ops.b_hi[pi], BF16, ops.b_rows[pi], ops.kdim[pi], ops.ldk[pi], Cfg::KB, BN);
-    if (SPLIT)
-      ok = ok &&
-           encode_2d(&P.a_lo[pi], ops.a_lo[pi], BF16, ops.a_rows[pi], ops.kdim[pi], ops.ldk[pi], Cfg::KB, TC_BM) &&
-           encode_2d(&P.b_lo[pi], ops.b_lo[pi], BF16, ops.b_rows[pi], ops.kdim[pi], ops.ldk[pi], Cfg::KB, BN);
-    if (!ok) return set_error(FTN_ECUDA, "cuTensorMapEncodeTiled failed");
+  for (int pi = 0; ops && pi < 2; ++pi) {
+    if (ops->a_rows[pi] <= 0 || ops->b_rows[pi] <= 0 || ops->kdim[pi] <= 0) continue;
+    if (!encode_set<BF16, SPLIT, BN>(*ops, pi, &P.a_hi[pi], &P.b_hi[pi], &P.a_lo[pi], &P.b_lo[pi]))
+      return set_error(FTN_ECUDA, "cuTensorMapEncodeTiled failed");
   }
+  P.gmaps = reinterpret_cast<const CUtensorMap*>(gmaps);
   P.probs = d_probs;
   P.C = c;
   P.err = ctx->dev_err;
@@ -483,29 +513,68 @@ int64_t tc_tiles_for(int M, int N, int bn) {
 }
 
 template <bool BF16, bool SPLIT>
-static ftn_status by_bn(ftn_ctx ctx, int bn, const TcOperands& ops, const GemmProb* d, int np, int64_t tiles,
-                        float* c) {
+static ftn_status by_bn(ftn_ctx ctx, int bn, const TcOperands* ops, const void* gm, const GemmProb* d, int np,
+                        int64_t tiles, float* c) {
   switch (bn) {
-    case 16: return run<BF16, SPLIT, 16>(ctx, ops, d, np, tiles, c);
-    case 32: return run<BF16, SPLIT, 32>(ctx, ops, d, np, tiles, c);
-    case 64: return run<BF16, SPLIT, 64>(ctx, ops, d, np, tiles, c);
-    case 128: return run<BF16, SPLIT, 128>(ctx, ops, d, np, tiles, c);
+    case 16: return run<BF16, SPLIT, 16>(ctx, ops, gm, d, np, tiles, c);
+    case 32: return run<BF16, SPLIT, 32>(ctx, ops, gm, d, np, tiles, c);
+    case 64: return run<BF16, SPLIT, 64>(ctx, ops, gm, d, np, tiles, c);
+    case 128: return run<BF16, SPLIT, 128>(ctx, ops, gm, d, np, tiles, c);
     default:
-      if constexpr (!SPLIT) return run<BF16, SPLIT, 256>(ctx, ops, d, np, tiles, c);
+      if constexpr (!SPLIT) return run<BF16, SPLIT, 256>(ctx, ops, gm, d, np, tiles, c);
       return set_error(FTN_EINVAL, "bad tile width");
+  }
+}
+
+static ftn_status dispatch(ftn_ctx ctx, ftn_prec prec, int bn, const TcOperands* ops, const void* gm,
+                           const GemmProb* d_probs, int nprobs, int64_t tiles, float* c) {
+  if (nprobs == 0 || tiles == 0) return FTN_OK;
+  switch (prec) {
+    case FTN_PREC_TF32: return by_bn<false, false>(ctx, bn, ops, gm, d_probs, nprobs, tiles, c);
+    case FTN_PREC_TF32X3: return by_bn<false, true>(ctx, bn, ops, gm, d_probs, nprobs, tiles, c);
+    case FTN_PREC_BF16: return by_bn<true, false>(ctx, bn, ops, gm, d_probs, nprobs, tiles, c);
+    case FTN_PREC_BF16X3: return by_bn<true, true>(ctx, bn, ops, gm, d_probs, nprobs, tiles, c);
+    default: return set_error(FTN_EUNSUPPORTED, "precision has no tensor-core path");
   }
 }
 
 ftn_status launch_gemm_tc(ftn_ctx ctx, ftn_prec prec, const TcOperands& ops, const GemmProb* d_probs, int nprobs,
                           int64_t tiles, int bn, float* c) {
-  if (nprobs == 0 || tiles == 0) return FTN_OK;
+  return dispatch(ctx, prec, bn, &ops, nullptr, d_probs, nprobs, tiles, c);
+}
+
+ftn_status launch_gemm_tc_maps(ftn_ctx ctx, ftn_prec prec, const TcMapSet* d_maps, const GemmProb* d_probs,
+                               int nprobs, int64_t tiles, int bn, float* c) {
+  if (!d_maps || ((uintptr_t)d_maps & 63)) return set_error(FTN_EINVAL, "internal error: tensor maps not 64-byte aligned");
+  return dispatch(ctx, prec, bn, nullptr, d_maps, d_probs, nprobs, tiles, c);
+}
+
+template <bool BF16, bool SPLIT>
+static bool enc_by_bn(int bn, const TcOperands& ops, int pi, TcMapSet* out) {
+  CUtensorMap* m = reinterpret_cast<CUtensorMap*>(out);
+  switch (bn) {
+    case 16: return encode_set<BF16, SPLIT, 16>(ops, pi, m, m + 1, m + 2, m + 3);
+    case 32: return encode_set<BF16, SPLIT, 32>(ops, pi, m, m + 1, m + 2, m + 3);
+    case 64: return encode_set<BF16, SPLIT, 64>(ops, pi, m, m + 1, m + 2, m + 3);
+    case 128: return encode_set<BF16, SPLIT, 128>(ops, pi, m, m + 1, m + 2, m + 3);
+    case 256: return !SPLIT && encode_set<BF16, SPLIT, 256>(ops, pi, m, m + 1, m + 2, m + 3);
+    default: return false;
+  }
+}
+
+ftn_status tc_encode_set(ftn_prec prec, int bn, const TcOperands& ops, int pi, TcMapSet* out) {
+  static_assert(sizeof(TcMapSet) == 4 * sizeof(CUtensorMap), "map set layout");
+  std::memset(out, 0, sizeof(TcMapSet));
+  if (ops.a_rows[pi] <= 0 || ops.b_rows[pi] <= 0 || ops.kdim[pi] <= 0) return FTN_OK;
+  bool ok = false;
   switch (prec) {
-    case FTN_PREC_TF32: return by_bn<false, false>(ctx, bn, ops, d_probs, nprobs, tiles, c);
-    case FTN_PREC_TF32X3: return by_bn<false, true>(ctx, bn, ops, d_probs, nprobs, tiles, c);
-    case FTN_PREC_BF16: return by_bn<true, false>(ctx, bn, ops, d_probs, nprobs, tiles, c);
-    case FTN_PREC_BF16X3: return by_bn<true, true>(ctx, bn, ops, d_probs, nprobs, tiles, c);
+    case FTN_PREC_TF32: ok = enc_by_bn<false, false>(bn, ops, pi, out); break;
+    case FTN_PREC_TF32X3: ok = enc_by_bn<false, true>(bn, ops, pi, out); break;
+    case FTN_PREC_BF16: ok = enc_by_bn<true, false>(bn, ops, pi, out); break;
+    case FTN_PREC_BF16X3: ok = enc_by_bn<true, true>(bn, ops, pi, out); break;
     default: return set_error(FTN_EUNSUPPORTED, "precision has no tensor-core path");
   }
+  return ok ? FTN_OK : set_error(FTN_ECUDA, "cuTensorMapEncodeTiled failed");
 }
 
 }  // namespace ftn

@@ -1,7 +1,9 @@
 // Small device kernels used by the contraction-tree executor: per-step
 // max-abs normalisation with an FP64 log-scale accumulator kept on the
 // device (no host round trip), and FP32 <-> FP64 casts.
-#include "common.h"
+#include <algorithm>
+
+#include "batch.h"
 
 namespace ftn {
 
@@ -24,9 +26,8 @@ __global__ void cast_kernel(const Ti* __restrict__ x, To* __restrict__ y, int64_
 // Small tensors: one CTA finds max |x|, scales and accumulates the log; it
 // also clears both max words of the large-tensor path.
 template <typename T>
-__global__ void __launch_bounds__(1024) normalize_small_kernel(T* __restrict__ x, int64_t n,
-                                                                double* __restrict__ logacc,
-                                                                unsigned long long* __restrict__ words) {
+__device__ __forceinline__ void normalize_small_body(T* __restrict__ x, int64_t n, double* __restrict__ logacc,
+                                                     unsigned long long* __restrict__ words) {
   if (threadIdx.x == 0) words[0] = words[1] = 0ull;
   __shared__ double red[32];
   double m = 0.0;
@@ -45,6 +46,13 @@ __global__ void __launch_bounds__(1024) normalize_small_kernel(T* __restrict__ x
   const T inv = (T)(1.0 / m);
   for (int64_t i = threadIdx.x; i < n; i += blockDim.x) x[i] *= inv;
   if (threadIdx.x == 0) *logacc += log(m);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(1024) normalize_small_kernel(T* __restrict__ x, int64_t n,
+                                                                double* __restrict__ logacc,
+                                                                unsigned long long* __restrict__ words) {
+  normalize_small_body<T>(x, n, logacc, words);
 }
 
 // Large tensors: max |x| into word `cur` (atomicMax), then scale; the scale
@@ -106,6 +114,134 @@ ftn_status cast_tensor(ftn_ctx ctx, ftn_tensor t, ftn_dtype to, ftn_tensor* out)
     cast_kernel<float, double><<<g, 256, 0, ctx->stream>>>((const float*)t->data, (double*)(*out)->data, t->numel);
   else
     FTN_CUDA(cudaMemcpyAsync((*out)->data, t->data, t->numel * dtype_size(to), cudaMemcpyDeviceToDevice, ctx->stream));
+  ctx->launches += 1;
+  FTN_CUDA(cudaGetLastError());
+  return FTN_OK;
+}
+
+// ---- batched forms (many tensors per launch, the same arithmetic) ----------------
+
+template <typename T>
+__global__ void __launch_bounds__(1024) normalize_small_batch_kernel(const NormJob* __restrict__ jobs) {
+  const NormJob J = jobs[blockIdx.x];
+  normalize_small_body<T>(reinterpret_cast<T*>(J.x), J.n, J.logacc, J.words);
+}
+
+// job of tile t: the last job whose first tile is <= t
+template <typename J>
+__device__ __forceinline__ const J& find_tile_job(const J* __restrict__ jobs, int n, int64_t t) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (jobs[mid].tile_begin <= t)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  return jobs[lo];
+}
+
+template <typename T>
+__global__ void maxabs_batch_kernel(const NormJob* __restrict__ jobs, int njobs, int64_t tiles) {
+  for (int64_t t = blockIdx.x; t < tiles; t += gridDim.x) {
+    const NormJob& J = find_tile_job(jobs, njobs, t);
+    const int64_t i0 = (t - J.tile_begin) * NORM_TILE;
+    const int64_t i1 = i0 + NORM_TILE < J.n ? i0 + NORM_TILE : J.n;
+    const T* x = reinterpret_cast<const T*>(J.x);
+    double m = 0.0;
+    for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) m = fmax(m, fabs((double)x[i]));
+    for (int o = 16; o; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0 && m > 0.0) atomicMax(J.words + J.cur, (unsigned long long)__double_as_longlong(m));
+  }
+}
+
+// Scales every tile by 1 / max; the job's first tile also clears the other
+// max word (for the next step) and adds log(max) to the accumulator.
+template <typename T>
+__global__ void scale_batch_kernel(const NormJob* __restrict__ jobs, int njobs, int64_t tiles) {
+  for (int64_t t = blockIdx.x; t < tiles; t += gridDim.x) {
+    const NormJob& J = find_tile_job(jobs, njobs, t);
+    const double m = __longlong_as_double((long long)J.words[J.cur]);
+    const bool first = t == J.tile_begin;
+    if (first && threadIdx.x == 0) J.words[J.cur ^ 1] = 0ull;
+    if (!(m > 0.0)) continue;
+    const int64_t i0 = (t - J.tile_begin) * NORM_TILE;
+    const int64_t i1 = i0 + NORM_TILE < J.n ? i0 + NORM_TILE : J.n;
+    T* x = reinterpret_cast<T*>(J.x);
+    const T inv = (T)(1.0 / m);
+    for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) x[i] *= inv;
+    if (first && threadIdx.x == 0) *J.logacc += log(m);
+  }
+}
+
+ftn_status launch_normalize_batch(ftn_ctx ctx, ftn_dtype dt, const NormJob* d_small, int nsmall,
+                                  const NormJob* d_large, int nlarge, int64_t large_tiles) {
+  const bool f64 = dt == FTN_F64;
+  if (nsmall > 0) {
+    if (f64)
+      normalize_small_batch_kernel<double><<<(unsigned)nsmall, 1024, 0, ctx->stream>>>(d_small);
+    else
+      normalize_small_batch_kernel<float><<<(unsigned)nsmall, 1024, 0, ctx->stream>>>(d_small);
+    ctx->launches += 1;
+    FTN_CUDA(cudaGetLastError());
+  }
+  if (nlarge > 0 && large_tiles > 0) {
+    const unsigned g = (unsigned)std::min<int64_t>(large_tiles, (int64_t)ctx->num_sms * 8);
+    if (f64) {
+      maxabs_batch_kernel<double><<<g, 256, 0, ctx->stream>>>(d_large, nlarge, large_tiles);
+      scale_batch_kernel<double><<<g, 256, 0, ctx->stream>>>(d_large, nlarge, large_tiles);
+    } else {
+      maxabs_batch_kernel<float><<<g, 256, 0, ctx->stream>>>(d_large, nlarge, large_tiles);
+      scale_batch_kernel<float><<<g, 256, 0, ctx->stream>>>(d_large, nlarge, large_tiles);
+    }
+    ctx->launches += 2;
+    FTN_CUDA(cudaGetLastError());
+  }
+  return FTN_OK;
+}
+
+template <typename Ti, typename To>
+__global__ void cast_batch_kernel(const CastJob* __restrict__ jobs, int njobs, int64_t tiles) {
+  for (int64_t t = blockIdx.x; t < tiles; t += gridDim.x) {
+    const CastJob& J = find_tile_job(jobs, njobs, t);
+    const int64_t i0 = (t - J.tile_begin) * CAST_TILE;
+    const int64_t i1 = i0 + CAST_TILE < J.n ? i0 + CAST_TILE : J.n;
+    const Ti* x = reinterpret_cast<const Ti*>(J.src);
+    To* y = reinterpret_cast<To*>(J.dst);
+    for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) y[i] = (To)x[i];
+  }
+}
+
+ftn_status launch_cast_batch(ftn_ctx ctx, ftn_dtype from, ftn_dtype to, const CastJob* d_jobs, int njobs,
+                             int64_t tiles) {
+  if (njobs == 0 || tiles == 0) return FTN_OK;
+  const unsigned g = (unsigned)std::min<int64_t>(tiles, (int64_t)ctx->num_sms * 8);
+  if (from == FTN_F64 && to == FTN_F32)
+    cast_batch_kernel<double, float><<<g, 256, 0, ctx->stream>>>(d_jobs, njobs, tiles);
+  else if (from == FTN_F32 && to == FTN_F64)
+    cast_batch_kernel<float, double><<<g, 256, 0, ctx->stream>>>(d_jobs, njobs, tiles);
+  else if (from == FTN_F64)
+    cast_batch_kernel<double, double><<<g, 256, 0, ctx->stream>>>(d_jobs, njobs, tiles);
+  else
+    cast_batch_kernel<float, float><<<g, 256, 0, ctx->stream>>>(d_jobs, njobs, tiles);
+  ctx->launches += 1;
+  FTN_CUDA(cudaGetLastError());
+  return FTN_OK;
+}
+
+__global__ void gather_results_kernel(const ResultJob* __restrict__ jobs, int njobs, double* __restrict__ out) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < njobs; i += gridDim.x * blockDim.x) {
+    const ResultJob J = jobs[i];
+    double v = 0.0;
+    if (J.value) v = J.f64 ? *reinterpret_cast<const double*>(J.value) : (double)*reinterpret_cast<const float*>(J.value);
+    out[2 * i] = v;
+    out[2 * i + 1] = *J.logacc;
+  }
+}
+
+ftn_status launch_gather_results(ftn_ctx ctx, const ResultJob* d_jobs, int njobs, double* out) {
+  if (njobs == 0) return FTN_OK;
+  gather_results_kernel<<<(unsigned)((njobs + 255) / 256), 256, 0, ctx->stream>>>(d_jobs, njobs, out);
   ctx->launches += 1;
   FTN_CUDA(cudaGetLastError());
   return FTN_OK;

@@ -1,8 +1,8 @@
 """PEPS norm and energy networks assembled for libftn's contraction executor.
 
 Marshalling only: this module builds bond lists and positions and calls the
-C ABI (ftn_tensor_dagger, ftn_hubbard_term, ftn_contract); every contraction,
-compression and reduction runs in libftn.
+C ABI (ftn_tensor_dagger, ftn_hubbard_term, ftn_contract, ftn_contract_batch);
+every contraction, compression and reduction runs in libftn.
 
 Networks follow the globally ordered picture of the norm (Sec. IV.B, Fig. 4a):
 the bra layer -- the daggers of the ket tensors, in reversed site order --
@@ -68,7 +68,7 @@ def term_network(layout, kets, bras, op, sites):
     return list(kets) + list(bras) + [op], bonds, pos
 
 
-def energy(ctx, layout, kets, t, u, tree_fn, mode="local", policy="exact", chi=0, prec="f64"):
+def energy(ctx, layout, kets, t, u, tree_fn, mode="local", policy="exact", chi=0, prec="f64", batch=0):
     """sum_t <h_t>/<Psi|Psi> over all nearest-neighbour hopping and on-site
     terms; each term and the norm are contracted with tree_fn(op_sites).
     Returns (energy, norm mantissa, norm log-scale).
@@ -78,7 +78,8 @@ def energy(ctx, layout, kets, t, u, tree_fn, mode="local", policy="exact", chi=0
     context, take them from a shared counter and run them concurrently on
     the GPU.  The kets, bras and operator tensors belong to the first
     context and are only read by the others.  The sum runs in term order,
-    so the result does not depend on the schedule."""
+    so the result does not depend on the schedule.  ``batch`` as in
+    :func:`contract_many` (bit-identical results either way)."""
     ctxs = list(ctx) if isinstance(ctx, (list, tuple)) else [ctx]
     c0 = ctxs[0]
     dt = ftn.F64 if prec == "f64" else ftn.F32
@@ -97,16 +98,34 @@ def energy(ctx, layout, kets, t, u, tree_fn, mode="local", policy="exact", chi=0
         tens, bonds, pos = term_network(layout, kets, bras, onsite, (s,))
         jobs.append((tens, bonds, pos, tree_fn((s,))))
 
-    def run(c, job):
-        tens, bonds, pos, tree = job
-        return ftn.contract(c, tens, bonds, tree, positions=pos if glob else None, policy=policy, chi=chi, prec=prec)
-
-    results = _run_jobs(ctxs, jobs, run)
+    nets = [{"tensors": tens, "bonds": bonds, "tree": tree, "positions": pos if glob else None, "policy": policy,
+             "chi": chi} for tens, bonds, pos, tree in jobs]
+    results = contract_many(ctxs, nets, prec, batch)
     nm, nl = results[0]
     total = 0.0
     for m, lg in results[1:]:
         total += m / nm * math.exp(lg - nl)
     return total, nm, nl
+
+
+def contract_many(ctx, networks, prec="f64", batch=0):
+    """(mantissa, log_scale) of every network (dicts as for
+    :func:`ftn.contract_batch`), in order.  ``batch`` = 0: one ftn_contract
+    per network; > 0: batches of up to ``batch`` networks per
+    ftn_contract_batch call.  With several contexts, host threads (one per
+    context) take networks or batches from a shared counter."""
+    ctxs = list(ctx) if isinstance(ctx, (list, tuple)) else [ctx]
+    nets = list(networks)
+    if batch and batch > 0:
+        chunks = [nets[i:i + batch] for i in range(0, len(nets), batch)]
+        res = _run_jobs(ctxs, chunks, lambda c, ch: ftn.contract_batch(c, ch, prec=prec))
+        return [r for part in res for r in part]
+
+    def run(c, job):
+        return ftn.contract(c, job["tensors"], job["bonds"], job["tree"], positions=job.get("positions"),
+                            policy=job.get("policy", "exact"), chi=job.get("chi", 0), prec=prec)
+
+    return _run_jobs(ctxs, nets, run)
 
 
 def _run_jobs(ctxs, jobs, run):
@@ -204,45 +223,56 @@ def cluster_network(layout, kets, bras, sites, dangling, gauge_of, op=None, targ
     return tensors, bonds, pos
 
 
-def cluster_energy(ctx, layout, kets, t, u, cluster_fn, gauges, policy="exact", chi=0, prec="f64"):
+def cluster_energy(ctx, layout, kets, t, u, cluster_fn, gauges, policy="exact", chi=0, prec="f64", batch=0):
     """Cluster approximation of sum_t <h_t>: every hopping and on-site term
     is the ratio of its cluster network with the operator to the same network
     without it, both contracted in the globally ordered formalism.
     ``cluster_fn(targets)`` gives (sites, dangling bonds, tree with the
     operator, tree without it); ``gauges[(s, t)]`` = (even, odd) weights of
     the bond's stand-in gauge.  ``ctx`` may be a list of contexts (the
-    contractions then run concurrently, as in :func:`energy`).  Returns
-    (energy, per-term ratios)."""
+    contractions then run concurrently, as in :func:`energy`); ``batch`` as
+    in :func:`contract_many`.  Returns (energy, per-term ratios)."""
+    return cluster_energies(ctx, [(layout, kets, cluster_fn, gauges)], t, u, policy, chi, prec, batch)[0]
+
+
+def cluster_energies(ctx, instances, t, u, policy="exact", chi=0, prec="f64", batch=0):
+    """:func:`cluster_energy` of several states at once: ``instances`` is a
+    list of (layout, kets, cluster_fn, gauges); the networks of all terms of
+    all instances are contracted together (in batches of up to ``batch``
+    networks when ``batch`` > 0).  Returns [(energy, ratios)] per instance."""
     ctxs = list(ctx) if isinstance(ctx, (list, tuple)) else [ctx]
     c0 = ctxs[0]
     dt = ftn.F64 if prec == "f64" else ftn.F32
-    bras = [ftn.dagger(c0, k) for k in kets]
-    cache = {}
-
-    def gauge_of(s, a):
-        key = (s, a)
-        if key not in cache:
-            nb = layout["nbrs"][s][a]
-            lam = gauges[(min(s, nb), max(s, nb))]
-            cache[key] = gauge_tensor(c0, lam[0], lam[1], kets[s].legs[a][2], dt)
-        return cache[key]
-
     hop = ftn.hubbard_term(c0, 0, t, 0.0, dt)
     onsite = ftn.hubbard_term(c0, 1, 0.0, u, dt)
-    terms = [((a, b), hop) for a, b in layout["edges"]] + [((s,), onsite) for s in range(layout["n"])]
-    jobs = []
-    for targets, op in terms:
-        sites, dang, tree_op, tree_norm = cluster_fn(list(targets))
-        jobs.append(cluster_network(layout, kets, bras, sites, dang, gauge_of, op, targets) + (tree_op,))
-        jobs.append(cluster_network(layout, kets, bras, sites, dang, gauge_of) + (tree_norm,))
+    nets, nterms, keep = [], [], []
+    for layout, kets, cluster_fn, gauges in instances:
+        bras = [ftn.dagger(c0, k) for k in kets]
+        cache = {}
 
-    def run(c, job):
-        tens, bonds, pos, tree = job
-        return ftn.contract(c, tens, bonds, tree, positions=pos, policy=policy, chi=chi, prec=prec)
+        def gauge_of(s, a, layout=layout, kets=kets, gauges=gauges, cache=cache):
+            if (s, a) not in cache:
+                nb = layout["nbrs"][s][a]
+                lam = gauges[(min(s, nb), max(s, nb))]
+                cache[(s, a)] = gauge_tensor(c0, lam[0], lam[1], kets[s].legs[a][2], dt)
+            return cache[(s, a)]
 
-    res = _run_jobs(ctxs, jobs, run)
-    ratios = []
-    for q in range(len(terms)):
-        (mn, ln), (md, ld) = res[2 * q], res[2 * q + 1]
-        ratios.append(mn / md * math.exp(ln - ld))
-    return float(sum(ratios)), ratios
+        terms = [((a, b), hop) for a, b in layout["edges"]] + [((s,), onsite) for s in range(layout["n"])]
+        for targets, op in terms:
+            sites, dang, tree_op, tree_norm = cluster_fn(list(targets))
+            for o, tree in ((op, tree_op), (None, tree_norm)):
+                tens, bonds, pos = cluster_network(layout, kets, bras, sites, dang, gauge_of, o, targets)
+                nets.append({"tensors": tens, "bonds": bonds, "tree": tree, "positions": pos, "policy": policy,
+                             "chi": chi})
+        nterms.append(len(terms))
+        keep.append((bras, cache))
+    res = contract_many(ctxs, nets, prec, batch)
+    out, q = [], 0
+    for nt in nterms:
+        ratios = []
+        for _ in range(nt):
+            (mn, ln), (md, ld) = res[q], res[q + 1]
+            ratios.append(mn / md * math.exp(ln - ld))
+            q += 2
+        out.append((float(sum(ratios)), ratios))
+    return out
