@@ -284,10 +284,13 @@ CLUSTER_WORKLOAD = ("Hubbard fPEPS energy terms by the cluster approximation (ra
                     "and without the operator")
 
 
-def cluster_bench(F, ctx, torch, n_graphs, streams, with_oracle):
+def cluster_bench(F, ctx, torch, n_graphs, streams, with_oracle, batch=128):
     """Energy terms per second of the cluster approximation over a set of
     random regular graphs (FP64 and mixed), and the oracle's rate on the
-    smallest graph of the set."""
+    smallest graph of the set.  The two cluster networks of every term of
+    every graph are contracted in lock-step batches of `batch` networks
+    (ftn_contract_batch) spread over `streams` contexts; the first graphs are
+    checked against one ftn_contract call per network."""
     import numpy as np
 
     from paper_2410_02215_gb300 import peps
@@ -315,18 +318,18 @@ def cluster_bench(F, ctx, torch, n_graphs, streams, with_oracle):
         kets = [[F.Tensor.from_blocks(ctx, lay["legs"][s], 0, bl[s], dt) for s in range(lay["n"])]
                 for lay, bl, _ in graphs]
         ctx.synchronize()
+        inst = [(lay, k, cfn(lay), gs) for (lay, _, gs), k in zip(graphs, kets)]
         for c in ctxs:  # warm-up: every context builds its plans
-            for (lay, _, gs), k in zip(graphs[:3], kets[:3]):
-                peps.cluster_energy(c, lay, k, 1.0, 8.0, cfn(lay), gs, policy="late", chi=32, prec=prec)
-        nterms, energies = 0, []
+            peps.cluster_energies(c, inst[:3], 1.0, 8.0, policy="late", chi=32, prec=prec, batch=batch)
+        one = peps.cluster_energies(ctx, inst[:3], 1.0, 8.0, policy="late", chi=32, prec=prec)  # per network
         t0 = time.perf_counter()
-        for (lay, _, gs), k in zip(graphs, kets):
-            en, rat = peps.cluster_energy(ctxs, lay, k, 1.0, 8.0, cfn(lay), gs, policy="late", chi=32, prec=prec)
-            nterms += len(rat)
-            energies.append(en)
+        got = peps.cluster_energies(ctxs, inst, 1.0, 8.0, policy="late", chi=32, prec=prec, batch=batch)
         dt_s = time.perf_counter() - t0
+        nterms = sum(len(r) for _, r in got)
+        energies = [e for e, _ in got]
         res[prec] = energies
-        out[prec] = {"terms_per_s": nterms / dt_s, "terms": nterms, "s": dt_s}
+        out[prec] = {"terms_per_s": nterms / dt_s, "terms": nterms, "s": dt_s, "batch": batch,
+                     "same_as_unbatched": got[:3] == one}
     e64, e32 = np.array(res["f64"]), np.array(res["tf32x3"])
     out["mixed_vs_f64_max_rel_err"] = float(np.max(np.abs(e32 - e64) / np.abs(e64)))
     if with_oracle:
@@ -518,11 +521,14 @@ ENERGY_WORKLOAD = ("Hubbard fPEPS energy <H>/<Psi|Psi> on a 4x4 open square latt
                    "24 hopping + 16 on-site terms + the norm = 41 contractions per evaluation")
 
 
-def energy_bench(F, ctx, evals, with_oracle, workers=8):
+def energy_bench(F, ctx, evals, with_oracle, workers=8, batches=(0, 2, 3, 6)):
     """fPEPS energy evaluations per second, FP64 and mixed (TF32x3 GEMMs with
     FP64 compression), and their errors.  The 41 contractions of an
     evaluation are independent: `workers` contexts on their own streams run
-    them concurrently (the value is the same as a sequential run)."""
+    them concurrently, either one contraction per ftn_contract call (batch 0)
+    or in lock-step batches of a few networks (ftn_contract_batch); the
+    batch size is picked by timing each candidate once after the warm-up.
+    Every configuration gives the same value bit for bit."""
     import torch
 
     from paper_2410_02215_gb300 import peps
@@ -545,15 +551,23 @@ def energy_bench(F, ctx, evals, with_oracle, workers=8):
         t0 = time.perf_counter()
         e1, _, _ = peps.energy(ctx, lay, kets, 1.0, 8.0, tf, policy="late", chi=32, prec=prec)
         one_s = time.perf_counter() - t0
+        trial = {}
+        for b in batches:
+            peps.energy(ctxs, lay, kets, 1.0, 8.0, tf, policy="late", chi=32, prec=prec, batch=b)
+            t0 = time.perf_counter()
+            eb, _, _ = peps.energy(ctxs, lay, kets, 1.0, 8.0, tf, policy="late", chi=32, prec=prec, batch=b)
+            trial[b] = (time.perf_counter() - t0, eb == e1)
+        best = min(trial, key=lambda b: trial[b][0])
         l0 = sum(c.launches() for c in ctxs)
         t0 = time.perf_counter()
         for _ in range(evals):
-            e, _, _ = peps.energy(ctxs, lay, kets, 1.0, 8.0, tf, policy="late", chi=32, prec=prec)
+            e, _, _ = peps.energy(ctxs, lay, kets, 1.0, 8.0, tf, policy="late", chi=32, prec=prec, batch=best)
         dt_s = time.perf_counter() - t0
         res[prec] = e
-        out[prec] = {"evals_per_s": evals / dt_s, "s_per_eval": dt_s / evals, "energy": e,
+        out[prec] = {"evals_per_s": evals / dt_s, "s_per_eval": dt_s / evals, "energy": e, "batch": best,
                      "gpu_launches_per_eval": (sum(c.launches() for c in ctxs) - l0) / evals,
-                     "one_stream_s_per_eval": one_s, "same_as_one_stream": e == e1}
+                     "one_stream_s_per_eval": one_s, "same_as_one_stream": e == e1 and all(v[1] for v in trial.values()),
+                     "trial_s_per_eval_by_batch": {str(b): round(v[0], 4) for b, v in trial.items()}}
     out["mixed_vs_f64_rel_err"] = abs(res["tf32x3"] - res["f64"]) / abs(res["f64"])
     out["speedup_mixed_vs_f64"] = out["tf32x3"]["evals_per_s"] / out["f64"]["evals_per_s"]
     if with_oracle:

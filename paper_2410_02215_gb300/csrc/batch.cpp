@@ -15,7 +15,7 @@ ftn_status tensordot_impl(ftn_ctx ctx, ftn_tensor A, ftn_tensor B, int n, const 
 
 namespace {
 
-// host tables packed at 256-byte offsets, uploaded with one copy
+// Small host tables packed at 256-byte offsets, uploaded with one copy.
 struct TablePack {
   std::vector<uint8_t> host;
   size_t put(const void* p, size_t bytes) {
@@ -30,6 +30,8 @@ struct TablePack {
     return upload_table(ctx, host.data(), host.size(), &dev.p);
   }
 };
+
+inline size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 inline const char* lowest256(const char* p) { return (const char*)((uintptr_t)p & ~(uintptr_t)255); }
 
@@ -66,27 +68,28 @@ ftn_status flush_perm(ftn_ctx ctx, PermBatch& pb, ftn_dtype in_type, int mode, i
     }
     sb = lowest256(sb);
     db = lowest256(db);
-    std::vector<PermJob> jobs;
-    jobs.reserve(v.size());
+    const size_t bytes = v.size() * sizeof(PermJob);
+    PermJob* jobs = (PermJob*)staging_begin(ctx, bytes);
+    if (!jobs) return set_error(FTN_ENOMEM, "host staging allocation failed");
     int64_t tiles = 0;
-    for (auto& it : v) {
+    for (size_t i = 0; i < v.size(); ++i) {
+      const auto& it = v[i];
       const int64_t ds = it.src - sb, dd = it.dst - db;
       if (ds % (int64_t)es_in || dd % (int64_t)es_out)
         return set_error(FTN_EINVAL, "batched permute: buffer not aligned to its element size");
-      PermJob j = it.j;
+      PermJob& j = jobs[i];
+      j = it.j;
       j.src_off += ds / (int64_t)es_in;
       j.dst_off += dd / (int64_t)es_out;
       j.tile_begin = tiles;
       tiles += it.tiles;
-      jobs.push_back(j);
     }
-    TablePack tp;
-    tp.put(jobs.data(), jobs.size() * sizeof(PermJob));
     DevTables dev;
-    FTN_TRY(tp.upload(ctx, dev));
+    dev.ctx = ctx;
+    FTN_TRY(staging_upload(ctx, bytes, &dev.p));
     char* d0 = const_cast<char*>(db);
     const int rec = prof_begin(ctx, "permute", 0, 0);
-    const ftn_status st = launch_permute(ctx, (const PermJob*)dev.p, (int)jobs.size(), tiles, kind, sb, d0,
+    const ftn_status st = launch_permute(ctx, (const PermJob*)dev.p, (int)v.size(), tiles, kind, sb, d0,
                                          lo_delta ? d0 + lo_delta : nullptr, in_type, mode);
     prof_end(ctx, rec);
     FTN_TRY(st);
@@ -140,82 +143,92 @@ ftn_status add_gemm_set(GemmF64Batch& gb, std::vector<GemmProb>& probs, const do
 
 ftn_status flush_gemm_f64(GemmF64Batch& gb) {
   ftn_ctx ctx = gb.ctx;
-  TablePack tp;
   struct L {
     size_t off;
     int n, bn;
     int64_t tiles;
-    const double* base;
+    const char* base;
+    const std::vector<GemmF64Batch::Item>* v;
   };
+  // layout of the tables (one staging chunk), then the rebased copies
   std::vector<L> launches;
-  double fl = 0;
+  size_t total = 0;
   for (auto& kv : gb.by_bn) {
     auto& v = kv.second;
     if (v.empty()) continue;
     const char* base = (const char*)v[0].a;
     for (auto& it : v) base = std::min({base, (const char*)it.a, (const char*)it.b, (const char*)it.c});
-    base = lowest256(base);
-    std::vector<GemmProb> probs;
-    probs.reserve(v.size());
-    int64_t tiles = 0;
-    for (auto& it : v) {
-      GemmProb g = it.g;
-      const int64_t da = (const char*)it.a - base, db = (const char*)it.b - base, dc = (const char*)it.c - base;
-      if ((da | db | dc) & 7) return set_error(FTN_EINVAL, "batched GEMM: buffer not 8-byte aligned");
-      g.a_off += da / 8;
-      g.b_off += db / 8;
-      g.c_off += dc / 8;
-      g.tile_begin = tiles;
-      tiles += (int64_t)g.tiles_m * g.tiles_n * (g.nsplit > 1 ? g.nsplit : 1);
-      fl += 2.0 * g.M * g.N * g.K;
-      probs.push_back(g);
-    }
-    launches.push_back({tp.put(probs.data(), probs.size() * sizeof(GemmProb)), (int)probs.size(), kv.first, tiles,
-                        (const double*)base});
+    launches.push_back({total, (int)v.size(), kv.first, 0, lowest256(base), &v});
+    total = al256(total + v.size() * sizeof(GemmProb));
   }
-  size_t red_off = 0;
-  int64_t red_total = 0;
-  const double* pbase = nullptr;
-  double* cbase = nullptr;
   const int nred = (int)gb.red.size();
+  const size_t red_off = total;
+  const char *pb = nullptr, *cb = nullptr;
   if (nred) {
-    const char *pb = (const char*)gb.red[0].part, *cb = (const char*)gb.red[0].c;
+    pb = (const char*)gb.red[0].part;
+    cb = (const char*)gb.red[0].c;
     for (auto& it : gb.red) {
       pb = std::min(pb, (const char*)it.part);
       cb = std::min(cb, (const char*)it.c);
     }
     pb = lowest256(pb);
     cb = lowest256(cb);
-    std::vector<GemmProb> red;
-    for (auto& it : gb.red) {
-      GemmProb r = it.r;
+    total += nred * sizeof(GemmProb);
+  }
+  if (launches.empty() && !nred) return FTN_OK;
+  uint8_t* h = (uint8_t*)staging_begin(ctx, total);
+  if (!h) return set_error(FTN_ENOMEM, "host staging allocation failed");
+  double fl = 0;
+  for (L& l : launches) {
+    GemmProb* out = (GemmProb*)(h + l.off);
+    int64_t tiles = 0;
+    for (size_t i = 0; i < l.v->size(); ++i) {
+      const auto& it = (*l.v)[i];
+      const int64_t da = (const char*)it.a - l.base, db = (const char*)it.b - l.base, dc = (const char*)it.c - l.base;
+      if ((da | db | dc) & 7) return set_error(FTN_EINVAL, "batched GEMM: buffer not 8-byte aligned");
+      GemmProb& g = out[i];
+      g = it.g;
+      g.a_off += da / 8;
+      g.b_off += db / 8;
+      g.c_off += dc / 8;
+      g.tile_begin = tiles;
+      tiles += (int64_t)g.tiles_m * g.tiles_n * (g.nsplit > 1 ? g.nsplit : 1);
+      fl += 2.0 * g.M * g.N * g.K;
+    }
+    l.tiles = tiles;
+  }
+  int64_t red_total = 0;
+  if (nred) {
+    GemmProb* out = (GemmProb*)(h + red_off);
+    for (int i = 0; i < nred; ++i) {
+      const auto& it = gb.red[i];
       const int64_t dp = (const char*)it.part - pb, dc = (const char*)it.c - cb;
       if ((dp | dc) & 7) return set_error(FTN_EINVAL, "batched reduction: buffer not 8-byte aligned");
+      GemmProb& r = out[i];
+      r = it.r;
       r.a_off += dp / 8;
       r.c_off += dc / 8;
       r.tile_begin = red_total;
       red_total += (int64_t)r.M * r.N;
-      red.push_back(r);
     }
-    red_off = tp.put(red.data(), red.size() * sizeof(GemmProb));
-    pbase = (const double*)pb;
-    cbase = (double*)const_cast<char*>(cb);
   }
-  gb.by_bn.clear();
-  gb.red.clear();
-  if (launches.empty() && !nred) return FTN_OK;
   DevTables dev;
-  FTN_TRY(tp.upload(ctx, dev));
+  dev.ctx = ctx;
+  FTN_TRY(staging_upload(ctx, total, &dev.p));
   const uint8_t* d = (const uint8_t*)dev.p;
   const int rec = prof_begin(ctx, "gemm_f64", 0, fl);
   ftn_status st = FTN_OK;
   for (const L& l : launches) {
-    st = launch_gemm_f64(ctx, (const GemmProb*)(d + l.off), l.n, l.tiles, l.base, l.base, (double*)l.base, l.bn);
+    const double* base = (const double*)l.base;
+    st = launch_gemm_f64(ctx, (const GemmProb*)(d + l.off), l.n, l.tiles, base, base, const_cast<double*>(base), l.bn);
     if (st != FTN_OK) break;
   }
   if (st == FTN_OK && nred)
-    st = launch_splitk_reduce(ctx, (const GemmProb*)(d + red_off), nred, red_total, pbase, cbase);
+    st = launch_splitk_reduce(ctx, (const GemmProb*)(d + red_off), nred, red_total, (const double*)pb,
+                              (double*)const_cast<char*>(cb));
   prof_end(ctx, rec);
+  gb.by_bn.clear();
+  gb.red.clear();
   return st;
 }
 
@@ -317,8 +330,14 @@ ftn_status tensordot_batch(ftn_ctx ctx, std::vector<TdItem>& items, ftn_prec pre
       const char* cb = (const char*)target(idx[0]);
       for (size_t i : idx) cb = std::min(cb, (const char*)target(i));
       cb = lowest256(cb);
-      std::vector<TcMapSet> maps(2 * idx.size());
-      std::vector<GemmProb> probs;
+      size_t np = 0;
+      for (size_t i : idx) np += plans[i]->probs.size();
+      const size_t om = 0, op = al256(2 * idx.size() * sizeof(TcMapSet));
+      uint8_t* h = (uint8_t*)staging_begin(ctx, op + np * sizeof(GemmProb));
+      if (!h) return set_error(FTN_ENOMEM, "host staging allocation failed");
+      TcMapSet* maps = (TcMapSet*)(h + om);
+      GemmProb* probs = (GemmProb*)(h + op);
+      size_t p0 = 0;
       int64_t tiles = 0;
       double fl = 0;
       for (size_t q = 0; q < idx.size(); ++q) {
@@ -338,27 +357,25 @@ ftn_status tensordot_batch(ftn_ctx ctx, std::vector<TdItem>& items, ftn_prec pre
         for (int pi = 0; pi < 2; ++pi) FTN_TRY(tc_encode_set(prec, bn, ops, pi, &maps[2 * q + pi]));
         const int64_t dc = (const char*)target(i) - cb;
         if (dc & 3) return set_error(FTN_EINVAL, "batched GEMM: output not 4-byte aligned");
-        const int p0 = (int)probs.size();
         for (const GemmProb& g0 : P.probs) {
-          GemmProb g = g0;
+          GemmProb& g = probs[p0 + (&g0 - P.probs.data())];
+          g = g0;
           g.pi = (int32_t)(2 * q) + g0.pi;
           g.tile_begin += tiles;
-          g.grp_first += p0;
+          g.grp_first += (int32_t)p0;
           g.c_off += dc / 4;
           fl += 2.0 * g.M * g.N * g.K;
-          probs.push_back(g);
         }
+        p0 += P.probs.size();
         tiles += P.gemm_tiles;
       }
-      TablePack tp;
-      const size_t om = tp.put(maps.data(), maps.size() * sizeof(TcMapSet));
-      const size_t op = tp.put(probs.data(), probs.size() * sizeof(GemmProb));
       DevTables dev;
-      FTN_TRY(tp.upload(ctx, dev));
+      dev.ctx = ctx;
+      FTN_TRY(staging_upload(ctx, op + np * sizeof(GemmProb), &dev.p));
       const uint8_t* d = (const uint8_t*)dev.p;
       const int rec = prof_begin(ctx, "gemm_tc", 0, fl);
       const ftn_status st = launch_gemm_tc_maps(ctx, prec, (const TcMapSet*)(d + om), (const GemmProb*)(d + op),
-                                                (int)probs.size(), tiles, bn, (float*)const_cast<char*>(cb));
+                                                (int)np, tiles, bn, (float*)const_cast<char*>(cb));
       prof_end(ctx, rec);
       FTN_TRY(st);
     }

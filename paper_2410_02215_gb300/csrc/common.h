@@ -160,6 +160,8 @@ struct ftn_ctx_s {
   // grow-only workspace arena (reused by every call on this context)
   void* ws = nullptr;
   size_t ws_bytes = 0;
+  // host buffer for the tables of batched launches (staging_begin)
+  std::vector<uint8_t> stage;
   // per-launch profiling (ftn_ctx_profile)
   bool prof_on = false;
   std::vector<ftn_prof_rec> prof;
@@ -284,6 +286,12 @@ int tc_pick_bn(int max_n, ftn_prec prec);
 int64_t tc_tiles_for(int M, int N, int bn);
 
 ftn_status upload_table(ftn_ctx ctx, const void* host, size_t bytes, void** dev);
+// Table upload without an intermediate copy: staging_begin returns the
+// context's host buffer (at least `bytes`, contents undefined) for the
+// caller to fill; staging_upload copies its first `bytes` into a new device
+// table on the context's stream.
+void* staging_begin(ftn_ctx ctx, size_t bytes);
+ftn_status staging_upload(ftn_ctx ctx, size_t bytes, void** dev);
 // profiling brackets around one launch (no-ops unless profiling is enabled)
 int prof_begin(ftn_ctx ctx, const char* label, double bytes, double flops);
 void prof_end(ftn_ctx ctx, int rec);

@@ -317,37 +317,44 @@ __global__ void __launch_bounds__(SVDC_WARPS * 32) svd_rows_cluster_kernel(const
   __shared__ unsigned char live[LA_MAX_DIM];  // this CTA's slots
   __shared__ unsigned char all_live[LA_MAX_DIM];
   __shared__ int n_act;
-  __shared__ double red[SVDC_WARPS];
+  __shared__ double rnorm[LA_MAX_DIM];  // this CTA's squared row norms
   const uint32_t rank = cluster_rank();
   const SvdJob jb = jobs[blockIdx.x / C];
   const int n = jb.n, m = jb.m;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int nloc = ((int)(n - rank) + C - 1) / C;  // rows rank, rank + C, ...
-  double ss = 0.0;
   for (int l = 0; l < nloc; ++l)
-    for (int i = threadIdx.x; i < m; i += blockDim.x) {
-      const double v = jb.T[(int64_t)(l * C + rank) * m + i];
-      rows[(int64_t)l * m + i] = v;
-      ss = fma(v, v, ss);
-    }
-  for (int o = 16; o; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
-  if (lane == 0) red[warp] = ss;
+    for (int i = threadIdx.x; i < m; i += blockDim.x) rows[(int64_t)l * m + i] = jb.T[(int64_t)(l * C + rank) * m + i];
   if (threadIdx.x == 0) flag[0] = flag[1] = 0;
   __syncthreads();
-  if (threadIdx.x == 0) {
-    double t = 0.0;
-    for (int w = 0; w < SVDC_WARPS; ++w) t += red[w];
-    part = t;
+  // squared row norms (one warp per row, lanes strided along the row)
+  for (int l = warp; l < nloc; l += SVDC_WARPS) {
+    const double* r = rows + (int64_t)l * m;
+    double q = 0.0;
+    for (int i = lane; i < m; i += 32) q = fma(r[i], r[i], q);
+    for (int o = 16; o; o >>= 1) q += __shfl_xor_sync(0xffffffffu, q, o);
+    if (lane == 0) rnorm[l] = q;
   }
   const uint32_t base = smem_u32(rows);
   cluster_sync_all();
-  // |T|_F^2 from the C partial sums, added in the same order in every CTA
-  double fro2 = 0.0;
-  for (int c = 0; c < C; ++c) {
-    double v;
-    asm volatile("ld.shared::cluster.f64 %0, [%1];" : "=d"(v) : "r"(map_rank(smem_u32(&part), (uint32_t)c)) : "memory");
-    fro2 += v;
+  // |T|_F^2 as the sum of the row norms in row order (lane-strided, then the
+  // shuffle tree): the same arithmetic for every cluster size, so a matrix's
+  // decomposition does not depend on the C it is launched with
+  if (warp == 0) {
+    double q = 0.0;
+    for (int i = lane; i < n; i += 32) {
+      double v;
+      asm volatile("ld.shared::cluster.f64 %0, [%1];"
+                   : "=d"(v)
+                   : "r"(map_rank(smem_u32(&rnorm[i / C]), (uint32_t)(i % C)))
+                   : "memory");
+      q += v;
+    }
+    for (int o = 16; o; o >>= 1) q += __shfl_xor_sync(0xffffffffu, q, o);
+    if (lane == 0) part = q;
   }
+  __syncthreads();
+  const double fro2 = part;
   const double tol2 = jacobi_tol2(m), tau2 = jacobi_tau2(m, fro2);
 
   // marks this CTA's live rows, then (after a cluster barrier) rebuilds the
@@ -945,12 +952,13 @@ ftn_status compress_batch(ftn_ctx ctx, std::vector<CompressItem>& items) {
     FTN_TRY(flush_gemm_f64(gb));
     if (!svd.empty()) {
       // rows up to 32 * SVDC_MAX_E long whose cluster share fits in shared
-      // memory go to the cluster kernel -- one launch per cluster size and
-      // row length, so that a decomposition does not depend on the others
-      // in the batch -- the others to the single-CTA one
+      // memory go to the cluster kernel (one launch; its arithmetic does not
+      // depend on the cluster size or row length it is launched with, so a
+      // decomposition does not depend on the other jobs of the batch), the
+      // others to the single-CTA one
       const int cmax = svd_cluster_max(ctx);
-      std::map<std::pair<int, int>, std::vector<SvdJob>> small;
-      std::vector<SvdJob> big;
+      std::vector<SvdJob> small, big;
+      int e_max = 1, c_use = 1;
       for (const SvdJob& j : svd) {
         const int np = j.n + (j.n & 1);
         int c = 1;
@@ -960,31 +968,25 @@ ftn_status compress_batch(ftn_ctx ctx, std::vector<CompressItem>& items) {
           big.push_back(j);
           continue;
         }
+        small.push_back(j);
+        c_use = std::max(c_use, c);
         int e = 1;
         while (32 * e < j.m) e *= 2;
-        small[{c, e}].push_back(j);
+        e_max = std::max(e_max, e);
       }
-      std::vector<SvdJob> all;
-      std::vector<size_t> first;
-      for (auto& kv : small) {
-        first.push_back(all.size());
-        all.insert(all.end(), kv.second.begin(), kv.second.end());
-      }
-      const size_t big0 = all.size();
+      std::vector<SvdJob> all(small);
       all.insert(all.end(), big.begin(), big.end());
       DevBuf t_svd(ctx);
       FTN_TRY(put_table(ctx, all, &t_svd.p));
       const int rec = prof_begin(ctx, "svd_jacobi", 0, 0);
-      size_t g = 0;
-      for (auto& kv : small) {
+      if (!small.empty()) {
         size_t smem = 0;
-        const int c = kv.first.first;
-        for (const SvdJob& j : kv.second) smem = std::max(smem, (size_t)((j.n + c - 1) / c) * j.m * 8);
-        FTN_TRY(launch_svd_cluster(ctx, (const SvdJob*)t_svd.p + first[g++], (int)kv.second.size(), c,
-                                   kv.first.second, smem));
+        for (const SvdJob& j : small) smem = std::max(smem, (size_t)((j.n + c_use - 1) / c_use) * j.m * 8);
+        FTN_TRY(launch_svd_cluster(ctx, (const SvdJob*)t_svd.p, (int)small.size(), c_use, e_max, smem));
       }
       if (!big.empty()) {
-        svd_rows_global_kernel<<<(unsigned)big.size(), LA_THREADS, 0, ctx->stream>>>((const SvdJob*)t_svd.p + big0);
+        svd_rows_global_kernel<<<(unsigned)big.size(), LA_THREADS, 0, ctx->stream>>>((const SvdJob*)t_svd.p +
+                                                                                   small.size());
         ctx->launches += 1;
         FTN_CUDA(cudaGetLastError());
       }

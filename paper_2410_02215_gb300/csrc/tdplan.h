@@ -1,5 +1,8 @@
 // Contraction plan shared by the tensordot and the compression code.
 #pragma once
+#include <string>
+#include <unordered_map>
+
 #include "common.h"
 
 namespace ftn {
@@ -9,6 +12,31 @@ struct DevTables {
   void* p = nullptr;
   ~DevTables() {
     if (p) dev_free(ctx, p);
+  }
+};
+
+// Plan-cache key: the raw bytes of every field that determines a plan, in a
+// fixed order, each variable-length part after its length (no text
+// formatting: keys are built once per contraction step).
+struct CacheKey {
+  std::string s;
+  CacheKey() { s.reserve(192); }
+  template <typename T>
+  CacheKey& put(T v) {
+    s.append(reinterpret_cast<const char*>(&v), sizeof(T));
+    return *this;
+  }
+  CacheKey& meta(const ftn_tensor_s* t) {
+    put<int32_t>(t->rank).put<int32_t>(t->parity).put<int32_t>((int32_t)t->dtype);
+    s.append(reinterpret_cast<const char*>(t->d0), sizeof(int32_t) * t->rank);
+    s.append(reinterpret_cast<const char*>(t->d1), sizeof(int32_t) * t->rank);
+    s.append(reinterpret_cast<const char*>(t->dual), t->rank);
+    return *this;
+  }
+  CacheKey& ints(const int* v, int n) {
+    put<int32_t>(n);
+    for (int i = 0; i < n; ++i) put<int32_t>(v[i]);
+    return *this;
   }
 };
 

@@ -114,6 +114,20 @@ ftn_status upload_table(ftn_ctx ctx, const void* host, size_t bytes, void** dev)
   return FTN_OK;
 }
 
+// ---- table staging ----------------------------------------------------------------
+// A small copy from pageable memory is staged by the driver when the call
+// returns, so the buffer is free for the next table at once.  (Measured: a
+// pinned ring with asynchronous copies was slower with several contexts on
+// their own streams.)
+void* staging_begin(ftn_ctx ctx, size_t bytes) {
+  ctx->stage.resize(std::max<size_t>(bytes, 256));
+  return ctx->stage.data();
+}
+
+ftn_status staging_upload(ftn_ctx ctx, size_t bytes, void** dev) {
+  return upload_table(ctx, ctx->stage.data(), bytes, dev);
+}
+
 // ---- permute job builder ------------------------------------------------------
 void add_perm_job(std::vector<PermJob>& jobs, int64_t& tiles, int rank, const int64_t* dims_in,
                   const int64_t* dstr_in, int64_t src_off, int64_t dst_off, int sign) {

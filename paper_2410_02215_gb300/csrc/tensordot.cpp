@@ -4,7 +4,6 @@
 // sector-matrix layout of Sec. IV.A, then sign-permute + grouped GEMM.
 #include <algorithm>
 #include <mutex>
-#include <sstream>
 
 #include "tdplan.h"
 
@@ -80,13 +79,6 @@ bool probs_in_bounds(const std::vector<GemmProb>& probs, int64_t a_n, int64_t b_
   return true;
 }
 
-static std::string meta_key(const ftn_tensor_s* t) {
-  std::ostringstream o;
-  o << t->rank << ':' << t->parity << ':' << (int)t->dtype << ':';
-  for (int k = 0; k < t->rank; ++k) o << t->d0[k] << ',' << t->d1[k] << ',' << (int)t->dual[k] << ';';
-  return o.str();
-}
-
 static ftn_status upload_plan(ftn_ctx ctx, TdPlan& P) {
   size_t sa = P.ja.size() * sizeof(PermJob), sb = P.jb.size() * sizeof(PermJob), sc = P.jc.size() * sizeof(PermJob),
          sp = P.probs.size() * sizeof(GemmProb), sr = P.red.size() * sizeof(GemmProb);
@@ -118,8 +110,8 @@ static ftn_status upload_plan(ftn_ctx ctx, TdPlan& P) {
 // context at a time), and std::map nodes do not move on insertion.
 static std::mutex g_cache_mu;
 
-static std::map<std::string, std::shared_ptr<TdPlan>>& plan_cache(ftn_ctx ctx) {
-  static std::map<ftn_ctx, std::map<std::string, std::shared_ptr<TdPlan>>> caches;
+static std::unordered_map<std::string, std::shared_ptr<TdPlan>>& plan_cache(ftn_ctx ctx) {
+  static std::map<ftn_ctx, std::unordered_map<std::string, std::shared_ptr<TdPlan>>> caches;
   std::lock_guard<std::mutex> lock(g_cache_mu);
   return caches[ctx];
 }
@@ -478,22 +470,20 @@ ftn_status validate_pairs(const ftn_tensor_s* A, const ftn_tensor_s* B, int n, c
 ftn_status get_plan(ftn_ctx ctx, const ftn_tensor_s* A, const ftn_tensor_s* B, int n, const int* ax,
                            const int* ay, uint64_t fa, uint64_t fb, const int* out_perm, ftn_prec prec,
                            std::shared_ptr<TdPlan>& P) {
-  std::ostringstream key;
-  key << "td|" << meta_key(A) << '|' << meta_key(B) << '|' << n << ':';
-  for (int i = 0; i < n; ++i) key << ax[i] << ',' << ay[i] << ';';
-  key << '|' << fa << '|' << fb << '|' << (int)prec << '|' << (((uintptr_t)A->data & 15) == 0)
-      << (((uintptr_t)B->data & 15) == 0) << '|';
-  if (out_perm)
-    for (int u = 0; u < A->rank + B->rank - 2 * n; ++u) key << out_perm[u] << ',';
+  CacheKey key;
+  key.meta(A).meta(B).ints(ax, n).ints(ay, n).put(fa).put(fb).put<int32_t>((int32_t)prec);
+  key.put<uint8_t>(((uintptr_t)A->data & 15) == 0).put<uint8_t>(((uintptr_t)B->data & 15) == 0);
+  key.put<uint8_t>(out_perm != nullptr);
+  if (out_perm) key.ints(out_perm, A->rank + B->rank - 2 * n);
   auto& cache = plan_cache(ctx);
-  auto it = cache.find(key.str());
+  auto it = cache.find(key.s);
   if (it != cache.end()) {
     P = it->second;
     return FTN_OK;
   }
   FTN_TRY(build_plan(ctx, A, B, n, ax, ay, fa, fb, out_perm, prec, P));
   if (cache.size() > 65536) cache.clear();
-  cache[key.str()] = P;
+  cache[key.s] = P;
   return FTN_OK;
 }
 
@@ -618,8 +608,8 @@ struct TrPlan {
   PermJob* d_jobs = nullptr;
 };
 
-static std::map<std::string, std::shared_ptr<TrPlan>>& tr_cache(ftn_ctx ctx) {
-  static std::map<ftn_ctx, std::map<std::string, std::shared_ptr<TrPlan>>> caches;
+static std::unordered_map<std::string, std::shared_ptr<TrPlan>>& tr_cache(ftn_ctx ctx) {
+  static std::map<ftn_ctx, std::unordered_map<std::string, std::shared_ptr<TrPlan>>> caches;
   std::lock_guard<std::mutex> lock(g_cache_mu);
   return caches[ctx];
 }
@@ -649,12 +639,11 @@ ftn_status permute_impl(ftn_ctx ctx, ftn_tensor t, const int* perm, bool fermion
     FTN_TRY(make_tensor(ctx, r, d0, d1, du, t->parity, t->dtype, &o));
     created = true;
   }
-  std::ostringstream key;
-  key << "tr|" << meta_key(t) << '|' << fermionic << '|' << (((uintptr_t)t->data & 15) == 0) << '|';
-  for (int u = 0; u < r; ++u) key << perm[u] << ',';
+  CacheKey key;
+  key.meta(t).put<uint8_t>(fermionic).put<uint8_t>(((uintptr_t)t->data & 15) == 0).ints(perm, r);
   auto& cache = tr_cache(ctx);
   std::shared_ptr<TrPlan> P;
-  auto it = cache.find(key.str());
+  auto it = cache.find(key.s);
   if (it != cache.end()) {
     P = it->second;
   } else {
@@ -694,7 +683,7 @@ ftn_status permute_impl(ftn_ctx ctx, ftn_tensor t, const int* perm, bool fermion
     P->dev->p = d;
     P->d_jobs = (PermJob*)d;
     if (cache.size() > 65536) cache.clear();
-    cache[key.str()] = P;
+    cache[key.s] = P;
   }
   int rec = prof_begin(ctx, "permute", 2.0 * t->numel * dtype_size(t->dtype), 0);
   ftn_status st = launch_permute(ctx, P->d_jobs, (int)P->jobs.size(), P->tiles, P->staged, t->data, o->data,

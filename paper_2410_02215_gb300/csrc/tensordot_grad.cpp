@@ -15,7 +15,6 @@
 #include <algorithm>
 #include <map>
 #include <mutex>
-#include <sstream>
 
 #include "tdplan.h"
 
@@ -53,17 +52,10 @@ struct GradPlan {
 
 std::mutex g_grad_mu;
 
-std::map<std::string, std::shared_ptr<GradPlan>>& grad_cache(ftn_ctx ctx) {
-  static std::map<ftn_ctx, std::map<std::string, std::shared_ptr<GradPlan>>> caches;
+std::unordered_map<std::string, std::shared_ptr<GradPlan>>& grad_cache(ftn_ctx ctx) {
+  static std::map<ftn_ctx, std::unordered_map<std::string, std::shared_ptr<GradPlan>>> caches;
   std::lock_guard<std::mutex> lock(g_grad_mu);
   return caches[ctx];
-}
-
-std::string meta_str(const ftn_tensor_s* t) {
-  std::ostringstream o;
-  o << t->rank << ':' << t->parity << ':' << (int)t->dtype << ':';
-  for (int k = 0; k < t->rank; ++k) o << t->d0[k] << ',' << t->d1[k] << ',' << (int)t->dual[k] << ';';
-  return o.str();
 }
 
 ftn_status upload(ftn_ctx ctx, GradPlan& P) {
@@ -346,23 +338,20 @@ ftn_status build(ftn_ctx ctx, const ftn_tensor_s* A, const ftn_tensor_s* B, cons
 ftn_status get_grad_plan(ftn_ctx ctx, const ftn_tensor_s* A, const ftn_tensor_s* B, const ftn_tensor_s* G, int n,
                          const int* ax, const int* ay, uint64_t fa, uint64_t fb, const int* out_perm, ftn_prec prec,
                          bool wrt_b, std::shared_ptr<GradPlan>& P) {
-  std::ostringstream key;
-  key << "grad|" << (wrt_b ? 'b' : 'a') << '|' << meta_str(A) << '|' << meta_str(B) << '|' << meta_str(G) << '|'
-      << n << ':';
-  for (int i = 0; i < n; ++i) key << ax[i] << ',' << ay[i] << ';';
-  key << '|' << fa << '|' << fb << '|' << (int)prec << '|' << (((uintptr_t)G->data & 15) == 0)
-      << (((uintptr_t)(wrt_b ? A : B)->data & 15) == 0) << '|';
-  if (out_perm)
-    for (int u = 0; u < A->rank + B->rank - 2 * n; ++u) key << out_perm[u] << ',';
+  CacheKey key;
+  key.put<uint8_t>(wrt_b).meta(A).meta(B).meta(G).ints(ax, n).ints(ay, n).put(fa).put(fb).put<int32_t>((int32_t)prec);
+  key.put<uint8_t>(((uintptr_t)G->data & 15) == 0).put<uint8_t>(((uintptr_t)(wrt_b ? A : B)->data & 15) == 0);
+  key.put<uint8_t>(out_perm != nullptr);
+  if (out_perm) key.ints(out_perm, A->rank + B->rank - 2 * n);
   auto& cache = grad_cache(ctx);
-  auto it = cache.find(key.str());
+  auto it = cache.find(key.s);
   if (it != cache.end()) {
     P = it->second;
     return FTN_OK;
   }
   FTN_TRY(build(ctx, A, B, G, n, ax, ay, fa, fb, out_perm, prec, wrt_b, P));
   if (cache.size() > 65536) cache.clear();
-  cache[key.str()] = P;
+  cache[key.s] = P;
   return FTN_OK;
 }
 
