@@ -40,7 +40,7 @@ if ROOT not in sys.path:
 import workloads as W  # noqa: E402
 
 CASES = ["T1", "T2", "T3", "T4"]
-PREC_DTYPE = {"f64": "f64", "tf32": "tf32", "bf16": "bf16", "tf32x3": "tf32x3", "bf16x3": "bf16x3"}
+PREC_DTYPE = {"f64": "f64", "tf32": "tf32", "bf16": "bf16", "tf32x3": "tf32x3", "bf16x3": "bf16x3", "f16x3": "f16x3"}
 WORKLOAD = ("fermionic tensordot microbenchmark T1-T4: rank-5 Z2 site tensors (D=8 as 4+4, phys 4 as 2+2), "
             "rank-6 environments (chi=64 as 32+32); T1 E.A over 2 D legs, T2 E.A over 3 D legs, "
             "T3 A.B over 2 D legs, T4 E.E' over (chi,D,D); random stored and output leg orders")
@@ -248,33 +248,81 @@ def one_step(F, ctx, cases, ins, outs, prec, tag=False):
         outs[c["name"]] = r
 
 
-def time_steps(F, ctx, torch, cases, prec, steps, warmup, flush, world, profile=False):
+def time_steps(F, ctx, torch, cases, prec, steps, warmup, flush, world, profile=False, graph=False):
+    """Times `steps` steps (L2 flushed before each, outside the events).
+    Eager: one library call per contraction per step.  profile=True adds a
+    second eager pass with per-launch CUDA events (ftn_ctx_profile) for the
+    roofline; graph=True adds a pass that replays the step captured once as a
+    CUDA graph (the same kernels with the same arguments), checked bit for bit
+    against the eager outputs.  Returns (ms eager, launches per step, profile,
+    inputs, outputs, graph info)."""
     ins = make_inputs(F, ctx, torch, cases, prec)
     outs = {}
     for _ in range(warmup):
         one_step(F, ctx, cases, ins, outs, prec)
     torch.cuda.synchronize()
-    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+
+    def timed(run):
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        barrier(world)
+        torch.cuda.synchronize()
+        for i in range(steps):
+            flush.zero_()
+            evs[i][0].record()
+            run()
+            evs[i][1].record()
+        torch.cuda.synchronize()
+        barrier(world)
+        return sum(a.elapsed_time(b) for a, b in evs)
+
+    l0 = ctx.launches()
+    ms = timed(lambda: one_step(F, ctx, cases, ins, outs, prec))
+    launches = (ctx.launches() - l0) // max(steps, 1)
+    prof = None
     if profile:
         ctx.profile(True)
-    l0 = ctx.launches()
-    barrier(world)
-    torch.cuda.synchronize()
-    for i in range(steps):
-        flush.zero_()
-        evs[i][0].record()
-        one_step(F, ctx, cases, ins, outs, prec, tag=profile)
-        evs[i][1].record()
-    torch.cuda.synchronize()
-    barrier(world)
-    launches = ctx.launches() - l0
-    ms = sum(a.elapsed_time(b) for a, b in evs)
-    prof = ctx.profile_read() if profile else None
-    if profile:
+        timed(lambda: one_step(F, ctx, cases, ins, outs, prec, tag=True))
+        prof = ctx.profile_read()
         ctx.profile(False)
         ctx.profile_tag("")
+    ginfo = None
+    if graph:
+        ginfo = graph_steps(F, ctx, torch, cases, ins, outs, prec, timed)
     ctx.synchronize()
-    return ms, launches, prof, ins, outs
+    return ms, launches, prof, ins, outs, ginfo
+
+
+def graph_steps(F, ctx, torch, cases, ins, outs, prec, timed):
+    """The step captured once as a CUDA graph on the context's stream and
+    replayed; the outputs of a replay must equal the eager step's bit for
+    bit.  Returns {"ms", "launches_per_step", "identical"} or {"error"}."""
+    ref = {k: v.view().clone() for k, v in outs.items()}
+    old = ctx.stream
+    g = torch.cuda.CUDAGraph()
+    try:
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):  # one eager step on the side stream first (capture etiquette)
+            ctx.set_stream(side)
+            one_step(F, ctx, cases, ins, outs, prec)
+        torch.cuda.current_stream().wait_stream(side)
+        l0 = ctx.launches()
+        with torch.cuda.graph(g):
+            ctx.set_stream(torch.cuda.current_stream())
+            one_step(F, ctx, cases, ins, outs, prec)
+        n = ctx.launches() - l0
+    except Exception as e:  # noqa: BLE001 -- reported, the eager number stands
+        ctx.set_stream(old)
+        return {"error": str(e)[:200]}
+    ctx.set_stream(old)
+    for v in outs.values():
+        v.view().zero_()
+    g.replay()
+    torch.cuda.synchronize()
+    same = all(torch.equal(outs[k].view(), ref[k]) for k in ref)
+    ms = timed(g.replay)
+    del g
+    return {"ms": ms, "launches_per_step": n, "identical": bool(same)}
 
 
 CLUSTER_WORKLOAD = ("Hubbard fPEPS energy terms by the cluster approximation (radius 1, Sec. V) on 64 random "
@@ -449,7 +497,7 @@ def traffic_for(label):
 def roofline(prof, peaks, prec="tf32x3"):
     """Roofline of the dominant kernel.  A tensor-core contraction takes the
     dense peak of its operand type (TF32: the measured bf16 burst x 1.1/2.25,
-    the nominal ratio; BF16: the measured bf16 burst).  The split modes run
+    the nominal ratio; BF16 and FP16: the measured bf16 burst).  The split modes run
     3 tensor-core products per algorithmic product, so beside `frac` the
     fraction of the peak / 3 is reported as `frac_of_split_peak`."""
     dom = max(prof, key=lambda r: r["ms"])
@@ -458,14 +506,16 @@ def roofline(prof, peaks, prec="tf32x3"):
     t_s = dom["ms"] / 1e3 / max(dom["launches"], 1)
     bytes_per = dom["bytes"] / max(dom["launches"], 1)
     flops_per = dom["flops"] / max(dom["launches"], 1)
-    bf16 = prec.startswith("bf16")
+    bf16 = prec.startswith("bf16") or prec.startswith("f16")  # 16-bit operands: the bf16 / fp16 rate
     tc_peak = peaks["bf16_tflops"] * (1.0 if bf16 else NOMINAL_TF32_OVER_BF16)
     passes = 3 if prec.endswith("x3") else 1
     out = {"kernel": label, "launches": dom["launches"], "avg_launch_ms": t_s * 1e3}
-    tensor_bound = kind == "gemm_tc" and flops_per / max(bytes_per, 1.0) > tc_peak * 1e12 / (peaks["hbm_gbs"] * 1e9)
+    # tensor-bound when the tensor work (passes x sector flops) per algorithmic byte exceeds the ridge
+    tensor_bound = (kind == "gemm_tc" and
+                    passes * flops_per / max(bytes_per, 1.0) > tc_peak * 1e12 / (peaks["hbm_gbs"] * 1e9))
     if tensor_bound:
         ach = flops_per / t_s / 1e12
-        note = (f"BF16 dense = {peaks['src']} bf16 burst" if bf16 else
+        note = (f"BF16 / FP16 dense = {peaks['src']} bf16 burst" if bf16 else
                 f"TF32 dense = {peaks['src']} bf16 burst x 1.1/2.25 (nominal ratio)")
         out.update({"bound": "tensor", "achieved": ach, "peak": tc_peak, "unit": "TFLOP/s", "frac": ach / tc_peak,
                     "peak_note": note})
@@ -599,9 +649,11 @@ def run_ours(args, rank, world, local):
     flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device="cuda")  # > 129 MB L2
     clk = ClockSampler(local)
     clk.start()
-    ms, launches, prof, ins, outs = time_steps(F, ctx, torch, cases, args.prec, args.steps, args.warmup, flush, world,
-                                               profile=True)
+    ms_eager, launches, prof, ins, outs, ginfo = time_steps(F, ctx, torch, cases, args.prec, args.steps, args.warmup,
+                                                            flush, world, profile=True, graph=not args.no_graph)
     clocks = clk.stop()
+    use_graph = bool(ginfo and ginfo.get("identical"))
+    ms = ginfo["ms"] if use_graph else ms_eager
     back = None
     if not args.no_backward:
         back = backward_bench(F, ctx, torch, cases, args.prec, max(2, args.steps // 2), args.warmup, flush, ins, outs,
@@ -616,8 +668,13 @@ def run_ours(args, rank, world, local):
         "config": {"workload": WORKLOAD, "precision": args.prec, "sector_gflop_per_step": flops_step / 1e9,
                    "l2": "flushed between steps (512 MB write, outside the timed events)",
                    "parallelism": f"replicas x{world} (independent problems, no collective)"},
-        "gpu_launches": launches,
+        "gpu_launches": launches * args.steps,
     }
+    result["config"]["launch"] = ("CUDA graph of the step, captured once and replayed (outputs bit-identical to the "
+                                  "eager step)" if use_graph else "eager: one library call per contraction")
+    result["eager_ms_per_step"] = max_over_ranks(ms_eager, world) / args.steps
+    if ginfo is not None:
+        result["graph"] = ginfo
     result["roofline"] = roofline(prof, peaks, args.prec)
     if back is not None:
         result["backward"] = back
@@ -632,7 +689,7 @@ def run_ours(args, rank, world, local):
     for p in args.compare:
         if p == args.prec:
             continue
-        pms, _, _, pin, pout = time_steps(F, ctx, torch, cases, p, max(2, args.steps // 4), 2, flush, 1)
+        pms, _, _, pin, pout, _ = time_steps(F, ctx, torch, cases, p, max(2, args.steps // 4), 2, flush, 1)
         del pin, pout
         precs[p] = {"tflops": flops_step * max(2, args.steps // 4) / (pms / 1e3) / 1e12,
                     "ms_per_step": pms / max(2, args.steps // 4)}
@@ -666,14 +723,15 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--prec", default="tf32x3", choices=list(PREC_DTYPE))
-    ap.add_argument("--compare", default="f64,tf32,bf16x3", type=lambda s: [x for x in s.split(",") if x])
+    ap.add_argument("--prec", default="f16x3", choices=list(PREC_DTYPE))
+    ap.add_argument("--compare", default="f64,tf32,bf16x3,tf32x3", type=lambda s: [x for x in s.split(",") if x])
     ap.add_argument("--cases", default=",".join(CASES), type=lambda s: [x for x in s.split(",") if x])
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-energy", action="store_true")
     ap.add_argument("--no-backward", action="store_true")
     ap.add_argument("--no-cluster", action="store_true")
+    ap.add_argument("--no-graph", action="store_true", help="time the step eagerly only (no CUDA-graph replay)")
     ap.add_argument("--cluster-graphs", type=int, default=64)
     ap.add_argument("--energy-evals", type=int, default=3)
     ap.add_argument("--energy-streams", type=int, default=8,

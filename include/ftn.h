@@ -71,14 +71,20 @@ typedef enum { FTN_F64 = 0, FTN_F32 = 1 } ftn_dtype;
 
 /* Arithmetic of the sector GEMMs.  FTN_PREC_F64 needs FP64 tensors (DFMA).
  * The others need FP32 tensors and run on the tcgen05 tensor cores with FP32
- * accumulation: TF32 and BF16 round each operand once; TF32X3 and BF16X3
- * split each operand x = hi + lo and sum hi*hi + hi*lo + lo*hi. */
+ * accumulation: TF32 and BF16 round each operand once; TF32X3, BF16X3 and
+ * F16X3 split each operand x = hi + lo and sum hi*hi + hi*lo + lo*hi.  F16X3
+ * (FP16 hi and lo: 11 + 11 significant bits at the 16-bit tensor rate) keeps
+ * TF32X3's accuracy, about 2^-22 of the largest operand entry, while that
+ * entry lies between 2^-3 and 2^15 in magnitude (FP16 overflows above
+ * 65504, and lo parts below 2^-14 lose bits to the subnormal spacing 2^-24);
+ * tensors of the contraction-tree executor are scaled to max |x| = 1. */
 typedef enum {
   FTN_PREC_F64 = 0,
   FTN_PREC_TF32 = 1,
   FTN_PREC_BF16 = 2,
   FTN_PREC_TF32X3 = 3,
-  FTN_PREC_BF16X3 = 4
+  FTN_PREC_BF16X3 = 4,
+  FTN_PREC_F16X3 = 5
 } ftn_prec;
 
 typedef void* (*ftn_alloc_fn)(size_t bytes, void* user);

@@ -40,7 +40,8 @@ size_t perm_out_size(ftn_dtype in_type, int mode) {
     case PERM_TF32:
     case PERM_TF32X2: return 4;
     case PERM_BF16:
-    case PERM_BF16X2: return 2;
+    case PERM_BF16X2:
+    case PERM_F16X2: return 2;
     default: return dtype_size(in_type);
   }
 }
@@ -240,10 +241,10 @@ ftn_status tensordot_batch(ftn_ctx ctx, std::vector<TdItem>& items, ftn_prec pre
     it.C = nullptr;
     return tensordot_impl(ctx, it.A, it.B, it.n, it.ax, it.ay, it.fa, it.fb, nullptr, prec, &it.C);
   }
-  if (prec < FTN_PREC_F64 || prec > FTN_PREC_BF16X3) return set_error(FTN_EINVAL, "bad precision");
+  if (!prec_valid(prec)) return set_error(FTN_EINVAL, "bad precision");
   const bool tc = prec != FTN_PREC_F64;
-  const bool split = prec == FTN_PREC_TF32X3 || prec == FTN_PREC_BF16X3;
-  const bool bf16 = prec == FTN_PREC_BF16 || prec == FTN_PREC_BF16X3;
+  const bool split = prec_split(prec);
+  const bool bf16 = prec_half(prec);  // 16-bit operands
   const ftn_dtype dt = tc ? FTN_F32 : FTN_F64;
   const size_t es = tc ? (bf16 ? 2 : 4) : 8, in_es = dtype_size(dt);
   std::vector<std::shared_ptr<TdPlan>> plans(items.size());
@@ -290,11 +291,7 @@ ftn_status tensordot_batch(ftn_ctx ctx, std::vector<TdItem>& items, ftn_prec pre
   }
   uint8_t* ws = (uint8_t*)workspace(ctx, off);
   if (!ws) return set_error(FTN_ENOMEM, "workspace allocation failed");
-  int mode = PERM_SAME;
-  if (prec == FTN_PREC_TF32) mode = PERM_TF32;
-  if (prec == FTN_PREC_TF32X3) mode = PERM_TF32X2;
-  if (prec == FTN_PREC_BF16) mode = PERM_BF16;
-  if (prec == FTN_PREC_BF16X3) mode = PERM_BF16X2;
+  const int mode = prec_perm_mode(prec);
   // ---- 1. operands into fused sector matrices ----
   PermBatch pb;
   for (size_t i = 0; i < items.size(); ++i) {

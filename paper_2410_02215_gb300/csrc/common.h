@@ -67,8 +67,28 @@ enum PermMode {
   PERM_TF32 = 1,      // FP32 -> TF32-rounded FP32
   PERM_TF32X2 = 2,    // FP32 -> TF32 hi + TF32 lo (two FP32 outputs)
   PERM_BF16 = 3,      // FP32 -> BF16
-  PERM_BF16X2 = 4     // FP32 -> BF16 hi + BF16 lo
+  PERM_BF16X2 = 4,    // FP32 -> BF16 hi + BF16 lo
+  PERM_F16X2 = 5      // FP32 -> FP16 hi + FP16 lo
 };
+
+// Properties of the sector-GEMM precisions (see ftn_prec).
+inline bool prec_valid(ftn_prec p) { return p >= FTN_PREC_F64 && p <= FTN_PREC_F16X3; }
+inline bool prec_split(ftn_prec p) {
+  return p == FTN_PREC_TF32X3 || p == FTN_PREC_BF16X3 || p == FTN_PREC_F16X3;
+}
+// 16-bit tensor-core operands (else TF32 in FP32 words, or FP64)
+inline bool prec_half(ftn_prec p) { return p == FTN_PREC_BF16 || p == FTN_PREC_BF16X3 || p == FTN_PREC_F16X3; }
+// the sign-permute's output conversion for the fused operand matrices
+inline int prec_perm_mode(ftn_prec p) {
+  switch (p) {
+    case FTN_PREC_TF32: return PERM_TF32;
+    case FTN_PREC_TF32X3: return PERM_TF32X2;
+    case FTN_PREC_BF16: return PERM_BF16;
+    case FTN_PREC_BF16X3: return PERM_BF16X2;
+    case FTN_PREC_F16X3: return PERM_F16X2;
+    default: return PERM_SAME;
+  }
+}
 
 // ---- grouped sector GEMM problem: C[m, n] = sum_k A[m, k] B[n, k] ------------
 // The result element (m, n) is stored at c_off + rowpart(m) + colpart(n)

@@ -320,7 +320,7 @@ ftn_status contract_batch_impl(ftn_ctx ctx, int count, const ftn_network* nets, 
   if (!ctx || count < 0 || (count > 0 && (!nets || !trees || !mantissa || !log_scale)))
     return set_error(FTN_EINVAL, "null argument");
   if (count == 0) return FTN_OK;
-  if (prec < FTN_PREC_F64 || prec > FTN_PREC_BF16X3) return set_error(FTN_EINVAL, "bad precision");
+  if (!prec_valid(prec)) return set_error(FTN_EINVAL, "bad precision");
   std::vector<std::unique_ptr<Exec>> ex(count);
   int max_steps = 0;
   for (int i = 0; i < count; ++i) {

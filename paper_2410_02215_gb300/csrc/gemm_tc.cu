@@ -4,14 +4,14 @@
 // fermionic contraction: C_blk[m, n] = sum_k A_pi[row0 + m, k] B_pi[col0 + n, k]
 // where A_pi / B_pi are the fused sector matrices of bond parity pi (K-major,
 // produced by the sign-permute kernel).  Warp roles per CTA:
-//   warp 0    TMA producer: 128 x 32 (TF32) or 128 x 64 (BF16) A tiles and
+//   warp 0    TMA producer: 128 x 32 (TF32) or 128 x 64 (BF16 / FP16) A tiles and
 //             BN x same B tiles into a STAGES-deep shared-memory ring;
 //   warp 1    MMA issuer: tcgen05.mma (M = 128, N = BN) into one of two TMEM
 //             accumulators, tcgen05.commit releases ring slots;
 //   warps 2-9 epilogue, two sets of four (one per TMEM accumulator buffer):
 //             tcgen05.ld of the accumulator (one row per thread), FP32
 //             stores into the output block.
-// Split modes (TF32X3 / BF16X3) load hi and lo planes; hi*hi goes into one
+// Split modes (TF32X3 / BF16X3 / F16X3) load hi and lo planes; hi*hi goes into one
 // TMEM accumulator and hi*lo + lo*hi into a second one, summed in FP32 by the
 // epilogue.  The tensor core's accumulation rounds each partial sum, so
 // keeping the large products apart from the two small cross terms cuts the
@@ -44,8 +44,11 @@ struct TcParams {
   int nprobs;
 };
 
-template <bool BF16, bool SPLIT, int BN>
+// FMT: operand format, the instruction descriptor's code (0 = FP16, 1 = BF16
+// with kind::f16; 2 = TF32 with kind::tf32); A and B always share it.
+template <int FMT, bool SPLIT, int BN>
 struct TcCfg {
+  static constexpr bool HALF = FMT != 2;
   static constexpr int A_BYTES = TC_BM * 128;
   static constexpr int B_BYTES = BN * 128;
   static constexpr int OPS = SPLIT ? 2 : 1;
@@ -61,8 +64,8 @@ struct TcCfg {
   // small cross terms in separate accumulators (ACC_W columns per buffer)
   static constexpr int ACC_W = SPLIT ? 2 * BN : BN;
   static constexpr int TMEM_COLS = (2 * ACC_W < 32) ? 32 : 2 * ACC_W;
-  static constexpr int KB = BF16 ? 64 : 32;  // K elements per stage (128 B)
-  static constexpr uint32_t IDESC = idesc_f32acc(TC_BM, BN, BF16 ? 1u : 2u);
+  static constexpr int KB = HALF ? 64 : 32;  // K elements per stage (128 B)
+  static constexpr uint32_t IDESC = idesc_f32acc(TC_BM, BN, (uint32_t)FMT);
   static_assert(STAGES >= 2, "shared memory ring too shallow");
 };
 
@@ -111,9 +114,9 @@ __device__ __forceinline__ const GemmProb* tc_decode(const TcParams& P, int64_t 
   return p;
 }
 
-template <bool BF16, bool SPLIT, int BN>
+template <int FMT, bool SPLIT, int BN>
 __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_constant__ TcParams P) {
-  using Cfg = TcCfg<BF16, SPLIT, BN>;
+  using Cfg = TcCfg<FMT, SPLIT, BN>;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + Cfg::STAGES * Cfg::STAGE_BYTES);
@@ -233,7 +236,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
             const uint64_t ad = sdesc_sw128(sa + 32 * j);
             const uint64_t bd = sdesc_sw128(sb + 32 * j);
             const uint32_t accum = (kb | j) != 0;
-            if constexpr (BF16)
+            if constexpr (Cfg::HALF)
               mma_f16(d, ad, bd, Cfg::IDESC, accum);
             else
               mma_tf32(d, ad, bd, Cfg::IDESC, accum);
@@ -242,7 +245,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
               const uint32_t sbl = sal + Cfg::A_BYTES;
               const uint64_t adl = sdesc_sw128(sal + 32 * j);
               const uint64_t bdl = sdesc_sw128(sbl + 32 * j);
-              if constexpr (BF16) {
+              if constexpr (Cfg::HALF) {
                 mma_f16(d_small, ad, bdl, Cfg::IDESC, accum);
                 mma_f16(d_small, adl, bd, Cfg::IDESC, 1);
               } else {
@@ -445,42 +448,45 @@ static PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
   return fn;
 }
 
-static bool encode_2d(CUtensorMap* m, const void* base, bool bf16, int64_t rows, int32_t kdim, int32_t ldk,
+// fmt: 0 = FP16, 1 = BF16, 2 = TF32 (FP32 words)
+static bool encode_2d(CUtensorMap* m, const void* base, int fmt, int64_t rows, int32_t kdim, int32_t ldk,
                       int box_k, int box_rows) {
   auto enc = get_encode();
   if (!enc) return false;
+  const CUtensorMapDataType ty = fmt == 0   ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
+                                 : fmt == 1 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
+                                            : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
   cuuint64_t dims[2] = {(cuuint64_t)kdim, (cuuint64_t)rows};
-  cuuint64_t strides[1] = {(cuuint64_t)ldk * (bf16 ? 2 : 4)};
+  cuuint64_t strides[1] = {(cuuint64_t)ldk * (fmt == 2 ? 4 : 2)};
   cuuint32_t box[2] = {(cuuint32_t)box_k, (cuuint32_t)box_rows};
   cuuint32_t es[2] = {1, 1};
-  CUresult r = enc(m, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
-                   const_cast<void*>(base), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+  CUresult r = enc(m, ty, 2, const_cast<void*>(base), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
                    CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS;
 }
 
 // The four maps (A hi, B hi, A lo, B lo) of fused-matrix pair pi.
-template <bool BF16, bool SPLIT, int BN>
+template <int FMT, bool SPLIT, int BN>
 static bool encode_set(const TcOperands& ops, int pi, CUtensorMap* a_hi, CUtensorMap* b_hi, CUtensorMap* a_lo,
                        CUtensorMap* b_lo) {
-  using Cfg = TcCfg<BF16, SPLIT, BN>;
-  bool ok = encode_2d(a_hi, ops.a_hi[pi], BF16, ops.a_rows[pi], ops.kdim[pi], ops.ldk[pi], Cfg::KB, TC_BM) &&
-            encode_2d(b_hi, ops.b_hi[pi], BF16, ops.b_rows[pi], ops.kdim[pi], ops.ldk[pi], Cfg::KB, BN);
+  using Cfg = TcCfg<FMT, SPLIT, BN>;
+  bool ok = encode_2d(a_hi, ops.a_hi[pi], FMT, ops.a_rows[pi], ops.kdim[pi], ops.ldk[pi], Cfg::KB, TC_BM) &&
+            encode_2d(b_hi, ops.b_hi[pi], FMT, ops.b_rows[pi], ops.kdim[pi], ops.ldk[pi], Cfg::KB, BN);
   if (SPLIT)
-    ok = ok && encode_2d(a_lo, ops.a_lo[pi], BF16, ops.a_rows[pi], ops.kdim[pi], ops.ldk[pi], Cfg::KB, TC_BM) &&
-         encode_2d(b_lo, ops.b_lo[pi], BF16, ops.b_rows[pi], ops.kdim[pi], ops.ldk[pi], Cfg::KB, BN);
+    ok = ok && encode_2d(a_lo, ops.a_lo[pi], FMT, ops.a_rows[pi], ops.kdim[pi], ops.ldk[pi], Cfg::KB, TC_BM) &&
+         encode_2d(b_lo, ops.b_lo[pi], FMT, ops.b_rows[pi], ops.kdim[pi], ops.ldk[pi], Cfg::KB, BN);
   return ok;
 }
 
-template <bool BF16, bool SPLIT, int BN>
+template <int FMT, bool SPLIT, int BN>
 static ftn_status run(ftn_ctx ctx, const TcOperands* ops, const void* gmaps, const GemmProb* d_probs, int nprobs,
                       int64_t tiles, float* c) {
-  using Cfg = TcCfg<BF16, SPLIT, BN>;
+  using Cfg = TcCfg<FMT, SPLIT, BN>;
   TcParams P;
   std::memset(&P, 0, sizeof(P));
   for (int pi = 0; ops && pi < 2; ++pi) {
     if (ops->a_rows[pi] <= 0 || ops->b_rows[pi] <= 0 || ops->kdim[pi] <= 0) continue;
-    if (!encode_set<BF16, SPLIT, BN>(*ops, pi, &P.a_hi[pi], &P.b_hi[pi], &P.a_lo[pi], &P.b_lo[pi]))
+    if (!encode_set<FMT, SPLIT, BN>(*ops, pi, &P.a_hi[pi], &P.b_hi[pi], &P.a_lo[pi], &P.b_lo[pi]))
       return set_error(FTN_ECUDA, "cuTensorMapEncodeTiled failed");
   }
   P.gmaps = reinterpret_cast<const CUtensorMap*>(gmaps);
@@ -489,11 +495,11 @@ static ftn_status run(ftn_ctx ctx, const TcOperands* ops, const void* gmaps, con
   P.err = ctx->dev_err;
   P.tiles = tiles;
   P.nprobs = nprobs;
-  static const cudaError_t attr = cudaFuncSetAttribute(tc_gemm_kernel<BF16, SPLIT, BN>,
+  static const cudaError_t attr = cudaFuncSetAttribute(tc_gemm_kernel<FMT, SPLIT, BN>,
                                                        cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM);
   if (attr != cudaSuccess) return cuda_error(attr, "cudaFuncSetAttribute(tc_gemm)");
   int64_t grid = tiles < ctx->num_sms ? tiles : ctx->num_sms;
-  tc_gemm_kernel<BF16, SPLIT, BN><<<(unsigned)grid, TC_THREADS, Cfg::SMEM, ctx->stream>>>(P);
+  tc_gemm_kernel<FMT, SPLIT, BN><<<(unsigned)grid, TC_THREADS, Cfg::SMEM, ctx->stream>>>(P);
   ctx->launches += 1;
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_error(e, "tc_gemm_kernel launch");
@@ -501,7 +507,7 @@ static ftn_status run(ftn_ctx ctx, const TcOperands* ops, const void* gmaps, con
 }
 
 int tc_pick_bn(int max_n, ftn_prec prec) {
-  const bool split = prec == FTN_PREC_TF32X3 || prec == FTN_PREC_BF16X3;
+  const bool split = prec_split(prec);
   const int cap = split ? 128 : 256;
   int bn = 16;
   while (bn < max_n && bn < cap) bn *= 2;
@@ -512,16 +518,16 @@ int64_t tc_tiles_for(int M, int N, int bn) {
   return (int64_t)((M + TC_BM - 1) / TC_BM) * ((N + bn - 1) / bn);
 }
 
-template <bool BF16, bool SPLIT>
+template <int FMT, bool SPLIT>
 static ftn_status by_bn(ftn_ctx ctx, int bn, const TcOperands* ops, const void* gm, const GemmProb* d, int np,
                         int64_t tiles, float* c) {
   switch (bn) {
-    case 16: return run<BF16, SPLIT, 16>(ctx, ops, gm, d, np, tiles, c);
-    case 32: return run<BF16, SPLIT, 32>(ctx, ops, gm, d, np, tiles, c);
-    case 64: return run<BF16, SPLIT, 64>(ctx, ops, gm, d, np, tiles, c);
-    case 128: return run<BF16, SPLIT, 128>(ctx, ops, gm, d, np, tiles, c);
+    case 16: return run<FMT, SPLIT, 16>(ctx, ops, gm, d, np, tiles, c);
+    case 32: return run<FMT, SPLIT, 32>(ctx, ops, gm, d, np, tiles, c);
+    case 64: return run<FMT, SPLIT, 64>(ctx, ops, gm, d, np, tiles, c);
+    case 128: return run<FMT, SPLIT, 128>(ctx, ops, gm, d, np, tiles, c);
     default:
-      if constexpr (!SPLIT) return run<BF16, SPLIT, 256>(ctx, ops, gm, d, np, tiles, c);
+      if constexpr (!SPLIT) return run<FMT, SPLIT, 256>(ctx, ops, gm, d, np, tiles, c);
       return set_error(FTN_EINVAL, "bad tile width");
   }
 }
@@ -530,10 +536,11 @@ static ftn_status dispatch(ftn_ctx ctx, ftn_prec prec, int bn, const TcOperands*
                            const GemmProb* d_probs, int nprobs, int64_t tiles, float* c) {
   if (nprobs == 0 || tiles == 0) return FTN_OK;
   switch (prec) {
-    case FTN_PREC_TF32: return by_bn<false, false>(ctx, bn, ops, gm, d_probs, nprobs, tiles, c);
-    case FTN_PREC_TF32X3: return by_bn<false, true>(ctx, bn, ops, gm, d_probs, nprobs, tiles, c);
-    case FTN_PREC_BF16: return by_bn<true, false>(ctx, bn, ops, gm, d_probs, nprobs, tiles, c);
-    case FTN_PREC_BF16X3: return by_bn<true, true>(ctx, bn, ops, gm, d_probs, nprobs, tiles, c);
+    case FTN_PREC_TF32: return by_bn<2, false>(ctx, bn, ops, gm, d_probs, nprobs, tiles, c);
+    case FTN_PREC_TF32X3: return by_bn<2, true>(ctx, bn, ops, gm, d_probs, nprobs, tiles, c);
+    case FTN_PREC_BF16: return by_bn<1, false>(ctx, bn, ops, gm, d_probs, nprobs, tiles, c);
+    case FTN_PREC_BF16X3: return by_bn<1, true>(ctx, bn, ops, gm, d_probs, nprobs, tiles, c);
+    case FTN_PREC_F16X3: return by_bn<0, true>(ctx, bn, ops, gm, d_probs, nprobs, tiles, c);
     default: return set_error(FTN_EUNSUPPORTED, "precision has no tensor-core path");
   }
 }
@@ -549,15 +556,15 @@ ftn_status launch_gemm_tc_maps(ftn_ctx ctx, ftn_prec prec, const TcMapSet* d_map
   return dispatch(ctx, prec, bn, nullptr, d_maps, d_probs, nprobs, tiles, c);
 }
 
-template <bool BF16, bool SPLIT>
+template <int FMT, bool SPLIT>
 static bool enc_by_bn(int bn, const TcOperands& ops, int pi, TcMapSet* out) {
   CUtensorMap* m = reinterpret_cast<CUtensorMap*>(out);
   switch (bn) {
-    case 16: return encode_set<BF16, SPLIT, 16>(ops, pi, m, m + 1, m + 2, m + 3);
-    case 32: return encode_set<BF16, SPLIT, 32>(ops, pi, m, m + 1, m + 2, m + 3);
-    case 64: return encode_set<BF16, SPLIT, 64>(ops, pi, m, m + 1, m + 2, m + 3);
-    case 128: return encode_set<BF16, SPLIT, 128>(ops, pi, m, m + 1, m + 2, m + 3);
-    case 256: return !SPLIT && encode_set<BF16, SPLIT, 256>(ops, pi, m, m + 1, m + 2, m + 3);
+    case 16: return encode_set<FMT, SPLIT, 16>(ops, pi, m, m + 1, m + 2, m + 3);
+    case 32: return encode_set<FMT, SPLIT, 32>(ops, pi, m, m + 1, m + 2, m + 3);
+    case 64: return encode_set<FMT, SPLIT, 64>(ops, pi, m, m + 1, m + 2, m + 3);
+    case 128: return encode_set<FMT, SPLIT, 128>(ops, pi, m, m + 1, m + 2, m + 3);
+    case 256: return !SPLIT && encode_set<FMT, SPLIT, 256>(ops, pi, m, m + 1, m + 2, m + 3);
     default: return false;
   }
 }
@@ -568,10 +575,11 @@ ftn_status tc_encode_set(ftn_prec prec, int bn, const TcOperands& ops, int pi, T
   if (ops.a_rows[pi] <= 0 || ops.b_rows[pi] <= 0 || ops.kdim[pi] <= 0) return FTN_OK;
   bool ok = false;
   switch (prec) {
-    case FTN_PREC_TF32: ok = enc_by_bn<false, false>(bn, ops, pi, out); break;
-    case FTN_PREC_TF32X3: ok = enc_by_bn<false, true>(bn, ops, pi, out); break;
-    case FTN_PREC_BF16: ok = enc_by_bn<true, false>(bn, ops, pi, out); break;
-    case FTN_PREC_BF16X3: ok = enc_by_bn<true, true>(bn, ops, pi, out); break;
+    case FTN_PREC_TF32: ok = enc_by_bn<2, false>(bn, ops, pi, out); break;
+    case FTN_PREC_TF32X3: ok = enc_by_bn<2, true>(bn, ops, pi, out); break;
+    case FTN_PREC_BF16: ok = enc_by_bn<1, false>(bn, ops, pi, out); break;
+    case FTN_PREC_BF16X3: ok = enc_by_bn<1, true>(bn, ops, pi, out); break;
+    case FTN_PREC_F16X3: ok = enc_by_bn<0, true>(bn, ops, pi, out); break;
     default: return set_error(FTN_EUNSUPPORTED, "precision has no tensor-core path");
   }
   return ok ? FTN_OK : set_error(FTN_ECUDA, "cuTensorMapEncodeTiled failed");

@@ -19,6 +19,7 @@
 // destination is also contiguous there.  Every thread keeps PERM_TO / 8 loads
 // in flight so that enough bytes are outstanding per SM to cover HBM latency.
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include "common.h"
 #include "ptx.cuh"
@@ -43,6 +44,10 @@ __device__ __forceinline__ void put(void* dst0, void* dst1, int64_t idx, Tin v) 
     reinterpret_cast<float*>(dst1)[idx] = tf32_rna((float)v - hi);
   } else if constexpr (MODE == PERM_BF16) {
     reinterpret_cast<__nv_bfloat16*>(dst0)[idx] = __float2bfloat16_rn((float)v);
+  } else if constexpr (MODE == PERM_F16X2) {
+    const __half hi = __float2half_rn((float)v);
+    reinterpret_cast<__half*>(dst0)[idx] = hi;
+    reinterpret_cast<__half*>(dst1)[idx] = __float2half_rn((float)v - __half2float(hi));
   } else {
     __nv_bfloat16 hi = __float2bfloat16_rn((float)v);
     reinterpret_cast<__nv_bfloat16*>(dst0)[idx] = hi;
@@ -69,6 +74,17 @@ __device__ __forceinline__ void put4(void* dst0, void* dst1, int64_t idx, Tin a,
     *reinterpret_cast<float4*>(reinterpret_cast<float*>(dst0) + idx) = make_float4(ha, hb, hc, hd);
     *reinterpret_cast<float4*>(reinterpret_cast<float*>(dst1) + idx) =
         make_float4(tf32_rna(a - ha), tf32_rna(b - hb), tf32_rna(c - hc), tf32_rna(d - hd));
+  } else if constexpr (MODE == PERM_F16X2) {
+    const __half2 h01 = __floats2half2_rn(a, b), h23 = __floats2half2_rn(c, d);
+    const float2 f01 = __half22float2(h01), f23 = __half22float2(h23);
+    const __half2 l01 = __floats2half2_rn(a - f01.x, b - f01.y), l23 = __floats2half2_rn(c - f23.x, d - f23.y);
+    uint2 hv, lv;
+    hv.x = *reinterpret_cast<const uint32_t*>(&h01);
+    hv.y = *reinterpret_cast<const uint32_t*>(&h23);
+    lv.x = *reinterpret_cast<const uint32_t*>(&l01);
+    lv.y = *reinterpret_cast<const uint32_t*>(&l23);
+    *reinterpret_cast<uint2*>(reinterpret_cast<__half*>(dst0) + idx) = hv;
+    *reinterpret_cast<uint2*>(reinterpret_cast<__half*>(dst1) + idx) = lv;
   } else {
     const __nv_bfloat162 h01 = __floats2bfloat162_rn(a, b), h23 = __floats2bfloat162_rn(c, d);
     uint2 hv;
@@ -559,6 +575,7 @@ ftn_status launch_permute(ftn_ctx ctx, const PermJob* d_jobs, int njobs, int64_t
       case PERM_TF32X2: e = pick<float, PERM_TF32X2>(ctx, staged, d_jobs, njobs, tiles, src, dst0, dst1); break;
       case PERM_BF16: e = pick<float, PERM_BF16>(ctx, staged, d_jobs, njobs, tiles, src, dst0, dst1); break;
       case PERM_BF16X2: e = pick<float, PERM_BF16X2>(ctx, staged, d_jobs, njobs, tiles, src, dst0, dst1); break;
+      case PERM_F16X2: e = pick<float, PERM_F16X2>(ctx, staged, d_jobs, njobs, tiles, src, dst0, dst1); break;
       default: return set_error(FTN_EINVAL, "bad permute mode");
     }
   }

@@ -493,7 +493,7 @@ ftn_status tensordot_impl(ftn_ctx ctx, ftn_tensor A, ftn_tensor B, int n, const 
   if (A->dtype != B->dtype) return set_error(FTN_EINVAL, "A and B must have the same dtype");
   if ((prec == FTN_PREC_F64) != (A->dtype == FTN_F64))
     return set_error(FTN_EUNSUPPORTED, "FTN_PREC_F64 needs FP64 tensors; tensor-core precisions need FP32 tensors");
-  if (prec < FTN_PREC_F64 || prec > FTN_PREC_BF16X3) return set_error(FTN_EINVAL, "bad precision");
+  if (!prec_valid(prec)) return set_error(FTN_EINVAL, "bad precision");
   FTN_TRY(validate_pairs(A, B, n, ax, ay));
   const int cr = A->rank + B->rank - 2 * n;
   if (out_perm) {
@@ -516,8 +516,8 @@ ftn_status tensordot_impl(ftn_ctx ctx, ftn_tensor A, ftn_tensor B, int n, const 
   }
   // workspace: A_f (hi, lo), B_f (hi, lo), pre-permutation result
   const bool tc = prec != FTN_PREC_F64;
-  const bool split = prec == FTN_PREC_TF32X3 || prec == FTN_PREC_BF16X3;
-  const bool bf16 = prec == FTN_PREC_BF16 || prec == FTN_PREC_BF16X3;
+  const bool split = prec_split(prec);
+  const bool bf16 = prec_half(prec);  // 16-bit operands
   const size_t es = tc ? (bf16 ? 2 : 4) : 8;
   auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
   const size_t a_b = al((size_t)P->af_elems * es), b_b = al((size_t)P->bf_elems * es);
@@ -535,11 +535,7 @@ ftn_status tensordot_impl(ftn_ctx ctx, ftn_tensor A, ftn_tensor B, int n, const 
   uint8_t* bf_lo = split ? bf_hi + b_b : nullptr;
   // the GEMM epilogue writes the final layout, or the plain one into workspace
   uint8_t* ctmp = P->fused ? (uint8_t*)out->data : bf_hi + b_b * (split ? 2 : 1);
-  int mode = PERM_SAME;
-  if (prec == FTN_PREC_TF32) mode = PERM_TF32;
-  if (prec == FTN_PREC_TF32X3) mode = PERM_TF32X2;
-  if (prec == FTN_PREC_BF16) mode = PERM_BF16;
-  if (prec == FTN_PREC_BF16X3) mode = PERM_BF16X2;
+  const int mode = prec_perm_mode(prec);
   const double in_es = (double)dtype_size(A->dtype), planes = split ? 2.0 : 1.0;
   double gemm_flops = 0;
   for (const GemmProb& g : P->probs) gemm_flops += 2.0 * g.M * g.N * g.K;

@@ -358,8 +358,8 @@ ftn_status get_grad_plan(ftn_ctx ctx, const ftn_tensor_s* A, const ftn_tensor_s*
 ftn_status run_grad(ftn_ctx ctx, const GradPlan& P, const ftn_tensor_s* G, const ftn_tensor_s* Y, ftn_prec prec,
                     ftn_tensor dX) {
   const bool tc = prec != FTN_PREC_F64;
-  const bool split = prec == FTN_PREC_TF32X3 || prec == FTN_PREC_BF16X3;
-  const bool bf16 = prec == FTN_PREC_BF16 || prec == FTN_PREC_BF16X3;
+  const bool split = prec_split(prec);
+  const bool bf16 = prec_half(prec);  // 16-bit operands
   const size_t es = tc ? (bf16 ? 2 : 4) : 8;
   auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
   const size_t g_b = al((size_t)P.g_elems * es), y_b = al((size_t)P.y_elems * es);
@@ -372,11 +372,7 @@ ftn_status run_grad(ftn_ctx ctx, const GradPlan& P, const ftn_tensor_s* G, const
   uint8_t* g_lo = split ? ws + g_b : nullptr;
   uint8_t* y_hi = ws + g_b * planes;
   uint8_t* y_lo = split ? y_hi + y_b : nullptr;
-  int mode = PERM_SAME;
-  if (prec == FTN_PREC_TF32) mode = PERM_TF32;
-  if (prec == FTN_PREC_TF32X3) mode = PERM_TF32X2;
-  if (prec == FTN_PREC_BF16) mode = PERM_BF16;
-  if (prec == FTN_PREC_BF16X3) mode = PERM_BF16X2;
+  const int mode = prec_perm_mode(prec);
   int rec = prof_begin(ctx, "permute", (double)G->numel * (dtype_size(G->dtype) + es * planes), 0);
   FTN_TRY(launch_permute(ctx, P.d_jg, (int)P.jg.size(), P.tg, P.sg, G->data, g_hi, g_lo, G->dtype, mode));
   FTN_TRY(launch_permute(ctx, P.d_jy, (int)P.jy.size(), P.ty, P.sy, Y->data, y_hi, y_lo, Y->dtype, mode));
@@ -432,7 +428,7 @@ ftn_status tensordot_grad_impl(ftn_ctx ctx, ftn_tensor A, ftn_tensor B, ftn_tens
   if (A->dtype != B->dtype || G->dtype != A->dtype) return set_error(FTN_EINVAL, "A, B and G must have one dtype");
   if ((prec == FTN_PREC_F64) != (A->dtype == FTN_F64))
     return set_error(FTN_EUNSUPPORTED, "FTN_PREC_F64 needs FP64 tensors; tensor-core precisions need FP32 tensors");
-  if (prec < FTN_PREC_F64 || prec > FTN_PREC_BF16X3) return set_error(FTN_EINVAL, "bad precision");
+  if (!prec_valid(prec)) return set_error(FTN_EINVAL, "bad precision");
   FTN_TRY(validate_pairs(A, B, n, ax, ay));
   const int cr = A->rank + B->rank - 2 * n;
   if (out_perm) {

@@ -19,8 +19,9 @@ LIB_PATH = os.path.join(_HERE, "_build", "libftn.so")
 
 FTN_MAX_RANK = 16
 F64, F32 = 0, 1
-PREC_F64, PREC_TF32, PREC_BF16, PREC_TF32X3, PREC_BF16X3 = 0, 1, 2, 3, 4
-PREC_NAMES = {"f64": PREC_F64, "tf32": PREC_TF32, "bf16": PREC_BF16, "tf32x3": PREC_TF32X3, "bf16x3": PREC_BF16X3}
+PREC_F64, PREC_TF32, PREC_BF16, PREC_TF32X3, PREC_BF16X3, PREC_F16X3 = 0, 1, 2, 3, 4, 5
+PREC_NAMES = {"f64": PREC_F64, "tf32": PREC_TF32, "bf16": PREC_BF16, "tf32x3": PREC_TF32X3, "bf16x3": PREC_BF16X3,
+              "f16x3": PREC_F16X3}
 POLICY_EXACT, POLICY_EARLY, POLICY_LATE = 0, 1, 2
 POLICY_NAMES = {"exact": POLICY_EXACT, "early": POLICY_EARLY, "late": POLICY_LATE}
 STATUS = {0: "FTN_OK", -1: "FTN_EINVAL", -2: "FTN_ESHAPE", -3: "FTN_EPARITY", -4: "FTN_EDUAL", -5: "FTN_ENOMEM",
@@ -161,6 +162,12 @@ class Context:
 
     def synchronize(self):
         _check(lib().ftn_ctx_synchronize(self.handle))
+
+    def set_stream(self, stream):
+        """Launch on another torch CUDA stream from now on (ftn_ctx_set_stream),
+        e.g. a stream under CUDA-graph capture."""
+        _check(lib().ftn_ctx_set_stream(self.handle, C.c_void_p(stream.cuda_stream)))
+        self.stream = stream
 
     def launches(self):
         return int(lib().ftn_ctx_launch_count(self.handle))

@@ -3,7 +3,7 @@ of a batch gives exactly (bit for bit) what it gives alone through
 ftn_contract -- the batch merges job tables but keeps each network's plans,
 tiles and reduction orders -- and the batched energies agree with the
 oracle.  Covered: cluster networks of random 3-regular graphs (globally
-ordered) in FP64 and TF32x3, exact and late policies (the batched
+ordered) in FP64, TF32x3 and F16X3, exact and late policies (the batched
 compression stages), intermediates above the one-CTA normalisation size,
 locally and globally ordered networks with different trees, policies and chi
 in one batch, and the error paths."""
@@ -81,7 +81,7 @@ def singles(F, ctx, nets, prec):
                        policy=j.get("policy", "exact"), chi=j.get("chi", 0), prec=prec) for j in nets]
 
 
-@pytest.mark.parametrize("prec", ["f64", "tf32x3"])
+@pytest.mark.parametrize("prec", ["f64", "tf32x3", "f16x3"])
 @pytest.mark.parametrize("policy,chi", [("exact", 0), ("late", 4)])
 def test_batch_equals_single_cluster_networks(F, ctx, prec, policy, chi):
     dt = F.F64 if prec == "f64" else F.F32
@@ -92,7 +92,7 @@ def test_batch_equals_single_cluster_networks(F, ctx, prec, policy, chi):
     assert F.contract_batch(ctx, nets[:7], prec=prec) + F.contract_batch(ctx, nets[7:], prec=prec) == ref
 
 
-@pytest.mark.parametrize("prec", ["f64", "tf32x3"])
+@pytest.mark.parametrize("prec", ["f64", "tf32x3", "f16x3"])
 def test_batch_large_intermediates_and_compression(F, ctx, prec):
     """D = 6 (4+2) bonds, late compression to chi = 32: merged-site
     intermediates of ~10^6 entries (the multi-CTA normalisation), batched

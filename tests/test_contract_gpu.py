@@ -47,7 +47,7 @@ def gpu_kets(F, ctx, lay, blocks, dt):
     return [F.Tensor.from_blocks(ctx, lay["legs"][s], 0, blocks[s], dt) for s in range(lay["n"])]
 
 
-@pytest.mark.parametrize("prec", ["f64", "tf32x3"])
+@pytest.mark.parametrize("prec", ["f64", "tf32x3", "f16x3"])
 def test_norm_2x2_orders_and_formalisms(F, ctx, prec):
     from paper_2410_02215_gb300 import peps
 
@@ -127,8 +127,8 @@ def test_approximate_energy_3x3_matches_oracle(F, ctx):
 def test_energy_4x4_compressed_fp64_and_mixed(F, ctx):
     """The energy workload of the benchmark (4x4 square lattice, D = 4 as 2+2,
     chi = 32, late compression): FP64 GPU vs the oracle (1e-9), and the
-    mixed path (FP32 tensors, TF32x3 sector GEMMs, FP64 compression) vs the
-    FP64 GPU path (1e-6)."""
+    mixed paths (FP32 tensors, TF32x3 or F16X3 sector GEMMs, FP64
+    compression) vs the FP64 GPU path (1e-6)."""
     from paper_2410_02215_gb300 import peps
 
     n, edges, lay, blocks = setup(4, 4, (2, 2), 1)
@@ -139,8 +139,9 @@ def test_energy_4x4_compressed_fp64_and_mixed(F, ctx):
     e64, _, _ = peps.energy(ctx, lay, k64, 1.0, 8.0, tf, policy="late", chi=32)
     assert abs(e64 - e_ref) <= 1e-9 * abs(e_ref)
     k32 = gpu_kets(F, ctx, lay, blocks, F.F32)
-    e32, _, _ = peps.energy(ctx, lay, k32, 1.0, 8.0, tf, policy="late", chi=32, prec="tf32x3")
-    assert abs(e32 - e64) <= 1e-6 * abs(e64)
+    for prec in ("tf32x3", "f16x3"):
+        e32, _, _ = peps.energy(ctx, lay, k32, 1.0, 8.0, tf, policy="late", chi=32, prec=prec)
+        assert abs(e32 - e64) <= 1e-6 * abs(e64), prec
 
 
 def test_energy_concurrent_streams_match_sequential(F, ctx):

@@ -13,7 +13,7 @@ import workloads as W
 
 pytestmark = pytest.mark.gpu
 
-TOL = {"f64": 1e-10, "tf32x3": 1e-5, "bf16x3": 5e-5, "tf32": 5e-3, "bf16": 5e-2}
+TOL = {"f64": 1e-10, "tf32x3": 1e-5, "f16x3": 1e-5, "bf16x3": 5e-5, "tf32": 5e-3, "bf16": 5e-2}
 
 
 @pytest.fixture(scope="module")
@@ -109,7 +109,7 @@ def random_pair_case(seed):
     return la, lb, ax, ay, pa, pb, perm, flip_a, flip_b
 
 
-@pytest.mark.parametrize("prec", ["f64", "tf32x3", "bf16x3", "tf32", "bf16"])
+@pytest.mark.parametrize("prec", ["f64", "tf32x3", "f16x3", "bf16x3", "tf32", "bf16"])
 def test_tensordot_random_small(F, ctx, prec):
     """Random ranks, sector sizes (incl. empty sectors), parities, arrows,
     extra bond parities and output permutations."""
@@ -130,7 +130,7 @@ def test_tensordot_random_small(F, ctx, prec):
 
 
 @pytest.mark.parametrize("name", ["T1", "T2", "T3", "T4"])
-@pytest.mark.parametrize("prec", ["f64", "tf32x3", "bf16x3", "tf32"])
+@pytest.mark.parametrize("prec", ["f64", "tf32x3", "f16x3", "bf16x3", "tf32"])
 def test_tensordot_cases_reduced(F, ctx, name, prec):
     """The four microbenchmark contractions with every sector dimension halved:
     full element-wise comparison (several tiles and ragged tails)."""
@@ -158,7 +158,7 @@ def read_entries(t, flat, indices):
 
 
 @pytest.mark.parametrize("name", ["T1", "T2", "T3", "T4"])
-@pytest.mark.parametrize("prec", ["f64", "tf32x3"])
+@pytest.mark.parametrize("prec", ["f64", "tf32x3", "f16x3"])
 def test_tensordot_cases_full_size_sampled(F, ctx, name, prec):
     """Full-size microbenchmark shapes, in the launch configuration the
     benchmark times (same permutations), on 400 sampled output entries."""
@@ -171,6 +171,23 @@ def test_tensordot_cases_full_size_sampled(F, ctx, name, prec):
     c = F.tensordot(ctx, a, b, case["axes_a"], case["axes_b"], out_perm=case["out_perm"], prec=prec)
     got = read_entries(c, c.download(), idx)
     assert relerr(got, ref) <= TOL[prec]
+    ctx.synchronize()
+
+
+@pytest.mark.parametrize("scale", [0.125, 1.0, 3000.0])
+def test_f16x3_within_its_range(F, ctx, scale):
+    """F16X3 keeps the FP32-level normwise accuracy while the largest operand
+    entry lies in its stated range (here N(0,1) data times scale, so the
+    largest entries are about 4 * scale)."""
+    case = W.tensordot_case("T3", seed=3, shrink=2)
+    ba = [(bits, blk * scale) for bits, blk in W.random_blocks(case["legs_a"], 0, case["seed_a"])]
+    bb = [(bits, blk * scale) for bits, blk in W.random_blocks(case["legs_b"], 0, case["seed_b"])]
+    ref = O.transpose(O.contract(dense(ba, case["legs_a"], 0), dense(bb, case["legs_b"], 0), case["axes_a"],
+                                 case["axes_b"]), case["out_perm"])
+    a, b = upload(F, ctx, case["legs_a"], 0, ba, "f16x3"), upload(F, ctx, case["legs_b"], 0, bb, "f16x3")
+    c = F.tensordot(ctx, a, b, case["axes_a"], case["axes_b"], out_perm=case["out_perm"], prec="f16x3")
+    got = dense(c.to_blocks(), c.legs, c.parity)
+    assert relerr(got.data, ref.data) <= TOL["f16x3"]
     ctx.synchronize()
 
 

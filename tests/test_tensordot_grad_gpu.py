@@ -10,7 +10,7 @@ import workloads as W
 
 pytestmark = pytest.mark.gpu
 
-TOL = {"f64": 1e-10, "tf32x3": 1e-5}
+TOL = {"f64": 1e-10, "tf32x3": 1e-5, "f16x3": 1e-5}
 
 
 @pytest.fixture(scope="module")
@@ -61,7 +61,7 @@ def small_case(seed):
     return la, lb, ax, ay, pa, pb, perm, fa, fb
 
 
-@pytest.mark.parametrize("prec", ["f64", "tf32x3"])
+@pytest.mark.parametrize("prec", ["f64", "tf32x3", "f16x3"])
 def test_grad_matches_oracle_by_definition(F, ctx, prec):
     dt = F.F64 if prec == "f64" else F.F32
     for seed in range(24):
@@ -137,12 +137,13 @@ def test_grad_rejects_wrong_result_legs(F, ctx):
         F.tensordot_grad(ctx, a, b, g, [1], [0])
 
 
+@pytest.mark.parametrize("prec", ["tf32x3", "f16x3"])
 @pytest.mark.parametrize("name", ["T1", "T2"])
-def test_long_contraction_gradient_full_size(F, ctx, name):
+def test_long_contraction_gradient_full_size(F, ctx, name, prec):
     """dB of T1 / T2 contracts over every free state of the environment
     (131072 / 16384 per sector): the tensor-core gradient runs it as K parts
     accumulated in FP32 and added in FP64.  TF32x3 vs FP64 gradients of the
-    same FP32-rounded inputs, normwise 1e-5."""
+    same FP32-rounded inputs, normwise 1e-5 (TF32x3 and F16X3)."""
     c = W.tensordot_case(name, seed=0)
     rnd = lambda legs, par, seed: [(k, v.astype(np.float32).astype(np.float64))  # noqa: E731
                                    for k, v in W.random_blocks(legs, par, seed)]
@@ -156,6 +157,6 @@ def test_long_contraction_gradient_full_size(F, ctx, name):
     a32 = F.Tensor.from_blocks(ctx, c["legs_a"], 0, ba, F.F32)
     b32 = F.Tensor.from_blocks(ctx, c["legs_b"], 0, bb, F.F32)
     g32 = F.Tensor.from_blocks(ctx, r.legs, r.parity, bg, F.F32)
-    got = F.tensordot_grad(ctx, a32, b32, g32, c["axes_a"], c["axes_b"], out_perm=c["out_perm"], prec="tf32x3")
+    got = F.tensordot_grad(ctx, a32, b32, g32, c["axes_a"], c["axes_b"], out_perm=c["out_perm"], prec=prec)
     for x, y in zip(got, ref):
-        assert relerr(x.download().astype(np.float64), y.download()) <= TOL["tf32x3"]
+        assert relerr(x.download().astype(np.float64), y.download()) <= TOL[prec]
