@@ -475,9 +475,11 @@ def accuracy(F, ctx, prec):
     return {"rel_err_inf": worst_inf, "rel_err_2": worst_2}
 
 
-def traffic_for(label):
+def traffic_for(label, prec):
     """DRAM bytes per launch from a committed ncu summary (profiles/traffic.txt),
-    when it was taken on the current kernel sources (else None)."""
+    when it was taken on the current kernel sources in this precision (else
+    None)."""
+    label = f"{label}@{prec}"
     p = os.path.join(ROOT, "profiles", "traffic.txt")
     if not os.path.exists(p):
         return None
@@ -527,7 +529,7 @@ def roofline(prof, peaks, prec="tf32x3"):
                     "frac": ach / peaks["hbm_gbs"], "peak_note": f"{peaks['src']} HBM copy bandwidth"})
     out["algorithmic_bytes_per_launch"] = bytes_per
     out["algorithmic_flops_per_launch"] = flops_per
-    out["traffic"] = traffic_for(label)
+    out["traffic"] = traffic_for(label, prec)
     return out
 
 

@@ -150,7 +150,8 @@ FTN_API ftn_status ftn_tensor_download(ftn_ctx ctx, ftn_tensor t, void* host);
 /* Fermionic transposition: out leg u = in leg perm[u]; every block is moved
  * and multiplied by (-1)^{sum of p_a p_b over leg pairs whose order the
  * permutation inverts}.  *out is created (same dtype) unless it is non-NULL
- * on entry, in which case it must already have the permuted metadata. */
+ * on entry, in which case it must already have the permuted metadata and
+ * 16-byte aligned data (else FTN_EINVAL). */
 FTN_API ftn_status ftn_tensor_transpose(ftn_ctx ctx, ftn_tensor t, const int* perm, ftn_tensor* out);
 /* Hermitian conjugate of one tensor (Sec. II.C): leg order reversed, duals
  * flipped, no sign (real data). */
@@ -164,7 +165,8 @@ FTN_API ftn_status ftn_tensor_dagger(ftn_ctx ctx, ftn_tensor t, ftn_tensor* out)
  * move accumulates, Sec. II.C).  If out_perm is not NULL the result is
  * fermionically transposed to out leg u = result leg out_perm[u].  A and B
  * must have the same dtype; prec selects the GEMM arithmetic.  *C is created
- * unless non-NULL on entry (then it must match the result's metadata).
+ * unless non-NULL on entry (then it must match the result's metadata and its
+ * data must be 16-byte aligned, else FTN_EINVAL).
  * n = 0 gives the outer product. */
 FTN_API ftn_status ftn_tensordot(ftn_ctx ctx, ftn_tensor A, ftn_tensor B, int n, const int* axes_a,
                          const int* axes_b, uint64_t flip_a, uint64_t flip_b, const int* out_perm,
@@ -176,7 +178,8 @@ FTN_API ftn_status ftn_tensordot(ftn_ctx ctx, ftn_tensor A, ftn_tensor B, int n,
  * flip_a, flip_b, out_perm): G holds dL/dC and must have exactly C's metadata
  * (legs after out_perm, parity p_A + p_B) and A's dtype.  dA (if dA is not
  * NULL) gets A's metadata and dL/dA, dB (if not NULL) B's and dL/dB; each is
- * created unless non-NULL on entry (then its metadata must match).  Every
+ * created unless non-NULL on entry (then its metadata must match and its
+ * data be 16-byte aligned).  Every
  * block pair of the forward product carries one sign (transposition of the
  * operands into the contraction order with the arrow and extra bond
  * parities, and of the result into out_perm); the adjoint applies the same

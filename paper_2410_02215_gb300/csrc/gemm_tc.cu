@@ -282,6 +282,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
     const int set = (warp - 2) >> 2;
     float* stg = epi + (warp - 2) * 32 * (Cfg::CW + 1);
     uint32_t j = 0;  // tiles with K > 0 seen so far (all sets count them)
+    const bool c16 = ((uintptr_t)P.C & 15) == 0;  // 16-byte vector stores need an aligned base
     int cur = -1;
     for (int64_t t = blockIdx.x; t < P.tiles; t += gridDim.x) {
       int m0, n0;
@@ -324,7 +325,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
             rp_c[ch] = rpl;
             cp_c[ch] = lane < Cfg::CW && lane < cn ? expand_index32(lcol + lane, mp->ncl, mp->cdim, mp->cstr) : 0;
             sg_c[ch] = (float)mp->c_sign;
-            fl_c[ch] = (mp->vec4 ? 1 : 0) | (mp->epi_rows ? 2 : 0);
+            fl_c[ch] = (mp->vec4 && c16 ? 1 : 0) | (mp->epi_rows ? 2 : 0);
           }
         }
       }
@@ -362,11 +363,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
 #pragma unroll
           for (int jj = 0; jj < Cfg::CW; ++jj) v[jj] = 0.0f;
         }
+        const int64_t cpart = cp_c[ch];
 #pragma unroll
         for (int jj = 0; jj < Cfg::CW; ++jj) stg[lane * (Cfg::CW + 1) + jj] = v[jj];
         __syncwarp();
         const bool okc = lane < Cfg::CW && lane < cn;
-        const int64_t cpart = cp_c[ch];
         if (fl_c[ch] & 1) {
           // 16-byte stores: quads of consecutive elements along the contiguous direction
           const int sub = lane & 7, grp = lane >> 3;

@@ -510,6 +510,8 @@ ftn_status tensordot_impl(ftn_ctx ctx, ftn_tensor A, ftn_tensor B, int n, const 
   if (out) {
     if (!same_meta(out, cr, P->cd0, P->cd1, P->cdual, P->cpar, A->dtype))
       return set_error(FTN_EINVAL, "preallocated output has the wrong metadata");
+    if ((uintptr_t)out->data & 15)  // the epilogues store 16-byte vectors
+      return set_error(FTN_EINVAL, "preallocated output must be 16-byte aligned");
   } else {
     FTN_TRY(make_tensor(ctx, cr, P->cd0, P->cd1, P->cdual, P->cpar, A->dtype, &out));
     created = true;
@@ -631,6 +633,8 @@ ftn_status permute_impl(ftn_ctx ctx, ftn_tensor t, const int* perm, bool fermion
   if (o) {
     if (!same_meta(o, r, d0, d1, du, t->parity, t->dtype))
       return set_error(FTN_EINVAL, "preallocated output has the wrong metadata");
+    if ((uintptr_t)o->data & 15)  // the permute stores 16-byte vectors
+      return set_error(FTN_EINVAL, "preallocated output must be 16-byte aligned");
   } else {
     FTN_TRY(make_tensor(ctx, r, d0, d1, du, t->parity, t->dtype, &o));
     created = true;

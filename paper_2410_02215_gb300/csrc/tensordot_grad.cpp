@@ -448,6 +448,8 @@ ftn_status tensordot_grad_impl(ftn_ctx ctx, ftn_tensor A, ftn_tensor B, ftn_tens
     if (out) {
       if (!same_meta(out, P->xrank, P->xd0, P->xd1, P->xdu, P->xpar, A->dtype))
         return set_error(FTN_EINVAL, "preallocated gradient has the wrong metadata");
+      if ((uintptr_t)out->data & 15)  // the epilogues store 16-byte vectors
+        return set_error(FTN_EINVAL, "preallocated gradient must be 16-byte aligned");
     } else {
       FTN_TRY(make_tensor(ctx, P->xrank, P->xd0, P->xd1, P->xdu, P->xpar, A->dtype, &out));
       created = true;

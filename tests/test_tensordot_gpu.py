@@ -232,6 +232,30 @@ def test_misaligned_wrapped_input_uses_fallback_permute(F, ctx):
     ctx.synchronize()
 
 
+def test_misaligned_preallocated_output_is_rejected(F, ctx):
+    """The epilogues and the permute write 16-byte vectors, so a caller's
+    preallocated output must be 16-byte aligned: a misaligned one is refused
+    before any launch, and an aligned one is accepted."""
+    import torch
+
+    case = W.tensordot_case("T3", seed=1, shrink=2)
+    a = upload(F, ctx, case["legs_a"], 0, W.random_blocks(case["legs_a"], 0, 1), "tf32x3")
+    b = upload(F, ctx, case["legs_b"], 0, W.random_blocks(case["legs_b"], 0, 2), "tf32x3")
+    c = F.tensordot(ctx, a, b, case["axes_a"], case["axes_b"], out_perm=case["out_perm"], prec="tf32x3")
+    store = torch.empty(c.numel + 4, dtype=torch.float32, device="cuda")
+    bad = F.Tensor.wrap(ctx, c.legs, c.parity, store[1:1 + c.numel])
+    assert bad.ptr % 16 != 0
+    with pytest.raises(F.FtnError) as e:
+        F.tensordot(ctx, a, b, case["axes_a"], case["axes_b"], out_perm=case["out_perm"], prec="tf32x3", out=bad)
+    assert e.value.status == -1  # FTN_EINVAL
+    with pytest.raises(F.FtnError):
+        F.transpose(ctx, c, list(range(len(c.legs))), out=bad)
+    good = F.Tensor.wrap(ctx, c.legs, c.parity, store[4:4 + c.numel])
+    F.tensordot(ctx, a, b, case["axes_a"], case["axes_b"], out_perm=case["out_perm"], prec="tf32x3", out=good)
+    assert np.array_equal(good.download(), c.download())
+    ctx.synchronize()
+
+
 NARROW = [
     # (A legs, B legs, axes A, axes B, out_perm): long contracted legs, few
     # output tiles (split-K with the ordered slab reduction) and narrow
