@@ -56,6 +56,7 @@ struct PermJob {
   int32_t wmask;         // I legs (bit l = l-th I leg) forming the destination's contiguous run
   int32_t qw;            // elements of that run (product of the wmask legs)
   int32_t wsuf;          // the run is the innermost I legs in the same order: source columns run with it
+  int32_t src_sel;       // source buffer: 0 = src, 1 = src1 (both operands of a contraction in one launch)
   int32_t dim[MAXR];     // I legs (source order), then O legs, then B legs
   int64_t sstr[MAXR];    // source strides
   int64_t dstr[MAXR];    // destination strides
@@ -259,6 +260,9 @@ void add_perm_job(std::vector<PermJob>& jobs, int64_t& tiles, int rank, const in
 int finalize_perm_jobs(std::vector<PermJob>& jobs, size_t elem_size, int64_t* tiles, bool allow_staged);
 ftn_status launch_permute(ftn_ctx ctx, const PermJob* d_jobs, int njobs, int64_t tiles, int staged, const void* src,
                           void* dst0, void* dst1, ftn_dtype in_type, int mode);
+// The same with a second source buffer for the jobs with src_sel = 1.
+ftn_status launch_permute2(ftn_ctx ctx, const PermJob* d_jobs, int njobs, int64_t tiles, int staged, const void* src,
+                           const void* src1, void* dst0, void* dst1, ftn_dtype in_type, int mode);
 // FP64 tiles are 64 x bn, bn in {16, 32, 64} (f64_pick_bn of the widest
 // problem); the problems' tiles_n must be counted with the same bn.
 ftn_status launch_gemm_f64(ftn_ctx ctx, const GemmProb* d_probs, int nprobs, int64_t tiles, const double* a,

@@ -106,8 +106,8 @@ constexpr int PR = PERM_TO / (PT / 32);  // rows per thread in a phase
 
 template <typename Tin, int MODE>
 __global__ void __launch_bounds__(PT) perm_kernel(const PermJob* __restrict__ jobs, int njobs, int64_t tiles,
-                                                  const Tin* __restrict__ src, void* __restrict__ dst0,
-                                                  void* __restrict__ dst1) {
+                                                  const Tin* __restrict__ src0, const Tin* __restrict__ src1,
+                                                  void* __restrict__ dst0, void* __restrict__ dst1) {
   __shared__ Tin tile[PERM_TO][PERM_TI + 1];
   __shared__ int32_t rowS[PERM_TO];
   __shared__ int32_t rowD[PERM_TO];
@@ -130,6 +130,7 @@ __global__ void __launch_bounds__(PT) perm_kernel(const PermJob* __restrict__ jo
     }
     __syncthreads();
     const PermJob* j = jobs + s_job;
+    const Tin* __restrict__ src = j->src_sel ? src1 : src0;
     const int nI = j->nI, nO = j->nO;
     const int PI = j->PI, PO = j->PO;
     const int64_t local = t - j->tile_begin;
@@ -358,8 +359,8 @@ constexpr int SPT = 32 * (SPW + SPP);
 
 template <typename Tin, int MODE>
 __global__ void __launch_bounds__(SPT) perm_staged_kernel(const PermJob* __restrict__ jobs, int njobs, int64_t tiles,
-                                                          const Tin* __restrict__ src, void* __restrict__ dst0,
-                                                          void* __restrict__ dst1, int* err) {
+                                                          const Tin* __restrict__ src, const Tin* __restrict__ src1,
+                                                          void* __restrict__ dst0, void* __restrict__ dst1, int* err) {
   using Cfg = StagedCfg<Tin>;
   extern __shared__ uint8_t sm_raw[];
   uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(sm_raw) + 127) & ~uintptr_t(127));
@@ -426,7 +427,7 @@ __global__ void __launch_bounds__(SPT) perm_staged_kernel(const PermJob* __restr
         failed = true;
         break;
       }
-      staged_issue<Tin>(sjob, t, src, buf + s * Cfg::STAGE_ELEMS, rowD + s * PERM_MAX_ROWS, colD + s * Cfg::MAXTI,
+      staged_issue<Tin>(sjob, t, sjob->src_sel ? src1 : src, buf + s * Cfg::STAGE_ELEMS, rowD + s * PERM_MAX_ROWS, colD + s * Cfg::MAXTI,
                         colS + s * Cfg::MAXTI, colP + s * Cfg::MAXTI, meta + s, &full[s], lane);
     }
     // after an early exit, wait for this producer's copies still in flight (on
@@ -530,7 +531,7 @@ __global__ void __launch_bounds__(SPT) perm_staged_kernel(const PermJob* __restr
 
 template <typename Tin, int MODE>
 static cudaError_t go_staged(ftn_ctx ctx, const PermJob* d_jobs, int njobs, int64_t tiles, const void* src,
-                             void* dst0, void* dst1) {
+                             const void* src1, void* dst0, void* dst1) {
   using Cfg = StagedCfg<Tin>;
   static const cudaError_t attr =
       cudaFuncSetAttribute(perm_staged_kernel<Tin, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::BYTES);
@@ -539,49 +540,56 @@ static cudaError_t go_staged(ftn_ctx ctx, const PermJob* d_jobs, int njobs, int6
   int64_t cap = (int64_t)ctx->num_sms * 3;
   if (grid > cap) grid = cap;
   perm_staged_kernel<Tin, MODE><<<(unsigned)grid, SPT, Cfg::BYTES, ctx->stream>>>(d_jobs, njobs, tiles,
-                                                                                 (const Tin*)src, dst0, dst1,
+                                                                                 (const Tin*)src, (const Tin*)src1,
+                                                                                 dst0, dst1,
                                                                                  ctx->dev_err);
   return cudaGetLastError();
 }
 
 template <typename Tin, int MODE>
-static cudaError_t go(ftn_ctx ctx, const PermJob* d_jobs, int njobs, int64_t tiles, const void* src, void* dst0,
-                      void* dst1) {
+static cudaError_t go(ftn_ctx ctx, const PermJob* d_jobs, int njobs, int64_t tiles, const void* src,
+                      const void* src1, void* dst0, void* dst1) {
   int64_t grid = tiles;
   int64_t cap = (int64_t)ctx->num_sms * 16;
   if (grid > cap) grid = cap;
-  perm_kernel<Tin, MODE><<<(unsigned)grid, PT, 0, ctx->stream>>>(d_jobs, njobs, tiles, (const Tin*)src, dst0, dst1);
+  perm_kernel<Tin, MODE><<<(unsigned)grid, PT, 0, ctx->stream>>>(d_jobs, njobs, tiles, (const Tin*)src,
+                                                                  (const Tin*)src1, dst0, dst1);
   return cudaGetLastError();
 }
 
 template <typename Tin, int MODE>
 static cudaError_t pick(ftn_ctx ctx, int staged, const PermJob* d_jobs, int njobs, int64_t tiles, const void* src,
-                        void* dst0, void* dst1) {
-  return staged ? go_staged<Tin, MODE>(ctx, d_jobs, njobs, tiles, src, dst0, dst1)
-                : go<Tin, MODE>(ctx, d_jobs, njobs, tiles, src, dst0, dst1);
+                        const void* src1, void* dst0, void* dst1) {
+  return staged ? go_staged<Tin, MODE>(ctx, d_jobs, njobs, tiles, src, src1, dst0, dst1)
+                : go<Tin, MODE>(ctx, d_jobs, njobs, tiles, src, src1, dst0, dst1);
 }
 
-ftn_status launch_permute(ftn_ctx ctx, const PermJob* d_jobs, int njobs, int64_t tiles, int staged, const void* src,
-                          void* dst0, void* dst1, ftn_dtype in_type, int mode) {
+ftn_status launch_permute2(ftn_ctx ctx, const PermJob* d_jobs, int njobs, int64_t tiles, int staged, const void* src,
+                           const void* src1, void* dst0, void* dst1, ftn_dtype in_type, int mode) {
   if (njobs == 0 || tiles == 0) return FTN_OK;
   cudaError_t e;
   if (in_type == FTN_F64) {
     if (mode != PERM_SAME) return set_error(FTN_EUNSUPPORTED, "FP64 permute supports only the same-type output");
-    e = pick<double, PERM_SAME>(ctx, staged, d_jobs, njobs, tiles, src, dst0, dst1);
+    e = pick<double, PERM_SAME>(ctx, staged, d_jobs, njobs, tiles, src, src1, dst0, dst1);
   } else {
     switch (mode) {
-      case PERM_SAME: e = pick<float, PERM_SAME>(ctx, staged, d_jobs, njobs, tiles, src, dst0, dst1); break;
-      case PERM_TF32: e = pick<float, PERM_TF32>(ctx, staged, d_jobs, njobs, tiles, src, dst0, dst1); break;
-      case PERM_TF32X2: e = pick<float, PERM_TF32X2>(ctx, staged, d_jobs, njobs, tiles, src, dst0, dst1); break;
-      case PERM_BF16: e = pick<float, PERM_BF16>(ctx, staged, d_jobs, njobs, tiles, src, dst0, dst1); break;
-      case PERM_BF16X2: e = pick<float, PERM_BF16X2>(ctx, staged, d_jobs, njobs, tiles, src, dst0, dst1); break;
-      case PERM_F16X2: e = pick<float, PERM_F16X2>(ctx, staged, d_jobs, njobs, tiles, src, dst0, dst1); break;
+      case PERM_SAME: e = pick<float, PERM_SAME>(ctx, staged, d_jobs, njobs, tiles, src, src1, dst0, dst1); break;
+      case PERM_TF32: e = pick<float, PERM_TF32>(ctx, staged, d_jobs, njobs, tiles, src, src1, dst0, dst1); break;
+      case PERM_TF32X2: e = pick<float, PERM_TF32X2>(ctx, staged, d_jobs, njobs, tiles, src, src1, dst0, dst1); break;
+      case PERM_BF16: e = pick<float, PERM_BF16>(ctx, staged, d_jobs, njobs, tiles, src, src1, dst0, dst1); break;
+      case PERM_BF16X2: e = pick<float, PERM_BF16X2>(ctx, staged, d_jobs, njobs, tiles, src, src1, dst0, dst1); break;
+      case PERM_F16X2: e = pick<float, PERM_F16X2>(ctx, staged, d_jobs, njobs, tiles, src, src1, dst0, dst1); break;
       default: return set_error(FTN_EINVAL, "bad permute mode");
     }
   }
   ctx->launches += 1;
   if (e != cudaSuccess) return cuda_error(e, "perm_kernel launch");
   return FTN_OK;
+}
+
+ftn_status launch_permute(ftn_ctx ctx, const PermJob* d_jobs, int njobs, int64_t tiles, int staged, const void* src,
+                          void* dst0, void* dst1, ftn_dtype in_type, int mode) {
+  return launch_permute2(ctx, d_jobs, njobs, tiles, staged, src, src, dst0, dst1, in_type, mode);
 }
 
 }  // namespace ftn

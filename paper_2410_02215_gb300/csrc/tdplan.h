@@ -50,6 +50,11 @@ struct TdPlan {
   std::vector<PermJob> ja, jb, jc;
   int64_t ta = 0, tb = 0, tc = 0;
   int sa = 0, sb = 0, sc = 0;  // staged (TMA) permute kernel usable
+  // Both operands in one launch (B's jobs read the second source and write
+  // after A's fused matrices): empty when the two need different kernels.
+  std::vector<PermJob> jab;
+  int64_t tab = 0;
+  int sab = 0;
   bool fused = true;           // the GEMM epilogue writes the final layout
   std::vector<GemmProb> probs;
   int64_t gemm_tiles = 0;
@@ -70,6 +75,7 @@ struct TdPlan {
   PermJob* d_ja = nullptr;
   PermJob* d_jb = nullptr;
   PermJob* d_jc = nullptr;
+  PermJob* d_jab = nullptr;
   GemmProb* d_probs = nullptr;
   GemmProb* d_red = nullptr;
 };

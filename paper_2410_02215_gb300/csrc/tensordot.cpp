@@ -81,14 +81,16 @@ bool probs_in_bounds(const std::vector<GemmProb>& probs, int64_t a_n, int64_t b_
 
 static ftn_status upload_plan(ftn_ctx ctx, TdPlan& P) {
   size_t sa = P.ja.size() * sizeof(PermJob), sb = P.jb.size() * sizeof(PermJob), sc = P.jc.size() * sizeof(PermJob),
-         sp = P.probs.size() * sizeof(GemmProb), sr = P.red.size() * sizeof(GemmProb);
-  size_t tot = sa + sb + sc + sp + sr;
+         sp = P.probs.size() * sizeof(GemmProb), sr = P.red.size() * sizeof(GemmProb),
+         sm = P.jab.size() * sizeof(PermJob);
+  size_t tot = sa + sb + sc + sp + sr + sm;
   std::vector<uint8_t> host(tot + 16);
   std::memcpy(host.data(), P.ja.data(), sa);
   std::memcpy(host.data() + sa, P.jb.data(), sb);
   std::memcpy(host.data() + sa + sb, P.jc.data(), sc);
   std::memcpy(host.data() + sa + sb + sc, P.probs.data(), sp);
   if (sr) std::memcpy(host.data() + sa + sb + sc + sp, P.red.data(), sr);
+  if (sm) std::memcpy(host.data() + sa + sb + sc + sp + sr, P.jab.data(), sm);
   P.dev = std::make_shared<DevTables>();
   P.dev->ctx = ctx;
   void* d = nullptr;
@@ -101,6 +103,7 @@ static ftn_status upload_plan(ftn_ctx ctx, TdPlan& P) {
   P.d_jc = (PermJob*)(b + sa + sb);
   P.d_probs = (GemmProb*)(b + sa + sb + sc);
   P.d_red = sr ? (GemmProb*)(b + sa + sb + sc + sp) : nullptr;
+  P.d_jab = sm ? (PermJob*)(b + sa + sb + sc + sp + sr) : nullptr;
   return FTN_OK;
 }
 
@@ -202,8 +205,32 @@ static ftn_status build_plan(ftn_ctx ctx, const ftn_tensor_s* A, const ftn_tenso
     add_perm_job(P->jb, P->tb, B->rank, dims, dstr, B->offsets[b], dst, sg ? -1 : 1);
   }
   // the staged permute needs 16-byte aligned source rows (buffer base included)
-  P->sa = finalize_perm_jobs(P->ja, dtype_size(A->dtype), &P->ta, ((uintptr_t)A->data & 15) == 0);
-  P->sb = finalize_perm_jobs(P->jb, dtype_size(B->dtype), &P->tb, ((uintptr_t)B->data & 15) == 0);
+  const bool al_a = ((uintptr_t)A->data & 15) == 0, al_b = ((uintptr_t)B->data & 15) == 0;
+  std::vector<PermJob> ja_raw = P->ja, jb_raw = P->jb;
+  P->sa = finalize_perm_jobs(P->ja, dtype_size(A->dtype), &P->ta, al_a);
+  P->sb = finalize_perm_jobs(P->jb, dtype_size(B->dtype), &P->tb, al_b);
+  // Both operands in one launch: B's jobs read the second source and write
+  // after A's fused matrices (the workspace holds [A hi | B hi | A lo | B lo]).
+  // Kept when the merged list runs on the TMA-staged kernel, or when both
+  // operands were on the register-staged one anyway.
+  if (!ja_raw.empty() && !jb_raw.empty()) {
+    const bool half = prec_half(prec);
+    const int64_t es_out = prec == FTN_PREC_F64 ? 8 : (half ? 2 : 4);
+    const int64_t a_bytes = ((int64_t)P->af_elems * es_out + 255) / 256 * 256;
+    std::vector<PermJob> m = ja_raw;
+    for (PermJob j : jb_raw) {
+      j.src_sel = 1;
+      j.dst_off += a_bytes / es_out;
+      m.push_back(j);
+    }
+    int64_t t = 0;
+    const int st = finalize_perm_jobs(m, dtype_size(A->dtype), &t, al_a && al_b);
+    if (st || (!P->sa && !P->sb)) {
+      P->jab = std::move(m);
+      P->tab = t;
+      P->sab = st;
+    }
+  }
   // ---- result metadata (before out_perm) ----
   const int cr = P->nfa + P->nfb;
   ftn_tensor_s tmp;
@@ -531,24 +558,33 @@ ftn_status tensordot_impl(ftn_ctx ctx, ftn_tensor A, ftn_tensor B, int n, const 
     if (created) ftn_tensor_free(out);
     return set_error(FTN_ENOMEM, "workspace allocation failed");
   }
+  // [A hi | B hi | A lo | B lo]: both lo planes at one offset from their hi planes
   uint8_t* af_hi = ws;
-  uint8_t* af_lo = split ? af_hi + a_b : nullptr;
-  uint8_t* bf_hi = ws + a_b * (split ? 2 : 1);
-  uint8_t* bf_lo = split ? bf_hi + b_b : nullptr;
+  uint8_t* bf_hi = ws + a_b;
+  uint8_t* af_lo = split ? ws + a_b + b_b : nullptr;
+  uint8_t* bf_lo = split ? af_lo + a_b : nullptr;
   // the GEMM epilogue writes the final layout, or the plain one into workspace
-  uint8_t* ctmp = P->fused ? (uint8_t*)out->data : bf_hi + b_b * (split ? 2 : 1);
+  uint8_t* ctmp = P->fused ? (uint8_t*)out->data : ws + (a_b + b_b) * (split ? 2 : 1);
   const int mode = prec_perm_mode(prec);
   const double in_es = (double)dtype_size(A->dtype), planes = split ? 2.0 : 1.0;
   double gemm_flops = 0;
   for (const GemmProb& g : P->probs) gemm_flops += 2.0 * g.M * g.N * g.K;
-  int rec = prof_begin(ctx, "permute", A->numel * (in_es + es * planes), 0);
-  ftn_status st =
-      launch_permute(ctx, P->d_ja, (int)P->ja.size(), P->ta, P->sa, A->data, af_hi, af_lo, A->dtype, mode);
-  prof_end(ctx, rec);
-  if (st == FTN_OK) {
-    rec = prof_begin(ctx, "permute", B->numel * (in_es + es * planes), 0);
-    st = launch_permute(ctx, P->d_jb, (int)P->jb.size(), P->tb, P->sb, B->data, bf_hi, bf_lo, B->dtype, mode);
+  ftn_status st = FTN_OK;
+  int rec = -1;
+  if (P->d_jab) {  // both operands in one launch
+    rec = prof_begin(ctx, "permute", (A->numel + B->numel) * (in_es + es * planes), 0);
+    st = launch_permute2(ctx, P->d_jab, (int)P->jab.size(), P->tab, P->sab, A->data, B->data, af_hi, af_lo,
+                         A->dtype, mode);
     prof_end(ctx, rec);
+  } else {
+    rec = prof_begin(ctx, "permute", A->numel * (in_es + es * planes), 0);
+    st = launch_permute(ctx, P->d_ja, (int)P->ja.size(), P->ta, P->sa, A->data, af_hi, af_lo, A->dtype, mode);
+    prof_end(ctx, rec);
+    if (st == FTN_OK) {
+      rec = prof_begin(ctx, "permute", B->numel * (in_es + es * planes), 0);
+      st = launch_permute(ctx, P->d_jb, (int)P->jb.size(), P->tb, P->sb, B->data, bf_hi, bf_lo, B->dtype, mode);
+      prof_end(ctx, rec);
+    }
   }
   if (st == FTN_OK) {
     double gb = 0;
