@@ -133,6 +133,35 @@ static ftn_status build_plan(ftn_ctx ctx, const ftn_tensor_s* A, const ftn_tenso
     if (!in_a[k]) P->fa[P->nfa++] = k;
   for (int k = 0; k < B->rank; ++k)
     if (!in_b[k]) P->fb[P->nfb++] = k;
+  // Order of the free legs inside the fused matrices (any order gives the
+  // same result: every sign is computed from the orders actually used).
+  // With an output permutation each side's free legs go in the order of
+  // their destination positions, the fastest last, so that the epilogue's
+  // write runs follow the GEMM row or column index.  gidx maps a result leg
+  // (A's free legs, then B's, in leg order) to its position in that order.
+  int gidx[MAXR];
+  for (int r = 0; r < P->nfa + P->nfb; ++r) gidx[r] = r;
+  if (out_perm) {
+    const int cr_api = P->nfa + P->nfb;
+    int outpos[MAXR];
+    for (int u = 0; u < cr_api; ++u) outpos[out_perm[u]] = u;
+    int oa[MAXR], ob[MAXR];
+    for (int j = 0; j < P->nfa; ++j) oa[j] = j;
+    for (int j = 0; j < P->nfb; ++j) ob[j] = P->nfa + j;
+    std::stable_sort(oa, oa + P->nfa, [&](int x, int y) { return outpos[x] < outpos[y]; });
+    std::stable_sort(ob, ob + P->nfb, [&](int x, int y) { return outpos[x] < outpos[y]; });
+    int fa_api[MAXR], fb_api[MAXR];
+    for (int j = 0; j < P->nfa; ++j) fa_api[j] = P->fa[j];
+    for (int j = 0; j < P->nfb; ++j) fb_api[j] = P->fb[j];
+    for (int i = 0; i < P->nfa; ++i) {
+      P->fa[i] = fa_api[oa[i]];
+      gidx[oa[i]] = i;
+    }
+    for (int i = 0; i < P->nfb; ++i) {
+      P->fb[i] = fb_api[ob[i] - P->nfa];
+      gidx[ob[i]] = P->nfa + i;
+    }
+  }
   const int pA = A->parity, pB = B->parity;
   // sector offsets of free rows (A), free columns (B) and the fused bond (K)
   int64_t fad0[MAXR], fad1[MAXR], fbd0[MAXR], fbd1[MAXR], kd0[MAXR], kd1[MAXR];
@@ -256,12 +285,12 @@ static ftn_status build_plan(ftn_ctx ctx, const ftn_tensor_s* A, const ftn_tenso
   // ---- final result layout (out_perm applied in the GEMM epilogue) ----
   P->cr = cr;
   P->cpar = tmp.parity;
-  bool ident = true;
-  if (out_perm)
-    for (int u = 0; u < cr; ++u) ident = ident && out_perm[u] == u;
-  P->out_perm = !ident;
+  // output leg u = leg perm[u] of the GEMM-order result
   int perm[MAXR];
-  for (int u = 0; u < cr; ++u) perm[u] = P->out_perm ? out_perm[u] : u;
+  for (int u = 0; u < cr; ++u) perm[u] = gidx[out_perm ? out_perm[u] : u];
+  bool ident = true;
+  for (int u = 0; u < cr; ++u) ident = ident && perm[u] == u;
+  P->out_perm = !ident;
   for (int u = 0; u < cr; ++u)
     P->cd0[u] = tmp.d0[perm[u]], P->cd1[u] = tmp.d1[perm[u]], P->cdual[u] = tmp.dual[perm[u]];
   ftn_tensor_s fin;
@@ -292,6 +321,10 @@ static ftn_status build_plan(ftn_ctx ctx, const ftn_tensor_s* A, const ftn_tenso
       epi_rows = 0;
     } else if (run_r >= 16) {
       epi_rows = 1;
+    } else if (fin_numel <= ((int64_t)1 << 22)) {
+      // short runs, small result: scattered epilogue stores cost less than a
+      // second pass over the result
+      epi_rows = run_r > run_c ? 1 : 0;
     } else {
       fuse = false;
     }
