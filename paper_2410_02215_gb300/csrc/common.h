@@ -286,6 +286,14 @@ ftn_status launch_splitk_reduce(ftn_ctx ctx, const GemmProb* d_red, int nred, in
 ftn_status launch_splitk_reduce_f32(ftn_ctx ctx, const GemmProb* d_red, int nred, int64_t total, const float* part,
                                     float* c);
 
+// One tile of a tensor-core GEMM launch, decoded once when the plan is
+// built: its problem (the group's first member when a tile spans a group's
+// members), origin, bond sector, operand rows and K range.
+struct TileEnt {
+  int32_t prob, m0, n0, pi;
+  int32_t a_y, b_y, K, k0;
+};
+
 struct TcOperands {
   // fused pi-matrices: rows x ldk elements, K-major; lo only for split modes
   const void* a_hi[2];
@@ -295,8 +303,11 @@ struct TcOperands {
   int64_t a_rows[2], b_rows[2];
   int32_t kdim[2], ldk[2];
 };
+// tt: the launch's tile table (tc_tile_table), or null to decode tiles in the kernel.
 ftn_status launch_gemm_tc(ftn_ctx ctx, ftn_prec prec, const TcOperands& ops, const GemmProb* d_probs, int nprobs,
-                          int64_t tiles, int bn, float* c);
+                          int64_t tiles, int bn, float* c, const TileEnt* tt = nullptr);
+// Fills d_out[t] for every tile t < tiles of a launch over d_probs (tile width bn).
+ftn_status tc_tile_table(ftn_ctx ctx, const GemmProb* d_probs, int nprobs, int64_t tiles, int bn, TileEnt* d_out);
 // Four TMA tensor maps (A hi, B hi, A lo, B lo) of one fused-matrix pair,
 // encoded for tile width bn, as stored in a device table for batched launches.
 struct alignas(64) TcMapSet {

@@ -16,6 +16,7 @@
 // epilogue.  The tensor core's accumulation rounds each partial sum, so
 // keeping the large products apart from the two small cross terms cuts the
 // number of roundings applied to the large accumulator by three.
+#include <algorithm>
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
@@ -37,6 +38,7 @@ struct TcParams {
   // reads its operands through gmaps[4 * p.pi + {0: A hi, 1: B hi, 2: A lo,
   // 3: B lo}] (global memory, 64-byte aligned) instead of the maps above.
   const CUtensorMap* gmaps;
+  const TileEnt* tt;  // decoded tiles (or null: decode with tc_decode)
   const GemmProb* probs;
   float* C;
   int* err;
@@ -114,6 +116,40 @@ __device__ __forceinline__ const GemmProb* tc_decode(const TcParams& P, int64_t 
   return p;
 }
 
+// Tile t as a TileEnt: from the launch's tile table when there is one (one
+// 32-byte load), else decoded here (`cur` as for tc_decode).
+template <int BN>
+__device__ __forceinline__ void tile_at(const TcParams& P, int64_t t, int& cur, TileEnt& e) {
+  if (P.tt) {
+    const int4* q = reinterpret_cast<const int4*>(P.tt + t);
+    const int4 a = q[0], b = q[1];
+    e.prob = a.x, e.m0 = a.y, e.n0 = a.z, e.pi = a.w;
+    e.a_y = b.x, e.b_y = b.y, e.K = b.z, e.k0 = b.w;
+    return;
+  }
+  int m0, n0;
+  const GemmProb* p = tc_decode<BN>(P, t, m0, n0, cur);
+  e.prob = (int32_t)(p - P.probs);
+  e.m0 = m0;
+  e.n0 = n0;
+  e.pi = p->pi;
+  e.a_y = p->a_row0 + m0;
+  e.b_y = p->b_row0 + n0;
+  e.K = p->K;
+  e.k0 = p->k0;
+}
+
+template <int BN>
+__global__ void tile_table_kernel(TcParams P, TileEnt* __restrict__ out) {
+  P.tt = nullptr;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < P.tiles; t += (int64_t)gridDim.x * blockDim.x) {
+    int cur = -1;
+    TileEnt e;
+    tile_at<BN>(P, t, cur, e);
+    out[t] = e;
+  }
+}
+
 template <int FMT, bool SPLIT, int BN>
 __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_constant__ TcParams P) {
   using Cfg = TcCfg<FMT, SPLIT, BN>;
@@ -157,11 +193,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
       uint32_t issued = 0, lastpar = 0;
       bool ok = true;
       int cur = -1, fenced = -1;
+      TileEnt nx;
+      if (blockIdx.x < P.tiles) tile_at<BN>(P, blockIdx.x, cur, nx);
       for (int64_t t = blockIdx.x; t < P.tiles && ok; t += gridDim.x) {
-        int m0, n0;
-        const GemmProb& p = *tc_decode<BN>(P, t, m0, n0, cur);
-        const int nk = (p.K + Cfg::KB - 1) / Cfg::KB;
-        const int pi = p.pi;
+        const TileEnt e = nx;  // this tile; the next one's entry is fetched while this one is issued
+        if (t + gridDim.x < P.tiles) tile_at<BN>(P, t + gridDim.x, cur, nx);
+        const int nk = (e.K + Cfg::KB - 1) / Cfg::KB;
+        const int pi = e.pi;
         const CUtensorMap *ma = &P.a_hi[pi & 1], *mb = &P.b_hi[pi & 1], *mal = &P.a_lo[pi & 1],
                           *mbl = &P.b_lo[pi & 1];
         if (P.gmaps) {
@@ -186,12 +224,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
           }
           uint8_t* sa = smem + stage * Cfg::STAGE_BYTES;
           mbar_expect_tx(&full[stage], Cfg::STAGE_BYTES);
-          const int kx = p.k0 + kb * Cfg::KB;  // K element; k0 is a multiple of KB
-          tma_load_2d(sa, ma, kx, p.a_row0 + m0, &full[stage]);
-          tma_load_2d(sa + Cfg::A_BYTES, mb, kx, p.b_row0 + n0, &full[stage]);
+          const int kx = e.k0 + kb * Cfg::KB;  // K element; k0 is a multiple of KB
+          tma_load_2d(sa, ma, kx, e.a_y, &full[stage]);
+          tma_load_2d(sa + Cfg::A_BYTES, mb, kx, e.b_y, &full[stage]);
           if constexpr (SPLIT) {
-            tma_load_2d(sa + Cfg::A_BYTES + Cfg::B_BYTES, mal, kx, p.a_row0 + m0, &full[stage]);
-            tma_load_2d(sa + 2 * Cfg::A_BYTES + Cfg::B_BYTES, mbl, kx, p.b_row0 + n0, &full[stage]);
+            tma_load_2d(sa + Cfg::A_BYTES + Cfg::B_BYTES, mal, kx, e.a_y, &full[stage]);
+            tma_load_2d(sa + 2 * Cfg::A_BYTES + Cfg::B_BYTES, mbl, kx, e.b_y, &full[stage]);
           }
           issued |= 1u << stage;
           lastpar = (lastpar & ~(1u << stage)) | (phase << stage);
@@ -214,10 +252,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
       uint32_t acc_phase = 0;
       bool ok = true;
       int cur = -1;
+      TileEnt nx;
+      if (blockIdx.x < P.tiles) tile_at<BN>(P, blockIdx.x, cur, nx);
       for (int64_t t = blockIdx.x; t < P.tiles && ok; t += gridDim.x) {
-        int m0, n0;
-        const GemmProb& p = *tc_decode<BN>(P, t, m0, n0, cur);
-        const int nk = (p.K + Cfg::KB - 1) / Cfg::KB;
+        const TileEnt e = nx;
+        if (t + gridDim.x < P.tiles) tile_at<BN>(P, t + gridDim.x, cur, nx);
+        const int nk = (e.K + Cfg::KB - 1) / Cfg::KB;
         if (nk == 0) continue;
         if (!mbar_wait(&tempty[acc], acc_phase ^ 1, P.err)) break;
         tc_fence_after();
@@ -284,10 +324,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
     uint32_t j = 0;  // tiles with K > 0 seen so far (all sets count them)
     const bool c16 = ((uintptr_t)P.C & 15) == 0;  // 16-byte vector stores need an aligned base
     int cur = -1;
+    TileEnt nx;
+    if (blockIdx.x < P.tiles) tile_at<BN>(P, blockIdx.x, cur, nx);
     for (int64_t t = blockIdx.x; t < P.tiles; t += gridDim.x) {
-      int m0, n0;
-      const GemmProb& p = *tc_decode<BN>(P, t, m0, n0, cur);
-      const int nk = (p.K + Cfg::KB - 1) / Cfg::KB;
+      const TileEnt e = nx;
+      if (t + gridDim.x < P.tiles) tile_at<BN>(P, t + gridDim.x, cur, nx);
+      const int m0 = e.m0, n0 = e.n0;
+      const GemmProb& p = P.probs[e.prob];
+      const int nk = (e.K + Cfg::KB - 1) / Cfg::KB;
       const int acc = (int)(j & 1);
       if (nk > 0) ++j;
       if (nk > 0 ? acc != set : set != 0) continue;
@@ -481,7 +525,7 @@ static bool encode_set(const TcOperands& ops, int pi, CUtensorMap* a_hi, CUtenso
 
 template <int FMT, bool SPLIT, int BN>
 static ftn_status run(ftn_ctx ctx, const TcOperands* ops, const void* gmaps, const GemmProb* d_probs, int nprobs,
-                      int64_t tiles, float* c) {
+                      int64_t tiles, float* c, const TileEnt* tt) {
   using Cfg = TcCfg<FMT, SPLIT, BN>;
   TcParams P;
   std::memset(&P, 0, sizeof(P));
@@ -491,6 +535,7 @@ static ftn_status run(ftn_ctx ctx, const TcOperands* ops, const void* gmaps, con
       return set_error(FTN_ECUDA, "cuTensorMapEncodeTiled failed");
   }
   P.gmaps = reinterpret_cast<const CUtensorMap*>(gmaps);
+  P.tt = tt;
   P.probs = d_probs;
   P.C = c;
   P.err = ctx->dev_err;
@@ -521,40 +566,61 @@ int64_t tc_tiles_for(int M, int N, int bn) {
 
 template <int FMT, bool SPLIT>
 static ftn_status by_bn(ftn_ctx ctx, int bn, const TcOperands* ops, const void* gm, const GemmProb* d, int np,
-                        int64_t tiles, float* c) {
+                        int64_t tiles, float* c, const TileEnt* tt) {
   switch (bn) {
-    case 16: return run<FMT, SPLIT, 16>(ctx, ops, gm, d, np, tiles, c);
-    case 32: return run<FMT, SPLIT, 32>(ctx, ops, gm, d, np, tiles, c);
-    case 64: return run<FMT, SPLIT, 64>(ctx, ops, gm, d, np, tiles, c);
-    case 128: return run<FMT, SPLIT, 128>(ctx, ops, gm, d, np, tiles, c);
+    case 16: return run<FMT, SPLIT, 16>(ctx, ops, gm, d, np, tiles, c, tt);
+    case 32: return run<FMT, SPLIT, 32>(ctx, ops, gm, d, np, tiles, c, tt);
+    case 64: return run<FMT, SPLIT, 64>(ctx, ops, gm, d, np, tiles, c, tt);
+    case 128: return run<FMT, SPLIT, 128>(ctx, ops, gm, d, np, tiles, c, tt);
     default:
-      if constexpr (!SPLIT) return run<FMT, SPLIT, 256>(ctx, ops, gm, d, np, tiles, c);
+      if constexpr (!SPLIT) return run<FMT, SPLIT, 256>(ctx, ops, gm, d, np, tiles, c, tt);
       return set_error(FTN_EINVAL, "bad tile width");
   }
 }
 
 static ftn_status dispatch(ftn_ctx ctx, ftn_prec prec, int bn, const TcOperands* ops, const void* gm,
-                           const GemmProb* d_probs, int nprobs, int64_t tiles, float* c) {
+                           const GemmProb* d_probs, int nprobs, int64_t tiles, float* c, const TileEnt* tt) {
   if (nprobs == 0 || tiles == 0) return FTN_OK;
   switch (prec) {
-    case FTN_PREC_TF32: return by_bn<2, false>(ctx, bn, ops, gm, d_probs, nprobs, tiles, c);
-    case FTN_PREC_TF32X3: return by_bn<2, true>(ctx, bn, ops, gm, d_probs, nprobs, tiles, c);
-    case FTN_PREC_BF16: return by_bn<1, false>(ctx, bn, ops, gm, d_probs, nprobs, tiles, c);
-    case FTN_PREC_BF16X3: return by_bn<1, true>(ctx, bn, ops, gm, d_probs, nprobs, tiles, c);
-    case FTN_PREC_F16X3: return by_bn<0, true>(ctx, bn, ops, gm, d_probs, nprobs, tiles, c);
+    case FTN_PREC_TF32: return by_bn<2, false>(ctx, bn, ops, gm, d_probs, nprobs, tiles, c, tt);
+    case FTN_PREC_TF32X3: return by_bn<2, true>(ctx, bn, ops, gm, d_probs, nprobs, tiles, c, tt);
+    case FTN_PREC_BF16: return by_bn<1, false>(ctx, bn, ops, gm, d_probs, nprobs, tiles, c, tt);
+    case FTN_PREC_BF16X3: return by_bn<1, true>(ctx, bn, ops, gm, d_probs, nprobs, tiles, c, tt);
+    case FTN_PREC_F16X3: return by_bn<0, true>(ctx, bn, ops, gm, d_probs, nprobs, tiles, c, tt);
     default: return set_error(FTN_EUNSUPPORTED, "precision has no tensor-core path");
   }
 }
 
 ftn_status launch_gemm_tc(ftn_ctx ctx, ftn_prec prec, const TcOperands& ops, const GemmProb* d_probs, int nprobs,
-                          int64_t tiles, int bn, float* c) {
-  return dispatch(ctx, prec, bn, &ops, nullptr, d_probs, nprobs, tiles, c);
+                          int64_t tiles, int bn, float* c, const TileEnt* tt) {
+  return dispatch(ctx, prec, bn, &ops, nullptr, d_probs, nprobs, tiles, c, tt);
+}
+
+ftn_status tc_tile_table(ftn_ctx ctx, const GemmProb* d_probs, int nprobs, int64_t tiles, int bn, TileEnt* d_out) {
+  if (tiles <= 0 || nprobs <= 0) return FTN_OK;
+  TcParams P;
+  std::memset(&P, 0, sizeof(P));
+  P.probs = d_probs;
+  P.nprobs = nprobs;
+  P.tiles = tiles;
+  const unsigned grid = (unsigned)std::min<int64_t>((tiles + 255) / 256, (int64_t)ctx->num_sms * 4);
+  switch (bn) {
+    case 16: tile_table_kernel<16><<<grid, 256, 0, ctx->stream>>>(P, d_out); break;
+    case 32: tile_table_kernel<32><<<grid, 256, 0, ctx->stream>>>(P, d_out); break;
+    case 64: tile_table_kernel<64><<<grid, 256, 0, ctx->stream>>>(P, d_out); break;
+    case 128: tile_table_kernel<128><<<grid, 256, 0, ctx->stream>>>(P, d_out); break;
+    case 256: tile_table_kernel<256><<<grid, 256, 0, ctx->stream>>>(P, d_out); break;
+    default: return set_error(FTN_EINVAL, "bad tile width");
+  }
+  ctx->launches += 1;
+  FTN_CUDA(cudaGetLastError());
+  return FTN_OK;
 }
 
 ftn_status launch_gemm_tc_maps(ftn_ctx ctx, ftn_prec prec, const TcMapSet* d_maps, const GemmProb* d_probs,
                                int nprobs, int64_t tiles, int bn, float* c) {
   if (!d_maps || ((uintptr_t)d_maps & 63)) return set_error(FTN_EINVAL, "internal error: tensor maps not 64-byte aligned");
-  return dispatch(ctx, prec, bn, nullptr, d_maps, d_probs, nprobs, tiles, c);
+  return dispatch(ctx, prec, bn, nullptr, d_maps, d_probs, nprobs, tiles, c, nullptr);
 }
 
 template <int FMT, bool SPLIT>

@@ -76,6 +76,8 @@ struct TdPlan {
   PermJob* d_jb = nullptr;
   PermJob* d_jc = nullptr;
   PermJob* d_jab = nullptr;
+  TileEnt* d_tt = nullptr;  // tensor-core path: the decoded tiles of the GEMM launch
+  bool tile_tab = false;
   GemmProb* d_probs = nullptr;
   GemmProb* d_red = nullptr;
 };

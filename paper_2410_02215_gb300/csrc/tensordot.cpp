@@ -83,6 +83,8 @@ static ftn_status upload_plan(ftn_ctx ctx, TdPlan& P) {
   size_t sa = P.ja.size() * sizeof(PermJob), sb = P.jb.size() * sizeof(PermJob), sc = P.jc.size() * sizeof(PermJob),
          sp = P.probs.size() * sizeof(GemmProb), sr = P.red.size() * sizeof(GemmProb),
          sm = P.jab.size() * sizeof(PermJob);
+  const size_t pre = (sa + sb + sc + sp + sr + sm + 255) & ~(size_t)255;
+  const size_t st = P.tile_tab ? (size_t)P.gemm_tiles * sizeof(TileEnt) : 0;
   size_t tot = sa + sb + sc + sp + sr + sm;
   std::vector<uint8_t> host(tot + 16);
   std::memcpy(host.data(), P.ja.data(), sa);
@@ -95,7 +97,13 @@ static ftn_status upload_plan(ftn_ctx ctx, TdPlan& P) {
   P.dev->ctx = ctx;
   void* d = nullptr;
   // (a pageable host-to-device copy has staged its source when the call returns)
-  FTN_TRY(upload_table(ctx, host.data(), tot, &d));
+  if (st) {  // room after the tables for the tile table, filled on the device below
+    d = dev_alloc(ctx, pre + st);
+    if (!d) return set_error(FTN_ENOMEM, "device allocation failed (plan tables)");
+    FTN_CUDA(cudaMemcpyAsync(d, host.data(), tot, cudaMemcpyHostToDevice, ctx->stream));
+  } else {
+    FTN_TRY(upload_table(ctx, host.data(), tot, &d));
+  }
   P.dev->p = d;
   uint8_t* b = (uint8_t*)d;
   P.d_ja = (PermJob*)b;
@@ -104,6 +112,10 @@ static ftn_status upload_plan(ftn_ctx ctx, TdPlan& P) {
   P.d_probs = (GemmProb*)(b + sa + sb + sc);
   P.d_red = sr ? (GemmProb*)(b + sa + sb + sc + sp) : nullptr;
   P.d_jab = sm ? (PermJob*)(b + sa + sb + sc + sp + sr) : nullptr;
+  if (st) {
+    P.d_tt = (TileEnt*)(b + pre);
+    FTN_TRY(tc_tile_table(ctx, P.d_probs, (int)P.probs.size(), P.gemm_tiles, P.bn, P.d_tt));
+  }
   return FTN_OK;
 }
 
@@ -505,6 +517,8 @@ static ftn_status build_plan(ftn_ctx ctx, const ftn_tensor_s* A, const ftn_tenso
       (P->part_elems && !red_in_bounds(P->red, P->part_elems, P->tmp_numel)) ||
       (!P->fused && !jobs_in_bounds(P->jc, P->tmp_numel, P->tmp_numel)))
     return set_error(FTN_EINVAL, "internal error: contraction plan out of bounds");
+  // tensor-core launches read their tiles from a table decoded once here
+  P->tile_tab = prec != FTN_PREC_F64 && P->gemm_tiles > 0 && P->gemm_tiles <= ((int64_t)1 << 20);
   FTN_TRY(upload_plan(ctx, *P));
   out = P;
   return FTN_OK;
@@ -649,7 +663,8 @@ ftn_status tensordot_impl(ftn_ctx ctx, ftn_tensor A, ftn_tensor B, int n, const 
         ops.ldk[pi] = (int32_t)P->ldk[pi];
       }
       rec = prof_begin(ctx, "gemm_tc", gb, gemm_flops);
-      st = launch_gemm_tc(ctx, prec, ops, P->d_probs, (int)P->probs.size(), P->gemm_tiles, P->bn, (float*)ctmp);
+      st = launch_gemm_tc(ctx, prec, ops, P->d_probs, (int)P->probs.size(), P->gemm_tiles, P->bn, (float*)ctmp,
+                          P->d_tt);
       prof_end(ctx, rec);
     }
   }
