@@ -13,7 +13,7 @@ import math
 
 import numpy as np
 
-from .graded import GTensor, contract, flip_legs, index_parity
+from .graded import GTensor, contract, flip_legs, index_parity, transpose
 from .compress import compress
 
 __all__ = ["Network", "contract_tree", "brute_force_global", "arrows_from_positions"]
@@ -117,7 +117,8 @@ def contract_tree(net, tree, mode="local", policy="exact", chi=None, normalize=F
     """Walk an SSA contraction tree (Fig. 1) and return (tensor, log_scale, leg ids).
 
     ``mode='local'``: pairwise contractions with the bond parity applied when a
-    bond is contracted against its arrow (Eq. fermionictn2).
+    bond is contracted against its arrow (Eq. fermionictn2); odd tensors are
+    made even with a dummy leg (see :func:`_contract_local_odd`).
     ``mode='global'``: the later tensor of each pair is first moved leftwards
     past every tensor between the two positions; each shared bond it passes
     carries a bond parity g and each odd tensor it passes a phase
@@ -131,6 +132,9 @@ def contract_tree(net, tree, mode="local", policy="exact", chi=None, normalize=F
     """
     if mode == "global" and net.positions is None:
         raise ValueError("global mode needs positions")
+    odd = [i for i, t in enumerate(net.tensors) if t.parity] if mode == "local" else []
+    if odd:
+        return _contract_local_odd(net, tree, policy, chi, normalize, odd)
     st = _State(net)
     n = len(net.tensors)
     log_scale = 0.0
@@ -186,6 +190,36 @@ def contract_tree(net, tree, mode="local", policy="exact", chi=None, normalize=F
                 log_scale += math.log(m)
     (last,) = list(st.t)
     return st.t[last], log_scale, st.ids[last]
+
+
+# Order of the dummy legs of odd tensors after a locally ordered contraction
+# (see _contract_local_odd).
+DUMMY_ORDER_DESCENDING = True
+
+
+def _contract_local_odd(net, tree, policy, chi, normalize, odd):
+    """Locally ordered formalism with odd tensors (Sec. II.D): every odd
+    tensor gets one more leg, odd and of size 1, which makes it even; the
+    network is contracted as an even one, the dummy legs stay open, and the
+    dummy legs left on the result are sorted by decreasing tensor index (a
+    fermionic transposition, so each exchange of two of them is a sign).
+    The value is that of the globally ordered network with the tensors in
+    index order (reading of the ordering convention, pinned in the tests
+    against the brute-force global value)."""
+    tensors = list(net.tensors)
+    for i in odd:
+        t = tensors[i]
+        tensors[i] = GTensor(t.data[..., None], list(t.legs) + [(0, 1, 0)], 0)
+    inner = Network(tensors, net.bonds, None)
+    res, log_scale, ids = contract_tree(inner, tree, mode="local", policy=policy, chi=chi, normalize=normalize)
+    owners = [tk[0] for tk in ids]
+    if sorted(owners) != sorted(odd):
+        raise ValueError("network is not closed")
+    order = sorted(range(len(ids)), key=lambda q: owners[q], reverse=DUMMY_ORDER_DESCENDING)
+    if len(order) > 1:
+        res = transpose(res, order)
+    val = res.data.reshape(-1)[0] if res.data.size else 0.0
+    return GTensor(np.array(val), [], 0), log_scale, []
 
 
 def brute_force_global(net):
