@@ -275,7 +275,10 @@ typedef struct {
 
 /* Contract a closed network along the tree.  Locally ordered when
  * positions == NULL (bond parity when a bond is contracted against its
- * arrow); globally ordered otherwise (the later tensor is moved past the
+ * arrow; each odd tensor carries a size-1 odd dummy leg (Sec. II.D), and
+ * the dummy legs left at the end are sorted by decreasing tensor index,
+ * which gives the value of the globally ordered network with the tensors
+ * in index order); globally ordered otherwise (the later tensor is moved past the
  * tensors between, each shared bond passed carrying g and each odd tensor
  * passed a phase, then plain F).  Late policy compresses, just before a
  * step, every other bond of both operands whose dimension exceeds chi;

@@ -49,6 +49,7 @@ struct Exec {
   std::map<int64_t, Live> live;
   std::map<int64_t, int64_t> partner;  // leg id -> leg id
   std::map<int64_t, int64_t> owner;    // leg id -> tensor id
+  std::map<int64_t, int> dummy;        // dummy leg id -> index of its odd tensor (locally ordered only)
   int64_t next_leg = 1ll << 40;
   int sign = 1;
   Exec() = default;
@@ -110,13 +111,27 @@ struct Exec {
       if (!t) return set_error(FTN_EINVAL, "null tensor in network");
       if (t->dtype != want) return set_error(FTN_EUNSUPPORTED, "tensor dtype does not match the precision");
       ftn_tensor view = nullptr;  // borrowed view: the executor never frees caller buffers
-      FTN_TRY(ftn_tensor_wrap(ctx, t->rank, t->d0, t->d1, t->dual, t->parity, t->dtype, t->data, &view));
       Live L;
+      if (!global && t->parity) {
+        // Locally ordered formalism, odd tensor (Sec. II.D): one more leg, odd
+        // and of size 1, makes it even.  Appended last, it keeps every
+        // nonzero block at the same offset with the same row-major shape, so
+        // the view reads the caller's buffer unchanged.
+        if (t->rank + 1 > MAXR) return set_error(FTN_EUNSUPPORTED, "odd tensor of maximal rank in the local formalism");
+        int32_t d0[MAXR], d1[MAXR];
+        uint8_t du[MAXR];
+        for (int k = 0; k < t->rank; ++k) d0[k] = t->d0[k], d1[k] = t->d1[k], du[k] = t->dual[k];
+        d0[t->rank] = 0, d1[t->rank] = 1, du[t->rank] = 0;
+        FTN_TRY(ftn_tensor_wrap(ctx, t->rank + 1, d0, d1, du, 0, t->dtype, t->data, &view));
+        dummy[(int64_t)i * 64 + t->rank] = i;
+      } else {
+        FTN_TRY(ftn_tensor_wrap(ctx, t->rank, t->d0, t->d1, t->dual, t->parity, t->dtype, t->data, &view));
+      }
       L.t = view;
       L.pos = global ? net->positions[i] : 0;
-      for (int k = 0; k < t->rank; ++k) L.ids.push_back((int64_t)i * 64 + k);
+      for (int k = 0; k < view->rank; ++k) L.ids.push_back((int64_t)i * 64 + k);
       live[i] = L;
-      for (int k = 0; k < t->rank; ++k) owner[(int64_t)i * 64 + k] = i;
+      for (int k = 0; k < view->rank; ++k) owner[(int64_t)i * 64 + k] = i;
     }
     for (int b = 0; b < net->n_bonds; ++b) {
       const int32_t* q = net->bonds + 4 * b;
@@ -384,7 +399,20 @@ ftn_status contract_batch_impl(ftn_ctx ctx, int count, const ftn_network* nets, 
     Exec& E = *ex[i];
     if (E.live.size() != 1) return set_error(FTN_EINVAL, "tree does not reduce the network to one tensor");
     ftn_tensor last = E.live.begin()->second.t;
-    if (last->rank != 0) return set_error(FTN_EINVAL, "network is not closed (open legs remain)");
+    // Only the dummy legs of odd tensors may remain (locally ordered
+    // formalism); sorting them by decreasing tensor index is a fermionic
+    // transposition of odd legs: one sign per inverted pair.
+    const std::vector<int64_t>& left = E.live.begin()->second.ids;
+    std::vector<int> own;
+    for (int64_t id : left) {
+      auto it = E.dummy.find(id);
+      if (it == E.dummy.end()) return set_error(FTN_EINVAL, "network is not closed (open legs remain)");
+      own.push_back(it->second);
+    }
+    if (own.size() != E.dummy.size()) return set_error(FTN_EINVAL, "internal error: dummy legs lost");
+    for (size_t p = 0; p < own.size(); ++p)
+      for (size_t q = p + 1; q < own.size(); ++q)
+        if (own[p] < own[q]) E.sign = -E.sign;
     res[i].value = last->numel ? last->data : nullptr;
     res[i].logacc = (const double*)state(i);
     res[i].f64 = last->dtype == FTN_F64 ? 1 : 0;

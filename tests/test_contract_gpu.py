@@ -165,3 +165,26 @@ def test_energy_concurrent_streams_match_sequential(F, ctx):
         for c in extra:
             c.synchronize()
             c.close()
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_local_formalism_with_odd_tensors(F, ctx, seed):
+    """Odd tensors in the locally ordered formalism (dummy legs, Sec. II.D):
+    the GPU value equals the oracle's, the brute-force global value and the
+    GPU's globally ordered contraction with the tensors in index order."""
+    from test_oracle_odd_local import rand_net, trees_of
+
+    net, legs, blocks, odd = rand_net(seed)
+    bf = O.brute_force_global(net)
+    tens = [F.Tensor.from_blocks(ctx, legs[i], 1 if i in odd else 0, blocks[i]) for i in range(len(legs))]
+    for tr in trees_of(net, 3):
+        ref, _, _ = O.contract_tree(net, tr, mode="local")
+        m, lg = F.contract(ctx, tens, net.bonds, tr)
+        mg, lgg = F.contract(ctx, tens, net.bonds, tr, positions=list(range(len(legs))))
+        v, vg = m * math.exp(lg), mg * math.exp(lgg)
+        assert abs(v - float(ref.data)) <= 1e-10 * max(1.0, abs(bf)), (seed, tr, v, float(ref.data))
+        assert abs(v - bf) <= 1e-10 * max(1.0, abs(bf))
+        assert abs(vg - bf) <= 1e-10 * max(1.0, abs(bf))
+    t32 = [F.Tensor.from_blocks(ctx, legs[i], 1 if i in odd else 0, blocks[i], F.F32) for i in range(len(legs))]
+    m, lg = F.contract(ctx, t32, net.bonds, trees_of(net, 1)[0], prec="f16x3")
+    assert abs(m * math.exp(lg) - bf) <= 1e-5 * max(1.0, abs(bf))
