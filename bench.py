@@ -362,7 +362,7 @@ def cluster_bench(F, ctx, torch, n_graphs, streams, with_oracle, batch=128):
     ctxs = [ctx] + [F.Context(stream=torch.cuda.Stream()) for _ in range(max(streams, 1) - 1)]
     out = {"workload": CLUSTER_WORKLOAD, "graphs": n_graphs, "streams": len(ctxs)}
     res = {}
-    for prec, dt in (("f64", F.F64), ("tf32x3", F.F32)):
+    for prec, dt in (("f64", F.F64), ("tf32x3", F.F32), ("f16x3", F.F32)):
         kets = [[F.Tensor.from_blocks(ctx, lay["legs"][s], 0, bl[s], dt) for s in range(lay["n"])]
                 for lay, bl, _ in graphs]
         ctx.synchronize()
@@ -378,8 +378,10 @@ def cluster_bench(F, ctx, torch, n_graphs, streams, with_oracle, batch=128):
         res[prec] = energies
         out[prec] = {"terms_per_s": nterms / dt_s, "terms": nterms, "s": dt_s, "batch": batch,
                      "same_as_unbatched": got[:3] == one}
-    e64, e32 = np.array(res["f64"]), np.array(res["tf32x3"])
-    out["mixed_vs_f64_max_rel_err"] = float(np.max(np.abs(e32 - e64) / np.abs(e64)))
+    e64 = np.array(res["f64"])
+    for p in ("tf32x3", "f16x3"):
+        out[p]["max_rel_err_vs_f64"] = float(np.max(np.abs(np.array(res[p]) - e64) / np.abs(e64)))
+    out["mixed_vs_f64_max_rel_err"] = out["tf32x3"]["max_rel_err_vs_f64"]
     if with_oracle:
         import oracle as O
 
@@ -614,7 +616,7 @@ def energy_bench(F, ctx, evals, with_oracle, workers=8, batches=(0, 2, 3, 6)):
     tf = lambda ops: W.double_layer_tree(n, st, ops)  # noqa: E731
     out = {"workload": ENERGY_WORKLOAD, "streams": len(ctxs)}
     res = {}
-    for prec, dt in (("f64", F.F64), ("tf32x3", F.F32)):
+    for prec, dt in (("f64", F.F64), ("tf32x3", F.F32), ("f16x3", F.F32)):
         kets = [F.Tensor.from_blocks(ctx, lay["legs"][s_], 0, blocks[s_], dt) for s_ in range(n)]
         ctx.synchronize()
         for c in ctxs:  # warm-up: every context builds its plans
@@ -640,8 +642,11 @@ def energy_bench(F, ctx, evals, with_oracle, workers=8, batches=(0, 2, 3, 6)):
                      "gpu_launches_per_eval": (sum(c.launches() for c in ctxs) - l0) / evals,
                      "one_stream_s_per_eval": one_s, "same_as_one_stream": e == e1 and all(v[1] for v in trial.values()),
                      "trial_s_per_eval_by_batch": {str(b): round(v[0], 4) for b, v in trial.items()}}
-    out["mixed_vs_f64_rel_err"] = abs(res["tf32x3"] - res["f64"]) / abs(res["f64"])
-    out["speedup_mixed_vs_f64"] = out["tf32x3"]["evals_per_s"] / out["f64"]["evals_per_s"]
+    for p in ("tf32x3", "f16x3"):
+        out[p]["rel_err_vs_f64"] = abs(res[p] - res["f64"]) / abs(res["f64"])
+        out[p]["speedup_vs_f64"] = out[p]["evals_per_s"] / out["f64"]["evals_per_s"]
+    out["mixed_vs_f64_rel_err"] = out["tf32x3"]["rel_err_vs_f64"]
+    out["speedup_mixed_vs_f64"] = out["tf32x3"]["speedup_vs_f64"]
     if with_oracle:
         import oracle as O
 
@@ -651,6 +656,7 @@ def energy_bench(F, ctx, evals, with_oracle, workers=8, batches=(0, 2, 3, 6)):
         out["oracle_s_per_eval"] = time.perf_counter() - t0
         out["f64_rel_err_vs_oracle"] = abs(res["f64"] - e_ref) / abs(e_ref)
         out["tf32x3_rel_err_vs_oracle"] = abs(res["tf32x3"] - e_ref) / abs(e_ref)
+        out["f16x3_rel_err_vs_oracle"] = abs(res["f16x3"] - e_ref) / abs(e_ref)
     for c in ctxs[1:]:
         c.synchronize()
         c.close()
