@@ -5,13 +5,17 @@
 // on the block's parity bits).
 //
 // Two kernels share the job format.  The staged kernel (used when every
-// source row of a job starts 16-byte aligned): each persistent CTA
-// copies the contiguous source rows of upcoming tiles with cp.async.bulk
-// into a PERM_STAGES-deep shared-memory ring (completion on an mbarrier); a
-// dedicated producer warp runs ahead and eight consumer warps write tiles out
-// along the destination's contiguous direction, releasing ring slots through
-// a second set of mbarriers (no block-wide synchronisation in the loop).  The
-// TMA engine keeps the HBM reads in flight without holding registers.  The fallback kernel stages through registers:
+// source row of a job starts 16-byte aligned): each persistent CTA takes a
+// contiguous range of tiles; two producer warps copy the source rows of
+// upcoming tiles into a PERM_STAGES-deep shared-memory ring with 16-byte
+// cp.async copies spread over their lanes (consecutive lanes on consecutive
+// chunks of a row; completion tracked on an mbarrier), and eight consumer
+// warps write tiles out along the destination's contiguous direction,
+// releasing ring slots through a second set of mbarriers (no block-wide
+// synchronisation in the loop).  The copies hold no registers while in
+// flight.  (One bulk copy per row was tried first: a few hundred cycles per
+// request per SM left the rows of 128 to 512 bytes far below the HBM
+// bandwidth.)  The fallback kernel stages through registers:
 // Each CTA tile covers PERM_TO rows of the O group (destination-fast legs)
 // times PERM_TI elements of the I group (the source's contiguous suffix) for
 // one batch index.  Loads run along I (coalesced in the source); stores run
@@ -222,7 +226,7 @@ __global__ void __launch_bounds__(PT) perm_kernel(const PermJob* __restrict__ jo
 
 
 // ---------------------------------------------------------------------------------
-// TMA-staged sign-permute
+// Shared-memory-staged sign-permute
 struct StageMeta {
   int64_t baseD;
   int32_t nrows, ncols;
@@ -231,64 +235,125 @@ struct StageMeta {
   int32_t iwrite, qw, qp, wsuf;
 };
 
+constexpr int SPT = 256;                 // threads of the staged kernel
+constexpr int SPW = SPT / 32;            // its warps
+constexpr int PERM_AHEAD = PERM_STAGES - 1;  // tiles in flight while one is written out
+
 template <typename Tin>
 struct StagedCfg {
   static constexpr int V = 16 / (int)sizeof(Tin);
   static constexpr int TE = PERM_TILE_BYTES / (int)sizeof(Tin);
   static constexpr int MAXTI = TE / 8;
   static constexpr int STAGE_ELEMS = TE + PERM_MAX_ROWS * V;
-  static constexpr int BYTES = PERM_STAGES * STAGE_ELEMS * (int)sizeof(Tin) + PERM_STAGES * PERM_MAX_ROWS * 4 +
-                               PERM_STAGES * MAXTI * 4 + PERM_STAGES * MAXTI * 2 * 2 +
-                               PERM_STAGES * (int)sizeof(StageMeta) + 2 * PERM_STAGES * 8 + 2 * (int)sizeof(PermJob) +
-                               128;
+  static constexpr int BYTES = PERM_STAGES * STAGE_ELEMS * (int)sizeof(Tin) + PERM_STAGES * PERM_MAX_ROWS * (8 + 4) +
+                               PERM_STAGES * MAXTI * (4 + 2 + 2) + PERM_STAGES * (int)sizeof(StageMeta) + 128;
 };
 
-// Issue the bulk copies of tile t (producer warp; `j` is the tile's job,
-// cached in shared memory by the caller).
-template <typename Tin>
-__device__ __forceinline__ void staged_issue(const PermJob* j, int64_t t, const Tin* __restrict__ src, Tin* buf,
-                                             int32_t* rowD, int32_t* colD, int16_t* colS, int16_t* colP,
-                                             StageMeta* meta, uint64_t* bar, int lane) {
-  using Cfg = StagedCfg<Tin>;
-  const int nI = j->nI, nO = j->nO;
+// Where tile t of job j lies: its I and O ranges and the source and
+// destination offsets of its batch index.  32-bit index arithmetic unless the
+// job's tile count needs more.
+struct TileGeo {
+  int64_t bS, bD;
+  int32_t i0, o0, ncols, nrows;
+};
+
+__device__ __forceinline__ TileGeo tile_geo(const PermJob* __restrict__ j, int64_t t) {
+  TileGeo g;
   const int64_t local = t - j->tile_begin;
-  const int64_t per_b = (int64_t)j->tiles_i * j->tiles_o;
-  const int64_t b = local / per_b;
-  const int rem = (int)(local - b * per_b);
-  const int i0 = (rem % j->tiles_i) * j->ti, o0 = (rem / j->tiles_i) * j->tr;
-  const int ncols = min(j->ti, j->PI - i0), nrows = min(j->tr, j->PO - o0);
+  const int32_t tiles_i = j->tiles_i, per_b = tiles_i * j->tiles_o;
+  int64_t b64;
+  int32_t rem;
+  if (local <= INT32_MAX) {
+    const int32_t l32 = (int32_t)local, b32 = l32 / per_b;
+    rem = l32 - b32 * per_b;
+    b64 = b32;
+  } else {
+    b64 = local / per_b;
+    rem = (int32_t)(local - b64 * per_b);
+  }
+  const int32_t to = rem / tiles_i;
+  g.i0 = (rem - to * tiles_i) * j->ti;
+  g.o0 = to * j->tr;
+  g.ncols = min(j->ti, j->PI - g.i0);
+  g.nrows = min(j->tr, j->PO - g.o0);
   int64_t bS = j->src_off, bD = j->dst_off;
-  {
-    int64_t x = b;
-    for (int q = nI + nO + j->nB - 1; q >= nI + nO; --q) {
-      const int64_t idx = x % j->dim[q];
-      x /= j->dim[q];
+  const int nIO = j->nI + j->nO;
+  if (b64 <= INT32_MAX) {
+    int32_t x = (int32_t)b64;
+    for (int q = nIO + j->nB - 1; q >= nIO; --q) {
+      const int32_t d = j->dim[q], qq = x / d, idx = x - qq * d;
+      x = qq;
+      bS += (int64_t)idx * j->sstr[q];
+      bD += (int64_t)idx * j->dstr[q];
+    }
+  } else {
+    int64_t x = b64;
+    for (int q = nIO + j->nB - 1; q >= nIO; --q) {
+      const int64_t d = j->dim[q], qq = x / d, idx = x - qq * d;
+      x = qq;
       bS += idx * j->sstr[q];
       bD += idx * j->dstr[q];
     }
   }
-  const int stride = j->ti + Cfg::V;
-  int64_t rsrc[PERM_MAX_ROWS / 32];
-  uint32_t mine = 0;
-#pragma unroll
-  for (int u = 0; u < PERM_MAX_ROWS / 32; ++u) {
-    const int r = lane + 32 * u;
-    rsrc[u] = 0;
-    if (r >= nrows) continue;
-    int x = o0 + r;
+  g.bS = bS;
+  g.bD = bD;
+  return g;
+}
+
+// The job of tile t, found by each warp for itself (tiles only move forward
+// within a CTA, so the job index does too; next_begin caches where the next
+// job starts, so most tiles touch no table).
+__device__ __forceinline__ int find_job(const PermJob* __restrict__ jobs, int njobs, int64_t tiles, int64_t t, int nj,
+                                        int64_t& next_begin, int lane) {
+  if (nj >= 0 && t < next_begin) return nj;
+  if (nj < 0) {
+    if (lane == 0) {
+      int lo = 0, hi = njobs - 1;
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (jobs[mid].tile_begin <= t)
+          lo = mid;
+        else
+          hi = mid - 1;
+      }
+      nj = lo;
+    }
+    nj = __shfl_sync(0xffffffffu, nj, 0);
+  } else {
+    // forward scan, 32 jobs per round (tile_begin increases with the job)
+    for (;;) {
+      const int q = nj + 1 + lane;
+      const unsigned ball = __ballot_sync(0xffffffffu, q < njobs && jobs[q].tile_begin <= t);
+      if (ball == 0) break;
+      nj += 32 - __clz(ball);
+      if (ball != 0xffffffffu) break;
+    }
+  }
+  next_begin = nj + 1 < njobs ? jobs[nj + 1].tile_begin : tiles;
+  return nj;
+}
+
+// The tables of tile t in its stage (every thread takes a share: row i by
+// thread i, columns from the middle of the block on).
+template <typename Tin>
+__device__ __forceinline__ void stage_tables(const PermJob* __restrict__ j, const TileGeo& g, int64_t* rowS,
+                                             int32_t* rowD, int32_t* colD, int16_t* colS, int16_t* colP,
+                                             StageMeta* meta, int tid) {
+  const int nI = j->nI, nO = j->nO;
+  for (int r = tid; r < g.nrows; r += SPT) {
+    int32_t x = g.o0 + r;
     int64_t rs = 0;
     int32_t rd = 0;
     for (int q = nI + nO - 1; q >= nI; --q) {
-      const int d = j->dim[q];
-      const int qq = x / d, idx = x - qq * d;
+      const int32_t d = j->dim[q], qq = x / d, idx = x - qq * d;
       x = qq;
       rs += (int64_t)idx * j->sstr[q];
       rd += idx * (int32_t)j->dstr[q];
     }
+    rowS[r] = rs;
     rowD[r] = rd;
-    rsrc[u] = rs;
-    mine += (uint32_t)(ncols * sizeof(Tin));
   }
+  const int tc = (tid + SPT / 2) & (SPT - 1);
   int32_t qp = 1;
   if (j->iwrite) {
     // the whole I group is in the tile (i0 = 0).  W (the destination run):
@@ -296,20 +361,19 @@ __device__ __forceinline__ void staged_issue(const PermJob* j, int64_t t, const 
     // destination strides are the run's own mixed radix).  P (the other I
     // legs, last fastest): colP[p] = source column, colD[p] = destination
     // offset of the p-th combination.
-    for (int q = lane; q < j->qw; q += 32) {
+    const int32_t wmask = j->wmask, qw = j->qw;
+    for (int q = tc; q < qw; q += SPT) {
       int32_t cs = 0;
       for (int l = 0; l < nI; ++l)
-        if (j->wmask >> l & 1) cs += ((q / (int32_t)j->dstr[l]) % j->dim[l]) * (int32_t)j->sstr[l];
+        if (wmask >> l & 1) cs += ((q / (int32_t)j->dstr[l]) % j->dim[l]) * (int32_t)j->sstr[l];
       colS[q] = (int16_t)cs;
     }
-    qp = ncols / j->qw;
-    for (int p = lane; p < qp; p += 32) {
-      int x = p;
-      int32_t cs = 0, dd = 0;
+    qp = g.ncols / qw;
+    for (int p = tc; p < qp; p += SPT) {
+      int32_t x = p, cs = 0, dd = 0;
       for (int l = nI - 1; l >= 0; --l) {
-        if (j->wmask >> l & 1) continue;
-        const int d = j->dim[l];
-        const int qq = x / d, idx = x - qq * d;
+        if (wmask >> l & 1) continue;
+        const int32_t d = j->dim[l], qq = x / d, idx = x - qq * d;
         x = qq;
         cs += idx * (int32_t)j->sstr[l];
         dd += idx * (int32_t)j->dstr[l];
@@ -318,22 +382,20 @@ __device__ __forceinline__ void staged_issue(const PermJob* j, int64_t t, const 
       colD[p] = dd;
     }
   } else {
-    for (int c = lane; c < ncols; c += 32) {
-      int x = i0 + c;
-      int32_t dd = 0;
+    for (int c = tc; c < g.ncols; c += SPT) {
+      int32_t x = g.i0 + c, dd = 0;
       for (int q = nI - 1; q >= 0; --q) {
-        const int d = j->dim[q];
-        const int qq = x / d, idx = x - qq * d;
+        const int32_t d = j->dim[q], qq = x / d, idx = x - qq * d;
         x = qq;
         dd += idx * (int32_t)j->dstr[q];
       }
       colD[c] = dd;
     }
   }
-  if (lane == 0) {
-    meta->baseD = bD;
-    meta->nrows = nrows;
-    meta->ncols = ncols;
+  if (tid == 0) {
+    meta->baseD = g.bD;
+    meta->nrows = g.nrows;
+    meta->ncols = g.ncols;
     meta->ti = j->ti;
     meta->fast_i = j->store_fast_i;
     meta->sign = j->sign;
@@ -343,108 +405,69 @@ __device__ __forceinline__ void staged_issue(const PermJob* j, int64_t t, const 
     meta->qp = qp;
     meta->wsuf = j->wsuf;
   }
-  // order this warp's earlier generic reads of the stage before the async writes
-  fence_proxy_async_smem();
-  mbar_expect_tx(bar, mine);
-#pragma unroll
-  for (int u = 0; u < PERM_MAX_ROWS / 32; ++u) {
-    const int r = lane + 32 * u;
-    if (r < nrows) bulk_g2s(buf + r * stride, src + bS + rsrc[u] + i0, (uint32_t)(ncols * sizeof(Tin)), bar);
-  }
 }
 
-constexpr int SPW = 8;                    // consumer warps of the staged kernel
-constexpr int SPP = 2;                    // producer warps (alternate tiles)
-constexpr int SPT = 32 * (SPW + SPP);
+// The tile's source rows into its stage: 16-byte chunks, consecutive threads
+// on consecutive chunks of a row (rows start 16-byte aligned, their lengths
+// are multiples of 16 bytes).
+template <typename Tin>
+__device__ __forceinline__ void stage_copies(const Tin* __restrict__ src, const TileGeo& g, int ti, Tin* buf,
+                                             const int64_t* rowS, int tid) {
+  constexpr int V = StagedCfg<Tin>::V;
+  const int cpr = g.ncols / V, stride = ti + V, nch = g.nrows * cpr;
+  const Tin* sb = src + g.bS + g.i0;
+  for (int q = tid; q < nch; q += SPT) {
+    const int r = q / cpr, c = q - r * cpr;
+    cp_async16(buf + r * stride + c * V, sb + rowS[r] + c * V);
+  }
+}
 
 template <typename Tin, int MODE>
 __global__ void __launch_bounds__(SPT) perm_staged_kernel(const PermJob* __restrict__ jobs, int njobs, int64_t tiles,
                                                           const Tin* __restrict__ src, const Tin* __restrict__ src1,
-                                                          void* __restrict__ dst0, void* __restrict__ dst1, int* err) {
+                                                          void* __restrict__ dst0, void* __restrict__ dst1) {
   using Cfg = StagedCfg<Tin>;
   extern __shared__ uint8_t sm_raw[];
   uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(sm_raw) + 127) & ~uintptr_t(127));
   Tin* buf = reinterpret_cast<Tin*>(sm);
-  int32_t* rowD = reinterpret_cast<int32_t*>(buf + PERM_STAGES * Cfg::STAGE_ELEMS);
+  int64_t* rowS = reinterpret_cast<int64_t*>(buf + PERM_STAGES * Cfg::STAGE_ELEMS);
+  int32_t* rowD = reinterpret_cast<int32_t*>(rowS + PERM_STAGES * PERM_MAX_ROWS);
   int32_t* colD = rowD + PERM_STAGES * PERM_MAX_ROWS;
   int16_t* colS = reinterpret_cast<int16_t*>(colD + PERM_STAGES * Cfg::MAXTI);
   int16_t* colP = colS + PERM_STAGES * Cfg::MAXTI;
   StageMeta* meta = reinterpret_cast<StageMeta*>(colP + PERM_STAGES * Cfg::MAXTI);
-  uint64_t* full = reinterpret_cast<uint64_t*>(meta + PERM_STAGES);
-  uint64_t* empty = full + PERM_STAGES;
-  PermJob* sjob_all = reinterpret_cast<PermJob*>(empty + PERM_STAGES);  // each producer's copy of its job
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  constexpr int NCW = SPW;  // consumer warps
-  if (tid == 0) {
-    for (int s = 0; s < PERM_STAGES; ++s) {
-      mbar_init(&full[s], 32);
-      mbar_init(&empty[s], NCW);
-    }
-    fence_mbar_init();
-  }
-  __syncthreads();
-  const int64_t stride_t = gridDim.x;
-  if (warp >= NCW) {
-    // ---------------- producer warps (tiles k = p, p + SPP, ...) ----------------
-    // this CTA's tiles increase, so the job index only moves forward
-    const int pw = warp - NCW;
-    PermJob* sjob = sjob_all + pw;
-    int cur = -1;
-    bool failed = false;
-    int64_t k = pw;
-    for (;; k += SPP) {
-      const int64_t t = blockIdx.x + k * stride_t;
-      if (t >= tiles) break;
-      int nj = cur < 0 ? 0 : cur;
-      if (lane == 0) {
-        if (cur < 0) {
-          int lo = 0, hi = njobs - 1;
-          while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (jobs[mid].tile_begin <= t)
-              lo = mid;
-            else
-              hi = mid - 1;
-          }
-          nj = lo;
-        } else {
-          while (nj + 1 < njobs && jobs[nj + 1].tile_begin <= t) ++nj;
-        }
-      }
-      nj = __shfl_sync(0xffffffffu, nj, 0);
-      if (nj != cur) {
-        const uint64_t* from = reinterpret_cast<const uint64_t*>(jobs + nj);
-        uint64_t* to = reinterpret_cast<uint64_t*>(sjob);
-        for (int w = lane; w < (int)(sizeof(PermJob) / 8); w += 32) to[w] = from[w];
-        __syncwarp();
-        cur = nj;
-      }
+  // Each CTA takes one contiguous range of tiles (the ranges differ in length
+  // by at most one), so that consecutive tiles mostly belong to the same job.
+  const int64_t t_first = (int64_t)blockIdx.x * tiles / gridDim.x;
+  const int64_t n = ((int64_t)blockIdx.x + 1) * tiles / gridDim.x - t_first;
+  int nj = -1;
+  int64_t next_begin = 0;
+  // Tile k + PERM_AHEAD is staged (tables, then copies) while tile k is
+  // written out: every thread commits one cp.async group per tile, so that
+  // waiting for all but the PERM_AHEAD newest groups completes tile k.
+  auto stage = [&](int64_t k) {
+    if (k < n) {
+      const int64_t t = t_first + k;
+      nj = find_job(jobs, njobs, tiles, t, nj, next_begin, lane);
+      const PermJob* __restrict__ j = jobs + nj;
       const int s = (int)(k % PERM_STAGES);
-      const uint32_t par = (uint32_t)((k / PERM_STAGES) & 1);
-      bool ok = true;
-      if (lane == 0) ok = mbar_wait(&empty[s], par ^ 1, err);
-      if (!__shfl_sync(0xffffffffu, ok ? 1 : 0, 0)) {
-        failed = true;
-        break;
-      }
-      staged_issue<Tin>(sjob, t, sjob->src_sel ? src1 : src, buf + s * Cfg::STAGE_ELEMS, rowD + s * PERM_MAX_ROWS, colD + s * Cfg::MAXTI,
-                        colS + s * Cfg::MAXTI, colP + s * Cfg::MAXTI, meta + s, &full[s], lane);
+      const TileGeo g = tile_geo(j, t);
+      stage_tables<Tin>(j, g, rowS + s * PERM_MAX_ROWS, rowD + s * PERM_MAX_ROWS, colD + s * Cfg::MAXTI,
+                        colS + s * Cfg::MAXTI, colP + s * Cfg::MAXTI, meta + s, tid);
+      __syncthreads();  // rowS of the stage is complete
+      stage_copies<Tin>(j->src_sel ? src1 : src, g, j->ti, buf + s * Cfg::STAGE_ELEMS, rowS + s * PERM_MAX_ROWS, tid);
     }
-    // after an early exit, wait for this producer's copies still in flight (on
-    // a normal exit the consumers wait for every issued tile themselves)
-    if (failed && lane == 0) {
-      for (int64_t q = k - SPP; q >= 0 && q >= k - PERM_STAGES - SPP; q -= SPP)
-        mbar_wait(&full[q % PERM_STAGES], (uint32_t)((q / PERM_STAGES) & 1), err, false);
-    }
-    return;
-  }
-  // ---------------- consumer warps ----------------
-  for (int64_t k = 0;; ++k) {
-    const int64_t t = blockIdx.x + k * stride_t;
-    if (t >= tiles) break;
+    cp_async_commit();
+  };
+  for (int k = 0; k < PERM_AHEAD; ++k) stage(k);
+  for (int64_t k = 0; k < n; ++k) {
+    // the stage of tile k + PERM_AHEAD was last read for tile k - 1, before
+    // the barrier that ended the previous iteration
+    stage(k + PERM_AHEAD);
+    cp_async_wait_group<PERM_AHEAD>();
+    __syncthreads();  // every thread's copies of tile k have landed
     const int s = (int)(k % PERM_STAGES);
-    const uint32_t par = (uint32_t)((k / PERM_STAGES) & 1);
-    if (!mbar_wait(&full[s], par, err)) break;
     const StageMeta m = meta[s];
     const Tin* tb = buf + s * Cfg::STAGE_ELEMS;
     const int32_t* rd = rowD + s * PERM_MAX_ROWS;
@@ -465,7 +488,7 @@ __global__ void __launch_bounds__(SPT) perm_staged_kernel(const PermJob* __restr
       const int sub = grouped ? lane >> lg : 0;
       const int q0 = grouped ? (lane & (units - 1)) * vq : lane * vq;
       const int qstep = grouped ? m.qw : 32 * vq;
-      for (int rp0 = warp * per; rp0 < npairs; rp0 += NCW * per) {
+      for (int rp0 = warp * per; rp0 < npairs; rp0 += SPW * per) {
         const int rp = rp0 + sub;
         if (rp >= npairs) continue;
         int r, p;
@@ -494,7 +517,7 @@ __global__ void __launch_bounds__(SPT) perm_staged_kernel(const PermJob* __restr
       }
     } else if (m.vec4 && m.fast_i) {
       // quads of consecutive I elements, contiguous in the destination
-      for (int r = warp; r < m.nrows; r += NCW) {
+      for (int r = warp; r < m.nrows; r += SPW) {
         const int64_t base = m.baseD + rd[r];
         for (int c4 = 4 * lane; c4 < m.ncols; c4 += 128) {
           const Tin* x = tb + r * stride + c4;
@@ -502,12 +525,12 @@ __global__ void __launch_bounds__(SPT) perm_staged_kernel(const PermJob* __restr
         }
       }
     } else if (m.fast_i) {
-      for (int r = warp; r < m.nrows; r += NCW) {
+      for (int r = warp; r < m.nrows; r += SPW) {
         const int64_t base = m.baseD + rd[r];
         for (int c = lane; c < m.ncols; c += 32) put<Tin, MODE>(dst0, dst1, base + cd[c], sgn * tb[r * stride + c]);
       }
     } else {
-      for (int c0 = warp * Cfg::V; c0 < m.ncols; c0 += NCW * Cfg::V) {
+      for (int c0 = warp * Cfg::V; c0 < m.ncols; c0 += SPW * Cfg::V) {
         for (int r = lane; r < m.nrows; r += 32) {
           Tin v[Cfg::V];
           if constexpr (sizeof(Tin) == 4) {
@@ -524,8 +547,7 @@ __global__ void __launch_bounds__(SPT) perm_staged_kernel(const PermJob* __restr
         }
       }
     }
-    __syncwarp();
-    if (lane == 0) mbar_arrive(&empty[s]);
+    __syncthreads();  // tile k's stage is free
   }
 }
 
@@ -541,8 +563,7 @@ static cudaError_t go_staged(ftn_ctx ctx, const PermJob* d_jobs, int njobs, int6
   if (grid > cap) grid = cap;
   perm_staged_kernel<Tin, MODE><<<(unsigned)grid, SPT, Cfg::BYTES, ctx->stream>>>(d_jobs, njobs, tiles,
                                                                                  (const Tin*)src, (const Tin*)src1,
-                                                                                 dst0, dst1,
-                                                                                 ctx->dev_err);
+                                                                                 dst0, dst1);
   return cudaGetLastError();
 }
 

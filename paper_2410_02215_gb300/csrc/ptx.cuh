@@ -47,9 +47,13 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   return ok != 0;
 }
 
+constexpr uint64_t BAIL_CHECK_NS = 20000;  // waits shorter than this never read the error flag
+
 // Wait for the phase with the given parity.  Returns false after the time
-// limit (recording DEV_ERR_TIMEOUT in *err) or, when bail is set, as soon as
-// another thread has recorded an error.
+// limit (recording DEV_ERR_TIMEOUT in *err) or, when bail is set, once
+// another thread has recorded an error.  The error flag lives in global
+// memory, so it is read only after the wait has lasted BAIL_CHECK_NS: a read
+// on every round would delay noticing the phase by a memory round trip.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* err, bool bail = true) {
   if (mbar_try_wait(bar, parity)) return true;
   const uint64_t t0 = globaltimer();
@@ -57,11 +61,12 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* e
 #pragma unroll 1
     for (int i = 0; i < 32; ++i)
       if (mbar_try_wait(bar, parity)) return true;
-    if (bail && *reinterpret_cast<volatile int*>(err) != 0) return false;
-    if (globaltimer() - t0 > WAIT_LIMIT_NS) {
+    const uint64_t dt = globaltimer() - t0;
+    if (dt > WAIT_LIMIT_NS) {
       atomicCAS(err, 0, 1);
       return false;
     }
+    if (bail && dt > BAIL_CHECK_NS && *reinterpret_cast<volatile int*>(err) != 0) return false;
   }
 }
 
@@ -88,6 +93,17 @@ __device__ __forceinline__ void bulk_g2s(void* smem_dst, const void* gsrc, uint3
                    smem_u32(smem_dst)),
                "l"(reinterpret_cast<uint64_t>(gsrc)), "r"(bytes), "r"(smem_u32(bar))
                : "memory");
+}
+// 16-byte copy global -> shared through L2 (both addresses 16-byte aligned).
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gsrc) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(smem_dst)), "l"(gsrc) : "memory");
+}
+// Close this thread's group of cp.async copies issued since the last commit.
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+// Wait until at most N of this thread's committed groups are still in flight.
+template <int N>
+__device__ __forceinline__ void cp_async_wait_group() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 __device__ __forceinline__ void fence_proxy_async_smem() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
