@@ -17,6 +17,7 @@
 // keeping the large products apart from the two small cross terms cuts the
 // number of roundings applied to the large accumulator by three.
 #include <algorithm>
+#include <cstddef>
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
@@ -184,6 +185,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tslot;
+  // Each CTA takes one contiguous range of tiles (the ranges differ in length
+  // by at most one): consecutive tiles of a CTA mostly share their problem,
+  // so the epilogue keeps its records and column offsets in registers.
+  const int64_t t_begin = (int64_t)blockIdx.x * P.tiles / gridDim.x;
+  const int64_t t_end = ((int64_t)blockIdx.x + 1) * P.tiles / gridDim.x;
 
   if (warp == 0) {
     if (lane == 0) {
@@ -194,10 +200,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
       bool ok = true;
       int cur = -1, fenced = -1;
       TileEnt nx;
-      if (blockIdx.x < P.tiles) tile_at<BN>(P, blockIdx.x, cur, nx);
-      for (int64_t t = blockIdx.x; t < P.tiles && ok; t += gridDim.x) {
+      if (t_begin < t_end) tile_at<BN>(P, t_begin, cur, nx);
+      for (int64_t t = t_begin; t < t_end && ok; ++t) {
         const TileEnt e = nx;  // this tile; the next one's entry is fetched while this one is issued
-        if (t + gridDim.x < P.tiles) tile_at<BN>(P, t + gridDim.x, cur, nx);
+        if (t + 1 < t_end) tile_at<BN>(P, t + 1, cur, nx);
         const int nk = (e.K + Cfg::KB - 1) / Cfg::KB;
         const int pi = e.pi;
         const CUtensorMap *ma = &P.a_hi[pi & 1], *mb = &P.b_hi[pi & 1], *mal = &P.a_lo[pi & 1],
@@ -253,10 +259,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
       bool ok = true;
       int cur = -1;
       TileEnt nx;
-      if (blockIdx.x < P.tiles) tile_at<BN>(P, blockIdx.x, cur, nx);
-      for (int64_t t = blockIdx.x; t < P.tiles && ok; t += gridDim.x) {
+      if (t_begin < t_end) tile_at<BN>(P, t_begin, cur, nx);
+      for (int64_t t = t_begin; t < t_end && ok; ++t) {
         const TileEnt e = nx;
-        if (t + gridDim.x < P.tiles) tile_at<BN>(P, t + gridDim.x, cur, nx);
+        if (t + 1 < t_end) tile_at<BN>(P, t + 1, cur, nx);
         const int nk = (e.K + Cfg::KB - 1) / Cfg::KB;
         if (nk == 0) continue;
         if (!mbar_wait(&tempty[acc], acc_phase ^ 1, P.err)) break;
@@ -324,53 +330,163 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
     uint32_t j = 0;  // tiles with K > 0 seen so far (all sets count them)
     const bool c16 = ((uintptr_t)P.C & 15) == 0;  // 16-byte vector stores need an aligned base
     int cur = -1;
-    TileEnt nx;
-    if (blockIdx.x < P.tiles) tile_at<BN>(P, blockIdx.x, cur, nx);
-    for (int64_t t = blockIdx.x; t < P.tiles; t += gridDim.x) {
+    // tile entries two tiles ahead (a set writes every other tile out)
+    TileEnt nx, nx2;
+    if (t_begin < t_end) tile_at<BN>(P, t_begin, cur, nx);
+    if (t_begin + 1 < t_end) tile_at<BN>(P, t_begin + 1, cur, nx2);
+    constexpr int NCH = BN / Cfg::CW;
+    // The problem records of the last tile written out, kept in registers
+    // while the tiles stay on the same problem and first column (in a
+    // grouped launch most consecutive tiles do): lane l < MAXR holds row leg
+    // l, MAXR <= l < 2 MAXR column leg l - MAXR, lanes 0..9 also the scalars
+    // below (32-bit words of the record); mi: each chunk's member.
+    int key_prob = -1, key_n0 = -1;
+    int gm = 0, pM = 0;
+    int32_t ldim[NCH];
+    int64_t lstr[NCH];
+    // column side of each chunk (independent of the tile's rows), kept with
+    // the records: column offset, valid columns, store mode, sign, the
+    // member's output offset, rows and row legs; rows_same: every chunk's
+    // member has the first one's row legs (one row expansion per tile)
+    int64_t cp_c[NCH], coff_c[NCH];
+    int cn_c[NCH], fl_c[NCH], mM_c[NCH], nrl_c[NCH];
+    float sg_c[NCH];
+    bool rows_same = true;
+    for (int64_t t = t_begin; t < t_end; ++t) {
       const TileEnt e = nx;
-      if (t + gridDim.x < P.tiles) tile_at<BN>(P, t + gridDim.x, cur, nx);
+      nx = nx2;
+      if (t + 2 < t_end) tile_at<BN>(P, t + 2, cur, nx2);
       const int m0 = e.m0, n0 = e.n0;
-      const GemmProb& p = P.probs[e.prob];
+      const GemmProb* __restrict__ pp = P.probs + e.prob;
       const int nk = (e.K + Cfg::KB - 1) / Cfg::KB;
       const int acc = (int)(j & 1);
       if (nk > 0) ++j;
       if (nk > 0 ? acc != set : set != 0) continue;
       const int row = m0 + 32 * q + lane;
-      const int nrows = p.M - (m0 + 32 * q) < 32 ? p.M - (m0 + 32 * q) : 32;
       // Per chunk of CW columns: its problem (a member of a merged group),
       // valid columns, this lane's row and column offsets, sign and store
-      // mode -- read from the problem table before waiting for the
-      // accumulator, so the table's latency overlaps the MMAs.
-      constexpr int NCH = BN / Cfg::CW;
-      int64_t rp_c[NCH], cp_c[NCH];
-      int cn_c[NCH], fl_c[NCH];
-      float sg_c[NCH];
-      {
-        const GemmProb* last = nullptr;
-        int64_t rpl = 0;
+      // mode.  When the tile's problem or first column differs from the last
+      // one's, the records are read again, spread over the lanes and issued
+      // together in two round trips (the group's member ends; then every
+      // chunk's leg tables and scalars) before waiting for the accumulator:
+      // walking the table with dependent reads for every tile cost more than
+      // the tile's stores.
+      int64_t rp_c[NCH];
+      if (e.prob != key_prob || n0 != key_n0) {
+        key_prob = e.prob;
+        key_n0 = n0;
+        gm = pp->gmerge;
+        pM = pp->M;
+        const int gc = pp->grp_count;
+        const bool in_tab = e.prob + lane < P.nprobs;
+        const int mg = in_tab ? pp[lane].gcol : 0, mn = in_tab ? pp[lane].N : 0;
+        int mi[NCH];
+        int32_t wsc[NCH];
 #pragma unroll
         for (int ch = 0; ch < NCH; ++ch) {
-          const GemmProb* mp = &p;
-          int lcol = n0 + ch * Cfg::CW;
-          if (p.gmerge) {
-            for (int qq = 1; qq < p.grp_count && lcol >= mp->gcol + mp->N; ++qq) ++mp;
-            lcol -= mp->gcol;
+          const int lcol = n0 + ch * Cfg::CW;
+          int m = 0;
+          if (gm) {
+            if (gc <= 32) {
+              // members are in column order: those ending at or before lcol
+              m = __popc(__ballot_sync(0xffffffffu, lane < gc - 1 && lcol >= mg + mn));
+            } else {
+              const GemmProb* mp = pp;
+              for (int qq = 1; qq < gc && lcol >= mp->gcol + mp->N; ++qq) ++mp;
+              m = (int)(mp - pp);
+            }
           }
-          const int cn = mp->N - lcol < Cfg::CW ? mp->N - lcol : Cfg::CW;
+          mi[ch] = m;
+        }
+        static_assert(2 * MAXR <= 32, "one warp holds the row and column legs");
+        constexpr int W_COFF = (int)(offsetof(GemmProb, c_off) / 4), W_M = (int)(offsetof(GemmProb, M) / 4),
+                      W_N = (int)(offsetof(GemmProb, N) / 4), W_SIGN = (int)(offsetof(GemmProb, c_sign) / 4),
+                      W_NRL = (int)(offsetof(GemmProb, nrl) / 4), W_NCL = (int)(offsetof(GemmProb, ncl) / 4),
+                      W_EROWS = (int)(offsetof(GemmProb, epi_rows) / 4), W_VEC4 = (int)(offsetof(GemmProb, vec4) / 4),
+                      W_GCOL = (int)(offsetof(GemmProb, gcol) / 4);
+        const int woff = lane == 0   ? W_COFF
+                         : lane == 1 ? W_COFF + 1
+                         : lane == 2 ? W_M
+                         : lane == 3 ? W_N
+                         : lane == 4 ? W_SIGN
+                         : lane == 5 ? W_NRL
+                         : lane == 6 ? W_NCL
+                         : lane == 7 ? W_EROWS
+                         : lane == 8 ? W_VEC4
+                                     : W_GCOL;
+#pragma unroll
+        for (int ch = 0; ch < NCH; ++ch) {
+          const GemmProb* __restrict__ mp = pp + mi[ch];
+          ldim[ch] = 1;
+          lstr[ch] = 0;
+          wsc[ch] = 0;
+          if (lane < MAXR) {
+            ldim[ch] = mp->rdim[lane];
+            lstr[ch] = mp->rstr[lane];
+          } else if (lane < 2 * MAXR) {
+            ldim[ch] = mp->cdim[lane - MAXR];
+            lstr[ch] = mp->cstr[lane - MAXR];
+          }
+          if (lane < 10) wsc[ch] = reinterpret_cast<const int32_t*>(mp)[woff];
+        }
+        const uint32_t fm = 0xffffffffu;
+        rows_same = true;
+#pragma unroll
+        for (int ch = 0; ch < NCH; ++ch) {
+          coff_c[ch] = (int64_t)(uint32_t)__shfl_sync(fm, wsc[ch], 0) | ((int64_t)__shfl_sync(fm, wsc[ch], 1) << 32);
+          mM_c[ch] = __shfl_sync(fm, wsc[ch], 2);
+          const int mN = __shfl_sync(fm, wsc[ch], 3);
+          const int csign = __shfl_sync(fm, wsc[ch], 4);
+          nrl_c[ch] = __shfl_sync(fm, wsc[ch], 5);
+          const int ncl = __shfl_sync(fm, wsc[ch], 6), erows = __shfl_sync(fm, wsc[ch], 7);
+          const int vec4 = __shfl_sync(fm, wsc[ch], 8), gcol = __shfl_sync(fm, wsc[ch], 9);
+          const int lcol = n0 + ch * Cfg::CW - (gm ? gcol : 0);
+          const int cn = mN - lcol < Cfg::CW ? mN - lcol : Cfg::CW;
           cn_c[ch] = cn;
-          rp_c[ch] = cp_c[ch] = 0;
+          cp_c[ch] = 0;
           sg_c[ch] = 1.0f;
           fl_c[ch] = 0;
           if (cn > 0) {
-            if (mp != last) {
-              last = mp;
-              rpl = row < mp->M ? mp->c_off + expand_index32(row, mp->nrl, mp->rdim, mp->rstr) : 0;
+            int xc = lcol + lane;
+            int64_t co = 0;
+            for (int l = ncl - 1; l >= 0; --l) {
+              const int d = __shfl_sync(fm, ldim[ch], MAXR + l);
+              const int64_t st = __shfl_sync(fm, lstr[ch], MAXR + l);
+              const int qq = xc / d;
+              co += (int64_t)(xc - qq * d) * st;
+              xc = qq;
             }
-            rp_c[ch] = rpl;
-            cp_c[ch] = lane < Cfg::CW && lane < cn ? expand_index32(lcol + lane, mp->ncl, mp->cdim, mp->cstr) : 0;
-            sg_c[ch] = (float)mp->c_sign;
-            fl_c[ch] = (mp->vec4 && c16 ? 1 : 0) | (mp->epi_rows ? 2 : 0);
+            cp_c[ch] = lane < Cfg::CW && lane < cn ? co : 0;
+            sg_c[ch] = (float)csign;
+            fl_c[ch] = (vec4 && c16 ? 1 : 0) | (erows ? 2 : 0);
           }
+          if (ch > 0)
+            rows_same = rows_same && nrl_c[ch] == nrl_c[0] &&
+                        __all_sync(fm, lane >= MAXR || (ldim[ch] == ldim[0] && lstr[ch] == lstr[0]));
+        }
+      }
+      const int nrows = pM - (m0 + 32 * q) < 32 ? pM - (m0 + 32 * q) : 32;
+      {
+        // row side: this lane's row within the member's output block
+        const uint32_t fm = 0xffffffffu;
+        int64_t r0 = 0;
+#pragma unroll
+        for (int ch = 0; ch < NCH; ++ch) {
+          rp_c[ch] = 0;
+          if (cn_c[ch] <= 0) continue;
+          if (ch == 0 || !rows_same) {
+            int x = row;
+            int64_t ro = 0;
+            for (int l = nrl_c[ch] - 1; l >= 0; --l) {
+              const int d = __shfl_sync(fm, ldim[ch], l);
+              const int64_t st = __shfl_sync(fm, lstr[ch], l);
+              const int qq = x / d;
+              ro += (int64_t)(x - qq * d) * st;
+              x = qq;
+            }
+            r0 = ro;
+          }
+          rp_c[ch] = row < mM_c[ch] ? coff_c[ch] + r0 : 0;
         }
       }
       if (nk > 0) {
