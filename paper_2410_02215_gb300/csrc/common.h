@@ -254,6 +254,29 @@ bool same_meta(const ftn_tensor_s* a, int rank, const int32_t* d0, const int32_t
 void add_perm_job(std::vector<PermJob>& jobs, int64_t& tiles, int rank, const int64_t* dims,
                   const int64_t* dst_strides, int64_t src_off, int64_t dst_off, int sign);
 
+// Launch with programmatic stream serialisation: the kernel may begin while
+// the kernel before it in the stream is still running.  Such a kernel only
+// reads tables that no kernel writes before griddepcontrol.wait (pdl_wait),
+// and signals griddepcontrol.launch_dependents only after that wait, so
+// every grid earlier in the stream has completed by the time the next one
+// can start.
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kernel)(KArgs...), unsigned grid, unsigned block, size_t smem, cudaStream_t stream,
+                       Args... args) {
+  cudaLaunchConfig_t cfg;
+  std::memset(&cfg, 0, sizeof(cfg));
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(block);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = stream;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 // kernel launchers (asynchronous on ctx->stream)
 // Chooses the kernel (returns 1 for the TMA-staged one) and fills the tiling
 // and tile prefix sums of every job; *tiles receives the total.

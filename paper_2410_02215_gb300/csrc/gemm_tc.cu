@@ -201,6 +201,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
       int cur = -1, fenced = -1;
       TileEnt nx;
       if (t_begin < t_end) tile_at<BN>(P, t_begin, cur, nx);
+      // the operands are read from here on (the tile and problem tables are
+      // not written by kernels): wait for the grid before this one, then let
+      // the next one start
+      pdl_wait();
+      pdl_launch_dependents();
       for (int64_t t = t_begin; t < t_end && ok; ++t) {
         const TileEnt e = nx;  // this tile; the next one's entry is fetched while this one is issued
         if (t + 1 < t_end) tile_at<BN>(P, t + 1, cur, nx);
@@ -340,6 +345,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
     // grouped launch most consecutive tiles do): lane l < MAXR holds row leg
     // l, MAXR <= l < 2 MAXR column leg l - MAXR, lanes 0..9 also the scalars
     // below (32-bit words of the record); mi: each chunk's member.
+    bool waited = false;
     int key_prob = -1, key_n0 = -1;
     int gm = 0, pM = 0;
     int32_t ldim[NCH];
@@ -488,6 +494,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
           }
           rp_c[ch] = row < mM_c[ch] ? coff_c[ch] + r0 : 0;
         }
+      }
+      if (!waited) {  // the first store of C: the grid before this one has completed
+        pdl_wait();
+        waited = true;
       }
       if (nk > 0) {
         if (!mbar_wait(&tfull[acc], ((j - 1) >> 1) & 1, P.err)) break;
@@ -661,9 +671,9 @@ static ftn_status run(ftn_ctx ctx, const TcOperands* ops, const void* gmaps, con
                                                        cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM);
   if (attr != cudaSuccess) return cuda_error(attr, "cudaFuncSetAttribute(tc_gemm)");
   int64_t grid = tiles < ctx->num_sms ? tiles : ctx->num_sms;
-  tc_gemm_kernel<FMT, SPLIT, BN><<<(unsigned)grid, TC_THREADS, Cfg::SMEM, ctx->stream>>>(P);
+  cudaError_t e = launch_pdl(tc_gemm_kernel<FMT, SPLIT, BN>, (unsigned)grid, TC_THREADS, Cfg::SMEM, ctx->stream, P);
   ctx->launches += 1;
-  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_error(e, "tc_gemm_kernel launch");
   return FTN_OK;
 }

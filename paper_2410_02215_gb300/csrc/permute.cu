@@ -246,10 +246,56 @@ struct StagedCfg {
   static constexpr int MAXTI = TE / 8;
   static constexpr int STAGE_ELEMS = TE + PERM_MAX_ROWS * V;
   static constexpr int BYTES = PERM_STAGES * STAGE_ELEMS * (int)sizeof(Tin) + PERM_STAGES * PERM_MAX_ROWS * (8 + 4) +
-                               PERM_STAGES * MAXTI * (4 + 2 + 2) + PERM_STAGES * (int)sizeof(StageMeta) + 128;
+                               PERM_STAGES * MAXTI * (4 + 2 + 2) + PERM_STAGES * (int)sizeof(StageMeta) +
+                               (int)sizeof(PermJob) + (MAXR + 2) * 8 + 128;
 };
 
-// Where tile t of job j lies: its I and O ranges and the source and
+// Exact division of 0 <= x < 2^31 by an invariant d >= 1 with a multiply and
+// a shift (Granlund and Montgomery, "Division by invariant integers using
+// multiplication", PLDI 1994): with l = ceil(log2 d), p = 31 + l and
+// m = ceil(2^p / d) < 2^32, x / d = (x m) >> p, because m d - 2^p < d <= 2^l
+// keeps the error term below 1 for every x < 2^31.
+struct FastDiv {
+  uint32_t m;
+  int32_t p;
+};
+
+__device__ __forceinline__ FastDiv make_fastdiv(uint32_t d) {
+  const int l = d > 1 ? 32 - __clz(d - 1) : 0;
+  FastDiv f;
+  f.p = 31 + l;
+  f.m = (uint32_t)(((1ull << f.p) + d - 1) / d);
+  return f;
+}
+
+__device__ __forceinline__ int32_t fdiv(int32_t x, FastDiv f) {
+  return (int32_t)(((uint64_t)(uint32_t)x * f.m) >> f.p);
+}
+
+// The job of the tiles being staged, in shared memory: its record and the
+// divisors of its leg dimensions and tile counts.
+struct JobView {
+  PermJob j;
+  FastDiv leg[MAXR];
+  FastDiv per_b, tiles_i;
+};
+
+// Copy job `jn` into the view (all threads of the block take part).
+__device__ __forceinline__ void load_job(const PermJob* __restrict__ jn, JobView* jv, int tid) {
+  const uint64_t* from = reinterpret_cast<const uint64_t*>(jn);
+  uint64_t* to = reinterpret_cast<uint64_t*>(&jv->j);
+  for (int w = tid; w < (int)(sizeof(PermJob) / 8); w += SPT) to[w] = from[w];
+  if (tid < MAXR) {
+    const int nl = jn->nI + jn->nO + jn->nB;
+    jv->leg[tid] = make_fastdiv(tid < nl ? (uint32_t)jn->dim[tid] : 1u);
+  } else if (tid == MAXR) {
+    jv->per_b = make_fastdiv((uint32_t)(jn->tiles_i * jn->tiles_o));
+  } else if (tid == MAXR + 1) {
+    jv->tiles_i = make_fastdiv((uint32_t)jn->tiles_i);
+  }
+}
+
+// Where tile t of the job lies: its I and O ranges and the source and
 // destination offsets of its batch index.  32-bit index arithmetic unless the
 // job's tile count needs more.
 struct TileGeo {
@@ -257,42 +303,43 @@ struct TileGeo {
   int32_t i0, o0, ncols, nrows;
 };
 
-__device__ __forceinline__ TileGeo tile_geo(const PermJob* __restrict__ j, int64_t t) {
+__device__ __forceinline__ TileGeo tile_geo(const JobView& v, int64_t t) {
+  const PermJob& j = v.j;
   TileGeo g;
-  const int64_t local = t - j->tile_begin;
-  const int32_t tiles_i = j->tiles_i, per_b = tiles_i * j->tiles_o;
+  const int64_t local = t - j.tile_begin;
+  const int32_t tiles_i = j.tiles_i, per_b = tiles_i * j.tiles_o;
   int64_t b64;
   int32_t rem;
   if (local <= INT32_MAX) {
-    const int32_t l32 = (int32_t)local, b32 = l32 / per_b;
+    const int32_t l32 = (int32_t)local, b32 = fdiv(l32, v.per_b);
     rem = l32 - b32 * per_b;
     b64 = b32;
   } else {
     b64 = local / per_b;
     rem = (int32_t)(local - b64 * per_b);
   }
-  const int32_t to = rem / tiles_i;
-  g.i0 = (rem - to * tiles_i) * j->ti;
-  g.o0 = to * j->tr;
-  g.ncols = min(j->ti, j->PI - g.i0);
-  g.nrows = min(j->tr, j->PO - g.o0);
-  int64_t bS = j->src_off, bD = j->dst_off;
-  const int nIO = j->nI + j->nO;
+  const int32_t to = fdiv(rem, v.tiles_i);
+  g.i0 = (rem - to * tiles_i) * j.ti;
+  g.o0 = to * j.tr;
+  g.ncols = min(j.ti, j.PI - g.i0);
+  g.nrows = min(j.tr, j.PO - g.o0);
+  int64_t bS = j.src_off, bD = j.dst_off;
+  const int nIO = j.nI + j.nO;
   if (b64 <= INT32_MAX) {
     int32_t x = (int32_t)b64;
-    for (int q = nIO + j->nB - 1; q >= nIO; --q) {
-      const int32_t d = j->dim[q], qq = x / d, idx = x - qq * d;
+    for (int q = nIO + j.nB - 1; q >= nIO; --q) {
+      const int32_t qq = fdiv(x, v.leg[q]), idx = x - qq * j.dim[q];
       x = qq;
-      bS += (int64_t)idx * j->sstr[q];
-      bD += (int64_t)idx * j->dstr[q];
+      bS += (int64_t)idx * j.sstr[q];
+      bD += (int64_t)idx * j.dstr[q];
     }
   } else {
     int64_t x = b64;
-    for (int q = nIO + j->nB - 1; q >= nIO; --q) {
-      const int64_t d = j->dim[q], qq = x / d, idx = x - qq * d;
+    for (int q = nIO + j.nB - 1; q >= nIO; --q) {
+      const int64_t d = j.dim[q], qq = x / d, idx = x - qq * d;
       x = qq;
-      bS += idx * j->sstr[q];
-      bD += idx * j->dstr[q];
+      bS += idx * j.sstr[q];
+      bD += idx * j.dstr[q];
     }
   }
   g.bS = bS;
@@ -307,18 +354,19 @@ __device__ __forceinline__ int find_job(const PermJob* __restrict__ jobs, int nj
                                         int64_t& next_begin, int lane) {
   if (nj >= 0 && t < next_begin) return nj;
   if (nj < 0) {
-    if (lane == 0) {
-      int lo = 0, hi = njobs - 1;
-      while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (jobs[mid].tile_begin <= t)
-          lo = mid;
-        else
-          hi = mid - 1;
-      }
-      nj = lo;
+    // 32-way search: each round the lanes sample the window at 32 evenly
+    // spaced jobs and keep the stretch after the last one starting at or
+    // before t (a window of w jobs shrinks to ceil(w / 32) per round trip)
+    int lo = 0, w = njobs;
+    while (w > 1) {
+      const int step = (w + 31) / 32;
+      const int q = lo + lane * step;
+      const unsigned ball = __ballot_sync(0xffffffffu, q < lo + w && jobs[q].tile_begin <= t);
+      const int last = 31 - __clz(ball);  // lane 0 samples job lo, which starts at or before t
+      lo += last * step;
+      w = min(step, njobs - lo);
     }
-    nj = __shfl_sync(0xffffffffu, nj, 0);
+    nj = lo;
   } else {
     // forward scan, 32 jobs per round (tile_begin increases with the job)
     for (;;) {
@@ -336,36 +384,36 @@ __device__ __forceinline__ int find_job(const PermJob* __restrict__ jobs, int nj
 // The tables of tile t in its stage (every thread takes a share: row i by
 // thread i, columns from the middle of the block on).
 template <typename Tin>
-__device__ __forceinline__ void stage_tables(const PermJob* __restrict__ j, const TileGeo& g, int64_t* rowS,
-                                             int32_t* rowD, int32_t* colD, int16_t* colS, int16_t* colP,
-                                             StageMeta* meta, int tid) {
-  const int nI = j->nI, nO = j->nO;
+__device__ __forceinline__ void stage_tables(const JobView& v, const TileGeo& g, int64_t* rowS, int32_t* rowD,
+                                             int32_t* colD, int16_t* colS, int16_t* colP, StageMeta* meta, int tid) {
+  const PermJob& j = v.j;
+  const int nI = j.nI, nO = j.nO;
   for (int r = tid; r < g.nrows; r += SPT) {
     int32_t x = g.o0 + r;
     int64_t rs = 0;
     int32_t rd = 0;
     for (int q = nI + nO - 1; q >= nI; --q) {
-      const int32_t d = j->dim[q], qq = x / d, idx = x - qq * d;
+      const int32_t qq = fdiv(x, v.leg[q]), idx = x - qq * j.dim[q];
       x = qq;
-      rs += (int64_t)idx * j->sstr[q];
-      rd += idx * (int32_t)j->dstr[q];
+      rs += (int64_t)idx * j.sstr[q];
+      rd += idx * (int32_t)j.dstr[q];
     }
     rowS[r] = rs;
     rowD[r] = rd;
   }
   const int tc = (tid + SPT / 2) & (SPT - 1);
   int32_t qp = 1;
-  if (j->iwrite) {
+  if (j.iwrite) {
     // the whole I group is in the tile (i0 = 0).  W (the destination run):
     // colS[q] = source column of the q-th element of the run (its legs'
     // destination strides are the run's own mixed radix).  P (the other I
     // legs, last fastest): colP[p] = source column, colD[p] = destination
     // offset of the p-th combination.
-    const int32_t wmask = j->wmask, qw = j->qw;
+    const int32_t wmask = j.wmask, qw = j.qw;
     for (int q = tc; q < qw; q += SPT) {
       int32_t cs = 0;
       for (int l = 0; l < nI; ++l)
-        if (wmask >> l & 1) cs += ((q / (int32_t)j->dstr[l]) % j->dim[l]) * (int32_t)j->sstr[l];
+        if (wmask >> l & 1) cs += ((q / (int32_t)j.dstr[l]) % j.dim[l]) * (int32_t)j.sstr[l];
       colS[q] = (int16_t)cs;
     }
     qp = g.ncols / qw;
@@ -373,10 +421,10 @@ __device__ __forceinline__ void stage_tables(const PermJob* __restrict__ j, cons
       int32_t x = p, cs = 0, dd = 0;
       for (int l = nI - 1; l >= 0; --l) {
         if (wmask >> l & 1) continue;
-        const int32_t d = j->dim[l], qq = x / d, idx = x - qq * d;
+        const int32_t qq = fdiv(x, v.leg[l]), idx = x - qq * j.dim[l];
         x = qq;
-        cs += idx * (int32_t)j->sstr[l];
-        dd += idx * (int32_t)j->dstr[l];
+        cs += idx * (int32_t)j.sstr[l];
+        dd += idx * (int32_t)j.dstr[l];
       }
       colP[p] = (int16_t)cs;
       colD[p] = dd;
@@ -385,9 +433,9 @@ __device__ __forceinline__ void stage_tables(const PermJob* __restrict__ j, cons
     for (int c = tc; c < g.ncols; c += SPT) {
       int32_t x = g.i0 + c, dd = 0;
       for (int q = nI - 1; q >= 0; --q) {
-        const int32_t d = j->dim[q], qq = x / d, idx = x - qq * d;
+        const int32_t qq = fdiv(x, v.leg[q]), idx = x - qq * j.dim[q];
         x = qq;
-        dd += idx * (int32_t)j->dstr[q];
+        dd += idx * (int32_t)j.dstr[q];
       }
       colD[c] = dd;
     }
@@ -396,14 +444,14 @@ __device__ __forceinline__ void stage_tables(const PermJob* __restrict__ j, cons
     meta->baseD = g.bD;
     meta->nrows = g.nrows;
     meta->ncols = g.ncols;
-    meta->ti = j->ti;
-    meta->fast_i = j->store_fast_i;
-    meta->sign = j->sign;
-    meta->vec4 = j->vec4;
-    meta->iwrite = j->iwrite;
-    meta->qw = j->qw;
+    meta->ti = j.ti;
+    meta->fast_i = j.store_fast_i;
+    meta->sign = j.sign;
+    meta->vec4 = j.vec4;
+    meta->iwrite = j.iwrite;
+    meta->qw = j.qw;
     meta->qp = qp;
-    meta->wsuf = j->wsuf;
+    meta->wsuf = j.wsuf;
   }
 }
 
@@ -416,9 +464,17 @@ __device__ __forceinline__ void stage_copies(const Tin* __restrict__ src, const 
   constexpr int V = StagedCfg<Tin>::V;
   const int cpr = g.ncols / V, stride = ti + V, nch = g.nrows * cpr;
   const Tin* sb = src + g.bS + g.i0;
-  for (int q = tid; q < nch; q += SPT) {
-    const int r = q / cpr, c = q - r * cpr;
-    cp_async16(buf + r * stride + c * V, sb + rowS[r] + c * V);
+  if ((cpr & (cpr - 1)) == 0) {
+    const int sh = __ffs(cpr) - 1;
+    for (int q = tid; q < nch; q += SPT) {
+      const int r = q >> sh, c = q & (cpr - 1);
+      cp_async16(buf + r * stride + c * V, sb + rowS[r] + c * V);
+    }
+  } else {
+    for (int q = tid; q < nch; q += SPT) {
+      const int r = q / cpr, c = q - r * cpr;
+      cp_async16(buf + r * stride + c * V, sb + rowS[r] + c * V);
+    }
   }
 }
 
@@ -436,12 +492,13 @@ __global__ void __launch_bounds__(SPT) perm_staged_kernel(const PermJob* __restr
   int16_t* colS = reinterpret_cast<int16_t*>(colD + PERM_STAGES * Cfg::MAXTI);
   int16_t* colP = colS + PERM_STAGES * Cfg::MAXTI;
   StageMeta* meta = reinterpret_cast<StageMeta*>(colP + PERM_STAGES * Cfg::MAXTI);
+  JobView* jv = reinterpret_cast<JobView*>(meta + PERM_STAGES);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   // Each CTA takes one contiguous range of tiles (the ranges differ in length
   // by at most one), so that consecutive tiles mostly belong to the same job.
   const int64_t t_first = (int64_t)blockIdx.x * tiles / gridDim.x;
   const int64_t n = ((int64_t)blockIdx.x + 1) * tiles / gridDim.x - t_first;
-  int nj = -1;
+  int nj = -1, loaded = -1;
   int64_t next_begin = 0;
   // Tile k + PERM_AHEAD is staged (tables, then copies) while tile k is
   // written out: every thread commits one cp.async group per tile, so that
@@ -450,13 +507,27 @@ __global__ void __launch_bounds__(SPT) perm_staged_kernel(const PermJob* __restr
     if (k < n) {
       const int64_t t = t_first + k;
       nj = find_job(jobs, njobs, tiles, t, nj, next_begin, lane);
-      const PermJob* __restrict__ j = jobs + nj;
+      if (nj != loaded) {  // the same for every warp
+        __syncthreads();   // nobody reads the view any more
+        load_job(jobs + nj, jv, tid);
+        __syncthreads();
+        loaded = nj;
+      }
       const int s = (int)(k % PERM_STAGES);
-      const TileGeo g = tile_geo(j, t);
-      stage_tables<Tin>(j, g, rowS + s * PERM_MAX_ROWS, rowD + s * PERM_MAX_ROWS, colD + s * Cfg::MAXTI,
+      const TileGeo g = tile_geo(*jv, t);
+      stage_tables<Tin>(*jv, g, rowS + s * PERM_MAX_ROWS, rowD + s * PERM_MAX_ROWS, colD + s * Cfg::MAXTI,
                         colS + s * Cfg::MAXTI, colP + s * Cfg::MAXTI, meta + s, tid);
+      const int ti = jv->j.ti;
+      const Tin* __restrict__ from = jv->j.src_sel ? src1 : src;
       __syncthreads();  // rowS of the stage is complete
-      stage_copies<Tin>(j->src_sel ? src1 : src, g, j->ti, buf + s * Cfg::STAGE_ELEMS, rowS + s * PERM_MAX_ROWS, tid);
+      if (k == 0) {
+        // tensors are touched from here on (the job table and the tables
+        // above are not written by kernels): wait for the grid before this
+        // one, then let the next one start
+        pdl_wait();
+        if (tid == 0) pdl_launch_dependents();
+      }
+      stage_copies<Tin>(from, g, ti, buf + s * Cfg::STAGE_ELEMS, rowS + s * PERM_MAX_ROWS, tid);
     }
     cp_async_commit();
   };
@@ -561,10 +632,8 @@ static cudaError_t go_staged(ftn_ctx ctx, const PermJob* d_jobs, int njobs, int6
   int64_t grid = tiles;
   int64_t cap = (int64_t)ctx->num_sms * 3;
   if (grid > cap) grid = cap;
-  perm_staged_kernel<Tin, MODE><<<(unsigned)grid, SPT, Cfg::BYTES, ctx->stream>>>(d_jobs, njobs, tiles,
-                                                                                 (const Tin*)src, (const Tin*)src1,
-                                                                                 dst0, dst1);
-  return cudaGetLastError();
+  return launch_pdl(perm_staged_kernel<Tin, MODE>, (unsigned)grid, SPT, Cfg::BYTES, ctx->stream, d_jobs, njobs, tiles,
+                    (const Tin*)src, (const Tin*)src1, dst0, dst1);
 }
 
 template <typename Tin, int MODE>

@@ -110,6 +110,15 @@ __device__ __forceinline__ void fence_proxy_async_smem() {
 }
 
 
+// ---- programmatic dependent launch ---------------------------------------------
+// Wait until the grids this one depends on have completed and their writes
+// are visible (returns at once for a normal launch).
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+// Let the next grid in the stream start launching (counted once per CTA).
+__device__ __forceinline__ void pdl_launch_dependents() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 // ---- tcgen05 -------------------------------------------------------------------
 __device__ __forceinline__ void tmem_alloc(uint32_t* slot, uint32_t ncols) {
   asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(slot)), "r"(ncols)
