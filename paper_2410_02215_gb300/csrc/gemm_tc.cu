@@ -45,6 +45,7 @@ struct TcParams {
   int* err;
   int64_t tiles;
   int nprobs;
+  int contig;  // 1: each CTA takes a contiguous range of tiles (else a strided set)
 };
 
 // FMT: operand format, the instruction descriptor's code (0 = FP16, 1 = BF16
@@ -185,11 +186,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tslot;
-  // Each CTA takes one contiguous range of tiles (the ranges differ in length
-  // by at most one): consecutive tiles of a CTA mostly share their problem,
-  // so the epilogue keeps its records and column offsets in registers.
-  const int64_t t_begin = (int64_t)blockIdx.x * P.tiles / gridDim.x;
-  const int64_t t_end = ((int64_t)blockIdx.x + 1) * P.tiles / gridDim.x;
+  // This CTA's tiles: one contiguous range when the launch has many tiles per
+  // CTA (the ranges differ in length by at most one; consecutive tiles then
+  // mostly share their problem, so the epilogue keeps its records and column
+  // offsets in registers), else every gridDim.x-th tile (concurrent CTAs then
+  // work on neighbouring tiles, whose operand rows and columns they share in
+  // L2).
+  const int64_t t_begin = P.contig ? (int64_t)blockIdx.x * P.tiles / gridDim.x : (int64_t)blockIdx.x;
+  const int64_t t_step = P.contig ? 1 : (int64_t)gridDim.x;
+  const int64_t n_my = P.contig ? ((int64_t)blockIdx.x + 1) * P.tiles / gridDim.x - t_begin
+                                : (P.tiles - blockIdx.x + gridDim.x - 1) / gridDim.x;
 
   if (warp == 0) {
     if (lane == 0) {
@@ -200,15 +206,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
       bool ok = true;
       int cur = -1, fenced = -1;
       TileEnt nx;
-      if (t_begin < t_end) tile_at<BN>(P, t_begin, cur, nx);
+      if (n_my > 0) tile_at<BN>(P, t_begin, cur, nx);
       // the operands are read from here on (the tile and problem tables are
       // not written by kernels): wait for the grid before this one, then let
       // the next one start
       pdl_wait();
       pdl_launch_dependents();
-      for (int64_t t = t_begin; t < t_end && ok; ++t) {
+      for (int64_t k = 0; k < n_my && ok; ++k) {
+        const int64_t t = t_begin + k * t_step;
         const TileEnt e = nx;  // this tile; the next one's entry is fetched while this one is issued
-        if (t + 1 < t_end) tile_at<BN>(P, t + 1, cur, nx);
+        if (k + 1 < n_my) tile_at<BN>(P, t + t_step, cur, nx);
         const int nk = (e.K + Cfg::KB - 1) / Cfg::KB;
         const int pi = e.pi;
         const CUtensorMap *ma = &P.a_hi[pi & 1], *mb = &P.b_hi[pi & 1], *mal = &P.a_lo[pi & 1],
@@ -264,10 +271,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
       bool ok = true;
       int cur = -1;
       TileEnt nx;
-      if (t_begin < t_end) tile_at<BN>(P, t_begin, cur, nx);
-      for (int64_t t = t_begin; t < t_end && ok; ++t) {
+      if (n_my > 0) tile_at<BN>(P, t_begin, cur, nx);
+      for (int64_t k = 0; k < n_my && ok; ++k) {
+        const int64_t t = t_begin + k * t_step;
         const TileEnt e = nx;
-        if (t + 1 < t_end) tile_at<BN>(P, t + 1, cur, nx);
+        if (k + 1 < n_my) tile_at<BN>(P, t + t_step, cur, nx);
         const int nk = (e.K + Cfg::KB - 1) / Cfg::KB;
         if (nk == 0) continue;
         if (!mbar_wait(&tempty[acc], acc_phase ^ 1, P.err)) break;
@@ -337,8 +345,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
     int cur = -1;
     // tile entries two tiles ahead (a set writes every other tile out)
     TileEnt nx, nx2;
-    if (t_begin < t_end) tile_at<BN>(P, t_begin, cur, nx);
-    if (t_begin + 1 < t_end) tile_at<BN>(P, t_begin + 1, cur, nx2);
+    if (n_my > 0) tile_at<BN>(P, t_begin, cur, nx);
+    if (n_my > 1) tile_at<BN>(P, t_begin + t_step, cur, nx2);
     constexpr int NCH = BN / Cfg::CW;
     // The problem records of the last tile written out, kept in registers
     // while the tiles stay on the same problem and first column (in a
@@ -358,10 +366,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
     int cn_c[NCH], fl_c[NCH], mM_c[NCH], nrl_c[NCH];
     float sg_c[NCH];
     bool rows_same = true;
-    for (int64_t t = t_begin; t < t_end; ++t) {
+    for (int64_t k = 0; k < n_my; ++k) {
+      const int64_t t = t_begin + k * t_step;
       const TileEnt e = nx;
       nx = nx2;
-      if (t + 2 < t_end) tile_at<BN>(P, t + 2, cur, nx2);
+      if (k + 2 < n_my) tile_at<BN>(P, t + 2 * t_step, cur, nx2);
       const int m0 = e.m0, n0 = e.n0;
       const GemmProb* __restrict__ pp = P.probs + e.prob;
       const int nk = (e.K + Cfg::KB - 1) / Cfg::KB;
@@ -671,6 +680,7 @@ static ftn_status run(ftn_ctx ctx, const TcOperands* ops, const void* gmaps, con
                                                        cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM);
   if (attr != cudaSuccess) return cuda_error(attr, "cudaFuncSetAttribute(tc_gemm)");
   int64_t grid = tiles < ctx->num_sms ? tiles : ctx->num_sms;
+  P.contig = tiles >= 8 * grid ? 1 : 0;
   cudaError_t e = launch_pdl(tc_gemm_kernel<FMT, SPLIT, BN>, (unsigned)grid, TC_THREADS, Cfg::SMEM, ctx->stream, P);
   ctx->launches += 1;
   if (e == cudaSuccess) e = cudaGetLastError();
