@@ -101,6 +101,16 @@ FTN_API ftn_status ftn_ctx_create(void* cuda_stream, ftn_alloc_fn alloc, ftn_fre
 FTN_API ftn_status ftn_ctx_destroy(ftn_ctx ctx);
 /* Change the stream later calls are issued on. */
 FTN_API ftn_status ftn_ctx_set_stream(ftn_ctx ctx, void* cuda_stream);
+/* Tile-width tuning of tensor-core contractions (on when a context is
+ * created; no counterpart in the paper, a property of this implementation).
+ * While on, the first ftn_tensordot of a contraction with at least 2^30
+ * sector flops (not issued under stream capture) also plans its GEMM with the
+ * tile width capped at half and a quarter of the default, runs every
+ * candidate twice (once timed with CUDA events, synchronising the context
+ * stream) and keeps the fastest in the context's plan cache.  The width does
+ * not change any result bit.  Off: every plan keeps the default width.
+ * Affects plans built after the call.  FTN_EINVAL for a null context. */
+FTN_API ftn_status ftn_ctx_set_tuning(ftn_ctx ctx, int on);
 /* Synchronise the context stream and report a device-side error recorded
  * since the last call (FTN_ETIMEOUT after a bounded wait gave up). */
 FTN_API ftn_status ftn_ctx_synchronize(ftn_ctx ctx);

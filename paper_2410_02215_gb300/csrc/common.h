@@ -178,6 +178,7 @@ struct ftn_ctx_s {
   int num_sms = 0;
   int* dev_err = nullptr;  // device error word (zeroed at creation)
   int64_t launches = 0;
+  bool tune = true;  // tile-width tuning of large tensor-core plans (ftn_ctx_set_tuning)
   // grow-only workspace arena (reused by every call on this context)
   void* ws = nullptr;
   size_t ws_bytes = 0;

@@ -82,8 +82,11 @@ struct TdPlan {
   GemmProb* d_red = nullptr;
 };
 
+// The cached plan of a contraction (built on first use; *fresh, when given,
+// tells whether it was built by this call).
 ftn_status get_plan(ftn_ctx ctx, const ftn_tensor_s* A, const ftn_tensor_s* B, int n, const int* ax, const int* ay,
-                    uint64_t fa, uint64_t fb, const int* out_perm, ftn_prec prec, std::shared_ptr<TdPlan>& P);
+                    uint64_t fa, uint64_t fb, const int* out_perm, ftn_prec prec, std::shared_ptr<TdPlan>& P,
+                    bool* fresh = nullptr);
 ftn_status validate_pairs(const ftn_tensor_s* A, const ftn_tensor_s* B, int n, const int* ax, const int* ay);
 int inversion_parity(int r, const int* perm, uint32_t mask);
 // bits legs[0..n) of mask, packed (bit i = bit legs[i])

@@ -461,6 +461,12 @@ ftn_status ftn_ctx_set_stream(ftn_ctx ctx, void* cuda_stream) {
   return FTN_OK;
 }
 
+ftn_status ftn_ctx_set_tuning(ftn_ctx ctx, int on) {
+  if (!ctx) return set_error(FTN_EINVAL, "null ctx");
+  ctx->tune = on != 0;
+  return FTN_OK;
+}
+
 ftn_status ftn_ctx_synchronize(ftn_ctx ctx) {
   if (!ctx) return set_error(FTN_EINVAL, "null ctx");
   FTN_CUDA(cudaStreamSynchronize(ctx->stream));

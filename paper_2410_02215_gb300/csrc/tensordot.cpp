@@ -131,9 +131,10 @@ static std::unordered_map<std::string, std::shared_ptr<TdPlan>>& plan_cache(ftn_
   return caches[ctx];
 }
 
+// bn_cap > 0 caps the tensor-core tile width (the tuner's candidates).
 static ftn_status build_plan(ftn_ctx ctx, const ftn_tensor_s* A, const ftn_tensor_s* B, int n, const int* ax,
                              const int* ay, uint64_t flip_a, uint64_t flip_b, const int* out_perm, ftn_prec prec,
-                             std::shared_ptr<TdPlan>& out) {
+                             std::shared_ptr<TdPlan>& out, int bn_cap = 0) {
   auto P = std::make_shared<TdPlan>();
   P->n = n;
   bool in_a[MAXR] = {}, in_b[MAXR] = {};
@@ -353,6 +354,7 @@ static ftn_status build_plan(ftn_ctx ctx, const ftn_tensor_s* A, const ftn_tenso
     maxN = std::max<int64_t>(maxN, colsz[pi][mB]);
   }
   P->bn = tc ? tc_pick_bn(maxN, prec) : f64_pick_bn(maxN);
+  if (tc && bn_cap > 0) P->bn = std::min(P->bn, bn_cap);
   for (int64_t b = 0; b < (int64_t)toff.size(); ++b) {
     uint32_t m = block_mask(cr, tmp.parity, b);
     uint32_t mA = m & ((1u << P->nfa) - 1u), mB = m >> P->nfa;
@@ -454,7 +456,7 @@ static ftn_status build_plan(ftn_ctx ctx, const ftn_tensor_s* A, const ftn_tenso
       }
       max_group_n = std::max(max_group_n, tot);
     }
-    const int bn_merged = tc_pick_bn(max_group_n, prec);
+    const int bn_merged = bn_cap > 0 ? std::min(tc_pick_bn(max_group_n, prec), bn_cap) : tc_pick_bn(max_group_n, prec);
     merge = merge && bn_merged > P->bn && bn_merged >= 32;
     if (merge) {  // only while the wider tiles still fill the GPU twice over
       int64_t mt = 0;
@@ -541,25 +543,39 @@ ftn_status validate_pairs(const ftn_tensor_s* A, const ftn_tensor_s* B, int n, c
   return FTN_OK;
 }
 
-ftn_status get_plan(ftn_ctx ctx, const ftn_tensor_s* A, const ftn_tensor_s* B, int n, const int* ax,
-                           const int* ay, uint64_t fa, uint64_t fb, const int* out_perm, ftn_prec prec,
-                           std::shared_ptr<TdPlan>& P) {
+static std::string plan_key(const ftn_tensor_s* A, const ftn_tensor_s* B, int n, const int* ax, const int* ay,
+                            uint64_t fa, uint64_t fb, const int* out_perm, ftn_prec prec) {
   CacheKey key;
   key.meta(A).meta(B).ints(ax, n).ints(ay, n).put(fa).put(fb).put<int32_t>((int32_t)prec);
   key.put<uint8_t>(((uintptr_t)A->data & 15) == 0).put<uint8_t>(((uintptr_t)B->data & 15) == 0);
   key.put<uint8_t>(out_perm != nullptr);
   if (out_perm) key.ints(out_perm, A->rank + B->rank - 2 * n);
+  return key.s;
+}
+
+ftn_status get_plan(ftn_ctx ctx, const ftn_tensor_s* A, const ftn_tensor_s* B, int n, const int* ax,
+                           const int* ay, uint64_t fa, uint64_t fb, const int* out_perm, ftn_prec prec,
+                           std::shared_ptr<TdPlan>& P, bool* fresh) {
+  const std::string key = plan_key(A, B, n, ax, ay, fa, fb, out_perm, prec);
   auto& cache = plan_cache(ctx);
-  auto it = cache.find(key.s);
+  auto it = cache.find(key);
   if (it != cache.end()) {
     P = it->second;
+    if (fresh) *fresh = false;
     return FTN_OK;
   }
   FTN_TRY(build_plan(ctx, A, B, n, ax, ay, fa, fb, out_perm, prec, P));
   if (cache.size() > 65536) cache.clear();
-  cache[key.s] = P;
+  cache[key] = P;
+  if (fresh) *fresh = true;
   return FTN_OK;
 }
+
+static ftn_status run_plan(ftn_ctx ctx, TdPlan& Pl, const ftn_tensor_s* A, const ftn_tensor_s* B, ftn_tensor out,
+                          ftn_prec prec);
+static ftn_status tune_plan(ftn_ctx ctx, const ftn_tensor_s* A, const ftn_tensor_s* B, int n, const int* ax,
+                           const int* ay, uint64_t fa, uint64_t fb, const int* out_perm, ftn_prec prec,
+                           std::shared_ptr<TdPlan>& P, ftn_tensor out);
 
 ftn_status tensordot_impl(ftn_ctx ctx, ftn_tensor A, ftn_tensor B, int n, const int* ax, const int* ay,
                           uint64_t flip_a, uint64_t flip_b, const int* out_perm, ftn_prec prec, ftn_tensor* C) {
@@ -578,7 +594,8 @@ ftn_status tensordot_impl(ftn_ctx ctx, ftn_tensor A, ftn_tensor B, int n, const 
     }
   }
   std::shared_ptr<TdPlan> P;
-  FTN_TRY(get_plan(ctx, A, B, n, ax, ay, flip_a, flip_b, out_perm, prec, P));
+  bool fresh = false;
+  FTN_TRY(get_plan(ctx, A, B, n, ax, ay, flip_a, flip_b, out_perm, prec, P, &fresh));
   ftn_tensor out = *C;
   bool created = false;
   if (out) {
@@ -590,6 +607,22 @@ ftn_status tensordot_impl(ftn_ctx ctx, ftn_tensor A, ftn_tensor B, int n, const 
     FTN_TRY(make_tensor(ctx, cr, P->cd0, P->cd1, P->cdual, P->cpar, A->dtype, &out));
     created = true;
   }
+  ftn_status st = FTN_OK;
+  if (fresh) st = tune_plan(ctx, A, B, n, ax, ay, flip_a, flip_b, out_perm, prec, P, out);
+  if (st == FTN_OK) st = run_plan(ctx, *P, A, B, out, prec);
+  if (st != FTN_OK) {
+    if (created) ftn_tensor_free(out);
+    return st;
+  }
+  *C = out;
+  return FTN_OK;
+}
+
+// One contraction along plan P into `out` (asynchronous on the context's
+// stream).
+static ftn_status run_plan(ftn_ctx ctx, TdPlan& Pl, const ftn_tensor_s* A, const ftn_tensor_s* B, ftn_tensor out,
+                          ftn_prec prec) {
+  TdPlan* P = &Pl;
   // workspace: A_f (hi, lo), B_f (hi, lo), pre-permutation result
   const bool tc = prec != FTN_PREC_F64;
   const bool split = prec_split(prec);
@@ -601,10 +634,7 @@ ftn_status tensordot_impl(ftn_ctx ctx, ftn_tensor A, ftn_tensor B, int n, const 
   const size_t p_b = al((size_t)P->part_elems * 8);
   const size_t need = a_b * (split ? 2 : 1) + b_b * (split ? 2 : 1) + c_b + p_b;
   uint8_t* ws = (uint8_t*)workspace(ctx, need);
-  if (!ws) {
-    if (created) ftn_tensor_free(out);
-    return set_error(FTN_ENOMEM, "workspace allocation failed");
-  }
+  if (!ws) return set_error(FTN_ENOMEM, "workspace allocation failed");
   // [A hi | B hi | A lo | B lo]: both lo planes at one offset from their hi planes
   uint8_t* af_hi = ws;
   uint8_t* bf_hi = ws + a_b;
@@ -618,6 +648,7 @@ ftn_status tensordot_impl(ftn_ctx ctx, ftn_tensor A, ftn_tensor B, int n, const 
   for (const GemmProb& g : P->probs) gemm_flops += 2.0 * g.M * g.N * g.K;
   ftn_status st = FTN_OK;
   int rec = -1;
+  const ftn_dtype in_type = A->dtype;
   if (P->d_jab) {  // both operands in one launch
     rec = prof_begin(ctx, "permute", (A->numel + B->numel) * (in_es + es * planes), 0);
     st = launch_permute2(ctx, P->d_jab, (int)P->jab.size(), P->tab, P->sab, A->data, B->data, af_hi, af_lo,
@@ -670,14 +701,60 @@ ftn_status tensordot_impl(ftn_ctx ctx, ftn_tensor A, ftn_tensor B, int n, const 
   }
   if (st == FTN_OK && !P->fused) {
     rec = prof_begin(ctx, "permute", 2.0 * P->tmp_numel * in_es, 0);
-    st = launch_permute(ctx, P->d_jc, (int)P->jc.size(), P->tc, P->sc, ctmp, out->data, nullptr, A->dtype, PERM_SAME);
+    st = launch_permute(ctx, P->d_jc, (int)P->jc.size(), P->tc, P->sc, ctmp, out->data, nullptr, in_type, PERM_SAME);
     prof_end(ctx, rec);
   }
-  if (st != FTN_OK) {
-    if (created) ftn_tensor_free(out);
-    return st;
+  return st;
+}
+
+// Tile-width tuner.  On the first use of a tensor-core plan of at least
+// 2^30 sector flops (outside stream capture) the same contraction is also
+// planned with the GEMM tile width capped at half and a quarter of the
+// default (at least 32), each candidate is run once to warm up and once
+// under CUDA events, and the fastest is kept in the plan cache.  The tile
+// width does not change any result bit: every output element accumulates
+// its K products in the same order whatever the tiling.  `out` holds the
+// contraction afterwards.
+static ftn_status tune_plan(ftn_ctx ctx, const ftn_tensor_s* A, const ftn_tensor_s* B, int n, const int* ax,
+                           const int* ay, uint64_t fa, uint64_t fb, const int* out_perm, ftn_prec prec,
+                           std::shared_ptr<TdPlan>& P, ftn_tensor out) {
+  if (!ctx->tune || prec == FTN_PREC_F64 || P->bn < 64) return FTN_OK;
+  double flops = 0;
+  for (const GemmProb& g : P->probs) flops += 2.0 * g.M * g.N * g.K;
+  if (flops < (double)(1 << 30)) return FTN_OK;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(ctx->stream, &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone) return FTN_OK;
+  std::vector<std::shared_ptr<TdPlan>> cands{P};
+  for (int cap_bn = P->bn / 2; cap_bn >= 32 && cap_bn >= P->bn / 4; cap_bn /= 2) {
+    std::shared_ptr<TdPlan> Q;
+    FTN_TRY(build_plan(ctx, A, B, n, ax, ay, fa, fb, out_perm, prec, Q, cap_bn));
+    if (Q->bn != cands.back()->bn) cands.push_back(Q);
   }
-  *C = out;
+  if (cands.size() < 2) return FTN_OK;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  FTN_CUDA(cudaEventCreate(&e0));
+  FTN_CUDA(cudaEventCreate(&e1));
+  ftn_status st = FTN_OK;
+  size_t best = 0;
+  float best_ms = 0;
+  for (size_t c = 0; c < cands.size() && st == FTN_OK; ++c) {
+    st = run_plan(ctx, *cands[c], A, B, out, prec);
+    if (st != FTN_OK) break;
+    cudaEventRecord(e0, ctx->stream);
+    st = run_plan(ctx, *cands[c], A, B, out, prec);
+    cudaEventRecord(e1, ctx->stream);
+    float ms = 0;
+    if (st == FTN_OK && cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess &&
+        (c == 0 || ms < best_ms)) {
+      best = c;
+      best_ms = ms;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != FTN_OK) return st;
+  P = cands[best];
+  plan_cache(ctx)[plan_key(A, B, n, ax, ay, fa, fb, out_perm, prec)] = P;
   return FTN_OK;
 }
 

@@ -69,6 +69,7 @@ def lib():
         "ftn_ctx_create": [vp, ALLOC_FN, FREE_FN, vp, C.POINTER(vp)],
         "ftn_ctx_destroy": [vp],
         "ftn_ctx_set_stream": [vp, vp],
+        "ftn_ctx_set_tuning": [vp, C.c_int],
         "ftn_ctx_synchronize": [vp],
         "ftn_tensor_create": [vp, C.c_int, i32p, i32p, u8p, C.c_int, C.c_int, C.POINTER(vp)],
         "ftn_tensor_wrap": [vp, C.c_int, i32p, i32p, u8p, C.c_int, C.c_int, vp, C.POINTER(vp)],
@@ -168,6 +169,11 @@ class Context:
         e.g. a stream under CUDA-graph capture."""
         _check(lib().ftn_ctx_set_stream(self.handle, C.c_void_p(stream.cuda_stream)))
         self.stream = stream
+
+    def set_tuning(self, on):
+        """Tile-width tuning of large tensor-core contractions on their first
+        use (ftn_ctx_set_tuning; on by default)."""
+        _check(lib().ftn_ctx_set_tuning(self.handle, 1 if on else 0))
 
     def launches(self):
         return int(lib().ftn_ctx_launch_count(self.handle))

@@ -283,3 +283,29 @@ def test_tensordot_f64_splitk_and_narrow_tiles(F, ctx, ci, parity):
         got = dense(c.to_blocks(), c.legs, c.parity)
         assert c.legs == ref.legs and c.parity == ref.parity
         assert relerr(got.data, ref.data) <= TOL["f64"]
+
+
+@pytest.mark.parametrize("name", ["T1", "T4"])
+def test_tile_width_tuning_keeps_every_bit(F, name):
+    """The first use of a large tensor-core contraction times its GEMM at a few
+    tile widths and keeps the fastest: a tuning context and one that keeps the
+    default width give the same result bit for bit (every output element
+    accumulates its K products in the same order whatever the tiling), and the
+    tuned plan's later calls repeat it."""
+    case = W.tensordot_case(name, seed=0)
+    ba = W.random_blocks(case["legs_a"], 0, case["seed_a"])
+    bb = W.random_blocks(case["legs_b"], 0, case["seed_b"])
+    outs = []
+    for tune in (True, False):
+        c = F.Context()
+        try:
+            c.set_tuning(tune)
+            a, b = upload(F, c, case["legs_a"], 0, ba, "f16x3"), upload(F, c, case["legs_b"], 0, bb, "f16x3")
+            r = [F.tensordot(c, a, b, case["axes_a"], case["axes_b"], out_perm=case["out_perm"],
+                             prec="f16x3").download() for _ in range(2)]
+            assert np.array_equal(r[0], r[1])
+            outs.append(r[0])
+        finally:
+            c.synchronize()
+            c.close()
+    assert np.array_equal(outs[0], outs[1])
