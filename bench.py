@@ -671,6 +671,8 @@ def run_ours(args, rank, world, local):
     torch.cuda.set_device(local)
     F.lib()
     ctx = F.Context()
+    if args.no_tune:
+        ctx.set_tuning(False)
     peaks = load_peaks()
     cases = [W.tensordot_case(n, seed=0) for n in args.cases]
     flops_step = sum(sector_flops(c) for c in cases)
@@ -760,6 +762,8 @@ def main():
     ap.add_argument("--no-backward", action="store_true")
     ap.add_argument("--no-cluster", action="store_true")
     ap.add_argument("--no-graph", action="store_true", help="time the step eagerly only (no CUDA-graph replay)")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="keep every plan's default GEMM tile width (for profiler runs, whose timings mislead the tuner)")
     ap.add_argument("--cluster-graphs", type=int, default=64)
     ap.add_argument("--energy-evals", type=int, default=3)
     ap.add_argument("--energy-streams", type=int, default=8,
