@@ -6,6 +6,7 @@
 #include <algorithm>
 
 #include "common.h"
+#include "ptx.cuh"
 
 namespace ftn {
 
@@ -155,6 +156,10 @@ __global__ void splitk_reduce_kernel(const GemmProb* __restrict__ red, int nred,
 // FP32 partial slabs (tensor-core K-split parts), added in FP64.
 __global__ void splitk_reduce_f32_kernel(const GemmProb* __restrict__ red, int nred, int64_t total,
                                          const float* __restrict__ part, float* __restrict__ C) {
+  // launched with programmatic serialisation (the adjoint's reduction follows its GEMM on one
+  // stream): nothing is read before this
+  pdl_wait();
+  pdl_launch_dependents();
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
     const GemmProb& g = red[find_prob(red, nred, e)];
     const int64_t local = e - g.tile_begin;
@@ -172,7 +177,7 @@ ftn_status launch_splitk_reduce_f32(ftn_ctx ctx, const GemmProb* d_red, int nred
   if (nred == 0 || total == 0) return FTN_OK;
   int64_t grid = (total + 255) / 256;
   if (grid > (int64_t)ctx->num_sms * 8) grid = (int64_t)ctx->num_sms * 8;
-  splitk_reduce_f32_kernel<<<(unsigned)grid, 256, 0, ctx->stream>>>(d_red, nred, total, part, c);
+  launch_pdl(splitk_reduce_f32_kernel, (unsigned)grid, 256, 0, ctx->stream, d_red, nred, total, part, c);
   ctx->launches += 1;
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_error(e, "splitk_reduce_f32_kernel launch");
