@@ -280,6 +280,8 @@ struct JobView {
   FastDiv per_b, tiles_i;
 };
 
+static_assert(sizeof(PermJob) % 8 == 0, "jobs are copied as 8-byte words");
+
 // Copy job `jn` into the view (all threads of the block take part).
 __device__ __forceinline__ void load_job(const PermJob* __restrict__ jn, JobView* jv, int tid) {
   const uint64_t* from = reinterpret_cast<const uint64_t*>(jn);

@@ -1,7 +1,8 @@
 // Inline-PTX helpers for sm_103a: mbarriers with bounded waits, TMA tile
-// loads, and the tcgen05 tensor-core path (TMEM allocation, MMA, commit,
-// TMEM loads).  Every wait gives up after a time limit and records an error
-// instead of spinning forever.
+// loads, cp.async copies and groups, programmatic dependent launch
+// (griddepcontrol), and the tcgen05 tensor-core path (TMEM allocation, MMA,
+// commit, TMEM loads).  Every mbarrier wait gives up after a time limit and
+// records an error instead of spinning forever.
 #pragma once
 #include <stdint.h>
 
@@ -86,14 +87,6 @@ __device__ __forceinline__ void tensormap_acquire(const void* tmap) {
                : "memory");
 }
 
-// 1-D bulk copy global -> shared (both 16-byte aligned, size a multiple of 16)
-// completing on an mbarrier's transaction count.
-__device__ __forceinline__ void bulk_g2s(void* smem_dst, const void* gsrc, uint32_t bytes, uint64_t* bar) {
-  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                   smem_u32(smem_dst)),
-               "l"(reinterpret_cast<uint64_t>(gsrc)), "r"(bytes), "r"(smem_u32(bar))
-               : "memory");
-}
 // 16-byte copy global -> shared through L2 (both addresses 16-byte aligned).
 __device__ __forceinline__ void cp_async16(void* smem_dst, const void* gsrc) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(smem_dst)), "l"(gsrc) : "memory");
@@ -104,9 +97,6 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait_group() {
   asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
-}
-__device__ __forceinline__ void fence_proxy_async_smem() {
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
 
