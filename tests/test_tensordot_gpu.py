@@ -309,3 +309,43 @@ def test_tile_width_tuning_keeps_every_bit(F, name):
             c.synchronize()
             c.close()
     assert np.array_equal(outs[0], outs[1])
+
+
+@pytest.mark.parametrize("dt", ["f64", "f32"])
+@pytest.mark.parametrize("parity", [0, 1])
+def test_transpose_many_jobs(F, ctx, dt, parity):
+    """2048 blocks of 64 entries (ten legs of dimension 1 + 1 around two
+    larger ones): the shared-memory-staged permute runs one job per tile, so
+    every CTA starts with a 32-way search over 2048 jobs and changes job on
+    every tile; exact against the oracle for several leg orders."""
+    legs = [(1, 1, q % 2) for q in range(5)] + [(32, 32, 0), (2, 2, 1)] + [(1, 1, q % 2) for q in range(5)]
+    blocks = W.random_blocks(legs, parity, 41 + parity)
+    assert len(blocks) == 2048
+    t = F.Tensor.from_blocks(ctx, legs, parity, blocks, F.F64 if dt == "f64" else F.F32)
+    ref_in = dense(blocks, legs, parity)
+    if dt == "f32":
+        ref_in = O.GTensor(ref_in.data.astype(np.float32).astype(np.float64), ref_in.legs, parity)
+    for s in range(3):
+        perm = W.random_perm(len(legs), 90 + s)
+        out = F.transpose(ctx, t, perm)
+        got = dense(out.to_blocks(), out.legs, out.parity)
+        ref = O.transpose(ref_in, perm)
+        assert np.array_equal(got.data, ref.data)
+    ctx.synchronize()
+
+
+@pytest.mark.parametrize("prec", ["tf32x3", "f16x3"])
+def test_merged_group_of_many_members(F, ctx, prec):
+    """B's 64 column blocks per bond sector, each 32 wide, form one merged
+    group per row block (more members than a warp's lanes): the GEMM epilogue
+    finds each 32-column chunk's member by walking the group.  Against the
+    oracle."""
+    la = [(64, 64, 0), (16, 16, 0), (4, 4, 0)]
+    lb = [(4, 4, 1)] + [(2, 2, 0)] * 5 + [(1, 1, 0)] * 2
+    ba, bb = W.random_blocks(la, 0, 61), W.random_blocks(lb, 0, 62)
+    ref = O.contract(dense(ba, la, 0), dense(bb, lb, 0), [2], [0])
+    a, b = upload(F, ctx, la, 0, ba, prec), upload(F, ctx, lb, 0, bb, prec)
+    c = F.tensordot(ctx, a, b, [2], [0], prec=prec)
+    got = dense(c.to_blocks(), c.legs, c.parity)
+    assert relerr(got.data, ref.data) <= TOL[prec]
+    ctx.synchronize()
