@@ -6,16 +6,20 @@
 //
 // Two kernels share the job format.  The staged kernel (used when every
 // source row of a job starts 16-byte aligned): each persistent CTA takes a
-// contiguous range of tiles; two producer warps copy the source rows of
-// upcoming tiles into a PERM_STAGES-deep shared-memory ring with 16-byte
+// contiguous range of tiles; two producer warps (alternate tiles) build a
+// tile's row and column tables -- with the job and multiply-shift
+// reciprocals of its leg dimensions cached in shared memory -- and copy its
+// source rows into a PERM_STAGES-deep shared-memory ring with 16-byte
 // cp.async copies spread over their lanes (consecutive lanes on consecutive
-// chunks of a row; completion tracked on an mbarrier), and eight consumer
-// warps write tiles out along the destination's contiguous direction,
+// chunks of a row; completion tracked on an mbarrier), while eight writer
+// warps write earlier tiles out along the destination's contiguous direction,
 // releasing ring slots through a second set of mbarriers (no block-wide
 // synchronisation in the loop).  The copies hold no registers while in
 // flight.  (One bulk copy per row was tried first: a few hundred cycles per
 // request per SM left the rows of 128 to 512 bytes far below the HBM
-// bandwidth.)  The fallback kernel stages through registers:
+// bandwidth.  All warps building tables and copying between block barriers
+// was tried next: the tables then ran in series with the writes.)  The
+// fallback kernel stages through registers:
 // Each CTA tile covers PERM_TO rows of the O group (destination-fast legs)
 // times PERM_TI elements of the I group (the source's contiguous suffix) for
 // one batch index.  Loads run along I (coalesced in the source); stores run
@@ -235,9 +239,9 @@ struct StageMeta {
   int32_t iwrite, qw, qp, wsuf;
 };
 
-constexpr int SPT = 256;                 // threads of the staged kernel
-constexpr int SPW = SPT / 32;            // its warps
-constexpr int PERM_AHEAD = PERM_STAGES - 1;  // tiles in flight while one is written out
+constexpr int SPW = 8;                   // writer warps of the staged kernel
+constexpr int SPP = 2;                   // producer warps (alternate tiles)
+constexpr int SPT = 32 * (SPW + SPP);    // its threads
 
 template <typename Tin>
 struct StagedCfg {
@@ -247,7 +251,7 @@ struct StagedCfg {
   static constexpr int STAGE_ELEMS = TE + PERM_MAX_ROWS * V;
   static constexpr int BYTES = PERM_STAGES * STAGE_ELEMS * (int)sizeof(Tin) + PERM_STAGES * PERM_MAX_ROWS * (8 + 4) +
                                PERM_STAGES * MAXTI * (4 + 2 + 2) + PERM_STAGES * (int)sizeof(StageMeta) +
-                               (int)sizeof(PermJob) + (MAXR + 2) * 8 + 128;
+                               SPP * ((int)sizeof(PermJob) + (MAXR + 2) * 8) + 2 * PERM_STAGES * 8 + 128;
 };
 
 // Exact division of 0 <= x < 2^31 by an invariant d >= 1 with a multiply and
@@ -282,11 +286,12 @@ struct JobView {
 
 static_assert(sizeof(PermJob) % 8 == 0, "jobs are copied as 8-byte words");
 
-// Copy job `jn` into the view (all threads of the block take part).
+// Copy job `jn` into the view (the lanes of one warp).
 __device__ __forceinline__ void load_job(const PermJob* __restrict__ jn, JobView* jv, int tid) {
+  static_assert(MAXR + 2 <= 32, "one lane per divisor");
   const uint64_t* from = reinterpret_cast<const uint64_t*>(jn);
   uint64_t* to = reinterpret_cast<uint64_t*>(&jv->j);
-  for (int w = tid; w < (int)(sizeof(PermJob) / 8); w += SPT) to[w] = from[w];
+  for (int w = tid; w < (int)(sizeof(PermJob) / 8); w += 32) to[w] = from[w];
   if (tid < MAXR) {
     const int nl = jn->nI + jn->nO + jn->nB;
     jv->leg[tid] = make_fastdiv(tid < nl ? (uint32_t)jn->dim[tid] : 1u);
@@ -383,14 +388,14 @@ __device__ __forceinline__ int find_job(const PermJob* __restrict__ jobs, int nj
   return nj;
 }
 
-// The tables of tile t in its stage (every thread takes a share: row i by
-// thread i, columns from the middle of the block on).
+// The tables of tile t in its stage (the lanes of one producer warp take
+// rows and columns in turn).
 template <typename Tin>
 __device__ __forceinline__ void stage_tables(const JobView& v, const TileGeo& g, int64_t* rowS, int32_t* rowD,
                                              int32_t* colD, int16_t* colS, int16_t* colP, StageMeta* meta, int tid) {
   const PermJob& j = v.j;
   const int nI = j.nI, nO = j.nO;
-  for (int r = tid; r < g.nrows; r += SPT) {
+  for (int r = tid; r < g.nrows; r += 32) {
     int32_t x = g.o0 + r;
     int64_t rs = 0;
     int32_t rd = 0;
@@ -403,7 +408,7 @@ __device__ __forceinline__ void stage_tables(const JobView& v, const TileGeo& g,
     rowS[r] = rs;
     rowD[r] = rd;
   }
-  const int tc = (tid + SPT / 2) & (SPT - 1);
+  const int tc = tid;
   int32_t qp = 1;
   if (j.iwrite) {
     // the whole I group is in the tile (i0 = 0).  W (the destination run):
@@ -412,14 +417,14 @@ __device__ __forceinline__ void stage_tables(const JobView& v, const TileGeo& g,
     // legs, last fastest): colP[p] = source column, colD[p] = destination
     // offset of the p-th combination.
     const int32_t wmask = j.wmask, qw = j.qw;
-    for (int q = tc; q < qw; q += SPT) {
+    for (int q = tc; q < qw; q += 32) {
       int32_t cs = 0;
       for (int l = 0; l < nI; ++l)
         if (wmask >> l & 1) cs += ((q / (int32_t)j.dstr[l]) % j.dim[l]) * (int32_t)j.sstr[l];
       colS[q] = (int16_t)cs;
     }
     qp = g.ncols / qw;
-    for (int p = tc; p < qp; p += SPT) {
+    for (int p = tc; p < qp; p += 32) {
       int32_t x = p, cs = 0, dd = 0;
       for (int l = nI - 1; l >= 0; --l) {
         if (wmask >> l & 1) continue;
@@ -432,7 +437,7 @@ __device__ __forceinline__ void stage_tables(const JobView& v, const TileGeo& g,
       colD[p] = dd;
     }
   } else {
-    for (int c = tc; c < g.ncols; c += SPT) {
+    for (int c = tc; c < g.ncols; c += 32) {
       int32_t x = g.i0 + c, dd = 0;
       for (int q = nI - 1; q >= 0; --q) {
         const int32_t qq = fdiv(x, v.leg[q]), idx = x - qq * j.dim[q];
@@ -457,9 +462,9 @@ __device__ __forceinline__ void stage_tables(const JobView& v, const TileGeo& g,
   }
 }
 
-// The tile's source rows into its stage: 16-byte chunks, consecutive threads
-// on consecutive chunks of a row (rows start 16-byte aligned, their lengths
-// are multiples of 16 bytes).
+// The tile's source rows into its stage: 16-byte chunks, consecutive lanes of
+// the producer warp on consecutive chunks of a row (rows start 16-byte
+// aligned, their lengths are multiples of 16 bytes).
 template <typename Tin>
 __device__ __forceinline__ void stage_copies(const Tin* __restrict__ src, const TileGeo& g, int ti, Tin* buf,
                                              const int64_t* rowS, int tid) {
@@ -468,12 +473,12 @@ __device__ __forceinline__ void stage_copies(const Tin* __restrict__ src, const 
   const Tin* sb = src + g.bS + g.i0;
   if ((cpr & (cpr - 1)) == 0) {
     const int sh = __ffs(cpr) - 1;
-    for (int q = tid; q < nch; q += SPT) {
+    for (int q = tid; q < nch; q += 32) {
       const int r = q >> sh, c = q & (cpr - 1);
       cp_async16(buf + r * stride + c * V, sb + rowS[r] + c * V);
     }
   } else {
-    for (int q = tid; q < nch; q += SPT) {
+    for (int q = tid; q < nch; q += 32) {
       const int r = q / cpr, c = q - r * cpr;
       cp_async16(buf + r * stride + c * V, sb + rowS[r] + c * V);
     }
@@ -481,9 +486,9 @@ __device__ __forceinline__ void stage_copies(const Tin* __restrict__ src, const 
 }
 
 template <typename Tin, int MODE>
-__global__ void __launch_bounds__(SPT) perm_staged_kernel(const PermJob* __restrict__ jobs, int njobs, int64_t tiles,
-                                                          const Tin* __restrict__ src, const Tin* __restrict__ src1,
-                                                          void* __restrict__ dst0, void* __restrict__ dst1) {
+__global__ void __launch_bounds__(SPT, 3) perm_staged_kernel(const PermJob* __restrict__ jobs, int njobs, int64_t tiles,
+                                                             const Tin* __restrict__ src, const Tin* __restrict__ src1,
+                                                             void* __restrict__ dst0, void* __restrict__ dst1, int* err) {
   using Cfg = StagedCfg<Tin>;
   extern __shared__ uint8_t sm_raw[];
   uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(sm_raw) + 127) & ~uintptr_t(127));
@@ -495,52 +500,78 @@ __global__ void __launch_bounds__(SPT) perm_staged_kernel(const PermJob* __restr
   int16_t* colP = colS + PERM_STAGES * Cfg::MAXTI;
   StageMeta* meta = reinterpret_cast<StageMeta*>(colP + PERM_STAGES * Cfg::MAXTI);
   JobView* jv = reinterpret_cast<JobView*>(meta + PERM_STAGES);
+  uint64_t* full = reinterpret_cast<uint64_t*>(jv + SPP);
+  uint64_t* empty = full + PERM_STAGES;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (tid == 0) {
+    for (int s = 0; s < PERM_STAGES; ++s) {
+      mbar_init(&full[s], 64);    // the producing warp's lanes: tables written (32), copies landed (32)
+      mbar_init(&empty[s], SPW);  // one per writer warp
+    }
+    fence_mbar_init();
+  }
+  __syncthreads();
   // Each CTA takes one contiguous range of tiles (the ranges differ in length
   // by at most one), so that consecutive tiles mostly belong to the same job.
   const int64_t t_first = (int64_t)blockIdx.x * tiles / gridDim.x;
   const int64_t n = ((int64_t)blockIdx.x + 1) * tiles / gridDim.x - t_first;
-  int nj = -1, loaded = -1;
-  int64_t next_begin = 0;
-  // Tile k + PERM_AHEAD is staged (tables, then copies) while tile k is
-  // written out: every thread commits one cp.async group per tile, so that
-  // waiting for all but the PERM_AHEAD newest groups completes tile k.
-  auto stage = [&](int64_t k) {
-    if (k < n) {
+  if (warp >= SPW) {
+    // ---- producer warps: tile k = p, p + SPP, ...: wait for its slot, build
+    // its tables, copy its source rows (the lanes' cp.async copies arrive on
+    // the slot's mbarrier when they land)
+    const int pw = warp - SPW;
+    JobView* v = jv + pw;
+    int nj = -1, loaded = -1;
+    int64_t next_begin = 0;
+    bool first = true;
+    for (int64_t k = pw; k < n; k += SPP) {
+      const int s = (int)(k % PERM_STAGES);
+      const uint32_t par = (uint32_t)((k / PERM_STAGES) & 1);
+      bool ok = true;
+      if (lane == 0) ok = mbar_wait(&empty[s], par ^ 1, err);
+      __syncwarp();  // the writers' reads of the slot come before this warp's writes
+      if (!__shfl_sync(0xffffffffu, ok ? 1 : 0, 0)) break;
       const int64_t t = t_first + k;
       nj = find_job(jobs, njobs, tiles, t, nj, next_begin, lane);
-      if (nj != loaded) {  // the same for every warp
-        __syncthreads();   // nobody reads the view any more
-        load_job(jobs + nj, jv, tid);
-        __syncthreads();
+      if (nj != loaded) {
+        load_job(jobs + nj, v, lane);
+        __syncwarp();
         loaded = nj;
       }
-      const int s = (int)(k % PERM_STAGES);
-      const TileGeo g = tile_geo(*jv, t);
-      stage_tables<Tin>(*jv, g, rowS + s * PERM_MAX_ROWS, rowD + s * PERM_MAX_ROWS, colD + s * Cfg::MAXTI,
-                        colS + s * Cfg::MAXTI, colP + s * Cfg::MAXTI, meta + s, tid);
-      const int ti = jv->j.ti;
-      const Tin* __restrict__ from = jv->j.src_sel ? src1 : src;
-      __syncthreads();  // rowS of the stage is complete
-      if (k == 0) {
+      const TileGeo g = tile_geo(*v, t);
+      stage_tables<Tin>(*v, g, rowS + s * PERM_MAX_ROWS, rowD + s * PERM_MAX_ROWS, colD + s * Cfg::MAXTI,
+                        colS + s * Cfg::MAXTI, colP + s * Cfg::MAXTI, meta + s, lane);
+      const int ti = v->j.ti;
+      const Tin* __restrict__ from = v->j.src_sel ? src1 : src;
+      __syncwarp();  // every lane's row offsets are in rowS
+      if (first) {
         // tensors are touched from here on (the job table and the tables
         // above are not written by kernels): wait for the grid before this
-        // one, then let the next one start
+        // one (launched with programmatic serialisation), then let the next
+        // one start
         pdl_wait();
-        if (tid == 0) pdl_launch_dependents();
+        if (pw == 0 && lane == 0) pdl_launch_dependents();
+        first = false;
       }
-      stage_copies<Tin>(from, g, ti, buf + s * Cfg::STAGE_ELEMS, rowS + s * PERM_MAX_ROWS, tid);
+      mbar_arrive(&full[s]);  // this lane's table entries are written
+      stage_copies<Tin>(from, g, ti, buf + s * Cfg::STAGE_ELEMS, rowS + s * PERM_MAX_ROWS, lane);
+      cp_async_mbar_arrive_noinc(&full[s]);  // ... and its copies have landed
     }
-    cp_async_commit();
-  };
-  for (int k = 0; k < PERM_AHEAD; ++k) stage(k);
+    // no copy of this warp may still be landing when the CTA's shared memory
+    // is released (after an early exit the writers no longer wait for them)
+    cp_async_wait_all();
+    return;
+  }
+  // ---- writer warps: tile k once its slot is full, then release the slot
+  bool first = true;
   for (int64_t k = 0; k < n; ++k) {
-    // the stage of tile k + PERM_AHEAD was last read for tile k - 1, before
-    // the barrier that ended the previous iteration
-    stage(k + PERM_AHEAD);
-    cp_async_wait_group<PERM_AHEAD>();
-    __syncthreads();  // every thread's copies of tile k have landed
     const int s = (int)(k % PERM_STAGES);
+    const uint32_t par = (uint32_t)((k / PERM_STAGES) & 1);
+    if (!mbar_wait(&full[s], par, err)) break;
+    if (first) {  // before the first store (the previous grid has completed)
+      pdl_wait();
+      first = false;
+    }
     const StageMeta m = meta[s];
     const Tin* tb = buf + s * Cfg::STAGE_ELEMS;
     const int32_t* rd = rowD + s * PERM_MAX_ROWS;
@@ -620,7 +651,8 @@ __global__ void __launch_bounds__(SPT) perm_staged_kernel(const PermJob* __restr
         }
       }
     }
-    __syncthreads();  // tile k's stage is free
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&empty[s]);
   }
 }
 
@@ -635,7 +667,7 @@ static cudaError_t go_staged(ftn_ctx ctx, const PermJob* d_jobs, int njobs, int6
   int64_t cap = (int64_t)ctx->num_sms * 3;
   if (grid > cap) grid = cap;
   return launch_pdl(perm_staged_kernel<Tin, MODE>, (unsigned)grid, SPT, Cfg::BYTES, ctx->stream, d_jobs, njobs, tiles,
-                    (const Tin*)src, (const Tin*)src1, dst0, dst1);
+                    (const Tin*)src, (const Tin*)src1, dst0, dst1, ctx->dev_err);
 }
 
 template <typename Tin, int MODE>

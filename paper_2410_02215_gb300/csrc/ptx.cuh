@@ -1,5 +1,5 @@
 // Inline-PTX helpers for sm_103a: mbarriers with bounded waits, TMA tile
-// loads, cp.async copies and groups, programmatic dependent launch
+// loads, cp.async copies tracked on mbarriers, programmatic dependent launch
 // (griddepcontrol), and the tcgen05 tensor-core path (TMEM allocation, MMA,
 // commit, TMEM loads).  Every mbarrier wait gives up after a time limit and
 // records an error instead of spinning forever.
@@ -91,13 +91,12 @@ __device__ __forceinline__ void tensormap_acquire(const void* tmap) {
 __device__ __forceinline__ void cp_async16(void* smem_dst, const void* gsrc) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(smem_dst)), "l"(gsrc) : "memory");
 }
-// Close this thread's group of cp.async copies issued since the last commit.
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-// Wait until at most N of this thread's committed groups are still in flight.
-template <int N>
-__device__ __forceinline__ void cp_async_wait_group() {
-  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+// One arrival on the mbarrier once every earlier cp.async of this thread has
+// landed (counted against the barrier's expected arrivals).
+__device__ __forceinline__ void cp_async_mbar_arrive_noinc(uint64_t* bar) {
+  asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 
 // ---- programmatic dependent launch ---------------------------------------------
