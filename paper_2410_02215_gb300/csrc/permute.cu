@@ -11,7 +11,7 @@
 // reciprocals of its leg dimensions cached in shared memory -- and copy its
 // source rows into a PERM_STAGES-deep shared-memory ring with 16-byte
 // cp.async copies spread over their lanes (consecutive lanes on consecutive
-// chunks of a row; completion tracked on an mbarrier), while eight writer
+// chunks of a row; completion tracked on an mbarrier), while six writer
 // warps write earlier tiles out along the destination's contiguous direction,
 // releasing ring slots through a second set of mbarriers (no block-wide
 // synchronisation in the loop).  The copies hold no registers while in
@@ -239,7 +239,7 @@ struct StageMeta {
   int32_t iwrite, qw, qp, wsuf;
 };
 
-constexpr int SPW = 8;                   // writer warps of the staged kernel
+constexpr int SPW = 6;                   // writer warps of the staged kernel
 constexpr int SPP = 2;                   // producer warps (alternate tiles)
 constexpr int SPT = 32 * (SPW + SPP);    // its threads
 
