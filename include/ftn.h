@@ -27,8 +27,12 @@
  *   after it).  Result legs: X's free legs in order, then Y's.  Contracted
  *   legs must have equal (d_even, d_odd) and opposite duals.
  * Streams: every call is asynchronous on the context's CUDA stream unless
- *   stated otherwise.  Errors are returned as ftn_status; no exception
- *   crosses the ABI; ftn_last_error() gives a message for the calling thread.
+ *   stated otherwise.  The sign-permute and tensor-core GEMM kernels are
+ *   launched with programmatic stream serialisation: they may begin while the
+ *   kernel before them in the stream is still running, but read or write no
+ *   tensor data until it has completed, so stream order is kept for any
+ *   earlier work.  Errors are returned as ftn_status; no exception crosses
+ *   the ABI; ftn_last_error() gives a message for the calling thread.
  * Ownership: the caller owns the tensors it creates or wraps and releases
  *   them with ftn_tensor_free.  Library-allocated buffers come from the
  *   context's allocator callbacks (or cudaMallocAsync on the context stream

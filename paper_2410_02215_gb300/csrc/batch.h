@@ -26,7 +26,7 @@ struct PermBatch {
     const char* src;
     char* dst;
   };
-  std::vector<Item> items[2];  // [register-staged kernel, TMA-staged kernel]
+  std::vector<Item> items[2];  // [register-staged kernel, shared-memory-staged kernel]
   // Adds the finalised jobs of one plan table (tile_begin prefix sums over
   // total tiles) read from src and written to dst (hi plane).
   void add(const std::vector<PermJob>& jobs, int64_t total_tiles, int staged, const void* src, void* dst);

@@ -25,10 +25,11 @@ constexpr int DEV_ERR_TIMEOUT = 1;
 //   O: legs with the smallest destination strides not in I (product PO),
 //   B: the rest (product PB).
 // A tile covers tr values of the O index times ti values of the I index for
-// one batch index.  Two kernels share the job format: a TMA-staged one
-// (bulk copies of contiguous source rows into a shared-memory ring; needs
-// 16-byte aligned rows) and a register-staged fallback with fixed 32 x 64
-// tiles.  finalize_perm_jobs() picks the kernel and the tiling.
+// one batch index.  Two kernels share the job format: a shared-memory-staged
+// one (16-byte cp.async copies of contiguous source rows into a
+// shared-memory ring; needs 16-byte aligned rows) and a register-staged
+// fallback with fixed 32 x 64 tiles.  finalize_perm_jobs() picks the kernel
+// and the tiling.
 constexpr int PERM_TI = 32;   // fallback tile: I extent
 constexpr int PERM_GROUP_MIN = 32;   // I group (source-contiguous suffix): at least this many elements,
 constexpr int PERM_GROUP_I = 128;    // grown further towards this many (never past PERM_GROUP_IMAX)
@@ -279,7 +280,7 @@ cudaError_t launch_pdl(void (*kernel)(KArgs...), unsigned grid, unsigned block, 
 }
 
 // kernel launchers (asynchronous on ctx->stream)
-// Chooses the kernel (returns 1 for the TMA-staged one) and fills the tiling
+// Chooses the kernel (returns 1 for the shared-memory-staged one) and fills the tiling
 // and tile prefix sums of every job; *tiles receives the total.
 int finalize_perm_jobs(std::vector<PermJob>& jobs, size_t elem_size, int64_t* tiles, bool allow_staged);
 ftn_status launch_permute(ftn_ctx ctx, const PermJob* d_jobs, int njobs, int64_t tiles, int staged, const void* src,

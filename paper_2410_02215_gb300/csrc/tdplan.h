@@ -49,7 +49,7 @@ struct TdPlan {
   int64_t af_elems = 0, bf_elems = 0;
   std::vector<PermJob> ja, jb, jc;
   int64_t ta = 0, tb = 0, tc = 0;
-  int sa = 0, sb = 0, sc = 0;  // staged (TMA) permute kernel usable
+  int sa = 0, sb = 0, sc = 0;  // shared-memory-staged permute kernel usable
   // Both operands in one launch (B's jobs read the second source and write
   // after A's fused matrices): empty when the two need different kernels.
   std::vector<PermJob> jab;

@@ -306,7 +306,7 @@ int finalize_perm_jobs(std::vector<PermJob>& jobs, size_t es, int64_t* tiles, bo
   bool staged = allow_staged && !jobs.empty();
   int64_t total = 0;
   for (const PermJob& j : jobs) total += (int64_t)j.PI * j.PO * j.PB;
-  if (total < 65536) staged = false;  // tiny tensors: launch latency dominates, skip the TMA round trip
+  if (total < 65536) staged = false;  // tiny tensors: launch latency dominates, skip the staging ring
   for (PermJob& j : jobs) {
     bool ok = (j.PI % V == 0) && (j.src_off % V == 0);
     for (int q = j.nI; q < j.nI + j.nO + j.nB; ++q) ok = ok && (j.sstr[q] % V == 0);

@@ -253,7 +253,7 @@ static ftn_status build_plan(ftn_ctx ctx, const ftn_tensor_s* A, const ftn_tenso
   P->sb = finalize_perm_jobs(P->jb, dtype_size(B->dtype), &P->tb, al_b);
   // Both operands in one launch: B's jobs read the second source and write
   // after A's fused matrices (the workspace holds [A hi | B hi | A lo | B lo]).
-  // Kept when the merged list runs on the TMA-staged kernel, or when both
+  // Kept when the merged list runs on the shared-memory-staged kernel, or when both
   // operands were on the register-staged one anyway.
   if (!ja_raw.empty() && !jb_raw.empty()) {
     const bool half = prec_half(prec);
