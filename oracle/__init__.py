@@ -21,7 +21,8 @@ explicitly to the dense arrays, following the paper (arXiv:2410.02215):
 * the gradient of a contraction with respect to either operand, by its
   definition (one contraction per parity-allowed entry);
 * the gradient of the QR/SVD compression, by the reverse-mode rules of its
-  steps (pinned by finite differences of the forward oracle);
+  steps, and of a closed network's value through its contraction tree and
+  compressions (both pinned by finite differences of the forward oracle);
 * the cluster approximation of local energy terms, Sec. V (cluster networks
   in the globally ordered formalism, Fig. 4b).
 
@@ -37,3 +38,4 @@ from .hubbard import *  # noqa: F401,F403
 from .adjoint import *  # noqa: F401,F403
 from .cluster import *  # noqa: F401,F403
 from .compress_adjoint import *  # noqa: F401,F403
+from .network_grad import *  # noqa: F401,F403
