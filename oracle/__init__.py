@@ -24,7 +24,8 @@ explicitly to the dense arrays, following the paper (arXiv:2410.02215):
   steps, and of a closed network's value through its contraction tree and
   compressions (both pinned by finite differences of the forward oracle);
 * the cluster approximation of local energy terms, Sec. V (cluster networks
-  in the globally ordered formalism, Fig. 4b).
+  in the globally ordered formalism, Fig. 4b);
+* U(1) x parity tensors (charges whose parity is the charge mod 2, Sec. II.B).
 
 Parity pins: every function is checked by ``tests/test_oracle_*.py`` against
 closed forms printed in the paper, textbook reductions (bosonic legs ->
@@ -39,3 +40,4 @@ from .adjoint import *  # noqa: F401,F403
 from .cluster import *  # noqa: F401,F403
 from .compress_adjoint import *  # noqa: F401,F403
 from .network_grad import *  # noqa: F401,F403
+from .u1 import *  # noqa: F401,F403
