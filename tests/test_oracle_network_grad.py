@@ -1,7 +1,8 @@
 """Pins of the oracle's network gradient (oracle.network_grad): reverse mode
 through the contraction tree and its compressions.
 
-* the value is the value of oracle.contract_tree (same walk);
+* the value is the value of oracle.contract_tree (same walk), in the
+  locally and in the globally ordered formalism;
 * exact contraction is linear in every tensor, so v = sum(T_i * dv/dT_i) for
   each input tensor T_i (Euler's identity for a function linear in T_i);
 * with late or early compression at a truncating chi (gaps checked), the
@@ -28,8 +29,8 @@ def setup(lx, ly, D, seed):
     return net, tree
 
 
-def value(net, tree, policy, chi):
-    return float(O.contract_tree(net, tree, mode="local", policy=policy, chi=chi)[0].data)
+def value(net, tree, policy, chi, mode="local"):
+    return float(O.contract_tree(net, tree, mode=mode, policy=policy, chi=chi)[0].data)
 
 
 def allowed_entries(t):
@@ -41,7 +42,7 @@ def allowed_entries(t):
     return out
 
 
-def fd_check(net, tree, policy, chi, grads, samples=20, seed=0, h=1e-6, scale=None):
+def fd_check(net, tree, policy, chi, grads, samples=20, seed=0, h=1e-6, scale=None, mode="local"):
     rng = np.random.default_rng(seed)
     worst = 0.0
     if scale is None:
@@ -56,36 +57,39 @@ def fd_check(net, tree, policy, chi, grads, samples=20, seed=0, h=1e-6, scale=No
             d = tensors[i].data.copy()
             d[idx] += sgn * h
             tensors[i] = O.GTensor(d, tensors[i].legs, tensors[i].parity)
-            vals.append(value(O.Network(tensors, net.bonds, net.positions), tree, policy, chi))
+            vals.append(value(O.Network(tensors, net.bonds, net.positions), tree, policy, chi, mode))
         fd = (vals[0] - vals[1]) / (2 * h)
         worst = max(worst, abs(fd - grads[i].data[idx]) / scale)
     return worst
 
 
+@pytest.mark.parametrize("mode", ["local", "global"])
 @pytest.mark.parametrize("lx,ly,D", [(2, 2, (1, 1)), (2, 3, (1, 1)), (2, 2, (2, 1))])
 @pytest.mark.parametrize("policy,chi", [("exact", None), ("late", 2), ("early", 2)])
-def test_value_is_the_executor_value(lx, ly, D, policy, chi):
+def test_value_is_the_executor_value(lx, ly, D, policy, chi, mode):
     net, tree = setup(lx, ly, D, 1)
-    v, _, _ = NG.contract_tree_grad(net, tree, policy, chi)
-    assert v == value(net, tree, policy, chi)
+    v, _, _ = NG.contract_tree_grad(net, tree, policy, chi, mode=mode)
+    assert v == value(net, tree, policy, chi, mode)
 
 
+@pytest.mark.parametrize("mode", ["local", "global"])
 @pytest.mark.parametrize("lx,ly,D", [(2, 2, (1, 1)), (2, 3, (1, 1)), (2, 2, (2, 1))])
-def test_exact_gradient_satisfies_euler_identity(lx, ly, D):
+def test_exact_gradient_satisfies_euler_identity(lx, ly, D, mode):
     net, tree = setup(lx, ly, D, 2)
-    v, grads, _ = NG.contract_tree_grad(net, tree)
+    v, grads, _ = NG.contract_tree_grad(net, tree, mode=mode)
     for t, g in zip(net.tensors, grads):
         assert abs(float(np.sum(t.data * g.data)) - v) <= 1e-12 * abs(v)
 
 
+@pytest.mark.parametrize("mode", ["local", "global"])
 @pytest.mark.parametrize("lx,ly,D,chi", [(2, 2, (1, 1), 2), (2, 3, (1, 1), 2), (2, 2, (2, 1), 3)])
 @pytest.mark.parametrize("policy", ["late", "early"])
-def test_truncated_gradient_matches_finite_differences(lx, ly, D, chi, policy):
+def test_truncated_gradient_matches_finite_differences(lx, ly, D, chi, policy, mode):
     net, tree = setup(lx, ly, D, 3)
-    v, grads, gap = NG.contract_tree_grad(net, tree, policy, chi)
+    v, grads, gap = NG.contract_tree_grad(net, tree, policy, chi, mode=mode)
     assert gap is not None and gap > 1e-4  # truncation happens, away from a degeneracy
-    assert v != value(net, tree, "exact", None)
-    assert fd_check(net, tree, policy, chi, grads) < 1e-6
+    assert v != value(net, tree, "exact", None, mode)
+    assert fd_check(net, tree, policy, chi, grads, mode=mode) < 1e-6
 
 
 def test_planted_mistake_fails_the_finite_differences(monkeypatch):
