@@ -153,6 +153,8 @@ def contract_sampled(x, y, ax, ay, out_perm, n_samples, seed, arrows=True):
     idx_out = []
     vals = []
     total_par = x.parity ^ y.parity
+    if n_samples > 0 and not np.any((_multi_parity(legs) & 1) == total_par):
+        raise ValueError("the result has no parity-allowed entry to sample")
     while len(vals) < n_samples:
         idx = [int(g.integers(d)) for d in dims]
         if sum(int(idx[k] >= legs[k][0]) for k in range(r)) % 2 != total_par:
