@@ -118,6 +118,19 @@ FTN_API ftn_status ftn_ctx_set_tuning(ftn_ctx ctx, int on);
 /* Synchronise the context stream and report a device-side error recorded
  * since the last call (FTN_ETIMEOUT after a bounded wait gave up). */
 FTN_API ftn_status ftn_ctx_synchronize(ftn_ctx ctx);
+/* Self-test of device-side failure reporting (no counterpart in the paper;
+ * a property of this implementation).  Every wait of the tensor-core GEMM
+ * and the staged sign-permute on an mbarrier gives up after 2 s, records a
+ * timeout in the context's device error word, lets the other waits of the
+ * launch bail out, and the kernel returns instead of hanging; the next
+ * ftn_ctx_synchronize reports FTN_ETIMEOUT and clears the word.  This call
+ * launches one single-thread kernel on the context stream that waits,
+ * through the same bounded-wait code, on an mbarrier phase nothing ever
+ * completes, with the limit limit_ns (1e3 to 1e10 ns, else FTN_EINVAL)
+ * instead of 2 s.  It faults nothing: the kernel returns after the limit.
+ * Results of other work issued on the context between this call and the
+ * next ftn_ctx_synchronize are unspecified (their waits may bail out). */
+FTN_API ftn_status ftn_ctx_wait_selftest(ftn_ctx ctx, uint64_t limit_ns);
 /* Number of kernels this context has launched so far. */
 FTN_API int64_t ftn_ctx_launch_count(ftn_ctx ctx);
 /* Per-launch timing: while enabled, every kernel launch is bracketed by CUDA
@@ -209,10 +222,10 @@ FTN_API ftn_status ftn_tensordot_grad(ftn_ctx ctx, ftn_tensor A, ftn_tensor B, f
 /* ---- tensordot without device allocation ---------------------------------- */
 
 /* The paper has no counterpart of this entry point; it exists for callers
- * that cannot allocate device memory, directly or through the library --
- * code running inside a stream capture that forbids allocation, plug-in
- * hosts that hand over only pre-reserved buffers, latency-critical loops
- * that cannot afford an allocator round trip.
+ * that cannot allocate device memory, directly or through the library:
+ * plug-in hosts that hand a library only the buffers they reserved up front,
+ * and processes whose device memory belongs to another framework's allocator
+ * that must not be grown behind its back.
  *
  * Same operation as ftn_tensordot (without the extra bond-parity masks) on
  * raw device buffers: A and B are described by their legs and parity and
@@ -226,11 +239,15 @@ FTN_API ftn_status ftn_tensordot_grad(ftn_ctx ctx, ftn_tensor A, ftn_tensor B, f
  * device-allocating routine (host bookkeeping uses the C++ heap).  A
  * contraction that needs more scratch than the array holds, or a result
  * larger than c_capacity, is rejected with FTN_EINVAL and a message.  The
- * first call on each device (that device current) looks up the array's
- * device address once; make it before any stream capture.  All calls share
- * the array and it keeps the last call's contents: calls whose work overlaps
- * on the GPU race on it (host threads are serialised, GPU streams are not).
- * The call synchronises `cuda_stream` once while it uploads its plan. */
+ * first call on each device (that device current)
+ * looks up the array's device address once.  All calls share the array and
+ * it keeps the last call's contents.  Work of two calls overlapping on the
+ * GPU would race on it; the call prevents that by serialising callers with a
+ * host lock and by returning only after its work on `cuda_stream` (and
+ * everything queued there before it) has finished: it copies its plan tables
+ * from pageable host memory on the stream and synchronises the stream at the
+ * end to read the device error word (FTN_ETIMEOUT when a bounded wait of the
+ * kernels gave up).  Tile-width tuning is off on this path. */
 #define FTN_NOALLOC_SCRATCH_BYTES ((size_t)64 << 20)
 FTN_API ftn_status ftn_tensordot_noalloc(void* cuda_stream, int rank_a, const int32_t* d_even_a,
                                          const int32_t* d_odd_a, const uint8_t* dual_a, int parity_a,

@@ -356,6 +356,8 @@ ftn_status staging_upload(ftn_ctx ctx, size_t bytes, void** dev);
 int prof_begin(ftn_ctx ctx, const char* label, double bytes, double flops);
 void prof_end(ftn_ctx ctx, int rec);
 void clear_plan_caches(ftn_ctx ctx);
+// One kernel whose bounded mbarrier wait never completes (ftn_ctx_wait_selftest).
+ftn_status launch_wait_selftest(ftn_ctx ctx, uint64_t limit_ns);
 bool probs_in_bounds(const std::vector<GemmProb>& probs, int64_t a_n, int64_t b_n, int64_t c_n);
 
 }  // namespace ftn

@@ -1,9 +1,11 @@
 // Small device kernels used by the contraction-tree executor: per-step
 // max-abs normalisation with an FP64 log-scale accumulator kept on the
-// device (no host round trip), and FP32 <-> FP64 casts.
+// device (no host round trip), and FP32 <-> FP64 casts; and the self-test of
+// the kernels' bounded waits.
 #include <algorithm>
 
 #include "batch.h"
+#include "ptx.cuh"
 
 namespace ftn {
 
@@ -242,6 +244,24 @@ __global__ void gather_results_kernel(const ResultJob* __restrict__ jobs, int nj
 ftn_status launch_gather_results(ftn_ctx ctx, const ResultJob* d_jobs, int njobs, double* out) {
   if (njobs == 0) return FTN_OK;
   gather_results_kernel<<<(unsigned)((njobs + 255) / 256), 256, 0, ctx->stream>>>(d_jobs, njobs, out);
+  ctx->launches += 1;
+  FTN_CUDA(cudaGetLastError());
+  return FTN_OK;
+}
+
+// One thread waits on an mbarrier phase that nothing completes, through the
+// same bounded-wait helper the tensor-core GEMM and the staged permute use,
+// so the wait gives up after limit_ns, records DEV_ERR_TIMEOUT in the error
+// word and the kernel returns.
+__global__ void wait_selftest_kernel(int* err, uint64_t limit_ns) {
+  __shared__ __align__(8) uint64_t bar;
+  mbar_init(&bar, 1);
+  fence_mbar_init();
+  mbar_wait_for(&bar, 0, err, limit_ns, false);
+}
+
+ftn_status launch_wait_selftest(ftn_ctx ctx, uint64_t limit_ns) {
+  wait_selftest_kernel<<<1, 1, 0, ctx->stream>>>(ctx->dev_err, limit_ns);
   ctx->launches += 1;
   FTN_CUDA(cudaGetLastError());
   return FTN_OK;

@@ -1,8 +1,8 @@
-// ftn_tensordot_noalloc: the fermionic tensordot for callers that must not
-// allocate device memory themselves or through the library -- for example
-// code running while a CUDA graph is being captured with allocation
-// forbidden, plug-in hosts that hand over only pre-reserved buffers, or
-// real-time callers that cannot afford an allocator round trip.
+// ftn_tensordot_noalloc: the fermionic tensordot for callers that cannot
+// allocate device memory themselves or through the library -- plug-in hosts
+// that hand a library only the buffers they reserved up front, or processes
+// whose device memory is owned by another framework's allocator and must not
+// be grown behind its back.
 //
 // Everything the contraction needs beyond its inputs and output (the fused
 // sector matrices, the plan tables, the device error word) is carved out of
@@ -11,9 +11,12 @@
 // Host code must never use the array's name as a device address: the name is
 // a host-side stand-in.  The first call on each device (with that device
 // current) asks the runtime for the array's device address once and caches
-// it; make that first call before any stream capture.  All calls share the
-// array and it keeps the last call's contents; calls whose work overlaps on
-// the GPU (different streams, no ordering between them) race on it.
+// it.  All calls share the array and it keeps the last call's contents (the
+// error word at its start is cleared by every call).  Work of two calls that
+// overlapped on the GPU would race on the array; this entry point prevents
+// that by holding a host lock for the whole call and returning only after its
+// work on the stream has finished (it synchronises the stream to read the
+// error word, so a bounded wait that gave up is reported as FTN_ETIMEOUT).
 #include <mutex>
 
 #include "tdplan.h"
@@ -73,6 +76,7 @@ extern "C" ftn_status ftn_tensordot_noalloc(void* cuda_stream, int rank_a, const
   ctx.free_fn = bump_free;
   ctx.user = &bump;
   ctx.device = dev;
+  ctx.tune = false;  // the tile-width tuner would take scratch per candidate and synchronise per run
   FTN_CUDA(cudaDeviceGetAttribute(&ctx.num_sms, cudaDevAttrMultiProcessorCount, dev));
   ctx.dev_err = (int*)bump_alloc(256, &bump);
   FTN_CUDA(cudaMemsetAsync(ctx.dev_err, 0, 256, ctx.stream));
@@ -118,6 +122,16 @@ extern "C" ftn_status ftn_tensordot_noalloc(void* cuda_stream, int rank_a, const
       st = set_error(FTN_EINVAL,
                      "ftn_tensordot_noalloc: the contraction needs more scratch than the static "
                      "FTN_NOALLOC_SCRATCH_BYTES array provides");
+  }
+  if (st == FTN_OK) {
+    // report a device-side bounded wait that gave up (error word at the array's start)
+    int err = 0;
+    cudaError_t e = cudaMemcpyAsync(&err, ctx.dev_err, sizeof(int), cudaMemcpyDeviceToHost, ctx.stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx.stream);
+    if (e != cudaSuccess)
+      st = cuda_error(e, "ftn_tensordot_noalloc: reading the device error word");
+    else if (err)
+      st = set_error(FTN_ETIMEOUT, "ftn_tensordot_noalloc: a device-side bounded wait timed out");
   }
   clear_plan_caches(&ctx);  // releases plan tables into the (no-op) sub-allocator
   ftn_tensor_free(A);

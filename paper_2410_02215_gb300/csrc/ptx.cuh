@@ -50,12 +50,13 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
 
 constexpr uint64_t BAIL_CHECK_NS = 20000;  // waits shorter than this never read the error flag
 
-// Wait for the phase with the given parity.  Returns false after the time
-// limit (recording DEV_ERR_TIMEOUT in *err) or, when bail is set, once
-// another thread has recorded an error.  The error flag lives in global
-// memory, so it is read only after the wait has lasted BAIL_CHECK_NS: a read
-// on every round would delay noticing the phase by a memory round trip.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* err, bool bail = true) {
+// Wait for the phase with the given parity.  Returns false after limit_ns
+// (recording DEV_ERR_TIMEOUT in *err) or, when bail is set, once another
+// thread has recorded an error.  The error flag lives in global memory, so
+// it is read only after the wait has lasted BAIL_CHECK_NS: a read on every
+// round would delay noticing the phase by a memory round trip.
+__device__ __forceinline__ bool mbar_wait_for(uint64_t* bar, uint32_t parity, int* err, uint64_t limit_ns,
+                                              bool bail) {
   if (mbar_try_wait(bar, parity)) return true;
   const uint64_t t0 = globaltimer();
   while (true) {
@@ -63,12 +64,17 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* e
     for (int i = 0; i < 32; ++i)
       if (mbar_try_wait(bar, parity)) return true;
     const uint64_t dt = globaltimer() - t0;
-    if (dt > WAIT_LIMIT_NS) {
+    if (dt > limit_ns) {
       atomicCAS(err, 0, 1);
       return false;
     }
     if (bail && dt > BAIL_CHECK_NS && *reinterpret_cast<volatile int*>(err) != 0) return false;
   }
+}
+
+// The kernels' waits: limit WAIT_LIMIT_NS.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* err, bool bail = true) {
+  return mbar_wait_for(bar, parity, err, WAIT_LIMIT_NS, bail);
 }
 
 __device__ __forceinline__ void tma_load_2d(void* smem_dst, const void* tmap, int x, int y, uint64_t* bar) {

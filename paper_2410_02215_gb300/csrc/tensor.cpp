@@ -479,6 +479,13 @@ ftn_status ftn_ctx_synchronize(ftn_ctx ctx) {
   return FTN_OK;
 }
 
+ftn_status ftn_ctx_wait_selftest(ftn_ctx ctx, uint64_t limit_ns) {
+  if (!ctx) return set_error(FTN_EINVAL, "null ctx");
+  if (limit_ns < 1000 || limit_ns > 10000000000ull)
+    return set_error(FTN_EINVAL, "ftn_ctx_wait_selftest: limit_ns must lie in [1e3, 1e10]");
+  return launch_wait_selftest(ctx, limit_ns);
+}
+
 int64_t ftn_ctx_launch_count(ftn_ctx ctx) { return ctx ? ctx->launches : 0; }
 
 ftn_status ftn_ctx_profile(ftn_ctx ctx, int enable) {

@@ -71,6 +71,7 @@ def lib():
         "ftn_ctx_set_stream": [vp, vp],
         "ftn_ctx_set_tuning": [vp, C.c_int],
         "ftn_ctx_synchronize": [vp],
+        "ftn_ctx_wait_selftest": [vp, C.c_uint64],
         "ftn_tensor_create": [vp, C.c_int, i32p, i32p, u8p, C.c_int, C.c_int, C.POINTER(vp)],
         "ftn_tensor_wrap": [vp, C.c_int, i32p, i32p, u8p, C.c_int, C.c_int, vp, C.POINTER(vp)],
         "ftn_tensor_free": [vp],
@@ -174,6 +175,10 @@ class Context:
         """Tile-width tuning of large tensor-core contractions on their first
         use (ftn_ctx_set_tuning; on by default)."""
         _check(lib().ftn_ctx_set_tuning(self.handle, 1 if on else 0))
+
+    def wait_selftest(self, limit_ns):
+        """Launch the bounded-wait self-test kernel (ftn_ctx_wait_selftest)."""
+        _check(lib().ftn_ctx_wait_selftest(self.handle, int(limit_ns)))
 
     def launches(self):
         return int(lib().ftn_ctx_launch_count(self.handle))
