@@ -5,9 +5,11 @@
 // GPU pipeline, FP64 throughout, per bond-parity sector pi:
 //   1. sign-permute X -> X_pi = [free_X | bond] and Y -> Y_pi^T = [free_Y | bond]
 //      (the fused layouts of the tensordot, bond parity of the arrow folded in);
-//   2. R factors with R^T R = X_pi^T X_pi (resp. Y_pi Y_pi^T): Gram matrix by the
-//      FP64 GEMM and a semi-definite Cholesky; a side with fewer rows than bond
-//      states uses the matrix itself (X_pi = I * X_pi);
+//   2. R factors of X_pi and Y_pi^T by Householder QR (only R is formed):
+//      each CTA streams a chunk of rows through shared memory into its own
+//      triangular factor, and a binary tree of the same kernel merges the
+//      chunks' factors (TSQR); a side with no more rows than bond states
+//      uses the matrix itself (X_pi = I * X_pi);
 //   3. core M_pi = R_X R_Y^T and its SVD by one-sided (Hestenes) Jacobi;
 //   4. one host synchronisation: the singular values of both sectors are
 //      pooled and the chi largest kept;
@@ -16,7 +18,9 @@
 // Step 5 is the projector form of X' = Q_X U sqrt(S), Y' = sqrt(S) V^T Q_Y^T:
 // Q_X U_k S_k = X R_Y^T V_k, so no orthogonal factor is ever formed.  With
 // chi at or above the rank, op(X', Y') = op(X, Y) exactly for any invertible
-// R factors.
+// R factors; below it the truncation is that of the exact SVD as long as the
+// R factors are backward stable (Householder: R^T R = (X + E)^T (X + E) with
+// |E| ~ eps |X|, whatever the condition of X).
 #include <algorithm>
 #include <cmath>
 #include <map>
@@ -30,9 +34,16 @@ namespace ftn {
 constexpr int LA_THREADS = 512;
 constexpr int LA_MAX_DIM = 1024;  // largest bond sector handled by the Jacobi SVD
 
-struct CholJob {
-  double* G;  // n x n row-major, symmetric; replaced by R (upper, R^T R = G)
-  int n;
+// One pass of the streaming Householder QR: the rows of src (rows x K, row
+// stride ld) are appended to the upper-triangular factor R (K x K row-major,
+// global memory) and R is updated so that R_new^T R_new = R^T R + src^T src.
+struct QrJob {
+  const double* src;
+  double* R;
+  int64_t rows, ld;
+  int K;
+  int init;  // 0: R starts as zero; 1: R holds a factor to extend
+  int tri;   // 1: src is upper triangular (row i is zero before column i)
 };
 
 struct SvdJob {
@@ -57,63 +68,93 @@ struct GatherJob {
   double* dr;
   double sl, sr;  // scale factors
   int nl, nr;
+  double* dsc;    // receives sc (the norm the n-side vector of this state gets)
+  double sc;
 };
 
-__device__ __forceinline__ double block_max(double v, double* red) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int o = 16; o; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
-  if (lane == 0) red[warp] = v;
-  __syncthreads();
-  if (warp == 0) {
-    v = lane < (int)(blockDim.x >> 5) ? red[lane] : 0.0;
-    for (int o = 16; o; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
-    if (lane == 0) red[32] = v;
-  }
-  __syncthreads();
-  return red[32];
-}
+// Kept n-side singular vectors of one bond sector: k rows of length n (row
+// stride n) in decreasing singular value, row j scaled to norm sc[j].
+struct OrthJob {
+  double* v;
+  const double* sc;
+  int k, n;
+};
 
-// Semi-definite Cholesky G = L L^T (right-looking); a pivot at or below
-// 1e-12 * max(diag G) marks a numerically dependent direction (a singular
-// value of the underlying matrix below 1e-6 of its largest, where a Gram
-// matrix carries only rounding noise) whose row of R is set to zero.
-// Writes R = L^T (upper triangle, zeros below).
-__global__ void __launch_bounds__(LA_THREADS) chol_kernel(const CholJob* jobs) {
-  __shared__ double red[33];
-  __shared__ double piv;
-  const CholJob jb = jobs[blockIdx.x];
-  double* G = jb.G;
-  const int n = jb.n;
-  double dmax = 0.0;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) dmax = fmax(dmax, G[(int64_t)i * n + i]);
-  dmax = block_max(dmax, red);
-  const double tol = 1e-12 * dmax;
-  for (int j = 0; j < n; ++j) {
-    if (threadIdx.x == 0) {
-      const double d = G[(int64_t)j * n + j];
-      piv = d > tol ? sqrt(d) : 0.0;
-      G[(int64_t)j * n + j] = piv;
+constexpr int QR_ROWS = 16;      // rows of src per pass (one per lane of warp 0 in the norm)
+constexpr int QR_THREADS = 128;
+
+// Householder QR, R factor only (Sec. II.A: the QR of each symmetry block).
+// Rows arrive in blocks of QR_ROWS held in shared memory.  For column j with
+// x = [a; b] = [R_jj; B(:, j)] the reflector H = I - tau v v^T, v = [1; b / (a
+// - beta)], beta = -sign(a) |x|, tau = (beta - a) / beta in [1, 2], maps x to
+// [beta; 0] and is applied to the trailing columns of R row j and of the
+// block (the form of LAPACK's dlarfg: |x| is taken after scaling by max|x|,
+// and no intermediate can overflow, however small b has become).  Row j of R
+// is read and written only at step j, so R stays in global memory (it is
+// L2-resident and each access is one coalesced row).  A column whose block
+// part is zero, or below 2^-960 in magnitude, needs no reflector (this also
+// skips the zero prefix of triangular sources).  Once a short block's rank
+// is absorbed its rows hold only rounding noise, which every further group
+// of reflectors shrinks by ~2^-52: that is where such tiny columns arise.
+__global__ void __launch_bounds__(QR_THREADS) qr_stream_kernel(const QrJob* jobs) {
+  extern __shared__ double qb[];  // QR_ROWS x K, row-major
+  __shared__ double refl[2];      // tau, 1 / (a - beta)
+  __shared__ int skip;
+  const QrJob J = jobs[blockIdx.x];
+  const int K = J.K, t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  double* R = J.R;
+  if (!J.init)
+    for (int64_t e = t; e < (int64_t)K * K; e += blockDim.x) R[e] = 0.0;
+  for (int64_t r0 = 0; r0 < J.rows; r0 += QR_ROWS) {
+    const int nb = (int)(J.rows - r0 < QR_ROWS ? J.rows - r0 : QR_ROWS);
+    __syncthreads();  // the previous block's last column is done (and R is zeroed)
+    for (int e = t; e < QR_ROWS * K; e += blockDim.x) {
+      const int i = e / K, c = e - i * K;
+      qb[e] = i < nb ? J.src[(r0 + i) * J.ld + c] : 0.0;
     }
     __syncthreads();
-    const double p = piv;
-    for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x)
-      G[(int64_t)i * n + j] = p > 0.0 ? G[(int64_t)i * n + j] / p : 0.0;
-    __syncthreads();
-    const int rest = n - j - 1;
-    const int64_t cnt = (int64_t)rest * rest;
-    for (int64_t e = threadIdx.x; e < cnt; e += blockDim.x) {
-      const int i = j + 1 + (int)(e / rest), k = j + 1 + (int)(e % rest);
-      if (k <= i) G[(int64_t)i * n + k] -= G[(int64_t)i * n + j] * G[(int64_t)k * n + j];
-    }
-    __syncthreads();
-  }
-  // R = L^T in place
-  const int64_t tot = (int64_t)n * n;
-  for (int64_t e = threadIdx.x; e < tot; e += blockDim.x) {
-    const int i = (int)(e / n), k = (int)(e % n);
-    if (i < k) {
-      G[(int64_t)i * n + k] = G[(int64_t)k * n + i];
-      G[(int64_t)k * n + i] = 0.0;
+    const int j0 = J.tri ? (int)(r0 < K ? r0 : K) : 0;
+    for (int j = j0; j < K; ++j) {
+      if (warp == 0) {
+        const double bj = lane < QR_ROWS ? qb[lane * K + j] : 0.0;
+        double mx = fabs(bj);
+        for (int o = 16; o; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        int sk = 1;
+        if (mx > 0x1p-960) {
+          const double a = R[(int64_t)j * K + j];
+          const double sc = fmax(mx, fabs(a));
+          const double u = bj / sc;
+          double ss = u * u;
+          for (int o = 16; o; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+          if (lane == 0) {
+            const double as = a / sc;
+            const double nrm = sc * sqrt(fma(as, as, ss));
+            const double beta = a > 0.0 ? -nrm : nrm;
+            refl[0] = (beta - a) / beta;
+            refl[1] = 1.0 / (a - beta);
+            R[(int64_t)j * K + j] = beta;
+          }
+          sk = 0;
+        }
+        if (lane == 0) skip = sk;
+      }
+      __syncthreads();
+      if (!skip) {
+        const double tau = refl[0], id = refl[1];
+        for (int c = j + 1 + t; c < K; c += blockDim.x) {
+          double* rp = R + (int64_t)j * K + c;
+          const double rjc = *rp;
+          double w = 0.0;
+#pragma unroll
+          for (int i = 0; i < QR_ROWS; ++i) w = fma(qb[i * K + j], qb[i * K + c], w);
+          w = tau * fma(w, id, rjc);
+          *rp = rjc - w;
+          const double wv = w * id;
+#pragma unroll
+          for (int i = 0; i < QR_ROWS; ++i) qb[i * K + c] = fma(-wv, qb[i * K + j], qb[i * K + c]);
+        }
+      }
+      __syncthreads();
     }
   }
 }
@@ -168,8 +209,9 @@ __device__ __forceinline__ bool jacobi_rotation(double al, double be, double ga,
 // |t_p . t_q| <= m eps |t_p| |t_q| (a computed dot product of length m
 // carries rounding of about m eps relative to |t_p| |t_q|, so a tighter test
 // would never be met).  Then T_f = Q^T T has rows s_j u_j^T (u_j the right
-// singular vectors of T) and the left ones follow as q_j = T u_j / s_j, so the
-// rotations themselves are never accumulated.
+// singular vectors of T) and the left ones follow as q_j = T u_j / s_j
+// (re-orthogonalised for the kept states, orth_rows_kernel), so the rotations
+// themselves are never accumulated.
 __device__ __forceinline__ double jacobi_tol2(int m) {
   const double tol = (double)(m > 8 ? m : 8) * 2.220446049250313e-16;
   return tol * tol;
@@ -509,6 +551,56 @@ __global__ void gather_kernel(const GatherJob* jobs) {
   const GatherJob g = jobs[blockIdx.x];
   for (int i = threadIdx.x; i < g.nl; i += blockDim.x) g.dl[i] = g.left[i] * g.sl;
   for (int i = threadIdx.x; i < g.nr; i += blockDim.x) g.dr[i] = g.right[i] * g.sr;
+  if (threadIdx.x == 0) *g.dsc = g.sc;
+}
+
+// The n-side vector q_j = T u_j / s_j inherits from u_j its rounding
+// components along the other singular directions, multiplied by s_i / s_j:
+// about m eps s_max / s_j along the directions of larger singular values,
+// which the projector form would amplify by s_j^{-1}.  Classical Gram-Schmidt
+// applied twice against the kept vectors of larger singular value (already
+// cleaned, in decreasing order) removes those components; the result keeps
+// both residuals |T u_j - s_j q_j| and |T^T q_j - s_j u_j| at the rounding
+// level of T, which is what the projectors X R_Y^T V S^{-1/2} need.  Rows
+// are renormalised to their target norms sc[j] = s_j^{-1/2}.
+__global__ void __launch_bounds__(256) orth_rows_kernel(const OrthJob* jobs) {
+  __shared__ double h[LA_MAX_DIM];
+  __shared__ double red[9];
+  const OrthJob J = jobs[blockIdx.x];
+  const int n = J.n, t = threadIdx.x, lane = t & 31, warp = t >> 5, nw = blockDim.x >> 5;
+  for (int j = 0; j < J.k; ++j) {
+    double* vj = J.v + (int64_t)j * n;
+    for (int pass = 0; pass < 2 && j > 0; ++pass) {
+      for (int i = warp; i < j; i += nw) {
+        const double* vi = J.v + (int64_t)i * n;
+        double d = 0.0;
+        for (int e = lane; e < n; e += 32) d = fma(vi[e], vj[e], d);
+        for (int o = 16; o; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+        if (lane == 0) h[i] = d / (J.sc[i] * J.sc[i]);
+      }
+      __syncthreads();
+      for (int e = t; e < n; e += blockDim.x) {
+        double a = vj[e];
+        for (int i = 0; i < j; ++i) a = fma(-h[i], J.v[(int64_t)i * n + e], a);
+        vj[e] = a;
+      }
+      __syncthreads();
+    }
+    double q = 0.0;
+    for (int e = t; e < n; e += blockDim.x) q = fma(vj[e], vj[e], q);
+    for (int o = 16; o; o >>= 1) q += __shfl_xor_sync(0xffffffffu, q, o);
+    if (lane == 0) red[warp] = q;
+    __syncthreads();
+    if (t == 0) {
+      double tot = 0.0;
+      for (int w = 0; w < nw; ++w) tot += red[w];
+      red[8] = tot > 0.0 ? J.sc[j] / sqrt(tot) : 0.0;
+    }
+    __syncthreads();
+    const double f = red[8];
+    for (int e = t; e < n; e += blockDim.x) vj[e] *= f;
+    __syncthreads();
+  }
 }
 
 // ---------------------------------------------------------------------------------
@@ -633,10 +725,14 @@ struct CJob {
   int64_t ws_n = 0, ws_off = 0;
   double* ws = nullptr;
   int64_t o_xf = 0, o_yf = 0;
-  int64_t o_px_part[2], o_py_part[2], o_gx[2], o_gy[2], o_m[2], o_tf[2], o_wk[2], o_zk[2], o_px[2], o_qy[2],
-      o_ms3[2], o_rxc[2], o_ryc[2];
+  int64_t o_gx[2], o_gy[2], o_m[2], o_tf[2], o_wk[2], o_zk[2], o_px[2], o_qy[2], o_ms3[2], o_rxc[2], o_ryc[2],
+      o_sc[2];
   int64_t s_off[2];  // singular values + sweep count in the batch's shared buffer
-  int sp_x[2], sp_y[2], rx[2], ry[2], ldx[2], ldy[2], nrot[2], mlen[2];
+  // Householder TSQR of the tall sides: chunks of qr_lx / qr_ly rows, one
+  // K x K factor slot per chunk at o_gx / o_gy (slot 0 holds the result)
+  int64_t qr_lx[2], qr_ly[2];
+  int qr_px[2], qr_py[2];
+  int rx[2], ry[2], ldx[2], ldy[2], nrot[2], mlen[2];
   int64_t rx_off[2], ry_off[2];
   bool tall_x[2], tall_y[2], trans[2];
   struct Cand {
@@ -678,23 +774,20 @@ ftn_status cj_prepare(ftn_ctx ctx, CJob& J) {
     J.tall_y[pi] = Cc > K;
     J.rx[pi] = (int)std::min(R, K);
     J.ry[pi] = (int)std::min(Cc, K);
-    J.o_gx[pi] = off;
-    off += J.tall_x[pi] ? al(K * K) : 0;
-    J.o_gy[pi] = off;
-    off += J.tall_y[pi] ? al(K * K) : 0;
-    // split-K over the long (row) dimension of the Gram products
-    auto split_for = [&](int64_t rows) {
-      const int64_t tiles = ((K + 63) / 64) * ((K + 63) / 64);
-      int64_t s = std::max<int64_t>(1, (2 * (int64_t)ctx->num_sms + tiles - 1) / tiles);
-      s = std::min<int64_t>(s, std::max<int64_t>(1, rows / 512));
-      return (int)std::min<int64_t>(s, 64);
+    // chunks of at least 2K rows (the merge tree then adds at most ~1/6 of
+    // the leaves' work), at most 256 per side
+    auto chunk_rows = [&](int64_t rows) {
+      int64_t L = std::max<int64_t>({2 * K, (rows + 255) / 256, (int64_t)QR_ROWS});
+      return (L + QR_ROWS - 1) / QR_ROWS * QR_ROWS;
     };
-    J.sp_x[pi] = J.tall_x[pi] ? split_for(R) : 1;
-    J.sp_y[pi] = J.tall_y[pi] ? split_for(Cc) : 1;
-    J.o_px_part[pi] = off;
-    off += J.sp_x[pi] > 1 ? al((int64_t)J.sp_x[pi] * K * K) : 0;
-    J.o_py_part[pi] = off;
-    off += J.sp_y[pi] > 1 ? al((int64_t)J.sp_y[pi] * K * K) : 0;
+    J.qr_lx[pi] = J.tall_x[pi] ? chunk_rows(R) : 0;
+    J.qr_px[pi] = J.tall_x[pi] ? (int)((R + J.qr_lx[pi] - 1) / J.qr_lx[pi]) : 0;
+    J.qr_ly[pi] = J.tall_y[pi] ? chunk_rows(Cc) : 0;
+    J.qr_py[pi] = J.tall_y[pi] ? (int)((Cc + J.qr_ly[pi] - 1) / J.qr_ly[pi]) : 0;
+    J.o_gx[pi] = off;
+    off += al((int64_t)J.qr_px[pi] * K * K);
+    J.o_gy[pi] = off;
+    off += al((int64_t)J.qr_py[pi] * K * K);
     J.o_rxc[pi] = off;
     off += al((int64_t)J.rx[pi] * K);
     J.o_ryc[pi] = off;
@@ -721,50 +814,43 @@ ftn_status cj_prepare(ftn_ctx ctx, CJob& J) {
     off += al((int64_t)J.nrot[pi] * K);
     J.o_qy[pi] = off;
     off += al((int64_t)J.nrot[pi] * K);
+    J.o_sc[pi] = off;
+    off += al(J.nrot[pi]);
   }
   J.ws_n = off;
   return FTN_OK;
 }
 
-// Gram products of the tall sides (split over rows where that gives more
-// tiles; the slabs are added by the ordered reduction) and their Cholesky jobs.
-ftn_status cj_gram(CJob& J, GemmF64Batch& gb, std::vector<CholJob>& chol) {
+// Householder TSQR jobs of the tall sides, by tree level: level 0 factors
+// every chunk into its own slot; level l >= 1 merges slot c + 2^(l-1) into
+// slot c for every c that is a multiple of 2^l (the merged factor is upper
+// triangular, its zero prefix skipped).  levels[l] receives the jobs.
+void cj_qr(CJob& J, std::vector<std::vector<QrJob>>& levels) {
   const TdPlan* P = J.P.get();
-  double* ws = J.ws;
-  std::vector<GemmProb> gram, reds;
-  auto add_gram = [&](int K, int rows, int64_t src, int64_t ld, int64_t dst, int64_t part, int nsplit) {
-    GemmProb g = make_prob(K, K, rows, src, 1, ld, src, 1, ld);
-    if (nsplit > 1) {
-      g.nsplit = nsplit;
-      g.kchunk = (rows + nsplit - 1) / nsplit;
-      g.kchunk = (g.kchunk + 15) / 16 * 16;
-      g.nsplit = (rows + g.kchunk - 1) / g.kchunk;
-      gemm_plain_output(g, part, K);
-      g.c_slab = (int64_t)K * K;
-      // the slabs at `part`, added in split order into the plain K x K result at dst
-      GemmProb r = make_prob(K, K, 0, part, 0, 0, 0, 0, 0);
-      gemm_plain_output(r, dst, K);
-      r.nsplit = g.nsplit;
-      r.c_slab = (int64_t)K * K;
-      reds.push_back(r);
-    } else {
-      gemm_plain_output(g, dst, K);
+  auto side = [&](int K, int64_t rows, int64_t src, int64_t ld, int64_t slots, int64_t L, int nchunk) {
+    if (nchunk == 0) return;
+    if (levels.empty()) levels.resize(1);
+    for (int c = 0; c < nchunk; ++c) {
+      const int64_t r0 = (int64_t)c * L;
+      levels[0].push_back({J.ws + src + r0 * ld, J.ws + slots + (int64_t)c * K * K, std::min(L, rows - r0), ld, K, 0,
+                           0});
     }
-    gram.push_back(g);
-    chol.push_back({ws + dst, K});
+    for (int l = 1; (1 << (l - 1)) < nchunk; ++l) {
+      if ((int)levels.size() <= l) levels.resize(l + 1);
+      const int h = 1 << (l - 1);
+      for (int c = 0; c + h < nchunk; c += 2 * h)
+        levels[l].push_back({J.ws + slots + (int64_t)(c + h) * K * K, J.ws + slots + (int64_t)c * K * K, K, K, K, 1,
+                             1});
+    }
   };
   for (int pi = 0; pi < 2; ++pi) {
     const int K = (int)P->K[pi];
     if (K == 0) continue;
     if (J.tall_x[pi] && P->M[pi] > 0)
-      add_gram(K, (int)P->M[pi], J.o_xf + P->afoff[pi], P->ldk[pi], J.o_gx[pi], J.o_px_part[pi], J.sp_x[pi]);
+      side(K, P->M[pi], J.o_xf + P->afoff[pi], P->ldk[pi], J.o_gx[pi], J.qr_lx[pi], J.qr_px[pi]);
     if (J.tall_y[pi] && P->N[pi] > 0)
-      add_gram(K, (int)P->N[pi], J.o_yf + P->bfoff[pi], P->ldk[pi], J.o_gy[pi], J.o_py_part[pi], J.sp_y[pi]);
+      side(K, P->N[pi], J.o_yf + P->bfoff[pi], P->ldk[pi], J.o_gy[pi], J.qr_ly[pi], J.qr_py[pi]);
   }
-  FTN_TRY(add_gemm_set(gb, gram, ws, ws, ws, J.ws_n, J.ws_n, J.ws_n));
-  if (!red_in_bounds(reds, J.ws_n, J.ws_n)) return set_error(FTN_EINVAL, "internal error: Gram reduction out of bounds");
-  add_reductions(gb, reds, ws, ws);
-  return FTN_OK;
 }
 
 // After the row counts: the compacted R factors and the core's shape.
@@ -882,17 +968,22 @@ ftn_status compress_batch(ftn_ctx ctx, std::vector<CompressItem>& items) {
     }
     FTN_TRY(flush_perm(ctx, pb, FTN_F64, PERM_SAME, 0));
   }
-  // ---- 2. Gram matrices and R factors ----
+  // ---- 2. R factors by Householder TSQR (one launch per tree level) ----
   {
-    GemmF64Batch gb(ctx);
-    std::vector<CholJob> chol;
-    for (CJob& J : jobs) FTN_TRY(cj_gram(J, gb, chol));
-    FTN_TRY(flush_gemm_f64(gb));
-    if (!chol.empty()) {
-      DevBuf t_chol(ctx);
-      FTN_TRY(put_table(ctx, chol, &t_chol.p));
-      const int rec = prof_begin(ctx, "cholesky", 0, 0);
-      chol_kernel<<<(unsigned)chol.size(), LA_THREADS, 0, ctx->stream>>>((const CholJob*)t_chol.p);
+    std::vector<std::vector<QrJob>> levels;
+    for (CJob& J : jobs) cj_qr(J, levels);
+    int kmax = 0;
+    for (auto& lv : levels)
+      for (const QrJob& q : lv) kmax = std::max(kmax, q.K);
+    const size_t smem = (size_t)QR_ROWS * kmax * sizeof(double);
+    if (smem > 48 * 1024) FTN_CUDA(cudaFuncSetAttribute(qr_stream_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                        (int)(QR_ROWS * LA_MAX_DIM * sizeof(double))));
+    for (auto& lv : levels) {
+      if (lv.empty()) continue;
+      DevBuf t_qr(ctx);
+      FTN_TRY(put_table(ctx, lv, &t_qr.p));
+      const int rec = prof_begin(ctx, "householder_qr", 0, 0);
+      qr_stream_kernel<<<(unsigned)lv.size(), QR_THREADS, smem, ctx->stream>>>((const QrJob*)t_qr.p);
       ctx->launches += 1;
       FTN_CUDA(cudaGetLastError());
       prof_end(ctx, rec);
@@ -1004,8 +1095,9 @@ ftn_status compress_batch(ftn_ctx ctx, std::vector<CompressItem>& items) {
   // m-side vectors (the orthogonalised rows' direction) come from T_f rows;
   // n-side vectors as T u_j / s_j by one GEMM with the untouched T.  Both are
   // wanted scaled by s^{-1/2}: MS = T_f row * s^{-3/2}, MS3 = T_f row * s^{-5/2}
-  // and NS = MS3 T^T.  Without transposition the m side is the right (ry)
-  // side of M, with it the left (rx) side.
+  // and NS = MS3 T^T, whose rows are then re-orthogonalised (orth_rows_kernel).
+  // Without transposition the m side is the right (ry) side of M, with it the
+  // left (rx) side.
   {
     std::vector<GatherJob> gat;
     for (CJob& J : jobs) {
@@ -1023,6 +1115,8 @@ ftn_status compress_batch(ftn_ctx ctx, std::vector<CompressItem>& items) {
         g.sr = is / (c.s * c.s);
         g.dl = J.ws + (J.trans[pi] ? J.o_wk[pi] : J.o_zk[pi]) + (int64_t)j * J.mlen[pi];
         g.dr = J.ws + J.o_ms3[pi] + (int64_t)j * J.mlen[pi];
+        g.dsc = J.ws + J.o_sc[pi] + j;
+        g.sc = is;
         gat.push_back(g);
       }
     }
@@ -1048,6 +1142,21 @@ ftn_status compress_batch(ftn_ctx ctx, std::vector<CompressItem>& items) {
       FTN_TRY(add_gemm_set(gb, nside, J.ws, J.ws, J.ws, J.ws_n, J.ws_n, J.ws_n));
     }
     FTN_TRY(flush_gemm_f64(gb));
+  }
+  {
+    // the n-side vectors re-orthogonalised against those of larger singular value
+    std::vector<OrthJob> orth;
+    for (CJob& J : jobs)
+      for (int pi = 0; pi < 2; ++pi)
+        if (J.k[pi] > 1)
+          orth.push_back({J.ws + (J.trans[pi] ? J.o_zk[pi] : J.o_wk[pi]), J.ws + J.o_sc[pi], J.k[pi], J.nrot[pi]});
+    if (!orth.empty()) {
+      DevBuf t_orth(ctx);
+      FTN_TRY(put_table(ctx, orth, &t_orth.p));
+      orth_rows_kernel<<<(unsigned)orth.size(), 256, 0, ctx->stream>>>((const OrthJob*)t_orth.p);
+      ctx->launches += 1;
+      FTN_CUDA(cudaGetLastError());
+    }
   }
   {
     // P_X^T = Z_k R_Y (k x K) and Q_Y^T = W_k R_X (k x K)

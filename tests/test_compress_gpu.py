@@ -195,3 +195,103 @@ def test_compress_wide_bond_cluster_jacobi(F, ctx, chi):
     assert np.max(np.abs(got.data - ref.data)) <= 1e-10 * np.max(np.abs(ref.data))
     assert tuple(info.kept) == tuple(info_r["kept"])
     assert abs(info.discarded_sq - info_r["discarded_sq"]) <= 1e-10 * info.total_sq
+
+
+def _orth(g, n, k):
+    q, r = np.linalg.qr(g.standard_normal((n, k)))
+    return q * np.sign(np.diag(r))
+
+
+def _graded_with_spectrum(legs, parity, bond_first, spectra, seed):
+    """A dense graded tensor whose bond-parity sector matrices have prescribed
+    singular values.  The bond is one leg, last (bond_first False: the
+    matrix is [free | bond]) or first (True: [bond | free]), so the
+    matricisation of the compression is a plain reshape up to column signs,
+    which leave singular values unchanged.  spectra[pi] lists the singular
+    values of sector pi (as many as the smaller side allows)."""
+    g = W.rng(seed)
+    free = legs[1:] if bond_first else legs[:-1]
+    bond = legs[0] if bond_first else legs[-1]
+    fdims = [a + b for a, b, _ in free]
+    fpar = np.zeros(1, np.int64)
+    for d0, d1, _ in free:
+        fpar = (fpar[:, None] + O.index_parity(d0, d1)[None, :]).reshape(-1) & 1
+    bpar = O.index_parity(bond[0], bond[1])
+    mat = np.zeros((int(np.prod(fdims)), bond[0] + bond[1]))
+    for pi in (0, 1):
+        rows = np.nonzero(fpar == (parity ^ pi))[0]
+        cols = np.nonzero(bpar == pi)[0]
+        k = min(len(rows), len(cols))
+        s = np.asarray(spectra[pi][:k], dtype=np.float64)
+        mat[np.ix_(rows, cols)] = (_orth(g, len(rows), k) * s) @ _orth(g, len(cols), k).T
+    if bond_first:
+        data = mat.T.reshape([bond[0] + bond[1]] + fdims)
+    else:
+        data = mat.reshape(fdims + [bond[0] + bond[1]])
+    t = O.GTensor(data, legs, parity)
+    assert t.check_symmetry()
+    return t
+
+
+def _spectrum(kind, n):
+    if kind == "log12":
+        return np.logspace(0, -12, n)
+    return 0.5 ** np.arange(n)  # the stand-in gauges of the cluster workload
+
+
+@pytest.mark.parametrize("kind", ["log12", "half"])
+@pytest.mark.parametrize("chi", [10**6, 30, 9])
+@pytest.mark.parametrize("other", ["ill", "gauss", "orthonormal"])
+@pytest.mark.parametrize("px", [0, 1])
+def test_compress_ill_conditioned(F, ctx, kind, chi, other, px):
+    """X's sector blocks U diag(sigma) V^T with sigma spanning 1 ... 1e-12 (or
+    0.5^k), against Y ill-conditioned the same way, N(0, 1), or with
+    orthonormal sector blocks: chi above the rank (the exact product must
+    survive) and chi cutting inside the spectrum, against the oracle at 1e-10
+    relative.  (A Gram matrix of X carries only rounding noise in its
+    directions below ~1e-8 of the largest; a one-sided ill-conditioned bond
+    exposes that.)"""
+    lx = [(6, 6, 0), (5, 5, 1), (24, 24, 0)]
+    ly = [(24, 24, 1), (7, 7, 0), (6, 6, 1)]
+    X = _graded_with_spectrum(lx, px, False, {0: _spectrum(kind, 24), 1: 0.7 * _spectrum(kind, 24)}, 5 + px)
+    if other == "ill":
+        Y = _graded_with_spectrum(ly, 0, True, {0: 0.9 * _spectrum(kind, 24), 1: _spectrum(kind, 24)}, 7 + px)
+    elif other == "gauss":
+        Y = O.embed_blocks(ly, 0, W.random_blocks(ly, 0, 9 + px))
+    else:
+        Y = _graded_with_spectrum(ly, 0, True, {0: np.ones(24), 1: np.ones(24)}, 7 + px)
+    xr, yr, info_r = O.compress(X, Y, [2], [0], chi)
+    ref = O.contract(xr, yr, [xr.rank - 1], [0])
+    x = F.Tensor.from_blocks(ctx, lx, px, sorted(O.extract_blocks(X).items()))
+    y = F.Tensor.from_blocks(ctx, ly, 0, sorted(O.extract_blocks(Y).items()))
+    xg, yg, info = F.compress(ctx, x, y, [2], [0], chi)
+    got = O.contract(dense(xg), dense(yg), [xg.rank - 1], [0])
+    err = np.max(np.abs(got.data - ref.data)) / np.max(np.abs(ref.data))
+    assert err <= 1e-10, err
+    if chi >= 48:
+        exact = O.contract(X, Y, [2], [0])
+        assert np.max(np.abs(got.data - exact.data)) <= 1e-10 * np.max(np.abs(exact.data))
+    elif info_r["gap"] > 1e-12 * info_r["singular_values"][0]:
+        # the kept set is decided by more than rounding
+        assert tuple(info.kept) == tuple(info_r["kept"])
+        assert abs(info.discarded_sq - info_r["discarded_sq"]) <= 1e-10 * info.total_sq
+
+
+@pytest.mark.parametrize("rows_odd,k", [(260, 128), (264, 128), (268, 128), (270, 128), (256, 128), (260, 64),
+                                         (129, 128)])
+def test_compress_qr_chunk_tails(F, ctx, rows_odd, k):
+    """The Householder QR splits a tall sector into chunks of 2K rows and
+    merges their factors: last chunks of 4, 8, 12 and 14 rows (after whose
+    rank the leftover rounding noise shrinks towards underflow), one chunk,
+    three chunks, and one row more than the bond."""
+    lx = [(300, rows_odd, 0), (k, k, 1)]
+    ly = [(k, k, 0), (280, 270, 1)]
+    bx, by = W.random_blocks(lx, 0, 41), W.random_blocks(ly, 0, 42)
+    X, Y = O.embed_blocks(lx, 0, bx), O.embed_blocks(ly, 0, by)
+    xr, yr, info_r = O.compress(X, Y, [1], [0], 10**6)
+    ref = O.contract(xr, yr, [1], [0])
+    xg, yg, info = F.compress(ctx, F.Tensor.from_blocks(ctx, lx, 0, bx), F.Tensor.from_blocks(ctx, ly, 0, by), [1],
+                              [0], 10**6)
+    got = O.contract(dense(xg), dense(yg), [1], [0])
+    assert np.max(np.abs(got.data - ref.data)) <= 1e-10 * np.max(np.abs(ref.data))
+    assert tuple(info.kept) == (k, k)
