@@ -5,11 +5,16 @@
 // GPU pipeline, FP64 throughout, per bond-parity sector pi:
 //   1. sign-permute X -> X_pi = [free_X | bond] and Y -> Y_pi^T = [free_Y | bond]
 //      (the fused layouts of the tensordot, bond parity of the arrow folded in);
-//   2. R factors of X_pi and Y_pi^T by Householder QR (only R is formed):
-//      each CTA streams a chunk of rows through shared memory into its own
-//      triangular factor, and a binary tree of the same kernel merges the
-//      chunks' factors (TSQR); a side with no more rows than bond states
-//      uses the matrix itself (X_pi = I * X_pi);
+//   2. R factors with R^T R = X_pi^T X_pi (resp. Y_pi Y_pi^T): Gram matrix by
+//      the FP64 GEMM and a semi-definite Cholesky.  A Gram matrix resolves
+//      singular values only down to ~1e-8 of the largest, so a side whose
+//      Cholesky meets a pivot that is neither exactly zero nor at least 1e-6
+//      of the largest diagonal is factored again by Householder QR (only R is
+//      formed: each CTA streams a chunk of rows through shared memory into
+//      its own triangular factor, and a binary tree of the same kernel merges
+//      the chunks' factors, TSQR), which is backward stable whatever the
+//      condition; a side with no more rows than bond states uses the matrix
+//      itself (X_pi = I * X_pi);
 //   3. core M_pi = R_X R_Y^T and its SVD by one-sided (Hestenes) Jacobi;
 //   4. one host synchronisation: the singular values of both sectors are
 //      pooled and the chi largest kept;
@@ -46,6 +51,13 @@ struct QrJob {
   int tri;   // 1: src is upper triangular (row i is zero before column i)
 };
 
+struct CholJob {
+  double* G;  // n x n row-major, symmetric; replaced by R (upper, R^T R = G)
+  int n;
+  int* flag;      // bit 0: a pivot in (1e-12, 1e-6) of the largest diagonal; bit 1: a nonzero pivot dropped
+  double* trace;  // receives trace(G) = |underlying matrix|_F^2
+};
+
 struct SvdJob {
   const double* T;  // n x m row-major input, left untouched
   double* Tf;       // n x m output: the rows orthogonalised (row j = s_j u_j^T)
@@ -80,35 +92,121 @@ struct OrthJob {
   int k, n;
 };
 
-constexpr int QR_ROWS = 16;      // rows of src per pass (one per lane of warp 0 in the norm)
+__device__ __forceinline__ double block_max(double v, double* red) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int o = 16; o; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  if (warp == 0) {
+    v = lane < (int)(blockDim.x >> 5) ? red[lane] : 0.0;
+    for (int o = 16; o; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if (lane == 0) red[32] = v;
+  }
+  __syncthreads();
+  return red[32];
+}
+
+// Semi-definite Cholesky G = L L^T (right-looking); a pivot at or below
+// 1e-12 * max(diag G) marks a numerically dependent direction (a singular
+// value of the underlying matrix below 1e-6 of its largest, where a Gram
+// matrix carries only rounding noise) whose row of R is set to zero.
+// Writes R = L^T (upper triangle, zeros below).  The Gram matrix resolves a
+// direction of the underlying matrix only down to ~1e-8 of its largest
+// singular value.  The factor is therefore kept as it is when every pivot is
+// exactly zero (an empty column) or at least 1e-6 of the largest diagonal.
+// A pivot between 1e-12 and 1e-6 (bit 0 of *flag) sends the side to the
+// Householder QR; dropped pivots that are not exactly zero (bit 1) mean
+// columns dependent on the kept ones up to rounding -- or directions the Gram
+// matrix cannot see -- and are settled by the residual test of
+// dropped_residual_kernel.
+__global__ void __launch_bounds__(LA_THREADS) chol_kernel(const CholJob* jobs) {
+  __shared__ double red[33];
+  __shared__ double piv;
+  const CholJob jb = jobs[blockIdx.x];
+  double* G = jb.G;
+  const int n = jb.n;
+  double dmax = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) dmax = fmax(dmax, G[(int64_t)i * n + i]);
+  dmax = block_max(dmax, red);
+  const double tol = 1e-12 * dmax;
+  if (threadIdx.x == 0 && jb.trace) {
+    double tr = 0.0;
+    for (int i = 0; i < n; ++i) tr += G[(int64_t)i * n + i];
+    *jb.trace = tr;
+  }
+  int fl = 0;
+  for (int j = 0; j < n; ++j) {
+    if (threadIdx.x == 0) {
+      const double d = G[(int64_t)j * n + j];
+      piv = d > tol ? sqrt(d) : 0.0;
+      G[(int64_t)j * n + j] = piv;
+      if (d > tol && d < 1e-6 * dmax) fl |= 1;
+      if (!(d > tol) && d != 0.0) fl |= 2;
+    }
+    __syncthreads();
+    const double p = piv;
+    for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x)
+      G[(int64_t)i * n + j] = p > 0.0 ? G[(int64_t)i * n + j] / p : 0.0;
+    __syncthreads();
+    const int rest = n - j - 1;
+    const int64_t cnt = (int64_t)rest * rest;
+    for (int64_t e = threadIdx.x; e < cnt; e += blockDim.x) {
+      const int i = j + 1 + (int)(e / rest), k = j + 1 + (int)(e % rest);
+      if (k <= i) G[(int64_t)i * n + k] -= G[(int64_t)i * n + j] * G[(int64_t)k * n + j];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0 && fl && jb.flag) *jb.flag = fl;
+  // R = L^T in place
+  const int64_t tot = (int64_t)n * n;
+  for (int64_t e = threadIdx.x; e < tot; e += blockDim.x) {
+    const int i = (int)(e / n), k = (int)(e % n);
+    if (i < k) {
+      G[(int64_t)i * n + k] = G[(int64_t)k * n + i];
+      G[(int64_t)k * n + i] = 0.0;
+    }
+  }
+}
+
+constexpr int QR_ROWS = 16;      // rows of src per pass when K > QR_WIDE_K
+constexpr int QR_ROWS_WIDE = 32; // rows per pass otherwise (one per lane of warp 0 in the norm)
+constexpr int QR_WIDE_K = 512;   // largest K streamed 32 rows at a time (32 x 512 doubles = 128 KB)
+constexpr int QR_RSMEM_K = 128;  // largest K whose factor stays in shared memory (128 KB)
 constexpr int QR_THREADS = 128;
 
 // Householder QR, R factor only (Sec. II.A: the QR of each symmetry block).
-// Rows arrive in blocks of QR_ROWS held in shared memory.  For column j with
+// Rows arrive in blocks of ROWS held in shared memory.  For column j with
 // x = [a; b] = [R_jj; B(:, j)] the reflector H = I - tau v v^T, v = [1; b / (a
 // - beta)], beta = -sign(a) |x|, tau = (beta - a) / beta in [1, 2], maps x to
 // [beta; 0] and is applied to the trailing columns of R row j and of the
-// block (the form of LAPACK's dlarfg: |x| is taken after scaling by max|x|,
-// and no intermediate can overflow, however small b has become).  Row j of R
-// is read and written only at step j, so R stays in global memory (it is
-// L2-resident and each access is one coalesced row).  A column whose block
-// part is zero, or below 2^-960 in magnitude, needs no reflector (this also
-// skips the zero prefix of triangular sources).  Once a short block's rank
-// is absorbed its rows hold only rounding noise, which every further group
-// of reflectors shrinks by ~2^-52: that is where such tiny columns arise.
+// block (the form of LAPACK's dlarfg; |x| is taken after scaling by max|x|
+// whenever a square or product could leave the normal range, so no
+// intermediate overflows or underflows, however small b has become).  Row j of R is read
+// and written only at step j: R stays in shared memory when RSMEM (K <=
+// QR_RSMEM_K), else in global memory (L2-resident; each access is one
+// coalesced row).  A column whose block part is zero, or below 2^-960 in
+// magnitude, needs no reflector (this also skips the zero prefix of
+// triangular sources).  Once a short block's rank is absorbed its rows hold
+// only rounding noise, which every further group of reflectors shrinks by
+// ~2^-52: that is where such tiny columns arise.
+template <int ROWS, bool RSMEM>
 __global__ void __launch_bounds__(QR_THREADS) qr_stream_kernel(const QrJob* jobs) {
-  extern __shared__ double qb[];  // QR_ROWS x K, row-major
-  __shared__ double refl[2];      // tau, 1 / (a - beta)
+  extern __shared__ double qsm[];  // [R (K x K) when RSMEM] then the block (ROWS x K, row-major)
+  __shared__ double refl[2];       // tau, 1 / (a - beta)
   __shared__ int skip;
   const QrJob J = jobs[blockIdx.x];
   const int K = J.K, t = threadIdx.x, lane = t & 31, warp = t >> 5;
-  double* R = J.R;
+  double* R = RSMEM ? qsm : J.R;
+  double* qb = RSMEM ? qsm + (size_t)K * K : qsm;
+  const int64_t kk = (int64_t)K * K;
   if (!J.init)
-    for (int64_t e = t; e < (int64_t)K * K; e += blockDim.x) R[e] = 0.0;
-  for (int64_t r0 = 0; r0 < J.rows; r0 += QR_ROWS) {
-    const int nb = (int)(J.rows - r0 < QR_ROWS ? J.rows - r0 : QR_ROWS);
-    __syncthreads();  // the previous block's last column is done (and R is zeroed)
-    for (int e = t; e < QR_ROWS * K; e += blockDim.x) {
+    for (int64_t e = t; e < kk; e += blockDim.x) R[e] = 0.0;
+  else if (RSMEM)
+    for (int64_t e = t; e < kk; e += blockDim.x) R[e] = J.R[e];
+  for (int64_t r0 = 0; r0 < J.rows; r0 += ROWS) {
+    const int nb = (int)(J.rows - r0 < ROWS ? J.rows - r0 : ROWS);
+    __syncthreads();  // the previous block's last column is done (and R is set up)
+    for (int e = t; e < ROWS * K; e += blockDim.x) {
       const int i = e / K, c = e - i * K;
       qb[e] = i < nb ? J.src[(r0 + i) * J.ld + c] : 0.0;
     }
@@ -116,27 +214,44 @@ __global__ void __launch_bounds__(QR_THREADS) qr_stream_kernel(const QrJob* jobs
     const int j0 = J.tri ? (int)(r0 < K ? r0 : K) : 0;
     for (int j = j0; j < K; ++j) {
       if (warp == 0) {
-        const double bj = lane < QR_ROWS ? qb[lane * K + j] : 0.0;
-        double mx = fabs(bj);
-        for (int o = 16; o; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-        int sk = 1;
-        if (mx > 0x1p-960) {
+        const double bj = lane < ROWS ? qb[lane * K + j] : 0.0;
+        double ss = bj * bj;
+        for (int o = 16; o; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+        if (lane == 0) {
           const double a = R[(int64_t)j * K + j];
-          const double sc = fmax(mx, fabs(a));
-          const double u = bj / sc;
-          double ss = u * u;
-          for (int o = 16; o; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
-          if (lane == 0) {
-            const double as = a / sc;
-            const double nrm = sc * sqrt(fma(as, as, ss));
+          int sk = 0;
+          if (ss >= 0x1p-900 && ss <= 0x1p900 && fabs(a) <= 0x1p450) {
+            // every square and product below stays in the normal range
+            const double nrm = sqrt(fma(a, a, ss));
             const double beta = a > 0.0 ? -nrm : nrm;
-            refl[0] = (beta - a) / beta;
-            refl[1] = 1.0 / (a - beta);
+            const double d = a - beta;  // |d| >= nrm, no cancellation
+            const double r = 1.0 / (beta * d);
+            refl[0] = -(d * d) * r;  // (beta - a) / beta
+            refl[1] = beta * r;      // 1 / (a - beta)
             R[(int64_t)j * K + j] = beta;
+          } else {
+            // rescaled by the largest magnitude of the column
+            double mx = 0.0;
+            for (int i = 0; i < ROWS; ++i) mx = fmax(mx, fabs(qb[i * K + j]));
+            if (mx > 0x1p-960) {
+              const double sc = fmax(mx, fabs(a)), rs = 1.0 / sc, as = a * rs;
+              double s2 = 0.0;
+              for (int i = 0; i < ROWS; ++i) {
+                const double u = qb[i * K + j] * rs;
+                s2 = fma(u, u, s2);
+              }
+              const double nrm = sc * sqrt(fma(as, as, s2));
+              const double beta = a > 0.0 ? -nrm : nrm;
+              const double d = a - beta;
+              refl[0] = -d / beta;
+              refl[1] = 1.0 / d;
+              R[(int64_t)j * K + j] = beta;
+            } else {
+              sk = 1;
+            }
           }
-          sk = 0;
+          skip = sk;
         }
-        if (lane == 0) skip = sk;
       }
       __syncthreads();
       if (!skip) {
@@ -144,18 +259,25 @@ __global__ void __launch_bounds__(QR_THREADS) qr_stream_kernel(const QrJob* jobs
         for (int c = j + 1 + t; c < K; c += blockDim.x) {
           double* rp = R + (int64_t)j * K + c;
           const double rjc = *rp;
-          double w = 0.0;
+          double w0 = 0.0, w1 = 0.0;
 #pragma unroll
-          for (int i = 0; i < QR_ROWS; ++i) w = fma(qb[i * K + j], qb[i * K + c], w);
-          w = tau * fma(w, id, rjc);
+          for (int i = 0; i < ROWS; i += 2) {
+            w0 = fma(qb[i * K + j], qb[i * K + c], w0);
+            w1 = fma(qb[(i + 1) * K + j], qb[(i + 1) * K + c], w1);
+          }
+          const double w = tau * fma(w0 + w1, id, rjc);
           *rp = rjc - w;
           const double wv = w * id;
 #pragma unroll
-          for (int i = 0; i < QR_ROWS; ++i) qb[i * K + c] = fma(-wv, qb[i * K + j], qb[i * K + c]);
+          for (int i = 0; i < ROWS; ++i) qb[i * K + c] = fma(-wv, qb[i * K + j], qb[i * K + c]);
         }
       }
       __syncthreads();
     }
+  }
+  if (RSMEM) {
+    __syncthreads();
+    for (int64_t e = t; e < kk; e += blockDim.x) J.R[e] = R[e];
   }
 }
 
@@ -500,6 +622,107 @@ __global__ void __launch_bounds__(SVDC_WARPS * 32) svd_rows_cluster_kernel(const
   cluster_sync_all();  // no CTA leaves while a peer may still read its flags
 }
 
+// Residual test of a Gram factor with dropped pivots.  With S the kept
+// pivots (R_jj > 0) and D the dropped ones, column d of T (K x K, row-major)
+// is e_d - Z R[S, d] for d in D, where Z holds R_SS^{-1} on the rows S, and 0
+// for d in S; then E = A T has the columns A_D - A_S R_SS^{-1} R_SD: what is
+// left of each dropped column after removing its part in the span of the kept
+// ones (R_SS^{-1} R_SD are the coefficients the Cholesky found for it).  E is
+// formed from A by a GEMM, so |E| is accurate to rounding of A itself (the
+// Gram matrix could only tell it down to ~1e-8 |A|).  Each warp takes a
+// column; lanes hold the right-hand side and the back substitution runs over
+// the kept indices below d.
+struct ResidTJob {
+  const double* R;  // K x K upper-triangular factor, zero rows for dropped pivots
+  double* T;
+  int K;
+  int c0;  // first column of this job's 32
+};
+
+constexpr int RESID_SMEM_K = 128;  // largest K staged in shared memory (R^T: 128 KB)
+
+template <bool SM>
+__global__ void __launch_bounds__(128) dropped_residual_kernel(const ResidTJob* jobs) {
+  extern __shared__ double rsm[];  // SM: R^T (K x K), 1 / R_ss (K), then one right-hand side (K) per warp
+  const ResidTJob J = jobs[blockIdx.x];
+  const int K = J.K, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  double* Rt = rsm;
+  double* inv = rsm + (SM ? (size_t)K * K : 0);
+  double* bw = inv + (SM ? K : 0) + (size_t)warp * K;
+  if (SM) {
+    for (int64_t e = threadIdx.x; e < (int64_t)K * K; e += blockDim.x) {
+      const int i = (int)(e / K), c = (int)(e - (int64_t)i * K);
+      Rt[(int64_t)c * K + i] = J.R[e];
+    }
+    for (int i = threadIdx.x; i < K; i += blockDim.x) {
+      const double r = J.R[(int64_t)i * K + i];
+      inv[i] = r != 0.0 ? 1.0 / r : 0.0;
+    }
+    __syncthreads();
+  }
+  // R[i, s] and the solve's right-hand side, from shared memory or from the
+  // output column itself
+  auto Ris = [&](int i, int sc) { return SM ? Rt[(int64_t)sc * K + i] : J.R[(int64_t)i * K + sc]; };
+  for (int d = J.c0 + warp; d < J.c0 + 32 && d < K; d += 4) {
+    double* Tc = J.T + d;  // column d, stride K
+    if (J.R[(int64_t)d * K + d] != 0.0) {
+      for (int i = lane; i < K; i += 32) Tc[(int64_t)i * K] = 0.0;
+      continue;
+    }
+    double* b = SM ? bw : nullptr;
+    // b = R[0..d-1, d]; x_s = (b_s - sum_{s < s' < d} R[s, s'] x_s') / R_ss over kept s; T[s, d] = -x_s
+    for (int i = lane; i < K; i += 32) {
+      const double v = i < d ? Ris(i, d) : 0.0;
+      if (SM) b[i] = v;
+      else Tc[(int64_t)i * K] = v;
+    }
+    __syncwarp();
+    for (int sc = d - 1; sc >= 0; --sc) {
+      const double rss = SM ? 1.0 : J.R[(int64_t)sc * K + sc];
+      const double bs = SM ? b[sc] : Tc[(int64_t)sc * K];
+      const double xs = SM ? bs * inv[sc] : (rss != 0.0 ? bs / rss : 0.0);
+      __syncwarp();
+      if (SM) {
+        if (lane == 0) b[sc] = -xs;
+        if (xs != 0.0)
+          for (int i = lane; i < sc; i += 32) b[i] = fma(-Ris(i, sc), xs, b[i]);
+      } else {
+        if (lane == 0) Tc[(int64_t)sc * K] = -xs;
+        if (xs != 0.0)
+          for (int i = lane; i < sc; i += 32) Tc[(int64_t)i * K] -= Ris(i, sc) * xs;
+      }
+      __syncwarp();
+    }
+    if (SM)
+      for (int i = lane; i < K; i += 32) Tc[(int64_t)i * K] = i == d ? 1.0 : (i < d ? b[i] : 0.0);
+    else if (lane == 0)
+      Tc[(int64_t)d * K] = 1.0;
+    __syncwarp();
+  }
+}
+
+// Sum of squares of each job's n elements (one CTA per job, fixed order).
+struct SumSqJob {
+  const double* x;
+  int64_t n;
+  double* out;
+};
+
+__global__ void __launch_bounds__(256) sumsq_kernel(const SumSqJob* jobs) {
+  __shared__ double red[8];
+  const SumSqJob J = jobs[blockIdx.x];
+  double q = 0.0;
+  for (int64_t e = threadIdx.x; e < J.n; e += blockDim.x) q = fma(J.x[e], J.x[e], q);
+  for (int o = 16; o; o >>= 1) q += __shfl_xor_sync(0xffffffffu, q, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = q;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < 8; ++w) t += red[w];
+    *J.out = t;
+  }
+}
+
 struct CompactJob {
   const double* src;  // rows x cols, leading dimension ld
   double* dst;        // the nonzero rows, packed (leading dimension cols)
@@ -605,6 +828,28 @@ __global__ void __launch_bounds__(256) orth_rows_kernel(const OrthJob* jobs) {
 
 // ---------------------------------------------------------------------------------
 namespace {
+
+// Opt the Householder QR and residual-test kernels into their shared-memory
+// sizes (once per process).
+ftn_status setup_qr_kernels() {
+  static std::once_flag once;
+  static cudaError_t err = cudaSuccess;
+  std::call_once(once, [] {
+    const int big = (QR_RSMEM_K * QR_RSMEM_K + QR_ROWS_WIDE * QR_RSMEM_K) * 8;
+    err = cudaFuncSetAttribute(qr_stream_kernel<QR_ROWS_WIDE, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+    if (err == cudaSuccess)
+      err = cudaFuncSetAttribute(qr_stream_kernel<QR_ROWS_WIDE, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 QR_ROWS_WIDE * QR_WIDE_K * 8);
+    if (err == cudaSuccess)
+      err = cudaFuncSetAttribute(qr_stream_kernel<QR_ROWS, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 QR_ROWS * LA_MAX_DIM * 8);
+    if (err == cudaSuccess)
+      err = cudaFuncSetAttribute(dropped_residual_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (RESID_SMEM_K * RESID_SMEM_K + 5 * RESID_SMEM_K) * 8);
+  });
+  if (err != cudaSuccess) return cuda_error(err, "cudaFuncSetAttribute (Householder QR)");
+  return FTN_OK;
+}
 
 template <typename T>
 ftn_status put_table(ftn_ctx ctx, const std::vector<T>& v, void** d) {
@@ -725,14 +970,18 @@ struct CJob {
   int64_t ws_n = 0, ws_off = 0;
   double* ws = nullptr;
   int64_t o_xf = 0, o_yf = 0;
-  int64_t o_gx[2], o_gy[2], o_m[2], o_tf[2], o_wk[2], o_zk[2], o_px[2], o_qy[2], o_ms3[2], o_rxc[2], o_ryc[2],
-      o_sc[2];
+  int64_t o_px_part[2], o_py_part[2], o_gx[2], o_gy[2], o_m[2], o_tf[2], o_wk[2], o_zk[2], o_px[2], o_qy[2],
+      o_ms3[2], o_rxc[2], o_ryc[2], o_sc[2];
   int64_t s_off[2];  // singular values + sweep count in the batch's shared buffer
-  // Householder TSQR of the tall sides: chunks of qr_lx / qr_ly rows, one
-  // K x K factor slot per chunk at o_gx / o_gy (slot 0 holds the result)
-  int64_t qr_lx[2], qr_ly[2];
+  // Householder TSQR of the tall sides whose Gram factor is not kept:
+  // chunks of qr_lx / qr_ly rows, one K x K factor slot per chunk at o_hx /
+  // o_hy (slot 0 holds the result)
+  int64_t o_hx[2], o_hy[2], qr_lx[2], qr_ly[2];
+  // residual test of a Gram factor with dropped pivots: T (K x K) per tall
+  // side at o_tx / o_ty; E = A T (rows x K) reuses the Householder slots
+  int64_t o_tx[2], o_ty[2];
   int qr_px[2], qr_py[2];
-  int rx[2], ry[2], ldx[2], ldy[2], nrot[2], mlen[2];
+  int sp_x[2], sp_y[2], rx[2], ry[2], ldx[2], ldy[2], nrot[2], mlen[2];
   int64_t rx_off[2], ry_off[2];
   bool tall_x[2], tall_y[2], trans[2];
   struct Cand {
@@ -774,20 +1023,42 @@ ftn_status cj_prepare(ftn_ctx ctx, CJob& J) {
     J.tall_y[pi] = Cc > K;
     J.rx[pi] = (int)std::min(R, K);
     J.ry[pi] = (int)std::min(Cc, K);
-    // chunks of at least 2K rows (the merge tree then adds at most ~1/6 of
-    // the leaves' work), at most 256 per side
+    J.o_gx[pi] = off;
+    off += J.tall_x[pi] ? al(K * K) : 0;
+    J.o_gy[pi] = off;
+    off += J.tall_y[pi] ? al(K * K) : 0;
+    // split-K over the long (row) dimension of the Gram products
+    auto split_for = [&](int64_t rows) {
+      const int64_t tiles = ((K + 63) / 64) * ((K + 63) / 64);
+      int64_t s = std::max<int64_t>(1, (2 * (int64_t)ctx->num_sms + tiles - 1) / tiles);
+      s = std::min<int64_t>(s, std::max<int64_t>(1, rows / 512));
+      return (int)std::min<int64_t>(s, 64);
+    };
+    J.sp_x[pi] = J.tall_x[pi] ? split_for(R) : 1;
+    J.sp_y[pi] = J.tall_y[pi] ? split_for(Cc) : 1;
+    J.o_px_part[pi] = off;
+    off += J.sp_x[pi] > 1 ? al((int64_t)J.sp_x[pi] * K * K) : 0;
+    J.o_py_part[pi] = off;
+    off += J.sp_y[pi] > 1 ? al((int64_t)J.sp_y[pi] * K * K) : 0;
+    // Householder chunks: at least K rows (a leaf costs about as much as
+    // two merges; the merge tree adds at most ~1/3 of the leaves' work), at
+    // most 256 per side, a multiple of the 32-row pass
     auto chunk_rows = [&](int64_t rows) {
-      int64_t L = std::max<int64_t>({2 * K, (rows + 255) / 256, (int64_t)QR_ROWS});
-      return (L + QR_ROWS - 1) / QR_ROWS * QR_ROWS;
+      int64_t L = std::max<int64_t>({K, (rows + 255) / 256, (int64_t)QR_ROWS_WIDE});
+      return (L + QR_ROWS_WIDE - 1) / QR_ROWS_WIDE * QR_ROWS_WIDE;
     };
     J.qr_lx[pi] = J.tall_x[pi] ? chunk_rows(R) : 0;
     J.qr_px[pi] = J.tall_x[pi] ? (int)((R + J.qr_lx[pi] - 1) / J.qr_lx[pi]) : 0;
     J.qr_ly[pi] = J.tall_y[pi] ? chunk_rows(Cc) : 0;
     J.qr_py[pi] = J.tall_y[pi] ? (int)((Cc + J.qr_ly[pi] - 1) / J.qr_ly[pi]) : 0;
-    J.o_gx[pi] = off;
-    off += al((int64_t)J.qr_px[pi] * K * K);
-    J.o_gy[pi] = off;
-    off += al((int64_t)J.qr_py[pi] * K * K);
+    J.o_hx[pi] = off;
+    off += J.tall_x[pi] ? al(std::max<int64_t>((int64_t)J.qr_px[pi] * K * K, R * K)) : 0;
+    J.o_hy[pi] = off;
+    off += J.tall_y[pi] ? al(std::max<int64_t>((int64_t)J.qr_py[pi] * K * K, Cc * K)) : 0;
+    J.o_tx[pi] = off;
+    off += J.tall_x[pi] ? al(K * K) : 0;
+    J.o_ty[pi] = off;
+    off += J.tall_y[pi] ? al(K * K) : 0;
     J.o_rxc[pi] = off;
     off += al((int64_t)J.rx[pi] * K);
     J.o_ryc[pi] = off;
@@ -821,11 +1092,56 @@ ftn_status cj_prepare(ftn_ctx ctx, CJob& J) {
   return FTN_OK;
 }
 
-// Householder TSQR jobs of the tall sides, by tree level: level 0 factors
+// Gram products of the tall sides (split over rows where that gives more
+// tiles; the slabs are added by the ordered reduction) and their Cholesky jobs.
+ftn_status cj_gram(CJob& J, GemmF64Batch& gb, std::vector<CholJob>& chol, int* flags, double* traces) {
+  const TdPlan* P = J.P.get();
+  double* ws = J.ws;
+  std::vector<GemmProb> gram, reds;
+  auto add_gram = [&](int K, int rows, int64_t src, int64_t ld, int64_t dst, int64_t part, int nsplit, int* flag,
+                      double* trace) {
+    GemmProb g = make_prob(K, K, rows, src, 1, ld, src, 1, ld);
+    if (nsplit > 1) {
+      g.nsplit = nsplit;
+      g.kchunk = (rows + nsplit - 1) / nsplit;
+      g.kchunk = (g.kchunk + 15) / 16 * 16;
+      g.nsplit = (rows + g.kchunk - 1) / g.kchunk;
+      gemm_plain_output(g, part, K);
+      g.c_slab = (int64_t)K * K;
+      // the slabs at `part`, added in split order into the plain K x K result at dst
+      GemmProb r = make_prob(K, K, 0, part, 0, 0, 0, 0, 0);
+      gemm_plain_output(r, dst, K);
+      r.nsplit = g.nsplit;
+      r.c_slab = (int64_t)K * K;
+      reds.push_back(r);
+    } else {
+      gemm_plain_output(g, dst, K);
+    }
+    gram.push_back(g);
+    chol.push_back({ws + dst, K, flag, trace});
+  };
+  for (int pi = 0; pi < 2; ++pi) {
+    const int K = (int)P->K[pi];
+    if (K == 0) continue;
+    if (J.tall_x[pi] && P->M[pi] > 0)
+      add_gram(K, (int)P->M[pi], J.o_xf + P->afoff[pi], P->ldk[pi], J.o_gx[pi], J.o_px_part[pi], J.sp_x[pi],
+               flags + 2 * pi, traces + 2 * pi);
+    if (J.tall_y[pi] && P->N[pi] > 0)
+      add_gram(K, (int)P->N[pi], J.o_yf + P->bfoff[pi], P->ldk[pi], J.o_gy[pi], J.o_py_part[pi], J.sp_y[pi],
+               flags + 2 * pi + 1, traces + 2 * pi + 1);
+  }
+  FTN_TRY(add_gemm_set(gb, gram, ws, ws, ws, J.ws_n, J.ws_n, J.ws_n));
+  if (!red_in_bounds(reds, J.ws_n, J.ws_n)) return set_error(FTN_EINVAL, "internal error: Gram reduction out of bounds");
+  add_reductions(gb, reds, ws, ws);
+  return FTN_OK;
+}
+
+// Householder TSQR jobs of the tall sides whose flag (index 2 * pi + side,
+// side 0 = X, 1 = Y) has bit 0 set, by tree level: level 0 factors
 // every chunk into its own slot; level l >= 1 merges slot c + 2^(l-1) into
 // slot c for every c that is a multiple of 2^l (the merged factor is upper
 // triangular, its zero prefix skipped).  levels[l] receives the jobs.
-void cj_qr(CJob& J, std::vector<std::vector<QrJob>>& levels) {
+void cj_qr(CJob& J, std::vector<std::vector<QrJob>>& levels, const int* flags) {
   const TdPlan* P = J.P.get();
   auto side = [&](int K, int64_t rows, int64_t src, int64_t ld, int64_t slots, int64_t L, int nchunk) {
     if (nchunk == 0) return;
@@ -846,10 +1162,10 @@ void cj_qr(CJob& J, std::vector<std::vector<QrJob>>& levels) {
   for (int pi = 0; pi < 2; ++pi) {
     const int K = (int)P->K[pi];
     if (K == 0) continue;
-    if (J.tall_x[pi] && P->M[pi] > 0)
-      side(K, P->M[pi], J.o_xf + P->afoff[pi], P->ldk[pi], J.o_gx[pi], J.qr_lx[pi], J.qr_px[pi]);
-    if (J.tall_y[pi] && P->N[pi] > 0)
-      side(K, P->N[pi], J.o_yf + P->bfoff[pi], P->ldk[pi], J.o_gy[pi], J.qr_ly[pi], J.qr_py[pi]);
+    if (J.tall_x[pi] && P->M[pi] > 0 && (flags[2 * pi] & 1))
+      side(K, P->M[pi], J.o_xf + P->afoff[pi], P->ldk[pi], J.o_hx[pi], J.qr_lx[pi], J.qr_px[pi]);
+    if (J.tall_y[pi] && P->N[pi] > 0 && (flags[2 * pi + 1] & 1))
+      side(K, P->N[pi], J.o_yf + P->bfoff[pi], P->ldk[pi], J.o_hy[pi], J.qr_ly[pi], J.qr_py[pi]);
   }
 }
 
@@ -944,19 +1260,22 @@ ftn_status compress_batch(ftn_ctx ctx, std::vector<CompressItem>& items) {
     jobs[i].ws_off = total;
     total += jobs[i].ws_n;
   }
-  // shared small buffers after the jobs' workspaces: [row counts: 4 ints per job | singular values]
+  // shared small buffers after the jobs' workspaces: [row counts and
+  // Cholesky flags: 8 ints per job | singular values]
   int64_t s_total = 0;
   for (CJob& J : jobs)
     for (int pi = 0; pi < 2; ++pi) {
       J.s_off[pi] = s_total;
       s_total += J.nrot[pi] + 1;  // values, then the sweep count
     }
-  const int64_t cnt_words = ((int64_t)jobs.size() * 4 * (int64_t)sizeof(int) + 7) / 8;
-  double* ws = (double*)workspace(ctx, (size_t)(total + cnt_words + s_total + 32) * 8);
+  const int64_t cnt_words = ((int64_t)jobs.size() * 8 * (int64_t)sizeof(int) + 7) / 8;
+  const int64_t chk_words = (int64_t)jobs.size() * 8;  // per job: |A|_F^2 of the 4 sides, then |E|_F^2
+  double* ws = (double*)workspace(ctx, (size_t)(total + cnt_words + chk_words + s_total + 32) * 8);
   if (!ws) return set_error(FTN_ENOMEM, "workspace allocation failed");
   for (CJob& J : jobs) J.ws = ws + J.ws_off;
   int* cnt = (int*)(ws + total);
-  double* sbuf = ws + total + cnt_words;
+  double* chk = ws + total + cnt_words;
+  double* sbuf = ws + total + cnt_words + chk_words;
 
   // ---- 1. fused matrices ----
   {
@@ -968,51 +1287,153 @@ ftn_status compress_batch(ftn_ctx ctx, std::vector<CompressItem>& items) {
     }
     FTN_TRY(flush_perm(ctx, pb, FTN_F64, PERM_SAME, 0));
   }
-  // ---- 2. R factors by Householder TSQR (one launch per tree level) ----
+  // ---- 2. R factors: Gram matrices and semi-definite Cholesky (flags unresolved sides) ----
+  // per job: cnt[8q + 2 pi + side] = nonzero rows of the factor, cnt[8q + 4 + 2 pi + side] = flag
+  FTN_CUDA(cudaMemsetAsync(cnt, 0, jobs.size() * 8 * sizeof(int), ctx->stream));
   {
-    std::vector<std::vector<QrJob>> levels;
-    for (CJob& J : jobs) cj_qr(J, levels);
-    int kmax = 0;
-    for (auto& lv : levels)
-      for (const QrJob& q : lv) kmax = std::max(kmax, q.K);
-    const size_t smem = (size_t)QR_ROWS * kmax * sizeof(double);
-    if (smem > 48 * 1024) FTN_CUDA(cudaFuncSetAttribute(qr_stream_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                        (int)(QR_ROWS * LA_MAX_DIM * sizeof(double))));
-    for (auto& lv : levels) {
-      if (lv.empty()) continue;
-      DevBuf t_qr(ctx);
-      FTN_TRY(put_table(ctx, lv, &t_qr.p));
-      const int rec = prof_begin(ctx, "householder_qr", 0, 0);
-      qr_stream_kernel<<<(unsigned)lv.size(), QR_THREADS, smem, ctx->stream>>>((const QrJob*)t_qr.p);
+    GemmF64Batch gb(ctx);
+    std::vector<CholJob> chol;
+    for (size_t q = 0; q < jobs.size(); ++q) FTN_TRY(cj_gram(jobs[q], gb, chol, cnt + 8 * q + 4, chk + 8 * q));
+    FTN_TRY(flush_gemm_f64(gb));
+    if (!chol.empty()) {
+      DevBuf t_chol(ctx);
+      FTN_TRY(put_table(ctx, chol, &t_chol.p));
+      const int rec = prof_begin(ctx, "cholesky", 0, 0);
+      chol_kernel<<<(unsigned)chol.size(), LA_THREADS, 0, ctx->stream>>>((const CholJob*)t_chol.p);
       ctx->launches += 1;
       FTN_CUDA(cudaGetLastError());
       prof_end(ctx, rec);
     }
   }
-  // ---- 2b. nonzero rows of the R factors (one synchronisation for the counts) ----
+  // ---- 2b. nonzero rows of the R factors (one synchronisation for the counts
+  //      and flags); flagged sides factored again by Householder TSQR, one
+  //      launch per tree level, and compacted again (a second synchronisation) ----
   {
-    std::vector<CompactJob> cj;
-    for (size_t q = 0; q < jobs.size(); ++q) {
-      CJob& J = jobs[q];
-      for (int pi = 0; pi < 2; ++pi) {
-        const int K = (int)J.P->K[pi];
-        if (K == 0 || J.rx[pi] == 0 || J.ry[pi] == 0) continue;
-        cj.push_back({J.ws + J.rx_off[pi], J.ws + J.o_rxc[pi], cnt + 4 * q + 2 * pi, J.rx[pi], K, J.ldx[pi]});
-        cj.push_back({J.ws + J.ry_off[pi], J.ws + J.o_ryc[pi], cnt + 4 * q + 2 * pi + 1, J.ry[pi], K, J.ldy[pi]});
+    std::vector<int> hc(8 * jobs.size(), 0);
+    auto compact = [&](bool flagged_only) -> ftn_status {
+      std::vector<CompactJob> cj;
+      for (size_t q = 0; q < jobs.size(); ++q) {
+        CJob& J = jobs[q];
+        for (int pi = 0; pi < 2; ++pi) {
+          const int K = (int)J.P->K[pi];
+          if (K == 0 || J.rx[pi] == 0 || J.ry[pi] == 0) continue;
+          if (!flagged_only || (hc[8 * q + 4 + 2 * pi] & 1))
+            cj.push_back({J.ws + J.rx_off[pi], J.ws + J.o_rxc[pi], cnt + 8 * q + 2 * pi, J.rx[pi], K, J.ldx[pi]});
+          if (!flagged_only || (hc[8 * q + 4 + 2 * pi + 1] & 1))
+            cj.push_back({J.ws + J.ry_off[pi], J.ws + J.o_ryc[pi], cnt + 8 * q + 2 * pi + 1, J.ry[pi], K, J.ldy[pi]});
+        }
       }
-    }
-    std::vector<int> hc(4 * jobs.size(), 0);
-    if (!cj.empty()) {
-      DevBuf t_cj(ctx);
-      FTN_TRY(put_table(ctx, cj, &t_cj.p));
-      FTN_CUDA(cudaMemsetAsync(cnt, 0, hc.size() * sizeof(int), ctx->stream));
-      compact_rows_kernel<<<(unsigned)cj.size(), 256, 0, ctx->stream>>>((const CompactJob*)t_cj.p);
-      ctx->launches += 1;
-      FTN_CUDA(cudaGetLastError());
+      if (!cj.empty()) {
+        DevBuf t_cj(ctx);
+        FTN_TRY(put_table(ctx, cj, &t_cj.p));
+        compact_rows_kernel<<<(unsigned)cj.size(), 256, 0, ctx->stream>>>((const CompactJob*)t_cj.p);
+        ctx->launches += 1;
+        FTN_CUDA(cudaGetLastError());
+      }
       FTN_CUDA(cudaMemcpyAsync(hc.data(), cnt, hc.size() * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
       FTN_CUDA(cudaStreamSynchronize(ctx->stream));
+      return FTN_OK;
+    };
+    FTN_TRY(compact(false));
+    // ---- residual test of the factors with dropped pivots (one more synchronisation) ----
+    {
+      std::vector<ResidTJob> rt[2];  // by variant: R^T in shared memory, in global memory
+      std::vector<SumSqJob> sq;
+      GemmF64Batch gb(ctx);
+      int kmax_sm = 0;
+      for (size_t q = 0; q < jobs.size(); ++q) {
+        CJob& J = jobs[q];
+        std::vector<GemmProb> eg;
+        for (int pi = 0; pi < 2; ++pi)
+          for (int side = 0; side < 2; ++side) {
+            const int f = hc[8 * q + 4 + 2 * pi + side];
+            if (f != 2) continue;  // only dropped pivots, none in the unresolved band
+            const int K = (int)J.P->K[pi];
+            const int64_t rows = side ? J.P->N[pi] : J.P->M[pi];
+            const int64_t src = side ? J.o_yf + J.P->bfoff[pi] : J.o_xf + J.P->afoff[pi];
+            const int64_t rf = side ? J.o_gy[pi] : J.o_gx[pi], tf = side ? J.o_ty[pi] : J.o_tx[pi];
+            const int64_t ef = side ? J.o_hy[pi] : J.o_hx[pi];
+            const int v = K <= RESID_SMEM_K ? 0 : 1;
+            if (!v) kmax_sm = std::max(kmax_sm, K);
+            for (int c0 = 0; c0 < K; c0 += 32) rt[v].push_back({J.ws + rf, J.ws + tf, K, c0});
+            GemmProb g = make_prob((int)rows, K, K, src, J.P->ldk[pi], 1, tf, 1, K);
+            gemm_plain_output(g, ef, K);
+            eg.push_back(g);
+            sq.push_back({J.ws + ef, rows * K, chk + 8 * q + 4 + 2 * pi + side});
+          }
+        if (!eg.empty()) FTN_TRY(add_gemm_set(gb, eg, J.ws, J.ws, J.ws, J.ws_n, J.ws_n, J.ws_n));
+      }
+      if (!sq.empty()) {
+        FTN_TRY(setup_qr_kernels());
+        for (int v = 0; v < 2; ++v) {
+          if (rt[v].empty()) continue;
+          DevBuf t_rt(ctx);
+          FTN_TRY(put_table(ctx, rt[v], &t_rt.p));
+          if (v == 0)
+            dropped_residual_kernel<true><<<(unsigned)rt[0].size(), 128,
+                                            ((size_t)kmax_sm * kmax_sm + 5 * (size_t)kmax_sm) * 8, ctx->stream>>>(
+                (const ResidTJob*)t_rt.p);
+          else
+            dropped_residual_kernel<false><<<(unsigned)rt[1].size(), 128, 0, ctx->stream>>>((const ResidTJob*)t_rt.p);
+          ctx->launches += 1;
+          FTN_CUDA(cudaGetLastError());
+        }
+        FTN_TRY(flush_gemm_f64(gb));
+        DevBuf t_sq(ctx);
+        FTN_TRY(put_table(ctx, sq, &t_sq.p));
+        sumsq_kernel<<<(unsigned)sq.size(), 256, 0, ctx->stream>>>((const SumSqJob*)t_sq.p);
+        ctx->launches += 1;
+        FTN_CUDA(cudaGetLastError());
+        std::vector<double> hk(chk_words);
+        FTN_CUDA(cudaMemcpyAsync(hk.data(), chk, chk_words * 8, cudaMemcpyDeviceToHost, ctx->stream));
+        FTN_CUDA(cudaStreamSynchronize(ctx->stream));
+        // the Gram factor stands when the dropped columns are within 1e-12 of the kept span
+        for (size_t q = 0; q < jobs.size(); ++q)
+          for (int k = 0; k < 4; ++k)
+            if (hc[8 * q + 4 + k] == 2 && !(hk[8 * q + 4 + k] <= 1e-24 * hk[8 * q + k])) hc[8 * q + 4 + k] |= 1;
+      }
     }
-    for (size_t q = 0; q < jobs.size(); ++q) FTN_TRY(cj_counts(jobs[q], hc.data() + 4 * q));
+    std::vector<std::vector<QrJob>> levels;
+    for (size_t q = 0; q < jobs.size(); ++q) cj_qr(jobs[q], levels, hc.data() + 8 * q + 4);
+    if (!levels.empty()) {
+      FTN_TRY(setup_qr_kernels());
+      for (auto& lv : levels) {
+        // three variants by bond width (one launch each): factor in shared
+        // memory, 32-row passes, 16-row passes
+        std::vector<QrJob> part[3];
+        for (const QrJob& qj : lv) part[qj.K <= QR_RSMEM_K ? 0 : qj.K <= QR_WIDE_K ? 1 : 2].push_back(qj);
+        for (int v = 0; v < 3; ++v) {
+          if (part[v].empty()) continue;
+          int kmax = 0;
+          for (const QrJob& qj : part[v]) kmax = std::max(kmax, qj.K);
+          DevBuf t_qr(ctx);
+          FTN_TRY(put_table(ctx, part[v], &t_qr.p));
+          const int rec = prof_begin(ctx, "householder_qr", 0, 0);
+          const unsigned g = (unsigned)part[v].size();
+          const QrJob* tj = (const QrJob*)t_qr.p;
+          if (v == 0)
+            qr_stream_kernel<QR_ROWS_WIDE, true><<<g, QR_THREADS, ((size_t)kmax * kmax + QR_ROWS_WIDE * kmax) * 8,
+                                                  ctx->stream>>>(tj);
+          else if (v == 1)
+            qr_stream_kernel<QR_ROWS_WIDE, false><<<g, QR_THREADS, (size_t)QR_ROWS_WIDE * kmax * 8, ctx->stream>>>(tj);
+          else
+            qr_stream_kernel<QR_ROWS, false><<<g, QR_THREADS, (size_t)QR_ROWS * kmax * 8, ctx->stream>>>(tj);
+          ctx->launches += 1;
+          FTN_CUDA(cudaGetLastError());
+          prof_end(ctx, rec);
+        }
+      }
+      for (size_t q = 0; q < jobs.size(); ++q)
+        for (int pi = 0; pi < 2; ++pi) {
+          if (hc[8 * q + 4 + 2 * pi] & 1) jobs[q].rx_off[pi] = jobs[q].o_hx[pi];
+          if (hc[8 * q + 4 + 2 * pi + 1] & 1) jobs[q].ry_off[pi] = jobs[q].o_hy[pi];
+        }
+      FTN_TRY(compact(true));
+    }
+    for (size_t q = 0; q < jobs.size(); ++q) {
+      const int c4[4] = {hc[8 * q], hc[8 * q + 1], hc[8 * q + 2], hc[8 * q + 3]};
+      FTN_TRY(cj_counts(jobs[q], c4));
+    }
   }
   // ---- 3. core M = R_X R_Y^T (stored with the rotated side as rows) and SVD ----
   {
@@ -1145,17 +1566,26 @@ ftn_status compress_batch(ftn_ctx ctx, std::vector<CompressItem>& items) {
   }
   {
     // the n-side vectors re-orthogonalised against those of larger singular value
+    // (needed where a kept singular value is small: the error of q_j is about
+    // m eps s_max / s_j, below 1e-11 once every kept s_j >= 1e-2 s_max)
     std::vector<OrthJob> orth;
     for (CJob& J : jobs)
-      for (int pi = 0; pi < 2; ++pi)
-        if (J.k[pi] > 1)
+      for (int pi = 0; pi < 2; ++pi) {
+        if (J.k[pi] < 2) continue;
+        double smin = J.kept.front().s;
+        for (auto& c : J.kept)
+          if (c.pi == pi) smin = std::min(smin, c.s);
+        if (smin < 1e-2 * J.kept.front().s)
           orth.push_back({J.ws + (J.trans[pi] ? J.o_zk[pi] : J.o_wk[pi]), J.ws + J.o_sc[pi], J.k[pi], J.nrot[pi]});
+      }
     if (!orth.empty()) {
       DevBuf t_orth(ctx);
       FTN_TRY(put_table(ctx, orth, &t_orth.p));
+      const int rec = prof_begin(ctx, "orth_nside", 0, 0);
       orth_rows_kernel<<<(unsigned)orth.size(), 256, 0, ctx->stream>>>((const OrthJob*)t_orth.p);
       ctx->launches += 1;
       FTN_CUDA(cudaGetLastError());
+      prof_end(ctx, rec);
     }
   }
   {
