@@ -339,6 +339,45 @@ FTN_API ftn_status ftn_contract(ftn_ctx ctx, const ftn_network* net, const ftn_t
 FTN_API ftn_status ftn_contract_batch(ftn_ctx ctx, int count, const ftn_network* nets, const ftn_tree* trees,
                               ftn_prec prec, double* mantissa, double* log_scale);
 
+/* ---- expectation values of local terms (Sec. V) --------------------------- */
+
+/* Per-term ratios and their sums from contracted network values.  Network i
+ * has the value mantissa[i] * exp(log_scale[i]) (as ftn_contract returns
+ * it); term t is the ratio ratios[t] = value(num[t]) / value(den[t]) =
+ * (mantissa[num[t]] / mantissa[den[t]]) * exp(log_scale[num[t]] -
+ * log_scale[den[t]]) -- <Psi|h_t|Psi> / <Psi|Psi> when num[t] is the term's
+ * network and den[t] the norm network (Sec. V; every term of a whole-state
+ * energy shares one norm network, a cluster term of Fig. 4b has its own).
+ * The terms are split into n_groups consecutive groups (group g ends before
+ * term group_end[g]; non-decreasing, at most n_terms) and energies[g]
+ * receives the FP64 sum of its ratios, added in term order (one group per
+ * state; terms after the last group_end belong to none).  ratios may be
+ * NULL.  Host arithmetic only: no device is touched, the result depends on
+ * nothing but the inputs.  FTN_EINVAL for an index out of [0, count), a
+ * null array that is needed, or a denominator whose value is zero or not
+ * finite. */
+FTN_API ftn_status ftn_energy_reduce(int count, const double* mantissa, const double* log_scale, int n_terms,
+                                     const int32_t* num, const int32_t* den, int n_groups, const int32_t* group_end,
+                                     double* ratios, double* energies);
+
+/* Contract the `count` closed networks nets[i] along trees[i] and reduce
+ * them as ftn_energy_reduce does.  The n_ctx contexts (same device, each on
+ * its own stream; ctxs[0] owns or may have produced the input tensors) each
+ * run on one host thread and take the next network -- or, with batch > 0,
+ * the next run of up to `batch` consecutive networks, contracted in lock
+ * step by ftn_contract_batch -- from a shared counter; the first context's
+ * stream is synchronised before any other reads the inputs.  Every network
+ * is contracted exactly as ftn_contract contracts it, whatever context or
+ * batch it lands in, so the values and sums are the same for any n_ctx and
+ * batch.  mantissa / log_scale (count entries, may be NULL) receive the
+ * network values.  Errors: those of ftn_contract / ftn_contract_batch (the
+ * first one met; the other threads stop taking work) and of
+ * ftn_energy_reduce.  Returns after every network has been contracted. */
+FTN_API ftn_status ftn_energy(int n_ctx, const ftn_ctx* ctxs, int count, const ftn_network* nets,
+                              const ftn_tree* trees, ftn_prec prec, int batch, double* mantissa, double* log_scale,
+                              int n_terms, const int32_t* num, const int32_t* den, int n_groups,
+                              const int32_t* group_end, double* ratios, double* energies);
+
 /* ---- Hubbard terms (Eq. fermi-hubbard-ham) -------------------------------- */
 
 /* Even operator tensors for <Psi| h_t |Psi> (physical leg (2,2): 0 = |0>,

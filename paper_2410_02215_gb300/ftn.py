@@ -89,6 +89,11 @@ def lib():
         "ftn_contract_batch": [vp, C.c_int, C.POINTER(Network), C.POINTER(Tree), C.c_int, C.POINTER(C.c_double),
                                C.POINTER(C.c_double)],
         "ftn_hubbard_term": [vp, C.c_int, C.c_double, C.c_double, C.c_int, C.POINTER(vp)],
+        "ftn_energy_reduce": [C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double), C.c_int, i32p, i32p, C.c_int,
+                              i32p, C.POINTER(C.c_double), C.POINTER(C.c_double)],
+        "ftn_energy": [C.c_int, C.POINTER(vp), C.c_int, C.POINTER(Network), C.POINTER(Tree), C.c_int, C.c_int,
+                       C.POINTER(C.c_double), C.POINTER(C.c_double), C.c_int, i32p, i32p, C.c_int, i32p,
+                       C.POINTER(C.c_double), C.POINTER(C.c_double)],
     }
     for name, args in sigs.items():
         f = getattr(L, name)
@@ -486,13 +491,9 @@ def contract(ctx, tensors, bonds, tree, positions=None, policy="exact", chi=0, p
     return m.value, lg.value
 
 
-def contract_batch(ctx, networks, prec="f64"):
-    """Contract many closed networks in one batched run (ftn_contract_batch).
-
-    ``networks``: sequence of dicts with keys ``tensors``, ``bonds``, ``tree``
-    and optionally ``positions``, ``policy`` ("exact") and ``chi`` (0).
-    Returns a list of (mantissa, log_scale), bit-identical to :func:`contract`
-    on each network alone."""
+def _network_arrays(networks):
+    """ctypes arrays of ftn_network / ftn_tree for a list of network dicts
+    (plus the buffers they point into, to be kept alive by the caller)."""
     nets = list(networks)
     n = len(nets)
     keep = []
@@ -510,10 +511,63 @@ def contract_batch(ctx, networks, prec="f64"):
         pol = job.get("policy", "exact")
         tree_arr[i] = Tree(len(job["tree"]), ft, POLICY_NAMES[pol] if isinstance(pol, str) else int(pol),
                            int(job.get("chi", 0)))
+    return n, net_arr, tree_arr, keep
+
+
+def contract_batch(ctx, networks, prec="f64"):
+    """Contract many closed networks in one batched run (ftn_contract_batch).
+
+    ``networks``: sequence of dicts with keys ``tensors``, ``bonds``, ``tree``
+    and optionally ``positions``, ``policy`` ("exact") and ``chi`` (0).
+    Returns a list of (mantissa, log_scale), bit-identical to :func:`contract`
+    on each network alone."""
+    n, net_arr, tree_arr, keep = _network_arrays(networks)
     m = (C.c_double * max(1, n))()
     lg = (C.c_double * max(1, n))()
     _check(lib().ftn_contract_batch(ctx.handle, n, net_arr, tree_arr, _prec(prec), m, lg))
+    del keep
     return [(m[i], lg[i]) for i in range(n)]
+
+
+def _terms(num, den, group_end):
+    num, den = list(num), list(den)
+    ge = list(group_end) if group_end is not None else [len(num)]
+    return len(num), _i32(num), _i32(den), len(ge), _i32(ge)
+
+
+def energy_reduce(values, num, den, group_end=None):
+    """Per-term ratios value(num[t]) / value(den[t]) and their sums per group
+    (ftn_energy_reduce).  ``values``: (mantissa, log_scale) of every network.
+    Returns (energies per group, ratios per term)."""
+    vals = list(values)
+    cnt = len(vals)
+    m = (C.c_double * max(1, cnt))(*[float(v[0]) for v in vals])
+    lg = (C.c_double * max(1, cnt))(*[float(v[1]) for v in vals])
+    nt, fn, fd, ng, fg = _terms(num, den, group_end)
+    r = (C.c_double * max(1, nt))()
+    e = (C.c_double * max(1, ng))()
+    _check(lib().ftn_energy_reduce(cnt, m, lg, nt, fn, fd, ng, fg, r, e))
+    return [e[g] for g in range(ng)], [r[t] for t in range(nt)]
+
+
+def energy(ctx, networks, num, den, group_end=None, prec="f64", batch=0):
+    """Contract every network (dicts as for :func:`contract_batch`) on the
+    given context(s) and reduce them to term ratios and group sums
+    (ftn_energy).  ``ctx``: one Context or a list (one host thread each).
+    Returns (energies per group, ratios per term, [(mantissa, log_scale)] per
+    network)."""
+    ctxs = list(ctx) if isinstance(ctx, (list, tuple)) else [ctx]
+    carr = (C.c_void_p * len(ctxs))(*[c.handle.value for c in ctxs])
+    n, net_arr, tree_arr, keep = _network_arrays(networks)
+    m = (C.c_double * max(1, n))()
+    lg = (C.c_double * max(1, n))()
+    nt, fn, fd, ng, fg = _terms(num, den, group_end)
+    r = (C.c_double * max(1, nt))()
+    e = (C.c_double * max(1, ng))()
+    _check(lib().ftn_energy(len(ctxs), carr, n, net_arr, tree_arr, _prec(prec), int(batch), m, lg, nt, fn, fd, ng, fg,
+                            r, e))
+    del keep
+    return [e[g] for g in range(ng)], [r[t] for t in range(nt)], [(m[i], lg[i]) for i in range(n)]
 
 
 def hubbard_term(ctx, kind, t=1.0, u=0.0, dtype=F64):

@@ -1,8 +1,9 @@
 """PEPS norm and energy networks assembled for libftn's contraction executor.
 
-Marshalling only: this module builds bond lists and positions and calls the
-C ABI (ftn_tensor_dagger, ftn_hubbard_term, ftn_contract, ftn_contract_batch);
-every contraction, compression and reduction runs in libftn.
+Marshalling only: this module builds bond lists, positions and term index
+tables and calls the C ABI (ftn_tensor_dagger, ftn_hubbard_term, ftn_energy,
+ftn_energy_reduce); every contraction, compression, ratio and sum runs in
+libftn.
 
 Networks follow the globally ordered picture of the norm (Sec. IV.B, Fig. 4a):
 the bra layer -- the daggers of the ket tensors, in reversed site order --
@@ -13,8 +14,6 @@ the same value.
 Tensor ids: ket s -> s, bra s -> n + s, operator -> 2n.
 """
 from __future__ import annotations
-
-import math
 
 from . import ftn
 
@@ -68,28 +67,19 @@ def term_network(layout, kets, bras, op, sites):
     return list(kets) + list(bras) + [op], bonds, pos
 
 
-def energy(ctx, layout, kets, t, u, tree_fn, mode="local", policy="exact", chi=0, prec="f64", batch=0):
-    """sum_t <h_t>/<Psi|Psi> over all nearest-neighbour hopping and on-site
-    terms; each term and the norm are contracted with tree_fn(op_sites).
-    Returns (energy, norm mantissa, norm log-scale).
-
-    ``ctx`` may be a list of contexts (each on its own stream): the norm and
-    the terms are independent contractions, so host threads, one per
-    context, take them from a shared counter and run them concurrently on
-    the GPU.  The kets, bras and operator tensors belong to the first
-    context and are only read by the others.  The sum runs in term order,
-    so the result does not depend on the schedule.  ``batch`` as in
-    :func:`contract_many` (bit-identical results either way)."""
-    ctxs = list(ctx) if isinstance(ctx, (list, tuple)) else [ctx]
-    c0 = ctxs[0]
-    dt = ftn.F64 if prec == "f64" else ftn.F32
+def energy_networks(ctx, layout, kets, t, u, tree_fn, mode="local", policy="exact", chi=0, dtype=ftn.F64):
+    """The norm network followed by one network per nearest-neighbour hopping
+    term and per on-site term, each with the tree tree_fn(op_sites), and the
+    term table of ftn_energy (term t = network t + 1 over network 0).
+    Returns (networks, num, den, group_end, keep) -- ``keep`` holds tensors
+    the networks borrow (bras, operators)."""
     n = layout["n"]
-    bras = [ftn.dagger(c0, k) for k in kets]
+    bras = [ftn.dagger(ctx, k) for k in kets]
     glob = mode == "global"
-    hop = ftn.hubbard_term(c0, 0, t, 0.0, dt)
-    onsite = ftn.hubbard_term(c0, 1, 0.0, u, dt)
+    hop = ftn.hubbard_term(ctx, 0, t, 0.0, dtype)
+    onsite = ftn.hubbard_term(ctx, 1, 0.0, u, dtype)
     jobs = []
-    tens, bonds, pos = norm_network(c0, layout, kets, bras)
+    tens, bonds, pos = norm_network(ctx, layout, kets, bras)
     jobs.append((tens, bonds, pos, tree_fn(())))
     for a, b in layout["edges"]:
         tens, bonds, pos = term_network(layout, kets, bras, hop, (a, b))
@@ -97,71 +87,29 @@ def energy(ctx, layout, kets, t, u, tree_fn, mode="local", policy="exact", chi=0
     for s in range(n):
         tens, bonds, pos = term_network(layout, kets, bras, onsite, (s,))
         jobs.append((tens, bonds, pos, tree_fn((s,))))
-
     nets = [{"tensors": tens, "bonds": bonds, "tree": tree, "positions": pos if glob else None, "policy": policy,
              "chi": chi} for tens, bonds, pos, tree in jobs]
-    results = contract_many(ctxs, nets, prec, batch)
-    nm, nl = results[0]
-    total = 0.0
-    for m, lg in results[1:]:
-        total += m / nm * math.exp(lg - nl)
-    return total, nm, nl
+    nt = len(nets) - 1
+    return nets, list(range(1, nt + 1)), [0] * nt, [nt], (bras, hop, onsite)
 
 
-def contract_many(ctx, networks, prec="f64", batch=0):
-    """(mantissa, log_scale) of every network (dicts as for
-    :func:`ftn.contract_batch`), in order.  ``batch`` = 0: one ftn_contract
-    per network; > 0: batches of up to ``batch`` networks per
-    ftn_contract_batch call.  With several contexts, host threads (one per
-    context) take networks or batches from a shared counter."""
+def energy(ctx, layout, kets, t, u, tree_fn, mode="local", policy="exact", chi=0, prec="f64", batch=0):
+    """sum_t <h_t>/<Psi|Psi> over all nearest-neighbour hopping and on-site
+    terms; each term and the norm are contracted with tree_fn(op_sites)
+    (ftn_energy).  Returns (energy, norm mantissa, norm log-scale).
+
+    ``ctx`` may be a list of contexts (each on its own stream): the norm and
+    the terms are independent contractions, which libftn's host threads, one
+    per context, take from a shared counter and run concurrently on the GPU.
+    The kets belong to the first context and are only read by the others.
+    ``batch`` > 0 contracts runs of up to ``batch`` networks in lock step
+    (ftn_contract_batch).  The value is the same bit for bit in every case."""
     ctxs = list(ctx) if isinstance(ctx, (list, tuple)) else [ctx]
-    nets = list(networks)
-    if batch and batch > 0:
-        chunks = [nets[i:i + batch] for i in range(0, len(nets), batch)]
-        res = _run_jobs(ctxs, chunks, lambda c, ch: ftn.contract_batch(c, ch, prec=prec))
-        return [r for part in res for r in part]
-
-    def run(c, job):
-        return ftn.contract(c, job["tensors"], job["bonds"], job["tree"], positions=job.get("positions"),
-                            policy=job.get("policy", "exact"), chi=job.get("chi", 0), prec=prec)
-
-    return _run_jobs(ctxs, nets, run)
-
-
-def _run_jobs(ctxs, jobs, run):
-    """run(ctx, job) for every job; with several contexts, host threads (one
-    per context) take jobs from a shared counter.  Results in job order."""
-    c0 = ctxs[0]
-    if len(ctxs) == 1:
-        return [run(c0, job) for job in jobs]
-    import threading
-
-    c0.synchronize()  # inputs ready before other streams read them
-    results = [None] * len(jobs)
-    errors = []
-    lock = threading.Lock()
-    nxt = [0]
-
-    def worker(c):
-        try:
-            while True:
-                with lock:
-                    i = nxt[0]
-                    nxt[0] += 1
-                if i >= len(jobs) or errors:
-                    return
-                results[i] = run(c, jobs[i])
-        except BaseException as e:  # re-raised on the calling thread
-            errors.append(e)
-
-    threads = [threading.Thread(target=worker, args=(c,)) for c in ctxs]
-    for th in threads:
-        th.start()
-    for th in threads:
-        th.join()
-    if errors:
-        raise errors[0]
-    return results
+    dt = ftn.F64 if prec == "f64" else ftn.F32
+    nets, num, den, ge, keep = energy_networks(ctxs[0], layout, kets, t, u, tree_fn, mode, policy, chi, dt)
+    en, _, vals = ftn.energy(ctxs, nets, num, den, ge, prec, batch)
+    del keep
+    return en[0], vals[0][0], vals[0][1]
 
 
 # ---- cluster approximation (Sec. V) -------------------------------------------
@@ -223,38 +171,24 @@ def cluster_network(layout, kets, bras, sites, dangling, gauge_of, op=None, targ
     return tensors, bonds, pos
 
 
-def cluster_energy(ctx, layout, kets, t, u, cluster_fn, gauges, policy="exact", chi=0, prec="f64", batch=0):
-    """Cluster approximation of sum_t <h_t>: every hopping and on-site term
-    is the ratio of its cluster network with the operator to the same network
-    without it, both contracted in the globally ordered formalism.
-    ``cluster_fn(targets)`` gives (sites, dangling bonds, tree with the
-    operator, tree without it); ``gauges[(s, t)]`` = (even, odd) weights of
-    the bond's stand-in gauge.  ``ctx`` may be a list of contexts (the
-    contractions then run concurrently, as in :func:`energy`); ``batch`` as
-    in :func:`contract_many`.  Returns (energy, per-term ratios)."""
-    return cluster_energies(ctx, [(layout, kets, cluster_fn, gauges)], t, u, policy, chi, prec, batch)[0]
-
-
-def cluster_energies(ctx, instances, t, u, policy="exact", chi=0, prec="f64", batch=0):
-    """:func:`cluster_energy` of several states at once: ``instances`` is a
-    list of (layout, kets, cluster_fn, gauges); the networks of all terms of
-    all instances are contracted together (in batches of up to ``batch``
-    networks when ``batch`` > 0).  Returns [(energy, ratios)] per instance."""
-    ctxs = list(ctx) if isinstance(ctx, (list, tuple)) else [ctx]
-    c0 = ctxs[0]
-    dt = ftn.F64 if prec == "f64" else ftn.F32
-    hop = ftn.hubbard_term(c0, 0, t, 0.0, dt)
-    onsite = ftn.hubbard_term(c0, 1, 0.0, u, dt)
-    nets, nterms, keep = [], [], []
+def cluster_networks(ctx, instances, t, u, policy="exact", chi=0, dtype=ftn.F64):
+    """Cluster networks of every hopping and on-site term of every instance
+    (layout, kets, cluster_fn, gauges): for each term the network with the
+    operator, then the same network without it (its normalisation), and the
+    term table of ftn_energy with one group per instance.  Returns
+    (networks, num, den, group_end, keep)."""
+    hop = ftn.hubbard_term(ctx, 0, t, 0.0, dtype)
+    onsite = ftn.hubbard_term(ctx, 1, 0.0, u, dtype)
+    nets, group_end, keep = [], [], [hop, onsite]
     for layout, kets, cluster_fn, gauges in instances:
-        bras = [ftn.dagger(c0, k) for k in kets]
+        bras = [ftn.dagger(ctx, k) for k in kets]
         cache = {}
 
         def gauge_of(s, a, layout=layout, kets=kets, gauges=gauges, cache=cache):
             if (s, a) not in cache:
                 nb = layout["nbrs"][s][a]
                 lam = gauges[(min(s, nb), max(s, nb))]
-                cache[(s, a)] = gauge_tensor(c0, lam[0], lam[1], kets[s].legs[a][2], dt)
+                cache[(s, a)] = gauge_tensor(ctx, lam[0], lam[1], kets[s].legs[a][2], dtype)
             return cache[(s, a)]
 
         terms = [((a, b), hop) for a, b in layout["edges"]] + [((s,), onsite) for s in range(layout["n"])]
@@ -264,15 +198,37 @@ def cluster_energies(ctx, instances, t, u, policy="exact", chi=0, prec="f64", ba
                 tens, bonds, pos = cluster_network(layout, kets, bras, sites, dang, gauge_of, o, targets)
                 nets.append({"tensors": tens, "bonds": bonds, "tree": tree, "positions": pos, "policy": policy,
                              "chi": chi})
-        nterms.append(len(terms))
+        group_end.append(len(nets) // 2)
         keep.append((bras, cache))
-    res = contract_many(ctxs, nets, prec, batch)
-    out, q = [], 0
-    for nt in nterms:
-        ratios = []
-        for _ in range(nt):
-            (mn, ln), (md, ld) = res[q], res[q + 1]
-            ratios.append(mn / md * math.exp(ln - ld))
-            q += 2
-        out.append((float(sum(ratios)), ratios))
+    nt = len(nets) // 2
+    return nets, [2 * q for q in range(nt)], [2 * q + 1 for q in range(nt)], group_end, keep
+
+
+def cluster_energy(ctx, layout, kets, t, u, cluster_fn, gauges, policy="exact", chi=0, prec="f64", batch=0):
+    """Cluster approximation of sum_t <h_t>: every hopping and on-site term
+    is the ratio of its cluster network with the operator to the same network
+    without it, both contracted in the globally ordered formalism.
+    ``cluster_fn(targets)`` gives (sites, dangling bonds, tree with the
+    operator, tree without it); ``gauges[(s, t)]`` = (even, odd) weights of
+    the bond's stand-in gauge.  ``ctx`` may be a list of contexts (the
+    contractions then run concurrently, as in :func:`energy`); ``batch`` as
+    in :func:`energy`.  Returns (energy, per-term ratios)."""
+    return cluster_energies(ctx, [(layout, kets, cluster_fn, gauges)], t, u, policy, chi, prec, batch)[0]
+
+
+def cluster_energies(ctx, instances, t, u, policy="exact", chi=0, prec="f64", batch=0):
+    """:func:`cluster_energy` of several states at once: ``instances`` is a
+    list of (layout, kets, cluster_fn, gauges); the networks of all terms of
+    all instances are contracted by one ftn_energy call (in lock-step runs of
+    up to ``batch`` networks when ``batch`` > 0).  Returns [(energy, ratios)]
+    per instance."""
+    ctxs = list(ctx) if isinstance(ctx, (list, tuple)) else [ctx]
+    dt = ftn.F64 if prec == "f64" else ftn.F32
+    nets, num, den, ge, keep = cluster_networks(ctxs[0], instances, t, u, policy, chi, dt)
+    en, ratios, _ = ftn.energy(ctxs, nets, num, den, ge, prec, batch)
+    del keep
+    out, t0 = [], 0
+    for g, t1 in enumerate(ge):
+        out.append((en[g], ratios[t0:t1]))
+        t0 = t1
     return out
