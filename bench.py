@@ -663,6 +663,117 @@ def energy_bench(F, ctx, evals, with_oracle, workers=8, batches=(0, 2, 3, 6)):
     return out
 
 
+DIAMOND_WORKLOAD = ("Hubbard fPEPS on the 2x2x2-conventional-cell diamond lattice (64 sites, 86 bonds, open "
+                    "boundaries), D=4 (2+2), phys 4 (2+2), t=1, U=8, N(0,1) site tensors (seed 1), stand-in gauges "
+                    "0.5^k per sector on dangling bonds; every hopping and on-site term (150) by the cluster "
+                    "approximation of radius 1 (cluster network with and without the operator, globally ordered), "
+                    "late compression chi=32 (at radius 1 every bond of every intermediate is at most D^2=16, so "
+                    "chi=32 and chi=64 give the same contraction)")
+
+
+def diamond_bench(F, ctx, torch, evals, streams, with_oracle, rank=0, world=1, batches=(0, 8, 32)):
+    """Energy evaluations per second of the 64-site diamond (radius-1 cluster
+    approximation of all 150 terms), FP64 and mixed, with their errors; the
+    term networks are split across ranks when world > 1 (dist.energy_sharded:
+    one all-reduce of the network values, the same reduction on every rank).
+    The oracle is timed on one representative term per cluster size and its
+    time for all terms extrapolated from the counts (labelled so)."""
+    import numpy as np
+
+    from paper_2410_02215_gb300 import dist as D
+    from paper_2410_02215_gb300 import peps
+
+    n, edges, _ = W.diamond_lattice(2, 2, 2)
+    lay = W.peps_layout(n, edges, (2, 2), (2, 2))
+    blocks = W.random_peps(lay, 1)
+    gs = W.bond_gauges(lay)
+
+    def cfn(targets):
+        sites = W.cluster_sites(lay, targets, 1)
+        return (sites, W.dangling_bonds(lay, sites), W.cluster_tree(lay, sites, targets, True),
+                W.cluster_tree(lay, sites, targets, False))
+
+    ctxs = [ctx] + [F.Context(stream=torch.cuda.Stream()) for _ in range(max(streams, 1) - 1)]
+    out = {"workload": DIAMOND_WORKLOAD, "streams": len(ctxs), "ranks": world,
+           "terms": len(lay["edges"]) + n, "networks_per_eval": 2 * (len(lay["edges"]) + n)}
+    res = {}
+    for prec, dt in (("f64", F.F64), ("tf32x3", F.F32), ("f16x3", F.F32)):
+        kets = [F.Tensor.from_blocks(ctx, lay["legs"][s], 0, blocks[s], dt) for s in range(n)]
+        ctx.synchronize()
+        nets, num, den, ge, keep = peps.cluster_networks(ctx, [(lay, kets, cfn, gs)], 1.0, 8.0, "late", 32, dt)
+
+        def evaluate(batch):
+            if world == 1:
+                return F.energy(ctxs, nets, num, den, ge, prec, batch)[:2]
+            return D.energy_sharded(nets, num, den, ge, rank, world,
+                                    lambda sub: F.energy(ctxs, sub, [], [], [], prec, batch)[2])
+
+        for c in ctxs:  # warm-up: every context builds its plans
+            F.energy(c, nets, num, den, ge, prec, 0)
+        trial = {}
+        for b in batches:
+            evaluate(b)
+            barrier(world)
+            t0 = time.perf_counter()
+            en, rat = evaluate(b)
+            trial[b] = time.perf_counter() - t0
+        best = min(trial, key=lambda b: trial[b])
+        l0 = sum(c.launches() for c in ctxs)
+        barrier(world)
+        t0 = time.perf_counter()
+        for _ in range(evals):
+            en, rat = evaluate(best)
+        barrier(world)
+        dt_s = max_over_ranks(time.perf_counter() - t0, world)
+        res[prec] = (en[0], rat)
+        out[prec] = {"evals_per_s": evals / dt_s, "s_per_eval": dt_s / evals, "terms_per_s": evals * len(rat) / dt_s,
+                     "energy": en[0], "energy_per_site": en[0] / n, "batch": best,
+                     "gpu_launches_per_eval": (sum(c.launches() for c in ctxs) - l0) / evals,
+                     "trial_s_per_eval_by_batch": {str(b): round(v, 4) for b, v in trial.items()}}
+        del keep
+    e64, r64 = res["f64"]
+    for p in ("tf32x3", "f16x3"):
+        out[p]["rel_err_vs_f64"] = abs(res[p][0] - e64) / abs(e64)
+        out[p]["max_term_err_vs_f64"] = max(abs(x - y) for x, y in zip(res[p][1], r64)) / max(abs(y) for y in r64)
+        out[p]["speedup_vs_f64"] = out[p]["evals_per_s"] / out["f64"]["evals_per_s"]
+    out["mixed_vs_f64_rel_err"] = out["tf32x3"]["rel_err_vs_f64"]
+    out["speedup_mixed_vs_f64"] = out["f16x3"]["speedup_vs_f64"]
+    if with_oracle:
+        import oracle as O
+
+        okets = O.ket_tensors(lay, blocks)
+        terms = [tuple(e) for e in lay["edges"]] + [(s,) for s in range(n)]
+        by_size = {}
+        for q, tg in enumerate(terms):
+            by_size.setdefault((len(tg), len(W.cluster_sites(lay, list(tg), 1))), []).append(q)
+        est, errs, sample_s = 0.0, [], 0.0
+        for key in sorted(by_size):
+            q = by_size[key][0]
+            tg = terms[q]
+            op = O.hop_gate(1.0) if len(tg) == 2 else O.onsite_gate(8.0)
+            sites, dang, tr_op, tr_norm = cfn(list(tg))
+            t0 = time.perf_counter()
+            rn, ln, _ = O.contract_tree(O.cluster_network(lay, okets, sites, dang, gs, op, list(tg)), tr_op,
+                                        mode="global", policy="late", chi=32, normalize=True)
+            rd, ld, _ = O.contract_tree(O.cluster_network(lay, okets, sites, dang, gs), tr_norm, mode="global",
+                                        policy="late", chi=32, normalize=True)
+            dt_t = time.perf_counter() - t0
+            ref = float(rn.data) / float(rd.data) * np.exp(ln - ld)
+            errs.append(abs(r64[q] - ref))
+            sample_s += dt_t
+            est += dt_t * len(by_size[key])
+        scale = max(abs(y) for y in r64)
+        out["oracle"] = {"s_per_eval_extrapolated": est, "evals_per_s_extrapolated": 1.0 / est,
+                         "cores": len(os.sched_getaffinity(0)),
+                         "sample": f"one term per (term kind, cluster size) class, {len(by_size)} terms in "
+                                   f"{sample_s:.1f} s; the full evaluation's time extrapolated from the class counts",
+                         "f64_gpu_max_term_err_on_sample": max(errs) / scale}
+    for c in ctxs[1:]:
+        c.synchronize()
+        c.close()
+    return out
+
+
 def run_ours(args, rank, world, local):
     import torch
 
@@ -738,6 +849,9 @@ def run_ours(args, rank, world, local):
     if not args.no_energy:
         result["energy"] = energy_bench(F, ctx, args.energy_evals, rank == 0 and world == 1 and not args.no_cpu,
                                         args.energy_streams)
+    if not args.no_diamond:
+        result["energy_diamond"] = diamond_bench(F, ctx, torch, args.diamond_evals, args.energy_streams,
+                                                 rank == 0 and world == 1 and not args.no_cpu, rank, world)
     if rank == 0 and world == 1 and not args.no_cpu:
         result["cpu_baseline"] = cpu_baseline(cases)
     ctx.synchronize()
@@ -769,6 +883,8 @@ def main():
     ap.add_argument("--energy-streams", type=int, default=8,
                     help="contexts (CUDA streams) that run an evaluation's contractions concurrently")
     ap.add_argument("--no-accuracy", action="store_true")
+    ap.add_argument("--no-diamond", action="store_true")
+    ap.add_argument("--diamond-evals", type=int, default=2)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

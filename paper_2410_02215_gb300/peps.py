@@ -171,12 +171,13 @@ def cluster_network(layout, kets, bras, sites, dangling, gauge_of, op=None, targ
     return tensors, bonds, pos
 
 
-def cluster_networks(ctx, instances, t, u, policy="exact", chi=0, dtype=ftn.F64):
+def cluster_networks(ctx, instances, t, u, policy="exact", chi=0, dtype=ftn.F64, terms=None):
     """Cluster networks of every hopping and on-site term of every instance
-    (layout, kets, cluster_fn, gauges): for each term the network with the
-    operator, then the same network without it (its normalisation), and the
-    term table of ftn_energy with one group per instance.  Returns
-    (networks, num, den, group_end, keep)."""
+    (layout, kets, cluster_fn, gauges) -- or of the target tuples ``terms``
+    (pairs are hopping terms, single sites on-site terms): for each term the
+    network with the operator, then the same network without it (its
+    normalisation), and the term table of ftn_energy with one group per
+    instance.  Returns (networks, num, den, group_end, keep)."""
     hop = ftn.hubbard_term(ctx, 0, t, 0.0, dtype)
     onsite = ftn.hubbard_term(ctx, 1, 0.0, u, dtype)
     nets, group_end, keep = [], [], [hop, onsite]
@@ -191,8 +192,11 @@ def cluster_networks(ctx, instances, t, u, policy="exact", chi=0, dtype=ftn.F64)
                 cache[(s, a)] = gauge_tensor(ctx, lam[0], lam[1], kets[s].legs[a][2], dtype)
             return cache[(s, a)]
 
-        terms = [((a, b), hop) for a, b in layout["edges"]] + [((s,), onsite) for s in range(layout["n"])]
-        for targets, op in terms:
+        if terms is None:
+            tl = [((a, b), hop) for a, b in layout["edges"]] + [((s,), onsite) for s in range(layout["n"])]
+        else:
+            tl = [(tuple(tg), hop if len(tg) == 2 else onsite) for tg in terms]
+        for targets, op in tl:
             sites, dang, tree_op, tree_norm = cluster_fn(list(targets))
             for o, tree in ((op, tree_op), (None, tree_norm)):
                 tens, bonds, pos = cluster_network(layout, kets, bras, sites, dang, gauge_of, o, targets)
@@ -216,15 +220,15 @@ def cluster_energy(ctx, layout, kets, t, u, cluster_fn, gauges, policy="exact", 
     return cluster_energies(ctx, [(layout, kets, cluster_fn, gauges)], t, u, policy, chi, prec, batch)[0]
 
 
-def cluster_energies(ctx, instances, t, u, policy="exact", chi=0, prec="f64", batch=0):
+def cluster_energies(ctx, instances, t, u, policy="exact", chi=0, prec="f64", batch=0, terms=None):
     """:func:`cluster_energy` of several states at once: ``instances`` is a
     list of (layout, kets, cluster_fn, gauges); the networks of all terms of
     all instances are contracted by one ftn_energy call (in lock-step runs of
-    up to ``batch`` networks when ``batch`` > 0).  Returns [(energy, ratios)]
-    per instance."""
+    up to ``batch`` networks when ``batch`` > 0); ``terms`` as in
+    :func:`cluster_networks`.  Returns [(energy, ratios)] per instance."""
     ctxs = list(ctx) if isinstance(ctx, (list, tuple)) else [ctx]
     dt = ftn.F64 if prec == "f64" else ftn.F32
-    nets, num, den, ge, keep = cluster_networks(ctxs[0], instances, t, u, policy, chi, dt)
+    nets, num, den, ge, keep = cluster_networks(ctxs[0], instances, t, u, policy, chi, dt, terms)
     en, ratios, _ = ftn.energy(ctxs, nets, num, den, ge, prec, batch)
     del keep
     out, t0 = [], 0

@@ -1,0 +1,131 @@
+"""The 64-site diamond workload (2x2x2 conventional cells, D = 4 as 2+2,
+physical 4 as 2+2, t = 1, U = 8) in the cluster approximation of radius 1
+(Sec. V, Fig. 4b), and ftn_energy itself.
+
+* Selected terms -- a bond between two 4-coordinated sites (8-site
+  cluster), a bond to a 1-coordinated site, on-site terms on a 4- and a
+  1-coordinated site -- against the oracle's cluster contraction: FP64 at
+  1e-10 (normwise over the terms), F16X3 within 1e-6 of FP64.  Late
+  compression at chi = 32 is requested as in the benchmark; at radius 1 every
+  bond of every intermediate is at most D^2 = 16, so nothing is compressed.
+* ftn_energy over several contexts and lock-step batch sizes returns the
+  network values of one ftn_contract per network bit for bit, and an error
+  met by a worker thread reaches the caller with its message.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def F():
+    import torch
+
+    from paper_2410_02215_gb300 import ftn
+
+    assert torch.cuda.is_available()
+    ftn.lib()
+    return ftn
+
+
+@pytest.fixture(scope="module")
+def ctx(F):
+    c = F.Context()
+    yield c
+    c.synchronize()
+    c.close()
+
+
+def diamond():
+    n, edges, _ = W.diamond_lattice(2, 2, 2)
+    lay = W.peps_layout(n, edges, (2, 2), (2, 2))
+    return lay, W.random_peps(lay, 1), W.bond_gauges(lay)
+
+
+def cfn(lay, r=1):
+    def f(targets):
+        sites = W.cluster_sites(lay, targets, r)
+        return (sites, W.dangling_bonds(lay, sites), W.cluster_tree(lay, sites, targets, True),
+                W.cluster_tree(lay, sites, targets, False))
+    return f
+
+
+def selected_terms(lay):
+    deg = [len(lay["nbrs"][s]) for s in range(lay["n"])]
+    bulk = [e for e in lay["edges"] if deg[e[0]] == 4 and deg[e[1]] == 4]
+    leaf = [e for e in lay["edges"] if min(deg[e[0]], deg[e[1]]) == 1]
+    s4 = next(s for s in range(lay["n"]) if deg[s] == 4)
+    s1 = next(s for s in range(lay["n"]) if deg[s] == 1)
+    return [bulk[0], leaf[0], (s4,), (s1,)]
+
+
+def oracle_term(lay, kets, gs, targets):
+    op = O.hop_gate(1.0) if len(targets) == 2 else O.onsite_gate(8.0)
+    sites = W.cluster_sites(lay, list(targets), 1)
+    dang = W.dangling_bonds(lay, sites)
+    num = O.cluster_network(lay, kets, sites, dang, gs, op, list(targets))
+    den = O.cluster_network(lay, kets, sites, dang, gs)
+    rn, ln, _ = O.contract_tree(num, W.cluster_tree(lay, sites, list(targets), True), mode="global", policy="late",
+                                chi=32, normalize=True)
+    rd, ld, _ = O.contract_tree(den, W.cluster_tree(lay, sites, list(targets), False), mode="global", policy="late",
+                                chi=32, normalize=True)
+    return float(rn.data) / float(rd.data) * np.exp(ln - ld)
+
+
+def test_diamond_terms_match_oracle(F, ctx):
+    from paper_2410_02215_gb300 import peps
+
+    lay, blocks, gs = diamond()
+    assert lay["n"] == 64 and len(lay["edges"]) == 86
+    terms = selected_terms(lay)
+    okets = O.ket_tensors(lay, blocks)
+    ref = [oracle_term(lay, okets, gs, t) for t in terms]
+    out = {}
+    for prec, dt in (("f64", F.F64), ("f16x3", F.F32)):
+        kets = [F.Tensor.from_blocks(ctx, lay["legs"][s], 0, blocks[s], dt) for s in range(lay["n"])]
+        (e, rat), = peps.cluster_energies(ctx, [(lay, kets, cfn(lay), gs)], 1.0, 8.0, policy="late", chi=32, prec=prec,
+                                          terms=terms)
+        assert e == sum(rat)
+        out[prec] = rat
+    scale = max(abs(y) for y in ref)
+    assert max(abs(x - y) for x, y in zip(out["f64"], ref)) <= 1e-10 * scale
+    assert max(abs(x - y) for x, y in zip(out["f16x3"], out["f64"])) <= 1e-6 * scale
+
+
+def test_ftn_energy_contexts_and_batches(F, ctx):
+    import torch
+
+    from paper_2410_02215_gb300 import peps
+
+    lay, blocks, gs = diamond()
+    deg = [len(lay["nbrs"][s]) for s in range(lay["n"])]
+    terms = [e for e in lay["edges"] if min(deg[e[0]], deg[e[1]]) <= 2][:6] + [(s,) for s in range(6)]
+    kets = [F.Tensor.from_blocks(ctx, lay["legs"][s], 0, blocks[s]) for s in range(lay["n"])]
+    nets, num, den, ge, keep = peps.cluster_networks(ctx, [(lay, kets, cfn(lay), gs)], 1.0, 8.0, "late", 32,
+                                                     terms=terms)
+    single = [F.contract(ctx, n["tensors"], n["bonds"], n["tree"], positions=n["positions"], policy=n["policy"],
+                         chi=n["chi"]) for n in nets]
+    extra = [F.Context(stream=torch.cuda.Stream()) for _ in range(3)]
+    try:
+        base = None
+        for nctx, batch in ((1, 0), (4, 0), (4, 3), (2, 7)):
+            en, rat, vals = F.energy([ctx] + extra[:nctx - 1], nets, num, den, ge, "f64", batch)
+            assert vals == single  # every network as ftn_contract computes it
+            if base is None:
+                base = (en, rat)
+            assert (en, rat) == base
+        bad = dict(nets[3])
+        bad["tree"] = [(0, 0)] + list(bad["tree"][1:])  # a tree that reuses an id
+        with pytest.raises(F.FtnError) as err:
+            F.energy([ctx] + extra, nets[:3] + [bad] + nets[4:], num, den, ge, "f64", 0)
+        assert err.value.status == -1 and "tree" in str(err.value)
+        F.energy([ctx] + extra, nets, num, den, ge, "f64", 2)  # the contexts are still usable
+    finally:
+        for c in extra:
+            c.synchronize()
+            c.close()
+    del keep

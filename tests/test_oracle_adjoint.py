@@ -66,8 +66,8 @@ def test_adjoint_identity(ci, px, py):
     dx = O.contract_grad(x, y, ax, ay, g, wrt="x", out_perm=perm)
     dy = O.contract_grad(x, y, ax, ay, g, wrt="y", out_perm=perm)
     form = float(np.sum(g.data * c.data))
-    assert abs(float(np.sum(dx.data * x.data)) - form) <= 1e-12 * max(1.0, abs(form))
-    assert abs(float(np.sum(dy.data * y.data)) - form) <= 1e-12 * max(1.0, abs(form))
+    assert abs(float(np.sum(dx.data * x.data)) - form) <= 1e-12 * abs(form)
+    assert abs(float(np.sum(dy.data * y.data)) - form) <= 1e-12 * abs(form)
 
 
 def test_planted_sign_mistake_is_detected():

@@ -80,7 +80,7 @@ def test_energy_matches_exact_diagonalisation(D, seed, U):
         for order in ([0, 1, 2, 3], [3, 1, 2, 0]):
             st = W.site_sweep_tree(order)
             e, *_ = O.energy_terms(lay, kets, 1.0, U, lambda ops: W.double_layer_tree(n, st, ops), mode=mode)
-            assert abs(e - e_ed) <= 1e-11 * max(1.0, abs(e_ed)), (mode, order)
+            assert abs(e - e_ed) <= 1e-11 * abs(e_ed), (mode, order)
 
 
 def test_ed_hopping_sign_with_jw_string():
@@ -95,7 +95,7 @@ def test_ed_hopping_sign_with_jw_string():
     net = O.term_network(lay, kets, O.hop_gate(1.0), (0, 2))
     r, lg, _ = O.contract_tree(net, W.double_layer_tree(n, st, (0, 2)), normalize=True)
     val = float(r.data) / float(nt.data) * np.exp(lg - nlog)
-    assert abs(val - e_ed) <= 1e-11 * max(1.0, abs(e_ed))
+    assert abs(val - e_ed) <= 1e-11 * abs(e_ed)
 
 
 def test_planted_mistakes_are_caught(monkeypatch):
