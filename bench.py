@@ -189,9 +189,34 @@ def cpu_baseline(cases, budget_s=20.0):
         flops += f
         secs += s
         reps += 1
-    return {"value": flops / secs / 1e12, "unit": "TFLOP/s", "cores": len(os.sched_getaffinity(0)), "kind": "oracle",
-            "sample": f"{reps} full oracle pass(es) over T1-T4 (dense FP64 numpy, data generation excluded), "
-                      f"{secs:.1f} s"}
+    out = {"value": flops / secs / 1e12, "unit": "TFLOP/s", "cores": len(os.sched_getaffinity(0)), "kind": "oracle",
+           "sample": f"{reps} full oracle pass(es) over T1-T4 (dense FP64 numpy, data generation excluded), "
+                     f"{secs:.1f} s"}
+    one = single_thread_oracle([c["name"] for c in cases])
+    if one is not None:
+        out["single_thread"] = one
+    return out
+
+
+def single_thread_oracle(names, timeout=120):
+    """The same oracle pass with one BLAS thread: a child process started with
+    the thread-count variables of the common BLAS libraries set to 1 before
+    numpy loads.  Returns {"value", "unit", "cores": 1, "sample"} or None."""
+    import subprocess
+
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "BLIS_NUM_THREADS"):
+        env[k] = "1"
+    code = ("import json, sys; sys.path.insert(0, %r); import bench, workloads as W; "
+            "cs = [W.tensordot_case(n, seed=0) for n in %r]; f, s = bench.oracle_pass(cs); "
+            "print(json.dumps([f, s]))") % (os.path.dirname(os.path.abspath(__file__)), list(names))
+    try:
+        r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=timeout)
+        f, s = json.loads(r.stdout.strip().splitlines()[-1])
+    except Exception:  # a missing or slow child only drops this figure
+        return None
+    return {"value": f / s / 1e12, "unit": "TFLOP/s", "cores": 1,
+            "sample": f"one full oracle pass over {','.join(names)} with one BLAS thread, {s:.1f} s"}
 
 
 def run_reference(args, rank, world):
