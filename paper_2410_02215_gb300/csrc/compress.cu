@@ -982,6 +982,7 @@ struct CJob {
   int64_t o_tx[2], o_ty[2];
   int qr_px[2], qr_py[2];
   int sp_x[2], sp_y[2], rx[2], ry[2], ldx[2], ldy[2], nrot[2], mlen[2];
+  int rx0[2], ry0[2];  // rows of the factors before compaction (min(rows, K))
   int64_t rx_off[2], ry_off[2];
   bool tall_x[2], tall_y[2], trans[2];
   struct Cand {
@@ -1021,8 +1022,8 @@ ftn_status cj_prepare(ftn_ctx ctx, CJob& J) {
     const int64_t K = P->K[pi], R = P->M[pi], Cc = P->N[pi];
     J.tall_x[pi] = R > K;
     J.tall_y[pi] = Cc > K;
-    J.rx[pi] = (int)std::min(R, K);
-    J.ry[pi] = (int)std::min(Cc, K);
+    J.rx[pi] = J.rx0[pi] = (int)std::min(R, K);
+    J.ry[pi] = J.ry0[pi] = (int)std::min(Cc, K);
     J.o_gx[pi] = off;
     off += J.tall_x[pi] ? al(K * K) : 0;
     J.o_gy[pi] = off;
@@ -1136,8 +1137,8 @@ ftn_status cj_gram(CJob& J, GemmF64Batch& gb, std::vector<CholJob>& chol, int* f
   return FTN_OK;
 }
 
-// Householder TSQR jobs of the tall sides whose flag (index 2 * pi + side,
-// side 0 = X, 1 = Y) has bit 0 set, by tree level: level 0 factors
+// Householder TSQR jobs of the tall sides selected by flags (index 2 * pi +
+// side, side 0 = X, 1 = Y; bit 0), by tree level: level 0 factors
 // every chunk into its own slot; level l >= 1 merges slot c + 2^(l-1) into
 // slot c for every c that is a multiple of 2^l (the merged factor is upper
 // triangular, its zero prefix skipped).  levels[l] receives the jobs.
@@ -1306,140 +1307,153 @@ ftn_status compress_batch(ftn_ctx ctx, std::vector<CompressItem>& items) {
     }
   }
   // ---- 2b. nonzero rows of the R factors (one synchronisation for the counts
-  //      and flags); flagged sides factored again by Householder TSQR, one
-  //      launch per tree level, and compacted again (a second synchronisation) ----
-  {
-    std::vector<int> hc(8 * jobs.size(), 0);
-    auto compact = [&](bool flagged_only) -> ftn_status {
-      std::vector<CompactJob> cj;
-      for (size_t q = 0; q < jobs.size(); ++q) {
-        CJob& J = jobs[q];
-        for (int pi = 0; pi < 2; ++pi) {
-          const int K = (int)J.P->K[pi];
-          if (K == 0 || J.rx[pi] == 0 || J.ry[pi] == 0) continue;
-          if (!flagged_only || (hc[8 * q + 4 + 2 * pi] & 1))
-            cj.push_back({J.ws + J.rx_off[pi], J.ws + J.o_rxc[pi], cnt + 8 * q + 2 * pi, J.rx[pi], K, J.ldx[pi]});
-          if (!flagged_only || (hc[8 * q + 4 + 2 * pi + 1] & 1))
-            cj.push_back({J.ws + J.ry_off[pi], J.ws + J.o_ryc[pi], cnt + 8 * q + 2 * pi + 1, J.ry[pi], K, J.ldy[pi]});
-        }
-      }
-      if (!cj.empty()) {
-        DevBuf t_cj(ctx);
-        FTN_TRY(put_table(ctx, cj, &t_cj.p));
-        compact_rows_kernel<<<(unsigned)cj.size(), 256, 0, ctx->stream>>>((const CompactJob*)t_cj.p);
-        ctx->launches += 1;
-        FTN_CUDA(cudaGetLastError());
-      }
-      FTN_CUDA(cudaMemcpyAsync(hc.data(), cnt, hc.size() * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
-      FTN_CUDA(cudaStreamSynchronize(ctx->stream));
-      return FTN_OK;
-    };
-    FTN_TRY(compact(false));
-    // ---- residual test of the factors with dropped pivots (one more synchronisation) ----
-    {
-      std::vector<ResidTJob> rt[2];  // by variant: R^T in shared memory, in global memory
-      std::vector<SumSqJob> sq;
-      GemmF64Batch gb(ctx);
-      int kmax_sm = 0;
-      for (size_t q = 0; q < jobs.size(); ++q) {
-        CJob& J = jobs[q];
-        std::vector<GemmProb> eg;
-        for (int pi = 0; pi < 2; ++pi)
-          for (int side = 0; side < 2; ++side) {
-            const int f = hc[8 * q + 4 + 2 * pi + side];
-            if (f != 2) continue;  // only dropped pivots, none in the unresolved band
-            const int K = (int)J.P->K[pi];
-            const int64_t rows = side ? J.P->N[pi] : J.P->M[pi];
-            const int64_t src = side ? J.o_yf + J.P->bfoff[pi] : J.o_xf + J.P->afoff[pi];
-            const int64_t rf = side ? J.o_gy[pi] : J.o_gx[pi], tf = side ? J.o_ty[pi] : J.o_tx[pi];
-            const int64_t ef = side ? J.o_hy[pi] : J.o_hx[pi];
-            const int v = K <= RESID_SMEM_K ? 0 : 1;
-            if (!v) kmax_sm = std::max(kmax_sm, K);
-            for (int c0 = 0; c0 < K; c0 += 32) rt[v].push_back({J.ws + rf, J.ws + tf, K, c0});
-            GemmProb g = make_prob((int)rows, K, K, src, J.P->ldk[pi], 1, tf, 1, K);
-            gemm_plain_output(g, ef, K);
-            eg.push_back(g);
-            sq.push_back({J.ws + ef, rows * K, chk + 8 * q + 4 + 2 * pi + side});
-          }
-        if (!eg.empty()) FTN_TRY(add_gemm_set(gb, eg, J.ws, J.ws, J.ws, J.ws_n, J.ws_n, J.ws_n));
-      }
-      if (!sq.empty()) {
-        FTN_TRY(setup_qr_kernels());
-        for (int v = 0; v < 2; ++v) {
-          if (rt[v].empty()) continue;
-          DevBuf t_rt(ctx);
-          FTN_TRY(put_table(ctx, rt[v], &t_rt.p));
-          if (v == 0)
-            dropped_residual_kernel<true><<<(unsigned)rt[0].size(), 128,
-                                            ((size_t)kmax_sm * kmax_sm + 5 * (size_t)kmax_sm) * 8, ctx->stream>>>(
-                (const ResidTJob*)t_rt.p);
-          else
-            dropped_residual_kernel<false><<<(unsigned)rt[1].size(), 128, 0, ctx->stream>>>((const ResidTJob*)t_rt.p);
-          ctx->launches += 1;
-          FTN_CUDA(cudaGetLastError());
-        }
-        FTN_TRY(flush_gemm_f64(gb));
-        DevBuf t_sq(ctx);
-        FTN_TRY(put_table(ctx, sq, &t_sq.p));
-        sumsq_kernel<<<(unsigned)sq.size(), 256, 0, ctx->stream>>>((const SumSqJob*)t_sq.p);
-        ctx->launches += 1;
-        FTN_CUDA(cudaGetLastError());
-        std::vector<double> hk(chk_words);
-        FTN_CUDA(cudaMemcpyAsync(hk.data(), chk, chk_words * 8, cudaMemcpyDeviceToHost, ctx->stream));
-        FTN_CUDA(cudaStreamSynchronize(ctx->stream));
-        // the Gram factor stands when the dropped columns are within 1e-12 of the kept span
-        for (size_t q = 0; q < jobs.size(); ++q)
-          for (int k = 0; k < 4; ++k)
-            if (hc[8 * q + 4 + k] == 2 && !(hk[8 * q + 4 + k] <= 1e-24 * hk[8 * q + k])) hc[8 * q + 4 + k] |= 1;
+  //      and flags).  Sides with an unresolved pivot are factored again by
+  //      Householder TSQR (one launch per tree level) and compacted again.  The
+  //      residual test of the sides with dropped pivots is launched here and
+  //      read back with the singular values, the Gram factor used meanwhile; a
+  //      side that fails it is factored by TSQR and its job's cores decomposed
+  //      again. ----
+  std::vector<int> hc(8 * jobs.size(), 0);
+  // sel[4 q + 2 pi + side] != 0 selects a side (side 0 = X, 1 = Y)
+  auto compact = [&](const std::vector<int>& sel) -> ftn_status {
+    std::vector<CompactJob> cj;
+    for (size_t q = 0; q < jobs.size(); ++q) {
+      CJob& J = jobs[q];
+      for (int pi = 0; pi < 2; ++pi) {
+        const int K = (int)J.P->K[pi];
+        if (K == 0 || J.rx0[pi] == 0 || J.ry0[pi] == 0) continue;
+        if (sel[4 * q + 2 * pi])
+          cj.push_back({J.ws + J.rx_off[pi], J.ws + J.o_rxc[pi], cnt + 8 * q + 2 * pi, J.rx0[pi], K, J.ldx[pi]});
+        if (sel[4 * q + 2 * pi + 1])
+          cj.push_back({J.ws + J.ry_off[pi], J.ws + J.o_ryc[pi], cnt + 8 * q + 2 * pi + 1, J.ry0[pi], K, J.ldy[pi]});
       }
     }
+    if (!cj.empty()) {
+      DevBuf t_cj(ctx);
+      FTN_TRY(put_table(ctx, cj, &t_cj.p));
+      compact_rows_kernel<<<(unsigned)cj.size(), 256, 0, ctx->stream>>>((const CompactJob*)t_cj.p);
+      ctx->launches += 1;
+      FTN_CUDA(cudaGetLastError());
+    }
+    FTN_CUDA(cudaMemcpyAsync(hc.data(), cnt, hc.size() * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    FTN_CUDA(cudaStreamSynchronize(ctx->stream));
+    return FTN_OK;
+  };
+  // Householder TSQR of the selected (tall) sides into their slots, then their
+  // compaction (profile label: the unresolved band's, or the failed residual's)
+  auto tsqr = [&](const std::vector<int>& sel, const char* label) -> ftn_status {
     std::vector<std::vector<QrJob>> levels;
-    for (size_t q = 0; q < jobs.size(); ++q) cj_qr(jobs[q], levels, hc.data() + 8 * q + 4);
-    if (!levels.empty()) {
-      FTN_TRY(setup_qr_kernels());
-      for (auto& lv : levels) {
-        // three variants by bond width (one launch each): factor in shared
-        // memory, 32-row passes, 16-row passes
-        std::vector<QrJob> part[3];
-        for (const QrJob& qj : lv) part[qj.K <= QR_RSMEM_K ? 0 : qj.K <= QR_WIDE_K ? 1 : 2].push_back(qj);
-        for (int v = 0; v < 3; ++v) {
-          if (part[v].empty()) continue;
-          int kmax = 0;
-          for (const QrJob& qj : part[v]) kmax = std::max(kmax, qj.K);
-          DevBuf t_qr(ctx);
-          FTN_TRY(put_table(ctx, part[v], &t_qr.p));
-          const int rec = prof_begin(ctx, "householder_qr", 0, 0);
-          const unsigned g = (unsigned)part[v].size();
-          const QrJob* tj = (const QrJob*)t_qr.p;
-          if (v == 0)
-            qr_stream_kernel<QR_ROWS_WIDE, true><<<g, QR_THREADS, ((size_t)kmax * kmax + QR_ROWS_WIDE * kmax) * 8,
-                                                  ctx->stream>>>(tj);
-          else if (v == 1)
-            qr_stream_kernel<QR_ROWS_WIDE, false><<<g, QR_THREADS, (size_t)QR_ROWS_WIDE * kmax * 8, ctx->stream>>>(tj);
-          else
-            qr_stream_kernel<QR_ROWS, false><<<g, QR_THREADS, (size_t)QR_ROWS * kmax * 8, ctx->stream>>>(tj);
-          ctx->launches += 1;
-          FTN_CUDA(cudaGetLastError());
-          prof_end(ctx, rec);
-        }
+    for (size_t q = 0; q < jobs.size(); ++q) cj_qr(jobs[q], levels, sel.data() + 4 * q);
+    if (levels.empty()) return FTN_OK;
+    FTN_TRY(setup_qr_kernels());
+    for (auto& lv : levels) {
+      // three variants by bond width (one launch each): factor in shared
+      // memory, 32-row passes, 16-row passes
+      std::vector<QrJob> part[3];
+      for (const QrJob& qj : lv) part[qj.K <= QR_RSMEM_K ? 0 : qj.K <= QR_WIDE_K ? 1 : 2].push_back(qj);
+      for (int v = 0; v < 3; ++v) {
+        if (part[v].empty()) continue;
+        int kmax = 0;
+        for (const QrJob& qj : part[v]) kmax = std::max(kmax, qj.K);
+        DevBuf t_qr(ctx);
+        FTN_TRY(put_table(ctx, part[v], &t_qr.p));
+        const int rec = prof_begin(ctx, label, 0, 0);
+        const unsigned g = (unsigned)part[v].size();
+        const QrJob* tj = (const QrJob*)t_qr.p;
+        if (v == 0)
+          qr_stream_kernel<QR_ROWS_WIDE, true><<<g, QR_THREADS, ((size_t)kmax * kmax + QR_ROWS_WIDE * kmax) * 8,
+                                                ctx->stream>>>(tj);
+        else if (v == 1)
+          qr_stream_kernel<QR_ROWS_WIDE, false><<<g, QR_THREADS, (size_t)QR_ROWS_WIDE * kmax * 8, ctx->stream>>>(tj);
+        else
+          qr_stream_kernel<QR_ROWS, false><<<g, QR_THREADS, (size_t)QR_ROWS * kmax * 8, ctx->stream>>>(tj);
+        ctx->launches += 1;
+        FTN_CUDA(cudaGetLastError());
+        prof_end(ctx, rec);
       }
-      for (size_t q = 0; q < jobs.size(); ++q)
-        for (int pi = 0; pi < 2; ++pi) {
-          if (hc[8 * q + 4 + 2 * pi] & 1) jobs[q].rx_off[pi] = jobs[q].o_hx[pi];
-          if (hc[8 * q + 4 + 2 * pi + 1] & 1) jobs[q].ry_off[pi] = jobs[q].o_hy[pi];
-        }
-      FTN_TRY(compact(true));
     }
     for (size_t q = 0; q < jobs.size(); ++q) {
-      const int c4[4] = {hc[8 * q], hc[8 * q + 1], hc[8 * q + 2], hc[8 * q + 3]};
-      FTN_TRY(cj_counts(jobs[q], c4));
+      CJob& J = jobs[q];
+      for (int pi = 0; pi < 2; ++pi) {
+        const int K = (int)J.P->K[pi];
+        if (sel[4 * q + 2 * pi]) J.rx_off[pi] = J.o_hx[pi], J.ldx[pi] = K;
+        if (sel[4 * q + 2 * pi + 1]) J.ry_off[pi] = J.o_hy[pi], J.ldy[pi] = K;
+      }
+    }
+    return compact(sel);
+  };
+  // shapes of a job's cores from the row counts of its compacted factors
+  auto counts = [&](size_t q) -> ftn_status {
+    CJob& J = jobs[q];
+    for (int pi = 0; pi < 2; ++pi) J.rx[pi] = J.rx0[pi], J.ry[pi] = J.ry0[pi];
+    const int c4[4] = {hc[8 * q], hc[8 * q + 1], hc[8 * q + 2], hc[8 * q + 3]};
+    return cj_counts(J, c4);
+  };
+  FTN_TRY(compact(std::vector<int>(4 * jobs.size(), 1)));
+  {
+    std::vector<int> band(4 * jobs.size(), 0);
+    for (size_t q = 0; q < jobs.size(); ++q)
+      for (int k = 0; k < 4; ++k) band[4 * q + k] = hc[8 * q + 4 + k] & 1;
+    FTN_TRY(tsqr(band, "householder_qr"));
+  }
+  bool residual_pending = false;
+  {
+    std::vector<ResidTJob> rt[2];  // by variant: R^T in shared memory, in global memory
+    std::vector<SumSqJob> sq;
+    GemmF64Batch gb(ctx);
+    int kmax_sm = 0;
+    for (size_t q = 0; q < jobs.size(); ++q) {
+      CJob& J = jobs[q];
+      std::vector<GemmProb> eg;
+      for (int pi = 0; pi < 2; ++pi)
+        for (int side = 0; side < 2; ++side) {
+          if (hc[8 * q + 4 + 2 * pi + side] != 2) continue;  // dropped pivots only, none unresolved
+          const int K = (int)J.P->K[pi];
+          const int64_t rows = side ? J.P->N[pi] : J.P->M[pi];
+          const int64_t src = side ? J.o_yf + J.P->bfoff[pi] : J.o_xf + J.P->afoff[pi];
+          const int64_t rf = side ? J.o_gy[pi] : J.o_gx[pi], tf = side ? J.o_ty[pi] : J.o_tx[pi];
+          const int64_t ef = side ? J.o_hy[pi] : J.o_hx[pi];
+          const int v = K <= RESID_SMEM_K ? 0 : 1;
+          if (!v) kmax_sm = std::max(kmax_sm, K);
+          for (int c0 = 0; c0 < K; c0 += 32) rt[v].push_back({J.ws + rf, J.ws + tf, K, c0});
+          GemmProb g = make_prob((int)rows, K, K, src, J.P->ldk[pi], 1, tf, 1, K);
+          gemm_plain_output(g, ef, K);
+          eg.push_back(g);
+          sq.push_back({J.ws + ef, rows * K, chk + 8 * q + 4 + 2 * pi + side});
+        }
+      if (!eg.empty()) FTN_TRY(add_gemm_set(gb, eg, J.ws, J.ws, J.ws, J.ws_n, J.ws_n, J.ws_n));
+    }
+    if (!sq.empty()) {
+      FTN_TRY(setup_qr_kernels());
+      for (int v = 0; v < 2; ++v) {
+        if (rt[v].empty()) continue;
+        DevBuf t_rt(ctx);
+        FTN_TRY(put_table(ctx, rt[v], &t_rt.p));
+        if (v == 0)
+          dropped_residual_kernel<true><<<(unsigned)rt[0].size(), 128,
+                                          ((size_t)kmax_sm * kmax_sm + 5 * (size_t)kmax_sm) * 8, ctx->stream>>>(
+              (const ResidTJob*)t_rt.p);
+        else
+          dropped_residual_kernel<false><<<(unsigned)rt[1].size(), 128, 0, ctx->stream>>>((const ResidTJob*)t_rt.p);
+        ctx->launches += 1;
+        FTN_CUDA(cudaGetLastError());
+      }
+      FTN_TRY(flush_gemm_f64(gb));
+      DevBuf t_sq(ctx);
+      FTN_TRY(put_table(ctx, sq, &t_sq.p));
+      sumsq_kernel<<<(unsigned)sq.size(), 256, 0, ctx->stream>>>((const SumSqJob*)t_sq.p);
+      ctx->launches += 1;
+      FTN_CUDA(cudaGetLastError());
+      residual_pending = true;
     }
   }
+  for (size_t q = 0; q < jobs.size(); ++q) FTN_TRY(counts(q));
   // ---- 3. core M = R_X R_Y^T (stored with the rotated side as rows) and SVD ----
-  {
+  auto core_svd = [&](const std::vector<size_t>& which) -> ftn_status {
     GemmF64Batch gb(ctx);
     std::vector<SvdJob> svd;
-    for (CJob& J : jobs) {
+    for (size_t q : which) {
+      CJob& J = jobs[q];
       std::vector<GemmProb> mg;
       for (int pi = 0; pi < 2; ++pi) {
         const int K = (int)J.P->K[pi];
@@ -1456,60 +1470,86 @@ ftn_status compress_batch(ftn_ctx ctx, std::vector<CompressItem>& items) {
           g.cstr[0] = J.rx[pi];
         }
         mg.push_back(g);
-        double* s = sbuf + J.s_off[pi];
-        svd.push_back({J.ws + J.o_m[pi], J.ws + J.o_tf[pi], s, (int*)(s + J.nrot[pi]), J.nrot[pi], J.mlen[pi]});
+        double* sp = sbuf + J.s_off[pi];
+        svd.push_back({J.ws + J.o_m[pi], J.ws + J.o_tf[pi], sp, (int*)(sp + J.nrot[pi]), J.nrot[pi], J.mlen[pi]});
       }
       FTN_TRY(add_gemm_set(gb, mg, J.ws, J.ws, J.ws, J.ws_n, J.ws_n, J.ws_n));
     }
     FTN_TRY(flush_gemm_f64(gb));
-    if (!svd.empty()) {
-      // rows up to 32 * SVDC_MAX_E long whose cluster share fits in shared
-      // memory go to the cluster kernel (one launch; its arithmetic does not
-      // depend on the cluster size or row length it is launched with, so a
-      // decomposition does not depend on the other jobs of the batch), the
-      // others to the single-CTA one
-      const int cmax = svd_cluster_max(ctx);
-      std::vector<SvdJob> small, big;
-      int e_max = 1, c_use = 1;
-      for (const SvdJob& j : svd) {
-        const int np = j.n + (j.n & 1);
-        int c = 1;
-        while (c < cmax && c * SVDC_WARPS < np / 2) c *= 2;
-        while (c < cmax && (int64_t)((j.n + c - 1) / c) * j.m * 8 > SVDC_SMEM_BYTES) c *= 2;
-        if (j.m > 32 * SVDC_MAX_E || (int64_t)((j.n + c - 1) / c) * j.m * 8 > SVDC_SMEM_BYTES) {
-          big.push_back(j);
-          continue;
-        }
-        small.push_back(j);
-        c_use = std::max(c_use, c);
-        int e = 1;
-        while (32 * e < j.m) e *= 2;
-        e_max = std::max(e_max, e);
+    if (svd.empty()) return FTN_OK;
+    // rows up to 32 * SVDC_MAX_E long whose cluster share fits in shared
+    // memory go to the cluster kernel (one launch; its arithmetic does not
+    // depend on the cluster size or row length it is launched with, so a
+    // decomposition does not depend on the other jobs of the batch), the
+    // others to the single-CTA one
+    const int cmax = svd_cluster_max(ctx);
+    std::vector<SvdJob> small, big;
+    int e_max = 1, c_use = 1;
+    for (const SvdJob& j : svd) {
+      const int np = j.n + (j.n & 1);
+      int c = 1;
+      while (c < cmax && c * SVDC_WARPS < np / 2) c *= 2;
+      while (c < cmax && (int64_t)((j.n + c - 1) / c) * j.m * 8 > SVDC_SMEM_BYTES) c *= 2;
+      if (j.m > 32 * SVDC_MAX_E || (int64_t)((j.n + c - 1) / c) * j.m * 8 > SVDC_SMEM_BYTES) {
+        big.push_back(j);
+        continue;
       }
-      std::vector<SvdJob> all(small);
-      all.insert(all.end(), big.begin(), big.end());
-      DevBuf t_svd(ctx);
-      FTN_TRY(put_table(ctx, all, &t_svd.p));
-      const int rec = prof_begin(ctx, "svd_jacobi", 0, 0);
-      if (!small.empty()) {
-        size_t smem = 0;
-        for (const SvdJob& j : small) smem = std::max(smem, (size_t)((j.n + c_use - 1) / c_use) * j.m * 8);
-        FTN_TRY(launch_svd_cluster(ctx, (const SvdJob*)t_svd.p, (int)small.size(), c_use, e_max, smem));
-      }
-      if (!big.empty()) {
-        svd_rows_global_kernel<<<(unsigned)big.size(), LA_THREADS, 0, ctx->stream>>>((const SvdJob*)t_svd.p +
-                                                                                   small.size());
-        ctx->launches += 1;
-        FTN_CUDA(cudaGetLastError());
-      }
-      prof_end(ctx, rec);
+      small.push_back(j);
+      c_use = std::max(c_use, c);
+      int e = 1;
+      while (32 * e < j.m) e *= 2;
+      e_max = std::max(e_max, e);
     }
-  }
-  // ---- 4. pooled truncation (one synchronisation) ----
+    std::vector<SvdJob> all(small);
+    all.insert(all.end(), big.begin(), big.end());
+    DevBuf t_svd(ctx);
+    FTN_TRY(put_table(ctx, all, &t_svd.p));
+    const int rec = prof_begin(ctx, "svd_jacobi", 0, 0);
+    if (!small.empty()) {
+      size_t smem = 0;
+      for (const SvdJob& j : small) smem = std::max(smem, (size_t)((j.n + c_use - 1) / c_use) * j.m * 8);
+      FTN_TRY(launch_svd_cluster(ctx, (const SvdJob*)t_svd.p, (int)small.size(), c_use, e_max, smem));
+    }
+    if (!big.empty()) {
+      svd_rows_global_kernel<<<(unsigned)big.size(), LA_THREADS, 0, ctx->stream>>>((const SvdJob*)t_svd.p +
+                                                                                 small.size());
+      ctx->launches += 1;
+      FTN_CUDA(cudaGetLastError());
+    }
+    prof_end(ctx, rec);
+    return FTN_OK;
+  };
   {
-    std::vector<double> sv(s_total + 1);
+    std::vector<size_t> every(jobs.size());
+    for (size_t q = 0; q < jobs.size(); ++q) every[q] = q;
+    FTN_TRY(core_svd(every));
+  }
+  // ---- 4. pooled truncation (one synchronisation for the singular values and
+  //      the residual norms; a second only when a residual test failed) ----
+  {
+    std::vector<double> sv(s_total + 1), hk(chk_words);
     if (s_total) FTN_CUDA(cudaMemcpyAsync(sv.data(), sbuf, s_total * 8, cudaMemcpyDeviceToHost, ctx->stream));
+    if (residual_pending)
+      FTN_CUDA(cudaMemcpyAsync(hk.data(), chk, chk_words * 8, cudaMemcpyDeviceToHost, ctx->stream));
     FTN_CUDA(cudaStreamSynchronize(ctx->stream));
+    if (residual_pending) {
+      // the Gram factor stands when the dropped columns are within 1e-12 of the kept span
+      std::vector<int> fail(4 * jobs.size(), 0);
+      std::vector<size_t> redo;
+      for (size_t q = 0; q < jobs.size(); ++q) {
+        bool any = false;
+        for (int k = 0; k < 4; ++k)
+          if (hc[8 * q + 4 + k] == 2 && !(hk[8 * q + 4 + k] <= 1e-24 * hk[8 * q + k])) fail[4 * q + k] = 1, any = true;
+        if (any) redo.push_back(q);
+      }
+      if (!redo.empty()) {
+        FTN_TRY(tsqr(fail, "householder_qr_redo"));
+        for (size_t q : redo) FTN_TRY(counts(q));
+        FTN_TRY(core_svd(redo));
+        if (s_total) FTN_CUDA(cudaMemcpyAsync(sv.data(), sbuf, s_total * 8, cudaMemcpyDeviceToHost, ctx->stream));
+        FTN_CUDA(cudaStreamSynchronize(ctx->stream));
+      }
+    }
     for (CJob& J : jobs) cj_truncate(J, sv.data());
   }
   // ---- 5. projectors and the new tensors ----

@@ -492,26 +492,41 @@ def contract(ctx, tensors, bonds, tree, positions=None, policy="exact", chi=0, p
 
 
 def _network_arrays(networks):
-    """ctypes arrays of ftn_network / ftn_tree for a list of network dicts
-    (plus the buffers they point into, to be kept alive by the caller)."""
+    """ctypes arrays of ftn_network / ftn_tree for a list of network dicts.
+    The handles, bonds, trees and positions of all networks are packed into
+    one flat numpy table each (the structs point into them), so packing costs
+    a few vectorised copies rather than one Python conversion per integer.
+    Returns (count, networks, trees, keep) -- ``keep`` holds the tables."""
     nets = list(networks)
     n = len(nets)
-    keep = []
     net_arr = (Network * max(1, n))()
     tree_arr = (Tree * max(1, n))()
+    if n == 0:
+        return 0, net_arr, tree_arr, []
+
+    def flat(rows):
+        parts = [np.asarray(r, dtype=np.int32).reshape(-1) for r in rows]
+        offs = np.zeros(len(parts) + 1, dtype=np.int64)
+        np.cumsum([q.size for q in parts], out=offs[1:])
+        return np.concatenate(parts + [np.zeros(1, np.int32)]), offs
+
+    hs = np.array([t.handle.value for job in nets for t in job["tensors"]] + [0], dtype=np.uint64)
+    hoff = np.zeros(n + 1, dtype=np.int64)
+    np.cumsum([len(job["tensors"]) for job in nets], out=hoff[1:])
+    fb, boff = flat(job["bonds"] for job in nets)
+    ft, toff = flat(job["tree"] for job in nets)
+    fp, poff = flat((job.get("positions") or ()) for job in nets)
+    hp, bp, tp, pp = hs.ctypes.data, fb.ctypes.data, ft.ctypes.data, fp.ctypes.data
+    vpp, i32p = C.POINTER(C.c_void_p), C.POINTER(C.c_int32)
     for i, job in enumerate(nets):
-        tens = job["tensors"]
-        arr = (C.c_void_p * max(1, len(tens)))(*[t.handle.value for t in tens])
-        fb = _i32([int(v) for b in job["bonds"] for v in b])
-        ft = _i32([int(v) for p in job["tree"] for v in p])
         pos = job.get("positions")
-        fp = _i32(pos) if pos is not None else None
-        keep += [arr, fb, ft, fp]
-        net_arr[i] = Network(len(tens), C.cast(arr, C.POINTER(C.c_void_p)), len(job["bonds"]), fb, fp)
+        net_arr[i] = Network(len(job["tensors"]), C.cast(hp + 8 * int(hoff[i]), vpp), len(job["bonds"]),
+                             C.cast(bp + 4 * int(boff[i]), i32p),
+                             C.cast(pp + 4 * int(poff[i]), i32p) if pos is not None else None)
         pol = job.get("policy", "exact")
-        tree_arr[i] = Tree(len(job["tree"]), ft, POLICY_NAMES[pol] if isinstance(pol, str) else int(pol),
-                           int(job.get("chi", 0)))
-    return n, net_arr, tree_arr, keep
+        tree_arr[i] = Tree(len(job["tree"]), C.cast(tp + 4 * int(toff[i]), i32p),
+                           POLICY_NAMES[pol] if isinstance(pol, str) else int(pol), int(job.get("chi", 0)))
+    return n, net_arr, tree_arr, [hs, fb, ft, fp]
 
 
 def contract_batch(ctx, networks, prec="f64"):

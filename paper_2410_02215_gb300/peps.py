@@ -181,6 +181,8 @@ def cluster_networks(ctx, instances, t, u, policy="exact", chi=0, dtype=ftn.F64,
     hop = ftn.hubbard_term(ctx, 0, t, 0.0, dtype)
     onsite = ftn.hubbard_term(ctx, 1, 0.0, u, dtype)
     nets, group_end, keep = [], [], [hop, onsite]
+    by_content = {}  # gauge tensors by (weights, duality): equal weights share one tensor
+    keep.append(by_content)
     for layout, kets, cluster_fn, gauges in instances:
         bras = [ftn.dagger(ctx, k) for k in kets]
         cache = {}
@@ -189,7 +191,10 @@ def cluster_networks(ctx, instances, t, u, policy="exact", chi=0, dtype=ftn.F64,
             if (s, a) not in cache:
                 nb = layout["nbrs"][s][a]
                 lam = gauges[(min(s, nb), max(s, nb))]
-                cache[(s, a)] = gauge_tensor(ctx, lam[0], lam[1], kets[s].legs[a][2], dtype)
+                key = (tuple(map(float, lam[0])), tuple(map(float, lam[1])), kets[s].legs[a][2])
+                if key not in by_content:
+                    by_content[key] = gauge_tensor(ctx, lam[0], lam[1], key[2], dtype)
+                cache[(s, a)] = by_content[key]
             return cache[(s, a)]
 
         if terms is None:

@@ -295,3 +295,33 @@ def test_compress_qr_chunk_tails(F, ctx, rows_odd, k):
     got = O.contract(dense(xg), dense(yg), [1], [0])
     assert np.max(np.abs(got.data - ref.data)) <= 1e-10 * np.max(np.abs(ref.data))
     assert tuple(info.kept) == (k, k)
+
+
+@pytest.mark.parametrize("small,redo", [(1e-8, True), (1e-14, False)])
+def test_compress_gram_residual_decides(F, ctx, small, redo):
+    """Sector blocks with singular values 1 (x12) and ``small`` (x12): the
+    Gram matrix's pivots for the small directions are at rounding level, so the
+    semi-definite Cholesky drops them; the residual certificate |A T|_F then
+    decides.  At 1e-8 the dropped directions matter (|E|^2 ~ 1e-16 |A|^2 >
+    1e-24 |A|^2): the side is factored again by Householder TSQR and the job's
+    cores decomposed again.  At 1e-14 they are below the certificate's 1e-12
+    and the Gram factor stands.  Both against the oracle at 1e-10."""
+    lx = [(6, 6, 0), (5, 5, 1), (24, 24, 0)]
+    ly = [(24, 24, 1), (7, 7, 0), (6, 6, 1)]
+    spec = np.concatenate([np.ones(12), np.full(12, small)])
+    X = _graded_with_spectrum(lx, 0, False, {0: spec, 1: 0.7 * spec}, 11)
+    Y = O.embed_blocks(ly, 0, W.random_blocks(ly, 0, 13))
+    xr, yr, _ = O.compress(X, Y, [2], [0], 10**6)
+    ref = O.contract(xr, yr, [xr.rank - 1], [0])
+    x = F.Tensor.from_blocks(ctx, lx, 0, sorted(O.extract_blocks(X).items()))
+    y = F.Tensor.from_blocks(ctx, ly, 0, sorted(O.extract_blocks(Y).items()))
+    ctx.profile(True)
+    try:
+        xg, yg, _ = F.compress(ctx, x, y, [2], [0], 10**6)
+        labels = {r["label"]: r["launches"] for r in ctx.profile_read()}
+    finally:
+        ctx.profile(False)
+    got = O.contract(dense(xg), dense(yg), [xg.rank - 1], [0])
+    assert np.max(np.abs(got.data - ref.data)) <= 1e-10 * np.max(np.abs(ref.data))
+    assert labels.get("householder_qr", 0) == 0  # no pivot in the unresolved band
+    assert (labels.get("householder_qr_redo", 0) > 0) == redo
