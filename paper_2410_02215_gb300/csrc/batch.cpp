@@ -146,22 +146,35 @@ ftn_status flush_gemm_f64(GemmF64Batch& gb) {
   ftn_ctx ctx = gb.ctx;
   struct L {
     size_t off;
-    int n, bn;
+    int n, bn;  // bn 0: the warp kernel's launch (its items follow the problems at items_off)
     int64_t tiles;
     const char* base;
-    const std::vector<GemmF64Batch::Item>* v;
+    std::vector<const GemmF64Batch::Item*> v;
   };
-  // layout of the tables (one staging chunk), then the rebased copies
+  // tiled problems by tile width, then every small problem in one warp launch
   std::vector<L> launches;
-  size_t total = 0;
+  L small{0, 0, 0, 0, nullptr, {}};
   for (auto& kv : gb.by_bn) {
-    auto& v = kv.second;
-    if (v.empty()) continue;
-    const char* base = (const char*)v[0].a;
-    for (auto& it : v) base = std::min({base, (const char*)it.a, (const char*)it.b, (const char*)it.c});
-    launches.push_back({total, (int)v.size(), kv.first, 0, lowest256(base), &v});
-    total = al256(total + v.size() * sizeof(GemmProb));
+    L l{0, 0, kv.first, 0, nullptr, {}};
+    for (auto& it : kv.second) (f64w_small(it.g) ? small : l).v.push_back(&it);
+    if (!l.v.empty()) launches.push_back(std::move(l));
   }
+  if (!small.v.empty()) launches.push_back(std::move(small));
+  size_t total = 0;
+  for (L& l : launches) {
+    const char* base = (const char*)l.v[0]->a;
+    for (auto* it : l.v) base = std::min({base, (const char*)it->a, (const char*)it->b, (const char*)it->c});
+    l.base = lowest256(base);
+    l.n = (int)l.v.size();
+    l.off = total;
+    total = al256(total + l.v.size() * sizeof(GemmProb));
+  }
+  std::vector<WarpItem> witems;
+  for (L& l : launches)
+    if (l.bn == 0)
+      for (int i = 0; i < l.n; ++i) f64w_items(l.v[i]->g, i, witems);
+  const size_t items_off = total;
+  total = al256(total + witems.size() * sizeof(WarpItem));
   const int nred = (int)gb.red.size();
   const size_t red_off = total;
   const char *pb = nullptr, *cb = nullptr;
@@ -183,8 +196,8 @@ ftn_status flush_gemm_f64(GemmF64Batch& gb) {
   for (L& l : launches) {
     GemmProb* out = (GemmProb*)(h + l.off);
     int64_t tiles = 0;
-    for (size_t i = 0; i < l.v->size(); ++i) {
-      const auto& it = (*l.v)[i];
+    for (int i = 0; i < l.n; ++i) {
+      const auto& it = *l.v[i];
       const int64_t da = (const char*)it.a - l.base, db = (const char*)it.b - l.base, dc = (const char*)it.c - l.base;
       if ((da | db | dc) & 7) return set_error(FTN_EINVAL, "batched GEMM: buffer not 8-byte aligned");
       GemmProb& g = out[i];
@@ -193,11 +206,12 @@ ftn_status flush_gemm_f64(GemmF64Batch& gb) {
       g.b_off += db / 8;
       g.c_off += dc / 8;
       g.tile_begin = tiles;
-      tiles += (int64_t)g.tiles_m * g.tiles_n * (g.nsplit > 1 ? g.nsplit : 1);
+      if (l.bn) tiles += (int64_t)g.tiles_m * g.tiles_n * (g.nsplit > 1 ? g.nsplit : 1);
       fl += 2.0 * g.M * g.N * g.K;
     }
     l.tiles = tiles;
   }
+  if (!witems.empty()) std::memcpy(h + items_off, witems.data(), witems.size() * sizeof(WarpItem));
   int64_t red_total = 0;
   if (nred) {
     GemmProb* out = (GemmProb*)(h + red_off);
@@ -221,7 +235,12 @@ ftn_status flush_gemm_f64(GemmF64Batch& gb) {
   ftn_status st = FTN_OK;
   for (const L& l : launches) {
     const double* base = (const double*)l.base;
-    st = launch_gemm_f64(ctx, (const GemmProb*)(d + l.off), l.n, l.tiles, base, base, const_cast<double*>(base), l.bn);
+    if (l.bn)
+      st = launch_gemm_f64(ctx, (const GemmProb*)(d + l.off), l.n, l.tiles, base, base, const_cast<double*>(base),
+                           l.bn);
+    else
+      st = launch_gemm_f64_warp(ctx, (const GemmProb*)(d + l.off), (const WarpItem*)(d + items_off),
+                                (int)witems.size(), base, base, const_cast<double*>(base));
     if (st != FTN_OK) break;
   }
   if (st == FTN_OK && nred)

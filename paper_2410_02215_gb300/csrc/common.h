@@ -6,6 +6,8 @@
 
 #include <cstring>
 #include <map>
+#include <mutex>
+#include <unordered_map>
 #include <memory>
 #include <string>
 #include <vector>
@@ -183,6 +185,13 @@ struct ftn_ctx_s {
   // grow-only workspace arena (reused by every call on this context)
   void* ws = nullptr;
   size_t ws_bytes = 0;
+  // device blocks freed on this context, kept by size class for its later
+  // allocations (dev_alloc / dev_free); block_class maps every live or cached
+  // block to its class.  The lock covers frees from other host threads.
+  std::mutex cache_mu;
+  std::unordered_map<size_t, std::vector<void*>> free_blocks;
+  std::unordered_map<void*, size_t> block_class;
+  size_t cached_bytes = 0;
   // host buffer for the tables of batched launches (staging_begin)
   std::vector<uint8_t> stage;
   // per-launch profiling (ftn_ctx_profile)
@@ -226,6 +235,8 @@ ftn_status cuda_error(cudaError_t e, const char* where);
 size_t dtype_size(ftn_dtype d);
 void* dev_alloc(ftn_ctx ctx, size_t bytes);
 void dev_free(ftn_ctx ctx, void* p);
+// hands the context's cached free blocks back to the stream-ordered allocator
+void release_cached_blocks(ftn_ctx ctx);
 // Workspace of at least `bytes` (contents undefined), valid until the next
 // call that asks for workspace on the same context.
 void* workspace(ftn_ctx ctx, size_t bytes);
@@ -293,6 +304,34 @@ ftn_status launch_permute2(ftn_ctx ctx, const PermJob* d_jobs, int njobs, int64_
 ftn_status launch_gemm_f64(ftn_ctx ctx, const GemmProb* d_probs, int nprobs, int64_t tiles, const double* a,
                            const double* b, double* c, int bn);
 int f64_pick_bn(int max_n);
+// Small FP64 problems (at most F64W_MAX_MN outputs) run on a warp kernel
+// instead of the 64 x bn tiles: one warp per item of up to F64W_PASSES
+// passes, each pass 32 / g outputs with g lanes splitting K (g from the
+// problem's own K or split length only, so a problem's arithmetic never
+// depends on the launch it is part of).
+struct WarpItem {
+  int32_t prob;  // problem index in the launch's table
+  int32_t ks;    // split-K slice
+  int32_t e0;    // first output (row-major over M x N)
+  int32_t cnt;   // outputs of this item
+};
+constexpr int64_t F64W_MAX_MN = 4096;
+constexpr int F64W_PASSES = 8;
+inline bool f64w_small(const GemmProb& g) { return (int64_t)g.M * g.N <= F64W_MAX_MN; }
+// K lanes: the largest power of two <= 32 that leaves each lane >= 8 terms
+__host__ __device__ inline int f64w_klanes(int klen) {
+  int g = 1;
+  while (g < 32 && 16 * g <= klen) g *= 2;
+  return g;
+}
+// appends the items of problem `prob` (all its split slices)
+void f64w_items(const GemmProb& g, int prob, std::vector<WarpItem>& out);
+ftn_status launch_gemm_f64_warp(ftn_ctx ctx, const GemmProb* d_probs, const WarpItem* d_items, int nitems,
+                                const double* a, const double* b, double* c);
+// Partitions a planned FP64 problem list: tiled problems first (tile_begin
+// recounted, returned tile total in tiles), the small ones after them with
+// their items.  Returns the number of tiled problems.
+int partition_f64(std::vector<GemmProb>& probs, std::vector<WarpItem>& items, int64_t& tiles);
 // plain row-major output block (rows x cols, row stride ld) at c_off
 void gemm_plain_output(GemmProb& g, int64_t c_off, int64_t ld);
 // dst[e] = sum_s src[s * slab + e] for e < count (split-K reduction)

@@ -731,7 +731,7 @@ struct CompactJob {
 };
 
 // Packs the rows of an R factor that are not identically zero (rows of
-// dropped Cholesky pivots, or zero rows of a short matrix used as its own
+// dropped Cholesky pivots, or zero rows of a side used as its own
 // factor).  They add nothing to M = R_X R_Y^T, so leaving them out gives the
 // same nonzero singular triplets from a smaller core.  rows <= LA_MAX_DIM.
 __global__ void __launch_bounds__(256) compact_rows_kernel(const CompactJob* jobs) {
@@ -1020,10 +1020,23 @@ ftn_status cj_prepare(ftn_ctx ctx, CJob& J) {
   off += al(P->bf_elems);
   for (int pi = 0; pi < 2; ++pi) {
     const int64_t K = P->K[pi], R = P->M[pi], Cc = P->N[pi];
-    J.tall_x[pi] = R > K;
-    J.tall_y[pi] = Cc > K;
-    J.rx[pi] = J.rx0[pi] = (int)std::min(R, K);
-    J.ry[pi] = J.ry0[pi] = (int)std::min(Cc, K);
+    // A side is replaced by an R factor (K rows) only where that shrinks the
+    // core enough to pay for the factorisation: rows beyond what the
+    // compaction and the SVD take as rows (LA_MAX_DIM), or at least 5/4 K
+    // rows while the partner side has more than K/8 rows (the SVD rotates
+    // the shorter side, so a long side whose partner is short only lengthens
+    // the rotated rows).  Any other side is its own factor (A = I A): no
+    // rounding is added, and the core keeps the same nonzero singular triplets.
+    // A sector that is empty on either side contributes nothing.
+    auto factored = [&](int64_t rows, int64_t other) {
+      if (rows <= K || other == 0) return false;
+      if (rows > LA_MAX_DIM) return true;
+      return 4 * rows >= 5 * K && 8 * std::min(other, K) > K;
+    };
+    J.tall_x[pi] = factored(R, Cc);
+    J.tall_y[pi] = factored(Cc, R);
+    J.rx[pi] = J.rx0[pi] = (R == 0 || Cc == 0) ? 0 : (int)(J.tall_x[pi] ? K : R);
+    J.ry[pi] = J.ry0[pi] = (R == 0 || Cc == 0) ? 0 : (int)(J.tall_y[pi] ? K : Cc);
     J.o_gx[pi] = off;
     off += J.tall_x[pi] ? al(K * K) : 0;
     J.o_gy[pi] = off;

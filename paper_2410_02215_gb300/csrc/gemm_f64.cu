@@ -1,8 +1,9 @@
 // Grouped FP64 sector GEMM (plain FP64 path): C[m, n] = sum_k A[m, k] B[n, k]
 // for every (row block, column block) pair of a fermionic contraction, both
 // operands K-major in the fused sector-matrix layout.  tcgen05 has no FP64
-// kind, so this is a DFMA kernel: 64x64 tiles, 4x4 outputs per thread,
-// persistent grid over the flattened tile list of all problems.
+// kind, so these are DFMA kernels: 64 x bn tiles with 4 x (bn / 16) outputs
+// per thread over a persistent grid for problems of more than 4096 outputs,
+// one warp per group of outputs for the smaller ones.
 #include <algorithm>
 
 #include "common.h"
@@ -112,6 +113,103 @@ __global__ void __launch_bounds__(256) gemm_f64_kernel(const GemmProb* __restric
 }
 
 int f64_pick_bn(int max_n) { return max_n <= 16 ? 16 : max_n <= 32 ? 32 : 64; }
+
+// Small problems: one warp per item.  A pass gives each group of g lanes one
+// output (m, n) = (e / N, e % N); lane kl of the group sums the terms k = kl,
+// kl + g, ... of its split slice into four accumulators (k mod 4g), adds them
+// pairwise, and the group's partial sums are added by a butterfly over the g
+// lanes.  Operands are read straight from global memory (L1-cached): FP64
+// arithmetic, not load bandwidth, bounds this path, and the many resident
+// warps hide the load latency that a 64 x bn tile per CTA cannot.
+__global__ void __launch_bounds__(128, 8) gemm_f64_warp_kernel(const GemmProb* __restrict__ probs,
+                                                            const WarpItem* __restrict__ items, int nitems,
+                                                            const double* __restrict__ A,
+                                                            const double* __restrict__ B, double* __restrict__ C) {
+  const int lane = threadIdx.x & 31;
+  const int nw = (int)((gridDim.x * blockDim.x) >> 5);
+  for (int w = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5); w < nitems; w += nw) {
+    const WarpItem it = items[w];
+    const GemmProb* __restrict__ p = probs + it.prob;
+    const int N = p->N, K = p->K;
+    const int nsp = p->nsplit > 1 ? p->nsplit : 1;
+    const int kbeg = nsp > 1 ? it.ks * p->kchunk : 0;
+    const int kend = nsp > 1 ? min(K, kbeg + p->kchunk) : K;
+    const int g = f64w_klanes(nsp > 1 ? p->kchunk : K);
+    const int lg = __ffs(g) - 1, opp = 32 >> lg;
+    const int o = lane >> lg, kl = lane & (g - 1);
+    const double* __restrict__ Ap = A + p->a_off;
+    const double* __restrict__ Bp = B + p->b_off;
+    const int64_t a_sm = p->a_sm, a_sk = p->a_sk, b_sn = p->b_sn, b_sk = p->b_sk;
+    const int64_t cbase = p->c_off + (int64_t)it.ks * p->c_slab;
+    const double sg = (double)p->c_sign;
+    const int npass = (it.cnt + opp - 1) / opp;
+    for (int q = 0; q < npass; ++q) {
+      const int le = q * opp + o;
+      const bool valid = le < it.cnt;
+      const int e = it.e0 + (valid ? le : 0);
+      const int m = e / N, n = e - m * N;
+      double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+      if (valid) {
+        const double* ar = Ap + (int64_t)m * a_sm;
+        const double* br = Bp + (int64_t)n * b_sn;
+        int k = kbeg + kl;
+        for (; k + 3 * g < kend; k += 4 * g) {
+          s0 = fma(ar[(int64_t)k * a_sk], br[(int64_t)k * b_sk], s0);
+          s1 = fma(ar[(int64_t)(k + g) * a_sk], br[(int64_t)(k + g) * b_sk], s1);
+          s2 = fma(ar[(int64_t)(k + 2 * g) * a_sk], br[(int64_t)(k + 2 * g) * b_sk], s2);
+          s3 = fma(ar[(int64_t)(k + 3 * g) * a_sk], br[(int64_t)(k + 3 * g) * b_sk], s3);
+        }
+        if (k < kend) s0 = fma(ar[(int64_t)k * a_sk], br[(int64_t)k * b_sk], s0);
+        if (k + g < kend) s1 = fma(ar[(int64_t)(k + g) * a_sk], br[(int64_t)(k + g) * b_sk], s1);
+        if (k + 2 * g < kend) s2 = fma(ar[(int64_t)(k + 2 * g) * a_sk], br[(int64_t)(k + 2 * g) * b_sk], s2);
+      }
+      double acc = (s0 + s1) + (s2 + s3);
+      for (int off = 1; off < g; off <<= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+      if (valid && kl == 0)
+        C[cbase + expand_index32(m, p->nrl, p->rdim, p->rstr) + expand_index32(n, p->ncl, p->cdim, p->cstr)] =
+            sg * acc;
+    }
+  }
+}
+
+void f64w_items(const GemmProb& g, int prob, std::vector<WarpItem>& out) {
+  const int nsp = g.nsplit > 1 ? g.nsplit : 1;
+  const int per = (32 / f64w_klanes(nsp > 1 ? g.kchunk : g.K)) * F64W_PASSES;
+  const int64_t mn = (int64_t)g.M * g.N;
+  for (int s = 0; s < nsp; ++s)
+    for (int64_t e = 0; e < mn; e += per) out.push_back({prob, s, (int32_t)e, (int32_t)std::min<int64_t>(per, mn - e)});
+}
+
+int partition_f64(std::vector<GemmProb>& probs, std::vector<WarpItem>& items, int64_t& tiles) {
+  std::stable_partition(probs.begin(), probs.end(), [](const GemmProb& g) { return !f64w_small(g); });
+  items.clear();
+  tiles = 0;
+  int nt = 0;
+  for (size_t i = 0; i < probs.size(); ++i) {
+    GemmProb& g = probs[i];
+    if (f64w_small(g)) {
+      f64w_items(g, (int)i, items);
+      continue;
+    }
+    g.tile_begin = tiles;
+    tiles += (int64_t)g.tiles_m * g.tiles_n * (g.nsplit > 1 ? g.nsplit : 1);
+    ++nt;
+  }
+  return nt;
+}
+
+ftn_status launch_gemm_f64_warp(ftn_ctx ctx, const GemmProb* d_probs, const WarpItem* d_items, int nitems,
+                                const double* a, const double* b, double* c) {
+  if (nitems == 0) return FTN_OK;
+  int64_t grid = ((int64_t)nitems + 3) / 4;
+  const int64_t cap = (int64_t)ctx->num_sms * 8;  // resident CTAs (64 registers, 128 threads)
+  if (grid > cap) grid = cap;
+  gemm_f64_warp_kernel<<<(unsigned)grid, 128, 0, ctx->stream>>>(d_probs, d_items, nitems, a, b, c);
+  ctx->launches += 1;
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_error(e, "gemm_f64_warp_kernel launch");
+  return FTN_OK;
+}
 
 __global__ void sum_slabs_kernel(double* __restrict__ dst, const double* __restrict__ src, int64_t count, int nsplit,
                                  int64_t slab) {

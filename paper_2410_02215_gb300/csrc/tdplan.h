@@ -58,6 +58,10 @@ struct TdPlan {
   bool fused = true;           // the GEMM epilogue writes the final layout
   std::vector<GemmProb> probs;
   int64_t gemm_tiles = 0;
+  // FP64: probs[0, n_tiled) run on the tiled kernel, the rest (small
+  // problems) on the warp kernel through witems
+  int n_tiled = 0;
+  std::vector<WarpItem> witems;
   // FP64 split-K (few output tiles): partial slabs and their reduction
   std::vector<GemmProb> red;
   int64_t part_elems = 0, red_total = 0;
@@ -80,6 +84,7 @@ struct TdPlan {
   bool tile_tab = false;
   GemmProb* d_probs = nullptr;
   GemmProb* d_red = nullptr;
+  WarpItem* d_witems = nullptr;
 };
 
 // The cached plan of a contraction (built on first use; *fresh, when given,

@@ -20,20 +20,86 @@ ftn_status cuda_error(cudaError_t e, const char* where) {
 
 size_t dtype_size(ftn_dtype d) { return d == FTN_F64 ? 8 : 4; }
 
+// Device memory of a context without a caller allocator: blocks from the
+// stream-ordered allocator on the context's stream, rounded to a size class
+// (256-byte steps up to 4 KB, then four classes per power of two) and, once
+// freed, kept for the context's later allocations of the same class.  All of
+// a context's work is ordered on its stream, so a block freed after the
+// launches that use it and handed out again to launches enqueued later is
+// never used by both at once (the guarantee cudaFreeAsync and
+// cudaMallocAsync give on one stream); the driver's allocator, whose calls
+// serialise when several host threads drive contexts, is left out of the
+// steady state.  Cached free blocks beyond CACHE_LIMIT go back to it.
+namespace {
+constexpr size_t CACHE_LIMIT = (size_t)2 << 30;
+
+size_t size_class(size_t b) {
+  if (b <= 4096) return (b + 255) & ~(size_t)255;
+  int e = 63;
+  while (!((b - 1) >> e)) --e;  // 2^e <= b - 1 < 2^(e + 1)
+  const size_t step = (size_t)1 << (e - 2);
+  return (b + step - 1) & ~(step - 1);
+}
+}  // namespace
+
 void* dev_alloc(ftn_ctx ctx, size_t bytes) {
   if (bytes == 0) bytes = 256;
   if (ctx->alloc) return ctx->alloc(bytes, ctx->user);
+  const size_t cls = size_class(bytes);
+  {
+    std::lock_guard<std::mutex> lock(ctx->cache_mu);
+    auto it = ctx->free_blocks.find(cls);
+    if (it != ctx->free_blocks.end() && !it->second.empty()) {
+      void* p = it->second.back();
+      it->second.pop_back();
+      ctx->cached_bytes -= cls;
+      return p;
+    }
+  }
   void* p = nullptr;
-  if (cudaMallocAsync(&p, bytes, ctx->stream) != cudaSuccess) return nullptr;
+  if (cudaMallocAsync(&p, cls, ctx->stream) != cudaSuccess) {
+    cudaGetLastError();
+    release_cached_blocks(ctx);  // one retry with the cache handed back
+    if (cudaMallocAsync(&p, cls, ctx->stream) != cudaSuccess) return nullptr;
+  }
+  std::lock_guard<std::mutex> lock(ctx->cache_mu);
+  ctx->block_class[p] = cls;
   return p;
 }
 
 void dev_free(ftn_ctx ctx, void* p) {
   if (!p) return;
-  if (ctx->free_fn)
+  if (ctx->free_fn) {
     ctx->free_fn(p, ctx->user);
-  else
+    return;
+  }
+  std::unique_lock<std::mutex> lock(ctx->cache_mu);
+  auto it = ctx->block_class.find(p);
+  if (it == ctx->block_class.end()) {  // not from dev_alloc (cannot happen): plain stream-ordered free
+    lock.unlock();
     cudaFreeAsync(p, ctx->stream);
+    return;
+  }
+  const size_t cls = it->second;
+  if (ctx->cached_bytes + cls > CACHE_LIMIT) {
+    ctx->block_class.erase(it);
+    lock.unlock();
+    cudaFreeAsync(p, ctx->stream);
+    return;
+  }
+  ctx->free_blocks[cls].push_back(p);
+  ctx->cached_bytes += cls;
+}
+
+void release_cached_blocks(ftn_ctx ctx) {
+  std::lock_guard<std::mutex> lock(ctx->cache_mu);
+  for (auto& kv : ctx->free_blocks)
+    for (void* p : kv.second) {
+      ctx->block_class.erase(p);
+      cudaFreeAsync(p, ctx->stream);
+    }
+  ctx->free_blocks.clear();
+  ctx->cached_bytes = 0;
 }
 
 void* workspace(ftn_ctx ctx, size_t bytes) {
@@ -450,6 +516,7 @@ ftn_status ftn_ctx_destroy(ftn_ctx ctx) {
   clear_plan_caches(ctx);
   dev_free(ctx, ctx->ws);
   dev_free(ctx, ctx->dev_err);
+  release_cached_blocks(ctx);
   cudaStreamSynchronize(ctx->stream);
   delete ctx;
   return FTN_OK;
@@ -457,6 +524,8 @@ ftn_status ftn_ctx_destroy(ftn_ctx ctx) {
 
 ftn_status ftn_ctx_set_stream(ftn_ctx ctx, void* cuda_stream) {
   if (!ctx) return set_error(FTN_EINVAL, "null ctx");
+  // cached blocks were freed in the old stream's order: let it finish first
+  if ((cudaStream_t)cuda_stream != ctx->stream) FTN_CUDA(cudaStreamSynchronize(ctx->stream));
   ctx->stream = (cudaStream_t)cuda_stream;
   return FTN_OK;
 }

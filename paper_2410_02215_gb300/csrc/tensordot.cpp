@@ -82,10 +82,10 @@ bool probs_in_bounds(const std::vector<GemmProb>& probs, int64_t a_n, int64_t b_
 static ftn_status upload_plan(ftn_ctx ctx, TdPlan& P) {
   size_t sa = P.ja.size() * sizeof(PermJob), sb = P.jb.size() * sizeof(PermJob), sc = P.jc.size() * sizeof(PermJob),
          sp = P.probs.size() * sizeof(GemmProb), sr = P.red.size() * sizeof(GemmProb),
-         sm = P.jab.size() * sizeof(PermJob);
-  const size_t pre = (sa + sb + sc + sp + sr + sm + 255) & ~(size_t)255;
+         sm = P.jab.size() * sizeof(PermJob), sw = P.witems.size() * sizeof(WarpItem);
+  const size_t pre = (sa + sb + sc + sp + sr + sm + sw + 255) & ~(size_t)255;
   const size_t st = P.tile_tab ? (size_t)P.gemm_tiles * sizeof(TileEnt) : 0;
-  size_t tot = sa + sb + sc + sp + sr + sm;
+  size_t tot = sa + sb + sc + sp + sr + sm + sw;
   std::vector<uint8_t> host(tot + 16);
   std::memcpy(host.data(), P.ja.data(), sa);
   std::memcpy(host.data() + sa, P.jb.data(), sb);
@@ -93,6 +93,7 @@ static ftn_status upload_plan(ftn_ctx ctx, TdPlan& P) {
   std::memcpy(host.data() + sa + sb + sc, P.probs.data(), sp);
   if (sr) std::memcpy(host.data() + sa + sb + sc + sp, P.red.data(), sr);
   if (sm) std::memcpy(host.data() + sa + sb + sc + sp + sr, P.jab.data(), sm);
+  if (sw) std::memcpy(host.data() + sa + sb + sc + sp + sr + sm, P.witems.data(), sw);
   P.dev = std::make_shared<DevTables>();
   P.dev->ctx = ctx;
   void* d = nullptr;
@@ -112,6 +113,7 @@ static ftn_status upload_plan(ftn_ctx ctx, TdPlan& P) {
   P.d_probs = (GemmProb*)(b + sa + sb + sc);
   P.d_red = sr ? (GemmProb*)(b + sa + sb + sc + sp) : nullptr;
   P.d_jab = sm ? (PermJob*)(b + sa + sb + sc + sp + sr) : nullptr;
+  P.d_witems = sw ? (WarpItem*)(b + sa + sb + sc + sp + sr + sm) : nullptr;
   if (st) {
     P.d_tt = (TileEnt*)(b + pre);
     FTN_TRY(tc_tile_table(ctx, P.d_probs, (int)P.probs.size(), P.gemm_tiles, P.bn, P.d_tt));
@@ -495,6 +497,7 @@ static ftn_status build_plan(ftn_ctx ctx, const ftn_tensor_s* A, const ftn_tenso
       P->gemm_tiles += (int64_t)g.tiles_m * g.tiles_n;
     }
     P->part_elems = plan_splitk_f64(P->probs, ctx->num_sms, P->red, P->gemm_tiles, P->red_total);
+    P->n_tiled = partition_f64(P->probs, P->witems, P->gemm_tiles);
   }
   // ---- the separate sign-permute of the result, when not fused ----
   if (!fuse) {
@@ -670,16 +673,14 @@ static ftn_status run_plan(ftn_ctx ctx, TdPlan& Pl, const ftn_tensor_s* A, const
     gb += (double)P->tmp_numel * in_es;
     if (!tc) {
       rec = prof_begin(ctx, "gemm_f64", gb, gemm_flops);
-      if (P->part_elems) {
-        double* part = (double*)(ws + need - p_b);
-        st = launch_gemm_f64(ctx, P->d_probs, (int)P->probs.size(), P->gemm_tiles, (const double*)af_hi,
-                             (const double*)bf_hi, part, P->bn);
-        if (st == FTN_OK)
-          st = launch_splitk_reduce(ctx, P->d_red, (int)P->red.size(), P->red_total, part, (double*)ctmp);
-      } else {
-        st = launch_gemm_f64(ctx, P->d_probs, (int)P->probs.size(), P->gemm_tiles, (const double*)af_hi,
-                             (const double*)bf_hi, (double*)ctmp, P->bn);
-      }
+      double* dst = P->part_elems ? (double*)(ws + need - p_b) : (double*)ctmp;
+      st = launch_gemm_f64(ctx, P->d_probs, P->n_tiled, P->gemm_tiles, (const double*)af_hi, (const double*)bf_hi, dst,
+                           P->bn);
+      if (st == FTN_OK)
+        st = launch_gemm_f64_warp(ctx, P->d_probs, P->d_witems, (int)P->witems.size(), (const double*)af_hi,
+                                  (const double*)bf_hi, dst);
+      if (st == FTN_OK && P->part_elems)
+        st = launch_splitk_reduce(ctx, P->d_red, (int)P->red.size(), P->red_total, dst, (double*)ctmp);
       prof_end(ctx, rec);
     } else {
       TcOperands ops;

@@ -278,23 +278,60 @@ def test_compress_ill_conditioned(F, ctx, kind, chi, other, px):
 
 
 @pytest.mark.parametrize("rows_odd,k", [(260, 128), (264, 128), (268, 128), (270, 128), (256, 128), (260, 64),
-                                         (129, 128)])
+                                         (161, 128)])
 def test_compress_qr_chunk_tails(F, ctx, rows_odd, k):
-    """The Householder QR splits a tall sector into chunks of 2K rows and
-    merges their factors: last chunks of 4, 8, 12 and 14 rows (after whose
+    """The Householder QR splits a tall sector into chunks of at least K rows
+    and merges their factors: last chunks of 4, 8, 12 and 14 rows (after whose
     rank the leftover rounding noise shrinks towards underflow), one chunk,
-    three chunks, and one row more than the bond."""
+    two chunks, and the shortest side still factored (5/4 K rows).  The
+    odd-parity sector of X has singular values over 1 ... 1e-10, so its Gram
+    factor has pivots in the unresolved band and the side goes to the
+    Householder QR (checked through the profile labels)."""
     lx = [(300, rows_odd, 0), (k, k, 1)]
     ly = [(k, k, 0), (280, 270, 1)]
-    bx, by = W.random_blocks(lx, 0, 41), W.random_blocks(ly, 0, 42)
+    bx, by = dict(W.random_blocks(lx, 0, 41)), W.random_blocks(ly, 0, 42)
+    g = W.rng(43)
+    u = np.linalg.qr(g.standard_normal((rows_odd, k)))[0]
+    v = np.linalg.qr(g.standard_normal((k, k)))[0]
+    bx[(1, 1)] = (u * np.logspace(0, -10, k)) @ v.T
+    bx = sorted(bx.items())
     X, Y = O.embed_blocks(lx, 0, bx), O.embed_blocks(ly, 0, by)
     xr, yr, info_r = O.compress(X, Y, [1], [0], 10**6)
     ref = O.contract(xr, yr, [1], [0])
-    xg, yg, info = F.compress(ctx, F.Tensor.from_blocks(ctx, lx, 0, bx), F.Tensor.from_blocks(ctx, ly, 0, by), [1],
-                              [0], 10**6)
+    ctx.profile(True)
+    try:
+        xg, yg, info = F.compress(ctx, F.Tensor.from_blocks(ctx, lx, 0, bx), F.Tensor.from_blocks(ctx, ly, 0, by),
+                                  [1], [0], 10**6)
+        labels = {r["label"]: r["launches"] for r in ctx.profile_read()}
+    finally:
+        ctx.profile(False)
     got = O.contract(dense(xg), dense(yg), [1], [0])
     assert np.max(np.abs(got.data - ref.data)) <= 1e-10 * np.max(np.abs(ref.data))
-    assert tuple(info.kept) == (k, k)
+    assert tuple(info.kept) == tuple(info_r["kept"])
+    assert labels.get("householder_qr", 0) > 0
+
+
+@pytest.mark.parametrize("rows,other", [(139, 128), (400, 12), (128, 128), (1100, 12)])
+def test_compress_side_as_own_factor(F, ctx, rows, other):
+    """Sides that are not factored: fewer than 5/4 K rows (139 x 128), or a
+    partner side of at most K/8 rows (400 x 128 against 12 rows), are their own
+    R factor; a side beyond 1024 rows is factored whatever its partner.  Each
+    against the oracle at 1e-10 with chi above the rank, and with chi = 7."""
+    k = 128
+    lx = [(rows, rows, 0), (k, k, 1)]
+    ly = [(k, k, 0), (other, other, 1)]
+    bx, by = W.random_blocks(lx, 0, 51), W.random_blocks(ly, 0, 52)
+    X, Y = O.embed_blocks(lx, 0, bx), O.embed_blocks(ly, 0, by)
+    for chi in (10**6, 7):
+        xr, yr, info_r = O.compress(X, Y, [1], [0], chi)
+        ref = O.contract(xr, yr, [1], [0])
+        xg, yg, info = F.compress(ctx, F.Tensor.from_blocks(ctx, lx, 0, bx), F.Tensor.from_blocks(ctx, ly, 0, by),
+                                  [1], [0], chi)
+        if info_r["gap"] is not None:  # a cut decided by more than rounding
+            assert info_r["gap"] > 1e-6 * info_r["singular_values"][0]
+        got = O.contract(dense(xg), dense(yg), [1], [0])
+        assert np.max(np.abs(got.data - ref.data)) <= 1e-10 * np.max(np.abs(ref.data))
+        assert tuple(info.kept) == tuple(info_r["kept"])
 
 
 @pytest.mark.parametrize("small,redo", [(1e-8, True), (1e-14, False)])
