@@ -869,13 +869,13 @@ def run_ours(args, rank, world, local):
     if not args.no_e2e:
         result["e2e"] = e2e_run(F, ctx, torch, cases, args.prec, max(4, min(args.steps, 10)), flops_step)
     if not args.no_cluster:
-        result["cluster"] = cluster_bench(F, ctx, torch, args.cluster_graphs, args.energy_streams,
+        result["cluster"] = cluster_bench(F, ctx, torch, args.cluster_graphs, args.cluster_streams,
                                           rank == 0 and world == 1 and not args.no_cpu)
     if not args.no_energy:
         result["energy"] = energy_bench(F, ctx, args.energy_evals, rank == 0 and world == 1 and not args.no_cpu,
                                         args.energy_streams)
     if not args.no_diamond:
-        result["energy_diamond"] = diamond_bench(F, ctx, torch, args.diamond_evals, args.energy_streams,
+        result["energy_diamond"] = diamond_bench(F, ctx, torch, args.diamond_evals, args.cluster_streams,
                                                  rank == 0 and world == 1 and not args.no_cpu, rank, world)
     if rank == 0 and world == 1 and not args.no_cpu:
         result["cpu_baseline"] = cpu_baseline(cases)
@@ -904,6 +904,8 @@ def main():
     ap.add_argument("--no-tune", action="store_true",
                     help="keep every plan's default GEMM tile width (for profiler runs, whose timings mislead the tuner)")
     ap.add_argument("--cluster-graphs", type=int, default=64)
+    ap.add_argument("--cluster-streams", type=int, default=16,
+                    help="contexts (one stream and host thread each) of the cluster-approximation workloads")
     ap.add_argument("--energy-evals", type=int, default=3)
     ap.add_argument("--energy-streams", type=int, default=8,
                     help="contexts (CUDA streams) that run an evaluation's contractions concurrently")

@@ -316,7 +316,7 @@ struct WarpItem {
   int32_t cnt;   // outputs of this item
 };
 constexpr int64_t F64W_MAX_MN = 4096;
-constexpr int F64W_PASSES = 8;
+constexpr int F64W_PASSES = 4;
 inline bool f64w_small(const GemmProb& g) { return (int64_t)g.M * g.N <= F64W_MAX_MN; }
 // K lanes: the largest power of two <= 32 that leaves each lane >= 8 terms
 __host__ __device__ inline int f64w_klanes(int klen) {

@@ -114,17 +114,18 @@ __global__ void __launch_bounds__(256) gemm_f64_kernel(const GemmProb* __restric
 
 int f64_pick_bn(int max_n) { return max_n <= 16 ? 16 : max_n <= 32 ? 32 : 64; }
 
-// Small problems: one warp per item.  A pass gives each group of g lanes one
-// output (m, n) = (e / N, e % N); lane kl of the group sums the terms k = kl,
-// kl + g, ... of its split slice into four accumulators (k mod 4g), adds them
-// pairwise, and the group's partial sums are added by a butterfly over the g
-// lanes.  Operands are read straight from global memory (L1-cached): FP64
-// arithmetic, not load bandwidth, bounds this path, and the many resident
-// warps hide the load latency that a 64 x bn tile per CTA cannot.
-__global__ void __launch_bounds__(128, 8) gemm_f64_warp_kernel(const GemmProb* __restrict__ probs,
-                                                            const WarpItem* __restrict__ items, int nitems,
-                                                            const double* __restrict__ A,
-                                                            const double* __restrict__ B, double* __restrict__ C) {
+// Small problems: one warp per item of up to F64W_PASSES passes.  Pass q
+// gives each group of g lanes one output (m, n) = (e / N, e % N); the item's
+// passes run together, so the loads of all its outputs are in flight at once
+// (the operands come straight from global memory, L1-cached: latency, not
+// bandwidth or FP64 rate, bounds these short dot products).  Lane kl of a
+// group sums the terms k = kl, kl + g, ... of its split slice in order, and
+// the group's partial sums are added by a butterfly over the g lanes.
+__global__ void __launch_bounds__(128, 6) gemm_f64_warp_kernel(const GemmProb* __restrict__ probs,
+                                                               const WarpItem* __restrict__ items, int nitems,
+                                                               const double* __restrict__ A,
+                                                               const double* __restrict__ B, double* __restrict__ C) {
+  constexpr int P = F64W_PASSES;
   const int lane = threadIdx.x & 31;
   const int nw = (int)((gridDim.x * blockDim.x) >> 5);
   for (int w = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5); w < nitems; w += nw) {
@@ -137,37 +138,37 @@ __global__ void __launch_bounds__(128, 8) gemm_f64_warp_kernel(const GemmProb* _
     const int g = f64w_klanes(nsp > 1 ? p->kchunk : K);
     const int lg = __ffs(g) - 1, opp = 32 >> lg;
     const int o = lane >> lg, kl = lane & (g - 1);
-    const double* __restrict__ Ap = A + p->a_off;
-    const double* __restrict__ Bp = B + p->b_off;
     const int64_t a_sm = p->a_sm, a_sk = p->a_sk, b_sn = p->b_sn, b_sk = p->b_sk;
+    const double* ar[P];
+    const double* br[P];
+    bool vq[P];
+    double s[P];
+#pragma unroll
+    for (int q = 0; q < P; ++q) {
+      const int le = q * opp + o;
+      vq[q] = le < it.cnt;
+      const int e = it.e0 + (vq[q] ? le : 0);
+      const int m = e / N;
+      ar[q] = A + p->a_off + (int64_t)m * a_sm;
+      br[q] = B + p->b_off + (int64_t)(e - m * N) * b_sn;
+      s[q] = 0.0;
+    }
+    for (int k = kbeg + kl; k < kend; k += g) {
+#pragma unroll
+      for (int q = 0; q < P; ++q)
+        if (vq[q]) s[q] = fma(ar[q][(int64_t)k * a_sk], br[q][(int64_t)k * b_sk], s[q]);
+    }
     const int64_t cbase = p->c_off + (int64_t)it.ks * p->c_slab;
     const double sg = (double)p->c_sign;
-    const int npass = (it.cnt + opp - 1) / opp;
-    for (int q = 0; q < npass; ++q) {
-      const int le = q * opp + o;
-      const bool valid = le < it.cnt;
-      const int e = it.e0 + (valid ? le : 0);
-      const int m = e / N, n = e - m * N;
-      double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
-      if (valid) {
-        const double* ar = Ap + (int64_t)m * a_sm;
-        const double* br = Bp + (int64_t)n * b_sn;
-        int k = kbeg + kl;
-        for (; k + 3 * g < kend; k += 4 * g) {
-          s0 = fma(ar[(int64_t)k * a_sk], br[(int64_t)k * b_sk], s0);
-          s1 = fma(ar[(int64_t)(k + g) * a_sk], br[(int64_t)(k + g) * b_sk], s1);
-          s2 = fma(ar[(int64_t)(k + 2 * g) * a_sk], br[(int64_t)(k + 2 * g) * b_sk], s2);
-          s3 = fma(ar[(int64_t)(k + 3 * g) * a_sk], br[(int64_t)(k + 3 * g) * b_sk], s3);
-        }
-        if (k < kend) s0 = fma(ar[(int64_t)k * a_sk], br[(int64_t)k * b_sk], s0);
-        if (k + g < kend) s1 = fma(ar[(int64_t)(k + g) * a_sk], br[(int64_t)(k + g) * b_sk], s1);
-        if (k + 2 * g < kend) s2 = fma(ar[(int64_t)(k + 2 * g) * a_sk], br[(int64_t)(k + 2 * g) * b_sk], s2);
-      }
-      double acc = (s0 + s1) + (s2 + s3);
+#pragma unroll
+    for (int q = 0; q < P; ++q) {
+      double acc = s[q];
       for (int off = 1; off < g; off <<= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
-      if (valid && kl == 0)
-        C[cbase + expand_index32(m, p->nrl, p->rdim, p->rstr) + expand_index32(n, p->ncl, p->cdim, p->cstr)] =
+      if (vq[q] && kl == 0) {
+        const int e = it.e0 + q * opp + o, m = e / N;
+        C[cbase + expand_index32(m, p->nrl, p->rdim, p->rstr) + expand_index32(e - m * N, p->ncl, p->cdim, p->cstr)] =
             sg * acc;
+      }
     }
   }
 }
@@ -202,7 +203,7 @@ ftn_status launch_gemm_f64_warp(ftn_ctx ctx, const GemmProb* d_probs, const Warp
                                 const double* a, const double* b, double* c) {
   if (nitems == 0) return FTN_OK;
   int64_t grid = ((int64_t)nitems + 3) / 4;
-  const int64_t cap = (int64_t)ctx->num_sms * 8;  // resident CTAs (64 registers, 128 threads)
+  const int64_t cap = (int64_t)ctx->num_sms * 6;  // resident CTAs (at most 80 registers, 128 threads)
   if (grid > cap) grid = cap;
   gemm_f64_warp_kernel<<<(unsigned)grid, 128, 0, ctx->stream>>>(d_probs, d_items, nitems, a, b, c);
   ctx->launches += 1;
