@@ -339,7 +339,7 @@ ftn_status tensordot_batch(ftn_ctx ctx, std::vector<TdItem>& items, ftn_prec pre
   } else {
     std::map<int, std::vector<size_t>> by_bn;
     for (size_t i = 0; i < items.size(); ++i)
-      if (!plans[i]->probs.empty()) by_bn[plans[i]->bn].push_back(i);
+      if (plans[i]->n_tiled > 0) by_bn[plans[i]->bn].push_back(i);
     for (auto& kv : by_bn) {
       const int bn = kv.first;
       const auto& idx = kv.second;
@@ -347,7 +347,7 @@ ftn_status tensordot_batch(ftn_ctx ctx, std::vector<TdItem>& items, ftn_prec pre
       for (size_t i : idx) cb = std::min(cb, (const char*)target(i));
       cb = lowest256(cb);
       size_t np = 0;
-      for (size_t i : idx) np += plans[i]->probs.size();
+      for (size_t i : idx) np += plans[i]->n_tiled;
       const size_t om = 0, op = al256(2 * idx.size() * sizeof(TcMapSet));
       uint8_t* h = (uint8_t*)staging_begin(ctx, op + np * sizeof(GemmProb));
       if (!h) return set_error(FTN_ENOMEM, "host staging allocation failed");
@@ -373,8 +373,9 @@ ftn_status tensordot_batch(ftn_ctx ctx, std::vector<TdItem>& items, ftn_prec pre
         for (int pi = 0; pi < 2; ++pi) FTN_TRY(tc_encode_set(prec, bn, ops, pi, &maps[2 * q + pi]));
         const int64_t dc = (const char*)target(i) - cb;
         if (dc & 3) return set_error(FTN_EINVAL, "batched GEMM: output not 4-byte aligned");
-        for (const GemmProb& g0 : P.probs) {
-          GemmProb& g = probs[p0 + (&g0 - P.probs.data())];
+        for (int j = 0; j < P.n_tiled; ++j) {
+          const GemmProb& g0 = P.probs[j];
+          GemmProb& g = probs[p0 + j];
           g = g0;
           g.pi = (int32_t)(2 * q) + g0.pi;
           g.tile_begin += tiles;
@@ -382,7 +383,7 @@ ftn_status tensordot_batch(ftn_ctx ctx, std::vector<TdItem>& items, ftn_prec pre
           g.c_off += dc / 4;
           fl += 2.0 * g.M * g.N * g.K;
         }
-        p0 += P.probs.size();
+        p0 += P.n_tiled;
         tiles += P.gemm_tiles;
       }
       DevTables dev;
@@ -392,6 +393,45 @@ ftn_status tensordot_batch(ftn_ctx ctx, std::vector<TdItem>& items, ftn_prec pre
       const int rec = prof_begin(ctx, "gemm_tc", 0, fl);
       const ftn_status st = launch_gemm_tc_maps(ctx, prec, (const TcMapSet*)(d + om), (const GemmProb*)(d + op),
                                                 (int)np, tiles, bn, (float*)const_cast<char*>(cb));
+      prof_end(ctx, rec);
+      FTN_TRY(st);
+    }
+    // the small problems of every plan in one CUDA-core launch: operands
+    // rebased onto the workspace (lo planes `hi` bytes after the hi ones),
+    // outputs onto the lowest target
+    std::vector<GemmProb> sp;
+    std::vector<WarpItem> wi;
+    const char* cb = nullptr;
+    for (size_t i = 0; i < items.size(); ++i)
+      if ((size_t)plans[i]->n_tiled < plans[i]->probs.size())
+        cb = cb ? std::min(cb, (const char*)target(i)) : (const char*)target(i);
+    if (cb) {
+      cb = lowest256(cb);
+      double fl = 0;
+      for (size_t i = 0; i < items.size(); ++i) {
+        const TdPlan& P = *plans[i];
+        const int64_t dc = (const char*)target(i) - cb;
+        if (dc & 3) return set_error(FTN_EINVAL, "batched GEMM: output not 4-byte aligned");
+        for (size_t j = (size_t)P.n_tiled; j < P.probs.size(); ++j) {
+          GemmProb g = P.probs[j];
+          g.a_off += (int64_t)(o_a[i] / es);
+          g.b_off += (int64_t)(o_b[i] / es);
+          g.c_off += dc / 4;
+          fl += 2.0 * g.M * g.N * g.K;
+          f64w_items(g, (int)sp.size(), wi);
+          sp.push_back(g);
+        }
+      }
+      TablePack tp;
+      const size_t op = tp.put(sp.data(), sp.size() * sizeof(GemmProb));
+      const size_t oi = tp.put(wi.data(), wi.size() * sizeof(WarpItem));
+      DevTables dev;
+      FTN_TRY(tp.upload(ctx, dev));
+      const uint8_t* d = (const uint8_t*)dev.p;
+      const int rec = prof_begin(ctx, "gemm_tc", 0, fl);
+      const ftn_status st = launch_gemm_f32_warp(ctx, prec, (const GemmProb*)(d + op), (const WarpItem*)(d + oi),
+                                                 (int)wi.size(), ws, ws, split ? (int64_t)(hi / es) : 0,
+                                                 (float*)const_cast<char*>(cb));
       prof_end(ctx, rec);
       FTN_TRY(st);
     }

@@ -328,6 +328,10 @@ __host__ __device__ inline int f64w_klanes(int klen) {
 void f64w_items(const GemmProb& g, int prob, std::vector<WarpItem>& out);
 ftn_status launch_gemm_f64_warp(ftn_ctx ctx, const GemmProb* d_probs, const WarpItem* d_items, int nitems,
                                 const double* a, const double* b, double* c);
+// The same for the tensor-core precisions' small problems: FP32 FMAs on the
+// sum of the operand planes (lo plane lo_delta elements after the hi one).
+ftn_status launch_gemm_f32_warp(ftn_ctx ctx, ftn_prec prec, const GemmProb* d_probs, const WarpItem* d_items,
+                                int nitems, const void* a, const void* b, int64_t lo_delta, float* c);
 // Partitions a planned FP64 problem list: tiled problems first (tile_begin
 // recounted, returned tile total in tiles), the small ones after them with
 // their items.  Returns the number of tiled problems.

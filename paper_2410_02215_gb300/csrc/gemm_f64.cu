@@ -4,7 +4,11 @@
 // kind, so these are DFMA kernels: 64 x bn tiles with 4 x (bn / 16) outputs
 // per thread over a persistent grid for problems of more than 4096 outputs,
 // one warp per group of outputs for the smaller ones.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
 #include <algorithm>
+#include <type_traits>
 
 #include "common.h"
 #include "ptx.cuh"
@@ -171,6 +175,118 @@ __global__ void __launch_bounds__(128, 6) gemm_f64_warp_kernel(const GemmProb* _
       }
     }
   }
+}
+
+// Small tensor-core-precision problems (the same size bound) on CUDA cores:
+// each operand element is its stored planes added in FP32 (hi + lo for the
+// split precisions, hi alone otherwise), products accumulated in FP32 FMAs.
+// That is at least as accurate as the tensor-core passes of the precision,
+// which multiply the same planes; the lane, pass and butterfly structure is
+// the FP64 warp kernel's.
+template <typename T>
+__device__ __forceinline__ float plane_val(const T* p) {
+  if constexpr (sizeof(T) == 4)
+    return *reinterpret_cast<const float*>(p);
+  else if constexpr (std::is_same<T, __half>::value)
+    return __half2float(*p);
+  else
+    return __bfloat162float(*p);
+}
+
+template <typename T, bool SPLIT>
+__global__ void __launch_bounds__(128, 8) gemm_f32_warp_kernel(const GemmProb* __restrict__ probs,
+                                                               const WarpItem* __restrict__ items, int nitems,
+                                                               const T* __restrict__ A, const T* __restrict__ B,
+                                                               int64_t lo_delta, float* __restrict__ C) {
+  constexpr int P = F64W_PASSES;
+  const int lane = threadIdx.x & 31;
+  const int nw = (int)((gridDim.x * blockDim.x) >> 5);
+  for (int w = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5); w < nitems; w += nw) {
+    const WarpItem it = items[w];
+    const GemmProb* __restrict__ p = probs + it.prob;
+    const int N = p->N, K = p->K;
+    const int g = f64w_klanes(K);
+    const int lg = __ffs(g) - 1, opp = 32 >> lg;
+    const int o = lane >> lg, kl = lane & (g - 1);
+    const int64_t a_sm = p->a_sm, a_sk = p->a_sk, b_sn = p->b_sn, b_sk = p->b_sk;
+    const T* ar[P];
+    const T* br[P];
+    bool vq[P];
+    float s[P];
+#pragma unroll
+    for (int q = 0; q < P; ++q) {
+      const int le = q * opp + o;
+      vq[q] = le < it.cnt;
+      const int e = it.e0 + (vq[q] ? le : 0);
+      const int m = e / N;
+      ar[q] = A + p->a_off + (int64_t)m * a_sm;
+      br[q] = B + p->b_off + (int64_t)(e - m * N) * b_sn;
+      s[q] = 0.0f;
+    }
+    for (int k = kl; k < K; k += g) {
+#pragma unroll
+      for (int q = 0; q < P; ++q)
+        if (vq[q]) {
+          const T* pa = ar[q] + (int64_t)k * a_sk;
+          const T* pb = br[q] + (int64_t)k * b_sk;
+          float a = plane_val(pa), b = plane_val(pb);
+          if constexpr (SPLIT) {
+            a += plane_val(pa + lo_delta);
+            b += plane_val(pb + lo_delta);
+          }
+          s[q] = fmaf(a, b, s[q]);
+        }
+    }
+    const float sg = (float)p->c_sign;
+#pragma unroll
+    for (int q = 0; q < P; ++q) {
+      float acc = s[q];
+      for (int off = 1; off < g; off <<= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+      if (vq[q] && kl == 0) {
+        const int e = it.e0 + q * opp + o, m = e / N;
+        C[p->c_off + expand_index32(m, p->nrl, p->rdim, p->rstr) + expand_index32(e - m * N, p->ncl, p->cdim, p->cstr)] =
+            sg * acc;
+      }
+    }
+  }
+}
+
+ftn_status launch_gemm_f32_warp(ftn_ctx ctx, ftn_prec prec, const GemmProb* d_probs, const WarpItem* d_items,
+                                int nitems, const void* a, const void* b, int64_t lo_delta, float* c) {
+  if (nitems == 0) return FTN_OK;
+  int64_t grid = ((int64_t)nitems + 3) / 4;
+  const int64_t cap = (int64_t)ctx->num_sms * 8;
+  if (grid > cap) grid = cap;
+  const unsigned gd = (unsigned)grid;
+  cudaStream_t s = ctx->stream;
+  switch (prec) {
+    case FTN_PREC_TF32:
+      gemm_f32_warp_kernel<float, false><<<gd, 128, 0, s>>>(d_probs, d_items, nitems, (const float*)a,
+                                                            (const float*)b, lo_delta, c);
+      break;
+    case FTN_PREC_TF32X3:
+      gemm_f32_warp_kernel<float, true><<<gd, 128, 0, s>>>(d_probs, d_items, nitems, (const float*)a,
+                                                           (const float*)b, lo_delta, c);
+      break;
+    case FTN_PREC_BF16:
+      gemm_f32_warp_kernel<__nv_bfloat16, false><<<gd, 128, 0, s>>>(
+          d_probs, d_items, nitems, (const __nv_bfloat16*)a, (const __nv_bfloat16*)b, lo_delta, c);
+      break;
+    case FTN_PREC_BF16X3:
+      gemm_f32_warp_kernel<__nv_bfloat16, true><<<gd, 128, 0, s>>>(
+          d_probs, d_items, nitems, (const __nv_bfloat16*)a, (const __nv_bfloat16*)b, lo_delta, c);
+      break;
+    case FTN_PREC_F16X3:
+      gemm_f32_warp_kernel<__half, true><<<gd, 128, 0, s>>>(d_probs, d_items, nitems, (const __half*)a,
+                                                            (const __half*)b, lo_delta, c);
+      break;
+    default:
+      return set_error(FTN_EINVAL, "internal error: CUDA-core GEMM precision");
+  }
+  ctx->launches += 1;
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_error(e, "gemm_f32_warp_kernel launch");
+  return FTN_OK;
 }
 
 void f64w_items(const GemmProb& g, int prob, std::vector<WarpItem>& out) {

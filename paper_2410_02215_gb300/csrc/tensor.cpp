@@ -30,8 +30,20 @@ size_t dtype_size(ftn_dtype d) { return d == FTN_F64 ? 8 : 4; }
 // cudaMallocAsync give on one stream); the driver's allocator, whose calls
 // serialise when several host threads drive contexts, is left out of the
 // steady state.  Cached free blocks beyond CACHE_LIMIT go back to it.
+// While the stream is being captured into a CUDA graph the cache is not
+// used at all: a block allocated in the capture belongs to the graph, and a
+// block the graph refers to must never be handed out again.
 namespace {
 constexpr size_t CACHE_LIMIT = (size_t)2 << 30;
+
+bool capturing(cudaStream_t s) {
+  cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &st) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return true;  // cannot tell (legacy stream beside a capture): the safe answer
+  }
+  return st != cudaStreamCaptureStatusNone;
+}
 
 size_t size_class(size_t b) {
   if (b <= 4096) return (b + 255) & ~(size_t)255;
@@ -45,6 +57,11 @@ size_t size_class(size_t b) {
 void* dev_alloc(ftn_ctx ctx, size_t bytes) {
   if (bytes == 0) bytes = 256;
   if (ctx->alloc) return ctx->alloc(bytes, ctx->user);
+  if (capturing(ctx->stream)) {
+    void* p = nullptr;
+    if (cudaMallocAsync(&p, bytes, ctx->stream) != cudaSuccess) return nullptr;
+    return p;
+  }
   const size_t cls = size_class(bytes);
   {
     std::lock_guard<std::mutex> lock(ctx->cache_mu);
@@ -73,15 +90,16 @@ void dev_free(ftn_ctx ctx, void* p) {
     ctx->free_fn(p, ctx->user);
     return;
   }
+  const bool cap = capturing(ctx->stream);
   std::unique_lock<std::mutex> lock(ctx->cache_mu);
   auto it = ctx->block_class.find(p);
-  if (it == ctx->block_class.end()) {  // not from dev_alloc (cannot happen): plain stream-ordered free
+  if (it == ctx->block_class.end()) {  // allocated during a capture: a plain stream-ordered free
     lock.unlock();
     cudaFreeAsync(p, ctx->stream);
     return;
   }
   const size_t cls = it->second;
-  if (ctx->cached_bytes + cls > CACHE_LIMIT) {
+  if (cap || ctx->cached_bytes + cls > CACHE_LIMIT) {
     ctx->block_class.erase(it);
     lock.unlock();
     cudaFreeAsync(p, ctx->stream);
@@ -525,7 +543,10 @@ ftn_status ftn_ctx_destroy(ftn_ctx ctx) {
 ftn_status ftn_ctx_set_stream(ftn_ctx ctx, void* cuda_stream) {
   if (!ctx) return set_error(FTN_EINVAL, "null ctx");
   // cached blocks were freed in the old stream's order: let it finish first
-  if ((cudaStream_t)cuda_stream != ctx->stream) FTN_CUDA(cudaStreamSynchronize(ctx->stream));
+  // (not while either stream is being captured: the cache is idle then, and
+  // a synchronisation would break the capture)
+  if ((cudaStream_t)cuda_stream != ctx->stream && !capturing((cudaStream_t)cuda_stream) && !capturing(ctx->stream))
+    FTN_CUDA(cudaStreamSynchronize(ctx->stream));
   ctx->stream = (cudaStream_t)cuda_stream;
   return FTN_OK;
 }

@@ -116,7 +116,7 @@ static ftn_status upload_plan(ftn_ctx ctx, TdPlan& P) {
   P.d_witems = sw ? (WarpItem*)(b + sa + sb + sc + sp + sr + sm) : nullptr;
   if (st) {
     P.d_tt = (TileEnt*)(b + pre);
-    FTN_TRY(tc_tile_table(ctx, P.d_probs, (int)P.probs.size(), P.gemm_tiles, P.bn, P.d_tt));
+    FTN_TRY(tc_tile_table(ctx, P.d_probs, P.n_tiled, P.gemm_tiles, P.bn, P.d_tt));
   }
   return FTN_OK;
 }
@@ -427,6 +427,14 @@ static ftn_status build_plan(ftn_ctx ctx, const ftn_tensor_s* A, const ftn_tenso
       if (!(!g.epi_rows && l == nf - 1)) ok = ok && g.cstr[l] % 4 == 0;
     g.vec4 = ok ? 1 : 0;
   }
+  // small tensor-core-precision problems run on CUDA cores (after the
+  // grouped tile list, which covers probs[0, n_tiled))
+  std::vector<GemmProb> small_tc;
+  if (tc) {
+    auto mid = std::stable_partition(P->probs.begin(), P->probs.end(), [](const GemmProb& g) { return !f64w_small(g); });
+    small_tc.assign(mid, P->probs.end());
+    P->probs.erase(mid, P->probs.end());
+  }
   if (tc) {
     // group problems by (pi, row block); inside a group the tiles run
     // m-tile by m-tile across all member problems (A tile reuse in L2)
@@ -490,6 +498,12 @@ static ftn_status build_plan(ftn_ctx ctx, const ftn_tensor_s* A, const ftn_tenso
         g.tile_begin = P->gemm_tiles;
       }
       P->gemm_tiles += (int64_t)P->probs[gr.first].tiles_m * row_tiles;
+    }
+    P->n_tiled = (int)P->probs.size();
+    P->witems.clear();
+    for (const GemmProb& g : small_tc) {
+      f64w_items(g, (int)P->probs.size(), P->witems);
+      P->probs.push_back(g);
     }
   } else {
     for (GemmProb& g : P->probs) {
@@ -695,8 +709,10 @@ static ftn_status run_plan(ftn_ctx ctx, TdPlan& Pl, const ftn_tensor_s* A, const
         ops.ldk[pi] = (int32_t)P->ldk[pi];
       }
       rec = prof_begin(ctx, "gemm_tc", gb, gemm_flops);
-      st = launch_gemm_tc(ctx, prec, ops, P->d_probs, (int)P->probs.size(), P->gemm_tiles, P->bn, (float*)ctmp,
-                          P->d_tt);
+      st = launch_gemm_tc(ctx, prec, ops, P->d_probs, P->n_tiled, P->gemm_tiles, P->bn, (float*)ctmp, P->d_tt);
+      if (st == FTN_OK)
+        st = launch_gemm_f32_warp(ctx, prec, P->d_probs, P->d_witems, (int)P->witems.size(), af_hi, bf_hi,
+                                  split ? (int64_t)((af_lo - af_hi) / (int64_t)es) : 0, (float*)ctmp);
       prof_end(ctx, rec);
     }
   }
