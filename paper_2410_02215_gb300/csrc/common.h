@@ -304,11 +304,13 @@ ftn_status launch_permute2(ftn_ctx ctx, const PermJob* d_jobs, int njobs, int64_
 ftn_status launch_gemm_f64(ftn_ctx ctx, const GemmProb* d_probs, int nprobs, int64_t tiles, const double* a,
                            const double* b, double* c, int bn);
 int f64_pick_bn(int max_n);
-// Small FP64 problems (at most F64W_MAX_MN outputs) run on a warp kernel
-// instead of the 64 x bn tiles: one warp per item of up to F64W_PASSES
-// passes, each pass 32 / g outputs with g lanes splitting K (g from the
-// problem's own K or split length only, so a problem's arithmetic never
-// depends on the launch it is part of).
+// Small FP64 problems (at most F64W_MAX_MN outputs, at most F64W_MAX_K
+// terms per output in their split slice) run on a warp kernel instead of the
+// 64 x bn tiles: one warp per item of up to F64W_PASSES passes, each pass
+// 32 / g outputs with g lanes splitting K (g from the problem's own K or
+// split length only, so a problem's arithmetic never depends on the launch
+// it is part of).  Longer dot products amortise a tile's overhead and reuse
+// its operands from shared memory, so they stay on the tiled kernel.
 struct WarpItem {
   int32_t prob;  // problem index in the launch's table
   int32_t ks;    // split-K slice
@@ -316,8 +318,11 @@ struct WarpItem {
   int32_t cnt;   // outputs of this item
 };
 constexpr int64_t F64W_MAX_MN = 4096;
+constexpr int F64W_MAX_K = 64;
 constexpr int F64W_PASSES = 4;
-inline bool f64w_small(const GemmProb& g) { return (int64_t)g.M * g.N <= F64W_MAX_MN; }
+inline bool f64w_small(const GemmProb& g) {
+  return (int64_t)g.M * g.N <= F64W_MAX_MN && (g.nsplit > 1 ? g.kchunk : g.K) <= F64W_MAX_K;
+}
 // K lanes: the largest power of two <= 32 that leaves each lane >= 8 terms
 __host__ __device__ inline int f64w_klanes(int klen) {
   int g = 1;
