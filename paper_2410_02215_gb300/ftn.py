@@ -499,10 +499,8 @@ def _network_arrays(networks):
     Returns (count, networks, trees, keep) -- ``keep`` holds the tables."""
     nets = list(networks)
     n = len(nets)
-    net_arr = (Network * max(1, n))()
-    tree_arr = (Tree * max(1, n))()
     if n == 0:
-        return 0, net_arr, tree_arr, []
+        return 0, (Network * 1)(), (Tree * 1)(), []
 
     def flat(rows):
         parts = [np.asarray(r, dtype=np.int32).reshape(-1) for r in rows]
@@ -510,23 +508,42 @@ def _network_arrays(networks):
         np.cumsum([q.size for q in parts], out=offs[1:])
         return np.concatenate(parts + [np.zeros(1, np.int32)]), offs
 
-    hs = np.array([t.handle.value for job in nets for t in job["tensors"]] + [0], dtype=np.uint64)
     hoff = np.zeros(n + 1, dtype=np.int64)
     np.cumsum([len(job["tensors"]) for job in nets], out=hoff[1:])
+    hs = np.zeros(int(hoff[-1]) + 1, dtype=np.uint64)
+    hs[:-1] = np.fromiter((t.handle.value for job in nets for t in job["tensors"]), dtype=np.uint64,
+                          count=int(hoff[-1]))
     fb, boff = flat(job["bonds"] for job in nets)
     ft, toff = flat(job["tree"] for job in nets)
-    fp, poff = flat((job.get("positions") or ()) for job in nets)
+    fp, poff = flat((() if job.get("positions") is None else job["positions"]) for job in nets)
     hp, bp, tp, pp = hs.ctypes.data, fb.ctypes.data, ft.ctypes.data, fp.ctypes.data
-    vpp, i32p = C.POINTER(C.c_void_p), C.POINTER(C.c_int32)
-    for i, job in enumerate(nets):
-        pos = job.get("positions")
-        net_arr[i] = Network(len(job["tensors"]), C.cast(hp + 8 * int(hoff[i]), vpp), len(job["bonds"]),
-                             C.cast(bp + 4 * int(boff[i]), i32p),
-                             C.cast(pp + 4 * int(poff[i]), i32p) if pos is not None else None)
-        pol = job.get("policy", "exact")
-        tree_arr[i] = Tree(len(job["tree"]), C.cast(tp + 4 * int(toff[i]), i32p),
-                           POLICY_NAMES[pol] if isinstance(pol, str) else int(pol), int(job.get("chi", 0)))
-    return n, net_arr, tree_arr, [hs, fb, ft, fp]
+    # the structs themselves, filled column by column in numpy views of the
+    # ctypes arrays (every pointer field is 8 bytes, every count a C int)
+    nd = np.zeros(n, dtype=np.dtype({"names": ["nt", "t", "nb", "b", "p"],
+                                     "formats": [np.int32, np.uint64, np.int32, np.uint64, np.uint64],
+                                     "offsets": [Network.n_tensors.offset, Network.tensors.offset,
+                                                 Network.n_bonds.offset, Network.bonds.offset,
+                                                 Network.positions.offset],
+                                     "itemsize": C.sizeof(Network)}))
+    td = np.zeros(n, dtype=np.dtype({"names": ["ns", "pairs", "pol", "chi"],
+                                     "formats": [np.int32, np.uint64, np.int32, np.int32],
+                                     "offsets": [Tree.n_steps.offset, Tree.pairs.offset, Tree.policy.offset,
+                                                 Tree.chi.offset],
+                                     "itemsize": C.sizeof(Tree)}))
+    has_pos = np.fromiter((job.get("positions") is not None for job in nets), dtype=bool, count=n)
+    nd["nt"] = np.diff(hoff)
+    nd["t"] = hp + 8 * hoff[:-1].astype(np.uint64)
+    nd["nb"] = np.diff(boff) // 4
+    nd["b"] = bp + 4 * boff[:-1].astype(np.uint64)
+    nd["p"] = np.where(has_pos, pp + 4 * poff[:-1].astype(np.uint64), 0).astype(np.uint64)
+    td["ns"] = np.diff(toff) // 2
+    td["pairs"] = tp + 4 * toff[:-1].astype(np.uint64)
+    pols = [job.get("policy", "exact") for job in nets]
+    td["pol"] = [POLICY_NAMES[q] if isinstance(q, str) else int(q) for q in pols]
+    td["chi"] = [int(job.get("chi", 0)) for job in nets]
+    net_arr = (Network * n).from_buffer(nd)
+    tree_arr = (Tree * n).from_buffer(td)
+    return n, net_arr, tree_arr, [hs, fb, ft, fp, nd, td]
 
 
 def contract_batch(ctx, networks, prec="f64"):

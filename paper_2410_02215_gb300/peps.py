@@ -15,7 +15,14 @@ Tensor ids: ket s -> s, bra s -> n + s, operator -> 2n.
 """
 from __future__ import annotations
 
+import weakref
+
 from . import ftn
+
+# Structure of cluster networks (bonds, positions, tree as int32 arrays) by
+# cluster function and (targets, with operator): it depends on the lattice
+# alone, so repeated evaluations of one lattice build it once.
+_CLUSTER_STRUCT: "weakref.WeakKeyDictionary" = weakref.WeakKeyDictionary()
 
 
 def layers(ctx, layout, kets):
@@ -171,13 +178,30 @@ def cluster_network(layout, kets, bras, sites, dangling, gauge_of, op=None, targ
     return tensors, bonds, pos
 
 
+def _cluster_structure(layout, kets, cluster_fn, targets):
+    """Sites, dangling bonds and, with and without the operator, the bonds,
+    positions and tree of a term's cluster network (int32 arrays)."""
+    import numpy as np
+
+    sites, dang, tree_op, tree_norm = cluster_fn(list(targets))
+    st = {"sites": list(sites), "dang": list(dang)}
+    for with_op, tree in ((True, tree_op), (False, tree_norm)):
+        _t, bonds, pos = cluster_network(layout, kets, kets, sites, dang, lambda s, a: None,
+                                         object() if with_op else None, targets)
+        st[with_op] = (np.asarray(bonds, dtype=np.int32).reshape(-1, 4), np.asarray(pos, dtype=np.int32),
+                       np.asarray(tree, dtype=np.int32).reshape(-1, 2))
+    return st
+
+
 def cluster_networks(ctx, instances, t, u, policy="exact", chi=0, dtype=ftn.F64, terms=None):
     """Cluster networks of every hopping and on-site term of every instance
     (layout, kets, cluster_fn, gauges) -- or of the target tuples ``terms``
     (pairs are hopping terms, single sites on-site terms): for each term the
     network with the operator, then the same network without it (its
     normalisation), and the term table of ftn_energy with one group per
-    instance.  Returns (networks, num, den, group_end, keep)."""
+    instance.  ``cluster_fn`` must depend on the targets alone: the
+    networks' structure is kept per cluster function and reused by later
+    calls.  Returns (networks, num, den, group_end, keep)."""
     hop = ftn.hubbard_term(ctx, 0, t, 0.0, dtype)
     onsite = ftn.hubbard_term(ctx, 1, 0.0, u, dtype)
     nets, group_end, keep = [], [], [hop, onsite]
@@ -201,10 +225,17 @@ def cluster_networks(ctx, instances, t, u, policy="exact", chi=0, dtype=ftn.F64,
             tl = [((a, b), hop) for a, b in layout["edges"]] + [((s,), onsite) for s in range(layout["n"])]
         else:
             tl = [(tuple(tg), hop if len(tg) == 2 else onsite) for tg in terms]
+        memo = _CLUSTER_STRUCT.setdefault(cluster_fn, {})
         for targets, op in tl:
-            sites, dang, tree_op, tree_norm = cluster_fn(list(targets))
-            for o, tree in ((op, tree_op), (None, tree_norm)):
-                tens, bonds, pos = cluster_network(layout, kets, bras, sites, dang, gauge_of, o, targets)
+            st = memo.get(targets)
+            if st is None:
+                st = memo[targets] = _cluster_structure(layout, kets, cluster_fn, targets)
+            sites, dang = st["sites"], st["dang"]
+            base = [kets[s] for s in sites] + [bras[s] for s in sites]
+            gauges = [gauge_of(s, a) for s, a, _t in dang]
+            for with_op, o in ((True, op), (False, None)):
+                bonds, pos, tree = st[with_op]
+                tens = base + ([o] if with_op else []) + gauges
                 nets.append({"tensors": tens, "bonds": bonds, "tree": tree, "positions": pos, "policy": policy,
                              "chi": chi})
         group_end.append(len(nets) // 2)

@@ -22,7 +22,7 @@ def test_network_arrays_round_trip():
                          "positions": [2, 0, 1] if i % 2 else None, "policy": ["exact", "early", "late"][i % 3],
                          "chi": 4 * i})
     n, na, ta, keep = F._network_arrays(nets)
-    assert n == len(nets) and len(keep) == 4
+    assert n == len(nets) and len(keep) == 6
     for i, job in enumerate(nets):
         N, T = na[i], ta[i]
         assert [N.tensors[k] for k in range(N.n_tensors)] == [t.handle.value for t in job["tensors"]]
@@ -32,3 +32,38 @@ def test_network_arrays_round_trip():
         assert pos == job["positions"]
         assert T.policy == F.POLICY_NAMES[job.get("policy", "exact")] and T.chi == job.get("chi", 0)
     assert F._network_arrays([])[0] == 0
+
+
+def test_cluster_structure_matches_network_assembly():
+    """The structure kept per cluster function (bonds, positions, tree as
+    int32 arrays) is what cluster_network assembles for the same term, with
+    and without the operator, on a random 3-regular graph."""
+    import numpy as np
+
+    import workloads as W
+    from paper_2410_02215_gb300 import peps
+
+    class _T:
+        def __init__(self, rank):
+            self.rank = rank
+
+    n, edges = W.random_regular_graph(12, 3, 5)
+    lay = W.peps_layout(n, edges, (2, 1), (2, 2))
+    kets = [_T(len(lay["legs"][s])) for s in range(n)]
+
+    def cfn(targets):
+        sites = W.cluster_sites(lay, targets, 1)
+        return (sites, W.dangling_bonds(lay, sites), W.cluster_tree(lay, sites, targets, True),
+                W.cluster_tree(lay, sites, targets, False))
+
+    for targets in [tuple(lay["edges"][0]), tuple(lay["edges"][5]), (3,)]:
+        st = peps._cluster_structure(lay, kets, cfn, targets)
+        sites, dang, tr_op, tr_norm = cfn(list(targets))
+        assert st["sites"] == list(sites) and st["dang"] == list(dang)
+        for with_op, tree in ((True, tr_op), (False, tr_norm)):
+            _t, bonds, pos = peps.cluster_network(lay, kets, kets, sites, dang, lambda s, a: None,
+                                                  object() if with_op else None, targets)
+            b, p, t = st[with_op]
+            assert b.tolist() == [list(x) for x in bonds]
+            assert p.tolist() == list(pos)
+            assert t.tolist() == [list(x) for x in tree]
