@@ -6,18 +6,22 @@ two rank-5 Z2 site tensors (four virtual legs D = 8 split 4+4, physical leg
 4 split 2+2) and rank-6 boundary environments (chi = 64 split 32+32),
 contracting 2-3 legs, every input stored in a seeded random leg order and
 every result permuted to a seeded random leg order; only parity-allowed
-blocks are stored.  Each tensordot = sign-permute of both inputs into the
-fused sector-matrix layout + one grouped sector GEMM + the output
-sign-permute, all in libftn's CUDA kernels.
+blocks are stored.  Each tensordot = one sign-permute launch of both inputs
+into the fused sector-matrix layout + one grouped sector GEMM whose epilogue
+writes the result straight into its permuted block layout (a separate output
+sign-permute only where the destination's fastest legs are too short for
+that), all in libftn's CUDA kernels.  The step is timed as a CUDA graph of
+these launches when its replay reproduces the eager step bit for bit.
 
 Metric: sector-GEMM TFLOP/s (the flops of the Z2-sector GEMMs, 2*M*N*K per
-block pair, over the time of the whole step).  The second half of the metric,
-fPEPS energy evaluations per second, is reported under "energy" (FP64 and
-mixed precision, with their errors against the oracle) on a compressed
-square-lattice Hubbard fPEPS (see ENERGY_WORKLOAD).  The primary arithmetic is
-TF32x3 (FP32-accurate split products on the tcgen05 tensor cores); the
-plain-FP64 GPU path and the other precisions are reported beside it with
-their error against the FP64 CPU oracle.
+block pair, over the time of the whole step).  The default arithmetic is
+F16X3 (FP16 hi/lo split products on the tcgen05 tensor cores, accumulated in
+FP32); the other precisions, the plain-FP64 path and their errors against
+the FP64 CPU oracle are reported beside it.  The second half of the metric,
+fPEPS energy evaluations per second, is reported under "energy" (4x4 square
+lattice, whole network), "energy_diamond" (the 64-site diamond by the
+cluster approximation) and "cluster" (energy terms per second over 64
+random 3-regular graphs), FP64 and mixed precision.
 
 ``--impl reference`` times the CPU oracle (the reference arm of this
 method: no other implementation exists) on the same metric and workload.

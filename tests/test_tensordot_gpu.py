@@ -364,3 +364,23 @@ def test_merged_group_of_many_members(F, ctx, prec):
     got = dense(c.to_blocks(), c.legs, c.parity)
     assert relerr(got.data, ref.data) <= TOL[prec]
     ctx.synchronize()
+
+
+@pytest.mark.parametrize("prec", ["tf32x3", "f16x3", "bf16x3"])
+@pytest.mark.parametrize("perm", [None, [1, 0]])
+def test_partial_last_round_and_ragged_columns(F, ctx, prec, perm):
+    """A launch of 152 + 20 tiles of 128 x 128 (one full round on the 152
+    SMs and 20 tiles in a second, partial one), one problem whose last
+    column tile holds 40 valid columns.  Every output entry against the
+    oracle, with and without an output permutation (fused epilogue writes)."""
+    la = [(1664, 128, 0), (64, 64, 1)]
+    lb = [(64, 64, 0), (1664, 296, 0)]
+    ba, bb = W.random_blocks(la, 0, 21), W.random_blocks(lb, 0, 22)
+    A, B = dense(ba, la, 0), dense(bb, lb, 0)
+    ref = O.contract(A, B, [1], [0])
+    if perm is not None:
+        ref = O.transpose(ref, perm)
+    a, b = upload(F, ctx, la, 0, ba, prec), upload(F, ctx, lb, 0, bb, prec)
+    c = F.tensordot(ctx, a, b, [1], [0], out_perm=perm, prec=prec)
+    assert relerr(c.download().astype(np.float64), packed_like(c, ref)) <= TOL[prec]
+    ctx.synchronize()
