@@ -285,6 +285,27 @@ typedef struct {
 FTN_API ftn_status ftn_compress(ftn_ctx ctx, ftn_tensor* X, ftn_tensor* Y, int n, const int* axes_x,
                         const int* axes_y, int chi, int arrows, ftn_compress_info* info);
 
+/* Adjoint of ftn_compress (the gradient of the Sec. II.A compression, which
+ * the paper does not differentiate): for a scalar L of the compressed pair
+ * (X', Y') = ftn_compress(X, Y, ...) with the same arguments, given the
+ * cotangents dXn = dL/dX' and dYn = dL/dY' (FP64 tensors with the legs and
+ * parity of X' and Y'), returns dX = dL/dX and dY = dL/dY as new
+ * library-owned tensors with X's and Y's legs.  X and Y are borrowed and left
+ * unchanged; the forward compression is recomputed (its kept set and
+ * factors).  Per bond-parity sector: the reverse-mode rules of the column
+ * scalings, of the thin SVD of the core (F-matrix 1/(s_j^2 - s_i^2) over every
+ * singular pair with a kept member, projections onto the complements of the
+ * kept vectors) and of the R factors, then the adjoint of the
+ * sign-permutes.  Defined where the compression is differentiable: a gap at
+ * the truncation cut, distinct nonzero singular values, full-rank sector
+ * blocks; a block whose factor drops rows or a core with a zero singular
+ * value gives FTN_EUNSUPPORTED, cotangents of the wrong shape FTN_ESHAPE.  A
+ * loss that depends on the gauge of the new bond (signs of its states) has
+ * no well-defined gradient.  FP64 throughout; synchronises as ftn_compress. */
+FTN_API ftn_status ftn_compress_grad(ftn_ctx ctx, ftn_tensor X, ftn_tensor Y, int n, const int* axes_x,
+                             const int* axes_y, int chi, int arrows, ftn_tensor dXn, ftn_tensor dYn,
+                             ftn_tensor* dX, ftn_tensor* dY);
+
 /* ---- contraction tree executor (Fig. 1, Secs. II.C-II.D, III) ------------ */
 
 typedef enum { FTN_POLICY_EXACT = 0, FTN_POLICY_EARLY = 1, FTN_POLICY_LATE = 2 } ftn_policy;

@@ -125,6 +125,11 @@ struct CompressItem {
   int chi = 0;
   int arrows = 1;
   ftn_compress_info* info = nullptr;
+  // ftn_compress_grad: cotangents of the compressed pair (tensors with the
+  // new X's and Y's legs); when set, X and Y are left in place and dX, dY
+  // receive the gradient with respect to them
+  ftn_tensor gXn = nullptr, gYn = nullptr;
+  ftn_tensor dX = nullptr, dY = nullptr;
 };
 // ftn_compress for every item (FP64 tensors).
 ftn_status compress_batch(ftn_ctx ctx, std::vector<CompressItem>& items);

@@ -958,6 +958,206 @@ ftn_status launch_svd_cluster(ftn_ctx ctx, const SvdJob* jobs, int njobs, int C,
   }
 }
 
+// ---- adjoint (gradient) of the compression: small dense kernels ----------------
+// The backward pass of ftn_compress_grad works per bond-parity sector on the
+// forward's factors: R_X, R_Y (compacted), the Jacobi rows T_f = s_j x (unit
+// vector), the kept vectors W = S^-1/2 U_k^T and Z = S^-1/2 V_k^T.  Products
+// go through the FP64 GEMM; these kernels do the rest (one CTA per matrix).
+
+// out[j, c] = in[j, c] / s[j] (rows x cols, row strides ld_in / ld_out)
+struct RowDivJob {
+  const double* in;
+  double* out;
+  const double* s;
+  int rows, cols;
+};
+__global__ void __launch_bounds__(256) row_div_kernel(const RowDivJob* jobs) {
+  const RowDivJob J = jobs[blockIdx.x];
+  const int64_t n = (int64_t)J.rows * J.cols;
+  for (int64_t e = threadIdx.x; e < n; e += blockDim.x) {
+    const int j = (int)(e / J.cols);
+    J.out[e] = J.in[e] / J.s[j];
+  }
+}
+
+// Cotangents of the thin SVD's factors from those of Z and W: for kept state
+// j (Jacobi row i = idx[j]) du_i = s_i^-1/2 dW[j], dv_i = s_i^-1/2 dZ[j] and
+// ds_i = -1/2 s_i^-3/2 (dZ[j] . v_i + dW[j] . u_i); zero for the others.
+struct CotJob {
+  const double* dZ;  // k x ry
+  const double* dW;  // k x rx
+  const double* Ut;  // r x rx (rows u_i)
+  const double* Vt;  // r x ry
+  const double* s;   // r (Jacobi order)
+  const int* idx;    // k: Jacobi row of kept state j
+  double* dUt;       // r x rx
+  double* dVt;       // r x ry
+  double* ds;        // r
+  int k, r, rx, ry;
+};
+__global__ void __launch_bounds__(256) svd_cot_kernel(const CotJob* jobs) {
+  const CotJob J = jobs[blockIdx.x];
+  for (int64_t e = threadIdx.x; e < (int64_t)J.r * J.rx; e += blockDim.x) J.dUt[e] = 0.0;
+  for (int64_t e = threadIdx.x; e < (int64_t)J.r * J.ry; e += blockDim.x) J.dVt[e] = 0.0;
+  for (int e = threadIdx.x; e < J.r; e += blockDim.x) J.ds[e] = 0.0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int j = warp; j < J.k; j += nw) {
+    const int i = J.idx[j];
+    const double si = J.s[i], a = 1.0 / sqrt(si);
+    double dot = 0.0;
+    for (int c = lane; c < J.rx; c += 32) {
+      const double w = J.dW[(int64_t)j * J.rx + c];
+      J.dUt[(int64_t)i * J.rx + c] = a * w;
+      dot = fma(w, J.Ut[(int64_t)i * J.rx + c], dot);
+    }
+    for (int c = lane; c < J.ry; c += 32) {
+      const double z = J.dZ[(int64_t)j * J.ry + c];
+      J.dVt[(int64_t)i * J.ry + c] = a * z;
+      dot = fma(z, J.Vt[(int64_t)i * J.ry + c], dot);
+    }
+    for (int o = 16; o; o >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, o);
+    if (lane == 0) J.ds[i] = -0.5 * dot * a / si;
+  }
+}
+
+// The core of the thin-SVD adjoint (r x r, Jacobi order):
+//   inner = (F o (X - X^T)) S + diag(ds) + S (F o (Y - Y^T)),
+// X = U^T dU, Y = V^T dV, F_ij = 1 / (s_j^2 - s_i^2) for i != j with i or j
+// kept (pairs of discarded states carry no cotangent), 0 otherwise.
+struct InnerJob {
+  const double* X;
+  const double* Y;
+  const double* s;
+  const double* ds;
+  const int* kept;  // r flags
+  double* inner;
+  int r;
+};
+__global__ void __launch_bounds__(256) svd_inner_kernel(const InnerJob* jobs) {
+  const InnerJob J = jobs[blockIdx.x];
+  const int r = J.r;
+  for (int64_t e = threadIdx.x; e < (int64_t)r * r; e += blockDim.x) {
+    const int i = (int)(e / r), j = (int)(e - (int64_t)i * r);
+    double v = 0.0;
+    if (i == j) {
+      v = J.ds[i];
+    } else if (J.kept[i] || J.kept[j]) {
+      const double si = J.s[i], sj = J.s[j];
+      const double f = 1.0 / ((sj - si) * (sj + si));
+      const double xa = J.X[(int64_t)i * r + j] - J.X[(int64_t)j * r + i];
+      const double ya = J.Y[(int64_t)i * r + j] - J.Y[(int64_t)j * r + i];
+      v = f * (xa * sj + si * ya);
+    }
+    J.inner[e] = v;
+  }
+}
+
+// out = a + sa * b (elementwise over n), or, with s set, out[j, c] = a[j, c]
+// + sa * b[j, c] * sinv_j with sinv_j = 1 / s_j for kept rows, 0 otherwise.
+struct AxpyJob {
+  const double* a;
+  const double* b;
+  double* out;
+  const double* s;
+  const int* kept;
+  int64_t n;
+  int cols;
+  double sa;
+};
+__global__ void __launch_bounds__(256) axpy_kernel(const AxpyJob* jobs) {
+  const AxpyJob J = jobs[blockIdx.x];
+  for (int64_t e = threadIdx.x; e < J.n; e += blockDim.x) {
+    double f = J.sa;
+    if (J.s) {
+      const int j = (int)(e / J.cols);
+      f = J.kept[j] ? f / J.s[j] : 0.0;
+    }
+    J.out[e] = (J.a ? J.a[e] : 0.0) + f * J.b[e];
+  }
+}
+
+// C := copyltu(C) = tril(C) + tril(C, -1)^T (n x n, in place)
+struct SqJob {
+  double* C;
+  const double* R;
+  int n;
+};
+__global__ void __launch_bounds__(256) copyltu_kernel(const SqJob* jobs) {
+  const SqJob J = jobs[blockIdx.x];
+  for (int64_t e = threadIdx.x; e < (int64_t)J.n * J.n; e += blockDim.x) {
+    const int i = (int)(e / J.n), j = (int)(e - (int64_t)i * J.n);
+    if (i < j) J.C[e] = J.C[(int64_t)j * J.n + i];
+  }
+}
+
+// C := R^-1 for an upper-triangular n x n R with nonzero diagonal: column j
+// of the inverse by back substitution (one thread per column).
+__global__ void __launch_bounds__(256) tri_inverse_kernel(const SqJob* jobs) {
+  const SqJob J = jobs[blockIdx.x];
+  const int n = J.n;
+  for (int j = threadIdx.x; j < n; j += blockDim.x) {
+    for (int i = n - 1; i >= 0; --i) {
+      double v = 0.0;
+      if (i <= j) {
+        v = i == j ? 1.0 : 0.0;
+        for (int c = i + 1; c <= j; ++c) v = fma(-J.R[(int64_t)i * n + c], J.C[(int64_t)c * n + j], v);
+        v /= J.R[(int64_t)i * n + i];
+      }
+      J.C[(int64_t)i * n + j] = v;
+    }
+  }
+}
+
+// Adjoint of a sign-permute job table: the forward wrote dst[dst position] =
+// sign * src[src position] for every element of every job; this writes
+// src[src position] = sign * dst[dst position] (one CTA per job).
+__global__ void __launch_bounds__(256) perm_adjoint_kernel(const PermJob* jobs, const double* __restrict__ dst,
+                                                           double* __restrict__ src) {
+  const PermJob& J = jobs[blockIdx.x];
+  const int nl = J.nI + J.nO + J.nB;
+  int64_t total = 1;
+  for (int l = 0; l < nl; ++l) total *= J.dim[l];
+  const double sg = (double)J.sign;
+  for (int64_t e = threadIdx.x; e < total; e += blockDim.x) {
+    int64_t x = e, so = J.src_off, dof = J.dst_off;
+    for (int l = nl - 1; l >= 0; --l) {
+      const int64_t q = x / J.dim[l];
+      const int64_t i = x - q * J.dim[l];
+      so += i * J.sstr[l];
+      dof += i * J.dstr[l];
+      x = q;
+    }
+    src[so] = sg * dst[dof];
+  }
+}
+
+// out[m, c] += a[m, c] (rows x cols; row strides lda, ldo)
+struct Add2Job {
+  const double* a;
+  double* out;
+  int rows, cols;
+  int64_t lda, ldo;
+};
+__global__ void __launch_bounds__(256) add2_kernel(const Add2Job* jobs) {
+  const Add2Job J = jobs[blockIdx.x];
+  for (int64_t e = threadIdx.x; e < (int64_t)J.rows * J.cols; e += blockDim.x) {
+    const int m = (int)(e / J.cols), c = (int)(e - (int64_t)m * J.cols);
+    J.out[m * J.ldo + c] += J.a[m * J.lda + c];
+  }
+}
+
+template <typename T>
+ftn_status launch_jobs(ftn_ctx ctx, void (*k)(const T*), const std::vector<T>& jobs) {
+  if (jobs.empty()) return FTN_OK;
+  DevBuf t(ctx);
+  FTN_TRY(put_table(ctx, jobs, &t.p));
+  k<<<(unsigned)jobs.size(), 256, 0, ctx->stream>>>((const T*)t.p);
+  ctx->launches += 1;
+  FTN_CUDA(cudaGetLastError());
+  return FTN_OK;
+}
+
 }  // namespace
 
 namespace {
@@ -1258,6 +1458,308 @@ void cj_truncate(CJob& J, const double* sv) {
   }
 }
 
+// ---- backward pass of the compression (ftn_compress_grad) -------------------
+// Per job with cotangents and per bond-parity sector with kept states, in the
+// projector form of the forward (A, B the fused sector matrices, M = R_X R_Y^T
+// = U S V^T over its r singular triplets, Z = S_k^-1/2 V_k^T, W = S_k^-1/2 U_k^T):
+//   X' = A R_Y^T Z^T,  Y' = W R_X B^T.
+// With E_A = dX'^T A and E_B = dY' B (k x K):
+//   dZ = E_A R_Y^T and dW = E_B R_X^T give dV, dU and dS (through S^-1/2);
+//   dM = the thin-SVD adjoint (the rule of oracle/compress_adjoint.py) over
+//        all r triplets, F_ij = 1 / (s_j^2 - s_i^2) where i or j is kept;
+//   dR_X = W^T E_B + dM R_Y,  dR_Y = Z^T E_A + dM^T R_X;
+//   dA = dX' Z R_Y + QR'(A, R_X, dR_X),  dB = dY'^T W R_X + QR'(B, R_Y, dR_Y),
+// with QR'(A, R, dR) = A R^-1 copyltu(R dR^T) R^-T for a factored side (R
+// square, full rank; no cotangent reaches Q: the projector form never forms
+// it) and dR itself for a side that is its own factor; then the adjoint of
+// the sign-permutes gives dX and dY.  Valid where the compression is
+// differentiable (a gap at the cut, distinct nonzero singular values, full
+// rank blocks); sides with dropped rows or a core with a zero singular value
+// are reported as unsupported.
+ftn_status cj_backward(ftn_ctx ctx, std::vector<CJob*>& gj, const std::vector<double>& sv, const double* sbuf) {
+  struct Sec {
+    CJob* J;
+    int pi, Ma, Nb, K, ldk, rx, ry, r, ml, k;
+    bool fx, fy;
+    const double *A, *B, *RX, *RY, *Ms, *Tf, *Z, *W, *PA, *QB, *s;
+    double *dXf, *dYt, *EA, *EB, *Rot, *Oth, *Ut, *Vt, *dZ, *dW, *dRX1, *dRY1, *dUt, *dVt, *ds, *X, *Y, *inner,
+        *XU, *YV, *Pt, *Qt, *T1, *SV, *dMa, *dMb, *dRX2, *dRY2, *dAd, *dBd, *RdRx, *Rix, *Hx, *Gx, *dAq, *RdRy, *Riy,
+        *Hy, *Gy, *dBq;
+    int *idx, *kept;
+  };
+  std::vector<Sec> secs;
+  std::vector<std::unique_ptr<DevBuf>> bufs;
+  std::vector<double*> dAf(gj.size()), dBf(gj.size());
+  for (size_t q = 0; q < gj.size(); ++q) {
+    CJob& J = *gj[q];
+    const TdPlan* P = J.P.get();
+    std::vector<Sec> js;
+    int64_t tot = P->af_elems + P->bf_elems;
+    for (int pi = 0; pi < 2; ++pi) {
+      if (J.k[pi] == 0) continue;
+      Sec c{};
+      c.J = &J;
+      c.pi = pi;
+      c.Ma = (int)P->M[pi], c.Nb = (int)P->N[pi], c.K = (int)P->K[pi], c.ldk = (int)P->ldk[pi];
+      c.rx = J.rx[pi], c.ry = J.ry[pi], c.r = J.nrot[pi], c.ml = J.mlen[pi], c.k = J.k[pi];
+      c.fx = J.tall_x[pi], c.fy = J.tall_y[pi];
+      if (c.rx != J.rx0[pi] || c.ry != J.ry0[pi])
+        return set_error(FTN_EUNSUPPORTED, "compression adjoint: a sector block is rank deficient (its factor has "
+                                           "dropped rows)");
+      for (int j = 0; j < c.r; ++j)
+        if (!(sv[J.s_off[pi] + j] > 0.0))
+          return set_error(FTN_EUNSUPPORTED, "compression adjoint: the core has a zero singular value");
+      const int64_t K = c.K, r = c.r, k = c.k, rx = c.rx, ry = c.ry;
+      tot += c.Ma * k + k * c.Nb + 2 * k * K + r * c.ml + r * r + k * ry + k * rx + (rx + ry) * K * 3 + r * (rx + ry) +
+             r + 3 * r * r + 2 * r * (rx + ry) + 2 * r * ry + 2 * rx * ry + (c.Ma + c.Nb) * K +
+             (c.fx ? 4 * K * K + c.Ma * K : 0) + (c.fy ? 4 * K * K + c.Nb * K : 0) + (k + r + 2) / 2 + 8;
+      js.push_back(c);
+    }
+    bufs.emplace_back(new DevBuf(ctx));
+    bufs.back()->p = dev_alloc(ctx, (size_t)(tot + 64) * 8);
+    if (!bufs.back()->p) return set_error(FTN_ENOMEM, "compression adjoint: workspace allocation failed");
+    double* p = (double*)bufs.back()->p;
+    dAf[q] = p;
+    p += P->af_elems;
+    dBf[q] = p;
+    p += P->bf_elems;
+    FTN_CUDA(cudaMemsetAsync(dAf[q], 0, (size_t)(P->af_elems + P->bf_elems) * 8, ctx->stream));
+    for (Sec& c : js) {
+      const int64_t K = c.K, r = c.r, k = c.k, rx = c.rx, ry = c.ry;
+      auto take = [&](int64_t n) {
+        double* x = p;
+        p += n;
+        return x;
+      };
+      c.dXf = take(c.Ma * k), c.dYt = take(k * c.Nb), c.EA = take(k * K), c.EB = take(k * K);
+      c.Rot = take(r * c.ml), c.Oth = take(r * r), c.dZ = take(k * ry), c.dW = take(k * rx);
+      c.dRX1 = take(rx * K), c.dRY1 = take(ry * K), c.dUt = take(r * rx), c.dVt = take(r * ry), c.ds = take(r);
+      c.X = take(r * r), c.Y = take(r * r), c.inner = take(r * r), c.XU = take(r * rx), c.YV = take(r * ry);
+      c.Pt = take(r * rx), c.Qt = take(r * ry), c.T1 = take(r * ry), c.SV = take(r * ry);
+      c.dMa = take(rx * ry), c.dMb = take(rx * ry), c.dRX2 = take(rx * K), c.dRY2 = take(ry * K);
+      c.dAd = take(c.Ma * K), c.dBd = take(c.Nb * K);
+      c.RdRx = c.Rix = c.Hx = c.Gx = c.dAq = c.RdRy = c.Riy = c.Hy = c.Gy = c.dBq = nullptr;
+      if (c.fx) c.RdRx = take(K * K), c.Rix = take(K * K), c.Hx = take(K * K), c.Gx = take(K * K), c.dAq = take(c.Ma * K);
+      if (c.fy) c.RdRy = take(K * K), c.Riy = take(K * K), c.Hy = take(K * K), c.Gy = take(K * K), c.dBq = take(c.Nb * K);
+      c.idx = reinterpret_cast<int*>(p);
+      c.kept = c.idx + k;
+      p += (k + r + 2) / 2 + 1;
+      CJob& J = *c.J;
+      c.A = J.ws + J.o_xf + P->afoff[c.pi];
+      c.B = J.ws + J.o_yf + P->bfoff[c.pi];
+      c.RX = J.ws + J.o_rxc[c.pi], c.RY = J.ws + J.o_ryc[c.pi];
+      c.Ms = J.ws + J.o_m[c.pi], c.Tf = J.ws + J.o_tf[c.pi];
+      c.Z = J.ws + J.o_zk[c.pi], c.W = J.ws + J.o_wk[c.pi];
+      c.PA = J.ws + J.o_px[c.pi], c.QB = J.ws + J.o_qy[c.pi];
+      c.s = sbuf + J.s_off[c.pi];
+      // rotated rows give V (the core stored as M) or U (stored as M^T)
+      c.Ut = J.trans[c.pi] ? c.Rot : c.Oth;
+      c.Vt = J.trans[c.pi] ? c.Oth : c.Rot;
+      // kept states in new-bond order -> Jacobi rows; kept flags per row
+      std::vector<int> hk(k + r, 0);
+      int j = 0;
+      for (auto& cd : J.kept)
+        if (cd.pi == c.pi) hk[j++] = cd.idx;
+      for (int t = 0; t < k; ++t) hk[k + hk[t]] = 1;
+      FTN_CUDA(cudaMemcpyAsync(c.idx, hk.data(), hk.size() * sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
+      // cotangents in the fused sector coordinates: dX' rows as A's rows,
+      // dY'^T columns as B's rows
+      ftn_tensor gX = J.it->gXn, gY = J.it->gYn;
+      const int nfa = P->nfa, nfb = P->nfb;
+      for (uint32_t mA = 0; mA < (1u << nfa); ++mA) {
+        if ((popc(mA) & 1) != (J.it->X->parity ^ c.pi) || P->rowsz[c.pi][mA] == 0) continue;
+        const uint32_t mask = mA | ((uint32_t)c.pi << nfa);
+        FTN_CUDA(cudaMemcpyAsync(c.dXf + P->rowoff[c.pi][mA] * k, (const double*)gX->data + gX->offsets[mask >> 1],
+                                 (size_t)P->rowsz[c.pi][mA] * k * 8, cudaMemcpyDeviceToDevice, ctx->stream));
+      }
+      for (uint32_t mB = 0; mB < (1u << nfb); ++mB) {
+        if ((popc(mB) & 1) != (J.it->Y->parity ^ c.pi) || P->colsz[c.pi][mB] == 0) continue;
+        const uint32_t mask = (uint32_t)c.pi | (mB << 1);
+        const int64_t cm = P->colsz[c.pi][mB];
+        FTN_CUDA(cudaMemcpy2DAsync(c.dYt + P->coloff[c.pi][mB], (size_t)c.Nb * 8,
+                                   (const double*)gY->data + gY->offsets[mask >> 1], (size_t)cm * 8, (size_t)cm * 8,
+                                   (size_t)k, cudaMemcpyDeviceToDevice, ctx->stream));
+      }
+      secs.push_back(c);
+    }
+  }
+  // C[m, n] = sum_k A[m, k] B[n, k] from absolute operand pointers (strides in
+  // elements), row-major C with row stride ldc
+  auto gemm = [&](GemmF64Batch& gb, int M, int N, int Kd, const double* a, int64_t a_sm, int64_t a_sk,
+                  const double* b, int64_t b_sn, int64_t b_sk, double* cc, int64_t ldc) -> ftn_status {
+    if (M <= 0 || N <= 0) return FTN_OK;
+    std::vector<GemmProb> v{make_prob(M, N, Kd, 0, a_sm, a_sk, 0, b_sn, b_sk)};
+    gemm_plain_output(v[0], 0, ldc);
+    const int64_t an = Kd > 0 ? (int64_t)(M - 1) * a_sm + (int64_t)(Kd - 1) * a_sk + 1 : 1;
+    const int64_t bn = Kd > 0 ? (int64_t)(N - 1) * b_sn + (int64_t)(Kd - 1) * b_sk + 1 : 1;
+    return add_gemm_set(gb, v, a, b, cc, an, bn, (int64_t)(M - 1) * ldc + N);
+  };
+  auto stage = [&](auto&& body) -> ftn_status {
+    GemmF64Batch gb(ctx);
+    for (Sec& c : secs) FTN_TRY(body(gb, c));
+    return flush_gemm_f64(gb);
+  };
+  // E_A = dX'^T A, E_B = dY' B; the rotated rows over their singular values
+  FTN_TRY(stage([&](GemmF64Batch& gb, Sec& c) -> ftn_status {
+    FTN_TRY(gemm(gb, c.k, c.K, c.Ma, c.dXf, 1, c.k, c.A, 1, c.ldk, c.EA, c.K));
+    return gemm(gb, c.k, c.K, c.Nb, c.dYt, c.Nb, 1, c.B, 1, c.ldk, c.EB, c.K);
+  }));
+  {
+    std::vector<RowDivJob> rd;
+    for (Sec& c : secs) rd.push_back({c.Tf, c.Rot, c.s, c.r, c.ml});
+    FTN_TRY(launch_jobs(ctx, row_div_kernel, rd));
+  }
+  // the other side's vectors (stored core times the rotated ones); dZ, dW, and
+  // the direct parts of dR_X, dR_Y
+  FTN_TRY(stage([&](GemmF64Batch& gb, Sec& c) -> ftn_status {
+    FTN_TRY(gemm(gb, c.r, c.r, c.ml, c.Rot, c.ml, 1, c.Ms, c.ml, 1, c.Oth, c.r));
+    FTN_TRY(gemm(gb, c.k, c.ry, c.K, c.EA, c.K, 1, c.RY, c.K, 1, c.dZ, c.ry));
+    FTN_TRY(gemm(gb, c.k, c.rx, c.K, c.EB, c.K, 1, c.RX, c.K, 1, c.dW, c.rx));
+    FTN_TRY(gemm(gb, c.ry, c.K, c.k, c.Z, 1, c.ry, c.EA, 1, c.K, c.dRY1, c.K));
+    return gemm(gb, c.rx, c.K, c.k, c.W, 1, c.rx, c.EB, 1, c.K, c.dRX1, c.K);
+  }));
+  {
+    std::vector<RowDivJob> rd;
+    std::vector<CotJob> cj;
+    for (Sec& c : secs) {
+      rd.push_back({c.Oth, c.Oth, c.s, c.r, c.r});
+      cj.push_back({c.dZ, c.dW, c.Ut, c.Vt, c.s, c.idx, c.dUt, c.dVt, c.ds, c.k, c.r, c.rx, c.ry});
+    }
+    FTN_TRY(launch_jobs(ctx, row_div_kernel, rd));
+    FTN_TRY(launch_jobs(ctx, svd_cot_kernel, cj));
+  }
+  // X = U^T dU, Y = V^T dV, then X^T Ut and Y^T Vt
+  FTN_TRY(stage([&](GemmF64Batch& gb, Sec& c) -> ftn_status {
+    FTN_TRY(gemm(gb, c.r, c.r, c.rx, c.Ut, c.rx, 1, c.dUt, c.rx, 1, c.X, c.r));
+    return gemm(gb, c.r, c.r, c.ry, c.Vt, c.ry, 1, c.dVt, c.ry, 1, c.Y, c.r);
+  }));
+  FTN_TRY(stage([&](GemmF64Batch& gb, Sec& c) -> ftn_status {
+    FTN_TRY(gemm(gb, c.r, c.rx, c.r, c.X, 1, c.r, c.Ut, 1, c.rx, c.XU, c.rx));
+    return gemm(gb, c.r, c.ry, c.r, c.Y, 1, c.r, c.Vt, 1, c.ry, c.YV, c.ry);
+  }));
+  {
+    std::vector<InnerJob> ij;
+    std::vector<AxpyJob> ax;
+    for (Sec& c : secs) {
+      ij.push_back({c.X, c.Y, c.s, c.ds, c.kept, c.inner, c.r});
+      ax.push_back({c.dUt, c.XU, c.Pt, nullptr, nullptr, (int64_t)c.r * c.rx, c.rx, -1.0});  // (I - U U^T) dU
+      ax.push_back({c.dVt, c.YV, c.Qt, nullptr, nullptr, (int64_t)c.r * c.ry, c.ry, -1.0});  // (I - V V^T) dV
+    }
+    FTN_TRY(launch_jobs(ctx, svd_inner_kernel, ij));
+    FTN_TRY(launch_jobs(ctx, axpy_kernel, ax));
+  }
+  FTN_TRY(stage([&](GemmF64Batch& gb, Sec& c) -> ftn_status {
+    return gemm(gb, c.r, c.ry, c.r, c.inner, c.r, 1, c.Vt, 1, c.ry, c.T1, c.ry);
+  }));
+  {
+    std::vector<AxpyJob> ax;
+    for (Sec& c : secs) {
+      ax.push_back({c.T1, c.Qt, c.T1, c.s, c.kept, (int64_t)c.r * c.ry, c.ry, 1.0});     // inner V^T + S^-1 dV^T (I - V V^T)
+      ax.push_back({nullptr, c.Vt, c.SV, c.s, c.kept, (int64_t)c.r * c.ry, c.ry, 1.0});  // S^-1 V^T
+    }
+    FTN_TRY(launch_jobs(ctx, axpy_kernel, ax));
+  }
+  // dM = U (inner V^T + S^-1 dV^T (I - V V^T)) + (I - U U^T) dU S^-1 V^T
+  FTN_TRY(stage([&](GemmF64Batch& gb, Sec& c) -> ftn_status {
+    FTN_TRY(gemm(gb, c.rx, c.ry, c.r, c.Ut, 1, c.rx, c.T1, 1, c.ry, c.dMa, c.ry));
+    return gemm(gb, c.rx, c.ry, c.r, c.Pt, 1, c.rx, c.SV, 1, c.ry, c.dMb, c.ry);
+  }));
+  {
+    std::vector<AxpyJob> ax;
+    for (Sec& c : secs) ax.push_back({c.dMa, c.dMb, c.dMa, nullptr, nullptr, (int64_t)c.rx * c.ry, c.ry, 1.0});
+    FTN_TRY(launch_jobs(ctx, axpy_kernel, ax));
+  }
+  // dR_X = W^T E_B + dM R_Y, dR_Y = Z^T E_A + dM^T R_X
+  FTN_TRY(stage([&](GemmF64Batch& gb, Sec& c) -> ftn_status {
+    FTN_TRY(gemm(gb, c.rx, c.K, c.ry, c.dMa, c.ry, 1, c.RY, 1, c.K, c.dRX2, c.K));
+    return gemm(gb, c.ry, c.K, c.rx, c.dMa, 1, c.ry, c.RX, 1, c.K, c.dRY2, c.K);
+  }));
+  {
+    std::vector<AxpyJob> ax;
+    for (Sec& c : secs) {
+      ax.push_back({c.dRX1, c.dRX2, c.dRX1, nullptr, nullptr, (int64_t)c.rx * c.K, c.K, 1.0});
+      ax.push_back({c.dRY1, c.dRY2, c.dRY1, nullptr, nullptr, (int64_t)c.ry * c.K, c.K, 1.0});
+    }
+    FTN_TRY(launch_jobs(ctx, axpy_kernel, ax));
+  }
+  // factored sides: R dR^T, R^-1
+  FTN_TRY(stage([&](GemmF64Batch& gb, Sec& c) -> ftn_status {
+    if (c.fx) FTN_TRY(gemm(gb, c.K, c.K, c.K, c.RX, c.K, 1, c.dRX1, c.K, 1, c.RdRx, c.K));
+    if (c.fy) FTN_TRY(gemm(gb, c.K, c.K, c.K, c.RY, c.K, 1, c.dRY1, c.K, 1, c.RdRy, c.K));
+    return FTN_OK;
+  }));
+  {
+    std::vector<SqJob> cl, ti;
+    for (Sec& c : secs) {
+      if (c.fx) cl.push_back({c.RdRx, nullptr, c.K}), ti.push_back({c.Rix, c.RX, c.K});
+      if (c.fy) cl.push_back({c.RdRy, nullptr, c.K}), ti.push_back({c.Riy, c.RY, c.K});
+    }
+    FTN_TRY(launch_jobs(ctx, copyltu_kernel, cl));
+    FTN_TRY(launch_jobs(ctx, tri_inverse_kernel, ti));
+  }
+  // H = R^-1 copyltu(R dR^T), G = H R^-T, then A G
+  FTN_TRY(stage([&](GemmF64Batch& gb, Sec& c) -> ftn_status {
+    if (c.fx) FTN_TRY(gemm(gb, c.K, c.K, c.K, c.Rix, c.K, 1, c.RdRx, 1, c.K, c.Hx, c.K));
+    if (c.fy) FTN_TRY(gemm(gb, c.K, c.K, c.K, c.Riy, c.K, 1, c.RdRy, 1, c.K, c.Hy, c.K));
+    return FTN_OK;
+  }));
+  FTN_TRY(stage([&](GemmF64Batch& gb, Sec& c) -> ftn_status {
+    if (c.fx) FTN_TRY(gemm(gb, c.K, c.K, c.K, c.Hx, c.K, 1, c.Rix, c.K, 1, c.Gx, c.K));
+    if (c.fy) FTN_TRY(gemm(gb, c.K, c.K, c.K, c.Hy, c.K, 1, c.Riy, c.K, 1, c.Gy, c.K));
+    return FTN_OK;
+  }));
+  // A G (factored) and the direct parts dX' P_X^T, dY'^T Q_Y^T
+  FTN_TRY(stage([&](GemmF64Batch& gb, Sec& c) -> ftn_status {
+    if (c.fx) FTN_TRY(gemm(gb, c.Ma, c.K, c.K, c.A, c.ldk, 1, c.Gx, 1, c.K, c.dAq, c.K));
+    if (c.fy) FTN_TRY(gemm(gb, c.Nb, c.K, c.K, c.B, c.ldk, 1, c.Gy, 1, c.K, c.dBq, c.K));
+    FTN_TRY(gemm(gb, c.Ma, c.K, c.k, c.dXf, c.k, 1, c.PA, 1, c.K, c.dAd, c.K));
+    return gemm(gb, c.Nb, c.K, c.k, c.dYt, 1, c.Nb, c.QB, 1, c.K, c.dBd, c.K);
+  }));
+  {
+    std::vector<Add2Job> ad;
+    for (Sec& c : secs) {
+      const TdPlan* P = c.J->P.get();
+      const size_t q = std::find(gj.begin(), gj.end(), c.J) - gj.begin();
+      double* da = dAf[q] + P->afoff[c.pi];
+      double* db = dBf[q] + P->bfoff[c.pi];
+      ad.push_back({c.dAd, da, c.Ma, c.K, c.K, c.ldk});
+      ad.push_back({c.fx ? c.dAq : c.dRX1, da, c.Ma, c.K, c.K, c.ldk});  // a side that is its own factor: rx = Ma
+      ad.push_back({c.dBd, db, c.Nb, c.K, c.K, c.ldk});
+      ad.push_back({c.fy ? c.dBq : c.dRY1, db, c.Nb, c.K, c.K, c.ldk});
+    }
+    // the four adds of a sector touch the same rows: one launch each, in order
+    for (int w = 0; w < 4; ++w) {
+      std::vector<Add2Job> one;
+      for (size_t i = w; i < ad.size(); i += 4) one.push_back(ad[i]);
+      FTN_TRY(launch_jobs(ctx, add2_kernel, one));
+    }
+  }
+  // dX, dY: the adjoint of the forward's sign-permutes
+  for (size_t q = 0; q < gj.size(); ++q) {
+    CJob& J = *gj[q];
+    const TdPlan* P = J.P.get();
+    ftn_tensor X = J.it->X, Y = J.it->Y;
+    int32_t xd0[MAXR], xd1[MAXR], yd0[MAXR], yd1[MAXR];
+    for (int l = 0; l < X->rank; ++l) xd0[l] = X->d0[l], xd1[l] = X->d1[l];
+    for (int l = 0; l < Y->rank; ++l) yd0[l] = Y->d0[l], yd1[l] = Y->d1[l];
+    FTN_TRY(make_tensor(ctx, X->rank, xd0, xd1, X->dual, X->parity, FTN_F64, &J.it->dX));
+    FTN_TRY(make_tensor(ctx, Y->rank, yd0, yd1, Y->dual, Y->parity, FTN_F64, &J.it->dY));
+    FTN_CUDA(cudaMemsetAsync(J.it->dX->data, 0, (size_t)J.it->dX->numel * 8, ctx->stream));
+    FTN_CUDA(cudaMemsetAsync(J.it->dY->data, 0, (size_t)J.it->dY->numel * 8, ctx->stream));
+    for (int side = 0; side < 2; ++side) {
+      const std::vector<PermJob>& jb = side ? P->jb : P->ja;
+      if (jb.empty()) continue;
+      DevBuf t(ctx);
+      FTN_TRY(put_table(ctx, jb, &t.p));
+      perm_adjoint_kernel<<<(unsigned)jb.size(), 256, 0, ctx->stream>>>(
+          (const PermJob*)t.p, side ? dBf[q] : dAf[q], (double*)(side ? J.it->dY->data : J.it->dX->data));
+      ctx->launches += 1;
+      FTN_CUDA(cudaGetLastError());
+    }
+  }
+  return FTN_OK;
+}
+
 }  // namespace
 
 // Batched compression: every stage of every job contributes to one launch
@@ -1537,10 +2039,13 @@ ftn_status compress_batch(ftn_ctx ctx, std::vector<CompressItem>& items) {
     for (size_t q = 0; q < jobs.size(); ++q) every[q] = q;
     FTN_TRY(core_svd(every));
   }
+  std::vector<double> sv_host;  // singular values (Jacobi order) and sweep counts, kept for the adjoint
   // ---- 4. pooled truncation (one synchronisation for the singular values and
   //      the residual norms; a second only when a residual test failed) ----
   {
-    std::vector<double> sv(s_total + 1), hk(chk_words);
+    std::vector<double>& sv = sv_host;
+    sv.assign(s_total + 1, 0.0);
+    std::vector<double> hk(chk_words);
     if (s_total) FTN_CUDA(cudaMemcpyAsync(sv.data(), sbuf, s_total * 8, cudaMemcpyDeviceToHost, ctx->stream));
     if (residual_pending)
       FTN_CUDA(cudaMemcpyAsync(hk.data(), chk, chk_words * 8, cudaMemcpyDeviceToHost, ctx->stream));
@@ -1722,8 +2227,31 @@ ftn_status compress_batch(ftn_ctx ctx, std::vector<CompressItem>& items) {
     }
     FTN_TRY(flush_gemm_f64(gb));
   }
+  // ---- 6. adjoint, for the items that carry cotangents of the new pair ----
+  {
+    std::vector<CJob*> gj;
+    for (CJob& J : jobs) {
+      if (!J.it->gXn && !J.it->gYn) continue;
+      const ftn_tensor g[2] = {J.it->gXn, J.it->gYn}, t[2] = {J.Xn, J.Yn};
+      for (int w = 0; w < 2; ++w) {
+        bool ok = g[w] && g[w]->dtype == FTN_F64 && g[w]->rank == t[w]->rank && g[w]->parity == t[w]->parity;
+        for (int l = 0; ok && l < t[w]->rank; ++l)
+          ok = g[w]->d0[l] == t[w]->d0[l] && g[w]->d1[l] == t[w]->d1[l] && g[w]->dual[l] == t[w]->dual[l];
+        if (!ok)
+          return set_error(FTN_ESHAPE, "compression adjoint: a cotangent does not have the legs, parity and FP64 "
+                                       "type of the compressed tensor");
+      }
+      gj.push_back(&J);
+    }
+    if (!gj.empty()) FTN_TRY(cj_backward(ctx, gj, sv_host, sbuf));
+  }
   outs.ok = true;
   for (CJob& J : jobs) {
+    if (J.it->gXn || J.it->gYn) {  // the adjoint keeps the inputs; the forward pair was only needed here
+      ftn_tensor_free(J.Xn);
+      ftn_tensor_free(J.Yn);
+      continue;
+    }
     ftn_tensor_free(J.it->X);
     ftn_tensor_free(J.it->Y);
     J.it->X = J.Xn;
@@ -1755,6 +2283,34 @@ ftn_status compress_impl(ftn_ctx ctx, ftn_tensor* pX, ftn_tensor* pY, int n, con
 }  // namespace ftn
 
 using namespace ftn;
+
+extern "C" ftn_status ftn_compress_grad(ftn_ctx ctx, ftn_tensor X, ftn_tensor Y, int n, const int* axes_x,
+                                        const int* axes_y, int chi, int arrows, ftn_tensor dXn, ftn_tensor dYn,
+                                        ftn_tensor* dX, ftn_tensor* dY) {
+  if (!ctx || !X || !Y || !dXn || !dYn || !dX || !dY || (n > 0 && (!axes_x || !axes_y)))
+    return set_error(FTN_EINVAL, "null argument");
+  if (n < 1) return set_error(FTN_EINVAL, "a bond needs at least one leg pair");
+  if (n > MAXR) return set_error(FTN_EINVAL, "too many bond legs");
+  std::vector<CompressItem> items(1);
+  CompressItem& it = items[0];
+  it.X = X;
+  it.Y = Y;
+  it.n = n;
+  for (int i = 0; i < n; ++i) it.ax[i] = axes_x[i], it.ay[i] = axes_y[i];
+  it.chi = chi;
+  it.arrows = arrows;
+  it.gXn = dXn;
+  it.gYn = dYn;
+  const ftn_status st = compress_batch(ctx, items);
+  if (st != FTN_OK) {
+    ftn_tensor_free(it.dX);
+    ftn_tensor_free(it.dY);
+    return st;
+  }
+  *dX = it.dX;
+  *dY = it.dY;
+  return FTN_OK;
+}
 
 extern "C" ftn_status ftn_compress(ftn_ctx ctx, ftn_tensor* X, ftn_tensor* Y, int n, const int* axes_x,
                                    const int* axes_y, int chi, int arrows, ftn_compress_info* info) {

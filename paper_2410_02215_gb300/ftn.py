@@ -85,6 +85,7 @@ def lib():
         "ftn_tensordot_grad": [vp, vp, vp, vp, C.c_int, ip, ip, C.c_uint64, C.c_uint64, ip, C.c_int, C.POINTER(vp),
                                C.POINTER(vp)],
         "ftn_compress": [vp, C.POINTER(vp), C.POINTER(vp), C.c_int, ip, ip, C.c_int, C.c_int, C.POINTER(CompressInfo)],
+        "ftn_compress_grad": [vp, vp, vp, C.c_int, ip, ip, C.c_int, C.c_int, vp, vp, C.POINTER(vp), C.POINTER(vp)],
         "ftn_contract": [vp, C.POINTER(Network), C.POINTER(Tree), C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double)],
         "ftn_contract_batch": [vp, C.c_int, C.POINTER(Network), C.POINTER(Tree), C.c_int, C.POINTER(C.c_double),
                                C.POINTER(C.c_double)],
@@ -476,6 +477,16 @@ def compress(ctx, x, y, axes_x, axes_y, chi, arrows=True):
     x.handle = None
     y.handle = None
     return Tensor(ctx, hx), Tensor(ctx, hy), info
+
+
+def compress_grad(ctx, x, y, axes_x, axes_y, chi, dxn, dyn, arrows=True):
+    """Gradient of a scalar of the compressed pair (ftn_compress_grad): given
+    dL/dX' and dL/dY' (tensors with the legs of compress(...)'s X' and Y'),
+    returns (dL/dX, dL/dY); x and y are left unchanged."""
+    hx, hy = C.c_void_p(), C.c_void_p()
+    _check(lib().ftn_compress_grad(ctx.handle, x.handle, y.handle, len(axes_x), _int(axes_x), _int(axes_y), int(chi),
+                                   1 if arrows else 0, dxn.handle, dyn.handle, C.byref(hx), C.byref(hy)))
+    return Tensor(ctx, hx), Tensor(ctx, hy)
 
 
 def contract(ctx, tensors, bonds, tree, positions=None, policy="exact", chi=0, prec="f64"):
