@@ -298,8 +298,10 @@ FTN_API ftn_status ftn_compress(ftn_ctx ctx, ftn_tensor* X, ftn_tensor* Y, int n
  * kept vectors) and of the R factors, then the adjoint of the
  * sign-permutes.  Defined where the compression is differentiable: a gap at
  * the truncation cut, distinct nonzero singular values, full-rank sector
- * blocks; a block whose factor drops rows or a core with a zero singular
- * value gives FTN_EUNSUPPORTED, cotangents of the wrong shape FTN_ESHAPE.  A
+ * blocks; a block whose factor drops rows gives FTN_EUNSUPPORTED, cotangents
+ * of the wrong shape FTN_ESHAPE.  Singular values of a core at or below
+ * 1e-12 of its largest count as zero: their directions are left to the
+ * complements the rule projects onto (a relative error of that order).  A
  * loss that depends on the gauge of the new bond (signs of its states) has
  * no well-defined gradient.  FP64 throughout; synchronises as ftn_compress. */
 FTN_API ftn_status ftn_compress_grad(ftn_ctx ctx, ftn_tensor X, ftn_tensor Y, int n, const int* axes_x,
@@ -359,6 +361,23 @@ FTN_API ftn_status ftn_contract(ftn_ctx ctx, const ftn_network* net, const ftn_t
  * compression, twice per sub-round of compressions. */
 FTN_API ftn_status ftn_contract_batch(ftn_ctx ctx, int count, const ftn_network* nets, const ftn_tree* trees,
                               ftn_prec prec, double* mantissa, double* log_scale);
+
+/* Value of a closed network of even FP64 tensors and its gradient with
+ * respect to every tensor of the network (each tensor an independent input,
+ * a bra that is the dagger of a ket included): *value = v (plain FP64, no
+ * per-step normalisation, so v must stay within FP64's range) and grads[i] =
+ * dv/dT_i, a new library-owned tensor with T_i's legs, for i < n_tensors.
+ * The forward is ftn_contract's walk of the tree (same pairs, flips, phases,
+ * and late / early compressions of the same bonds); the backward passes each
+ * result's cotangent to its operands by ftn_tensordot_grad and each
+ * compression's by ftn_compress_grad, in reverse order (the paper gives no
+ * gradient; variational fPEPS optimisation needs one, Sec. II.D).  Defined
+ * where every compression is differentiable (ftn_compress_grad's
+ * conditions; FTN_EUNSUPPORTED otherwise) and for even tensors only.  Keeps
+ * every intermediate until the call returns; synchronises at the end and
+ * as every compression does. */
+FTN_API ftn_status ftn_contract_grad(ftn_ctx ctx, const ftn_network* net, const ftn_tree* tree, double* value,
+                             ftn_tensor* grads);
 
 /* ---- expectation values of local terms (Sec. V) --------------------------- */
 

@@ -130,6 +130,9 @@ struct CompressItem {
   // receive the gradient with respect to them
   ftn_tensor gXn = nullptr, gYn = nullptr;
   ftn_tensor dX = nullptr, dY = nullptr;
+  // keep X and Y (the caller still owns them) while X, Y are replaced by the
+  // compressed pair
+  bool keep_inputs = false;
 };
 // ftn_compress for every item (FP64 tensors).
 ftn_status compress_batch(ftn_ctx ctx, std::vector<CompressItem>& items);

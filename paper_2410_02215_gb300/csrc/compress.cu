@@ -964,19 +964,22 @@ ftn_status launch_svd_cluster(ftn_ctx ctx, const SvdJob* jobs, int njobs, int C,
 // vector), the kept vectors W = S^-1/2 U_k^T and Z = S^-1/2 V_k^T.  Products
 // go through the FP64 GEMM; these kernels do the rest (one CTA per matrix).
 
-// out[j, c] = in[j, c] / s[j] (rows x cols, row strides ld_in / ld_out)
+// out[j, c] = in[j, c] / s[j] for s[j] > tol, 0 otherwise (rows x cols,
+// contiguous rows): a singular direction at or below tol is left out of the
+// rebuilt factors and falls into the complements the adjoint projects onto
 struct RowDivJob {
   const double* in;
   double* out;
   const double* s;
   int rows, cols;
+  double tol;
 };
 __global__ void __launch_bounds__(256) row_div_kernel(const RowDivJob* jobs) {
   const RowDivJob J = jobs[blockIdx.x];
   const int64_t n = (int64_t)J.rows * J.cols;
   for (int64_t e = threadIdx.x; e < n; e += blockDim.x) {
     const int j = (int)(e / J.cols);
-    J.out[e] = J.in[e] / J.s[j];
+    J.out[e] = J.s[j] > J.tol ? J.in[e] / J.s[j] : 0.0;
   }
 }
 
@@ -1024,13 +1027,15 @@ __global__ void __launch_bounds__(256) svd_cot_kernel(const CotJob* jobs) {
 // The core of the thin-SVD adjoint (r x r, Jacobi order):
 //   inner = (F o (X - X^T)) S + diag(ds) + S (F o (Y - Y^T)),
 // X = U^T dU, Y = V^T dV, F_ij = 1 / (s_j^2 - s_i^2) for i != j with i or j
-// kept (pairs of discarded states carry no cotangent), 0 otherwise.
+// kept (pairs of discarded states carry no cotangent) and neither left out
+// (a direction left out belongs to the complements: its terms are those of
+// the projections), 0 otherwise.
 struct InnerJob {
   const double* X;
   const double* Y;
   const double* s;
   const double* ds;
-  const int* kept;  // r flags
+  const int* kept;  // r flags: 1 kept, 0 discarded, -1 left out (singular value at rounding level)
   double* inner;
   int r;
 };
@@ -1042,7 +1047,7 @@ __global__ void __launch_bounds__(256) svd_inner_kernel(const InnerJob* jobs) {
     double v = 0.0;
     if (i == j) {
       v = J.ds[i];
-    } else if (J.kept[i] || J.kept[j]) {
+    } else if ((J.kept[i] > 0 || J.kept[j] > 0) && J.kept[i] >= 0 && J.kept[j] >= 0) {
       const double si = J.s[i], sj = J.s[j];
       const double f = 1.0 / ((sj - si) * (sj + si));
       const double xa = J.X[(int64_t)i * r + j] - J.X[(int64_t)j * r + i];
@@ -1071,7 +1076,7 @@ __global__ void __launch_bounds__(256) axpy_kernel(const AxpyJob* jobs) {
     double f = J.sa;
     if (J.s) {
       const int j = (int)(e / J.cols);
-      f = J.kept[j] ? f / J.s[j] : 0.0;
+      f = J.kept[j] > 0 ? f / J.s[j] : 0.0;
     }
     J.out[e] = (J.a ? J.a[e] : 0.0) + f * J.b[e];
   }
@@ -1482,6 +1487,7 @@ ftn_status cj_backward(ftn_ctx ctx, std::vector<CJob*>& gj, const std::vector<do
     int pi, Ma, Nb, K, ldk, rx, ry, r, ml, k;
     bool fx, fy;
     const double *A, *B, *RX, *RY, *Ms, *Tf, *Z, *W, *PA, *QB, *s;
+    double tol;  // singular values at or below it (rounding level of the core) are left out
     double *dXf, *dYt, *EA, *EB, *Rot, *Oth, *Ut, *Vt, *dZ, *dW, *dRX1, *dRY1, *dUt, *dVt, *ds, *X, *Y, *inner,
         *XU, *YV, *Pt, *Qt, *T1, *SV, *dMa, *dMb, *dRX2, *dRY2, *dAd, *dBd, *RdRx, *Rix, *Hx, *Gx, *dAq, *RdRy, *Riy,
         *Hy, *Gy, *dBq;
@@ -1506,9 +1512,6 @@ ftn_status cj_backward(ftn_ctx ctx, std::vector<CJob*>& gj, const std::vector<do
       if (c.rx != J.rx0[pi] || c.ry != J.ry0[pi])
         return set_error(FTN_EUNSUPPORTED, "compression adjoint: a sector block is rank deficient (its factor has "
                                            "dropped rows)");
-      for (int j = 0; j < c.r; ++j)
-        if (!(sv[J.s_off[pi] + j] > 0.0))
-          return set_error(FTN_EUNSUPPORTED, "compression adjoint: the core has a zero singular value");
       const int64_t K = c.K, r = c.r, k = c.k, rx = c.rx, ry = c.ry;
       tot += c.Ma * k + k * c.Nb + 2 * k * K + r * c.ml + r * r + k * ry + k * rx + (rx + ry) * K * 3 + r * (rx + ry) +
              r + 3 * r * r + 2 * r * (rx + ry) + 2 * r * ry + 2 * rx * ry + (c.Ma + c.Nb) * K +
@@ -1560,6 +1563,11 @@ ftn_status cj_backward(ftn_ctx ctx, std::vector<CJob*>& gj, const std::vector<do
       int j = 0;
       for (auto& cd : J.kept)
         if (cd.pi == c.pi) hk[j++] = cd.idx;
+      double smax = 0.0;
+      for (int t = 0; t < r; ++t) smax = std::max(smax, sv[J.s_off[c.pi] + t]);
+      c.tol = 1e-12 * smax;
+      for (int t = 0; t < r; ++t)
+        if (!(sv[J.s_off[c.pi] + t] > c.tol)) hk[k + t] = -1;
       for (int t = 0; t < k; ++t) hk[k + hk[t]] = 1;
       FTN_CUDA(cudaMemcpyAsync(c.idx, hk.data(), hk.size() * sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
       // cotangents in the fused sector coordinates: dX' rows as A's rows,
@@ -1606,7 +1614,7 @@ ftn_status cj_backward(ftn_ctx ctx, std::vector<CJob*>& gj, const std::vector<do
   }));
   {
     std::vector<RowDivJob> rd;
-    for (Sec& c : secs) rd.push_back({c.Tf, c.Rot, c.s, c.r, c.ml});
+    for (Sec& c : secs) rd.push_back({c.Tf, c.Rot, c.s, c.r, c.ml, c.tol});
     FTN_TRY(launch_jobs(ctx, row_div_kernel, rd));
   }
   // the other side's vectors (stored core times the rotated ones); dZ, dW, and
@@ -1622,7 +1630,7 @@ ftn_status cj_backward(ftn_ctx ctx, std::vector<CJob*>& gj, const std::vector<do
     std::vector<RowDivJob> rd;
     std::vector<CotJob> cj;
     for (Sec& c : secs) {
-      rd.push_back({c.Oth, c.Oth, c.s, c.r, c.r});
+      rd.push_back({c.Oth, c.Oth, c.s, c.r, c.r, c.tol});
       cj.push_back({c.dZ, c.dW, c.Ut, c.Vt, c.s, c.idx, c.dUt, c.dVt, c.ds, c.k, c.r, c.rx, c.ry});
     }
     FTN_TRY(launch_jobs(ctx, row_div_kernel, rd));
@@ -2252,8 +2260,10 @@ ftn_status compress_batch(ftn_ctx ctx, std::vector<CompressItem>& items) {
       ftn_tensor_free(J.Yn);
       continue;
     }
-    ftn_tensor_free(J.it->X);
-    ftn_tensor_free(J.it->Y);
+    if (!J.it->keep_inputs) {
+      ftn_tensor_free(J.it->X);
+      ftn_tensor_free(J.it->Y);
+    }
     J.it->X = J.Xn;
     J.it->Y = J.Yn;
   }

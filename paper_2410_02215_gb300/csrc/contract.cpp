@@ -52,6 +52,9 @@ struct Exec {
   std::map<int64_t, int> dummy;        // dummy leg id -> index of its odd tensor (locally ordered only)
   int64_t next_leg = 1ll << 40;
   int sign = 1;
+  // when set, consumed tensors are handed here instead of freed (the
+  // gradient executor keeps every operand of its tape)
+  std::vector<ftn_tensor>* retain = nullptr;
   Exec() = default;
   Exec(const Exec&) = delete;
   Exec& operator=(const Exec&) = delete;
@@ -257,8 +260,13 @@ struct Exec {
       else
         partner.erase(live[l].ids[k]);
     const int64_t pos = live[e].pos;
-    ftn_tensor_free(live[e].t);
-    ftn_tensor_free(live[l].t);
+    if (retain) {
+      retain->push_back(live[e].t);
+      retain->push_back(live[l].t);
+    } else {
+      ftn_tensor_free(live[e].t);
+      ftn_tensor_free(live[l].t);
+    }
     live.erase(e);
     live.erase(l);
     const int64_t id = n + s;
@@ -440,6 +448,167 @@ ftn_status contract_batch_impl(ftn_ctx ctx, int count, const ftn_network* nets, 
   return FTN_OK;
 }
 
+// ---- gradient of a network's value (ftn_contract_grad) ----------------------
+// Forward: the executor's walk (same pairs, same late / early compressions of
+// the same bonds, same flips and phases) without the per-step normalisation,
+// one network, FP64, every consumed tensor kept on a tape.  Backward: the
+// cotangent of the final scalar is its sign; each contraction passes the
+// cotangent of its result to its operands by ftn_tensordot_grad (the same
+// flips), each compression the cotangents of X', Y' to X, Y by
+// ftn_compress_grad (forward recomputed, same kept set); the leaves' cotangents
+// are dv/dT.  Scope: even tensors (no dummy legs), the compression's
+// differentiability conditions; the value must stay within FP64's range.
+ftn_status contract_grad_impl(ftn_ctx ctx, const ftn_network* net, const ftn_tree* tree, double* value,
+                              ftn_tensor* grads) {
+  if (!ctx || !net || !tree || !value || !grads) return set_error(FTN_EINVAL, "null argument");
+  for (int i = 0; i < net->n_tensors; ++i) grads[i] = nullptr;
+  Exec E;
+  FTN_TRY(E.init(ctx, net, tree, FTN_PREC_F64));
+  for (int i = 0; i < E.n; ++i)
+    if (net->tensors[i]->parity) return set_error(FTN_EUNSUPPORTED, "network gradient: even tensors only");
+  struct Op {
+    bool td;
+    ftn_tensor a, b, c, d;  // td: A, B, C; compression: X, Y, X', Y'
+    int n;
+    int ax[MAXR], ay[MAXR];
+    uint64_t fa, fb;
+    int chi, arrows;
+  };
+  std::vector<Op> tape;
+  std::vector<ftn_tensor> kept;  // every tensor the tape refers to (freed at the end)
+  std::map<ftn_tensor, ftn_tensor> g;
+  struct Cleanup {
+    std::vector<ftn_tensor>& k;
+    std::map<ftn_tensor, ftn_tensor>& g;
+    ~Cleanup() {
+      for (ftn_tensor t : k) ftn_tensor_free(t);
+      for (auto& kv : g) ftn_tensor_free(kv.second);
+    }
+  } cleanup{kept, g};
+  E.retain = &kept;
+  std::vector<ftn_tensor> leaves(E.n);  // the executor's views of the caller's tensors
+  for (int i = 0; i < E.n; ++i) leaves[i] = E.live[i].t;
+  auto compress_pair = [&](int64_t x, int64_t y) -> ftn_status {
+    std::vector<CompressItem> items(1);
+    E.compress_item(x, y, items[0]);
+    items[0].keep_inputs = true;
+    Op op{};
+    op.td = false;
+    op.a = items[0].X;
+    op.b = items[0].Y;
+    op.n = items[0].n;
+    for (int i = 0; i < op.n; ++i) op.ax[i] = items[0].ax[i], op.ay[i] = items[0].ay[i];
+    op.chi = items[0].chi;
+    op.arrows = items[0].arrows;
+    FTN_TRY(compress_batch(ctx, items));
+    kept.push_back(op.a);
+    kept.push_back(op.b);
+    op.c = items[0].X;
+    op.d = items[0].Y;
+    E.live[x].t = op.c;
+    E.live[y].t = op.d;
+    E.compress_done(x, y, items[0]);
+    tape.push_back(op);
+    return FTN_OK;
+  };
+  for (int s = 0; s < E.n - 1; ++s) {
+    int64_t a, b;
+    FTN_TRY(E.step_pair(s, a, b));
+    if (tree->policy == FTN_POLICY_LATE)
+      for (auto& pr : E.late_pairs(a, b)) FTN_TRY(compress_pair(pr.first, pr.second));
+    std::vector<TdItem> items(1);
+    int64_t e, l;
+    E.step_item(a, b, e, l, items[0]);
+    FTN_TRY(tensordot_batch(ctx, items, FTN_PREC_F64));
+    Op op{};
+    op.td = true;
+    op.a = items[0].A;
+    op.b = items[0].B;
+    op.c = items[0].C;
+    op.n = items[0].n;
+    for (int i = 0; i < op.n; ++i) op.ax[i] = items[0].ax[i], op.ay[i] = items[0].ay[i];
+    op.fa = items[0].fa;
+    op.fb = items[0].fb;
+    tape.push_back(op);
+    const int64_t id = E.step_done(s, e, l, items[0]);
+    if (tree->policy == FTN_POLICY_EARLY)
+      for (auto& pr : E.early_pairs(id)) FTN_TRY(compress_pair(pr.first, pr.second));
+  }
+  if (E.live.size() != 1) return set_error(FTN_EINVAL, "tree does not reduce the network to one tensor");
+  ftn_tensor last = E.live.begin()->second.t;
+  if (last->numel != 1) return set_error(FTN_EINVAL, "network is not closed (open legs remain)");
+  double v = 0.0;
+  FTN_CUDA(cudaMemcpyAsync(&v, last->data, 8, cudaMemcpyDeviceToHost, ctx->stream));
+  FTN_CUDA(cudaStreamSynchronize(ctx->stream));
+  *value = E.sign * v;
+  // seed: dv/d(last) = sign
+  {
+    ftn_tensor seed = nullptr;
+    FTN_TRY(make_tensor(ctx, last->rank, last->d0, last->d1, last->dual, last->parity, FTN_F64, &seed));
+    g[last] = seed;
+    const double sg = (double)E.sign;
+    FTN_CUDA(cudaMemcpyAsync(seed->data, &sg, 8, cudaMemcpyHostToDevice, ctx->stream));
+    FTN_CUDA(cudaStreamSynchronize(ctx->stream));  // the host source goes out of scope
+  }
+  auto cot = [&](ftn_tensor t, ftn_tensor* out) -> ftn_status {  // the cotangent of t (zeros if none reached it)
+    auto it = g.find(t);
+    if (it != g.end()) {
+      *out = it->second;
+      return FTN_OK;
+    }
+    ftn_tensor z = nullptr;
+    FTN_TRY(make_tensor(ctx, t->rank, t->d0, t->d1, t->dual, t->parity, FTN_F64, &z));
+    g[t] = z;
+    FTN_CUDA(cudaMemsetAsync(z->data, 0, (size_t)z->numel * 8, ctx->stream));
+    *out = z;
+    return FTN_OK;
+  };
+  auto put = [&](ftn_tensor t, ftn_tensor d) -> ftn_status {
+    if (g.count(t)) {
+      ftn_tensor_free(d);
+      return set_error(FTN_EINVAL, "internal error: a tensor of the tape is consumed twice");
+    }
+    g[t] = d;
+    return FTN_OK;
+  };
+  for (auto it = tape.rbegin(); it != tape.rend(); ++it) {
+    const Op& op = *it;
+    if (op.td) {
+      ftn_tensor G = nullptr, dA = nullptr, dB = nullptr;
+      FTN_TRY(cot(op.c, &G));
+      FTN_TRY(ftn_tensordot_grad(ctx, op.a, op.b, G, op.n, op.ax, op.ay, op.fa, op.fb, nullptr, FTN_PREC_F64, &dA,
+                                 &dB));
+      FTN_TRY(put(op.a, dA));
+      FTN_TRY(put(op.b, dB));
+    } else {
+      ftn_tensor gx = nullptr, gy = nullptr, dX = nullptr, dY = nullptr;
+      FTN_TRY(cot(op.c, &gx));
+      FTN_TRY(cot(op.d, &gy));
+      FTN_TRY(ftn_compress_grad(ctx, op.a, op.b, op.n, op.ax, op.ay, op.chi, op.arrows, gx, gy, &dX, &dY));
+      FTN_TRY(put(op.a, dX));
+      FTN_TRY(put(op.b, dY));
+    }
+  }
+  // the leaves' cotangents (the views have the caller's legs)
+  for (int i = 0; i < E.n; ++i) {
+    ftn_tensor d = nullptr;
+    if (leaves[i]) {
+      auto f = g.find(leaves[i]);
+      if (f != g.end()) {
+        d = f->second;
+        g.erase(f);
+      }
+    }
+    if (!d) {  // a tensor whose value does not reach the result (cannot happen in a connected tree)
+      FTN_TRY(make_tensor(ctx, net->tensors[i]->rank, net->tensors[i]->d0, net->tensors[i]->d1,
+                          net->tensors[i]->dual, 0, FTN_F64, &d));
+      FTN_CUDA(cudaMemsetAsync(d->data, 0, (size_t)d->numel * 8, ctx->stream));
+    }
+    grads[i] = d;
+  }
+  return FTN_OK;
+}
+
 ftn_status contract_impl(ftn_ctx ctx, const ftn_network* net, const ftn_tree* tree, ftn_prec prec, double* mantissa,
                          double* log_scale) {
   if (!ctx || !net || !tree || !mantissa || !log_scale) return set_error(FTN_EINVAL, "null argument");
@@ -541,6 +710,11 @@ extern "C" {
 ftn_status ftn_contract(ftn_ctx ctx, const ftn_network* net, const ftn_tree* tree, ftn_prec prec, double* mantissa,
                         double* log_scale) {
   return contract_impl(ctx, net, tree, prec, mantissa, log_scale);
+}
+
+ftn_status ftn_contract_grad(ftn_ctx ctx, const ftn_network* net, const ftn_tree* tree, double* value,
+                             ftn_tensor* grads) {
+  return contract_grad_impl(ctx, net, tree, value, grads);
 }
 
 ftn_status ftn_contract_batch(ftn_ctx ctx, int count, const ftn_network* nets, const ftn_tree* trees, ftn_prec prec,

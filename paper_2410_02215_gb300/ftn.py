@@ -89,6 +89,7 @@ def lib():
         "ftn_contract": [vp, C.POINTER(Network), C.POINTER(Tree), C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double)],
         "ftn_contract_batch": [vp, C.c_int, C.POINTER(Network), C.POINTER(Tree), C.c_int, C.POINTER(C.c_double),
                                C.POINTER(C.c_double)],
+        "ftn_contract_grad": [vp, C.POINTER(Network), C.POINTER(Tree), C.POINTER(C.c_double), C.POINTER(vp)],
         "ftn_hubbard_term": [vp, C.c_int, C.c_double, C.c_double, C.c_int, C.POINTER(vp)],
         "ftn_energy_reduce": [C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double), C.c_int, i32p, i32p, C.c_int,
                               i32p, C.POINTER(C.c_double), C.POINTER(C.c_double)],
@@ -500,6 +501,18 @@ def contract(ctx, tensors, bonds, tree, positions=None, policy="exact", chi=0, p
     m, lg = C.c_double(), C.c_double()
     _check(lib().ftn_contract(ctx.handle, C.byref(net), C.byref(tr), _prec(prec), C.byref(m), C.byref(lg)))
     return m.value, lg.value
+
+
+def contract_grad(ctx, tensors, bonds, tree, positions=None, policy="exact", chi=0):
+    """Value of a closed network of even FP64 tensors and dv/dT for every
+    tensor (ftn_contract_grad): returns (value, [gradient tensors])."""
+    n, net_arr, tree_arr, keep = _network_arrays([{"tensors": tensors, "bonds": bonds, "tree": tree,
+                                                   "positions": positions, "policy": policy, "chi": chi}])
+    v = C.c_double()
+    out = (C.c_void_p * max(1, len(tensors)))()
+    _check(lib().ftn_contract_grad(ctx.handle, net_arr, tree_arr, C.byref(v), out))
+    del keep
+    return v.value, [Tensor(ctx, C.c_void_p(out[i])) for i in range(len(tensors))]
 
 
 def _network_arrays(networks):

@@ -1,0 +1,75 @@
+"""The network gradient on the GPU (ftn_contract_grad) against the oracle's
+(oracle.network_grad, pinned by finite differences and Euler's identity in
+tests/test_oracle_network_grad.py): PEPS norm networks on 2x2 and 2x3 open
+lattices with the row-sweep double-layer tree, exact, late and early
+compression at a truncating chi, in the locally and the globally ordered
+formalism.  Value at 1e-10 (and equal to ftn_contract's normalised value),
+every gradient entry at 1e-9 of the largest."""
+import numpy as np
+import pytest
+
+import oracle as O
+import oracle.network_grad as NG
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def F():
+    import torch
+
+    from paper_2410_02215_gb300 import ftn
+
+    assert torch.cuda.is_available()
+    ftn.lib()
+    return ftn
+
+
+@pytest.fixture(scope="module")
+def ctx(F):
+    c = F.Context()
+    yield c
+    c.synchronize()
+    c.close()
+
+
+def setup(lx, ly, D, seed):
+    n, edges = W.square_lattice(lx, ly)
+    lay = W.peps_layout(n, edges, D, (2, 2))
+    kets = O.ket_tensors(lay, W.random_peps(lay, seed))
+    net = O.norm_network(lay, kets)
+    tree = W.double_layer_tree(n, W.site_sweep_tree(list(range(n))))
+    return net, tree
+
+
+def dense(t):
+    return O.embed_blocks(t.legs, t.parity, t.to_blocks())
+
+
+@pytest.mark.parametrize("mode", ["local", "global"])
+@pytest.mark.parametrize("lx,ly,D,chi", [(2, 2, (1, 1), 2), (2, 3, (1, 1), 2), (2, 2, (2, 1), 3)])
+@pytest.mark.parametrize("policy", ["exact", "late", "early"])
+def test_network_grad_against_oracle(F, ctx, lx, ly, D, chi, policy, mode):
+    net, tree = setup(lx, ly, D, 3)
+    c = None if policy == "exact" else chi
+    v_o, g_o, _ = NG.contract_tree_grad(net, tree, policy, c, mode=mode)
+    tensors = [F.Tensor.from_blocks(ctx, t.legs, t.parity, sorted(O.extract_blocks(t).items())) for t in net.tensors]
+    pos = list(net.positions) if mode == "global" else None
+    v, grads = F.contract_grad(ctx, tensors, net.bonds, tree, positions=pos, policy=policy, chi=c or 0)
+    assert abs(v - v_o) <= 1e-10 * abs(v_o)
+    m, lg = F.contract(ctx, tensors, net.bonds, tree, positions=pos, policy=policy, chi=c or 0)
+    assert abs(m * np.exp(lg) - v) <= 1e-12 * abs(v)
+    scale = max(np.max(np.abs(g.data)) for g in g_o)
+    for t, gg, go in zip(net.tensors, grads, g_o):
+        assert gg.legs == t.legs or list(gg.legs) == list(t.legs)
+        assert np.max(np.abs(dense(gg).data - go.data)) <= 1e-9 * scale
+
+
+def test_network_grad_rejects_odd_tensors(F, ctx):
+    la = [(1, 1, 0), (1, 1, 1)]
+    a = F.Tensor.from_blocks(ctx, la, 1, W.random_blocks(la, 1, 1))
+    b = F.Tensor.from_blocks(ctx, [(1, 1, 1), (1, 1, 0)], 1, W.random_blocks([(1, 1, 1), (1, 1, 0)], 1, 2))
+    with pytest.raises(F.FtnError) as e:
+        F.contract_grad(ctx, [a, b], [(0, 0, 1, 0), (0, 1, 1, 1)], [(0, 1)])
+    assert e.value.status == -8
