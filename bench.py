@@ -712,6 +712,68 @@ def energy_bench(F, ctx, evals, with_oracle, workers=8, batches=(0, 2, 3, 6)):
     return out
 
 
+GRADIENT_WORKLOAD = ("gradient of the norm <Psi|Psi> of an fPEPS on a 6x6 open square lattice, D=4 (2+2), phys 4 "
+                     "(2+2), N(0,1) site tensors (seed 5), boundary-MPS row sweep (ket and bra of a site merged; "
+                     "one boundary tensor per column absorbs its column's sites row by row, the horizontal bonds "
+                     "between column tensors capped by late compression at chi=48; columns merged at the end), "
+                     "locally ordered; dv/dT for all 72 tensors (kets and bras as independent inputs), FP64")
+
+
+def gradient_bench(F, ctx, evals, samples=20, h=1e-6):
+    """Gradient evaluations per second of the compressed norm network (the
+    config-5 workload) through ftn_contract_grad, its value against
+    ftn_contract's, and central finite differences of ftn_contract on
+    `samples` seeded entries (h = 1e-6, FP64)."""
+    import numpy as np
+
+    from paper_2410_02215_gb300 import peps
+
+    n, edges = W.square_lattice(6, 6)
+    lay = W.peps_layout(n, edges, (2, 2), (2, 2))
+    blocks = W.random_peps(lay, 5)
+    kets = [F.Tensor.from_blocks(ctx, lay["legs"][s], 0, blocks[s]) for s in range(n)]
+    tensors, bonds, _ = peps.norm_network(ctx, lay, kets)
+    tree = W.double_layer_tree(n, W.boundary_mps_tree(6, 6))
+    v, grads = F.contract_grad(ctx, tensors, bonds, tree, policy="late", chi=48)  # warm-up (plans)
+    del grads
+    ctx.synchronize()
+    l0 = ctx.launches()
+    t0 = time.perf_counter()
+    for _ in range(evals):
+        v, grads = F.contract_grad(ctx, tensors, bonds, tree, policy="late", chi=48)
+    ctx.synchronize()
+    dt_s = time.perf_counter() - t0
+    launches = (ctx.launches() - l0) / evals
+    m, lg = F.contract(ctx, tensors, bonds, tree, policy="late", chi=48)
+    host = [dict(g.to_blocks()) for g in grads]
+    scale = max(float(np.max(np.abs(b))) for d in host for b in d.values())
+    rng = np.random.default_rng(0)
+    worst = 0.0
+    t1 = time.perf_counter()
+    for _ in range(samples):
+        i = int(rng.integers(len(tensors)))
+        tb = dict(tensors[i].to_blocks())
+        key = sorted(tb)[int(rng.integers(len(tb)))]
+        idx = tuple(int(rng.integers(d)) for d in tb[key].shape)
+        vals = []
+        for sg in (1.0, -1.0):
+            pb = {k: b.copy() for k, b in tb.items()}
+            pb[key][idx] += sg * h
+            t = F.Tensor.from_blocks(ctx, tensors[i].legs, tensors[i].parity, sorted(pb.items()))
+            mm, ll = F.contract(ctx, tensors[:i] + [t] + tensors[i + 1:], bonds, tree, policy="late", chi=48)
+            vals.append(mm * np.exp(ll))
+            del t
+        fd = (vals[0] - vals[1]) / (2 * h)
+        worst = max(worst, abs(fd - float(host[i][key][idx])) / scale)
+    fd_s = time.perf_counter() - t1
+    return {"workload": GRADIENT_WORKLOAD, "gradient_evals_per_s": evals / dt_s, "s_per_gradient": dt_s / evals,
+            "gpu_launches_per_gradient": launches, "value": v,
+            "value_rel_err_vs_contract": abs(m * np.exp(lg) - v) / abs(v),
+            "fd": {"samples": samples, "h": h, "max_abs_err_over_max_grad": worst, "s": fd_s,
+                   "note": "central differences of ftn_contract (normalised forward) on seeded entries of seeded "
+                           "tensors, against dv/dT"}}
+
+
 DIAMOND_WORKLOAD = ("Hubbard fPEPS on the 2x2x2-conventional-cell diamond lattice (64 sites, 86 bonds, open "
                     "boundaries), D=4 (2+2), phys 4 (2+2), t=1, U=8, N(0,1) site tensors (seed 1), stand-in gauges "
                     "0.5^k per sector on dangling bonds; every hopping and on-site term (150) by the cluster "
@@ -898,6 +960,8 @@ def run_ours(args, rank, world, local):
     if not args.no_energy:
         result["energy"] = energy_bench(F, ctx, args.energy_evals, rank == 0 and world == 1 and not args.no_cpu,
                                         args.energy_streams)
+    if not args.no_gradient:
+        result["gradient"] = gradient_bench(F, ctx, args.gradient_evals)
     if not args.no_diamond:
         result["energy_diamond"] = diamond_bench(F, ctx, torch, args.diamond_evals, args.cluster_streams,
                                                  rank == 0 and world == 1 and not args.no_cpu, rank, world)
@@ -935,6 +999,8 @@ def main():
                     help="contexts (CUDA streams) that run an evaluation's contractions concurrently")
     ap.add_argument("--no-accuracy", action="store_true")
     ap.add_argument("--no-diamond", action="store_true")
+    ap.add_argument("--no-gradient", action="store_true")
+    ap.add_argument("--gradient-evals", type=int, default=3)
     ap.add_argument("--diamond-evals", type=int, default=2)
     args = ap.parse_args()
     if args.warmup < 3:

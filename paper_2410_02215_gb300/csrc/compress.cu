@@ -1137,6 +1137,57 @@ __global__ void __launch_bounds__(256) perm_adjoint_kernel(const PermJob* jobs, 
   }
 }
 
+// Rebuilt singular vectors (rows of v, length n) taken in the order ord[0],
+// ord[1], ... (decreasing singular value): each orthogonalised twice against
+// the ones before it by classical Gram-Schmidt and scaled to unit norm.  The
+// n-side vectors core x v_j / s_j carry ~eps s_max / s_j of the directions of
+// larger singular values, which the F-matrix terms of the adjoint would pick
+// up; this removes them, as the forward does for its kept vectors.
+struct OrdOrthJob {
+  double* v;
+  const int* ord;
+  int nv, n;
+};
+__global__ void __launch_bounds__(256) orth_ordered_kernel(const OrdOrthJob* jobs) {
+  __shared__ double h[LA_MAX_DIM];
+  __shared__ double red[9];
+  const OrdOrthJob J = jobs[blockIdx.x];
+  const int n = J.n, t = threadIdx.x, lane = t & 31, warp = t >> 5, nw = blockDim.x >> 5;
+  for (int q = 0; q < J.nv; ++q) {
+    double* vj = J.v + (int64_t)J.ord[q] * n;
+    for (int pass = 0; pass < 2 && q > 0; ++pass) {
+      for (int i = warp; i < q; i += nw) {
+        const double* vi = J.v + (int64_t)J.ord[i] * n;
+        double d = 0.0;
+        for (int e = lane; e < n; e += 32) d = fma(vi[e], vj[e], d);
+        for (int o = 16; o; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+        if (lane == 0) h[i] = d;
+      }
+      __syncthreads();
+      for (int e = t; e < n; e += blockDim.x) {
+        double a = vj[e];
+        for (int i = 0; i < q; ++i) a = fma(-h[i], J.v[(int64_t)J.ord[i] * n + e], a);
+        vj[e] = a;
+      }
+      __syncthreads();
+    }
+    double s2 = 0.0;
+    for (int e = t; e < n; e += blockDim.x) s2 = fma(vj[e], vj[e], s2);
+    for (int o = 16; o; o >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+    if (lane == 0) red[warp] = s2;
+    __syncthreads();
+    if (t == 0) {
+      double tot = 0.0;
+      for (int w = 0; w < nw; ++w) tot += red[w];
+      red[8] = tot > 0.0 ? 1.0 / sqrt(tot) : 0.0;
+    }
+    __syncthreads();
+    const double f = red[8];
+    for (int e = t; e < n; e += blockDim.x) vj[e] *= f;
+    __syncthreads();
+  }
+}
+
 // out[m, c] += a[m, c] (rows x cols; row strides lda, ldo)
 struct Add2Job {
   const double* a;
@@ -1491,7 +1542,8 @@ ftn_status cj_backward(ftn_ctx ctx, std::vector<CJob*>& gj, const std::vector<do
     double *dXf, *dYt, *EA, *EB, *Rot, *Oth, *Ut, *Vt, *dZ, *dW, *dRX1, *dRY1, *dUt, *dVt, *ds, *X, *Y, *inner,
         *XU, *YV, *Pt, *Qt, *T1, *SV, *dMa, *dMb, *dRX2, *dRY2, *dAd, *dBd, *RdRx, *Rix, *Hx, *Gx, *dAq, *RdRy, *Riy,
         *Hy, *Gy, *dBq;
-    int *idx, *kept;
+    int *idx, *kept, *ord;
+    int nord;  // rows in ord: singular values above tol, decreasing
   };
   std::vector<Sec> secs;
   std::vector<std::unique_ptr<DevBuf>> bufs;
@@ -1515,7 +1567,7 @@ ftn_status cj_backward(ftn_ctx ctx, std::vector<CJob*>& gj, const std::vector<do
       const int64_t K = c.K, r = c.r, k = c.k, rx = c.rx, ry = c.ry;
       tot += c.Ma * k + k * c.Nb + 2 * k * K + r * c.ml + r * r + k * ry + k * rx + (rx + ry) * K * 3 + r * (rx + ry) +
              r + 3 * r * r + 2 * r * (rx + ry) + 2 * r * ry + 2 * rx * ry + (c.Ma + c.Nb) * K +
-             (c.fx ? 4 * K * K + c.Ma * K : 0) + (c.fy ? 4 * K * K + c.Nb * K : 0) + (k + r + 2) / 2 + 8;
+             (c.fx ? 4 * K * K + c.Ma * K : 0) + (c.fy ? 4 * K * K + c.Nb * K : 0) + (k + 2 * r + 2) / 2 + 8;
       js.push_back(c);
     }
     bufs.emplace_back(new DevBuf(ctx));
@@ -1546,7 +1598,8 @@ ftn_status cj_backward(ftn_ctx ctx, std::vector<CJob*>& gj, const std::vector<do
       if (c.fy) c.RdRy = take(K * K), c.Riy = take(K * K), c.Hy = take(K * K), c.Gy = take(K * K), c.dBq = take(c.Nb * K);
       c.idx = reinterpret_cast<int*>(p);
       c.kept = c.idx + k;
-      p += (k + r + 2) / 2 + 1;
+      c.ord = c.kept + r;
+      p += (k + 2 * r + 2) / 2 + 1;
       CJob& J = *c.J;
       c.A = J.ws + J.o_xf + P->afoff[c.pi];
       c.B = J.ws + J.o_yf + P->bfoff[c.pi];
@@ -1559,16 +1612,23 @@ ftn_status cj_backward(ftn_ctx ctx, std::vector<CJob*>& gj, const std::vector<do
       c.Ut = J.trans[c.pi] ? c.Rot : c.Oth;
       c.Vt = J.trans[c.pi] ? c.Oth : c.Rot;
       // kept states in new-bond order -> Jacobi rows; kept flags per row
-      std::vector<int> hk(k + r, 0);
+      std::vector<int> hk(k + 2 * r, 0);
       int j = 0;
       for (auto& cd : J.kept)
         if (cd.pi == c.pi) hk[j++] = cd.idx;
       double smax = 0.0;
-      for (int t = 0; t < r; ++t) smax = std::max(smax, sv[J.s_off[c.pi] + t]);
+      const double* sj = sv.data() + J.s_off[c.pi];
+      for (int t = 0; t < r; ++t) smax = std::max(smax, sj[t]);
       c.tol = 1e-12 * smax;
       for (int t = 0; t < r; ++t)
-        if (!(sv[J.s_off[c.pi] + t] > c.tol)) hk[k + t] = -1;
+        if (!(sj[t] > c.tol)) hk[k + t] = -1;
       for (int t = 0; t < k; ++t) hk[k + hk[t]] = 1;
+      std::vector<int> ord;
+      for (int t = 0; t < r; ++t)
+        if (sj[t] > c.tol) ord.push_back(t);
+      std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) { return sj[a] > sj[b]; });
+      c.nord = (int)ord.size();
+      std::copy(ord.begin(), ord.end(), hk.begin() + k + r);
       FTN_CUDA(cudaMemcpyAsync(c.idx, hk.data(), hk.size() * sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
       // cotangents in the fused sector coordinates: dX' rows as A's rows,
       // dY'^T columns as B's rows
@@ -1634,6 +1694,9 @@ ftn_status cj_backward(ftn_ctx ctx, std::vector<CJob*>& gj, const std::vector<do
       cj.push_back({c.dZ, c.dW, c.Ut, c.Vt, c.s, c.idx, c.dUt, c.dVt, c.ds, c.k, c.r, c.rx, c.ry});
     }
     FTN_TRY(launch_jobs(ctx, row_div_kernel, rd));
+    std::vector<OrdOrthJob> oj;
+    for (Sec& c : secs) oj.push_back({c.Oth, c.ord, c.nord, c.r});
+    FTN_TRY(launch_jobs(ctx, orth_ordered_kernel, oj));
     FTN_TRY(launch_jobs(ctx, svd_cot_kernel, cj));
   }
   // X = U^T dU, Y = V^T dV, then X^T Ut and Y^T Vt

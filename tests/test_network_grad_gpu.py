@@ -1,7 +1,8 @@
 """The network gradient on the GPU (ftn_contract_grad) against the oracle's
 (oracle.network_grad, pinned by finite differences and Euler's identity in
 tests/test_oracle_network_grad.py): PEPS norm networks on 2x2 and 2x3 open
-lattices with the row-sweep double-layer tree, exact, late and early
+lattices with the site-sweep double-layer tree and on a 3x3 lattice with the
+boundary-MPS row sweep, exact, late and early
 compression at a truncating chi, in the locally and the globally ordered
 formalism.  Value at 1e-10 (and equal to ftn_contract's normalised value),
 every gradient entry at 1e-9 of the largest."""
@@ -34,13 +35,13 @@ def ctx(F):
     c.close()
 
 
-def setup(lx, ly, D, seed):
+def setup(lx, ly, D, seed, boundary=False):
     n, edges = W.square_lattice(lx, ly)
     lay = W.peps_layout(n, edges, D, (2, 2))
     kets = O.ket_tensors(lay, W.random_peps(lay, seed))
     net = O.norm_network(lay, kets)
-    tree = W.double_layer_tree(n, W.site_sweep_tree(list(range(n))))
-    return net, tree
+    site_tree = W.boundary_mps_tree(lx, ly) if boundary else W.site_sweep_tree(list(range(n)))
+    return net, W.double_layer_tree(n, site_tree)
 
 
 def dense(t):
@@ -64,6 +65,56 @@ def test_network_grad_against_oracle(F, ctx, lx, ly, D, chi, policy, mode):
     for t, gg, go in zip(net.tensors, grads, g_o):
         assert gg.legs == t.legs or list(gg.legs) == list(t.legs)
         assert np.max(np.abs(dense(gg).data - go.data)) <= 1e-9 * scale
+
+
+@pytest.mark.parametrize("mode", ["local", "global"])
+@pytest.mark.parametrize("lx,ly,D,chi", [(2, 3, (2, 1), 4)])
+def test_boundary_mps_gradient_against_oracle(F, ctx, lx, ly, D, chi, mode):
+    """The boundary-MPS row sweep (one tensor per column, horizontal bonds
+    capped at chi by late compression)."""
+    net, tree = setup(lx, ly, D, 3, boundary=True)
+    v_o, g_o, gap = NG.contract_tree_grad(net, tree, "late", chi, mode=mode)
+    assert gap is not None and gap > 1e-3
+    tensors = [F.Tensor.from_blocks(ctx, t.legs, t.parity, sorted(O.extract_blocks(t).items())) for t in net.tensors]
+    pos = list(net.positions) if mode == "global" else None
+    v, grads = F.contract_grad(ctx, tensors, net.bonds, tree, positions=pos, policy="late", chi=chi)
+    assert abs(v - v_o) <= 1e-10 * abs(v_o)
+    scale = max(np.max(np.abs(g.data)) for g in g_o)
+    for gg, go in zip(grads, g_o):
+        assert np.max(np.abs(dense(gg).data - go.data)) <= 1e-9 * scale
+
+
+@pytest.mark.parametrize("mode", ["local", "global"])
+def test_boundary_mps_gradient_finite_differences(F, ctx, mode):
+    """3x3, D = 2 (1+1), chi = 3: some compressed blocks are square and rank
+    deficient (their boundary tensor came out of an earlier truncation), where
+    the oracle's QR rule, which inverts R, is off (its own finite-difference
+    error here is ~2e-4); the GPU takes blocks of fewer than 5/4 K rows as
+    their own factor and needs no inverse.  Its gradient against central
+    differences of ftn_contract on 20 seeded entries (h = 1e-6)."""
+    net, tree = setup(3, 3, (1, 1), 3, boundary=True)
+    tensors = [F.Tensor.from_blocks(ctx, t.legs, t.parity, sorted(O.extract_blocks(t).items())) for t in net.tensors]
+    pos = list(net.positions) if mode == "global" else None
+    v, grads = F.contract_grad(ctx, tensors, net.bonds, tree, positions=pos, policy="late", chi=3)
+    host = [dict(g.to_blocks()) for g in grads]
+    scale = max(float(np.max(np.abs(b))) for d in host for b in d.values())
+    rng = np.random.default_rng(0)
+    worst, h = 0.0, 1e-6
+    for _ in range(20):
+        i = int(rng.integers(len(tensors)))
+        tb = dict(tensors[i].to_blocks())
+        key = sorted(tb)[int(rng.integers(len(tb)))]
+        idx = tuple(int(rng.integers(d)) for d in tb[key].shape)
+        vals = []
+        for sg in (1.0, -1.0):
+            pb = {k: b.copy() for k, b in tb.items()}
+            pb[key][idx] += sg * h
+            t = F.Tensor.from_blocks(ctx, tensors[i].legs, tensors[i].parity, sorted(pb.items()))
+            m, lg = F.contract(ctx, tensors[:i] + [t] + tensors[i + 1:], net.bonds, tree, positions=pos,
+                               policy="late", chi=3)
+            vals.append(m * np.exp(lg))
+        worst = max(worst, abs((vals[0] - vals[1]) / (2 * h) - float(host[i][key][idx])) / scale)
+    assert worst < 1e-6, worst
 
 
 def test_network_grad_rejects_odd_tensors(F, ctx):

@@ -10,7 +10,8 @@ from __future__ import annotations
 
 from .gen import random_blocks
 
-__all__ = ["peps_layout", "random_peps", "double_layer_tree", "site_sweep_tree", "cluster_sites", "dangling_bonds",
+__all__ = ["peps_layout", "random_peps", "double_layer_tree", "site_sweep_tree", "boundary_mps_tree", "cluster_sites",
+           "dangling_bonds",
            "bond_gauges", "cluster_ids", "cluster_tree"]
 
 
@@ -74,6 +75,31 @@ def double_layer_tree(n, site_tree, op_sites=()):
     for q, (a, b) in enumerate(site_tree):
         pairs.append((remap[a], remap[b]))
         remap[n + q] = nxt
+        nxt += 1
+    return pairs
+
+
+def boundary_mps_tree(lx, ly):
+    """Site-level SSA tree of the boundary-MPS row sweep on an lx-by-ly open
+    square lattice (sites row-major, site = x * ly + y): column y's boundary
+    tensor starts as site (0, y) and absorbs (1, y), (2, y), ... row by row
+    (row x into every column before row x + 1), so the boundary stays a chain
+    of one tensor per column whose horizontal bonds grow by the vertical bond
+    dimension per row (the bonds a late compression caps at chi); after the
+    last row the column tensors are merged left to right."""
+    n = lx * ly
+    pairs = []
+    cur = list(range(ly))
+    nxt = n
+    for x in range(1, lx):
+        for y in range(ly):
+            pairs.append((cur[y], x * ly + y))
+            cur[y] = nxt
+            nxt += 1
+    acc = cur[0]
+    for y in range(1, ly):
+        pairs.append((acc, cur[y]))
+        acc = nxt
         nxt += 1
     return pairs
 
