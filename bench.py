@@ -721,10 +721,17 @@ GRADIENT_WORKLOAD = ("gradient of the norm <Psi|Psi> of an fPEPS on a 6x6 open s
 
 def gradient_bench(F, ctx, evals, samples=20, h=1e-6):
     """Gradient evaluations per second of the compressed norm network (the
-    config-5 workload) through ftn_contract_grad, its value against
-    ftn_contract's, and central finite differences of ftn_contract on
+    config-5 workload) through ftn_contract_grad with checkpointed
+    recomputation (the walk's state kept every ceil(sqrt(steps)) steps, each
+    segment replayed in the backward) and with every intermediate kept; the
+    library's peak device memory of each (its allocations routed through
+    torch's allocator); the two gradients compared bit for bit; the value
+    against ftn_contract's; central finite differences of ftn_contract on
     `samples` seeded entries (h = 1e-6, FP64)."""
+    import math
+
     import numpy as np
+    import torch
 
     from paper_2410_02215_gb300 import peps
 
@@ -734,18 +741,35 @@ def gradient_bench(F, ctx, evals, samples=20, h=1e-6):
     kets = [F.Tensor.from_blocks(ctx, lay["legs"][s], 0, blocks[s]) for s in range(n)]
     tensors, bonds, _ = peps.norm_network(ctx, lay, kets)
     tree = W.double_layer_tree(n, W.boundary_mps_tree(6, 6))
-    v, grads = F.contract_grad(ctx, tensors, bonds, tree, policy="late", chi=48)  # warm-up (plans)
-    del grads
     ctx.synchronize()
-    l0 = ctx.launches()
-    t0 = time.perf_counter()
-    for _ in range(evals):
-        v, grads = F.contract_grad(ctx, tensors, bonds, tree, policy="late", chi=48)
-    ctx.synchronize()
-    dt_s = time.perf_counter() - t0
-    launches = (ctx.launches() - l0) / evals
+    k_ck = int(math.ceil(math.sqrt(len(tree))))
+
+    def run(k):
+        c = F.Context(use_torch_allocator=True)  # same stream as ctx
+        try:
+            torch.cuda.synchronize()
+            base = torch.cuda.memory_allocated()
+            torch.cuda.reset_peak_memory_stats()
+            v, grads = F.contract_grad(c, tensors, bonds, tree, policy="late", chi=48, checkpoint=k)  # warm-up
+            c.synchronize()
+            peak = torch.cuda.max_memory_allocated() - base
+            host = [dict(g.to_blocks()) for g in grads]
+            del grads
+            l0 = c.launches()
+            t0 = time.perf_counter()
+            for _ in range(evals):
+                v, grads = F.contract_grad(c, tensors, bonds, tree, policy="late", chi=48, checkpoint=k)
+                del grads
+            c.synchronize()
+            dt = time.perf_counter() - t0
+            return v, host, dt / evals, (c.launches() - l0) / evals, peak
+        finally:
+            c.close()
+
+    v, host, s_ck, launches, peak_ck = run(k_ck)
+    v0, host0, s_0, launches0, peak_0 = run(0)
+    same = v == v0 and all(np.array_equal(a[key], b[key]) for a, b in zip(host, host0) for key in a)
     m, lg = F.contract(ctx, tensors, bonds, tree, policy="late", chi=48)
-    host = [dict(g.to_blocks()) for g in grads]
     scale = max(float(np.max(np.abs(b))) for d in host for b in d.values())
     rng = np.random.default_rng(0)
     worst = 0.0
@@ -766,7 +790,12 @@ def gradient_bench(F, ctx, evals, samples=20, h=1e-6):
         fd = (vals[0] - vals[1]) / (2 * h)
         worst = max(worst, abs(fd - float(host[i][key][idx])) / scale)
     fd_s = time.perf_counter() - t1
-    return {"workload": GRADIENT_WORKLOAD, "gradient_evals_per_s": evals / dt_s, "s_per_gradient": dt_s / evals,
+    return {"workload": GRADIENT_WORKLOAD, "gradient_evals_per_s": 1.0 / s_ck, "s_per_gradient": s_ck,
+            "checkpoint": {"every_steps": k_ck, "steps": len(tree), "peak_bytes": peak_ck,
+                           "note": "the walk's state kept every k steps, each segment replayed in the backward"},
+            "no_checkpoint": {"gradient_evals_per_s": 1.0 / s_0, "s_per_gradient": s_0, "peak_bytes": peak_0,
+                              "gpu_launches_per_gradient": launches0},
+            "same_as_no_checkpoint": bool(same),
             "gpu_launches_per_gradient": launches, "value": v,
             "value_rel_err_vs_contract": abs(m * np.exp(lg) - v) / abs(v),
             "fd": {"samples": samples, "h": h, "max_abs_err_over_max_grad": worst, "s": fd_s,

@@ -373,11 +373,19 @@ FTN_API ftn_status ftn_contract_batch(ftn_ctx ctx, int count, const ftn_network*
  * compression's by ftn_compress_grad, in reverse order (the paper gives no
  * gradient; variational fPEPS optimisation needs one, Sec. II.D).  Defined
  * where every compression is differentiable (ftn_compress_grad's
- * conditions; FTN_EUNSUPPORTED otherwise) and for even tensors only.  Keeps
- * every intermediate until the call returns; synchronises at the end and
- * as every compression does. */
-FTN_API ftn_status ftn_contract_grad(ftn_ctx ctx, const ftn_network* net, const ftn_tree* tree, double* value,
-                             ftn_tensor* grads);
+ * conditions; FTN_EUNSUPPORTED otherwise) and for even tensors only.
+ * checkpoint = 0 keeps every intermediate until the call returns.
+ * checkpoint = k > 0 keeps only the walk's state every k steps (its live
+ * tensors and the executor's leg bookkeeping) and frees the rest; the
+ * backward replays each segment of k steps from its checkpoint, keeping that
+ * segment's operands, before passing the cotangents through it -- one extra
+ * forward pass (all but the last segment) for memory of the checkpoints and
+ * one segment.  The replay is bit-identical to the first walk (the kernels
+ * are deterministic), so the value and gradient do not depend on k.
+ * FTN_EINVAL for k < 0.  Synchronises at the end and as every compression
+ * does. */
+FTN_API ftn_status ftn_contract_grad(ftn_ctx ctx, const ftn_network* net, const ftn_tree* tree, int checkpoint,
+                             double* value, ftn_tensor* grads);
 
 /* ---- expectation values of local terms (Sec. V) --------------------------- */
 

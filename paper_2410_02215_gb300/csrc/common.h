@@ -323,6 +323,14 @@ constexpr int F64W_PASSES = 4;
 inline bool f64w_small(const GemmProb& g) {
   return (int64_t)g.M * g.N <= F64W_MAX_MN && (g.nsplit > 1 ? g.kchunk : g.K) <= F64W_MAX_K;
 }
+// Tensor-core-precision problems go to the FP32 warp kernel only when, small
+// as above, their dot products are also short (K <= TCW_MAX_K): a longer K
+// amortises the tcgen05 tile's fixed cost even when the tile is mostly empty
+// (32 x 32 sector blocks with K = 32 took 10 us on tcgen05 against 16.5 us on
+// the warp kernel; the tiny, short-K problems of cluster networks gain from
+// the warp kernel).
+constexpr int TCW_MAX_K = 16;
+inline bool tcw_small(const GemmProb& g) { return f64w_small(g) && g.K <= TCW_MAX_K; }
 // K lanes: the largest power of two <= 32 that leaves each lane >= 8 terms
 __host__ __device__ inline int f64w_klanes(int klen) {
   int g = 1;

@@ -55,6 +55,32 @@ struct Exec {
   // when set, consumed tensors are handed here instead of freed (the
   // gradient executor keeps every operand of its tape)
   std::vector<ftn_tensor>* retain = nullptr;
+
+  // The walk's state between two steps (the tensors are referred to, not
+  // owned): taken at a checkpoint, put back to replay the steps after it.
+  struct State {
+    std::map<int64_t, Live> live;
+    std::map<int64_t, int64_t> partner, owner;
+    std::map<int64_t, int> dummy;
+    int64_t next_leg = 0;
+    int sign = 1;
+  };
+  void save(State& st) const {
+    st.live = live;
+    st.partner = partner;
+    st.owner = owner;
+    st.dummy = dummy;
+    st.next_leg = next_leg;
+    st.sign = sign;
+  }
+  void load(const State& st) {  // the current live tensors are the caller's to free
+    live = st.live;
+    partner = st.partner;
+    owner = st.owner;
+    dummy = st.dummy;
+    next_leg = st.next_leg;
+    sign = st.sign;
+  }
   Exec() = default;
   Exec(const Exec&) = delete;
   Exec& operator=(const Exec&) = delete;
@@ -451,16 +477,29 @@ ftn_status contract_batch_impl(ftn_ctx ctx, int count, const ftn_network* nets, 
 // ---- gradient of a network's value (ftn_contract_grad) ----------------------
 // Forward: the executor's walk (same pairs, same late / early compressions of
 // the same bonds, same flips and phases) without the per-step normalisation,
-// one network, FP64, every consumed tensor kept on a tape.  Backward: the
-// cotangent of the final scalar is its sign; each contraction passes the
-// cotangent of its result to its operands by ftn_tensordot_grad (the same
-// flips), each compression the cotangents of X', Y' to X, Y by
-// ftn_compress_grad (forward recomputed, same kept set); the leaves' cotangents
-// are dv/dT.  Scope: even tensors (no dummy legs), the compression's
-// differentiability conditions; the value must stay within FP64's range.
-ftn_status contract_grad_impl(ftn_ctx ctx, const ftn_network* net, const ftn_tree* tree, double* value,
-                              ftn_tensor* grads) {
+// one network, FP64.  Backward: the cotangent of the final scalar is its
+// sign; each contraction passes the cotangent of its result to its operands
+// by ftn_tensordot_grad (the same flips), each compression the cotangents of
+// X', Y' to X, Y by ftn_compress_grad (forward recomputed, same kept set); the
+// leaves' cotangents are dv/dT.  Scope: even tensors (no dummy legs), the
+// compression's differentiability conditions; the value must stay within
+// FP64's range.
+//
+// Checkpointing (checkpoint = k > 0): the steps are cut into segments of k.
+// A first walk keeps only the state at each segment start (its live tensors
+// and the executor's bookkeeping) and frees every other intermediate; the
+// backward then takes the segments last to first, puts the segment's
+// starting state back, replays its steps keeping their operands, and runs
+// them backwards.  The cotangents reaching the end of a replayed segment are
+// those of the next segment's starting tensors, matched by tensor id: the
+// kernels are deterministic, so a replay reproduces the first walk's tensors
+// (and kept sets) bit for bit.  Memory: the checkpoints plus one segment's
+// operands, for one extra forward pass over all but the last segment.
+// checkpoint = 0 is one segment: every operand kept, no replay.
+ftn_status contract_grad_impl(ftn_ctx ctx, const ftn_network* net, const ftn_tree* tree, int checkpoint,
+                              double* value, ftn_tensor* grads) {
   if (!ctx || !net || !tree || !value || !grads) return set_error(FTN_EINVAL, "null argument");
+  if (checkpoint < 0) return set_error(FTN_EINVAL, "checkpoint must be >= 0");
   for (int i = 0; i < net->n_tensors; ++i) grads[i] = nullptr;
   Exec E;
   FTN_TRY(E.init(ctx, net, tree, FTN_PREC_F64));
@@ -474,21 +513,27 @@ ftn_status contract_grad_impl(ftn_ctx ctx, const ftn_network* net, const ftn_tre
     uint64_t fa, fb;
     int chi, arrows;
   };
-  std::vector<Op> tape;
-  std::vector<ftn_tensor> kept;  // every tensor the tape refers to (freed at the end)
+  // Every tensor made here (the leaves' views included) is in `owned` until
+  // it is freed, every cotangent in `g`; both are released on every return.
+  std::set<ftn_tensor> owned;
   std::map<ftn_tensor, ftn_tensor> g;
   struct Cleanup {
-    std::vector<ftn_tensor>& k;
+    Exec& e;
+    std::set<ftn_tensor>& o;
     std::map<ftn_tensor, ftn_tensor>& g;
     ~Cleanup() {
-      for (ftn_tensor t : k) ftn_tensor_free(t);
+      e.live.clear();  // owned below, not by the executor
+      for (ftn_tensor t : o) ftn_tensor_free(t);
       for (auto& kv : g) ftn_tensor_free(kv.second);
     }
-  } cleanup{kept, g};
-  E.retain = &kept;
-  std::vector<ftn_tensor> leaves(E.n);  // the executor's views of the caller's tensors
-  for (int i = 0; i < E.n; ++i) leaves[i] = E.live[i].t;
-  auto compress_pair = [&](int64_t x, int64_t y) -> ftn_status {
+  } cleanup{E, owned, g};
+  for (auto& kv : E.live) owned.insert(kv.second.t);
+  auto drop = [&](ftn_tensor t) {
+    if (owned.erase(t)) ftn_tensor_free(t);
+  };
+  std::vector<ftn_tensor> consumed;  // operands of the current step (freed or kept by the caller)
+  E.retain = &consumed;
+  auto compress_pair = [&](int64_t x, int64_t y, std::vector<Op>* tape) -> ftn_status {
     std::vector<CompressItem> items(1);
     E.compress_item(x, y, items[0]);
     items[0].keep_inputs = true;
@@ -501,54 +546,64 @@ ftn_status contract_grad_impl(ftn_ctx ctx, const ftn_network* net, const ftn_tre
     op.chi = items[0].chi;
     op.arrows = items[0].arrows;
     FTN_TRY(compress_batch(ctx, items));
-    kept.push_back(op.a);
-    kept.push_back(op.b);
+    consumed.push_back(op.a);
+    consumed.push_back(op.b);
     op.c = items[0].X;
     op.d = items[0].Y;
+    owned.insert(op.c);
+    owned.insert(op.d);
     E.live[x].t = op.c;
     E.live[y].t = op.d;
     E.compress_done(x, y, items[0]);
-    tape.push_back(op);
+    if (tape) tape->push_back(op);
     return FTN_OK;
   };
-  for (int s = 0; s < E.n - 1; ++s) {
+  auto run_step = [&](int s, std::vector<Op>* tape) -> ftn_status {
     int64_t a, b;
     FTN_TRY(E.step_pair(s, a, b));
     if (tree->policy == FTN_POLICY_LATE)
-      for (auto& pr : E.late_pairs(a, b)) FTN_TRY(compress_pair(pr.first, pr.second));
+      for (auto& pr : E.late_pairs(a, b)) FTN_TRY(compress_pair(pr.first, pr.second, tape));
     std::vector<TdItem> items(1);
     int64_t e, l;
     E.step_item(a, b, e, l, items[0]);
     FTN_TRY(tensordot_batch(ctx, items, FTN_PREC_F64));
-    Op op{};
-    op.td = true;
-    op.a = items[0].A;
-    op.b = items[0].B;
-    op.c = items[0].C;
-    op.n = items[0].n;
-    for (int i = 0; i < op.n; ++i) op.ax[i] = items[0].ax[i], op.ay[i] = items[0].ay[i];
-    op.fa = items[0].fa;
-    op.fb = items[0].fb;
-    tape.push_back(op);
+    owned.insert(items[0].C);
+    if (tape) {
+      Op op{};
+      op.td = true;
+      op.a = items[0].A;
+      op.b = items[0].B;
+      op.c = items[0].C;
+      op.n = items[0].n;
+      for (int i = 0; i < op.n; ++i) op.ax[i] = items[0].ax[i], op.ay[i] = items[0].ay[i];
+      op.fa = items[0].fa;
+      op.fb = items[0].fb;
+      tape->push_back(op);
+    }
     const int64_t id = E.step_done(s, e, l, items[0]);
     if (tree->policy == FTN_POLICY_EARLY)
-      for (auto& pr : E.early_pairs(id)) FTN_TRY(compress_pair(pr.first, pr.second));
-  }
-  if (E.live.size() != 1) return set_error(FTN_EINVAL, "tree does not reduce the network to one tensor");
-  ftn_tensor last = E.live.begin()->second.t;
-  if (last->numel != 1) return set_error(FTN_EINVAL, "network is not closed (open legs remain)");
-  double v = 0.0;
-  FTN_CUDA(cudaMemcpyAsync(&v, last->data, 8, cudaMemcpyDeviceToHost, ctx->stream));
-  FTN_CUDA(cudaStreamSynchronize(ctx->stream));
-  *value = E.sign * v;
-  // seed: dv/d(last) = sign
-  {
-    ftn_tensor seed = nullptr;
-    FTN_TRY(make_tensor(ctx, last->rank, last->d0, last->d1, last->dual, last->parity, FTN_F64, &seed));
-    g[last] = seed;
-    const double sg = (double)E.sign;
-    FTN_CUDA(cudaMemcpyAsync(seed->data, &sg, 8, cudaMemcpyHostToDevice, ctx->stream));
-    FTN_CUDA(cudaStreamSynchronize(ctx->stream));  // the host source goes out of scope
+      for (auto& pr : E.early_pairs(id)) FTN_TRY(compress_pair(pr.first, pr.second, tape));
+    return FTN_OK;
+  };
+  const int S = E.n - 1;
+  const int k = (checkpoint == 0 || checkpoint >= S) ? std::max(S, 1) : checkpoint;
+  const int J = S <= 0 ? 1 : (S + k - 1) / k;
+  std::vector<Exec::State> snaps(J);
+  std::set<ftn_tensor> pinned;  // the checkpoints' tensors (kept until the end)
+  std::vector<ftn_tensor> leaves(E.n);  // the executor's views of the caller's tensors
+  for (int i = 0; i < E.n; ++i) leaves[i] = E.live[i].t;
+  E.save(snaps[0]);
+  for (auto& kv : E.live) pinned.insert(kv.second.t);
+  // first walk: up to the last checkpoint, keeping only the checkpoints
+  for (int s = 0; s < (J - 1) * k; ++s) {
+    FTN_TRY(run_step(s, nullptr));
+    for (ftn_tensor t : consumed)
+      if (!pinned.count(t)) drop(t);
+    consumed.clear();
+    if ((s + 1) % k == 0) {
+      E.save(snaps[(s + 1) / k]);
+      for (auto& kv : E.live) pinned.insert(kv.second.t);
+    }
   }
   auto cot = [&](ftn_tensor t, ftn_tensor* out) -> ftn_status {  // the cotangent of t (zeros if none reached it)
     auto it = g.find(t);
@@ -571,23 +626,80 @@ ftn_status contract_grad_impl(ftn_ctx ctx, const ftn_network* net, const ftn_tre
     g[t] = d;
     return FTN_OK;
   };
-  for (auto it = tape.rbegin(); it != tape.rend(); ++it) {
-    const Op& op = *it;
-    if (op.td) {
-      ftn_tensor G = nullptr, dA = nullptr, dB = nullptr;
-      FTN_TRY(cot(op.c, &G));
-      FTN_TRY(ftn_tensordot_grad(ctx, op.a, op.b, G, op.n, op.ax, op.ay, op.fa, op.fb, nullptr, FTN_PREC_F64, &dA,
-                                 &dB));
-      FTN_TRY(put(op.a, dA));
-      FTN_TRY(put(op.b, dB));
+  auto release = [&](ftn_tensor t) {  // a cotangent that has been passed on
+    auto it = g.find(t);
+    if (it == g.end()) return;
+    ftn_tensor_free(it->second);
+    g.erase(it);
+  };
+  for (int j = J - 1; j >= 0; --j) {
+    // replay segment j from its checkpoint, keeping its operands
+    E.load(snaps[j]);
+    std::vector<Op> tape;
+    consumed.clear();
+    const int s_end = std::min(S, (j + 1) * k);
+    for (int s = j * k; s < s_end; ++s) FTN_TRY(run_step(s, &tape));
+    if (j == J - 1) {
+      if (E.live.size() != 1) return set_error(FTN_EINVAL, "tree does not reduce the network to one tensor");
+      ftn_tensor last = E.live.begin()->second.t;
+      if (last->numel != 1) return set_error(FTN_EINVAL, "network is not closed (open legs remain)");
+      double v = 0.0;
+      FTN_CUDA(cudaMemcpyAsync(&v, last->data, 8, cudaMemcpyDeviceToHost, ctx->stream));
+      FTN_CUDA(cudaStreamSynchronize(ctx->stream));
+      *value = E.sign * v;
+      // seed: dv/d(last) = sign
+      ftn_tensor seed = nullptr;
+      FTN_TRY(make_tensor(ctx, last->rank, last->d0, last->d1, last->dual, last->parity, FTN_F64, &seed));
+      g[last] = seed;
+      const double sg = (double)E.sign;
+      FTN_CUDA(cudaMemcpyAsync(seed->data, &sg, 8, cudaMemcpyHostToDevice, ctx->stream));
+      FTN_CUDA(cudaStreamSynchronize(ctx->stream));  // the host source goes out of scope
     } else {
-      ftn_tensor gx = nullptr, gy = nullptr, dX = nullptr, dY = nullptr;
-      FTN_TRY(cot(op.c, &gx));
-      FTN_TRY(cot(op.d, &gy));
-      FTN_TRY(ftn_compress_grad(ctx, op.a, op.b, op.n, op.ax, op.ay, op.chi, op.arrows, gx, gy, &dX, &dY));
-      FTN_TRY(put(op.a, dX));
-      FTN_TRY(put(op.b, dY));
+      // the replayed end state is checkpoint j + 1: its tensors take the
+      // cotangents of that checkpoint's (same ids, same values)
+      if (E.live.size() != snaps[j + 1].live.size())
+        return set_error(FTN_EINVAL, "internal error: a replayed segment ends in another state");
+      for (auto& kv : E.live) {
+        auto sn = snaps[j + 1].live.find(kv.first);
+        if (sn == snaps[j + 1].live.end())
+          return set_error(FTN_EINVAL, "internal error: a replayed segment ends in another state");
+        const ftn_tensor ts = sn->second.t, tr = kv.second.t;
+        if (ts == tr) continue;
+        auto it = g.find(ts);
+        if (it == g.end()) continue;
+        const ftn_tensor d = it->second;
+        g.erase(it);
+        FTN_TRY(put(tr, d));
+      }
     }
+    for (auto it = tape.rbegin(); it != tape.rend(); ++it) {
+      const Op& op = *it;
+      if (op.td) {
+        ftn_tensor G = nullptr, dA = nullptr, dB = nullptr;
+        FTN_TRY(cot(op.c, &G));
+        FTN_TRY(ftn_tensordot_grad(ctx, op.a, op.b, G, op.n, op.ax, op.ay, op.fa, op.fb, nullptr, FTN_PREC_F64, &dA,
+                                   &dB));
+        release(op.c);
+        FTN_TRY(put(op.a, dA));
+        FTN_TRY(put(op.b, dB));
+      } else {
+        ftn_tensor gx = nullptr, gy = nullptr, dX = nullptr, dY = nullptr;
+        FTN_TRY(cot(op.c, &gx));
+        FTN_TRY(cot(op.d, &gy));
+        FTN_TRY(ftn_compress_grad(ctx, op.a, op.b, op.n, op.ax, op.ay, op.chi, op.arrows, gx, gy, &dX, &dY));
+        release(op.c);
+        release(op.d);
+        FTN_TRY(put(op.a, dX));
+        FTN_TRY(put(op.b, dY));
+      }
+    }
+    // the segment's tensors, but for the checkpoints', are no longer needed
+    for (ftn_tensor t : consumed)
+      if (!pinned.count(t)) drop(t);
+    consumed.clear();
+    for (auto& kv : E.live)
+      if (!pinned.count(kv.second.t)) drop(kv.second.t);
+    E.live.clear();
   }
   // the leaves' cotangents (the views have the caller's legs)
   for (int i = 0; i < E.n; ++i) {
@@ -712,9 +824,9 @@ ftn_status ftn_contract(ftn_ctx ctx, const ftn_network* net, const ftn_tree* tre
   return contract_impl(ctx, net, tree, prec, mantissa, log_scale);
 }
 
-ftn_status ftn_contract_grad(ftn_ctx ctx, const ftn_network* net, const ftn_tree* tree, double* value,
-                             ftn_tensor* grads) {
-  return contract_grad_impl(ctx, net, tree, value, grads);
+ftn_status ftn_contract_grad(ftn_ctx ctx, const ftn_network* net, const ftn_tree* tree, int checkpoint,
+                             double* value, ftn_tensor* grads) {
+  return contract_grad_impl(ctx, net, tree, checkpoint, value, grads);
 }
 
 ftn_status ftn_contract_batch(ftn_ctx ctx, int count, const ftn_network* nets, const ftn_tree* trees, ftn_prec prec,

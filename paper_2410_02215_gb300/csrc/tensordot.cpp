@@ -431,7 +431,7 @@ static ftn_status build_plan(ftn_ctx ctx, const ftn_tensor_s* A, const ftn_tenso
   // grouped tile list, which covers probs[0, n_tiled))
   std::vector<GemmProb> small_tc;
   if (tc) {
-    auto mid = std::stable_partition(P->probs.begin(), P->probs.end(), [](const GemmProb& g) { return !f64w_small(g); });
+    auto mid = std::stable_partition(P->probs.begin(), P->probs.end(), [](const GemmProb& g) { return !tcw_small(g); });
     small_tc.assign(mid, P->probs.end());
     P->probs.erase(mid, P->probs.end());
   }

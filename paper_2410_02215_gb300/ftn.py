@@ -89,7 +89,7 @@ def lib():
         "ftn_contract": [vp, C.POINTER(Network), C.POINTER(Tree), C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double)],
         "ftn_contract_batch": [vp, C.c_int, C.POINTER(Network), C.POINTER(Tree), C.c_int, C.POINTER(C.c_double),
                                C.POINTER(C.c_double)],
-        "ftn_contract_grad": [vp, C.POINTER(Network), C.POINTER(Tree), C.POINTER(C.c_double), C.POINTER(vp)],
+        "ftn_contract_grad": [vp, C.POINTER(Network), C.POINTER(Tree), C.c_int, C.POINTER(C.c_double), C.POINTER(vp)],
         "ftn_hubbard_term": [vp, C.c_int, C.c_double, C.c_double, C.c_int, C.POINTER(vp)],
         "ftn_energy_reduce": [C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double), C.c_int, i32p, i32p, C.c_int,
                               i32p, C.POINTER(C.c_double), C.POINTER(C.c_double)],
@@ -457,6 +457,109 @@ def tensordot_autograd(ctx, a_data, legs_a, parity_a, b_data, legs_b, parity_b, 
     return c, _result_legs(spec[1], spec[3], spec[5], spec[6], spec[9]), spec[2] ^ spec[4]
 
 
+class _CompressFn:
+    """torch.autograd.Function over ftn_compress (forward) and
+    ftn_compress_grad (backward) on flat FP64 block-data tensors (built
+    lazily so that importing this module does not need torch)."""
+
+    _cls = None
+
+    @classmethod
+    def get(cls):
+        if cls._cls is None:
+            import torch
+
+            class Fn(torch.autograd.Function):
+                @staticmethod
+                def forward(fctx, x_data, y_data, spec):
+                    ctx, lx, px, ly, py, axx, axy, chi, arrows, out = spec
+                    # ftn_compress consumes its operands: it gets copies
+                    x = Tensor.wrap(ctx, lx, px, x_data.detach().clone(), F64)
+                    y = Tensor.wrap(ctx, ly, py, y_data.detach().clone(), F64)
+                    xn, yn, info = compress(ctx, x, y, axx, axy, chi, arrows)
+                    out.update(legs_x=xn.legs, parity_x=xn.parity, legs_y=yn.legs, parity_y=yn.parity, info=info)
+                    fctx.save_for_backward(x_data, y_data)
+                    fctx.spec = spec
+                    xd, yd = xn.view().clone(), yn.view().clone()
+                    ctx.synchronize()
+                    return xd, yd
+
+                @staticmethod
+                def backward(fctx, gx, gy):
+                    x_data, y_data = fctx.saved_tensors
+                    ctx, lx, px, ly, py, axx, axy, chi, arrows, out = fctx.spec
+                    x = Tensor.wrap(ctx, lx, px, x_data, F64)
+                    y = Tensor.wrap(ctx, ly, py, y_data, F64)
+                    nx = _numel(out["legs_x"], out["parity_x"])
+                    ny = _numel(out["legs_y"], out["parity_y"])
+                    gx = torch.zeros(nx, dtype=torch.float64, device=x_data.device) if gx is None else gx.contiguous()
+                    gy = torch.zeros(ny, dtype=torch.float64, device=x_data.device) if gy is None else gy.contiguous()
+                    dxn = Tensor.wrap(ctx, out["legs_x"], out["parity_x"], gx, F64)
+                    dyn = Tensor.wrap(ctx, out["legs_y"], out["parity_y"], gy, F64)
+                    dx, dy = compress_grad(ctx, x, y, axx, axy, chi, dxn, dyn, arrows)
+                    dxd, dyd = dx.view().clone(), dy.view().clone()
+                    ctx.synchronize()
+                    return dxd, dyd, None
+
+            cls._cls = Fn
+        return cls._cls
+
+
+def compress_autograd(ctx, x_data, legs_x, parity_x, y_data, legs_y, parity_y, axes_x, axes_y, chi, arrows=True):
+    """Differentiable bond compression on flat FP64 torch CUDA tensors holding
+    the blocks of X and Y: returns (X' data, X' legs, X' parity, Y' data, Y'
+    legs, Y' parity).  Forward ftn_compress (on copies: x_data and y_data are
+    left as they are), backward ftn_compress_grad."""
+    out = {}
+    spec = (ctx, [tuple(l) for l in legs_x], int(parity_x), [tuple(l) for l in legs_y], int(parity_y),
+            list(axes_x), list(axes_y), int(chi), bool(arrows), out)
+    xd, yd = _CompressFn.get().apply(x_data, y_data, spec)
+    return xd, out["legs_x"], out["parity_x"], yd, out["legs_y"], out["parity_y"]
+
+
+class _NetworkValueFn:
+    """torch.autograd.Function for the value of a closed network of even FP64
+    tensors: the forward runs ftn_contract_grad, which forms the gradient with
+    the value; the backward hands it on, scaled by the incoming cotangent."""
+
+    _cls = None
+
+    @classmethod
+    def get(cls):
+        if cls._cls is None:
+            import torch
+
+            class Fn(torch.autograd.Function):
+                @staticmethod
+                def forward(fctx, spec, *datas):
+                    ctx, legs, parities, job, checkpoint = spec
+                    ts = [Tensor.wrap(ctx, lg, p, d.detach().contiguous(), F64) for lg, p, d in zip(legs, parities, datas)]
+                    v, grads = contract_grad(ctx, ts, job["bonds"], job["tree"], job.get("positions"),
+                                             job.get("policy", "exact"), job.get("chi", 0), checkpoint)
+                    gd = [g.view().clone() for g in grads]
+                    ctx.synchronize()
+                    fctx.save_for_backward(*gd)
+                    return torch.tensor(v, dtype=torch.float64, device=datas[0].device)
+
+                @staticmethod
+                def backward(fctx, gv):
+                    return (None,) + tuple(gv * g for g in fctx.saved_tensors)
+
+            cls._cls = Fn
+        return cls._cls
+
+
+def network_value_autograd(ctx, datas, legs, parities, bonds, tree, positions=None, policy="exact", chi=0,
+                           checkpoint=0):
+    """Differentiable value of a closed network (ftn_contract_grad) of even
+    FP64 tensors given as flat torch CUDA tensors of block data with their
+    legs and parities; returns a 0-dim FP64 tensor.  ``checkpoint`` as in
+    contract_grad."""
+    job = {"bonds": bonds, "tree": tree, "positions": positions, "policy": policy, "chi": chi}
+    spec = (ctx, [[tuple(l) for l in lg] for lg in legs], [int(p) for p in parities], job, int(checkpoint))
+    return _NetworkValueFn.get().apply(spec, *datas)
+
+
 def transpose(ctx, t, perm, out=None):
     h = C.c_void_p(out.handle.value if out is not None else None)
     _check(lib().ftn_tensor_transpose(ctx.handle, t.handle, _int(perm), C.byref(h)))
@@ -503,14 +606,16 @@ def contract(ctx, tensors, bonds, tree, positions=None, policy="exact", chi=0, p
     return m.value, lg.value
 
 
-def contract_grad(ctx, tensors, bonds, tree, positions=None, policy="exact", chi=0):
+def contract_grad(ctx, tensors, bonds, tree, positions=None, policy="exact", chi=0, checkpoint=0):
     """Value of a closed network of even FP64 tensors and dv/dT for every
-    tensor (ftn_contract_grad): returns (value, [gradient tensors])."""
+    tensor (ftn_contract_grad): returns (value, [gradient tensors]).
+    ``checkpoint`` = k > 0 keeps the walk's state every k steps and replays
+    the segments in the backward (0: every intermediate kept)."""
     n, net_arr, tree_arr, keep = _network_arrays([{"tensors": tensors, "bonds": bonds, "tree": tree,
                                                    "positions": positions, "policy": policy, "chi": chi}])
     v = C.c_double()
     out = (C.c_void_p * max(1, len(tensors)))()
-    _check(lib().ftn_contract_grad(ctx.handle, net_arr, tree_arr, C.byref(v), out))
+    _check(lib().ftn_contract_grad(ctx.handle, net_arr, tree_arr, int(checkpoint), C.byref(v), out))
     del keep
     return v.value, [Tensor(ctx, C.c_void_p(out[i])) for i in range(len(tensors))]
 

@@ -117,6 +117,41 @@ def test_boundary_mps_gradient_finite_differences(F, ctx, mode):
     assert worst < 1e-6, worst
 
 
+@pytest.mark.parametrize("mode", ["local", "global"])
+@pytest.mark.parametrize("case", ["exact", "late", "early", "boundary"])
+def test_checkpointed_gradient_is_bit_identical(F, ctx, case, mode):
+    """checkpoint = k keeps the walk's state every k steps and replays each
+    segment in the backward: the value and every gradient entry equal those
+    of the fully taped walk (checkpoint = 0) bit for bit, for segments of one
+    step up to past the whole tree."""
+    if case == "boundary":
+        net, tree = setup(3, 3, (1, 1), 3, boundary=True)
+        policy, chi = "late", 3
+    else:
+        net, tree = setup(2, 3, (1, 1), 3)
+        policy, chi = case, (0 if case == "exact" else 2)
+    tensors = [F.Tensor.from_blocks(ctx, t.legs, t.parity, sorted(O.extract_blocks(t).items())) for t in net.tensors]
+    pos = list(net.positions) if mode == "global" else None
+    v0, g0 = F.contract_grad(ctx, tensors, net.bonds, tree, positions=pos, policy=policy, chi=chi)
+    ref = [g.download() for g in g0]
+    steps = len(tree)
+    for k in sorted({1, 2, 3, 5, steps - 1, steps, steps + 4}):
+        v, gk = F.contract_grad(ctx, tensors, net.bonds, tree, positions=pos, policy=policy, chi=chi, checkpoint=k)
+        assert v == v0, k
+        for r, gg in zip(ref, gk):
+            assert np.array_equal(r, gg.download()), k
+
+
+def test_checkpoint_argument_checked(F, ctx):
+    net, tree = setup(2, 2, (1, 1), 3)
+    tensors = [F.Tensor.from_blocks(ctx, t.legs, t.parity, sorted(O.extract_blocks(t).items())) for t in net.tensors]
+    with pytest.raises(F.FtnError) as e:
+        F.contract_grad(ctx, tensors, net.bonds, tree, checkpoint=-1)
+    assert e.value.status == -1
+    v, grads = F.contract_grad(ctx, tensors, net.bonds, tree, checkpoint=1)  # the context is still usable
+    assert np.isfinite(v) and len(grads) == len(tensors)
+
+
 def test_network_grad_rejects_odd_tensors(F, ctx):
     la = [(1, 1, 0), (1, 1, 1)]
     a = F.Tensor.from_blocks(ctx, la, 1, W.random_blocks(la, 1, 1))
