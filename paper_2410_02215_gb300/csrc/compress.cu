@@ -1143,49 +1143,66 @@ __global__ void __launch_bounds__(256) perm_adjoint_kernel(const PermJob* jobs, 
 // n-side vectors core x v_j / s_j carry ~eps s_max / s_j of the directions of
 // larger singular values, which the F-matrix terms of the adjoint would pick
 // up; this removes them, as the forward does for its kept vectors.
-struct OrdOrthJob {
-  double* v;
-  const int* ord;
-  int nv, n;
+// Rows moved between the core's row order and the order of decreasing
+// singular values: dst row q = src row idx[q] (gather) or dst row idx[q] =
+// src row q (scatter); rows of len doubles.
+struct RowsJob {
+  const double* src;
+  double* dst;
+  const int* idx;
+  int nrows, len, scatter;
 };
-__global__ void __launch_bounds__(256) orth_ordered_kernel(const OrdOrthJob* jobs) {
-  __shared__ double h[LA_MAX_DIM];
-  __shared__ double red[9];
-  const OrdOrthJob J = jobs[blockIdx.x];
-  const int n = J.n, t = threadIdx.x, lane = t & 31, warp = t >> 5, nw = blockDim.x >> 5;
-  for (int q = 0; q < J.nv; ++q) {
-    double* vj = J.v + (int64_t)J.ord[q] * n;
-    for (int pass = 0; pass < 2 && q > 0; ++pass) {
-      for (int i = warp; i < q; i += nw) {
-        const double* vi = J.v + (int64_t)J.ord[i] * n;
-        double d = 0.0;
-        for (int e = lane; e < n; e += 32) d = fma(vi[e], vj[e], d);
-        for (int o = 16; o; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
-        if (lane == 0) h[i] = d;
-      }
-      __syncthreads();
-      for (int e = t; e < n; e += blockDim.x) {
-        double a = vj[e];
-        for (int i = 0; i < q; ++i) a = fma(-h[i], J.v[(int64_t)J.ord[i] * n + e], a);
-        vj[e] = a;
-      }
-      __syncthreads();
-    }
-    double s2 = 0.0;
-    for (int e = t; e < n; e += blockDim.x) s2 = fma(vj[e], vj[e], s2);
-    for (int o = 16; o; o >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, o);
-    if (lane == 0) red[warp] = s2;
+__global__ void __launch_bounds__(256) rows_move_kernel(const RowsJob* jobs) {
+  const RowsJob J = jobs[blockIdx.x];
+  for (int64_t e = threadIdx.x; e < (int64_t)J.nrows * J.len; e += blockDim.x) {
+    const int q = (int)(e / J.len), c = (int)(e - (int64_t)q * J.len);
+    const int64_t a = (int64_t)q * J.len + c, b = (int64_t)J.idx[q] * J.len + c;
+    J.dst[J.scatter ? b : a] = J.src[J.scatter ? a : b];
+  }
+}
+
+// G (n x n, row-major, symmetric positive definite, n <= ORTH_B) := L^{-1},
+// G = L L^T with L lower triangular (Cholesky, column by column), the
+// inverse by forward substitution, one column per thread.  A pivot that is
+// not positive zeroes its row of the inverse.
+constexpr int ORTH_B = 48;
+struct CholInvJob {
+  double* g;
+  int n;
+};
+__global__ void __launch_bounds__(256) chol_inv_small_kernel(const CholInvJob* jobs) {
+  __shared__ double L[ORTH_B][ORTH_B + 1];
+  __shared__ double Y[ORTH_B][ORTH_B + 1];
+  const CholInvJob J = jobs[blockIdx.x];
+  const int n = J.n, t = threadIdx.x;
+  for (int e = t; e < n * n; e += blockDim.x) L[e / n][e % n] = J.g[e];
+  __syncthreads();
+  for (int j = 0; j < n; ++j) {
+    if (t == 0) L[j][j] = L[j][j] > 0.0 ? sqrt(L[j][j]) : 0.0;
     __syncthreads();
-    if (t == 0) {
-      double tot = 0.0;
-      for (int w = 0; w < nw; ++w) tot += red[w];
-      red[8] = tot > 0.0 ? 1.0 / sqrt(tot) : 0.0;
-    }
+    const double dj = L[j][j];
+    for (int i = j + 1 + t; i < n; i += blockDim.x) L[i][j] = dj > 0.0 ? L[i][j] / dj : 0.0;
     __syncthreads();
-    const double f = red[8];
-    for (int e = t; e < n; e += blockDim.x) vj[e] *= f;
+    const int w = n - j - 1;
+    for (int e = t; e < w * w; e += blockDim.x) {
+      const int a = j + 1 + e / w, b = j + 1 + e % w;
+      if (b <= a) L[a][b] = fma(-L[a][j], L[b][j], L[a][b]);
+    }
     __syncthreads();
   }
+  for (int c = t; c < n; c += blockDim.x) {
+    for (int i = 0; i < n; ++i) {
+      if (i < c || L[i][i] == 0.0) {
+        Y[i][c] = 0.0;
+        continue;
+      }
+      double v = i == c ? 1.0 : 0.0;
+      for (int k = c; k < i; ++k) v = fma(-L[i][k], Y[k][c], v);
+      Y[i][c] = v / L[i][i];
+    }
+  }
+  __syncthreads();
+  for (int e = t; e < n * n; e += blockDim.x) J.g[e] = Y[e / n][e % n];
 }
 
 // out[m, c] += a[m, c] (rows x cols; row strides lda, ldo)
@@ -1195,20 +1212,19 @@ struct Add2Job {
   int rows, cols;
   int64_t lda, ldo;
 };
+// (grid: jobs x row slices; slice y takes rows y, y + gridDim.y, ...)
 __global__ void __launch_bounds__(256) add2_kernel(const Add2Job* jobs) {
   const Add2Job J = jobs[blockIdx.x];
-  for (int64_t e = threadIdx.x; e < (int64_t)J.rows * J.cols; e += blockDim.x) {
-    const int m = (int)(e / J.cols), c = (int)(e - (int64_t)m * J.cols);
-    J.out[m * J.ldo + c] += J.a[m * J.lda + c];
-  }
+  for (int m = blockIdx.y; m < J.rows; m += gridDim.y)
+    for (int c = threadIdx.x; c < J.cols; c += blockDim.x) J.out[m * J.ldo + c] += J.a[m * J.lda + c];
 }
 
 template <typename T>
-ftn_status launch_jobs(ftn_ctx ctx, void (*k)(const T*), const std::vector<T>& jobs) {
+ftn_status launch_jobs(ftn_ctx ctx, void (*k)(const T*), const std::vector<T>& jobs, unsigned slices = 1) {
   if (jobs.empty()) return FTN_OK;
   DevBuf t(ctx);
   FTN_TRY(put_table(ctx, jobs, &t.p));
-  k<<<(unsigned)jobs.size(), 256, 0, ctx->stream>>>((const T*)t.p);
+  k<<<dim3((unsigned)jobs.size(), slices), 256, 0, ctx->stream>>>((const T*)t.p);
   ctx->launches += 1;
   FTN_CUDA(cudaGetLastError());
   return FTN_OK;
@@ -1688,15 +1704,96 @@ ftn_status cj_backward(ftn_ctx ctx, std::vector<CJob*>& gj, const std::vector<do
   }));
   {
     std::vector<RowDivJob> rd;
-    std::vector<CotJob> cj;
-    for (Sec& c : secs) {
-      rd.push_back({c.Oth, c.Oth, c.s, c.r, c.r, c.tol});
-      cj.push_back({c.dZ, c.dW, c.Ut, c.Vt, c.s, c.idx, c.dUt, c.dVt, c.ds, c.k, c.r, c.rx, c.ry});
-    }
+    for (Sec& c : secs) rd.push_back({c.Oth, c.Oth, c.s, c.r, c.r, c.tol});
     FTN_TRY(launch_jobs(ctx, row_div_kernel, rd));
-    std::vector<OrdOrthJob> oj;
-    for (Sec& c : secs) oj.push_back({c.Oth, c.ord, c.nord, c.r});
-    FTN_TRY(launch_jobs(ctx, orth_ordered_kernel, oj));
+  }
+  // The rebuilt vectors (rows of Oth, each of length r) re-orthonormalised in
+  // the order of decreasing singular values (Gram-Schmidt order: the vectors
+  // of the larger singular values, the more accurate ones, first).  Blocks of
+  // ORTH_B rows of the ordered copy Vo: a block is projected twice against
+  // every row before it (H = V_prev V_b^T, V_b -= H^T V_prev), then made
+  // orthonormal within itself by CholeskyQR (G = V_b V_b^T = L L^T, V_b :=
+  // L^{-1} V_b), which the near-orthonormal rows keep stable.  In exact
+  // arithmetic this is the QR factorisation's Q, as Gram-Schmidt gives it;
+  // the products run as grouped FP64 GEMMs across the GPU.
+  {
+    struct Orth {
+      double *Vo, *H, *T, *G;
+    };
+    std::vector<Orth> ow(secs.size());
+    std::vector<std::unique_ptr<DevBuf>> obufs;
+    std::vector<RowsJob> mv;
+    int nblk = 0;
+    for (size_t q = 0; q < secs.size(); ++q) {
+      const Sec& c = secs[q];
+      if (c.nord == 0 || c.r == 0) continue;
+      const int64_t nr = c.nord, r = c.r;
+      obufs.emplace_back(new DevBuf(ctx));
+      obufs.back()->p = dev_alloc(ctx, (size_t)(nr * r + nr * ORTH_B + ORTH_B * r + ORTH_B * ORTH_B + 16) * 8);
+      if (!obufs.back()->p) return set_error(FTN_ENOMEM, "compression adjoint: workspace allocation failed");
+      double* p = (double*)obufs.back()->p;
+      ow[q] = {p, p + nr * r, p + nr * r + nr * ORTH_B, p + nr * r + nr * ORTH_B + ORTH_B * r};
+      mv.push_back({c.Oth, ow[q].Vo, c.ord, c.nord, c.r, 0});
+      nblk = std::max(nblk, (c.nord + ORTH_B - 1) / ORTH_B);
+    }
+    FTN_TRY(launch_jobs(ctx, rows_move_kernel, mv));
+    for (int bk = 0; bk < nblk; ++bk) {
+      const int prev = bk * ORTH_B;
+      auto in_blk = [&](const Sec& c) { return c.r > 0 && prev < c.nord; };
+      auto nb_of = [&](const Sec& c) { return std::min(ORTH_B, c.nord - prev); };
+      for (int pass = 0; pass < 2 && prev > 0; ++pass) {
+        FTN_TRY(stage([&](GemmF64Batch& gb, Sec& c) -> ftn_status {
+          if (!in_blk(c)) return FTN_OK;
+          const Orth& o = ow[&c - secs.data()];
+          const double* Vb = o.Vo + (int64_t)prev * c.r;
+          return gemm(gb, prev, nb_of(c), c.r, o.Vo, c.r, 1, Vb, c.r, 1, o.H, nb_of(c));
+        }));
+        FTN_TRY(stage([&](GemmF64Batch& gb, Sec& c) -> ftn_status {
+          if (!in_blk(c)) return FTN_OK;
+          const Orth& o = ow[&c - secs.data()];
+          return gemm(gb, nb_of(c), c.r, prev, o.H, 1, nb_of(c), o.Vo, 1, c.r, o.T, c.r);
+        }));
+        std::vector<AxpyJob> sub;
+        for (Sec& c : secs)
+          if (in_blk(c)) {
+            double* Vb = ow[&c - secs.data()].Vo + (int64_t)prev * c.r;
+            sub.push_back({Vb, ow[&c - secs.data()].T, Vb, nullptr, nullptr, (int64_t)nb_of(c) * c.r, c.r, -1.0});
+          }
+        FTN_TRY(launch_jobs(ctx, axpy_kernel, sub));
+      }
+      FTN_TRY(stage([&](GemmF64Batch& gb, Sec& c) -> ftn_status {
+        if (!in_blk(c)) return FTN_OK;
+        const Orth& o = ow[&c - secs.data()];
+        const double* Vb = o.Vo + (int64_t)prev * c.r;
+        return gemm(gb, nb_of(c), nb_of(c), c.r, Vb, c.r, 1, Vb, c.r, 1, o.G, nb_of(c));
+      }));
+      std::vector<CholInvJob> ci;
+      for (Sec& c : secs)
+        if (in_blk(c)) ci.push_back({ow[&c - secs.data()].G, nb_of(c)});
+      FTN_TRY(launch_jobs(ctx, chol_inv_small_kernel, ci));
+      FTN_TRY(stage([&](GemmF64Batch& gb, Sec& c) -> ftn_status {
+        if (!in_blk(c)) return FTN_OK;
+        const Orth& o = ow[&c - secs.data()];
+        const double* Vb = o.Vo + (int64_t)prev * c.r;
+        return gemm(gb, nb_of(c), c.r, nb_of(c), o.G, nb_of(c), 1, Vb, 1, c.r, o.T, c.r);
+      }));
+      std::vector<AxpyJob> cp;
+      for (Sec& c : secs)
+        if (in_blk(c)) {
+          double* Vb = ow[&c - secs.data()].Vo + (int64_t)prev * c.r;
+          cp.push_back({nullptr, ow[&c - secs.data()].T, Vb, nullptr, nullptr, (int64_t)nb_of(c) * c.r, c.r, 1.0});
+        }
+      FTN_TRY(launch_jobs(ctx, axpy_kernel, cp));
+    }
+    std::vector<RowsJob> back;
+    for (size_t q = 0; q < secs.size(); ++q)
+      if (secs[q].nord > 0 && secs[q].r > 0)
+        back.push_back({ow[q].Vo, secs[q].Oth, secs[q].ord, secs[q].nord, secs[q].r, 1});
+    FTN_TRY(launch_jobs(ctx, rows_move_kernel, back));
+  }
+  {
+    std::vector<CotJob> cj;
+    for (Sec& c : secs) cj.push_back({c.dZ, c.dW, c.Ut, c.Vt, c.s, c.idx, c.dUt, c.dVt, c.ds, c.k, c.r, c.rx, c.ry});
     FTN_TRY(launch_jobs(ctx, svd_cot_kernel, cj));
   }
   // X = U^T dU, Y = V^T dV, then X^T Ut and Y^T Vt
@@ -1802,7 +1899,7 @@ ftn_status cj_backward(ftn_ctx ctx, std::vector<CJob*>& gj, const std::vector<do
     for (int w = 0; w < 4; ++w) {
       std::vector<Add2Job> one;
       for (size_t i = w; i < ad.size(); i += 4) one.push_back(ad[i]);
-      FTN_TRY(launch_jobs(ctx, add2_kernel, one));
+      FTN_TRY(launch_jobs(ctx, add2_kernel, one, 32));
     }
   }
   // dX, dY: the adjoint of the forward's sign-permutes

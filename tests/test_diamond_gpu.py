@@ -89,7 +89,10 @@ def test_diamond_terms_match_oracle(F, ctx):
         kets = [F.Tensor.from_blocks(ctx, lay["legs"][s], 0, blocks[s], dt) for s in range(lay["n"])]
         (e, rat), = peps.cluster_energies(ctx, [(lay, kets, cfn(lay), gs)], 1.0, 8.0, policy="late", chi=32, prec=prec,
                                           terms=terms)
-        assert e == sum(rat)
+        acc = 0.0  # the documented order: ratios added one by one in term order (Python's sum() compensates)
+        for r in rat:
+            acc += r
+        assert e == acc
         out[prec] = rat
     scale = max(abs(y) for y in ref)
     assert max(abs(x - y) for x, y in zip(out["f64"], ref)) <= 1e-10 * scale
