@@ -719,7 +719,34 @@ GRADIENT_WORKLOAD = ("gradient of the norm <Psi|Psi> of an fPEPS on a 6x6 open s
                      "locally ordered; dv/dT for all 72 tensors (kets and bras as independent inputs), FP64")
 
 
-def gradient_bench(F, ctx, evals, samples=20, h=1e-6):
+def kernel_breakdown(torch, fn, top=12):
+    """Device time per kernel of one call of fn, from torch's profiler (CUDA
+    activity; a profile, not a timing: the numbers reported as rates come
+    from the runs outside it)."""
+    import collections
+
+    from torch.profiler import ProfilerActivity, profile
+
+    fn()  # the profiler's first session can miss kernels: one call outside it first
+    torch.cuda.synchronize()
+    with profile(activities=[ProfilerActivity.CUDA]) as prof:
+        fn()
+        torch.cuda.synchronize()
+    agg = collections.defaultdict(lambda: [0, 0.0])
+    for ev in prof.events():
+        if ev.device_type == torch.autograd.DeviceType.CUDA:
+            t = getattr(ev, "device_time_total", None)
+            if t is None:
+                t = ev.cuda_time_total
+            a = agg[ev.name.split("(")[0]]
+            a[0] += 1
+            a[1] += t / 1000.0
+    tot = sum(v[1] for v in agg.values()) or 1.0
+    rows = sorted(agg.items(), key=lambda kv: -kv[1][1])[:top]
+    return {"total_ms": tot, "kernels": [{"name": k, "launches": c, "ms": ms, "share": ms / tot} for k, (c, ms) in rows]}
+
+
+def gradient_bench(F, ctx, evals, samples=20, h=1e-6, kernels=False):
     """Gradient evaluations per second of the compressed norm network (the
     config-5 workload) through ftn_contract_grad with checkpointed
     recomputation (the walk's state kept every ceil(sqrt(steps)) steps, each
@@ -766,6 +793,13 @@ def gradient_bench(F, ctx, evals, samples=20, h=1e-6):
         finally:
             c.close()
 
+    breakdown = None
+    if kernels:
+        c = F.Context()
+        try:
+            breakdown = kernel_breakdown(torch, lambda: F.contract_grad(c, tensors, bonds, tree, policy="late", chi=48))
+        finally:
+            c.close()
     v, host, s_ck, launches, peak_ck = run(k_ck)
     v0, host0, s_0, launches0, peak_0 = run(0)
     same = v == v0 and all(np.array_equal(a[key], b[key]) for a, b in zip(host, host0) for key in a)
@@ -796,6 +830,7 @@ def gradient_bench(F, ctx, evals, samples=20, h=1e-6):
             "no_checkpoint": {"gradient_evals_per_s": 1.0 / s_0, "s_per_gradient": s_0, "peak_bytes": peak_0,
                               "gpu_launches_per_gradient": launches0},
             "same_as_no_checkpoint": bool(same),
+            **({"kernel_breakdown_no_checkpoint": breakdown} if breakdown else {}),
             "gpu_launches_per_gradient": launches, "value": v,
             "value_rel_err_vs_contract": abs(m * np.exp(lg) - v) / abs(v),
             "fd": {"samples": samples, "h": h, "max_abs_err_over_max_grad": worst, "s": fd_s,
@@ -990,7 +1025,7 @@ def run_ours(args, rank, world, local):
         result["energy"] = energy_bench(F, ctx, args.energy_evals, rank == 0 and world == 1 and not args.no_cpu,
                                         args.energy_streams)
     if not args.no_gradient:
-        result["gradient"] = gradient_bench(F, ctx, args.gradient_evals)
+        result["gradient"] = gradient_bench(F, ctx, args.gradient_evals, kernels=args.gradient_kernels)
     if not args.no_diamond:
         result["energy_diamond"] = diamond_bench(F, ctx, torch, args.diamond_evals, args.cluster_streams,
                                                  rank == 0 and world == 1 and not args.no_cpu, rank, world)
@@ -1030,6 +1065,8 @@ def main():
     ap.add_argument("--no-diamond", action="store_true")
     ap.add_argument("--no-gradient", action="store_true")
     ap.add_argument("--gradient-evals", type=int, default=3)
+    ap.add_argument("--gradient-kernels", action="store_true",
+                    help="add a per-kernel device-time breakdown of one gradient (torch profiler)")
     ap.add_argument("--diamond-evals", type=int, default=2)
     args = ap.parse_args()
     if args.warmup < 3:
