@@ -727,8 +727,12 @@ def kernel_breakdown(torch, fn, top=12):
 
     from torch.profiler import ProfilerActivity, profile
 
-    fn()  # the profiler's first session can miss kernels: one call outside it first
-    torch.cuda.synchronize()
+    # the first profiler session of a process records no kernels: one
+    # session is spent on a warm-up call
+    for _ in range(2):
+        with profile(activities=[ProfilerActivity.CUDA]) as prof:
+            fn()
+            torch.cuda.synchronize()
     with profile(activities=[ProfilerActivity.CUDA]) as prof:
         fn()
         torch.cuda.synchronize()
@@ -738,7 +742,7 @@ def kernel_breakdown(torch, fn, top=12):
             t = getattr(ev, "device_time_total", None)
             if t is None:
                 t = ev.cuda_time_total
-            a = agg[ev.name.split("(")[0]]
+            a = agg[ev.name.replace("(anonymous namespace)::", "").split("(")[0]]
             a[0] += 1
             a[1] += t / 1000.0
     tot = sum(v[1] for v in agg.values()) or 1.0
