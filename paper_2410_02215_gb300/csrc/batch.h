@@ -118,6 +118,8 @@ struct TdItem {
 // share one dtype matching prec.
 ftn_status tensordot_batch(ftn_ctx ctx, std::vector<TdItem>& items, ftn_prec prec);
 
+struct CompressState;  // a compression's forward kept for its adjoint (compress.cu)
+
 struct CompressItem {
   ftn_tensor X = nullptr, Y = nullptr;  // replaced by the compressed pair (inputs freed)
   int n = 0;
@@ -133,9 +135,21 @@ struct CompressItem {
   // keep X and Y (the caller still owns them) while X, Y are replaced by the
   // compressed pair
   bool keep_inputs = false;
+  // a batch of one with keep_inputs: the forward's state (its workspace, job
+  // and singular values) is kept in *keep_state for compress_backward, which
+  // then runs the adjoint without recomputing the forward
+  CompressState** keep_state = nullptr;
 };
 // ftn_compress for every item (FP64 tensors).
 ftn_status compress_batch(ftn_ctx ctx, std::vector<CompressItem>& items);
+
+// The adjoint of a kept compression (CompressItem::keep_state): gXn, gYn are
+// the cotangents of the compressed pair, dX, dY receive new tensors with the
+// inputs' legs.  The inputs must still be alive; the state stays valid (and
+// is released by free_compress_state).
+ftn_status compress_backward(ftn_ctx ctx, CompressState* st, ftn_tensor gXn, ftn_tensor gYn, ftn_tensor* dX,
+                             ftn_tensor* dY);
+void free_compress_state(CompressState* st);
 
 struct NormItem {
   ftn_tensor t;

@@ -1930,6 +1930,20 @@ ftn_status cj_backward(ftn_ctx ctx, std::vector<CJob*>& gj, const std::vector<do
 
 }  // namespace
 
+// A compression's forward kept for its adjoint: the item (inputs, bond, chi),
+// its job (plan, offsets into the workspace, kept states), the workspace it
+// ran in, and the singular values it read back.
+struct CompressState {
+  ftn_ctx ctx = nullptr;
+  CompressItem item;
+  std::vector<CJob> jobs;
+  void* buf = nullptr;
+  std::vector<double> sv;
+  double* sbuf = nullptr;
+  int64_t xn_numel = 0, yn_numel = 0;
+  int xn_parity = 0, yn_parity = 0;
+};
+
 // Batched compression: every stage of every job contributes to one launch
 // per kernel; two host synchronisations per batch (the R-factor row counts
 // and the singular values).
@@ -1954,7 +1968,15 @@ ftn_status compress_batch(ftn_ctx ctx, std::vector<CompressItem>& items) {
     }
   const int64_t cnt_words = ((int64_t)jobs.size() * 8 * (int64_t)sizeof(int) + 7) / 8;
   const int64_t chk_words = (int64_t)jobs.size() * 8;  // per job: |A|_F^2 of the 4 sides, then |E|_F^2
-  double* ws = (double*)workspace(ctx, (size_t)(total + cnt_words + chk_words + s_total + 32) * 8);
+  // a kept forward (batch of one, inputs kept, no cotangents) gets a
+  // workspace of its own, handed to the state at the end
+  const bool keep = items.size() == 1 && items[0].keep_state && items[0].keep_inputs && !items[0].gXn &&
+                    !items[0].gYn;
+  const ftn_tensor in_x = items[0].X, in_y = items[0].Y;
+  DevBuf own(ctx);
+  const size_t ws_bytes = (size_t)(total + cnt_words + chk_words + s_total + 32) * 8;
+  if (keep) own.p = dev_alloc(ctx, ws_bytes);
+  double* ws = keep ? (double*)own.p : (double*)workspace(ctx, ws_bytes);
   if (!ws) return set_error(FTN_ENOMEM, "workspace allocation failed");
   for (CJob& J : jobs) J.ws = ws + J.ws_off;
   int* cnt = (int*)(ws + total);
@@ -2427,7 +2449,57 @@ ftn_status compress_batch(ftn_ctx ctx, std::vector<CompressItem>& items) {
     J.it->X = J.Xn;
     J.it->Y = J.Yn;
   }
+  if (keep) {
+    CompressState* st = new CompressState;
+    st->ctx = ctx;
+    st->item = items[0];
+    st->item.X = in_x;
+    st->item.Y = in_y;
+    st->item.keep_state = nullptr;
+    st->item.info = nullptr;
+    st->xn_numel = jobs[0].Xn->numel, st->yn_numel = jobs[0].Yn->numel;
+    st->xn_parity = jobs[0].Xn->parity, st->yn_parity = jobs[0].Yn->parity;
+    st->jobs = std::move(jobs);
+    st->jobs[0].it = &st->item;
+    st->jobs[0].Xn = st->jobs[0].Yn = nullptr;  // the compressed pair belongs to the caller
+    st->buf = own.p;
+    own.p = nullptr;
+    st->sv = sv_host;
+    st->sbuf = sbuf;
+    *items[0].keep_state = st;
+  }
   return FTN_OK;
+}
+
+ftn_status compress_backward(ftn_ctx ctx, CompressState* st, ftn_tensor gXn, ftn_tensor gYn, ftn_tensor* dX,
+                             ftn_tensor* dY) {
+  if (!ctx || !st || !gXn || !gYn || !dX || !dY) return set_error(FTN_EINVAL, "null argument");
+  if (st->ctx != ctx) return set_error(FTN_EINVAL, "compression adjoint: state of another context");
+  if (gXn->dtype != FTN_F64 || gYn->dtype != FTN_F64 || gXn->numel != st->xn_numel || gYn->numel != st->yn_numel ||
+      gXn->parity != st->xn_parity || gYn->parity != st->yn_parity)
+    return set_error(FTN_ESHAPE, "compression adjoint: a cotangent does not match the compressed pair");
+  st->item.gXn = gXn;
+  st->item.gYn = gYn;
+  st->item.dX = st->item.dY = nullptr;
+  std::vector<CJob*> gj{&st->jobs[0]};
+  const ftn_status s = cj_backward(ctx, gj, st->sv, st->sbuf);
+  st->item.gXn = st->item.gYn = nullptr;
+  if (s != FTN_OK) {
+    ftn_tensor_free(st->item.dX);
+    ftn_tensor_free(st->item.dY);
+    st->item.dX = st->item.dY = nullptr;
+    return s;
+  }
+  *dX = st->item.dX;
+  *dY = st->item.dY;
+  st->item.dX = st->item.dY = nullptr;
+  return FTN_OK;
+}
+
+void free_compress_state(CompressState* st) {
+  if (!st) return;
+  if (st->buf) dev_free(st->ctx, st->buf);
+  delete st;
 }
 
 ftn_status compress_impl(ftn_ctx ctx, ftn_tensor* pX, ftn_tensor* pY, int n, const int* ax, const int* ay, int chi,

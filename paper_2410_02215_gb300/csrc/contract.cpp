@@ -512,6 +512,7 @@ ftn_status contract_grad_impl(ftn_ctx ctx, const ftn_network* net, const ftn_tre
     int ax[MAXR], ay[MAXR];
     uint64_t fa, fb;
     int chi, arrows;
+    CompressState* st;  // compression: its forward, kept for the adjoint (taped walks)
   };
   // Every tensor made here (the leaves' views included) is in `owned` until
   // it is freed, every cotangent in `g`; both are released on every return.
@@ -545,6 +546,7 @@ ftn_status contract_grad_impl(ftn_ctx ctx, const ftn_network* net, const ftn_tre
     for (int i = 0; i < op.n; ++i) op.ax[i] = items[0].ax[i], op.ay[i] = items[0].ay[i];
     op.chi = items[0].chi;
     op.arrows = items[0].arrows;
+    if (tape) items[0].keep_state = &op.st;  // the adjoint reuses this forward instead of recomputing it
     FTN_TRY(compress_batch(ctx, items));
     consumed.push_back(op.a);
     consumed.push_back(op.b);
@@ -557,6 +559,13 @@ ftn_status contract_grad_impl(ftn_ctx ctx, const ftn_network* net, const ftn_tre
     E.compress_done(x, y, items[0]);
     if (tape) tape->push_back(op);
     return FTN_OK;
+  };
+  struct TapeStates {  // kept compression states not yet consumed (an early return)
+    std::vector<Op>* t = nullptr;
+    ~TapeStates() {
+      if (t)
+        for (Op& o : *t) free_compress_state(o.st);
+    }
   };
   auto run_step = [&](int s, std::vector<Op>* tape) -> ftn_status {
     int64_t a, b;
@@ -636,6 +645,8 @@ ftn_status contract_grad_impl(ftn_ctx ctx, const ftn_network* net, const ftn_tre
     // replay segment j from its checkpoint, keeping its operands
     E.load(snaps[j]);
     std::vector<Op> tape;
+    TapeStates tape_states;
+    tape_states.t = &tape;
     consumed.clear();
     const int s_end = std::min(S, (j + 1) * k);
     for (int s = j * k; s < s_end; ++s) FTN_TRY(run_step(s, &tape));
@@ -673,7 +684,7 @@ ftn_status contract_grad_impl(ftn_ctx ctx, const ftn_network* net, const ftn_tre
       }
     }
     for (auto it = tape.rbegin(); it != tape.rend(); ++it) {
-      const Op& op = *it;
+      Op& op = *it;
       if (op.td) {
         ftn_tensor G = nullptr, dA = nullptr, dB = nullptr;
         FTN_TRY(cot(op.c, &G));
@@ -686,7 +697,13 @@ ftn_status contract_grad_impl(ftn_ctx ctx, const ftn_network* net, const ftn_tre
         ftn_tensor gx = nullptr, gy = nullptr, dX = nullptr, dY = nullptr;
         FTN_TRY(cot(op.c, &gx));
         FTN_TRY(cot(op.d, &gy));
-        FTN_TRY(ftn_compress_grad(ctx, op.a, op.b, op.n, op.ax, op.ay, op.chi, op.arrows, gx, gy, &dX, &dY));
+        if (op.st) {
+          FTN_TRY(compress_backward(ctx, op.st, gx, gy, &dX, &dY));
+          free_compress_state(op.st);
+          op.st = nullptr;
+        } else {
+          FTN_TRY(ftn_compress_grad(ctx, op.a, op.b, op.n, op.ax, op.ay, op.chi, op.arrows, gx, gy, &dX, &dY));
+        }
         release(op.c);
         release(op.d);
         FTN_TRY(put(op.a, dX));
