@@ -362,6 +362,24 @@ FTN_API ftn_status ftn_contract(ftn_ctx ctx, const ftn_network* net, const ftn_t
 FTN_API ftn_status ftn_contract_batch(ftn_ctx ctx, int count, const ftn_network* nets, const ftn_tree* trees,
                               ftn_prec prec, double* mantissa, double* log_scale);
 
+/* ftn_contract_batch with the values left on the device and no host
+ * synchronisation: d_out (2 * count doubles of device memory, owned by the
+ * caller) receives d_out[2 i] = the mantissa of network i (its sign
+ * included) and d_out[2 i + 1] = its natural-log scale, written in the order
+ * of ctx's stream.  The call may be captured into a CUDA graph on ctx's
+ * stream (stream capture) -- all local terms of many networks replayed as one
+ * graph launch -- provided every contraction's plan already exists on this
+ * context (each network contracted once before, same shapes) and no
+ * compression runs (a compression reads its kept dimensions back to the
+ * host); otherwise FTN_EUNSUPPORTED, and the capture holds a partial graph
+ * that must not be replayed.  Tables uploaded during a capture come from
+ * pinned host copies that the context keeps until it is destroyed; a graph
+ * reads the networks' tensors at replay, so it stays valid while they and
+ * the context live (their values may change between replays).  Errors
+ * otherwise as ftn_contract_batch. */
+FTN_API ftn_status ftn_contract_batch_async(ftn_ctx ctx, int count, const ftn_network* nets, const ftn_tree* trees,
+                                    ftn_prec prec, double* d_out);
+
 /* Value of a closed network of even FP64 tensors and its gradient with
  * respect to every tensor of the network (each tensor an independent input,
  * a bra that is the dagger of a ket included): *value = v (plain FP64, no

@@ -101,9 +101,9 @@ struct ResultJob {
   const void* value;  // rank-0 data, or null (no allowed entry: the value is 0)
   const double* logacc;
   int32_t f64;
-  int32_t pad_;
+  int32_t sign;  // the walk's sign (+1 or -1)
 };
-// out[2 i] = value, out[2 i + 1] = log-scale accumulator
+// out[2 i] = sign * value, out[2 i + 1] = log-scale accumulator
 ftn_status launch_gather_results(ftn_ctx ctx, const ResultJob* d_jobs, int njobs, double* out);
 
 // ---- batched operations ------------------------------------------------------------

@@ -194,6 +194,10 @@ struct ftn_ctx_s {
   size_t cached_bytes = 0;
   // host buffer for the tables of batched launches (staging_begin)
   std::vector<uint8_t> stage;
+  // pinned copies of the tables uploaded while the stream is captured into a
+  // CUDA graph (the graph's copy nodes read them at every replay); freed with
+  // the context
+  std::vector<void*> graph_host;
   // per-launch profiling (ftn_ctx_profile)
   bool prof_on = false;
   std::vector<ftn_prof_rec> prof;
@@ -240,6 +244,12 @@ void release_cached_blocks(ftn_ctx ctx);
 // Workspace of at least `bytes` (contents undefined), valid until the next
 // call that asks for workspace on the same context.
 void* workspace(ftn_ctx ctx, size_t bytes);
+// Whether work on the stream is being captured into a CUDA graph.
+bool stream_capturing(cudaStream_t s);
+// The host source of a host-to-device copy: the buffer itself, or while the
+// context's stream is captured, a pinned copy kept until the context goes
+// (null if that allocation fails).
+const void* capture_source(ftn_ctx ctx, const void* host, size_t bytes);
 
 inline int popc(uint32_t x) { return __builtin_popcount(x); }
 inline uint32_t block_mask(int rank, int parity, int64_t b) {

@@ -1950,6 +1950,8 @@ struct CompressState {
 ftn_status compress_batch(ftn_ctx ctx, std::vector<CompressItem>& items) {
   if (!ctx) return set_error(FTN_EINVAL, "null argument");
   if (items.empty()) return FTN_OK;
+  if (stream_capturing(ctx->stream))  // the kept dimensions are read back to the host
+    return set_error(FTN_EUNSUPPORTED, "compression cannot run while the stream is captured into a graph");
   std::vector<CJob> jobs(items.size());
   int64_t total = 0;
   for (size_t i = 0; i < items.size(); ++i) {

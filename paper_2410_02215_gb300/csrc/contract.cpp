@@ -364,12 +364,12 @@ ftn_status compress_lists(ftn_ctx ctx, std::vector<Exec*>& nets,
 
 }  // namespace
 
-ftn_status contract_batch_impl(ftn_ctx ctx, int count, const ftn_network* nets, const ftn_tree* trees, ftn_prec prec,
-                               double* mantissa, double* log_scale) {
-  if (!ctx || count < 0 || (count > 0 && (!nets || !trees || !mantissa || !log_scale)))
-    return set_error(FTN_EINVAL, "null argument");
-  if (count == 0) return FTN_OK;
-  if (!prec_valid(prec)) return set_error(FTN_EINVAL, "bad precision");
+// Every network walked in lock step; d_out[2 i] = sign x mantissa and
+// d_out[2 i + 1] = log-scale of network i, written on the device in stream
+// order (no host synchronisation, so the call can be captured into a graph
+// when every plan exists and no compression runs).
+static ftn_status contract_batch_run(ftn_ctx ctx, int count, const ftn_network* nets, const ftn_tree* trees,
+                                     ftn_prec prec, double* d_out) {
   std::vector<std::unique_ptr<Exec>> ex(count);
   int max_steps = 0;
   for (int i = 0; i < count; ++i) {
@@ -450,28 +450,47 @@ ftn_status contract_batch_impl(ftn_ctx ctx, int count, const ftn_network* nets, 
     res[i].value = last->numel ? last->data : nullptr;
     res[i].logacc = (const double*)state(i);
     res[i].f64 = last->dtype == FTN_F64 ? 1 : 0;
-    res[i].pad_ = 0;
+    res[i].sign = E.sign;
   }
-  // [result jobs | two doubles per network] in one device buffer, one copy back
-  const size_t jb = ((size_t)count * sizeof(ResultJob) + 255) & ~(size_t)255;
-  void* d_res = dev_alloc(ctx, jb + (size_t)count * 16);
-  if (!d_res) return set_error(FTN_ENOMEM, "device allocation failed");
   struct Guard2 {
     ftn_ctx c;
     void* p;
     ~Guard2() { dev_free(c, p); }
-  } guard2{ctx, d_res};
-  FTN_CUDA(cudaMemcpyAsync(d_res, res.data(), (size_t)count * sizeof(ResultJob), cudaMemcpyHostToDevice, ctx->stream));
-  double* d_out = (double*)((char*)d_res + jb);
-  FTN_TRY(launch_gather_results(ctx, (const ResultJob*)d_res, count, d_out));
+  } guard2{ctx, nullptr};
+  FTN_TRY(upload_table(ctx, res.data(), (size_t)count * sizeof(ResultJob), &guard2.p));
+  return launch_gather_results(ctx, (const ResultJob*)guard2.p, count, d_out);
+}
+
+ftn_status contract_batch_impl(ftn_ctx ctx, int count, const ftn_network* nets, const ftn_tree* trees, ftn_prec prec,
+                               double* mantissa, double* log_scale) {
+  if (!ctx || count < 0 || (count > 0 && (!nets || !trees || !mantissa || !log_scale)))
+    return set_error(FTN_EINVAL, "null argument");
+  if (count == 0) return FTN_OK;
+  if (!prec_valid(prec)) return set_error(FTN_EINVAL, "bad precision");
+  void* d_out = dev_alloc(ctx, (size_t)count * 16);
+  if (!d_out) return set_error(FTN_ENOMEM, "device allocation failed");
+  struct Guard {
+    ftn_ctx c;
+    void* p;
+    ~Guard() { dev_free(c, p); }
+  } guard{ctx, d_out};
+  FTN_TRY(contract_batch_run(ctx, count, nets, trees, prec, (double*)d_out));
   std::vector<double> host(2 * (size_t)count);
   FTN_CUDA(cudaMemcpyAsync(host.data(), d_out, host.size() * 8, cudaMemcpyDeviceToHost, ctx->stream));
   FTN_CUDA(cudaStreamSynchronize(ctx->stream));
   for (int i = 0; i < count; ++i) {
-    mantissa[i] = host[2 * i] * ex[i]->sign;
+    mantissa[i] = host[2 * i];
     log_scale[i] = host[2 * i + 1];
   }
   return FTN_OK;
+}
+
+ftn_status contract_batch_async_impl(ftn_ctx ctx, int count, const ftn_network* nets, const ftn_tree* trees,
+                                     ftn_prec prec, double* d_out) {
+  if (!ctx || count < 0 || (count > 0 && (!nets || !trees || !d_out))) return set_error(FTN_EINVAL, "null argument");
+  if (count == 0) return FTN_OK;
+  if (!prec_valid(prec)) return set_error(FTN_EINVAL, "bad precision");
+  return contract_batch_run(ctx, count, nets, trees, prec, d_out);
 }
 
 // ---- gradient of a network's value (ftn_contract_grad) ----------------------
@@ -849,6 +868,11 @@ ftn_status ftn_contract_grad(ftn_ctx ctx, const ftn_network* net, const ftn_tree
 ftn_status ftn_contract_batch(ftn_ctx ctx, int count, const ftn_network* nets, const ftn_tree* trees, ftn_prec prec,
                               double* mantissa, double* log_scale) {
   return contract_batch_impl(ctx, count, nets, trees, prec, mantissa, log_scale);
+}
+
+ftn_status ftn_contract_batch_async(ftn_ctx ctx, int count, const ftn_network* nets, const ftn_tree* trees,
+                                    ftn_prec prec, double* d_out) {
+  return contract_batch_async_impl(ctx, count, nets, trees, prec, d_out);
 }
 
 ftn_status ftn_hubbard_term(ftn_ctx ctx, int kind, double t, double u, ftn_dtype dtype, ftn_tensor* out) {

@@ -236,7 +236,7 @@ __global__ void gather_results_kernel(const ResultJob* __restrict__ jobs, int nj
     const ResultJob J = jobs[i];
     double v = 0.0;
     if (J.value) v = J.f64 ? *reinterpret_cast<const double*>(J.value) : (double)*reinterpret_cast<const float*>(J.value);
-    out[2 * i] = v;
+    out[2 * i] = J.sign < 0 ? -v : v;
     out[2 * i + 1] = *J.logacc;
   }
 }

@@ -1,5 +1,6 @@
 // Context, tensor objects (packed sector table), allocation and error handling.
 #include <algorithm>
+#include <cstring>
 #include <cstdio>
 #include <mutex>
 
@@ -191,10 +192,32 @@ ftn_status make_tensor(ftn_ctx ctx, int rank, const int32_t* d0, const int32_t* 
   return FTN_OK;
 }
 
+bool stream_capturing(cudaStream_t s) { return capturing(s); }
+
+const void* capture_source(ftn_ctx ctx, const void* host, size_t bytes) {
+  if (!bytes || !capturing(ctx->stream)) return host;
+  // a pinned allocation is not a stream operation: allowed on this thread
+  // for the duration of the call in relaxed capture mode
+  cudaStreamCaptureMode mode = cudaStreamCaptureModeRelaxed;
+  cudaThreadExchangeStreamCaptureMode(&mode);
+  void* p = nullptr;
+  const cudaError_t e = cudaHostAlloc(&p, bytes, cudaHostAllocDefault);
+  cudaThreadExchangeStreamCaptureMode(&mode);
+  if (e != cudaSuccess) {
+    (void)cudaGetLastError();
+    return nullptr;
+  }
+  std::memcpy(p, host, bytes);
+  ctx->graph_host.push_back(p);
+  return p;
+}
+
 ftn_status upload_table(ftn_ctx ctx, const void* host, size_t bytes, void** dev) {
   *dev = dev_alloc(ctx, bytes);
   if (!*dev) return set_error(FTN_ENOMEM, "device allocation failed (table)");
-  if (bytes) FTN_CUDA(cudaMemcpyAsync(*dev, host, bytes, cudaMemcpyHostToDevice, ctx->stream));
+  const void* src = capture_source(ctx, host, bytes);
+  if (!src) return set_error(FTN_ENOMEM, "pinned host allocation failed (table under stream capture)");
+  if (bytes) FTN_CUDA(cudaMemcpyAsync(*dev, src, bytes, cudaMemcpyHostToDevice, ctx->stream));
   return FTN_OK;
 }
 
@@ -536,6 +559,7 @@ ftn_status ftn_ctx_destroy(ftn_ctx ctx) {
   dev_free(ctx, ctx->dev_err);
   release_cached_blocks(ctx);
   cudaStreamSynchronize(ctx->stream);
+  for (void* p : ctx->graph_host) cudaFreeHost(p);
   delete ctx;
   return FTN_OK;
 }

@@ -581,6 +581,9 @@ ftn_status get_plan(ftn_ctx ctx, const ftn_tensor_s* A, const ftn_tensor_s* B, i
     if (fresh) *fresh = false;
     return FTN_OK;
   }
+  if (stream_capturing(ctx->stream))
+    return set_error(FTN_EUNSUPPORTED, "a contraction's plan is not built while the stream is captured: run the "
+                                       "contraction once before capturing it");
   FTN_TRY(build_plan(ctx, A, B, n, ax, ay, fa, fb, out_perm, prec, P));
   if (cache.size() > 65536) cache.clear();
   cache[key] = P;

@@ -89,6 +89,7 @@ def lib():
         "ftn_contract": [vp, C.POINTER(Network), C.POINTER(Tree), C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double)],
         "ftn_contract_batch": [vp, C.c_int, C.POINTER(Network), C.POINTER(Tree), C.c_int, C.POINTER(C.c_double),
                                C.POINTER(C.c_double)],
+        "ftn_contract_batch_async": [vp, C.c_int, C.POINTER(Network), C.POINTER(Tree), C.c_int, vp],
         "ftn_contract_grad": [vp, C.POINTER(Network), C.POINTER(Tree), C.c_int, C.POINTER(C.c_double), C.POINTER(vp)],
         "ftn_hubbard_term": [vp, C.c_int, C.c_double, C.c_double, C.c_int, C.POINTER(vp)],
         "ftn_energy_reduce": [C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double), C.c_int, i32p, i32p, C.c_int,
@@ -688,6 +689,21 @@ def contract_batch(ctx, networks, prec="f64"):
     _check(lib().ftn_contract_batch(ctx.handle, n, net_arr, tree_arr, _prec(prec), m, lg))
     del keep
     return [(m[i], lg[i]) for i in range(n)]
+
+
+def contract_batch_async(ctx, networks, d_out, prec="f64"):
+    """ftn_contract_batch_async: the values of ``networks`` (as for
+    :func:`contract_batch`) written on the device into ``d_out`` (a float64
+    CUDA tensor of at least 2 * len(networks) elements: mantissa with its
+    sign, then log-scale, per network), in stream order and without a host
+    synchronisation; capturable into a CUDA graph on ctx's stream once every
+    network has been contracted on this context."""
+    n, net_arr, tree_arr, keep = _network_arrays(networks)
+    torch = ctx._torch
+    if d_out.dtype != torch.float64 or not d_out.is_cuda or not d_out.is_contiguous() or d_out.numel() < 2 * n:
+        raise ValueError("d_out must be a contiguous float64 CUDA tensor of at least 2 * len(networks) elements")
+    _check(lib().ftn_contract_batch_async(ctx.handle, n, net_arr, tree_arr, _prec(prec), C.c_void_p(d_out.data_ptr())))
+    del keep
 
 
 def _terms(num, den, group_end):
