@@ -277,6 +277,27 @@ def one_step(F, ctx, cases, ins, outs, prec, tag=False):
         outs[c["name"]] = r
 
 
+def copy_reference_ms(torch, traffic_bytes, flush, reps=10):
+    """A plain device copy (torch's copy kernel) of traffic_bytes / 2 bytes,
+    so traffic_bytes of reads and writes, L2 flushed before each: CUDA-event
+    ms per copy, the mean of `reps` after two warm-up copies.  The size-matched
+    scale for a sign-permute of the same algorithmic bytes (the measured HBM
+    peak comes from a 2 GiB copy, whose fixed costs vanish)."""
+    n = max(int(traffic_bytes) // 2, 1)
+    src = torch.ones(n, dtype=torch.uint8, device="cuda")
+    dst = torch.empty_like(src)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+    for _ in range(2):
+        dst.copy_(src)
+    for a, b in ev:
+        flush.zero_()
+        a.record()
+        dst.copy_(src)
+        b.record()
+    torch.cuda.synchronize()
+    return sum(a.elapsed_time(b) for a, b in ev) / reps
+
+
 def time_steps(F, ctx, torch, cases, prec, steps, warmup, flush, world, profile=False, graph=False):
     """Times `steps` steps (L2 flushed before each, outside the events).
     Eager: one library call per contraction per step.  profile=True adds a
@@ -1070,6 +1091,14 @@ def run_ours(args, rank, world, local):
                           "gbs": r["bytes"] / (r["ms"] / 1e3) / 1e9 if r["ms"] else None,
                           "tflops": r["flops"] / (r["ms"] / 1e3) / 1e12 if r["ms"] and r["flops"] else None}
                          for r in prof]
+    # each sign-permute beside a plain copy of the same bytes (cold L2)
+    copy_ms = {}
+    for k, r in zip(result["kernels"], prof):
+        if r["label"].endswith("/permute") and r["bytes"] and r["launches"]:
+            b = int(r["bytes"] / r["launches"])
+            if b not in copy_ms:
+                copy_ms[b] = copy_reference_ms(torch, b, flush)
+            k["copy_ms_per_launch_same_bytes"] = copy_ms[b]
     if clocks:
         result["clocks"] = clocks
     # the other precisions of the same step, and their errors
