@@ -933,7 +933,8 @@ def diamond_graph(F, torch, nets, num, den, ge, prec, streams, chunk, evals, ene
             c.close()
 
 
-def diamond_bench(F, ctx, torch, evals, streams, with_oracle, rank=0, world=1, batches=(0, 8, 32), graphs=True):
+def diamond_bench(F, ctx, torch, evals, streams, with_oracle, rank=0, world=1, batches=(0, 8, 32), graphs=True,
+                  kernels=False):
     """Energy evaluations per second of the 64-site diamond (radius-1 cluster
     approximation of all 150 terms), FP64 and mixed, with their errors; the
     term networks are split across ranks when world > 1 (dist.energy_sharded:
@@ -992,6 +993,9 @@ def diamond_bench(F, ctx, torch, evals, streams, with_oracle, rank=0, world=1, b
                      "energy": en[0], "energy_per_site": en[0] / n, "batch": best,
                      "gpu_launches_per_eval": (sum(c.launches() for c in ctxs) - l0) / evals,
                      "trial_s_per_eval_by_batch": {str(b): round(v, 4) for b, v in trial.items()}}
+        if kernels and prec in ("f64", "f16x3"):
+            out[prec]["kernel_breakdown_one_stream"] = kernel_breakdown(
+                torch, lambda: F.energy(ctx, nets, num, den, ge, prec, best), top=14)
         if world == 1 and graphs:
             try:
                 out[prec]["graph"] = diamond_graph(F, torch, nets, num, den, ge, prec, len(ctxs), max(best, 1),
@@ -1129,7 +1133,8 @@ def run_ours(args, rank, world, local):
         result["gradient"] = gradient_bench(F, ctx, args.gradient_evals, kernels=args.gradient_kernels)
     if not args.no_diamond:
         result["energy_diamond"] = diamond_bench(F, ctx, torch, args.diamond_evals, args.cluster_streams,
-                                                 rank == 0 and world == 1 and not args.no_cpu, rank, world)
+                                                 rank == 0 and world == 1 and not args.no_cpu, rank, world,
+                                                 kernels=args.diamond_kernels)
     if rank == 0 and world == 1 and not args.no_cpu:
         result["cpu_baseline"] = cpu_baseline(cases)
     ctx.synchronize()
@@ -1169,6 +1174,9 @@ def main():
     ap.add_argument("--gradient-kernels", action="store_true",
                     help="add a per-kernel device-time breakdown of one gradient (torch profiler)")
     ap.add_argument("--diamond-evals", type=int, default=2)
+    ap.add_argument("--diamond-kernels", action="store_true",
+                    help="add a per-kernel device-time breakdown of one diamond evaluation on one stream "
+                         "(torch profiler)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
