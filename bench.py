@@ -772,8 +772,9 @@ def kernel_breakdown(torch, fn, top=12):
 
 
 def gradient_bench(F, ctx, evals, samples=20, h=1e-6, kernels=False):
-    """Gradient evaluations per second of the compressed norm network (the
-    config-5 workload) through ftn_contract_grad with checkpointed
+    """Gradient evaluations per second of the compressed norm network (6x6
+    open lattice, D=4, boundary-MPS row sweep, chi=48) through
+    ftn_contract_grad with checkpointed
     recomputation (the walk's state kept every ceil(sqrt(steps)) steps, each
     segment replayed in the backward) and with every intermediate kept; the
     library's peak device memory of each (its allocations routed through

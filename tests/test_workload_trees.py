@@ -1,4 +1,4 @@
-"""The boundary-MPS row sweep (the config-5 gradient's tree): a valid SSA tree
+"""The boundary-MPS row sweep (the tree of the 6 x 6 gradient): a valid SSA tree
 for open lattices up to 6 x 6 -- every input and every intermediate consumed
 exactly once, one tensor left -- whose column structure is the one its
 docstring states; and, on a 2 x 3 lattice, the exact network value along it
